@@ -1,0 +1,96 @@
+"""The whole loop-estimate path on one gauge configuration, step by step (Sec. 5, 7).
+
+Test infrastructure (see ``oracle/__init__.py``).
+
+  1. special right-hand side b0 = Z(4) noise NOISE_SPECIAL:
+       GMRES-DR(m, k) on M   -> deflation space (V_{k+1}, Hbar_k) for GMRES-Proj,
+       MINRES-DR(m, k) on M' -> Q = k eigenpairs (lambda'_q, e'_q) of M' for HFES;
+  2. Min-Res polynomial coefficients a from the noise NOISE_POLY (Sec. 5.2);
+  3. hopping traces t_k by probing (Sec. 5.1); 1/xi'_q for HFPS and HFPOLY (Sec. 5.5);
+  4. for every noise n: eta = Z(4) noise n, x = M^{-1} eta by GMRES-Proj, and for every mode the
+     subtraction vector tilde x; the noise terms eta^dag Theta (x - tilde x) per timeslice;
+  5. add-backs and the summary (mean, error bar) per mode and operator.
+"""
+import time
+
+import numpy as np
+
+from . import estimate as E
+from . import krylov as Kr
+from . import lattice as L
+from . import operators as O
+from . import rng
+from . import subtract as S
+
+
+def setup(U, kappa, dims, seed, m, k, K, npoly, tol_special, max_cycles=2000):
+    A = lambda v: L.flat(L.wilson(U, kappa, L.unflat(v, dims)))
+    Ap = lambda v: L.flat(L.wilson_g5(U, kappa, L.unflat(v, dims)))
+    b0 = L.flat(rng.z4_noise(seed, rng.NOISE_SPECIAL, dims))
+    _, info_m, defl_m = Kr.gmres_dr(A, b0, m, k, tol_special, max_cycles)
+    _, info_h, defl_h = Kr.gmres_dr(Ap, b0, m, k, tol_special, max_cycles, hermitian=True)
+    lam, Ev, eres = Kr.ritz_pairs(defl_h, hermitian=True)
+    Af = lambda f: L.wilson(U, kappa, f)
+    a = S.poly_coeffs(Af, rng.z4_noise(seed, rng.NOISE_POLY, dims), npoly)
+    t = S.hop_traces(U, kappa, max(K, npoly + 1), dims)
+    pert = lambda f: S.hop_series(U, kappa, f, K)
+    poly = lambda f: S.poly_apply(Af, a, f)
+    xi_p = S.xi_inverse(Ev, pert, dims)
+    xi_q = S.xi_inverse(Ev, poly, dims)
+    return dict(A=A, defl_m=defl_m, info_m=info_m, info_h=info_h, lam=lam, Ev=Ev, eig_resid=eres,
+                a=a, b=S.a_to_b(a), t=t, xi_pert=xi_p, xi_poly=xi_q, pert=pert, poly=poly)
+
+
+def addbacks(U, kappa, dims, st, K):
+    lam, Ev = st["lam"], st["Ev"]
+    add = dict(none=np.zeros((O.NOPS,) + L.site_shape(dims), dtype=np.complex128),
+               pert=S.pert_addback(st["t"], kappa, K),
+               poly=S.poly_addback(st["t"], kappa, st["b"]),
+               defl=S.defl_addback(U, kappa, Ev, 1 / lam, dims))
+    add["defl_pert"] = add["pert"] + S.defl_addback(U, kappa, Ev, 1 / lam - st["xi_pert"], dims)
+    add["defl_poly"] = add["poly"] + S.defl_addback(U, kappa, Ev, 1 / lam - st["xi_poly"], dims)
+    return add
+
+
+def subtraction_vector(mode, st, eta):
+    lam, Ev = st["lam"], st["Ev"]
+    if mode == "none":
+        return np.zeros_like(eta)
+    if mode == "pert":
+        return st["pert"](eta)
+    if mode == "poly":
+        return st["poly"](eta)
+    if mode == "defl":
+        return S.defl_vector(Ev, 1 / lam, eta)
+    if mode == "defl_pert":
+        return st["pert"](eta) + S.defl_vector(Ev, 1 / lam - st["xi_pert"], eta)
+    if mode == "defl_poly":
+        return st["poly"](eta) + S.defl_vector(Ev, 1 / lam - st["xi_poly"], eta)
+    raise ValueError(mode)
+
+
+def solve_noises(st, dims, seed, first, count, m_inner, tol, max_cycles=2000):
+    xs, infos = [], []
+    for n in range(first, first + count):
+        eta = L.flat(rng.z4_noise(seed, n, dims))
+        x, info = Kr.gmres_proj(st["A"], eta, st["defl_m"], m_inner, tol, max_cycles)
+        xs.append(L.unflat(x, dims))
+        infos.append(info)
+    return np.stack(xs), infos
+
+
+def loop_estimate(U, kappa, dims, seed, nnoise, m, k, K, npoly, tol, tol_special, modes=E.MODES):
+    """Run steps 1-5; returns (results per mode, setup state, timing)."""
+    t0 = time.perf_counter()
+    st = setup(U, kappa, dims, seed, m, k, K, npoly, tol_special)
+    add = addbacks(U, kappa, dims, st, K)
+    t1 = time.perf_counter()
+    xs, infos = solve_noises(st, dims, seed, 0, nnoise, m - k, tol)
+    etas = rng.z4_block(seed, 0, nnoise, dims)
+    out = {}
+    for mode in modes:
+        ws = xs - np.stack([subtraction_vector(mode, st, e) for e in etas])
+        out[mode] = E.summarize(E.noise_terms(U, kappa, etas, ws), O.per_t(add[mode]))
+        out[mode]["addback_t"] = O.per_t(add[mode])
+    t2 = time.perf_counter()
+    return out, st, dict(setup_s=t1 - t0, noise_s=t2 - t1, solve_infos=infos)

@@ -1,0 +1,154 @@
+"""Subtraction matrices tilde M^{-1} of Sec. 5 and their trace add-backs.
+
+Test infrastructure (see ``oracle/__init__.py``).
+
+  PS      tilde x = sum_{k=0}^{K-1} (kappa P)^k eta            (Sec. 5.1; "seventh order" = K = 7 terms)
+  POLY    tilde x = sum_{j=0}^{n} a_j M^j eta, a from the Min-Res projection (Sec. 5.2)
+  HFES    tilde x = gamma_5 V' Lambda'^{-1} V'^dag eta          (Sec. 5.4)
+  HFPS /  tilde x = tilde x_{pert|poly} + gamma_5 V' (Lambda'^{-1} - Xi^{-1}) V'^dag eta,
+  HFPOLY  1/xi'_q = e'_q^dag gamma_5 tilde M^{-1}_{pert|poly} e'_q (Sec. 5.5, reading of tilde M'^{-1} = gamma_5 tilde M^{-1})
+
+Add-backs Tr(Theta tilde M^{-1}) (Sec. 5.1-5.5) are returned as per-site densities over the base
+site of each operator (see ``operators.densities``).  The hopping traces t_k(Theta) = Tr(Theta P^k)
+are taken from the exact diagonal by probing: with probe vectors z_c = sum over a colour class
+of unit vectors e_i, every off-diagonal term e_i^dag Theta P^k e_j (i != j in one class) vanishes
+when distinct members of a class are further apart (taxicab, on the torus) than k + 1 hops, so
+sum_c densities(z_c, P^k z_c) is the exact diagonal density.  With every site its own class this
+is the paper's sum_i e_i^dag Theta tilde M^{-1} e_i (Sec. 5.1) term by term.
+"""
+import math
+
+import numpy as np
+
+from . import lattice as L
+from . import operators as O
+
+
+def hop_series(U, kappa, eta, K):
+    """PS: sum_{k=0}^{K-1} (kappa P)^k eta."""
+    term = eta.copy()
+    acc = eta.copy()
+    for _ in range(1, K):
+        term = kappa * L.hop(U, term)
+        acc = acc + term
+    return acc
+
+
+def poly_coeffs(A, b, n):
+    """Min-Res polynomial P_n(M) = sum_{j=0}^n a_j M^j (Eq. xyz646): a minimises ||b - M P_n(M) b||.
+    The paper writes the normal equations (v^dag v) a = v^dag b with v = (Mb, M^2 b, .., M^{n+1} b);
+    reading: their solution is computed by a Householder QR of v (same minimiser, stable)."""
+    cols = []
+    w = b.copy()
+    for _ in range(n + 1):
+        w = A(w)
+        cols.append(w.ravel())
+    v = np.stack(cols, axis=1)
+    Q, R = np.linalg.qr(v)
+    a = np.linalg.solve(R, Q.conj().T @ b.ravel())
+    return a
+
+
+def poly_apply(A, a, eta):
+    """POLY: sum_j a_j M^j eta, powers applied one after another."""
+    term = eta.copy()
+    acc = a[0] * eta
+    for j in range(1, len(a)):
+        term = A(term)
+        acc = acc + a[j] * term
+    return acc
+
+
+def a_to_b(a):
+    """Coefficients of the same polynomial in powers of kappa P (Sec. 5.2): with M = 1 - kappa P,
+    M^j = sum_k C(j, k) (-kappa P)^k, so b_k = (-1)^k sum_{j >= k} C(j, k) a_j.  (The text's
+    'M = I + kappa P' at this point contradicts Eq. xyz556; reading: Eq. xyz556 holds.)"""
+    n = len(a) - 1
+    b = np.zeros(n + 1, dtype=np.complex128)
+    for k in range(n + 1):
+        for j in range(k, n + 1):
+            b[k] += ((-1) ** k) * math.comb(j, k) * a[j]
+    return b
+
+
+def probe_classes(dims, spacing):
+    """Colour class of each site for probing with periods spacing = (px, py, pz, pt), each dividing
+    the extent: class = (x mod px, y mod py, z mod pz, t mod pt).  Returns (class_of_site (T,Z,Y,X), n_classes)."""
+    lx, ly, lz, lt = dims
+    px, py, pz, pt = spacing
+    t, z, y, x = np.meshgrid(np.arange(lt), np.arange(lz), np.arange(ly), np.arange(lx), indexing='ij')
+    cls = (x % px) + px * ((y % py) + py * ((z % pz) + pz * (t % pt)))
+    return cls, px * py * pz * pt
+
+
+def default_spacing(dims, K):
+    """Smallest period >= K + 1 dividing each extent (paths of up to K-1 hops plus the one hop of
+    a point-split operator then never join two members of a class), else the full extent."""
+    out = []
+    for l in dims:
+        p = l
+        for cand in range(K + 1, l):
+            if l % cand == 0:
+                p = cand
+                break
+        out.append(p)
+    return tuple(out)
+
+
+def hop_traces(U, kappa, K, dims, spacing=None, batch=256):
+    """Per-site densities of t_k(Theta) = Tr(Theta P^k) for k = 0..K-1 and all nine operators.
+    Returns t[k, op, T, Z, Y, X] (complex).  kappa only enters the point-split operators' own
+    kappa prefactor (Table Table903)."""
+    if spacing is None:
+        spacing = default_spacing(dims, K)
+    cls, ncls = probe_classes(dims, spacing)
+    out = np.zeros((K, O.NOPS) + L.site_shape(dims), dtype=np.complex128)
+    probes = [(c, a) for c in range(ncls) for a in range(12)]
+    for i0 in range(0, len(probes), batch):
+        chunk = probes[i0:i0 + batch]
+        z = np.zeros(L.field_shape(dims, (len(chunk),)), dtype=np.complex128)
+        for b_, (c, a) in enumerate(chunk):
+            z[b_][cls == c, a // 3, a % 3] = 1.0
+        w = z.copy()
+        for k in range(K):
+            if k > 0:
+                w = L.hop(U, w)
+            out[k] += O.densities(U, kappa, z, w).sum(axis=1)
+    return out
+
+
+def pert_addback(t, kappa, K):
+    """PS add-back densities: sum_{k<K} kappa^k t_k."""
+    return sum((kappa ** k) * t[k] for k in range(K))
+
+
+def poly_addback(t, kappa, b):
+    """POLY add-back densities: sum_k b_k kappa^k t_k."""
+    return sum(b[k] * (kappa ** k) * t[k] for k in range(len(b)))
+
+
+def defl_vector(E, dvals, eta):
+    """gamma_5 V' diag(dvals) V'^dag eta for fields eta (..., T, Z, Y, X, 4, 3); E is (N_dim, Q)."""
+    dims_shape = eta.shape[-6:]
+    ef = eta.reshape(eta.shape[:-6] + (-1,))
+    c = ef @ E.conj()                     # (..., Q) = V'^dag eta
+    y = (c * dvals) @ E.T                 # (..., N_dim)
+    return L.g5(y.reshape(eta.shape[:-6] + dims_shape))
+
+
+def defl_addback(U, kappa, E, dvals, dims):
+    """Densities of Tr(Theta gamma_5 V' diag(dvals) V'^dag) = sum_q dvals_q e'_q^dag Theta gamma_5 e'_q."""
+    out = np.zeros((O.NOPS,) + L.site_shape(dims), dtype=np.complex128)
+    for q in range(E.shape[1]):
+        e = L.unflat(E[:, q], dims)
+        out += dvals[q] * O.densities(U, kappa, e, L.g5(e))
+    return out
+
+
+def xi_inverse(E, apply_tilde, dims):
+    """1/xi'_q = e'_q^dag gamma_5 tilde M^{-1} e'_q for each eigenvector (Sec. 5.5)."""
+    out = np.zeros(E.shape[1], dtype=np.complex128)
+    for q in range(E.shape[1]):
+        e = L.unflat(E[:, q], dims)
+        out[q] = np.vdot(e, L.g5(apply_tilde(e)))
+    return out
