@@ -1,0 +1,270 @@
+/*
+ * lqcd.h -- C ABI of the GB300 (sm_103a) library for disconnected-loop noise estimation with
+ * deflation, perturbative and polynomial subtraction (Baral, Whyte, Wilcox, Morgan,
+ * "Disconnected Loop Subtraction Methods in Lattice QCD").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Complex numbers are interleaved FP64 pairs (re, im) ("complex128").  A spinor field of one
+ *  right-hand side is 12 V complex numbers in the canonical order
+ *        [T][Z][Y][X][spin 4][colour 3],  site s = x + Lx (y + Ly (z + Lz t)),
+ *  and a block of nrhs fields is nrhs such fields back to back.  Gauge links are
+ *        [mu 4][T][Z][Y][X][3][3]  complex128, mu = x, y, z, t, row-major colour matrices.
+ *  Gamma matrices: Euclidean Hermitian, Dirac representation,
+ *        gamma_k = [[0, -i sigma_k], [i sigma_k, 0]], gamma_4 = diag(1, 1, -1, -1),
+ *        gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4.
+ *  Boundary conditions are periodic in all four directions (Sec. 7).
+ *
+ *  Unless a parameter says "host", every array argument is a caller-owned DEVICE pointer on the
+ *  device that was current when the context was created, 16-byte aligned.  The library owns only
+ *  its internal workspace (held by the context) and the deflation-space objects it returns.
+ *  Calls are enqueued on the context's stream; a call that returns host data synchronises that
+ *  stream before returning.  No call aborts the process: every call returns an lqcd_status and,
+ *  on failure, lqcd_last_error_string(ctx) describes the first problem found.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LQCD_OK = 0,
+  LQCD_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, unsupported option            */
+  LQCD_ERR_NONFINITE = 2,     /* NaN or Inf found in an input or a solver iterate      */
+  LQCD_ERR_NOT_CONVERGED = 3, /* solver stopped at max_cycles above its tolerance      */
+  LQCD_ERR_TIMEOUT = 4,       /* a bounded device wait ran out                         */
+  LQCD_ERR_CUDA = 5,          /* a CUDA runtime call failed (message has the details)  */
+  LQCD_ERR_OOM = 6            /* workspace allocation failed                           */
+} lqcd_status;
+
+/* Arithmetic of an operator application.  F64 is the plain FP64 path. */
+typedef enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1 } lqcd_prec;
+
+/* lqcd_wilson_apply flags (may be OR-ed only where stated) */
+#define LQCD_APPLY_M 0     /* out = M in,  M = 1 - kappa P                      (Eq. xyz556) */
+#define LQCD_APPLY_G5R 1   /* out = M gamma_5 in  (M' of Sec. 5.4, Hermitian)                */
+#define LQCD_APPLY_DAG 2   /* out = M^dagger in = gamma_5 M gamma_5 in                      */
+#define LQCD_APPLY_HOP 3   /* out = P in  (the hopping matrix below Eq. xyz556)              */
+
+/* Which linear system a solver works on */
+#define LQCD_SYS_M 0       /* M x = b                                                       */
+#define LQCD_SYS_MG5 1     /* M gamma_5 y = b  (then x = gamma_5 y solves M x = b)          */
+
+/* Subtraction modes of Sec. 5 (bit mask for lqcd_loop_estimate) */
+#define LQCD_SUB_NONE (1 << 0)      /* NS                                                   */
+#define LQCD_SUB_PERT (1 << 1)      /* PS, Sec. 5.1                                         */
+#define LQCD_SUB_POLY (1 << 2)      /* POLY, Sec. 5.2                                       */
+#define LQCD_SUB_DEFL (1 << 3)      /* HFES, Sec. 5.4                                       */
+#define LQCD_SUB_DEFL_PERT (1 << 4) /* HFPS, Sec. 5.5                                       */
+#define LQCD_SUB_DEFL_POLY (1 << 5) /* HFPOLY, Sec. 5.5                                     */
+#define LQCD_SUB_ALL 63
+#define LQCD_NMODES 6
+#define LQCD_NOPS 9 /* 0 scalar, 1-4 local vector mu = x,y,z,t, 5-8 point-split mu = x,y,z,t */
+
+typedef struct lqcd_ctx lqcd_ctx;
+typedef struct lqcd_defl lqcd_defl;
+
+typedef struct {
+  int m;             /* Krylov subspace size per cycle (GMRES-DR(m, k))                      */
+  int k;             /* deflation size: harmonic Ritz vectors kept at restart (0 = GMRES(m)) */
+  double tol;        /* stop when ||b - A x|| <= tol ||b|| (relative true residual)          */
+  int max_cycles;    /* restart cycles before LQCD_ERR_NOT_CONVERGED                         */
+  int system;        /* LQCD_SYS_M or LQCD_SYS_MG5                                           */
+  int prec;          /* lqcd_prec of the inner operator; LQCD_PREC_F64 for the plain path    */
+} lqcd_krylov_opts;
+
+typedef struct {
+  int cycles;        /* restart cycles used (largest over the right-hand sides)              */
+  long matvecs;      /* operator applications, summed over right-hand sides                  */
+  int converged;     /* 1 when every right-hand side met tol                                 */
+  double true_resid; /* largest relative true residual over the right-hand sides (FP64)      */
+  double seconds;    /* wall time of the call                                                */
+} lqcd_solve_info;
+
+/* ---- context --------------------------------------------------------------------------- */
+
+/* Create a context for an Lx x Ly x Lz x Lt lattice (dims[0..3] = Lx, Ly, Lz, Lt, each >= 2) on
+ * the current CUDA device.  link_recon must be 18 (full links).  stream is a cudaStream_t (NULL
+ * = legacy default stream).  Returns LQCD_ERR_INVALID_ARG for bad dims, LQCD_ERR_CUDA if no
+ * device is usable. */
+lqcd_status lqcd_ctx_create(lqcd_ctx **ctx, const int dims[4], int link_recon, void *stream);
+lqcd_status lqcd_ctx_destroy(lqcd_ctx *ctx);
+lqcd_status lqcd_set_stream(lqcd_ctx *ctx, void *stream);
+/* Message of the last failure on this context ("" if none); valid until the next call. */
+const char *lqcd_last_error_string(const lqcd_ctx *ctx);
+/* Library version string (static storage). */
+const char *lqcd_version(void);
+/* Number of kernels this context has launched since creation (diagnostics). */
+long lqcd_kernel_launches(const lqcd_ctx *ctx);
+
+/* Per-kernel-class device timing (diagnostics; the paper has no counterpart).  While enabled,
+ * every kernel launched through this context is bracketed by CUDA events on the context's stream
+ * (a small per-launch cost).  lqcd_timing_read synchronises the stream and returns, for one class
+ * since the last reset, the summed device milliseconds, the launch count and the summed work
+ * units (may be NULL): site x right-hand-side pairs for WILSON, CONTRACT, NOISE and PROBE;
+ * complex multiply-adds for DOT, AXPY and COMBINE; complex elements for NORM and BLAS1. */
+#define LQCD_K_WILSON 0   /* Wilson operator (Eq. xyz556)                               */
+#define LQCD_K_DOT 1      /* batched inner products (Gram-Schmidt, projections)          */
+#define LQCD_K_AXPY 2     /* batched multi-vector updates                                */
+#define LQCD_K_COMBINE 3  /* basis rotations V P (restarts, Ritz vectors)                */
+#define LQCD_K_NORM 4     /* batched norms                                               */
+#define LQCD_K_CONTRACT 5 /* operator contractions (Sec. 6)                              */
+#define LQCD_K_BLAS1 6    /* copies, scalings, gamma_5, axpy                             */
+#define LQCD_K_NOISE 7    /* Z(4) noise generation                                       */
+#define LQCD_K_PROBE 8    /* probe-vector generation for the hopping traces              */
+#define LQCD_K_NCLASS 9
+lqcd_status lqcd_timing_enable(lqcd_ctx *ctx, int enable);
+lqcd_status lqcd_timing_reset(lqcd_ctx *ctx);
+lqcd_status lqcd_timing_read(lqcd_ctx *ctx, int cls, double *total_ms, long *launches, double *units);
+
+/* ---- a1: Z(4) noise (Sec. 2, 3) ------------------------------------------------------- */
+
+/* out[n] = Z(4) noise number first_noise + n, n < nrhs: entry (s, spin, colour) is
+ * {1, i, -1, -i}[(w >> 2c) & 3] with c = 3 spin + colour and w word 0 of Philox-4x32-10
+ * (Salmon et al., SC'11) with key (seed mod 2^32, seed >> 32) and counter (noise, s, 0, 0).
+ * out: device, nrhs * 12 V complex128.  Bit-exact. */
+lqcd_status lqcd_noise_z4(lqcd_ctx *ctx, uint64_t seed, uint32_t first_noise, int nrhs, double *out);
+
+/* ---- a2: Wilson operator (Eq. xyz556; Sec. 5.4) --------------------------------------- */
+
+/* out = A in for nrhs fields, A selected by flags (LQCD_APPLY_*).  links: device gauge field;
+ * in/out: device, nrhs * 12 V complex128, must not overlap.  prec must be LQCD_PREC_F64 or
+ * LQCD_PREC_F32 (FP32 arithmetic on FP64 data, for testing the inner operator). */
+lqcd_status lqcd_wilson_apply(lqcd_ctx *ctx, const double *links, double kappa, const double *in,
+                              double *out, int nrhs, int prec, int flags);
+
+/* ---- a3 / a4: GMRES-DR and MINRES-DR (Sec. 5.3, 7, 8) --------------------------------- */
+
+/* GMRES-DR(m, k) for nrhs independent right-hand sides (each with its own Krylov basis).
+ * b, x: device, nrhs * 12 V complex128 (x is overwritten; the initial guess is zero).
+ * opts->system selects M or M gamma_5.  If defl_out is not NULL and nrhs == 1, *defl_out
+ * receives the deflation space of the final cycle: V_{k+1} (12 V x (k+1)), Hbar_k
+ * ((k+1) x k) with A V_k = V_{k+1} Hbar_k, and the Rayleigh-Ritz eigenpairs of A on V_k;
+ * free it with lqcd_defl_destroy.  Host info may be NULL. */
+lqcd_status lqcd_gmresdr_solve(lqcd_ctx *ctx, const double *links, double kappa, const double *b,
+                               double *x, int nrhs, const lqcd_krylov_opts *opts,
+                               lqcd_solve_info *info, lqcd_defl **defl_out);
+
+/* MINRES-DR: the same cycle for the Hermitian M' = M gamma_5 (opts->system is ignored and taken
+ * as LQCD_SYS_MG5); the harmonic Ritz problem is solved in its Hermitian-definite form and the
+ * returned eigenpairs (lambda'_q, e'_q) are real / orthonormal (Sec. 5.4, 8). */
+lqcd_status lqcd_minresdr_solve(lqcd_ctx *ctx, const double *links, double kappa, const double *b,
+                                double *x, int nrhs, const lqcd_krylov_opts *opts,
+                                lqcd_solve_info *info, lqcd_defl **defl_out);
+
+/* ---- a5: deflated multi-RHS solves (GMRES-Proj, Sec. 5.3, 7) --------------------------- */
+
+/* Solve A x = b for nrhs right-hand sides with GMRES-Proj over defl (made by one of the two
+ * solvers above on the same A): each cycle is a minimum-residual projection over V_{k+1} and
+ * Hbar_k followed by GMRES(opts->m).  opts->k is ignored.  b, x: device (nrhs * 12 V). */
+lqcd_status lqcd_proj_solve(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl,
+                            const double *b, double *x, int nrhs, const lqcd_krylov_opts *opts,
+                            lqcd_solve_info *info);
+
+/* ---- deflation-space objects ------------------------------------------------------------ */
+
+lqcd_status lqcd_defl_destroy(lqcd_defl *defl);
+/* k and whether it came from the Hermitian solver (host outputs). */
+lqcd_status lqcd_defl_info(const lqcd_defl *defl, int *k, int *hermitian);
+/* Copy out, each optional (NULL skips):  V (device, (k+1) x 12V, vector-major), Hbar (host,
+ * (k+1) x k complex row-major), lam (host, k complex eigenvalues, increasing |lam|),
+ * E (device, k x 12V eigenvectors, vector-major), eig_resid (host, k doubles ||A e - lam e||). */
+lqcd_status lqcd_defl_export(const lqcd_defl *defl, double *V, double *Hbar, double *lam, double *E,
+                             double *eig_resid);
+/* Build a deflation object from caller data (e.g. eigenvectors from elsewhere): E (device,
+ * k x 12V orthonormal eigenvectors of M' = M gamma_5), lam (host, k complex).  Only usable for
+ * lqcd_deflate_project / lqcd_xi_inverse / lqcd_loop_estimate subtraction (no projection data). */
+lqcd_status lqcd_defl_import(lqcd_ctx *ctx, int k, const double *E, const double *lam,
+                             lqcd_defl **defl_out);
+
+/* ---- a6: deflation projection (HFES, Sec. 5.4) ----------------------------------------- */
+
+/* out = gamma_5 V' diag(d) V'^dagger eta for nrhs fields, V' the k eigenvectors of defl and d a
+ * host array of k complex weights (1/lambda' for HFES, 1/lambda' - 1/xi' for HFPS/HFPOLY).
+ * eta, out: device, nrhs * 12 V. */
+lqcd_status lqcd_deflate_project(lqcd_ctx *ctx, const lqcd_defl *defl, const double *eta,
+                                 double *out, int nrhs, const double *d);
+
+/* ---- a7 / a8: perturbative and polynomial series (Sec. 5.1, 5.2) ---------------------- */
+
+/* out = sum_{k=0}^{K-1} c_k (kappa P)^k eta; c: host K complex, or NULL for all ones (PS). */
+lqcd_status lqcd_hop_series(lqcd_ctx *ctx, const double *links, double kappa, const double *eta,
+                            double *out, int nrhs, int K, const double *c);
+/* out = sum_{j=0}^{n} a_j M^j eta; a: host n+1 complex (POLY). */
+lqcd_status lqcd_poly_apply(lqcd_ctx *ctx, const double *links, double kappa, const double *eta,
+                            double *out, int nrhs, int n, const double *a);
+/* Min-Res coefficients a_0..a_n (host out, n+1 complex) minimising ||b - M P_n(M) b|| for
+ * b = Z(4) noise number 2^32 - 1 of the given seed (Sec. 5.2, "one single noise vector"). */
+lqcd_status lqcd_poly_coeffs(lqcd_ctx *ctx, const double *links, double kappa, uint64_t seed, int n,
+                             double *a);
+
+/* ---- a9: hopping traces (Sec. 5.1) ------------------------------------------------------ */
+
+/* t[k][op][t] = sum over the timeslice t of the exact diagonal density of Tr(Theta_op P^k),
+ * k < K, by probing with colour classes whose members are more than K hops apart (host out,
+ * K x 9 x Lt complex).  kappa enters only the point-split operators' own prefactor. */
+lqcd_status lqcd_hop_traces(lqcd_ctx *ctx, const double *links, double kappa, int K, double *t);
+
+/* ---- a10: 1/xi' for HFPS / HFPOLY (Sec. 5.5) ------------------------------------------- */
+
+/* xi[q] = e'_q^dagger gamma_5 tilde M^{-1} e'_q (host out, k complex) with tilde M^{-1} the PS
+ * series of K terms (sub = LQCD_SUB_PERT, coeffs ignored) or the POLY polynomial with the n+1 =
+ * K host coefficients coeffs (sub = LQCD_SUB_POLY). */
+lqcd_status lqcd_xi_inverse(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl,
+                            int sub, int K, const double *coeffs, double *xi);
+
+/* ---- a11: operator contractions (Sec. 6, Table Table903) ------------------------------ */
+
+/* out[n][op][t] = sum over timeslice t of the density of eta_n^dagger Theta_op w_n (host out,
+ * nrhs x 9 x Lt complex), compensated FP64 sums.  Densities: scalar eta^dag w; local
+ * eta^dag gamma_mu w; point-split kappa [eta(x+mu)^dag (1+gamma_mu) U_mu(x)^dag w(x)
+ * - eta(x)^dag (1-gamma_mu) U_mu(x) w(x+mu)] at base site x. */
+lqcd_status lqcd_contract(lqcd_ctx *ctx, const double *links, double kappa, const double *eta,
+                          const double *w, int nrhs, double *out);
+
+/* ---- whole path: loop estimate on one gauge configuration ----------------------------- */
+
+typedef struct {
+  uint64_t seed;      /* noise seed (noises 0 .. nnoise-1; specials 2^32-2 and 2^32-1)       */
+  int nnoise;         /* N                                                                   */
+  int block;          /* right-hand sides solved together (multi-RHS block width b)          */
+  int m, k;           /* GMRES-DR(m, k) / MINRES-DR(m, k) for the special right-hand side    */
+  int m_inner;        /* GMRES cycle length inside GMRES-Proj (m - k if 0)                   */
+  int K;              /* PS terms: I .. (kappa P)^{K-1}  ("seventh order" = 7)               */
+  int npoly;          /* POLY degree n (n + 1 coefficients)                                  */
+  double tol;         /* noise solves: relative true residual                                */
+  double tol_special; /* super-convergence tolerance of the special right-hand side         */
+  int max_cycles;
+  int modes;          /* LQCD_SUB_* bit mask                                                 */
+  int prec;           /* LQCD_PREC_F64 (plain)                                               */
+} lqcd_est_opts;
+
+typedef struct {
+  /* host arrays supplied by the caller (any may be NULL):                                   */
+  double *per_noise;  /* [6 modes][nnoise][9 ops] complex: eta^dag Theta (x - tilde x), summed */
+  double *per_t;      /* [6][9][Lt] complex: per-timeslice mean over noises of the noise term */
+  double *addback;    /* [6][9][Lt] complex: Tr(Theta tilde M^{-1}) per timeslice            */
+  double *mean;       /* [6][9] complex: estimate of Tr(Theta M^{-1})                         */
+  double *stderr_;    /* [6][9] double: error bar of the signal part (Re scalar, Im vectors)  */
+  double *lam;        /* [k] complex: eigenvalues lambda'_q of M' used for deflation          */
+  double *poly_a;     /* [npoly+1] complex: Min-Res coefficients                              */
+  /* filled by the library:                                                                  */
+  long matvecs_setup, matvecs_noise;
+  double seconds_setup, seconds_noise;
+  double max_true_resid;
+  int converged;
+} lqcd_estimate;
+
+/* Tr(Theta M^{-1}) for the nine operators and the requested subtraction modes (Sec. 5-7). */
+lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, double kappa,
+                               const lqcd_est_opts *opts, lqcd_estimate *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQCD_H */

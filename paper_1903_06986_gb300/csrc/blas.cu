@@ -1,0 +1,347 @@
+// Batched FP64 complex level-1/level-2 kernels for the Krylov solvers, and the Z(4) noise kernel.
+//
+// A "block" of nrhs vectors of length n is stored vector after vector; a multi-vector (a Krylov
+// basis) stores basis vector i of right-hand side r at V + i * vstride + r * n.  Every reduction
+// is two-stage with a fixed order (per-block partial sums, then one block per result), so results
+// are reproducible run to run.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int BT = 256;      // threads per block
+constexpr int GROUP = 8;     // basis vectors reduced together in multidot
+
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// partial[(i * nrhs + r) * nb + blockIdx.x] = sum over this block's chunk of conj(V_i^r) w^r
+__global__ void __launch_bounds__(BT) multidot_partial(const double2 *__restrict__ V, long long vstride,
+                                                       long long vrs, int nvec, const double2 *__restrict__ w,
+                                                       long long n, int nrhs, double2 *__restrict__ partial) {
+  const int r = blockIdx.y;
+  const int nb = gridDim.x;
+  const long long chunk = (n + nb - 1) / nb;
+  const long long e0 = blockIdx.x * chunk;
+  const long long e1 = min(n, e0 + chunk);
+  const double2 *wr = w + r * n;
+  __shared__ double2 red[BT / 32][GROUP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < nvec; i0 += GROUP) {
+    const int g = min(GROUP, nvec - i0);
+    double2 acc[GROUP];
+#pragma unroll
+    for (int j = 0; j < GROUP; ++j) acc[j] = make_double2(0.0, 0.0);
+    for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
+      const double2 wv = wr[e];
+#pragma unroll
+      for (int j = 0; j < GROUP; ++j)
+        if (j < g) cfma_conj(acc[j], V[(long long)(i0 + j) * vstride + r * vrs + e], wv);
+    }
+#pragma unroll
+    for (int j = 0; j < GROUP; ++j) {
+      double2 v = warp_sum2(acc[j]);
+      if (lane == 0) red[warp][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < g) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int q = 0; q < BT / 32; ++q) s = cadd(s, red[q][threadIdx.x]);
+      partial[((long long)(i0 + threadIdx.x) * nrhs + r) * nb + blockIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[idx] = sum_b partial[idx * nb + b]   (one block per idx, fixed order)
+__global__ void __launch_bounds__(128) reduce_partials(const double2 *__restrict__ partial, int nb,
+                                                       double2 *__restrict__ out) {
+  const int idx = blockIdx.x;
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = threadIdx.x; b < nb; b += 128) s = cadd(s, partial[(long long)idx * nb + b]);
+  s = warp_sum2(s);
+  __shared__ double2 red[4];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) out[idx] = cadd(cadd(red[0], red[1]), cadd(red[2], red[3]));
+}
+
+__global__ void __launch_bounds__(BT) norm2_partial(const double2 *__restrict__ x, long long n, double *__restrict__ partial) {
+  const int r = blockIdx.y;
+  const int nb = gridDim.x;
+  const long long chunk = (n + nb - 1) / nb;
+  const long long e0 = blockIdx.x * chunk;
+  const long long e1 = min(n, e0 + chunk);
+  const double2 *xr = x + r * n;
+  double acc = 0.0;
+  for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
+    double2 v = xr[e];
+    acc = fma(v.x, v.x, acc);
+    acc = fma(v.y, v.y, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red[BT / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < BT / 32; ++q) s += red[q];
+    partial[(long long)r * nb + blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(128) norm2_final(const double *__restrict__ partial, int nb, double *__restrict__ out) {
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 128) s += partial[(long long)r * nb + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double red[4];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) out[r] = sqrt((red[0] + red[1]) + (red[2] + red[3]));
+}
+
+// w^r += sign * sum_i V_i^r h[i * nrhs + r]
+__global__ void __launch_bounds__(BT) multiaxpy_kernel(const double2 *__restrict__ V, long long vstride,
+                                                       long long vrs, int nvec, const double2 *__restrict__ h,
+                                                       double sign, double2 *__restrict__ w, long long n, int nrhs) {
+  const long long e = (long long)blockIdx.x * BT + threadIdx.x;
+  const int r = blockIdx.y;
+  if (e >= n) return;
+  double2 acc = w[r * n + e];
+  for (int i = 0; i < nvec; ++i) {
+    double2 c = h[(long long)i * nrhs + r];
+    c = cscale(c, sign);
+    cfma(acc, V[(long long)i * vstride + r * vrs + e], c);
+  }
+  w[r * n + e] = acc;
+}
+
+constexpr int CT = 8;  // output columns per pass in combine
+// out_c^r = sum_i V_i^r C[(i * ncol + c) * nrhs + r]
+__global__ void __launch_bounds__(BT) combine_kernel(const double2 *__restrict__ V, long long vstride,
+                                                     long long vrs, int nvec, const double2 *__restrict__ C,
+                                                     int ncol, double2 *__restrict__ out, long long ostride,
+                                                     long long n, int nrhs) {
+  const long long e = (long long)blockIdx.x * BT + threadIdx.x;
+  const int r = blockIdx.y;
+  if (e >= n) return;
+  for (int c0 = 0; c0 < ncol; c0 += CT) {
+    const int g = min(CT, ncol - c0);
+    double2 acc[CT];
+#pragma unroll
+    for (int j = 0; j < CT; ++j) acc[j] = make_double2(0.0, 0.0);
+    for (int i = 0; i < nvec; ++i) {
+      const double2 v = V[(long long)i * vstride + r * vrs + e];
+#pragma unroll
+      for (int j = 0; j < CT; ++j)
+        if (j < g) cfma(acc[j], v, C[((long long)i * ncol + c0 + j) * nrhs + r]);
+    }
+#pragma unroll
+    for (int j = 0; j < CT; ++j)
+      if (j < g) out[(long long)(c0 + j) * ostride + r * n + e] = acc[j];
+  }
+}
+
+__global__ void invscale_kernel(double2 *__restrict__ x, const double *__restrict__ s, long long n) {
+  const long long e = (long long)blockIdx.x * BT + threadIdx.x;
+  const int r = blockIdx.y;
+  if (e >= n) return;
+  const double d = s[r];
+  const double f = d > 0.0 ? 1.0 / d : 0.0;
+  double2 v = x[r * n + e];
+  x[r * n + e] = make_double2(v.x * f, v.y * f);
+}
+
+__global__ void copy_kernel(const double2 *__restrict__ x, double2 *__restrict__ y, long long n) {
+  for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT) y[e] = x[e];
+}
+
+__global__ void zero_kernel(double2 *__restrict__ y, long long n) {
+  for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT)
+    y[e] = make_double2(0.0, 0.0);
+}
+
+__global__ void axpy_kernel(double2 a, const double2 *__restrict__ x, double2 *__restrict__ y, long long n) {
+  for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT) {
+    double2 v = y[e];
+    cfma(v, a, x[e]);
+    y[e] = v;
+  }
+}
+
+__global__ void bminus_kernel(double2 *__restrict__ t, const double2 *__restrict__ b, long long n) {
+  for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT)
+    t[e] = csub(b[e], t[e]);
+}
+
+// gamma_5 = -[[0,1],[1,0]] on spin: one thread per (site, rhs) pair
+__global__ void g5_kernel(const double2 *__restrict__ x, double2 *__restrict__ y, long long sites) {
+  const long long s = (long long)blockIdx.x * BT + threadIdx.x;
+  if (s >= sites) return;
+  const double2 *a = x + 12 * s;
+  double2 *b = y + 12 * s;
+  double2 t[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) t[i] = a[i];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    b[0 + c] = make_double2(-t[6 + c].x, -t[6 + c].y);
+    b[3 + c] = make_double2(-t[9 + c].x, -t[9 + c].y);
+    b[6 + c] = make_double2(-t[0 + c].x, -t[0 + c].y);
+    b[9 + c] = make_double2(-t[3 + c].x, -t[3 + c].y);
+  }
+}
+
+// ---- Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Z(4) noise -------------------------
+struct U4 { uint32_t v[4]; };
+
+__device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = M0 * c.v[0], hi0 = __umulhi(M0, c.v[0]);
+    const uint32_t lo1 = M1 * c.v[2], hi1 = __umulhi(M1, c.v[2]);
+    U4 d;
+    d.v[0] = hi1 ^ c.v[1] ^ k0;
+    d.v[1] = lo1;
+    d.v[2] = hi0 ^ c.v[3] ^ k1;
+    d.v[3] = lo0;
+    c = d;
+    k0 += W0;
+    k1 += W1;
+  }
+  return c;
+}
+
+__global__ void noise_kernel(uint32_t key0, uint32_t key1, uint32_t first, int V, double2 *__restrict__ out) {
+  const int s = blockIdx.x * BT + threadIdx.x;
+  const int n = blockIdx.y;
+  if (s >= V) return;
+  U4 c;
+  c.v[0] = first + (uint32_t)n;
+  c.v[1] = (uint32_t)s;
+  c.v[2] = 0u;
+  c.v[3] = 0u;
+  const uint32_t w = philox10(c, key0, key1).v[0];
+  double2 *o = out + ((long long)n * V + s) * 12;
+#pragma unroll
+  for (int e = 0; e < 12; ++e) {
+    const uint32_t code = (w >> (2 * e)) & 3u;
+    // 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
+    const double re = (code == 0u) ? 1.0 : ((code == 2u) ? -1.0 : 0.0);
+    const double im = (code == 1u) ? 1.0 : ((code == 3u) ? -1.0 : 0.0);
+    o[e] = make_double2(re, im);
+  }
+}
+
+int blocks_for(long long n) { return (int)std::min<long long>((n + BT - 1) / BT, 1 << 20); }
+
+int partial_blocks(lqcd_ctx *ctx, long long n, int nrhs) {
+  long long want = std::max<long long>(1, (4LL * ctx->sms) / std::max(1, nrhs));
+  long long maxb = std::max<long long>(1, (n + BT - 1) / BT);
+  return (int)std::max<long long>(1, std::min<long long>(std::min(want, maxb), 1024));
+}
+
+}  // namespace
+
+lqcd_status blas_copy(lqcd_ctx *ctx, const double2 *x, double2 *y, long long n) {
+  kbegin(ctx);
+  copy_kernel<<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(x, y, n);
+  return launch_check(ctx, "copy_kernel", K_BLAS1, (double)n);
+}
+
+lqcd_status blas_zero(lqcd_ctx *ctx, double2 *y, long long n) {
+  kbegin(ctx);
+  zero_kernel<<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(y, n);
+  return launch_check(ctx, "zero_kernel", K_BLAS1, (double)n);
+}
+
+lqcd_status blas_axpy(lqcd_ctx *ctx, double2 a, const double2 *x, double2 *y, long long n) {
+  kbegin(ctx);
+  axpy_kernel<<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(a, x, y, n);
+  return launch_check(ctx, "axpy_kernel", K_BLAS1, (double)n);
+}
+
+lqcd_status blas_bminus(lqcd_ctx *ctx, double2 *t, const double2 *b, long long n) {
+  kbegin(ctx);
+  bminus_kernel<<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(t, b, n);
+  return launch_check(ctx, "bminus_kernel", K_BLAS1, (double)n);
+}
+
+lqcd_status blas_g5(lqcd_ctx *ctx, const double2 *x, double2 *y, int nrhs) {
+  long long sites = (long long)ctx->V * nrhs;
+  kbegin(ctx);
+  g5_kernel<<<(int)((sites + BT - 1) / BT), BT, 0, ctx->stream>>>(x, y, sites);
+  return launch_check(ctx, "g5_kernel", K_BLAS1, (double)sites * 12);
+}
+
+lqcd_status blas_norms(lqcd_ctx *ctx, const double2 *x, long long n, int nrhs, double *norms) {
+  const int nb = partial_blocks(ctx, n, nrhs);
+  void *p = nullptr;
+  LQCD_TRY(ws_get(ctx, WS_SCAL, sizeof(double) * (size_t)nb * nrhs, &p));
+  kbegin(ctx);
+  norm2_partial<<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(x, n, (double *)p);
+  LQCD_TRY(launch_check(ctx, "norm2_partial", K_NORM, (double)n * nrhs));
+  kbegin(ctx);
+  norm2_final<<<nrhs, 128, 0, ctx->stream>>>((const double *)p, nb, norms);
+  return launch_check(ctx, "norm2_final", K_NORM, 0.0);
+}
+
+lqcd_status blas_multidot(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
+                          const double2 *w, long long n, int nrhs, double2 *h) {
+  if (nvec <= 0) return LQCD_OK;
+  const int nb = partial_blocks(ctx, n, nrhs);
+  void *p = nullptr;
+  LQCD_TRY(ws_get(ctx, WS_PARTIAL, sizeof(double2) * (size_t)nb * nrhs * nvec, &p));
+  kbegin(ctx);
+  multidot_partial<<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, (double2 *)p);
+  LQCD_TRY(launch_check(ctx, "multidot_partial", K_DOT, (double)n * nrhs * nvec));
+  kbegin(ctx);
+  reduce_partials<<<nvec * nrhs, 128, 0, ctx->stream>>>((const double2 *)p, nb, h);
+  return launch_check(ctx, "reduce_partials", K_DOT, 0.0);
+}
+
+lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
+                           const double2 *h, double sign, double2 *w, long long n, int nrhs) {
+  if (nvec <= 0) return LQCD_OK;
+  kbegin(ctx);
+  multiaxpy_kernel<<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, h, sign, w, n, nrhs);
+  return launch_check(ctx, "multiaxpy_kernel", K_AXPY, (double)n * nrhs * nvec);
+}
+
+lqcd_status blas_combine(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
+                         const double2 *C, int ncol, double2 *out, long long ostride, long long n, int nrhs) {
+  if (ncol <= 0) return LQCD_OK;
+  kbegin(ctx);
+  combine_kernel<<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, C, ncol, out, ostride, n, nrhs);
+  return launch_check(ctx, "combine_kernel", K_COMBINE, (double)n * nrhs * nvec * ncol);
+}
+
+lqcd_status blas_invscale(lqcd_ctx *ctx, double2 *x, const double *s, long long n, int nrhs) {
+  kbegin(ctx);
+  invscale_kernel<<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(x, s, n);
+  return launch_check(ctx, "invscale_kernel", K_BLAS1, (double)n * nrhs);
+}
+
+lqcd_status noise_launch(lqcd_ctx *ctx, uint64_t seed, uint32_t first, int nrhs, double2 *out) {
+  kbegin(ctx);
+  noise_kernel<<<dim3(ceil_div(ctx->V, BT), nrhs), BT, 0, ctx->stream>>>((uint32_t)(seed & 0xffffffffu),
+                                                                          (uint32_t)(seed >> 32), first, ctx->V, out);
+  return launch_check(ctx, "noise_kernel", K_NOISE, (double)ctx->V * nrhs);
+}
+
+extern "C" lqcd_status lqcd_noise_z4(lqcd_ctx *ctx, uint64_t seed, uint32_t first_noise, int nrhs, double *out) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!out || nrhs <= 0 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "noise_z4: bad arguments");
+  return noise_launch(ctx, seed, first_noise, nrhs, (double2 *)out);
+}

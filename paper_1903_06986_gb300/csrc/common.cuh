@@ -1,0 +1,169 @@
+// Shared definitions of the liblqcd CUDA sources: context, status plumbing, complex helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "lqcd.h"
+
+// kernel classes for the optional per-class device timing (values of LQCD_K_* in lqcd.h)
+enum KClass { K_WILSON = 0, K_DOT, K_AXPY, K_COMBINE, K_NORM, K_CONTRACT, K_BLAS1, K_NOISE, K_PROBE, K_NCLASS };
+
+struct TimedLaunch {
+  int start, end, cls;  // indices into lqcd_ctx::ev_pool
+  double units;         // work units of the launch (see lqcd_timing_read)
+};
+
+struct lqcd_ctx {
+  int dims[4];          // Lx, Ly, Lz, Lt
+  int V;                // sites
+  long long N;          // complex unknowns per field, 12 V
+  int device;
+  int sms;
+  cudaStream_t stream;
+  std::string err;
+  long launches;
+  // named, growable device workspace (slot -> buffer); freed by lqcd_ctx_destroy
+  std::vector<void *> ws_ptr;
+  std::vector<size_t> ws_size;
+  double *host_pinned;  // small pinned host staging buffer
+  size_t host_pinned_size;
+  // optional kernel timing: events bracket every launch while enabled
+  bool timing;
+  int pending_start;
+  std::vector<cudaEvent_t> ev_pool;
+  int ev_used;
+  std::vector<TimedLaunch> timed;
+  double t_ms[K_NCLASS];
+  long t_count[K_NCLASS];
+  double t_units[K_NCLASS];
+};
+
+struct lqcd_defl {
+  lqcd_ctx *ctx;
+  int k;
+  int hermitian;
+  long long N;
+  double2 *V;           // (k+1) vectors of N (device), NULL when imported
+  double2 *E;           // k eigenvectors of N (device)
+  std::vector<double2> Hbar;  // (k+1) x k row-major (host)
+  std::vector<double2> lam;   // k eigenvalues (host)
+  std::vector<double> eres;   // k eigen residual norms (host)
+  double2 *Hbar_dev;    // (k+1) x k row-major (device), NULL when imported
+};
+
+// ----- status plumbing ------------------------------------------------------------------
+lqcd_status set_err(lqcd_ctx *ctx, lqcd_status st, const char *fmt, ...);
+
+#define LQCD_CUDA(ctx, call)                                                               \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return set_err((ctx), LQCD_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,      \
+                     cudaGetErrorString(e_));                                              \
+  } while (0)
+
+#define LQCD_TRY(expr)                                                                     \
+  do {                                                                                     \
+    lqcd_status s_ = (expr);                                                               \
+    if (s_ != LQCD_OK) return s_;                                                          \
+  } while (0)
+
+// record the start event of the next launch (when timing is enabled)
+void kbegin(lqcd_ctx *ctx);
+// check the launch that was just enqueued, count it, and record its end event when timing
+lqcd_status launch_check(lqcd_ctx *ctx, const char *what, int cls, double units);
+
+// growable workspace slot (device memory owned by the context)
+enum WsSlot {
+  WS_PARTIAL = 0, WS_SCAL, WS_TMP0, WS_TMP1, WS_TMP2, WS_TMP3, WS_BASIS, WS_HESS, WS_COEF,
+  WS_BASIS2, WS_TMP4, WS_TMP5, WS_EST0, WS_EST1, WS_EST2, WS_PROBE, WS_NSLOTS
+};
+lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr);
+lqcd_status host_stage(lqcd_ctx *ctx, size_t bytes, double **ptr);
+
+// ----- complex helpers (device) -----------------------------------------------------------
+__host__ __device__ __forceinline__ double2 cmake(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+// i * a and -i * a
+__host__ __device__ __forceinline__ double2 cmuli(double2 a) { return make_double2(-a.y, a.x); }
+__host__ __device__ __forceinline__ double2 cmulmi(double2 a) { return make_double2(a.y, -a.x); }
+// acc += a * b
+__device__ __forceinline__ void cfma(double2 &acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cfma_conj(double2 &acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+// Neumaier compensated accumulation of one double
+struct KSum {
+  double s, c;
+  __device__ __forceinline__ void init() { s = 0.0; c = 0.0; }
+  __device__ __forceinline__ void add(double v) {
+    double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v; else c += (v - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return s + c; }
+};
+
+static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ----- kernel launchers shared between translation units ---------------------------------
+// Wilson operator on nrhs fields (see lqcd_wilson_apply); in and out must not overlap.
+lqcd_status wilson_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in,
+                          double2 *out, int nrhs, int prec, int flags);
+// y[r] = a * x[r] + y[r] style batched level-1 kernels (blas.cu)
+lqcd_status blas_copy(lqcd_ctx *ctx, const double2 *x, double2 *y, long long n);
+lqcd_status blas_zero(lqcd_ctx *ctx, double2 *y, long long n);
+lqcd_status blas_g5(lqcd_ctx *ctx, const double2 *x, double2 *y, int nrhs);
+// t = b - t
+lqcd_status blas_bminus(lqcd_ctx *ctx, double2 *t, const double2 *b, long long n);
+// norms[r] = ||x_r||_2 for nrhs vectors of length n (device output)
+lqcd_status blas_norms(lqcd_ctx *ctx, const double2 *x, long long n, int nrhs, double *norms);
+// Basis vector i of right-hand side r is V_i^r = V + i*vstride + r*vrs (vrs = 0: one basis shared
+// by every right-hand side); w^r = w + r*n.
+// h[i*nrhs + r] = <V_i^r, w^r> for i < nvec
+lqcd_status blas_multidot(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
+                          const double2 *w, long long n, int nrhs, double2 *h);
+// w^r += sign * sum_i V_i^r h[i*nrhs + r]
+lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
+                           const double2 *h, double sign, double2 *w, long long n, int nrhs);
+// out_c^r = out + c*ostride + r*n = sum_i V_i^r C[(i*ncol + c)*nrhs + r] for c < ncol (no aliasing)
+lqcd_status blas_combine(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
+                         const double2 *C, int ncol, double2 *out, long long ostride, long long n,
+                         int nrhs);
+// x^r *= 1 / s[r] (s device); zero vector if s[r] == 0
+lqcd_status blas_invscale(lqcd_ctx *ctx, double2 *x, const double *s, long long n, int nrhs);
+// y += a x with a host scalar a
+lqcd_status blas_axpy(lqcd_ctx *ctx, double2 a, const double2 *x, double2 *y, long long n);
+// contraction densities summed per timeslice (loops.cu); out device [nrhs][9][Lt]
+lqcd_status contract_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *eta,
+                            const double2 *w, int nrhs, double2 *out_dev);
+lqcd_status noise_launch(lqcd_ctx *ctx, uint64_t seed, uint32_t first, int nrhs, double2 *out);

@@ -1,0 +1,209 @@
+// Context lifetime, error reporting and workspace management of liblqcd.
+#include <cstdarg>
+#include <cstring>
+
+#include "common.cuh"
+
+lqcd_status set_err(lqcd_ctx *ctx, lqcd_status st, const char *fmt, ...) {
+  if (ctx) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+static lqcd_status timing_collect(lqcd_ctx *ctx);
+
+static int next_event(lqcd_ctx *ctx) {
+  if (ctx->ev_used == (int)ctx->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    ctx->ev_pool.push_back(e);
+  }
+  return ctx->ev_used++;
+}
+
+void kbegin(lqcd_ctx *ctx) {
+  ctx->pending_start = -1;
+  if (!ctx->timing) return;
+  const int i = next_event(ctx);
+  if (i >= 0 && cudaEventRecord(ctx->ev_pool[i], ctx->stream) == cudaSuccess) ctx->pending_start = i;
+}
+
+lqcd_status launch_check(lqcd_ctx *ctx, const char *what, int cls, double units) {
+  ctx->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(ctx, LQCD_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+  if (ctx->timing && ctx->pending_start >= 0) {
+    const int j = next_event(ctx);
+    if (j >= 0 && cudaEventRecord(ctx->ev_pool[j], ctx->stream) == cudaSuccess)
+      ctx->timed.push_back(TimedLaunch{ctx->pending_start, j, cls, units});
+    ctx->pending_start = -1;
+    if (ctx->timed.size() >= 16384) return timing_collect(ctx);  // bound the event pool
+  }
+  return LQCD_OK;
+}
+
+// fold recorded launch times into the per-class totals and recycle the events
+static lqcd_status timing_collect(lqcd_ctx *ctx) {
+  if (ctx->timed.empty()) {
+    ctx->ev_used = 0;
+    return LQCD_OK;
+  }
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (const TimedLaunch &t : ctx->timed) {
+    float ms = 0.f;
+    LQCD_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_pool[t.start], ctx->ev_pool[t.end]));
+    ctx->t_ms[t.cls] += ms;
+    ctx->t_count[t.cls] += 1;
+    ctx->t_units[t.cls] += t.units;
+  }
+  ctx->timed.clear();
+  ctx->ev_used = 0;
+  return LQCD_OK;
+}
+
+lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr) {
+  if (slot < 0 || slot >= WS_NSLOTS) return set_err(ctx, LQCD_ERR_INVALID_ARG, "bad workspace slot %d", slot);
+  if (bytes == 0) bytes = 16;
+  if (ctx->ws_size[slot] < bytes) {
+    if (ctx->ws_ptr[slot]) {
+      // the old buffer may still be read by queued work
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return set_err(ctx, LQCD_ERR_CUDA, "sync before workspace growth: %s", cudaGetErrorString(e));
+      cudaFree(ctx->ws_ptr[slot]);
+      ctx->ws_ptr[slot] = nullptr;
+      ctx->ws_size[slot] = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(ctx, LQCD_ERR_OOM, "workspace slot %d: cudaMalloc(%zu) failed: %s", slot, bytes, cudaGetErrorString(e));
+    }
+    ctx->ws_ptr[slot] = p;
+    ctx->ws_size[slot] = bytes;
+  }
+  *ptr = ctx->ws_ptr[slot];
+  return LQCD_OK;
+}
+
+lqcd_status host_stage(lqcd_ctx *ctx, size_t bytes, double **ptr) {
+  if (ctx->host_pinned_size < bytes) {
+    if (ctx->host_pinned) {
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return set_err(ctx, LQCD_ERR_CUDA, "sync before staging growth: %s", cudaGetErrorString(e));
+      cudaFreeHost(ctx->host_pinned);
+      ctx->host_pinned = nullptr;
+      ctx->host_pinned_size = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMallocHost(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(ctx, LQCD_ERR_OOM, "pinned staging of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->host_pinned = (double *)p;
+    ctx->host_pinned_size = bytes;
+  }
+  *ptr = ctx->host_pinned;
+  return LQCD_OK;
+}
+
+extern "C" {
+
+const char *lqcd_version(void) { return "lqcd-gb300 0.1 (sm_103a)"; }
+
+lqcd_status lqcd_ctx_create(lqcd_ctx **out, const int dims[4], int link_recon, void *stream) {
+  if (!out || !dims) return LQCD_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2 || dims[i] > 1024) return LQCD_ERR_INVALID_ARG;
+  if (link_recon != 18) return LQCD_ERR_INVALID_ARG;
+  long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+  if (V > (1LL << 28)) return LQCD_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return LQCD_ERR_CUDA; }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) { cudaGetLastError(); return LQCD_ERR_CUDA; }
+  lqcd_ctx *c = new lqcd_ctx();
+  memcpy(c->dims, dims, sizeof(int) * 4);
+  c->V = (int)V;
+  c->N = 12 * V;
+  c->device = dev;
+  c->sms = prop.multiProcessorCount;
+  c->stream = (cudaStream_t)stream;
+  c->launches = 0;
+  c->ws_ptr.assign(WS_NSLOTS, nullptr);
+  c->ws_size.assign(WS_NSLOTS, 0);
+  c->host_pinned = nullptr;
+  c->host_pinned_size = 0;
+  c->timing = false;
+  c->pending_start = -1;
+  c->ev_used = 0;
+  for (int k = 0; k < K_NCLASS; ++k) {
+    c->t_ms[k] = 0.0;
+    c->t_count[k] = 0;
+    c->t_units[k] = 0.0;
+  }
+  *out = c;
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_ctx_destroy(lqcd_ctx *ctx) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  for (void *p : ctx->ws_ptr)
+    if (p) cudaFree(p);
+  if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_set_stream(lqcd_ctx *ctx, void *stream) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return LQCD_OK;
+}
+
+const char *lqcd_last_error_string(const lqcd_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+long lqcd_kernel_launches(const lqcd_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+lqcd_status lqcd_timing_enable(lqcd_ctx *ctx, int enable) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!enable) LQCD_TRY(timing_collect(ctx));
+  ctx->timing = enable != 0;
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_timing_reset(lqcd_ctx *ctx) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(timing_collect(ctx));
+  for (int k = 0; k < K_NCLASS; ++k) {
+    ctx->t_ms[k] = 0.0;
+    ctx->t_count[k] = 0;
+    ctx->t_units[k] = 0.0;
+  }
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_timing_read(lqcd_ctx *ctx, int cls, double *total_ms, long *launches, double *units) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (cls < 0 || cls >= K_NCLASS || !total_ms || !launches) return set_err(ctx, LQCD_ERR_INVALID_ARG, "timing_read: bad class");
+  LQCD_TRY(timing_collect(ctx));
+  *total_ms = ctx->t_ms[cls];
+  *launches = ctx->t_count[cls];
+  if (units) *units = ctx->t_units[cls];
+  return LQCD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,672 @@
+// GMRES-DR(m, k), its Hermitian form (MINRES-DR) and GMRES-Proj on the GPU (Sec. 5.3, 7, 8).
+//
+// Every right-hand side of a block has its own Krylov basis; all of them advance together, so
+// each Arnoldi step is one multi-RHS Wilson launch plus batched classical Gram-Schmidt (applied
+// twice) and a batched norm, all without a host round trip.  At the end of a cycle the Hessenberg
+// coefficients come back to the host, where the small FP64 problems are solved per right-hand
+// side (least squares, harmonic Ritz values, the restart basis P_{k+1}); the restart
+// V_{k+1} <- V_{m+1} P_{k+1} and the solution update x += V_m d run on the GPU.
+//
+// GMRES-DR cycle (Morgan's algorithm, as used in Sec. 7):
+//   Arnoldi from column j0 to m;  d = argmin ||c - Hbar d||;  x += V_m d;  s = c - Hbar d;
+//   harmonic Ritz (H_m + |h_{m+1,m}|^2 H_m^{-H} e_m e_m^T) g = theta g, k smallest |theta|;
+//   P_{k+1} = orthonormal [g_1..g_k (zero-padded), s];  V <- V P;  Hbar <- P^H Hbar P_k;
+//   c <- P^H s;  j0 = k.
+// Hermitian form (MINRES-DR, Sec. 8): the harmonic Ritz problem is solved as the Hermitian-
+// definite H_m g = (1/theta) Hbar^H Hbar g, which gives real theta.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+#include "common.cuh"
+#include "dense.h"
+
+using dense::cd;
+using dense::Mat;
+
+namespace {
+
+struct Op {
+  const double2 *U;
+  double kappa;
+  int flags;  // LQCD_APPLY_M or LQCD_APPLY_G5R
+  int prec;
+};
+
+lqcd_status apply_op(lqcd_ctx *ctx, const Op &op, const double2 *in, double2 *out, int nrhs) {
+  return wilson_launch(ctx, op.U, op.kappa, in, out, nrhs, op.prec, op.flags);
+}
+
+lqcd_status upload(lqcd_ctx *ctx, const std::vector<cd> &h, void *dev) {
+  if (h.empty()) return LQCD_OK;
+  double *st = nullptr;
+  LQCD_TRY(host_stage(ctx, sizeof(cd) * h.size(), &st));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // staging buffer may be in use
+  memcpy(st, h.data(), sizeof(cd) * h.size());
+  LQCD_CUDA(ctx, cudaMemcpyAsync(dev, st, sizeof(cd) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return LQCD_OK;
+}
+
+template <typename T>
+lqcd_status download(lqcd_ctx *ctx, const void *dev, std::vector<T> &h, size_t count) {
+  h.resize(count);
+  if (count == 0) return LQCD_OK;
+  double *st = nullptr;
+  LQCD_TRY(host_stage(ctx, sizeof(T) * count, &st));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  LQCD_CUDA(ctx, cudaMemcpyAsync(st, dev, sizeof(T) * count, cudaMemcpyDeviceToHost, ctx->stream));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  memcpy(h.data(), st, sizeof(T) * count);
+  return LQCD_OK;
+}
+
+bool finite(cd v) { return std::isfinite(v.real()) && std::isfinite(v.imag()); }
+
+// Per right-hand side host state of a cycle
+struct Rhs {
+  Mat H;                 // (m+1) x m
+  std::vector<cd> c;     // m+1
+  bool active = true;
+  double bnorm = 0.0;
+  double rel = 0.0;
+};
+
+// Enqueue Arnoldi steps j0..m-1 for every right-hand side (basis Vb with vector stride vs =
+// nrhs * N) and fill columns j0..m-1 of each Rhs::H.  Inactive right-hand sides are processed
+// too (their results are ignored).
+struct Arnoldi {
+  lqcd_ctx *ctx;
+  Op op;
+  int nrhs, m;
+  long long N;
+  double2 *Vb;
+  double2 *hd1, *hd2;  // [j][i][r] device, (m) x (m+1) x nrhs
+  double *nrm;         // [j][r]
+};
+
+lqcd_status arnoldi_run(Arnoldi &a, int j0, std::vector<Rhs> &R, long long &matvecs) {
+  lqcd_ctx *ctx = a.ctx;
+  const long long N = a.N, vs = (long long)a.nrhs * N;
+  for (int j = j0; j < a.m; ++j) {
+    double2 *vj = a.Vb + j * vs, *w = a.Vb + (j + 1) * vs;
+    LQCD_TRY(apply_op(ctx, a.op, vj, w, a.nrhs));
+    double2 *h1 = a.hd1 + (long long)j * (a.m + 1) * a.nrhs;
+    double2 *h2 = a.hd2 + (long long)j * (a.m + 1) * a.nrhs;
+    LQCD_TRY(blas_multidot(ctx, a.Vb, vs, N, j + 1, w, N, a.nrhs, h1));
+    LQCD_TRY(blas_multiaxpy(ctx, a.Vb, vs, N, j + 1, h1, -1.0, w, N, a.nrhs));
+    LQCD_TRY(blas_multidot(ctx, a.Vb, vs, N, j + 1, w, N, a.nrhs, h2));
+    LQCD_TRY(blas_multiaxpy(ctx, a.Vb, vs, N, j + 1, h2, -1.0, w, N, a.nrhs));
+    LQCD_TRY(blas_norms(ctx, w, N, a.nrhs, a.nrm + (long long)j * a.nrhs));
+    LQCD_TRY(blas_invscale(ctx, w, a.nrm + (long long)j * a.nrhs, N, a.nrhs));
+  }
+  for (int r = 0; r < a.nrhs; ++r)
+    if (R[r].active) matvecs += a.m - j0;
+  if (j0 >= a.m) return LQCD_OK;
+  const size_t hcount = (size_t)a.m * (a.m + 1) * a.nrhs;
+  std::vector<double2> h1, h2;
+  std::vector<double> nr;
+  LQCD_TRY(download(ctx, a.hd1, h1, hcount));
+  LQCD_TRY(download(ctx, a.hd2, h2, hcount));
+  LQCD_TRY(download(ctx, a.nrm, nr, (size_t)a.m * a.nrhs));
+  for (int r = 0; r < a.nrhs; ++r) {
+    if (!R[r].active) continue;
+    for (int j = j0; j < a.m; ++j) {
+      for (int i = 0; i <= j; ++i) {
+        const double2 x1 = h1[((size_t)j * (a.m + 1) + i) * a.nrhs + r];
+        const double2 x2 = h2[((size_t)j * (a.m + 1) + i) * a.nrhs + r];
+        R[r].H(i, j) = cd(x1.x + x2.x, x1.y + x2.y);
+      }
+      R[r].H(j + 1, j) = cd(nr[(size_t)j * a.nrhs + r], 0.0);
+      for (int i = 0; i <= j + 1; ++i)
+        if (!finite(R[r].H(i, j)))
+          return set_err(ctx, LQCD_ERR_NONFINITE, "non-finite Hessenberg entry (rhs %d, column %d)", r, j);
+    }
+  }
+  return LQCD_OK;
+}
+
+// Harmonic Ritz pairs of Hbar ((m+1) x m), k with smallest |theta| first
+bool harmonic_ritz(const Mat &H, int k, bool hermitian, std::vector<cd> &theta, Mat &G) {
+  const int m = H.c;
+  Mat Hm(m, m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) Hm(i, j) = H(i, j);
+  std::vector<int> order(m);
+  std::vector<cd> th(m);
+  Mat X;
+  if (hermitian) {
+    Mat Hs(m, m);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) Hs(i, j) = 0.5 * (Hm(i, j) + std::conj(Hm(j, i)));
+    Mat B = dense::matmul(dense::adjoint(H), H);
+    std::vector<double> mu;
+    if (!dense::eigh_gen(Hs, B, mu, X)) return false;
+    for (int i = 0; i < m; ++i) th[i] = cd(1.0 / mu[i], 0.0);
+  } else {
+    std::vector<cd> em(m, cd(0.0, 0.0)), f;
+    em[m - 1] = 1.0;
+    if (!dense::solve(dense::adjoint(Hm), em, f)) return false;
+    const double h2 = std::norm(H(m, m - 1));
+    Mat F = Hm;
+    for (int i = 0; i < m; ++i) F(i, m - 1) += h2 * f[i];
+    if (!dense::eig(F, th, X)) return false;
+  }
+  for (int i = 0; i < m; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return std::abs(th[a]) < std::abs(th[b]); });
+  theta.resize(k);
+  G = Mat(m, k);
+  for (int q = 0; q < k; ++q) {
+    theta[q] = th[order[q]];
+    for (int i = 0; i < m; ++i) G(i, q) = X(i, order[q]);
+  }
+  return true;
+}
+
+// P_{k+1}: orthonormal [g (zero-padded to m+1 rows) | s]
+Mat restart_basis(const Mat &G, const std::vector<cd> &s) {
+  const int m1 = (int)s.size(), k = G.c;
+  Mat A(m1, k + 1);
+  for (int q = 0; q < k; ++q)
+    for (int i = 0; i + 1 < m1; ++i) A(i, q) = G(i, q);
+  for (int i = 0; i < m1; ++i) A(i, k) = s[i];
+  return dense::orthonormalize(A);
+}
+
+struct Workspace {
+  double2 *Vb = nullptr, *Vt = nullptr, *hd1 = nullptr, *hd2 = nullptr, *coef = nullptr, *tmp = nullptr;
+  double *nrm = nullptr;
+};
+
+lqcd_status get_workspace(lqcd_ctx *ctx, int m, int k, int nrhs, Workspace &w) {
+  const long long vs = (long long)nrhs * ctx->N;
+  void *p;
+  LQCD_TRY(ws_get(ctx, WS_BASIS, sizeof(double2) * (size_t)(m + 1) * vs, &p));
+  w.Vb = (double2 *)p;
+  LQCD_TRY(ws_get(ctx, WS_BASIS2, sizeof(double2) * (size_t)(std::max(k, 1) + 1) * vs, &p));
+  w.Vt = (double2 *)p;
+  const size_t hc = (size_t)std::max(m, 1) * (m + 1) * nrhs;
+  LQCD_TRY(ws_get(ctx, WS_HESS, sizeof(double2) * 2 * hc + sizeof(double) * (size_t)std::max(m, 1) * nrhs + 64, &p));
+  w.hd1 = (double2 *)p;
+  w.hd2 = w.hd1 + hc;
+  w.nrm = (double *)(w.hd2 + hc);
+  LQCD_TRY(ws_get(ctx, WS_COEF, sizeof(double2) * (size_t)(m + 2) * (m + 2) * nrhs, &p));
+  w.coef = (double2 *)p;
+  LQCD_TRY(ws_get(ctx, WS_TMP0, sizeof(double2) * (size_t)vs, &p));
+  w.tmp = (double2 *)p;
+  return LQCD_OK;
+}
+
+// relative true residuals ||b - A x|| / ||b|| for every right-hand side
+lqcd_status true_residuals(lqcd_ctx *ctx, const Op &op, const double2 *b, const double2 *x, double2 *tmp, int nrhs,
+                           const std::vector<Rhs> &R, std::vector<double> &rel) {
+  const long long N = ctx->N;
+  LQCD_TRY(apply_op(ctx, op, x, tmp, nrhs));
+  // tmp = b - tmp  via tmp = -tmp + b
+  LQCD_TRY(blas_bminus(ctx, tmp, b, (long long)nrhs * N));
+  double *nd;
+  LQCD_TRY(ws_get(ctx, WS_TMP5, sizeof(double) * nrhs, (void **)&nd));
+  LQCD_TRY(blas_norms(ctx, tmp, N, nrhs, nd));
+  std::vector<double> h;
+  LQCD_TRY(download(ctx, nd, h, nrhs));
+  rel.resize(nrhs);
+  for (int r = 0; r < nrhs; ++r) rel[r] = R[r].bnorm > 0.0 ? h[r] / R[r].bnorm : h[r];
+  return LQCD_OK;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+lqcd_status check_opts(lqcd_ctx *ctx, const lqcd_krylov_opts *o, int nrhs) {
+  if (!o) return set_err(ctx, LQCD_ERR_INVALID_ARG, "NULL solver options");
+  if (o->m < 1 || o->m > 1000 || o->k < 0 || o->k >= o->m)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "need 0 <= k < m <= 1000 (m=%d k=%d)", o->m, o->k);
+  if (!(o->tol > 0.0) || o->max_cycles < 1) return set_err(ctx, LQCD_ERR_INVALID_ARG, "need tol > 0 and max_cycles >= 1");
+  if (nrhs < 1 || nrhs > 4096) return set_err(ctx, LQCD_ERR_INVALID_ARG, "nrhs %d out of range", nrhs);
+  if (o->prec != LQCD_PREC_F64 && o->prec != LQCD_PREC_F32) return set_err(ctx, LQCD_ERR_INVALID_ARG, "bad precision");
+  return LQCD_OK;
+}
+
+// Rayleigh-Ritz eigenpairs on span(V_k): T = Hbar_k[:k,:k]
+lqcd_status ritz_pairs(lqcd_ctx *ctx, lqcd_defl *d) {
+  const int k = d->k;
+  Mat T(k, k);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      const double2 v = d->Hbar[(size_t)i * k + j];
+      T(i, j) = cd(v.x, v.y);
+    }
+  std::vector<cd> lam(k);
+  Mat Y;
+  if (d->hermitian) {
+    std::vector<double> w;
+    if (!dense::eigh(T, w, Y)) return set_err(ctx, LQCD_ERR_NOT_CONVERGED, "Rayleigh-Ritz eigensolver failed");
+    for (int i = 0; i < k; ++i) lam[i] = cd(w[i], 0.0);
+  } else {
+    if (!dense::eig(T, lam, Y)) return set_err(ctx, LQCD_ERR_NOT_CONVERGED, "Rayleigh-Ritz eigensolver failed");
+  }
+  std::vector<int> order(k);
+  for (int i = 0; i < k; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return std::abs(lam[a]) < std::abs(lam[b]); });
+  d->lam.resize(k);
+  d->eres.resize(k);
+  std::vector<cd> C((size_t)k * k);
+  for (int q = 0; q < k; ++q) {
+    const int o = order[q];
+    d->lam[q] = make_double2(lam[o].real(), lam[o].imag());
+    for (int i = 0; i < k; ++i) C[(size_t)i * k + q] = Y(i, o);
+    // ||Hbar_k y - lam [y; 0]||
+    double r2 = 0.0;
+    for (int i = 0; i <= k; ++i) {
+      cd s = 0.0;
+      for (int j = 0; j < k; ++j) {
+        const double2 hv = d->Hbar[(size_t)i * k + j];
+        s += cd(hv.x, hv.y) * Y(j, o);
+      }
+      if (i < k) s -= lam[o] * Y(i, o);
+      r2 += std::norm(s);
+    }
+    d->eres[q] = std::sqrt(r2);
+  }
+  void *p;
+  LQCD_TRY(ws_get(ctx, WS_COEF, sizeof(cd) * C.size(), &p));
+  LQCD_TRY(upload(ctx, C, p));
+  return blas_combine(ctx, d->V, d->N, 0, k, (const double2 *)p, k, d->E, d->N, d->N, 1);
+}
+
+lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 *x, int nrhs,
+                         const lqcd_krylov_opts *o, bool hermitian, lqcd_solve_info *info, lqcd_defl **defl_out) {
+  const double t0 = now_s();
+  LQCD_TRY(check_opts(ctx, o, nrhs));
+  const int m = o->m, k = o->k;
+  const long long N = ctx->N, vs = (long long)nrhs * N;
+  Workspace W;
+  LQCD_TRY(get_workspace(ctx, m, k, nrhs, W));
+  std::vector<Rhs> R(nrhs);
+  for (auto &r : R) {
+    r.H = Mat(m + 1, m);
+    r.c.assign(m + 1, cd(0.0, 0.0));
+  }
+  // x = 0, v_0 = b / ||b||, c = ||b|| e_1
+  LQCD_TRY(blas_zero(ctx, x, vs));
+  LQCD_TRY(blas_copy(ctx, b, W.Vb, vs));
+  LQCD_TRY(blas_norms(ctx, b, N, nrhs, W.nrm));
+  std::vector<double> bn;
+  LQCD_TRY(download(ctx, W.nrm, bn, nrhs));
+  for (int r = 0; r < nrhs; ++r) {
+    R[r].bnorm = bn[r];
+    R[r].c[0] = bn[r];
+    if (!(bn[r] > 0.0)) R[r].active = false;
+  }
+  LQCD_TRY(blas_invscale(ctx, W.Vb, W.nrm, N, nrhs));
+  Arnoldi A{ctx, op, nrhs, m, N, W.Vb, W.hd1, W.hd2, W.nrm};
+  long long matvecs = 0;
+  int j0 = 0, cycles = 0;
+  bool all_conv = false;
+  std::vector<std::vector<cd>> theta_keep(nrhs);
+  std::vector<Mat> P_keep(nrhs);
+  for (int cyc = 0; cyc < o->max_cycles; ++cyc) {
+    cycles = cyc + 1;
+    LQCD_TRY(arnoldi_run(A, j0, R, matvecs));
+    // least squares per right-hand side, x += V_m d
+    std::vector<cd> dcoef((size_t)m * nrhs, cd(0.0, 0.0));
+    std::vector<std::vector<cd>> s(nrhs);
+    for (int r = 0; r < nrhs; ++r) {
+      if (!R[r].active) continue;
+      std::vector<cd> d = dense::lstsq(R[r].H, R[r].c);
+      s[r] = R[r].c;
+      for (int i = 0; i <= m; ++i)
+        for (int j = 0; j < m; ++j) s[r][i] -= R[r].H(i, j) * d[j];
+      double sn = 0.0;
+      for (const cd &v : s[r]) sn += std::norm(v);
+      R[r].rel = std::sqrt(sn) / R[r].bnorm;
+      for (int j = 0; j < m; ++j) dcoef[(size_t)j * nrhs + r] = d[j];
+    }
+    LQCD_TRY(upload(ctx, dcoef, W.coef));
+    LQCD_TRY(blas_multiaxpy(ctx, W.Vb, vs, N, m, W.coef, 1.0, x, N, nrhs));
+    // harmonic Ritz restart (also computed on the final cycle: it defines the deflation space)
+    all_conv = true;
+    std::vector<cd> pcoef((size_t)(m + 1) * (k + 1) * nrhs, cd(0.0, 0.0));
+    for (int r = 0; r < nrhs; ++r) {
+      if (!R[r].active) {
+        for (int i = 0; i <= k; ++i) pcoef[((size_t)i * (k + 1) + i) * nrhs + r] = 1.0;
+        continue;
+      }
+      std::vector<cd> th;
+      Mat G;
+      if (k > 0) {
+        if (!harmonic_ritz(R[r].H, k, hermitian, th, G))
+          return set_err(ctx, LQCD_ERR_NOT_CONVERGED, "harmonic Ritz eigenproblem failed (rhs %d, cycle %d)", r, cyc);
+      } else {
+        G = Mat(m, 0);
+      }
+      Mat P = restart_basis(G, s[r]);
+      for (int i = 0; i <= m; ++i)
+        for (int c = 0; c <= k; ++c) pcoef[((size_t)i * (k + 1) + c) * nrhs + r] = P(i, c);
+      theta_keep[r] = th;
+      P_keep[r] = P;
+      if (R[r].rel > o->tol) all_conv = false;
+    }
+    const bool last = all_conv || cyc + 1 == o->max_cycles;
+    if (last) break;
+    LQCD_TRY(upload(ctx, pcoef, W.coef));
+    LQCD_TRY(blas_combine(ctx, W.Vb, vs, N, m + 1, W.coef, k + 1, W.Vt, vs, N, nrhs));
+    LQCD_TRY(blas_copy(ctx, W.Vt, W.Vb, (long long)(k + 1) * vs));
+    for (int r = 0; r < nrhs; ++r) {
+      if (!R[r].active) continue;
+      const Mat &P = P_keep[r];
+      // Hbar_new = P^H Hbar P_k  ((k+1) x k), c_new = P^H s
+      Mat Pk(m, k);
+      for (int i = 0; i < m; ++i)
+        for (int c = 0; c < k; ++c) Pk(i, c) = P(i, c);
+      Mat Hn = dense::matmul(dense::adjoint(P), dense::matmul(R[r].H, Pk));
+      Mat Hfull(m + 1, m);
+      for (int i = 0; i <= k; ++i)
+        for (int j = 0; j < k; ++j) Hfull(i, j) = Hn(i, j);
+      R[r].H = Hfull;
+      std::vector<cd> cn(m + 1, cd(0.0, 0.0));
+      for (int i = 0; i <= k; ++i) {
+        cd v = 0.0;
+        for (int q = 0; q <= m; ++q) v += std::conj(P(q, i)) * s[r][q];
+        cn[i] = v;
+      }
+      R[r].c = cn;
+      if (R[r].rel <= o->tol) R[r].active = false;
+    }
+    j0 = k;
+  }
+  std::vector<double> rel;
+  LQCD_TRY(true_residuals(ctx, op, b, x, W.tmp, nrhs, R, rel));
+  double worst = 0.0;
+  for (int r = 0; r < nrhs; ++r) worst = std::max(worst, rel[r]);
+  matvecs += nrhs;
+  if (defl_out && nrhs == 1 && k > 0) {
+    lqcd_defl *d = new lqcd_defl();
+    d->ctx = ctx;
+    d->k = k;
+    d->hermitian = hermitian ? 1 : 0;
+    d->N = N;
+    d->V = d->E = nullptr;
+    d->Hbar_dev = nullptr;
+    cudaError_t e1 = cudaMalloc(&d->V, sizeof(double2) * (size_t)(k + 1) * N);
+    cudaError_t e2 = cudaMalloc(&d->E, sizeof(double2) * (size_t)k * N);
+    cudaError_t e3 = cudaMalloc(&d->Hbar_dev, sizeof(double2) * (size_t)(k + 1) * k);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+      cudaGetLastError();
+      if (d->V) cudaFree(d->V);
+      if (d->E) cudaFree(d->E);
+      if (d->Hbar_dev) cudaFree(d->Hbar_dev);
+      delete d;
+      return set_err(ctx, LQCD_ERR_OOM, "deflation space allocation failed");
+    }
+    const Mat &P = P_keep[0];
+    std::vector<cd> pc((size_t)(m + 1) * (k + 1));
+    for (int i = 0; i <= m; ++i)
+      for (int c = 0; c <= k; ++c) pc[(size_t)i * (k + 1) + c] = P(i, c);
+    LQCD_TRY(upload(ctx, pc, W.coef));
+    LQCD_TRY(blas_combine(ctx, W.Vb, vs, N, m + 1, W.coef, k + 1, d->V, N, N, 1));
+    Mat Pk(m, k);
+    for (int i = 0; i < m; ++i)
+      for (int c = 0; c < k; ++c) Pk(i, c) = P(i, c);
+    Mat Hn = dense::matmul(dense::adjoint(P), dense::matmul(R[0].H, Pk));
+    d->Hbar.resize((size_t)(k + 1) * k);
+    std::vector<cd> hrow((size_t)(k + 1) * k);
+    for (int i = 0; i <= k; ++i)
+      for (int j = 0; j < k; ++j) {
+        d->Hbar[(size_t)i * k + j] = make_double2(Hn(i, j).real(), Hn(i, j).imag());
+        hrow[(size_t)i * k + j] = Hn(i, j);
+      }
+    LQCD_TRY(upload(ctx, hrow, d->Hbar_dev));
+    LQCD_TRY(ritz_pairs(ctx, d));
+    LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *defl_out = d;
+  }
+  if (info) {
+    info->cycles = cycles;
+    info->matvecs = (long)matvecs;
+    info->converged = (worst <= o->tol) ? 1 : 0;
+    info->true_resid = worst;
+    info->seconds = now_s() - t0;
+  }
+  bool conv = all_conv;
+  return conv ? LQCD_OK : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "GMRES-DR: no convergence in %d cycles (rel %.3e)", cycles, worst);
+}
+
+}  // namespace
+
+// ---- GMRES-Proj ----------------------------------------------------------------------------
+lqcd_status proj_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const double2 *b, double2 *x, int nrhs,
+                      const lqcd_krylov_opts *o, lqcd_solve_info *info) {
+  const double t0 = now_s();
+  LQCD_TRY(check_opts(ctx, o, nrhs));
+  if (!defl || !defl->V || !defl->Hbar_dev) return set_err(ctx, LQCD_ERR_INVALID_ARG, "GMRES-Proj needs a solver-made deflation space");
+  const int m = o->m, k = defl->k;
+  const long long N = ctx->N, vs = (long long)nrhs * N;
+  Workspace W;
+  LQCD_TRY(get_workspace(ctx, std::max(m, k + 1), 0, nrhs, W));
+  double2 *r_dev;
+  LQCD_TRY(ws_get(ctx, WS_TMP1, sizeof(double2) * (size_t)vs, (void **)&r_dev));
+  std::vector<Rhs> R(nrhs);
+  Mat Hk(k + 1, k);
+  for (int i = 0; i <= k; ++i)
+    for (int j = 0; j < k; ++j) {
+      const double2 v = defl->Hbar[(size_t)i * k + j];
+      Hk(i, j) = cd(v.x, v.y);
+    }
+  LQCD_TRY(blas_zero(ctx, x, vs));
+  LQCD_TRY(blas_copy(ctx, b, r_dev, vs));
+  LQCD_TRY(blas_norms(ctx, b, N, nrhs, W.nrm));
+  std::vector<double> bn;
+  LQCD_TRY(download(ctx, W.nrm, bn, nrhs));
+  for (int r = 0; r < nrhs; ++r) {
+    R[r].bnorm = bn[r];
+    R[r].H = Mat(m + 1, m);
+    if (!(bn[r] > 0.0)) R[r].active = false;
+  }
+  Arnoldi A{ctx, op, nrhs, m, N, W.Vb, W.hd1, W.hd2, W.nrm};
+  long long matvecs = 0;
+  int cycles = 0;
+  bool all_conv = false;
+  double worst = 0.0;
+  for (int cyc = 0; cyc < o->max_cycles; ++cyc) {
+    cycles = cyc + 1;
+    // (i) projection over the deflation space: d = argmin ||V_{k+1}^H r - Hbar_k d||
+    LQCD_TRY(blas_multidot(ctx, defl->V, N, 0, k + 1, r_dev, N, nrhs, W.coef));
+    std::vector<double2> cp;
+    LQCD_TRY(download(ctx, W.coef, cp, (size_t)(k + 1) * nrhs));
+    std::vector<cd> dk((size_t)k * nrhs, cd(0.0, 0.0)), zk((size_t)(k + 1) * nrhs, cd(0.0, 0.0));
+    for (int r = 0; r < nrhs; ++r) {
+      if (!R[r].active) continue;
+      std::vector<cd> c(k + 1);
+      for (int i = 0; i <= k; ++i) c[i] = cd(cp[(size_t)i * nrhs + r].x, cp[(size_t)i * nrhs + r].y);
+      std::vector<cd> d = dense::lstsq(Hk, c);
+      for (int j = 0; j < k; ++j) dk[(size_t)j * nrhs + r] = d[j];
+      for (int i = 0; i <= k; ++i) {
+        cd v = 0.0;
+        for (int j = 0; j < k; ++j) v += Hk(i, j) * d[j];
+        zk[(size_t)i * nrhs + r] = v;
+      }
+    }
+    LQCD_TRY(upload(ctx, dk, W.coef));
+    LQCD_TRY(blas_multiaxpy(ctx, defl->V, N, 0, k, W.coef, 1.0, x, N, nrhs));
+    LQCD_TRY(upload(ctx, zk, W.coef));
+    LQCD_TRY(blas_multiaxpy(ctx, defl->V, N, 0, k + 1, W.coef, -1.0, r_dev, N, nrhs));
+    // (ii) one GMRES(m) cycle from r
+    LQCD_TRY(blas_norms(ctx, r_dev, N, nrhs, W.nrm));
+    std::vector<double> beta;
+    LQCD_TRY(download(ctx, W.nrm, beta, nrhs));
+    LQCD_TRY(blas_copy(ctx, r_dev, W.Vb, vs));
+    LQCD_TRY(blas_invscale(ctx, W.Vb, W.nrm, N, nrhs));
+    for (int r = 0; r < nrhs; ++r) {
+      R[r].c.assign(m + 1, cd(0.0, 0.0));
+      R[r].c[0] = beta[r];
+      if (R[r].active && !(beta[r] > 0.0)) R[r].active = false;
+    }
+    LQCD_TRY(arnoldi_run(A, 0, R, matvecs));
+    std::vector<cd> dcoef((size_t)m * nrhs, cd(0.0, 0.0)), scoef((size_t)(m + 1) * nrhs, cd(0.0, 0.0));
+    all_conv = true;
+    for (int r = 0; r < nrhs; ++r) {
+      if (!R[r].active) {
+        scoef[r] = beta[r];  // keep r unchanged: r = V_0 * beta
+        continue;
+      }
+      std::vector<cd> d = dense::lstsq(R[r].H, R[r].c);
+      std::vector<cd> s = R[r].c;
+      for (int i = 0; i <= m; ++i)
+        for (int j = 0; j < m; ++j) s[i] -= R[r].H(i, j) * d[j];
+      double sn = 0.0;
+      for (const cd &v : s) sn += std::norm(v);
+      R[r].rel = std::sqrt(sn) / R[r].bnorm;
+      for (int j = 0; j < m; ++j) dcoef[(size_t)j * nrhs + r] = d[j];
+      for (int i = 0; i <= m; ++i) scoef[(size_t)i * nrhs + r] = s[i];
+      if (R[r].rel > o->tol) all_conv = false;
+    }
+    LQCD_TRY(upload(ctx, dcoef, W.coef));
+    LQCD_TRY(blas_multiaxpy(ctx, W.Vb, vs, N, m, W.coef, 1.0, x, N, nrhs));
+    LQCD_TRY(upload(ctx, scoef, W.coef));
+    LQCD_TRY(blas_combine(ctx, W.Vb, vs, N, m + 1, W.coef, 1, r_dev, vs, N, nrhs));
+    if (all_conv) {
+      // confirm with the true residual; continue from it where the recursion drifted
+      std::vector<double> rel;
+      LQCD_TRY(true_residuals(ctx, op, b, x, W.tmp, nrhs, R, rel));
+      matvecs += nrhs;
+      worst = 0.0;
+      bool ok = true;
+      for (int r = 0; r < nrhs; ++r) {
+        worst = std::max(worst, rel[r]);
+        if (rel[r] > o->tol) ok = false;
+      }
+      if (ok) break;
+      all_conv = false;
+      LQCD_TRY(blas_copy(ctx, W.tmp, r_dev, vs));
+      for (int r = 0; r < nrhs; ++r) R[r].active = rel[r] > o->tol;
+    }
+    for (int r = 0; r < nrhs; ++r)
+      if (R[r].active && R[r].rel <= o->tol) R[r].active = false;
+  }
+  if (!all_conv) {
+    std::vector<double> rel;
+    LQCD_TRY(true_residuals(ctx, op, b, x, W.tmp, nrhs, R, rel));
+    matvecs += nrhs;
+    worst = 0.0;
+    for (int r = 0; r < nrhs; ++r) worst = std::max(worst, rel[r]);
+  }
+  if (info) {
+    info->cycles = cycles;
+    info->matvecs = (long)matvecs;
+    info->converged = (worst <= o->tol) ? 1 : 0;
+    info->true_resid = worst;
+    info->seconds = now_s() - t0;
+  }
+  return (worst <= o->tol) ? LQCD_OK
+                           : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "GMRES-Proj: no convergence in %d cycles (rel %.3e)", cycles, worst);
+}
+
+lqcd_status proj_core_entry(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, const double2 *b,
+                            double2 *x, int nrhs, const lqcd_krylov_opts *o, lqcd_solve_info *info) {
+  const int sys = defl->hermitian ? LQCD_SYS_MG5 : o->system;
+  Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, o->prec};
+  return proj_core(ctx, op, defl, b, x, nrhs, o, info);
+}
+
+lqcd_status gmresdr_entry(lqcd_ctx *ctx, const double *links, double kappa, const double *b, double *x, int nrhs,
+                          const lqcd_krylov_opts *opts, lqcd_solve_info *info, lqcd_defl **defl_out, bool hermitian) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !b || !x || !opts) return set_err(ctx, LQCD_ERR_INVALID_ARG, "NULL argument");
+  if (defl_out) *defl_out = nullptr;
+  const int sys = hermitian ? LQCD_SYS_MG5 : opts->system;
+  if (sys != LQCD_SYS_M && sys != LQCD_SYS_MG5) return set_err(ctx, LQCD_ERR_INVALID_ARG, "bad system %d", sys);
+  Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, opts->prec};
+  return gmresdr_core(ctx, op, (const double2 *)b, (double2 *)x, nrhs, opts, hermitian, info, defl_out);
+}
+
+extern "C" {
+
+lqcd_status lqcd_gmresdr_solve(lqcd_ctx *ctx, const double *links, double kappa, const double *b, double *x, int nrhs,
+                               const lqcd_krylov_opts *opts, lqcd_solve_info *info, lqcd_defl **defl_out) {
+  return gmresdr_entry(ctx, links, kappa, b, x, nrhs, opts, info, defl_out, false);
+}
+
+lqcd_status lqcd_minresdr_solve(lqcd_ctx *ctx, const double *links, double kappa, const double *b, double *x, int nrhs,
+                                const lqcd_krylov_opts *opts, lqcd_solve_info *info, lqcd_defl **defl_out) {
+  return gmresdr_entry(ctx, links, kappa, b, x, nrhs, opts, info, defl_out, true);
+}
+
+lqcd_status lqcd_proj_solve(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, const double *b,
+                            double *x, int nrhs, const lqcd_krylov_opts *opts, lqcd_solve_info *info) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !b || !x || !opts || !defl) return set_err(ctx, LQCD_ERR_INVALID_ARG, "NULL argument");
+  const int sys = defl->hermitian ? LQCD_SYS_MG5 : opts->system;
+  Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, opts->prec};
+  return proj_core(ctx, op, defl, (const double2 *)b, (double2 *)x, nrhs, opts, info);
+}
+
+lqcd_status lqcd_defl_destroy(lqcd_defl *d) {
+  if (!d) return LQCD_ERR_INVALID_ARG;
+  if (d->ctx) cudaStreamSynchronize(d->ctx->stream);
+  if (d->V) cudaFree(d->V);
+  if (d->E) cudaFree(d->E);
+  if (d->Hbar_dev) cudaFree(d->Hbar_dev);
+  delete d;
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_defl_info(const lqcd_defl *d, int *k, int *hermitian) {
+  if (!d) return LQCD_ERR_INVALID_ARG;
+  if (k) *k = d->k;
+  if (hermitian) *hermitian = d->hermitian;
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_defl_export(const lqcd_defl *d, double *V, double *Hbar, double *lam, double *E, double *eig_resid) {
+  if (!d) return LQCD_ERR_INVALID_ARG;
+  lqcd_ctx *ctx = d->ctx;
+  if (V) {
+    if (!d->V) return set_err(ctx, LQCD_ERR_INVALID_ARG, "deflation object has no Krylov basis");
+    LQCD_CUDA(ctx, cudaMemcpyAsync(V, d->V, sizeof(double2) * (size_t)(d->k + 1) * d->N, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  if (E) LQCD_CUDA(ctx, cudaMemcpyAsync(E, d->E, sizeof(double2) * (size_t)d->k * d->N, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (Hbar) {
+    if (d->Hbar.empty()) return set_err(ctx, LQCD_ERR_INVALID_ARG, "deflation object has no Hessenberg matrix");
+    memcpy(Hbar, d->Hbar.data(), sizeof(double2) * d->Hbar.size());
+  }
+  if (lam) memcpy(lam, d->lam.data(), sizeof(double2) * d->lam.size());
+  if (eig_resid) memcpy(eig_resid, d->eres.data(), sizeof(double) * d->eres.size());
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_defl_import(lqcd_ctx *ctx, int k, const double *E, const double *lam, lqcd_defl **out) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!E || !lam || !out || k < 1) return set_err(ctx, LQCD_ERR_INVALID_ARG, "defl_import: bad arguments");
+  lqcd_defl *d = new lqcd_defl();
+  d->ctx = ctx;
+  d->k = k;
+  d->hermitian = 1;
+  d->N = ctx->N;
+  d->V = nullptr;
+  d->Hbar_dev = nullptr;
+  d->E = nullptr;
+  if (cudaMalloc(&d->E, sizeof(double2) * (size_t)k * ctx->N) != cudaSuccess) {
+    cudaGetLastError();
+    delete d;
+    return set_err(ctx, LQCD_ERR_OOM, "defl_import: allocation failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(d->E, E, sizeof(double2) * (size_t)k * ctx->N, cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaFree(d->E);
+    delete d;
+    return set_err(ctx, LQCD_ERR_CUDA, "defl_import: copy failed: %s", cudaGetErrorString(e));
+  }
+  d->lam.resize(k);
+  memcpy(d->lam.data(), lam, sizeof(double2) * k);
+  d->eres.assign(k, 0.0);
+  cudaStreamSynchronize(ctx->stream);
+  *out = d;
+  return LQCD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,702 @@
+// Loop-estimate stage: operator contractions (Sec. 6), perturbative / polynomial series (Sec. 5.1,
+// 5.2), deflation projection (Sec. 5.4), 1/xi' (Sec. 5.5), hopping traces by probing (Sec. 5.1)
+// and the whole estimate on one gauge configuration.
+//
+// Contraction densities of eta^dag Theta w at base site x (Table Table903):
+//   scalar       eta(x)^dag w(x)
+//   local        eta(x)^dag gamma_mu w(x)
+//   point-split  kappa [ eta(x+mu)^dag (1 + g_mu) U_mu(x)^dag w(x) - eta(x)^dag (1 - g_mu) U_mu(x) w(x+mu) ]
+// summed per timeslice with Neumaier-compensated FP64 accumulation.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+#include "common.cuh"
+#include "dense.h"
+#include "spin.cuh"
+
+using dense::cd;
+
+namespace {
+
+using namespace spin;
+
+constexpr int CBT = 128;  // threads per contraction block
+
+__device__ __forceinline__ Cx<double> dotc(const Cx<double> a[4][3], const Cx<double> b[4][3]) {
+  double re = 0.0, im = 0.0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      re = fma(a[s][c].x, b[s][c].x, re);
+      re = fma(a[s][c].y, b[s][c].y, re);
+      im = fma(a[s][c].x, b[s][c].y, im);
+      im = fma(-a[s][c].y, b[s][c].x, im);
+    }
+  return mk<double>(re, im);
+}
+
+// gamma_mu w in the Dirac basis
+template <int MU>
+__device__ __forceinline__ void gamma_apply(const Cx<double> w[4][3], Cx<double> o[4][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (MU == 0) { o[0][c] = tmi(w[3][c]); o[1][c] = tmi(w[2][c]); o[2][c] = ti(w[1][c]); o[3][c] = ti(w[0][c]); }
+    if (MU == 1) { o[0][c] = neg(w[3][c]); o[1][c] = w[2][c]; o[2][c] = w[1][c]; o[3][c] = neg(w[0][c]); }
+    if (MU == 2) { o[0][c] = tmi(w[2][c]); o[1][c] = ti(w[3][c]); o[2][c] = ti(w[0][c]); o[3][c] = tmi(w[1][c]); }
+    if (MU == 3) { o[0][c] = w[0][c]; o[1][c] = w[1][c]; o[2][c] = neg(w[2][c]); o[3][c] = neg(w[3][c]); }
+  }
+}
+
+template <int MU>
+__device__ __forceinline__ void zero_sp(Cx<double> a[4][3]) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[s][c] = mk<double>(0.0, 0.0);
+}
+
+// point-split density of direction MU at site s
+template <int MU>
+__device__ __forceinline__ Cx<double> psplit(const double2 *U, const double2 *eta, const double2 *w, int s, int sp,
+                                             long long V, const Cx<double> eta_s[4][3], const Cx<double> w_s[4][3]) {
+  Cx<double> u[9], a[4][3], nb[4][3];
+  load_link<double>(U, (long long)MU * V + s, u);
+  // (1 + g_mu) U_mu(s)^dag w(s), then contracted with eta(s + mu)
+  zero_sp<MU>(a);
+  term_bwd<double, MU>(w_s, u, a);
+  load_spinor<double, false>(eta + 12LL * sp, nb);
+  Cx<double> t1 = dotc(nb, a);
+  // (1 - g_mu) U_mu(s) w(s + mu), contracted with eta(s)
+  zero_sp<MU>(a);
+  load_spinor<double, false>(w + 12LL * sp, nb);
+  term_fwd<double, MU>(nb, u, a);
+  Cx<double> t2 = dotc(eta_s, a);
+  return t1 - t2;
+}
+
+// partial[((r * Lt + t) * nchunk + chunk) * 9 + op]; grid (nchunk * Lt, nrhs)
+__global__ void __launch_bounds__(CBT) contract_kernel(const double2 *__restrict__ U, double kappa,
+                                                       const double2 *__restrict__ eta, const double2 *__restrict__ w,
+                                                       int Lx, int Ly, int Lz, int Lt, int nchunk,
+                                                       double2 *__restrict__ partial) {
+  const int r = blockIdx.y;
+  const int t = blockIdx.x / nchunk;
+  const int chunk = blockIdx.x % nchunk;
+  const int Vs = Lx * Ly * Lz;
+  const long long V = (long long)Vs * Lt;
+  const double2 *er = eta + (long long)r * V * 12, *wr = w + (long long)r * V * 12;
+  const int per = (Vs + nchunk - 1) / nchunk;
+  const int i0 = chunk * per, i1 = min(Vs, i0 + per);
+  KSum acc[18];
+#pragma unroll
+  for (int q = 0; q < 18; ++q) acc[q].init();
+  for (int i = i0 + threadIdx.x; i < i1; i += CBT) {
+    const int s = t * Vs + i;
+    const int x = i % Lx, y = (i / Lx) % Ly, z = i / (Lx * Ly);
+    Cx<double> es[4][3], ws[4][3], g[4][3];
+    load_spinor<double, false>(er + 12LL * s, es);
+    load_spinor<double, false>(wr + 12LL * s, ws);
+    Cx<double> d = dotc(es, ws);
+    acc[0].add(d.x); acc[1].add(d.y);
+    gamma_apply<0>(ws, g); d = dotc(es, g); acc[2].add(d.x); acc[3].add(d.y);
+    gamma_apply<1>(ws, g); d = dotc(es, g); acc[4].add(d.x); acc[5].add(d.y);
+    gamma_apply<2>(ws, g); d = dotc(es, g); acc[6].add(d.x); acc[7].add(d.y);
+    gamma_apply<3>(ws, g); d = dotc(es, g); acc[8].add(d.x); acc[9].add(d.y);
+    const int xp = (x + 1 == Lx) ? s - (Lx - 1) : s + 1;
+    const int yp = (y + 1 == Ly) ? s - (Ly - 1) * Lx : s + Lx;
+    const int zp = (z + 1 == Lz) ? s - (Lz - 1) * Lx * Ly : s + Lx * Ly;
+    const int tp = (t + 1 == Lt) ? s - (Lt - 1) * Vs : s + Vs;
+    d = psplit<0>(U, er, wr, s, xp, V, es, ws); acc[10].add(kappa * d.x); acc[11].add(kappa * d.y);
+    d = psplit<1>(U, er, wr, s, yp, V, es, ws); acc[12].add(kappa * d.x); acc[13].add(kappa * d.y);
+    d = psplit<2>(U, er, wr, s, zp, V, es, ws); acc[14].add(kappa * d.x); acc[15].add(kappa * d.y);
+    d = psplit<3>(U, er, wr, s, tp, V, es, ws); acc[16].add(kappa * d.x); acc[17].add(kappa * d.y);
+  }
+  __shared__ double red[CBT / 32][18];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 18; ++q) {
+    double v = acc[q].value();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double re = 0.0, im = 0.0;
+    for (int q = 0; q < CBT / 32; ++q) {
+      re += red[q][2 * threadIdx.x];
+      im += red[q][2 * threadIdx.x + 1];
+    }
+    partial[(((long long)r * Lt + t) * nchunk + chunk) * 9 + threadIdx.x] = make_double2(re, im);
+  }
+}
+
+// out[(r * 9 + op) * Lt + t] = sum over chunks (fixed order)
+__global__ void contract_final(const double2 *__restrict__ partial, int nchunk, int Lt, int nrhs,
+                               double2 *__restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nrhs * 9 * Lt) return;
+  const int t = idx % Lt, op = (idx / Lt) % 9, r = idx / (9 * Lt);
+  double re = 0.0, ce = 0.0, im = 0.0, ci = 0.0;
+  for (int c = 0; c < nchunk; ++c) {
+    const double2 v = partial[(((long long)r * Lt + t) * nchunk + c) * 9 + op];
+    double tt = re + v.x;
+    ce += (fabs(re) >= fabs(v.x)) ? (re - tt) + v.x : (v.x - tt) + re;
+    re = tt;
+    tt = im + v.y;
+    ci += (fabs(im) >= fabs(v.y)) ? (im - tt) + v.y : (v.y - tt) + im;
+    im = tt;
+  }
+  out[idx] = make_double2(re + ce, im + ci);
+}
+
+// y = a * x + y over nrhs fields with a per-rhs scale a[r] (device); one thread per element
+__global__ void scaled_acc_kernel(const double2 *__restrict__ x, double2 *__restrict__ y, double2 a, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double2 v = y[e];
+    cfma(v, a, x[e]);
+    y[e] = v;
+  }
+}
+
+// Probe vectors: probe p of the batch = sum over the sites of colour class cls(p) of unit vectors
+// at spin-colour component comp(p); classes by (x mod px, y mod py, z mod pz, t mod pt).
+__global__ void probe_kernel(int first, int nprobe, int Lx, int Ly, int Lz, int Lt, int px, int py, int pz, int pt,
+                             double2 *__restrict__ out) {
+  const long long V = (long long)Lx * Ly * Lz * Lt;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (s >= V || p >= nprobe) return;
+  const int x = s % Lx, y = (s / Lx) % Ly, z = (s / (Lx * Ly)) % Lz, t = s / (Lx * Ly * Lz);
+  const int cls = (x % px) + px * ((y % py) + py * ((z % pz) + pz * (t % pt)));
+  const int g = first + p;
+  const int pc = g / 12, comp = g % 12;
+  double2 *o = out + ((long long)p * V + s) * 12;
+#pragma unroll
+  for (int e = 0; e < 12; ++e) o[e] = make_double2((cls == pc && e == comp) ? 1.0 : 0.0, 0.0);
+}
+
+template <typename T>
+lqcd_status download_v(lqcd_ctx *ctx, const void *dev, std::vector<T> &h, size_t count) {
+  h.resize(count);
+  if (!count) return LQCD_OK;
+  LQCD_CUDA(ctx, cudaMemcpyAsync(h.data(), dev, sizeof(T) * count, cudaMemcpyDeviceToHost, ctx->stream));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return LQCD_OK;
+}
+
+lqcd_status upload_v(lqcd_ctx *ctx, const void *host, void *dev, size_t bytes) {
+  if (!bytes) return LQCD_OK;
+  LQCD_CUDA(ctx, cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return LQCD_OK;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int probe_period(int L, int K) {
+  for (int p = K + 1; p < L; ++p)
+    if (L % p == 0) return p;
+  return L;
+}
+
+}  // namespace
+
+lqcd_status contract_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *eta, const double2 *w,
+                            int nrhs, double2 *out_dev) {
+  const int *d = ctx->dims;
+  const int Lt = d[3], Vs = d[0] * d[1] * d[2];
+  int nchunk = std::max(1, std::min((Vs + CBT - 1) / CBT, std::max(1, (4 * ctx->sms) / std::max(1, nrhs * Lt))));
+  void *p;
+  LQCD_TRY(ws_get(ctx, WS_EST2, sizeof(double2) * (size_t)nrhs * Lt * nchunk * 9, &p));
+  kbegin(ctx);
+  contract_kernel<<<dim3(nchunk * Lt, nrhs), CBT, 0, ctx->stream>>>(U, kappa, eta, w, d[0], d[1], d[2], d[3], nchunk,
+                                                                   (double2 *)p);
+  LQCD_TRY(launch_check(ctx, "contract_kernel", K_CONTRACT, (double)ctx->V * nrhs));
+  const int tot = nrhs * 9 * Lt;
+  kbegin(ctx);
+  contract_final<<<ceil_div(tot, 128), 128, 0, ctx->stream>>>((const double2 *)p, nchunk, Lt, nrhs, out_dev);
+  return launch_check(ctx, "contract_final", K_CONTRACT, 0.0);
+}
+
+static lqcd_status scaled_acc(lqcd_ctx *ctx, const double2 *x, double2 *y, cd a, long long n) {
+  kbegin(ctx);
+  scaled_acc_kernel<<<std::min(ceil_div(n, 256), 8 * ctx->sms), 256, 0, ctx->stream>>>(x, y, make_double2(a.real(), a.imag()), n);
+  return launch_check(ctx, "scaled_acc_kernel", K_BLAS1, (double)n);
+}
+
+// out = sum_k c_k (kappa P)^k eta   (c == NULL: all ones)
+static lqcd_status hop_series_dev(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *eta, double2 *out,
+                                  int nrhs, int K, const cd *c) {
+  const long long n = (long long)nrhs * ctx->N;
+  double2 *t0, *t1;
+  LQCD_TRY(ws_get(ctx, WS_TMP2, sizeof(double2) * (size_t)n, (void **)&t0));
+  LQCD_TRY(ws_get(ctx, WS_TMP3, sizeof(double2) * (size_t)n, (void **)&t1));
+  LQCD_TRY(blas_zero(ctx, out, n));
+  LQCD_TRY(scaled_acc(ctx, eta, out, c ? c[0] : cd(1.0, 0.0), n));
+  const double2 *cur = eta;
+  for (int k = 1; k < K; ++k) {
+    double2 *nxt = (k & 1) ? t0 : t1;
+    LQCD_TRY(wilson_launch(ctx, U, kappa, cur, nxt, nrhs, LQCD_PREC_F64, LQCD_APPLY_HOP));
+    // term_k = kappa P term_{k-1}: fold kappa^k into the coefficient
+    LQCD_TRY(scaled_acc(ctx, nxt, out, (c ? c[k] : cd(1.0, 0.0)) * std::pow(kappa, k), n));
+    cur = nxt;
+  }
+  return LQCD_OK;
+}
+
+// out = sum_j a_j M^j eta
+static lqcd_status poly_apply_dev(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *eta, double2 *out,
+                                  int nrhs, int n, const cd *a) {
+  const long long len = (long long)nrhs * ctx->N;
+  double2 *t0, *t1;
+  LQCD_TRY(ws_get(ctx, WS_TMP2, sizeof(double2) * (size_t)len, (void **)&t0));
+  LQCD_TRY(ws_get(ctx, WS_TMP3, sizeof(double2) * (size_t)len, (void **)&t1));
+  LQCD_TRY(blas_zero(ctx, out, len));
+  LQCD_TRY(scaled_acc(ctx, eta, out, a[0], len));
+  const double2 *cur = eta;
+  for (int j = 1; j <= n; ++j) {
+    double2 *nxt = (j & 1) ? t0 : t1;
+    LQCD_TRY(wilson_launch(ctx, U, kappa, cur, nxt, nrhs, LQCD_PREC_F64, LQCD_APPLY_M));
+    LQCD_TRY(scaled_acc(ctx, nxt, out, a[j], len));
+    cur = nxt;
+  }
+  return LQCD_OK;
+}
+
+// out = gamma_5 E diag(d) E^dag eta
+static lqcd_status deflate_dev(lqcd_ctx *ctx, const lqcd_defl *defl, const double2 *eta, double2 *out, int nrhs,
+                               const cd *d) {
+  const int k = defl->k;
+  const long long N = ctx->N;
+  double2 *coef, *tmp;
+  LQCD_TRY(ws_get(ctx, WS_EST1, sizeof(double2) * (size_t)k * nrhs, (void **)&coef));
+  LQCD_TRY(ws_get(ctx, WS_TMP4, sizeof(double2) * (size_t)nrhs * N, (void **)&tmp));
+  LQCD_TRY(blas_multidot(ctx, defl->E, N, 0, k, eta, N, nrhs, coef));
+  std::vector<double2> c;
+  LQCD_TRY(download_v(ctx, coef, c, (size_t)k * nrhs));
+  for (int q = 0; q < k; ++q)
+    for (int r = 0; r < nrhs; ++r) {
+      const double2 v = c[(size_t)q * nrhs + r];
+      const cd w = cd(v.x, v.y) * d[q];
+      c[(size_t)q * nrhs + r] = make_double2(w.real(), w.imag());
+    }
+  LQCD_TRY(upload_v(ctx, c.data(), coef, sizeof(double2) * c.size()));
+  LQCD_TRY(blas_combine(ctx, defl->E, N, 0, k, coef, 1, tmp, N, N, nrhs));
+  return blas_g5(ctx, tmp, out, nrhs);
+}
+
+// Min-Res coefficients: QR (classical Gram-Schmidt twice) of v = (M b, .., M^{n+1} b)
+static lqcd_status poly_coeffs_dev(lqcd_ctx *ctx, const double2 *U, double kappa, uint64_t seed, int n,
+                                   std::vector<cd> &a) {
+  const long long N = ctx->N;
+  double2 *Q, *b, *h;
+  double *nrm;
+  LQCD_TRY(ws_get(ctx, WS_PROBE, sizeof(double2) * (size_t)(n + 2) * N, (void **)&Q));
+  LQCD_TRY(ws_get(ctx, WS_TMP4, sizeof(double2) * (size_t)N, (void **)&b));
+  LQCD_TRY(ws_get(ctx, WS_EST1, sizeof(double2) * (size_t)(2 * (n + 2) + 4), (void **)&h));
+  nrm = (double *)(h + 2 * (n + 2));
+  LQCD_TRY(noise_launch(ctx, seed, 0xFFFFFFFFu, 1, b));
+  // column j of v is M^{j+1} b; build the powers in place, then orthogonalise
+  const double2 *prev = b;
+  for (int j = 0; j <= n; ++j) {
+    LQCD_TRY(wilson_launch(ctx, U, kappa, prev, Q + (long long)j * N, 1, LQCD_PREC_F64, LQCD_APPLY_M));
+    prev = Q + (long long)j * N;
+  }
+  dense::Mat R(n + 1, n + 1);
+  for (int j = 0; j <= n; ++j) {
+    double2 *w = Q + (long long)j * N;
+    std::vector<double2> h1, h2;
+    if (j > 0) {
+      LQCD_TRY(blas_multidot(ctx, Q, N, 0, j, w, N, 1, h));
+      LQCD_TRY(blas_multiaxpy(ctx, Q, N, 0, j, h, -1.0, w, N, 1));
+      LQCD_TRY(download_v(ctx, h, h1, j));
+      LQCD_TRY(blas_multidot(ctx, Q, N, 0, j, w, N, 1, h));
+      LQCD_TRY(blas_multiaxpy(ctx, Q, N, 0, j, h, -1.0, w, N, 1));
+      LQCD_TRY(download_v(ctx, h, h2, j));
+    }
+    LQCD_TRY(blas_norms(ctx, w, N, 1, nrm));
+    std::vector<double> nr;
+    LQCD_TRY(download_v(ctx, nrm, nr, 1));
+    for (int i = 0; i < j; ++i) R(i, j) = cd(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+    R(j, j) = nr[0];
+    if (!(nr[0] > 0.0)) return set_err(ctx, LQCD_ERR_INVALID_ARG, "poly_coeffs: Krylov powers are linearly dependent");
+    LQCD_TRY(blas_invscale(ctx, w, nrm, N, 1));
+  }
+  LQCD_TRY(blas_multidot(ctx, Q, N, 0, n + 1, b, N, 1, h));
+  std::vector<double2> y;
+  LQCD_TRY(download_v(ctx, h, y, n + 1));
+  a.assign(n + 1, cd(0.0, 0.0));
+  for (int i = n; i >= 0; --i) {
+    cd s = cd(y[i].x, y[i].y);
+    for (int j = i + 1; j <= n; ++j) s -= R(i, j) * a[j];
+    a[i] = s / R(i, i);
+  }
+  return LQCD_OK;
+}
+
+// t[(k * 9 + op) * Lt + t] for k < K
+static lqcd_status hop_traces_dev(lqcd_ctx *ctx, const double2 *U, double kappa, int K, std::vector<cd> &tr) {
+  const int *d = ctx->dims;
+  const int Lt = d[3];
+  const long long N = ctx->N;
+  const int px = probe_period(d[0], K), py = probe_period(d[1], K), pz = probe_period(d[2], K), pt = probe_period(d[3], K);
+  const long long nprobes = 12LL * px * py * pz * pt;
+  // probes per batch: bounded by memory (three probe-sized buffers) and by the launch grid
+  const int B = (int)std::min<long long>(nprobes, std::max<long long>(1, std::min<long long>(64, (1LL << 31) / (N * 16 * 3))));
+  double2 *Z, *W0, *W1, *cd_dev;
+  LQCD_TRY(ws_get(ctx, WS_PROBE, sizeof(double2) * (size_t)B * N, (void **)&Z));
+  LQCD_TRY(ws_get(ctx, WS_TMP2, sizeof(double2) * (size_t)B * N, (void **)&W0));
+  LQCD_TRY(ws_get(ctx, WS_TMP3, sizeof(double2) * (size_t)B * N, (void **)&W1));
+  LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)K * B * 9 * Lt, (void **)&cd_dev));
+  tr.assign((size_t)K * 9 * Lt, cd(0.0, 0.0));
+  std::vector<double2> h;
+  for (long long p0 = 0; p0 < nprobes; p0 += B) {
+    const int nb = (int)std::min<long long>(B, nprobes - p0);
+    kbegin(ctx);
+    probe_kernel<<<dim3(ceil_div(ctx->V, 128), nb), 128, 0, ctx->stream>>>((int)p0, nb, d[0], d[1], d[2], d[3], px, py,
+                                                                           pz, pt, Z);
+    LQCD_TRY(launch_check(ctx, "probe_kernel", K_PROBE, (double)ctx->V * nb));
+    LQCD_TRY(contract_launch(ctx, U, kappa, Z, Z, nb, cd_dev));
+    const double2 *cur = Z;
+    for (int k = 1; k < K; ++k) {
+      double2 *nxt = (k & 1) ? W0 : W1;
+      LQCD_TRY(wilson_launch(ctx, U, kappa, cur, nxt, nb, LQCD_PREC_F64, LQCD_APPLY_HOP));
+      LQCD_TRY(contract_launch(ctx, U, kappa, Z, nxt, nb, cd_dev + (size_t)k * nb * 9 * Lt));
+      cur = nxt;
+    }
+    LQCD_TRY(download_v(ctx, cd_dev, h, (size_t)K * nb * 9 * Lt));
+    for (int k = 0; k < K; ++k)
+      for (int p = 0; p < nb; ++p)
+        for (int q = 0; q < 9 * Lt; ++q) {
+          const double2 v = h[((size_t)k * nb + p) * 9 * Lt + q];
+          tr[(size_t)k * 9 * Lt + q] += cd(v.x, v.y);
+        }
+  }
+  return LQCD_OK;
+}
+
+// xi[q] = e_q^dag gamma_5 tilde M^{-1} e_q
+static lqcd_status xi_dev(lqcd_ctx *ctx, const double2 *U, double kappa, const lqcd_defl *defl, int sub, int K,
+                          const cd *coeffs, std::vector<cd> &xi) {
+  const int k = defl->k;
+  const long long N = ctx->N;
+  double2 *T, *G, *h;
+  LQCD_TRY(ws_get(ctx, WS_TMP5, sizeof(double2) * (size_t)k * N, (void **)&T));
+  LQCD_TRY(ws_get(ctx, WS_TMP1, sizeof(double2) * (size_t)k * N, (void **)&G));
+  LQCD_TRY(ws_get(ctx, WS_EST1, sizeof(double2) * (size_t)k, (void **)&h));
+  if (sub == LQCD_SUB_PERT) {
+    LQCD_TRY(hop_series_dev(ctx, U, kappa, defl->E, T, k, K, nullptr));
+  } else if (sub == LQCD_SUB_POLY) {
+    LQCD_TRY(poly_apply_dev(ctx, U, kappa, defl->E, T, k, K - 1, coeffs));
+  } else {
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "xi_inverse: sub must be LQCD_SUB_PERT or LQCD_SUB_POLY");
+  }
+  LQCD_TRY(blas_g5(ctx, T, G, k));
+  // per-vector dot <e_q, g5 T_q>: basis of right-hand side q is e_q itself (vrs = N)
+  LQCD_TRY(blas_multidot(ctx, defl->E, 0, N, 1, G, N, k, h));
+  std::vector<double2> hv;
+  LQCD_TRY(download_v(ctx, h, hv, k));
+  xi.resize(k);
+  for (int q = 0; q < k; ++q) xi[q] = cd(hv[q].x, hv[q].y);
+  return LQCD_OK;
+}
+
+// ---- C ABI -----------------------------------------------------------------------------------
+extern "C" {
+
+lqcd_status lqcd_contract(lqcd_ctx *ctx, const double *links, double kappa, const double *eta, const double *w,
+                          int nrhs, double *out) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !eta || !w || !out || nrhs < 1 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "contract: bad arguments");
+  double2 *dev;
+  const size_t cnt = (size_t)nrhs * 9 * ctx->dims[3];
+  LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * cnt, (void **)&dev));
+  LQCD_TRY(contract_launch(ctx, (const double2 *)links, kappa, (const double2 *)eta, (const double2 *)w, nrhs, dev));
+  LQCD_CUDA(ctx, cudaMemcpyAsync(out, dev, sizeof(double2) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_hop_series(lqcd_ctx *ctx, const double *links, double kappa, const double *eta, double *out, int nrhs,
+                            int K, const double *c) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !eta || !out || nrhs < 1 || K < 1 || K > 64 || eta == out)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "hop_series: bad arguments");
+  std::vector<cd> cc;
+  if (c) cc.assign((const cd *)c, (const cd *)c + K);
+  return hop_series_dev(ctx, (const double2 *)links, kappa, (const double2 *)eta, (double2 *)out, nrhs, K,
+                        c ? cc.data() : nullptr);
+}
+
+lqcd_status lqcd_poly_apply(lqcd_ctx *ctx, const double *links, double kappa, const double *eta, double *out, int nrhs,
+                            int n, const double *a) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !eta || !out || !a || nrhs < 1 || n < 0 || n > 64 || eta == out)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "poly_apply: bad arguments");
+  std::vector<cd> aa((const cd *)a, (const cd *)a + n + 1);
+  return poly_apply_dev(ctx, (const double2 *)links, kappa, (const double2 *)eta, (double2 *)out, nrhs, n, aa.data());
+}
+
+lqcd_status lqcd_poly_coeffs(lqcd_ctx *ctx, const double *links, double kappa, uint64_t seed, int n, double *a) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !a || n < 0 || n > 64) return set_err(ctx, LQCD_ERR_INVALID_ARG, "poly_coeffs: bad arguments");
+  std::vector<cd> av;
+  LQCD_TRY(poly_coeffs_dev(ctx, (const double2 *)links, kappa, seed, n, av));
+  memcpy(a, av.data(), sizeof(cd) * av.size());
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_deflate_project(lqcd_ctx *ctx, const lqcd_defl *defl, const double *eta, double *out, int nrhs,
+                                 const double *d) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!defl || !eta || !out || !d || nrhs < 1 || eta == out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "deflate_project: bad arguments");
+  std::vector<cd> dd((const cd *)d, (const cd *)d + defl->k);
+  return deflate_dev(ctx, defl, (const double2 *)eta, (double2 *)out, nrhs, dd.data());
+}
+
+lqcd_status lqcd_hop_traces(lqcd_ctx *ctx, const double *links, double kappa, int K, double *t) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !t || K < 1 || K > 64) return set_err(ctx, LQCD_ERR_INVALID_ARG, "hop_traces: bad arguments");
+  std::vector<cd> tr;
+  LQCD_TRY(hop_traces_dev(ctx, (const double2 *)links, kappa, K, tr));
+  memcpy(t, tr.data(), sizeof(cd) * tr.size());
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_xi_inverse(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, int sub, int K,
+                            const double *coeffs, double *xi) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !defl || !xi || K < 1 || K > 65 || (sub == LQCD_SUB_POLY && !coeffs))
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "xi_inverse: bad arguments");
+  std::vector<cd> cc;
+  if (coeffs) cc.assign((const cd *)coeffs, (const cd *)coeffs + K);
+  std::vector<cd> out;
+  LQCD_TRY(xi_dev(ctx, (const double2 *)links, kappa, defl, sub, K, coeffs ? cc.data() : nullptr, out));
+  memcpy(xi, out.data(), sizeof(cd) * out.size());
+  return LQCD_OK;
+}
+
+}  // extern "C"
+
+// ---- whole loop estimate ----------------------------------------------------------------------
+lqcd_status proj_core_entry(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, const double2 *b,
+                            double2 *x, int nrhs, const lqcd_krylov_opts *o, lqcd_solve_info *info);
+
+extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *o,
+                                          lqcd_estimate *out) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !o || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: NULL argument");
+  if (o->nnoise < 1 || o->block < 1 || o->m < 2 || o->k < 1 || o->k >= o->m || o->K < 1 || o->npoly < 0 ||
+      o->npoly > 63 || o->K > 64 || !(o->tol > 0) || !(o->tol_special > 0) || o->max_cycles < 1)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: bad options");
+  if (o->prec != LQCD_PREC_F64) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: only LQCD_PREC_F64");
+  const double2 *U = (const double2 *)links;
+  const int Lt = ctx->dims[3];
+  const long long N = ctx->N;
+  const int Kt = std::max(o->K, o->npoly + 1);
+  const int modes = o->modes ? o->modes : LQCD_SUB_ALL;
+  const double t0 = now_s();
+  // 1. special right-hand side: GMRES-DR on M (projection space), MINRES-DR on M' (eigenpairs)
+  double2 *x0;
+  LQCD_CUDA(ctx, cudaMalloc(&x0, sizeof(double2) * (size_t)N));
+  struct Guard {
+    void *p;
+    lqcd_defl *a, *b;
+    ~Guard() {
+      if (p) cudaFree(p);
+      if (a) lqcd_defl_destroy(a);
+      if (b) lqcd_defl_destroy(b);
+    }
+  } guard{x0, nullptr, nullptr};
+  double2 *bs;
+  LQCD_CUDA(ctx, cudaMalloc(&bs, sizeof(double2) * (size_t)N));
+  struct Guard2 { void *p; ~Guard2() { if (p) cudaFree(p); } } g2{bs};
+  LQCD_TRY(noise_launch(ctx, o->seed, 0xFFFFFFFEu, 1, bs));
+  lqcd_krylov_opts ko{o->m, o->k, o->tol_special, o->max_cycles, LQCD_SYS_M, LQCD_PREC_F64};
+  lqcd_solve_info si{};
+  lqcd_status st = lqcd_gmresdr_solve(ctx, links, kappa, (const double *)bs, (double *)x0, 1, &ko, &si, &guard.a);
+  if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
+  long matvecs_setup = si.matvecs;
+  st = lqcd_minresdr_solve(ctx, links, kappa, (const double *)bs, (double *)x0, 1, &ko, &si, &guard.b);
+  if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
+  matvecs_setup += si.matvecs;
+  const lqcd_defl *dm = guard.a, *dh = guard.b;
+  if (!dm || !dh) return set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop_estimate: no deflation space");
+  const int Q = dh->k;
+  // 2. Min-Res polynomial, 3. hopping traces and 1/xi'
+  std::vector<cd> a;
+  LQCD_TRY(poly_coeffs_dev(ctx, U, kappa, o->seed, o->npoly, a));
+  matvecs_setup += o->npoly + 1;
+  std::vector<cd> bcoef(o->npoly + 1, cd(0.0, 0.0));  // b_k = (-1)^k sum_{j>=k} C(j,k) a_j
+  for (int k = 0; k <= o->npoly; ++k) {
+    double binom = 1.0;  // C(j, k) for j = k
+    for (int j = k; j <= o->npoly; ++j) {
+      bcoef[k] += ((k & 1) ? -1.0 : 1.0) * binom * a[j];
+      binom = binom * (j + 1) / (j + 1 - k);
+    }
+  }
+  std::vector<cd> tr;
+  LQCD_TRY(hop_traces_dev(ctx, U, kappa, Kt, tr));
+  std::vector<cd> xi_p, xi_q;
+  LQCD_TRY(xi_dev(ctx, U, kappa, dh, LQCD_SUB_PERT, o->K, nullptr, xi_p));
+  LQCD_TRY(xi_dev(ctx, U, kappa, dh, LQCD_SUB_POLY, o->npoly + 1, a.data(), xi_q));
+  // eigen add-back densities: contract(e_q, g5 e_q) per q
+  std::vector<cd> eig_t((size_t)Q * 9 * Lt);
+  {
+    double2 *G, *cdv;
+    LQCD_TRY(ws_get(ctx, WS_TMP1, sizeof(double2) * (size_t)Q * N, (void **)&G));
+    LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)Q * 9 * Lt, (void **)&cdv));
+    LQCD_TRY(blas_g5(ctx, dh->E, G, Q));
+    LQCD_TRY(contract_launch(ctx, U, kappa, dh->E, G, Q, cdv));
+    std::vector<double2> h;
+    LQCD_TRY(download_v(ctx, cdv, h, (size_t)Q * 9 * Lt));
+    for (size_t i = 0; i < h.size(); ++i) eig_t[i] = cd(h[i].x, h[i].y);
+  }
+  std::vector<cd> lam(Q), dl(Q), dlp(Q), dlq(Q);
+  for (int q = 0; q < Q; ++q) {
+    lam[q] = cd(dh->lam[q].x, dh->lam[q].y);
+    dl[q] = 1.0 / lam[q];
+    dlp[q] = 1.0 / lam[q] - xi_p[q];
+    dlq[q] = 1.0 / lam[q] - xi_q[q];
+  }
+  // add-backs per mode [6][9][Lt]
+  std::vector<cd> add((size_t)LQCD_NMODES * 9 * Lt, cd(0.0, 0.0));
+  auto A = [&](int mode, int op, int t) -> cd & { return add[((size_t)mode * 9 + op) * Lt + t]; };
+  for (int op = 0; op < 9; ++op)
+    for (int t = 0; t < Lt; ++t) {
+      cd pert = 0.0, poly = 0.0, e1 = 0.0, ep = 0.0, eq = 0.0;
+      double kk = 1.0;
+      for (int k = 0; k < Kt; ++k) {
+        const cd tk = tr[((size_t)k * 9 + op) * Lt + t];
+        if (k < o->K) pert += kk * tk;
+        if (k <= o->npoly) poly += bcoef[k] * kk * tk;
+        kk *= kappa;
+      }
+      for (int q = 0; q < Q; ++q) {
+        const cd et = eig_t[((size_t)q * 9 + op) * Lt + t];
+        e1 += dl[q] * et;
+        ep += dlp[q] * et;
+        eq += dlq[q] * et;
+      }
+      A(1, op, t) = pert;
+      A(2, op, t) = poly;
+      A(3, op, t) = e1;
+      A(4, op, t) = pert + ep;
+      A(5, op, t) = poly + eq;
+    }
+  const double t1 = now_s();
+  // 4. noise blocks
+  const int bw = std::min(o->block, o->nnoise);
+  const long long bn = (long long)bw * N;
+  double2 *eta, *x, *xp, *xq, *y, *w, *cdv;
+  LQCD_CUDA(ctx, cudaMalloc(&eta, sizeof(double2) * (size_t)bn * 6));
+  struct Guard3 { void *p; ~Guard3() { if (p) cudaFree(p); } } g3{eta};
+  x = eta + bn;
+  xp = x + bn;
+  xq = xp + bn;
+  y = xq + bn;
+  w = y + bn;
+  LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)bw * 9 * Lt, (void **)&cdv));
+  const int nn = o->nnoise;
+  std::vector<cd> per_noise_t((size_t)LQCD_NMODES * nn * 9 * Lt, cd(0.0, 0.0));
+  lqcd_krylov_opts po{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, LQCD_PREC_F64};
+  long matvecs_noise = 0;
+  double worst = 0.0;
+  int conv = 1;
+  std::vector<double2> h;
+  for (int first = 0; first < nn; first += bw) {
+    const int nb = std::min(bw, nn - first);
+    const long long len = (long long)nb * N;
+    LQCD_TRY(noise_launch(ctx, o->seed, (uint32_t)first, nb, eta));
+    lqcd_solve_info pi{};
+    st = proj_core_entry(ctx, links, kappa, dm, eta, x, nb, &po, &pi);
+    if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
+    if (!pi.converged) conv = 0;
+    worst = std::max(worst, pi.true_resid);
+    matvecs_noise += pi.matvecs;
+    const bool need_p = modes & (LQCD_SUB_PERT | LQCD_SUB_DEFL_PERT);
+    const bool need_q = modes & (LQCD_SUB_POLY | LQCD_SUB_DEFL_POLY);
+    if (need_p) LQCD_TRY(hop_series_dev(ctx, U, kappa, eta, xp, nb, o->K, nullptr));
+    if (need_q) LQCD_TRY(poly_apply_dev(ctx, U, kappa, eta, xq, nb, o->npoly, a.data()));
+    for (int mode = 0; mode < LQCD_NMODES; ++mode) {
+      if (!(modes & (1 << mode))) continue;
+      // w = x - tilde x
+      LQCD_TRY(blas_copy(ctx, x, w, len));
+      if (mode == 1 || mode == 4) LQCD_TRY(scaled_acc(ctx, xp, w, cd(-1.0, 0.0), len));
+      if (mode == 2 || mode == 5) LQCD_TRY(scaled_acc(ctx, xq, w, cd(-1.0, 0.0), len));
+      if (mode >= 3) {
+        const cd *dv = (mode == 3) ? dl.data() : (mode == 4 ? dlp.data() : dlq.data());
+        LQCD_TRY(deflate_dev(ctx, dh, eta, y, nb, dv));
+        LQCD_TRY(scaled_acc(ctx, y, w, cd(-1.0, 0.0), len));
+      }
+      LQCD_TRY(contract_launch(ctx, U, kappa, eta, w, nb, cdv));
+      LQCD_TRY(download_v(ctx, cdv, h, (size_t)nb * 9 * Lt));
+      for (int r = 0; r < nb; ++r)
+        for (int q = 0; q < 9 * Lt; ++q)
+          per_noise_t[(((size_t)mode * nn + first + r) * 9 * Lt) + q] = cd(h[(size_t)r * 9 * Lt + q].x, h[(size_t)r * 9 * Lt + q].y);
+    }
+  }
+  const double t2 = now_s();
+  // 5. summary
+  for (int mode = 0; mode < LQCD_NMODES; ++mode) {
+    for (int op = 0; op < 9; ++op) {
+      cd addtot = 0.0;
+      for (int t = 0; t < Lt; ++t) addtot += A(mode, op, t);
+      std::vector<cd> tot(nn);
+      for (int n = 0; n < nn; ++n) {
+        cd s = 0.0;
+        for (int t = 0; t < Lt; ++t) s += per_noise_t[(((size_t)mode * nn + n) * 9 + op) * Lt + t];
+        tot[n] = s + addtot;
+        if (out->per_noise) {
+          out->per_noise[((((size_t)mode * nn + n) * 9 + op) * 2)] = tot[n].real();
+          out->per_noise[((((size_t)mode * nn + n) * 9 + op) * 2) + 1] = tot[n].imag();
+        }
+      }
+      cd mean = 0.0;
+      for (int n = 0; n < nn; ++n) mean += tot[n];
+      mean /= (double)nn;
+      double ps = 0.0, pm = 0.0;
+      for (int n = 0; n < nn; ++n) pm += (op == 0) ? tot[n].real() : tot[n].imag();
+      pm /= nn;
+      for (int n = 0; n < nn; ++n) {
+        const double v = ((op == 0) ? tot[n].real() : tot[n].imag()) - pm;
+        ps += v * v;
+      }
+      const double err = nn > 1 ? std::sqrt(ps / (nn - 1)) / std::sqrt((double)nn) : NAN;
+      if (out->mean) {
+        out->mean[((size_t)mode * 9 + op) * 2] = mean.real();
+        out->mean[((size_t)mode * 9 + op) * 2 + 1] = mean.imag();
+      }
+      if (out->stderr_) out->stderr_[(size_t)mode * 9 + op] = err;
+      for (int t = 0; t < Lt; ++t) {
+        cd pt = 0.0;
+        for (int n = 0; n < nn; ++n) pt += per_noise_t[(((size_t)mode * nn + n) * 9 + op) * Lt + t];
+        pt /= (double)nn;
+        if (out->per_t) {
+          out->per_t[(((size_t)mode * 9 + op) * Lt + t) * 2] = pt.real();
+          out->per_t[(((size_t)mode * 9 + op) * Lt + t) * 2 + 1] = pt.imag();
+        }
+        if (out->addback) {
+          out->addback[(((size_t)mode * 9 + op) * Lt + t) * 2] = A(mode, op, t).real();
+          out->addback[(((size_t)mode * 9 + op) * Lt + t) * 2 + 1] = A(mode, op, t).imag();
+        }
+      }
+    }
+  }
+  if (out->lam) memcpy(out->lam, lam.data(), sizeof(cd) * Q);
+  if (out->poly_a) memcpy(out->poly_a, a.data(), sizeof(cd) * a.size());
+  out->matvecs_setup = matvecs_setup + (long)Q * (o->K - 1 + o->npoly);
+  out->matvecs_noise = matvecs_noise;
+  out->seconds_setup = t1 - t0;
+  out->seconds_noise = t2 - t1;
+  out->max_true_resid = worst;
+  out->converged = conv;
+  return conv ? LQCD_OK : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop_estimate: a noise solve did not converge (rel %.3e)", worst);
+}

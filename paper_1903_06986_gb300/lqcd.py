@@ -1,0 +1,387 @@
+"""Thin ctypes binding of liblqcd (include/lqcd.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts torch tensors (complex128,
+contiguous, on the context's device) to raw pointers and host arrays to ctypes buffers.  There is
+no fallback: if the library is missing or a call fails, an exception is raised.
+
+Shapes: gauge links (4, T, Z, Y, X, 3, 3); a block of fields (nrhs, T, Z, Y, X, 4, 3), or one
+field (T, Z, Y, X, 4, 3).  Lattice dims are given as (Lx, Ly, Lz, Lt).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_INVALID_ARG, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_OOM = range(7)
+PREC_F64, PREC_F32 = 0, 1
+APPLY_M, APPLY_G5R, APPLY_DAG, APPLY_HOP = 0, 1, 2, 3
+SYS_M, SYS_MG5 = 0, 1
+SUB_NONE, SUB_PERT, SUB_POLY, SUB_DEFL, SUB_DEFL_PERT, SUB_DEFL_POLY = (1 << i for i in range(6))
+SUB_ALL = 63
+MODES = ["none", "pert", "poly", "defl", "defl_pert", "defl_poly"]
+NOPS = 9
+KERNEL_CLASSES = ["wilson", "dot", "axpy", "combine", "norm", "contract", "blas1", "noise", "probe"]
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("lqcd status %d: %s" % (status, msg))
+        self.status = status
+
+
+class KrylovOpts(C.Structure):
+    _fields_ = [("m", C.c_int), ("k", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int),
+                ("system", C.c_int), ("prec", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("matvecs", C.c_long), ("converged", C.c_int),
+                ("true_resid", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class EstOpts(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("nnoise", C.c_int), ("block", C.c_int), ("m", C.c_int), ("k", C.c_int),
+                ("m_inner", C.c_int), ("K", C.c_int), ("npoly", C.c_int), ("tol", C.c_double),
+                ("tol_special", C.c_double), ("max_cycles", C.c_int), ("modes", C.c_int), ("prec", C.c_int)]
+
+
+_dp = C.POINTER(C.c_double)
+
+
+class Estimate(C.Structure):
+    _fields_ = [("per_noise", _dp), ("per_t", _dp), ("addback", _dp), ("mean", _dp), ("stderr_", _dp),
+                ("lam", _dp), ("poly_a", _dp), ("matvecs_setup", C.c_long), ("matvecs_noise", C.c_long),
+                ("seconds_setup", C.c_double), ("seconds_noise", C.c_double), ("max_true_resid", C.c_double),
+                ("converged", C.c_int)]
+
+
+_LIB = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(path=None):
+    """Load liblqcd.so (built by paper_1903_06986_gb300.build); raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("liblqcd.so not found at %s: run `python -m paper_1903_06986_gb300.build`" % path)
+    lib = C.CDLL(path)
+    vp, i, d, u64, u32 = C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_uint32
+    sig = {
+        "lqcd_ctx_create": [C.POINTER(vp), C.POINTER(C.c_int), i, vp],
+        "lqcd_ctx_destroy": [vp],
+        "lqcd_set_stream": [vp, vp],
+        "lqcd_noise_z4": [vp, u64, u32, i, vp],
+        "lqcd_wilson_apply": [vp, vp, d, vp, vp, i, i, i],
+        "lqcd_gmresdr_solve": [vp, vp, d, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo), C.POINTER(vp)],
+        "lqcd_minresdr_solve": [vp, vp, d, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo), C.POINTER(vp)],
+        "lqcd_proj_solve": [vp, vp, d, vp, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo)],
+        "lqcd_defl_destroy": [vp],
+        "lqcd_defl_info": [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+        "lqcd_defl_export": [vp, vp, vp, vp, vp, vp],
+        "lqcd_defl_import": [vp, i, vp, vp, C.POINTER(vp)],
+        "lqcd_deflate_project": [vp, vp, vp, vp, i, vp],
+        "lqcd_hop_series": [vp, vp, d, vp, vp, i, i, vp],
+        "lqcd_poly_apply": [vp, vp, d, vp, vp, i, i, vp],
+        "lqcd_poly_coeffs": [vp, vp, d, u64, i, vp],
+        "lqcd_hop_traces": [vp, vp, d, i, vp],
+        "lqcd_xi_inverse": [vp, vp, d, vp, i, i, vp, vp],
+        "lqcd_contract": [vp, vp, d, vp, vp, i, vp],
+        "lqcd_loop_estimate": [vp, vp, d, C.POINTER(EstOpts), C.POINTER(Estimate)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.lqcd_last_error_string.argtypes = [vp]
+    lib.lqcd_last_error_string.restype = C.c_char_p
+    lib.lqcd_version.argtypes = []
+    lib.lqcd_version.restype = C.c_char_p
+    lib.lqcd_kernel_launches.argtypes = [vp]
+    lib.lqcd_kernel_launches.restype = C.c_long
+    lib.lqcd_timing_enable.argtypes = [vp, i]
+    lib.lqcd_timing_enable.restype = C.c_int
+    lib.lqcd_timing_reset.argtypes = [vp]
+    lib.lqcd_timing_reset.restype = C.c_int
+    lib.lqcd_timing_read.argtypes = [vp, i, C.POINTER(C.c_double), C.POINTER(C.c_long), C.POINTER(C.c_double)]
+    lib.lqcd_timing_read.restype = C.c_int
+    _LIB = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or t.dtype != torch.complex128 or not t.is_contiguous():
+        raise ValueError("tensors must be contiguous complex128 CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _host_c(arr):
+    a = np.ascontiguousarray(np.asarray(arr, dtype=np.complex128))
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+class Defl:
+    """A deflation space made by a solver (V_{k+1}, Hbar_k, Ritz pairs) or imported eigenpairs."""
+
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.h = handle
+
+    @property
+    def k(self):
+        k, herm = C.c_int(), C.c_int()
+        self.ctx._check(self.ctx.lib.lqcd_defl_info(self.h, C.byref(k), C.byref(herm)))
+        return k.value
+
+    def export(self, basis=True, eigvecs=True):
+        torch = _torch()
+        k = self.k
+        N = self.ctx.N
+        V = torch.empty((k + 1, N), dtype=torch.complex128, device=self.ctx.device) if basis else None
+        E = torch.empty((k, N), dtype=torch.complex128, device=self.ctx.device) if eigvecs else None
+        H = np.zeros((k + 1, k), dtype=np.complex128) if basis else None
+        lam = np.zeros(k, dtype=np.complex128)
+        eres = np.zeros(k, dtype=np.float64)
+        self.ctx._check(self.ctx.lib.lqcd_defl_export(
+            self.h, _ptr(V), H.ctypes.data_as(C.c_void_p) if H is not None else None,
+            lam.ctypes.data_as(C.c_void_p), _ptr(E), eres.ctypes.data_as(C.c_void_p)))
+        return dict(V=V, Hbar=H, lam=lam, E=E, eig_resid=eres)
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.lqcd_defl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """An lqcd_ctx bound to the current CUDA device and torch's current stream."""
+
+    def __init__(self, dims, stream=None):
+        torch = _torch()
+        self.lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        self.N = 12 * self.V
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        h = C.c_void_p()
+        dd = (C.c_int * 4)(*self.dims)
+        st = self.lib.lqcd_ctx_create(C.byref(h), dd, 18, C.c_void_p(s))
+        if st != OK:
+            raise LqcdError(st, "lqcd_ctx_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lqcd_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise LqcdError(st, self.lib.lqcd_last_error_string(self.h).decode())
+        return st
+
+    @property
+    def launches(self):
+        return self.lib.lqcd_kernel_launches(self.h)
+
+    def timing(self, enable):
+        """Bracket every kernel launch with CUDA events (diagnostics)."""
+        self._check(self.lib.lqcd_timing_enable(self.h, 1 if enable else 0))
+
+    def timing_reset(self):
+        self._check(self.lib.lqcd_timing_reset(self.h))
+
+    def timing_read(self):
+        """{class: (total device ms, launches, work units)} since the last reset."""
+        out = {}
+        for i, name in enumerate(KERNEL_CLASSES):
+            ms, n, u = C.c_double(), C.c_long(), C.c_double()
+            self._check(self.lib.lqcd_timing_read(self.h, i, C.byref(ms), C.byref(n), C.byref(u)))
+            out[name] = (ms.value, n.value, u.value)
+        return out
+
+    def set_stream(self, stream):
+        self._check(self.lib.lqcd_set_stream(self.h, C.c_void_p(stream)))
+
+    def field(self, nrhs=None):
+        torch = _torch()
+        lx, ly, lz, lt = self.dims
+        shp = (lt, lz, ly, lx, 4, 3) if nrhs is None else (nrhs, lt, lz, ly, lx, 4, 3)
+        return torch.empty(shp, dtype=torch.complex128, device=self.device)
+
+    def _nrhs(self, t):
+        n = t.numel() // self.N
+        if n * self.N != t.numel():
+            raise ValueError("field size %d is not a multiple of 12 V = %d" % (t.numel(), self.N))
+        return n
+
+    # a1
+    def noise_z4(self, seed, first, nrhs, out=None):
+        out = self.field(nrhs) if out is None else out
+        self._check(self.lib.lqcd_noise_z4(self.h, seed, first, nrhs, _ptr(out)))
+        return out
+
+    # a2
+    def wilson_apply(self, links, kappa, inp, out=None, flags=APPLY_M, prec=PREC_F64):
+        out = _torch().empty_like(inp) if out is None else out
+        self._check(self.lib.lqcd_wilson_apply(self.h, _ptr(links), kappa, _ptr(inp), _ptr(out),
+                                               self._nrhs(inp), prec, flags))
+        return out
+
+    # a3 / a4
+    def _krylov(self, fn, links, kappa, b, m, k, tol, max_cycles, system, want_defl, prec):
+        x = _torch().empty_like(b)
+        o = KrylovOpts(m, k, tol, max_cycles, system, prec)
+        info = SolveInfo()
+        dh = C.c_void_p()
+        st = fn(self.h, _ptr(links), kappa, _ptr(b), _ptr(x), self._nrhs(b), C.byref(o), C.byref(info),
+                C.byref(dh) if want_defl else None)
+        if st not in (OK, ERR_NOT_CONVERGED):
+            self._check(st)
+        defl = Defl(self, dh) if (want_defl and dh.value) else None
+        return x, info.as_dict(), defl
+
+    def gmresdr_solve(self, links, kappa, b, m, k, tol, max_cycles=1000, system=SYS_M, want_defl=False,
+                      prec=PREC_F64):
+        return self._krylov(self.lib.lqcd_gmresdr_solve, links, kappa, b, m, k, tol, max_cycles, system,
+                            want_defl, prec)
+
+    def minresdr_solve(self, links, kappa, b, m, k, tol, max_cycles=1000, want_defl=False, prec=PREC_F64):
+        return self._krylov(self.lib.lqcd_minresdr_solve, links, kappa, b, m, k, tol, max_cycles, SYS_MG5,
+                            want_defl, prec)
+
+    # a5
+    def proj_solve(self, links, kappa, defl, b, m, tol, max_cycles=1000, system=SYS_M, prec=PREC_F64):
+        x = _torch().empty_like(b)
+        o = KrylovOpts(m, 0, tol, max_cycles, system, prec)
+        info = SolveInfo()
+        st = self.lib.lqcd_proj_solve(self.h, _ptr(links), kappa, defl.h, _ptr(b), _ptr(x), self._nrhs(b),
+                                      C.byref(o), C.byref(info))
+        if st not in (OK, ERR_NOT_CONVERGED):
+            self._check(st)
+        return x, info.as_dict()
+
+    def defl_import(self, E, lam):
+        lamh, lp = _host_c(lam)
+        dh = C.c_void_p()
+        self._check(self.lib.lqcd_defl_import(self.h, len(lamh), _ptr(E), lp, C.byref(dh)))
+        return Defl(self, dh)
+
+    # a6
+    def deflate_project(self, defl, eta, d):
+        out = _torch().empty_like(eta)
+        dh, dp = _host_c(d)
+        self._check(self.lib.lqcd_deflate_project(self.h, defl.h, _ptr(eta), _ptr(out), self._nrhs(eta), dp))
+        return out
+
+    # a7 / a8
+    def hop_series(self, links, kappa, eta, K, c=None):
+        out = _torch().empty_like(eta)
+        if c is not None:
+            ch, cp = _host_c(c)
+        else:
+            cp = None
+        self._check(self.lib.lqcd_hop_series(self.h, _ptr(links), kappa, _ptr(eta), _ptr(out), self._nrhs(eta),
+                                             K, cp))
+        return out
+
+    def poly_apply(self, links, kappa, eta, a):
+        out = _torch().empty_like(eta)
+        ah, ap = _host_c(a)
+        self._check(self.lib.lqcd_poly_apply(self.h, _ptr(links), kappa, _ptr(eta), _ptr(out), self._nrhs(eta),
+                                             len(ah) - 1, ap))
+        return out
+
+    def poly_coeffs(self, links, kappa, seed, n):
+        a = np.zeros(n + 1, dtype=np.complex128)
+        self._check(self.lib.lqcd_poly_coeffs(self.h, _ptr(links), kappa, seed, n, a.ctypes.data_as(C.c_void_p)))
+        return a
+
+    # a9
+    def hop_traces(self, links, kappa, K):
+        t = np.zeros((K, NOPS, self.dims[3]), dtype=np.complex128)
+        self._check(self.lib.lqcd_hop_traces(self.h, _ptr(links), kappa, K, t.ctypes.data_as(C.c_void_p)))
+        return t
+
+    # a10
+    def xi_inverse(self, links, kappa, defl, sub, K, coeffs=None):
+        xi = np.zeros(defl.k, dtype=np.complex128)
+        if coeffs is not None:
+            ch, cp = _host_c(coeffs)
+        else:
+            cp = None
+        self._check(self.lib.lqcd_xi_inverse(self.h, _ptr(links), kappa, defl.h, sub, K, cp,
+                                             xi.ctypes.data_as(C.c_void_p)))
+        return xi
+
+    # a11
+    def contract(self, links, kappa, eta, w):
+        n = self._nrhs(eta)
+        out = np.zeros((n, NOPS, self.dims[3]), dtype=np.complex128)
+        self._check(self.lib.lqcd_contract(self.h, _ptr(links), kappa, _ptr(eta), _ptr(w), n,
+                                           out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    # whole path
+    def loop_estimate(self, links, kappa, seed, nnoise, block, m, k, K, npoly, tol, tol_special,
+                      m_inner=0, max_cycles=2000, modes=SUB_ALL, prec=PREC_F64):
+        lt = self.dims[3]
+        o = EstOpts(seed, nnoise, block, m, k, m_inner, K, npoly, tol, tol_special, max_cycles, modes, prec)
+        per_noise = np.zeros((6, nnoise, NOPS), dtype=np.complex128)
+        per_t = np.zeros((6, NOPS, lt), dtype=np.complex128)
+        addback = np.zeros((6, NOPS, lt), dtype=np.complex128)
+        mean = np.zeros((6, NOPS), dtype=np.complex128)
+        err = np.zeros((6, NOPS), dtype=np.float64)
+        lam = np.zeros(k, dtype=np.complex128)
+        pa = np.zeros(npoly + 1, dtype=np.complex128)
+        as_dp = lambda a: a.ctypes.data_as(_dp)
+        est = Estimate(as_dp(per_noise), as_dp(per_t), as_dp(addback), as_dp(mean), as_dp(err), as_dp(lam),
+                       as_dp(pa), 0, 0, 0.0, 0.0, 0.0, 0)
+        st = self.lib.lqcd_loop_estimate(self.h, _ptr(links), kappa, C.byref(o), C.byref(est))
+        if st not in (OK, ERR_NOT_CONVERGED):
+            self._check(st)
+        return dict(per_noise=per_noise, per_t=per_t, addback=addback, mean=mean, stderr=err, lam=lam,
+                    poly_a=pa, matvecs_setup=est.matvecs_setup, matvecs_noise=est.matvecs_noise,
+                    seconds_setup=est.seconds_setup, seconds_noise=est.seconds_noise,
+                    max_true_resid=est.max_true_resid, converged=bool(est.converged), status=st)
+
+
+def header_functions(header=None):
+    """Names of the functions declared in include/lqcd.h (for the ABI export check)."""
+    import re
+    header = header or os.path.join(_build.ROOT, "include", "lqcd.h")
+    txt = open(header).read()
+    return sorted(set(re.findall(r"\b(lqcd_[a-z0-9_]+)\s*\(", txt)))

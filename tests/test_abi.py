@@ -1,0 +1,42 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports every function that
+include/lqcd.h declares.  No compute call is made (there is no GPU here)."""
+import ctypes
+import shutil
+
+import pytest
+
+from paper_1903_06986_gb300 import build, lqcd
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not __import__("os").path.exists(build.LIB):
+        pytest.skip("nvcc not available")
+    build.build()
+    return lqcd.load()
+
+
+def test_header_declares_the_boundary():
+    names = lqcd.header_functions()
+    for required in ["lqcd_wilson_apply", "lqcd_gmresdr_solve", "lqcd_minresdr_solve", "lqcd_deflate_project",
+                     "lqcd_loop_estimate", "lqcd_noise_z4", "lqcd_ctx_create", "lqcd_hop_traces",
+                     "lqcd_poly_coeffs", "lqcd_proj_solve", "lqcd_contract", "lqcd_xi_inverse"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    raw = ctypes.CDLL(build.LIB)
+    missing = [n for n in lqcd.header_functions() if not hasattr(raw, n)]
+    assert missing == []
+
+
+def test_version_and_argument_checks(lib):
+    assert b"sm_103a" in lib.lqcd_version()
+    # argument validation happens before any CUDA call
+    assert lib.lqcd_ctx_create(None, None, 18, None) == lqcd.ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    bad = (ctypes.c_int * 4)(4, 4, 1, 4)
+    assert lib.lqcd_ctx_create(ctypes.byref(h), bad, 18, None) == lqcd.ERR_INVALID_ARG
+    good = (ctypes.c_int * 4)(4, 4, 4, 4)
+    assert lib.lqcd_ctx_create(ctypes.byref(h), good, 12, None) == lqcd.ERR_INVALID_ARG
+    assert lib.lqcd_wilson_apply(None, None, 0.1, None, None, 1, 0, 0) == lqcd.ERR_INVALID_ARG

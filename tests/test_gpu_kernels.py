@@ -1,0 +1,153 @@
+"""GPU parity of the single-step kernels against the oracle, element by element, on seeded inputs:
+Z(4) noise (bit-exact), the Wilson operator in all four forms, the contractions, the PS and POLY
+series, the deflation projection, 1/xi', the Min-Res coefficients and the hopping traces.
+Lattices span several thread blocks and ragged tails (odd extents, V not a multiple of 128)."""
+import numpy as np
+import pytest
+
+from oracle import lattice as L, operators as O, rng, subtract as S
+from paper_1903_06986_gb300 import synth
+from tests.gpu_util import context, dev, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [(2, 2, 2, 2), (4, 4, 4, 4), (3, 5, 2, 7), (8, 8, 8, 16)]
+FP64_TOL = 1e-14       # one operator application: a few roundings per output
+CONTRACT_TOL = 1e-13   # sums of 12 V terms with compensated accumulation
+
+
+def rand_fields(dims, n, seed):
+    r = np.random.default_rng(seed)
+    shp = L.field_shape(dims, (n,))
+    return r.standard_normal(shp) + 1j * r.standard_normal(shp)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+def test_noise_bit_exact(dims):
+    ctx = context(dims)
+    for seed, first, n in [(1, 0, 3), ((7 << 40) + 12345, 1000, 2), (99, rng.NOISE_SPECIAL, 2)]:
+        got = host(ctx.noise_z4(seed, first, n))
+        ref = rng.z4_block(seed, first, n, dims)
+        assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+def test_wilson_all_forms(dims):
+    ctx = context(dims)
+    U = synth.su3_links(dims, 0.45, 3)
+    kappa = 0.1537
+    psi = rand_fields(dims, 3, 4)
+    Ud, pd = dev(U), dev(psi)
+    forms = {0: lambda f: L.wilson(U, kappa, f), 1: lambda f: L.wilson_g5(U, kappa, f),
+             2: lambda f: L.wilson_dag(U, kappa, f), 3: lambda f: L.hop(U, f)}
+    for flag, ref in forms.items():
+        got = host(ctx.wilson_apply(Ud, kappa, pd, flags=flag))
+        assert rel_err(got, ref(psi)) < FP64_TOL, flag
+    # FP32 arithmetic on the same data (the inner operator of mixed precision)
+    got = host(ctx.wilson_apply(Ud, kappa, pd, flags=0, prec=1))
+    assert rel_err(got, forms[0](psi)) < 2e-6
+
+
+@pytest.mark.parametrize("dims", DIMS[:3])
+def test_contract_all_operators(dims):
+    ctx = context(dims)
+    U = synth.su3_links(dims, 0.5, 5)
+    kappa = 0.14
+    eta, w = rand_fields(dims, 2, 6), rand_fields(dims, 2, 7)
+    got = ctx.contract(dev(U), kappa, dev(eta), dev(w))
+    ref = O.per_t(O.densities(U, kappa, eta, w)).transpose(1, 0, 2)   # [n, op, t]
+    assert rel_err(got, ref) < CONTRACT_TOL
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (3, 5, 2, 7)])
+def test_hop_series_and_poly(dims):
+    ctx = context(dims)
+    U = synth.su3_links(dims, 0.45, 8)
+    kappa = 0.15
+    eta = rng.z4_block(3, 0, 2, dims)
+    Ud, ed = dev(U), dev(eta)
+    got = host(ctx.hop_series(Ud, kappa, ed, 7))
+    assert rel_err(got, S.hop_series(U, kappa, eta, 7)) < 1e-13
+    c = np.array([1.0, 0.5 - 0.25j, 2.0, -1.0, 0.1j])
+    got = host(ctx.hop_series(Ud, kappa, ed, 5, c))
+    ref = sum(c[k] * S.hop_series(U, kappa, eta, k + 1) - (c[k] * S.hop_series(U, kappa, eta, k) if k else 0)
+              for k in range(5))
+    assert rel_err(got, ref) < 1e-13
+    a = np.array([6.4, -20.6, 39.4, -47.6, 36.7, -17.5, 4.7]) + 0.01j
+    got = host(ctx.poly_apply(Ud, kappa, ed, a))
+    assert rel_err(got, S.poly_apply(lambda f: L.wilson(U, kappa, f), a, eta)) < 1e-13
+
+
+def _orthonormal(n, k, seed):
+    r = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(r.standard_normal((n, k)) + 1j * r.standard_normal((n, k)))
+    return Q
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (3, 5, 2, 7)])
+def test_deflate_project_and_xi(dims):
+    ctx = context(dims)
+    U = synth.su3_links(dims, 0.45, 9)
+    kappa = 0.15
+    n = 12 * L.volume(dims)
+    E = _orthonormal(n, 6, 10)
+    lam = np.array([0.11, -0.12, 0.2, -0.25, 0.3, 0.31], dtype=np.complex128)
+    defl = ctx.defl_import(dev(E.T), lam)
+    eta = rng.z4_block(4, 0, 3, dims)
+    d = 1.0 / lam - 0.3j
+    got = host(ctx.deflate_project(defl, dev(eta), d))
+    assert rel_err(got, S.defl_vector(E, d, eta)) < 1e-13
+    Ud = dev(U)
+    got = ctx.xi_inverse(Ud, kappa, defl, 2, 7)      # LQCD_SUB_PERT
+    ref = S.xi_inverse(E, lambda f: S.hop_series(U, kappa, f, 7), dims)
+    assert rel_err(got, ref) < 1e-12
+    a = np.array([3.0, -4.0 + 0.1j, 2.5, -0.7])
+    got = ctx.xi_inverse(Ud, kappa, defl, 4, 4, a)    # LQCD_SUB_POLY
+    ref = S.xi_inverse(E, lambda f: S.poly_apply(lambda g: L.wilson(U, kappa, g), a, f), dims)
+    assert rel_err(got, ref) < 1e-12
+
+
+def test_poly_coeffs_minimiser():
+    dims = (4, 4, 4, 4)
+    ctx = context(dims)
+    U = synth.su3_links(dims, 0.3, 1)
+    kappa, n, seed = 0.15, 6, 17
+    got = ctx.poly_coeffs(dev(U), kappa, seed, n)
+    A = lambda f: L.wilson(U, kappa, f)
+    b = rng.z4_noise(seed, rng.NOISE_POLY, dims)
+    ref = S.poly_coeffs(A, b, n)
+    # the same minimiser: residual norms agree, and P(M) b agrees
+    r_got = np.linalg.norm(b - A(S.poly_apply(A, got, b)))
+    r_ref = np.linalg.norm(b - A(S.poly_apply(A, ref, b)))
+    assert abs(r_got - r_ref) <= 1e-10 * r_ref
+    assert rel_err(S.poly_apply(A, got, b), S.poly_apply(A, ref, b)) < 1e-9
+    assert rel_err(got, ref) < 1e-7
+
+
+@pytest.mark.parametrize("dims,K", [((4, 4, 4, 4), 5), ((2, 2, 2, 8), 3), ((3, 2, 2, 6), 4)])
+def test_hop_traces_small(dims, K):
+    ctx = context(dims)
+    U = synth.su3_links(dims, 0.5, 11)
+    kappa = 0.13
+    got = ctx.hop_traces(dev(U), kappa, K)
+    ref = O.per_t(S.hop_traces(U, kappa, K, dims))          # [k, op, t]
+    assert rel_err(got, ref) < 1e-13
+
+
+def test_hop_traces_full_size_properties():
+    """8^3 x 16 with K = 7 (the PS order of the paper): free field against the momentum-space
+    closed form, and for an interacting field the vanishing orders (Sec. 5.1) and t_0 = 12 V."""
+    from tests.test_oracle_traces import free_hop_traces
+    dims, K, kappa = (8, 8, 8, 16), 7, 0.157
+    ctx = context(dims)
+    got = ctx.hop_traces(dev(synth.unit_links(dims)), kappa, K).sum(axis=-1)
+    ref = free_hop_traces(dims, kappa, K)
+    assert rel_err(got, ref) < 1e-12
+    t = ctx.hop_traces(dev(synth.su3_links(dims, 0.437, 2)), kappa, K).sum(axis=-1)
+    scale = abs(t[0, 0])
+    assert t[0, 0] == 12 * L.volume(dims)
+    for k in (1, 2, 3, 5):
+        assert np.abs(t[k, 0:5]).max() < 1e-12 * scale
+    for k in (0, 2, 4, 6):
+        assert np.abs(t[k, 5:9]).max() < 1e-12 * scale
+    assert abs(t[4, 0]) > 1.0 and abs(t[6, 0]) > 1.0

@@ -1,0 +1,100 @@
+"""GPU parity of GMRES-DR, MINRES-DR and GMRES-Proj with the oracle (Sec. 5.3, 7, 8).
+
+The GPU and the oracle run the same algorithm in different rounding orders, so iterates agree to
+rounding after a fixed number of cycles, and converged solutions agree within cond(M) * tol.
+Ritz values are checked against the dense spectrum; eigenvectors only where they are converged."""
+import numpy as np
+import pytest
+
+from oracle import krylov as Kr, lattice as L, rng
+from paper_1903_06986_gb300 import synth
+from tests.gpu_util import context, dev, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (4, 4, 4, 4)
+KAPPA = 0.150
+
+
+@pytest.fixture(scope="module")
+def setup():
+    U = synth.su3_links(DIMS, 0.3, 1)
+    A = lambda v: L.flat(L.wilson(U, KAPPA, L.unflat(v, DIMS)))
+    Ap = lambda v: L.flat(L.wilson_g5(U, KAPPA, L.unflat(v, DIMS)))
+    b = L.flat(rng.z4_noise(1, rng.NOISE_SPECIAL, DIMS))
+    M = L.dense(lambda f: L.wilson(U, KAPPA, f), DIMS)
+    return dict(U=U, A=A, Ap=Ap, b=b, M=M, cond=np.linalg.cond(M), ctx=context(DIMS), Ud=dev(U))
+
+
+@pytest.mark.parametrize("cycles", [1, 3])
+def test_gmresdr_iterates_match_oracle(setup, cycles):
+    s = setup
+    x_ref, _, _ = Kr.gmres_dr(s["A"], s["b"], 20, 5, 1e-30, cycles)
+    x, info, _ = s["ctx"].gmresdr_solve(s["Ud"], KAPPA, dev(L.unflat(s["b"], DIMS)), 20, 5, 1e-30, cycles)
+    assert info["cycles"] == cycles
+    assert rel_err(L.flat(host(x)), x_ref) < 1e-10
+
+
+def test_gmresdr_converges_and_deflates(setup):
+    s = setup
+    tol = 1e-12
+    x, info, defl = s["ctx"].gmresdr_solve(s["Ud"], KAPPA, dev(L.unflat(s["b"], DIMS)), 20, 5, tol, 500,
+                                           want_defl=True)
+    assert info["converged"] and info["true_resid"] <= tol
+    xe = np.linalg.solve(s["M"], s["b"])
+    assert np.linalg.norm(L.flat(host(x)) - xe) <= 10 * s["cond"] * tol * np.linalg.norm(xe)
+    # the exported deflation space satisfies M V_k = V_{k+1} Hbar_k with orthonormal V_{k+1}
+    ex = defl.export()
+    V = host(ex["V"]).T
+    H = ex["Hbar"]
+    assert np.abs(V.conj().T @ V - np.eye(6)).max() < 1e-12
+    assert np.abs(s["M"] @ V[:, :5] - V @ H).max() < 1e-10
+
+
+def test_minresdr_ritz_values_and_solution(setup):
+    s = setup
+    tol = 1e-13
+    y, info, defl = s["ctx"].minresdr_solve(s["Ud"], KAPPA, dev(L.unflat(s["b"], DIMS)), 40, 12, tol, 500,
+                                            want_defl=True)
+    assert info["converged"]
+    x = L.flat(L.g5(host(y)))
+    assert np.linalg.norm(s["M"] @ x - s["b"]) <= 1.01 * tol * np.linalg.norm(s["b"]) * 10
+    ex = defl.export()
+    lam, E, res = ex["lam"], host(ex["E"]).T, ex["eig_resid"]
+    assert np.abs(lam.imag).max() == 0.0
+    Mp = L.dense(lambda f: L.wilson_g5(s["U"], KAPPA, f), DIMS)
+    w = np.linalg.eigvalsh(Mp)
+    assert np.abs(E.conj().T @ E - np.eye(12)).max() < 1e-12
+    for q in range(12):
+        r = Mp @ E[:, q] - lam[q] * E[:, q]
+        assert abs(np.linalg.norm(r) - res[q]) < 1e-9 + 1e-6 * res[q]
+        # Hermitian: a Ritz value lies within its residual norm of an eigenvalue
+        assert np.abs(w - lam[q].real).min() <= res[q] * (1 + 1e-8) + 1e-12
+    # iterates after 2 cycles match the oracle's Hermitian form
+    y_ref, _, _ = Kr.gmres_dr(s["Ap"], s["b"], 40, 12, 1e-30, 2, hermitian=True)
+    y2, _, _ = s["ctx"].minresdr_solve(s["Ud"], KAPPA, dev(L.unflat(s["b"], DIMS)), 40, 12, 1e-30, 2)
+    assert rel_err(L.flat(host(y2)), y_ref) < 1e-10
+
+
+def test_gmres_proj_multi_rhs(setup):
+    s = setup
+    ctx = s["ctx"]
+    _, _, defl = ctx.gmresdr_solve(s["Ud"], KAPPA, dev(L.unflat(s["b"], DIMS)), 20, 5, 1e-13, 500, want_defl=True)
+    ex = defl.export()
+    dref = dict(V=host(ex["V"]).T, Hbar=ex["Hbar"])
+    etas = rng.z4_block(1, 0, 3, DIMS)
+    # one cycle: identical algorithm on identical deflation data
+    x1, _ = ctx.proj_solve(s["Ud"], KAPPA, defl, dev(etas), 15, 1e-30, 1)
+    for r in range(3):
+        xr, _ = Kr.gmres_proj(s["A"], L.flat(etas[r]), dref, 15, 1e-30, 1)
+        assert rel_err(L.flat(host(x1)[r]), xr) < 1e-10
+    # to convergence; every right-hand side meets the tolerance with its true residual
+    tol = 1e-12
+    x, info = ctx.proj_solve(s["Ud"], KAPPA, defl, dev(etas), 15, tol, 500)
+    assert info["converged"] and info["true_resid"] <= tol
+    for r in range(3):
+        xe = np.linalg.solve(s["M"], L.flat(etas[r]))
+        assert np.linalg.norm(L.flat(host(x)[r]) - xe) <= 10 * s["cond"] * tol * np.linalg.norm(xe)
+    # solving one right-hand side alone gives the same answer
+    xa, _ = ctx.proj_solve(s["Ud"], KAPPA, defl, dev(etas[1:2]), 15, tol, 500)
+    assert rel_err(host(xa)[0], host(x)[1]) < 10 * s["cond"] * tol
