@@ -161,7 +161,10 @@ lqcd_status lqcd_minresdr_solve(lqcd_ctx *ctx, const double *links, double kappa
 
 /* Solve A x = b for nrhs right-hand sides with GMRES-Proj over defl (made by one of the two
  * solvers above on the same A): each cycle is a minimum-residual projection over V_{k+1} and
- * Hbar_k followed by GMRES(opts->m).  opts->k is ignored.  b, x: device (nrhs * 12 V). */
+ * Hbar_k followed by GMRES(opts->m).  opts->k is ignored.  b, x: device (nrhs * 12 V).
+ * opts->prec = LQCD_PREC_F32 selects mixed precision: an FP64 defect-correction loop around the
+ * same GMRES-Proj run with FP32 storage and arithmetic (inner relative residual 5e-6), stopping
+ * on the FP64 true residual ||b - A x|| <= tol ||b||; opts->max_cycles bounds the inner cycles. */
 lqcd_status lqcd_proj_solve(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl,
                             const double *b, double *x, int nrhs, const lqcd_krylov_opts *opts,
                             lqcd_solve_info *info);
@@ -241,7 +244,8 @@ typedef struct {
   double tol_special; /* super-convergence tolerance of the special right-hand side         */
   int max_cycles;
   int modes;          /* LQCD_SUB_* bit mask                                                 */
-  int prec;           /* LQCD_PREC_F64 (plain)                                               */
+  int prec;           /* LQCD_PREC_F64 (plain) or LQCD_PREC_F32 (mixed-precision noise solves;
+                         special solves, series, projections and contractions stay FP64)   */
 } lqcd_est_opts;
 
 typedef struct {

@@ -1,9 +1,11 @@
-// Batched FP64 complex level-1/level-2 kernels for the Krylov solvers, and the Z(4) noise kernel.
+// Batched complex level-1/level-2 kernels for the Krylov solvers, and the Z(4) noise kernel.
 //
 // A "block" of nrhs vectors of length n is stored vector after vector; a multi-vector (a Krylov
-// basis) stores basis vector i of right-hand side r at V + i * vstride + r * n.  Every reduction
-// is two-stage with a fixed order (per-block partial sums, then one block per result), so results
-// are reproducible run to run.
+// basis) stores basis vector i of right-hand side r at V + i * vstride + r * vrs.  The kernels are
+// templates on the storage type: double2 (the FP64 path) or float2 (the FP32 inner solver of the
+// mixed-precision path, which accumulates each thread's terms in FP32 and reduces across threads
+// in FP64).  Every reduction is two-stage with a fixed order (per-block partial sums, then one
+// block per result), so results are reproducible run to run.
 #include <algorithm>
 
 #include "common.cuh"
@@ -12,6 +14,28 @@ namespace {
 
 constexpr int BT = 256;      // threads per block
 constexpr int GROUP = 8;     // basis vectors reduced together in multidot
+
+template <typename S> __device__ __forceinline__ S cz();
+template <> __device__ __forceinline__ double2 cz<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 cz<float2>() { return make_float2(0.f, 0.f); }
+template <typename S> __device__ __forceinline__ S from_d2(double2 v);
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
+// acc += a * b and acc += conj(a) * b for double2 / float2
+template <typename S> __device__ __forceinline__ void gfma(S &acc, S a, S b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename S> __device__ __forceinline__ void gfma_conj(S &acc, S a, S b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
 
 __device__ __forceinline__ double2 warp_sum2(double2 v) {
 #pragma unroll
@@ -23,31 +47,32 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
 }
 
 // partial[(i * nrhs + r) * nb + blockIdx.x] = sum over this block's chunk of conj(V_i^r) w^r
-__global__ void __launch_bounds__(BT) multidot_partial(const double2 *__restrict__ V, long long vstride,
-                                                       long long vrs, int nvec, const double2 *__restrict__ w,
+template <typename S>
+__global__ void __launch_bounds__(BT) multidot_partial(const S *__restrict__ V, long long vstride,
+                                                       long long vrs, int nvec, const S *__restrict__ w,
                                                        long long n, int nrhs, double2 *__restrict__ partial) {
   const int r = blockIdx.y;
   const int nb = gridDim.x;
   const long long chunk = (n + nb - 1) / nb;
   const long long e0 = blockIdx.x * chunk;
   const long long e1 = min(n, e0 + chunk);
-  const double2 *wr = w + r * n;
+  const S *wr = w + r * n;
   __shared__ double2 red[BT / 32][GROUP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i0 = 0; i0 < nvec; i0 += GROUP) {
     const int g = min(GROUP, nvec - i0);
-    double2 acc[GROUP];
+    S acc[GROUP];
 #pragma unroll
-    for (int j = 0; j < GROUP; ++j) acc[j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < GROUP; ++j) acc[j] = cz<S>();
     for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
-      const double2 wv = wr[e];
+      const S wv = wr[e];
 #pragma unroll
       for (int j = 0; j < GROUP; ++j)
-        if (j < g) cfma_conj(acc[j], V[(long long)(i0 + j) * vstride + r * vrs + e], wv);
+        if (j < g) gfma_conj(acc[j], V[(long long)(i0 + j) * vstride + r * vrs + e], wv);
     }
 #pragma unroll
     for (int j = 0; j < GROUP; ++j) {
-      double2 v = warp_sum2(acc[j]);
+      double2 v = warp_sum2(to_d2(acc[j]));
       if (lane == 0) red[warp][j] = v;
     }
     __syncthreads();
@@ -73,19 +98,21 @@ __global__ void __launch_bounds__(128) reduce_partials(const double2 *__restrict
   if (threadIdx.x == 0) out[idx] = cadd(cadd(red[0], red[1]), cadd(red[2], red[3]));
 }
 
-__global__ void __launch_bounds__(BT) norm2_partial(const double2 *__restrict__ x, long long n, double *__restrict__ partial) {
+template <typename S>
+__global__ void __launch_bounds__(BT) norm2_partial(const S *__restrict__ x, long long n, double *__restrict__ partial) {
   const int r = blockIdx.y;
   const int nb = gridDim.x;
   const long long chunk = (n + nb - 1) / nb;
   const long long e0 = blockIdx.x * chunk;
   const long long e1 = min(n, e0 + chunk);
-  const double2 *xr = x + r * n;
-  double acc = 0.0;
+  const S *xr = x + r * n;
+  decltype(S().x) a = 0;
   for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
-    double2 v = xr[e];
-    acc = fma(v.x, v.x, acc);
-    acc = fma(v.y, v.y, acc);
+    const S v = xr[e];
+    a = fma(v.x, v.x, a);
+    a = fma(v.y, v.y, a);
   }
+  double acc = (double)a;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   __shared__ double red[BT / 32];
@@ -111,40 +138,41 @@ __global__ void __launch_bounds__(128) norm2_final(const double *__restrict__ pa
 }
 
 // w^r += sign * sum_i V_i^r h[i * nrhs + r]
-__global__ void __launch_bounds__(BT) multiaxpy_kernel(const double2 *__restrict__ V, long long vstride,
+template <typename S>
+__global__ void __launch_bounds__(BT) multiaxpy_kernel(const S *__restrict__ V, long long vstride,
                                                        long long vrs, int nvec, const double2 *__restrict__ h,
-                                                       double sign, double2 *__restrict__ w, long long n, int nrhs) {
+                                                       double sign, S *__restrict__ w, long long n, int nrhs) {
   const long long e = (long long)blockIdx.x * BT + threadIdx.x;
   const int r = blockIdx.y;
   if (e >= n) return;
-  double2 acc = w[r * n + e];
+  S acc = w[r * n + e];
   for (int i = 0; i < nvec; ++i) {
-    double2 c = h[(long long)i * nrhs + r];
-    c = cscale(c, sign);
-    cfma(acc, V[(long long)i * vstride + r * vrs + e], c);
+    const S c = from_d2<S>(cscale(h[(long long)i * nrhs + r], sign));
+    gfma(acc, V[(long long)i * vstride + r * vrs + e], c);
   }
   w[r * n + e] = acc;
 }
 
 constexpr int CT = 8;  // output columns per pass in combine
 // out_c^r = sum_i V_i^r C[(i * ncol + c) * nrhs + r]
-__global__ void __launch_bounds__(BT) combine_kernel(const double2 *__restrict__ V, long long vstride,
+template <typename S>
+__global__ void __launch_bounds__(BT) combine_kernel(const S *__restrict__ V, long long vstride,
                                                      long long vrs, int nvec, const double2 *__restrict__ C,
-                                                     int ncol, double2 *__restrict__ out, long long ostride,
+                                                     int ncol, S *__restrict__ out, long long ostride,
                                                      long long n, int nrhs) {
   const long long e = (long long)blockIdx.x * BT + threadIdx.x;
   const int r = blockIdx.y;
   if (e >= n) return;
   for (int c0 = 0; c0 < ncol; c0 += CT) {
     const int g = min(CT, ncol - c0);
-    double2 acc[CT];
+    S acc[CT];
 #pragma unroll
-    for (int j = 0; j < CT; ++j) acc[j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < CT; ++j) acc[j] = cz<S>();
     for (int i = 0; i < nvec; ++i) {
-      const double2 v = V[(long long)i * vstride + r * vrs + e];
+      const S v = V[(long long)i * vstride + r * vrs + e];
 #pragma unroll
       for (int j = 0; j < CT; ++j)
-        if (j < g) cfma(acc[j], v, C[((long long)i * ncol + c0 + j) * nrhs + r]);
+        if (j < g) gfma(acc[j], v, from_d2<S>(C[((long long)i * ncol + c0 + j) * nrhs + r]));
     }
 #pragma unroll
     for (int j = 0; j < CT; ++j)
@@ -152,23 +180,59 @@ __global__ void __launch_bounds__(BT) combine_kernel(const double2 *__restrict__
   }
 }
 
-__global__ void invscale_kernel(double2 *__restrict__ x, const double *__restrict__ s, long long n) {
+template <typename S>
+__global__ void invscale_kernel(S *__restrict__ x, const double *__restrict__ s, long long n) {
   const long long e = (long long)blockIdx.x * BT + threadIdx.x;
   const int r = blockIdx.y;
   if (e >= n) return;
   const double d = s[r];
   const double f = d > 0.0 ? 1.0 / d : 0.0;
-  double2 v = x[r * n + e];
-  x[r * n + e] = make_double2(v.x * f, v.y * f);
+  S v = x[r * n + e];
+  v.x *= f;
+  v.y *= f;
+  x[r * n + e] = v;
 }
 
-__global__ void copy_kernel(const double2 *__restrict__ x, double2 *__restrict__ y, long long n) {
+template <typename S>
+__global__ void copy_kernel(const S *__restrict__ x, S *__restrict__ y, long long n) {
   for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT) y[e] = x[e];
 }
 
-__global__ void zero_kernel(double2 *__restrict__ y, long long n) {
+template <typename S>
+__global__ void zero_kernel(S *__restrict__ y, long long n) {
+  for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT) y[e] = cz<S>();
+}
+
+// y^r = float(x^r / s[r]): FP64 residual block -> normalised FP32 right-hand side
+__global__ void demote_kernel(const double2 *__restrict__ x, const double *__restrict__ s, float2 *__restrict__ y,
+                              long long n) {
+  const long long e = (long long)blockIdx.x * BT + threadIdx.x;
+  const int r = blockIdx.y;
+  if (e >= n) return;
+  const double d = s[r];
+  const double f = d > 0.0 ? 1.0 / d : 0.0;
+  const double2 v = x[r * n + e];
+  y[r * n + e] = make_float2((float)(v.x * f), (float)(v.y * f));
+}
+
+// x^r += s[r] * double(e^r): FP32 correction folded into the FP64 solution
+__global__ void promote_acc_kernel(const float2 *__restrict__ c, const double *__restrict__ s, double2 *__restrict__ x,
+                                   long long n) {
+  const long long e = (long long)blockIdx.x * BT + threadIdx.x;
+  const int r = blockIdx.y;
+  if (e >= n) return;
+  const double d = s[r];
+  const float2 v = c[r * n + e];
+  double2 o = x[r * n + e];
+  o.x = fma(d, (double)v.x, o.x);
+  o.y = fma(d, (double)v.y, o.y);
+  x[r * n + e] = o;
+}
+
+// elementwise conversion double2 -> float2 (gauge links of the FP32 operator)
+__global__ void to_f32_kernel(const double2 *__restrict__ x, float2 *__restrict__ y, long long n) {
   for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT)
-    y[e] = make_double2(0.0, 0.0);
+    y[e] = make_float2((float)x[e].x, (float)x[e].y);
 }
 
 __global__ void axpy_kernel(double2 a, const double2 *__restrict__ x, double2 *__restrict__ y, long long n) {
@@ -254,15 +318,17 @@ int partial_blocks(lqcd_ctx *ctx, long long n, int nrhs) {
 
 }  // namespace
 
-lqcd_status blas_copy(lqcd_ctx *ctx, const double2 *x, double2 *y, long long n) {
+template <typename S>
+lqcd_status blas_copy(lqcd_ctx *ctx, const S *x, S *y, long long n) {
   kbegin(ctx);
-  copy_kernel<<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(x, y, n);
+  copy_kernel<S><<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(x, y, n);
   return launch_check(ctx, "copy_kernel", K_BLAS1, (double)n);
 }
 
-lqcd_status blas_zero(lqcd_ctx *ctx, double2 *y, long long n) {
+template <typename S>
+lqcd_status blas_zero(lqcd_ctx *ctx, S *y, long long n) {
   kbegin(ctx);
-  zero_kernel<<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(y, n);
+  zero_kernel<S><<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(y, n);
   return launch_check(ctx, "zero_kernel", K_BLAS1, (double)n);
 }
 
@@ -285,53 +351,90 @@ lqcd_status blas_g5(lqcd_ctx *ctx, const double2 *x, double2 *y, int nrhs) {
   return launch_check(ctx, "g5_kernel", K_BLAS1, (double)sites * 12);
 }
 
-lqcd_status blas_norms(lqcd_ctx *ctx, const double2 *x, long long n, int nrhs, double *norms) {
+template <typename S>
+lqcd_status blas_norms(lqcd_ctx *ctx, const S *x, long long n, int nrhs, double *norms) {
   const int nb = partial_blocks(ctx, n, nrhs);
   void *p = nullptr;
   LQCD_TRY(ws_get(ctx, WS_SCAL, sizeof(double) * (size_t)nb * nrhs, &p));
   kbegin(ctx);
-  norm2_partial<<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(x, n, (double *)p);
+  norm2_partial<S><<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(x, n, (double *)p);
   LQCD_TRY(launch_check(ctx, "norm2_partial", K_NORM, (double)n * nrhs));
   kbegin(ctx);
   norm2_final<<<nrhs, 128, 0, ctx->stream>>>((const double *)p, nb, norms);
   return launch_check(ctx, "norm2_final", K_NORM, 0.0);
 }
 
-lqcd_status blas_multidot(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
-                          const double2 *w, long long n, int nrhs, double2 *h) {
+template <typename S>
+lqcd_status blas_multidot(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const S *w,
+                          long long n, int nrhs, double2 *h) {
   if (nvec <= 0) return LQCD_OK;
   const int nb = partial_blocks(ctx, n, nrhs);
   void *p = nullptr;
   LQCD_TRY(ws_get(ctx, WS_PARTIAL, sizeof(double2) * (size_t)nb * nrhs * nvec, &p));
   kbegin(ctx);
-  multidot_partial<<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, (double2 *)p);
+  multidot_partial<S><<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, (double2 *)p);
   LQCD_TRY(launch_check(ctx, "multidot_partial", K_DOT, (double)n * nrhs * nvec));
   kbegin(ctx);
   reduce_partials<<<nvec * nrhs, 128, 0, ctx->stream>>>((const double2 *)p, nb, h);
   return launch_check(ctx, "reduce_partials", K_DOT, 0.0);
 }
 
-lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
-                           const double2 *h, double sign, double2 *w, long long n, int nrhs) {
+template <typename S>
+lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const double2 *h,
+                           double sign, S *w, long long n, int nrhs) {
   if (nvec <= 0) return LQCD_OK;
   kbegin(ctx);
-  multiaxpy_kernel<<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, h, sign, w, n, nrhs);
+  multiaxpy_kernel<S><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, h, sign, w, n, nrhs);
   return launch_check(ctx, "multiaxpy_kernel", K_AXPY, (double)n * nrhs * nvec);
 }
 
-lqcd_status blas_combine(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
-                         const double2 *C, int ncol, double2 *out, long long ostride, long long n, int nrhs) {
+template <typename S>
+lqcd_status blas_combine(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const double2 *C,
+                         int ncol, S *out, long long ostride, long long n, int nrhs) {
   if (ncol <= 0) return LQCD_OK;
   kbegin(ctx);
-  combine_kernel<<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, C, ncol, out, ostride, n, nrhs);
+  combine_kernel<S><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, C, ncol, out, ostride, n, nrhs);
   return launch_check(ctx, "combine_kernel", K_COMBINE, (double)n * nrhs * nvec * ncol);
 }
 
-lqcd_status blas_invscale(lqcd_ctx *ctx, double2 *x, const double *s, long long n, int nrhs) {
+template <typename S>
+lqcd_status blas_invscale(lqcd_ctx *ctx, S *x, const double *s, long long n, int nrhs) {
   kbegin(ctx);
-  invscale_kernel<<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(x, s, n);
+  invscale_kernel<S><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(x, s, n);
   return launch_check(ctx, "invscale_kernel", K_BLAS1, (double)n * nrhs);
 }
+
+lqcd_status blas_demote(lqcd_ctx *ctx, const double2 *x, const double *s, float2 *y, long long n, int nrhs) {
+  kbegin(ctx);
+  demote_kernel<<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(x, s, y, n);
+  return launch_check(ctx, "demote_kernel", K_BLAS1, (double)n * nrhs);
+}
+
+lqcd_status blas_promote_acc(lqcd_ctx *ctx, const float2 *c, const double *s, double2 *x, long long n, int nrhs) {
+  kbegin(ctx);
+  promote_acc_kernel<<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(c, s, x, n);
+  return launch_check(ctx, "promote_acc_kernel", K_BLAS1, (double)n * nrhs);
+}
+
+lqcd_status blas_to_f32(lqcd_ctx *ctx, const double2 *x, float2 *y, long long n) {
+  kbegin(ctx);
+  to_f32_kernel<<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(x, y, n);
+  return launch_check(ctx, "to_f32_kernel", K_BLAS1, (double)n);
+}
+
+#define LQCD_BLAS_INSTANTIATE(S)                                                                               \
+  template lqcd_status blas_copy<S>(lqcd_ctx *, const S *, S *, long long);                                     \
+  template lqcd_status blas_zero<S>(lqcd_ctx *, S *, long long);                                                \
+  template lqcd_status blas_norms<S>(lqcd_ctx *, const S *, long long, int, double *);                          \
+  template lqcd_status blas_multidot<S>(lqcd_ctx *, const S *, long long, long long, int, const S *, long long,  \
+                                        int, double2 *);                                                        \
+  template lqcd_status blas_multiaxpy<S>(lqcd_ctx *, const S *, long long, long long, int, const double2 *,     \
+                                         double, S *, long long, int);                                          \
+  template lqcd_status blas_combine<S>(lqcd_ctx *, const S *, long long, long long, int, const double2 *, int,  \
+                                       S *, long long, long long, int);                                         \
+  template lqcd_status blas_invscale<S>(lqcd_ctx *, S *, const double *, long long, int);
+LQCD_BLAS_INSTANTIATE(double2)
+LQCD_BLAS_INSTANTIATE(float2)
 
 lqcd_status noise_launch(lqcd_ctx *ctx, uint64_t seed, uint32_t first, int nrhs, double2 *out) {
   kbegin(ctx);

@@ -81,7 +81,8 @@ lqcd_status launch_check(lqcd_ctx *ctx, const char *what, int cls, double units)
 // growable workspace slot (device memory owned by the context)
 enum WsSlot {
   WS_PARTIAL = 0, WS_SCAL, WS_TMP0, WS_TMP1, WS_TMP2, WS_TMP3, WS_BASIS, WS_HESS, WS_COEF,
-  WS_BASIS2, WS_TMP4, WS_TMP5, WS_EST0, WS_EST1, WS_EST2, WS_PROBE, WS_NSLOTS
+  WS_BASIS2, WS_TMP4, WS_TMP5, WS_EST0, WS_EST1, WS_EST2, WS_PROBE,
+  WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_NSLOTS
 };
 lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr);
 lqcd_status host_stage(lqcd_ctx *ctx, size_t bytes, double **ptr);
@@ -139,30 +140,40 @@ static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) 
 // Wilson operator on nrhs fields (see lqcd_wilson_apply); in and out must not overlap.
 lqcd_status wilson_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in,
                           double2 *out, int nrhs, int prec, int flags);
-// y[r] = a * x[r] + y[r] style batched level-1 kernels (blas.cu)
-lqcd_status blas_copy(lqcd_ctx *ctx, const double2 *x, double2 *y, long long n);
-lqcd_status blas_zero(lqcd_ctx *ctx, double2 *y, long long n);
+// FP32 storage and arithmetic (links converted to FP32 by the caller)
+lqcd_status wilson_launch_f32(lqcd_ctx *ctx, const float2 *U, double kappa, const float2 *in, float2 *out,
+                              int nrhs, int flags);
+// Batched level-1/level-2 kernels (blas.cu).  Templates are instantiated for S = double2 (FP64
+// path) and S = float2 (FP32 inner solver); coefficients and reductions are always FP64.
+template <typename S> lqcd_status blas_copy(lqcd_ctx *ctx, const S *x, S *y, long long n);
+template <typename S> lqcd_status blas_zero(lqcd_ctx *ctx, S *y, long long n);
 lqcd_status blas_g5(lqcd_ctx *ctx, const double2 *x, double2 *y, int nrhs);
 // t = b - t
 lqcd_status blas_bminus(lqcd_ctx *ctx, double2 *t, const double2 *b, long long n);
 // norms[r] = ||x_r||_2 for nrhs vectors of length n (device output)
-lqcd_status blas_norms(lqcd_ctx *ctx, const double2 *x, long long n, int nrhs, double *norms);
+template <typename S> lqcd_status blas_norms(lqcd_ctx *ctx, const S *x, long long n, int nrhs, double *norms);
 // Basis vector i of right-hand side r is V_i^r = V + i*vstride + r*vrs (vrs = 0: one basis shared
 // by every right-hand side); w^r = w + r*n.
 // h[i*nrhs + r] = <V_i^r, w^r> for i < nvec
-lqcd_status blas_multidot(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
-                          const double2 *w, long long n, int nrhs, double2 *h);
+template <typename S>
+lqcd_status blas_multidot(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const S *w,
+                          long long n, int nrhs, double2 *h);
 // w^r += sign * sum_i V_i^r h[i*nrhs + r]
-lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
-                           const double2 *h, double sign, double2 *w, long long n, int nrhs);
+template <typename S>
+lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const double2 *h,
+                           double sign, S *w, long long n, int nrhs);
 // out_c^r = out + c*ostride + r*n = sum_i V_i^r C[(i*ncol + c)*nrhs + r] for c < ncol (no aliasing)
-lqcd_status blas_combine(lqcd_ctx *ctx, const double2 *V, long long vstride, long long vrs, int nvec,
-                         const double2 *C, int ncol, double2 *out, long long ostride, long long n,
-                         int nrhs);
+template <typename S>
+lqcd_status blas_combine(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const double2 *C,
+                         int ncol, S *out, long long ostride, long long n, int nrhs);
 // x^r *= 1 / s[r] (s device); zero vector if s[r] == 0
-lqcd_status blas_invscale(lqcd_ctx *ctx, double2 *x, const double *s, long long n, int nrhs);
+template <typename S> lqcd_status blas_invscale(lqcd_ctx *ctx, S *x, const double *s, long long n, int nrhs);
 // y += a x with a host scalar a
 lqcd_status blas_axpy(lqcd_ctx *ctx, double2 a, const double2 *x, double2 *y, long long n);
+// y^r = float(x^r / s[r])  and  x^r += s[r] * double(c^r)  (mixed-precision defect correction)
+lqcd_status blas_demote(lqcd_ctx *ctx, const double2 *x, const double *s, float2 *y, long long n, int nrhs);
+lqcd_status blas_promote_acc(lqcd_ctx *ctx, const float2 *c, const double *s, double2 *x, long long n, int nrhs);
+lqcd_status blas_to_f32(lqcd_ctx *ctx, const double2 *x, float2 *y, long long n);
 // contraction densities summed per timeslice (loops.cu); out device [nrhs][9][Lt]
 lqcd_status contract_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *eta,
                             const double2 *w, int nrhs, double2 *out_dev);

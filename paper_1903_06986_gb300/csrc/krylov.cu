@@ -19,6 +19,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 #include "dense.h"
@@ -28,15 +29,30 @@ using dense::Mat;
 
 namespace {
 
-struct Op {
+// The operator of a solve: M or M gamma_5 (flags LQCD_APPLY_M / LQCD_APPLY_G5R) on FP64 storage
+// (arithmetic prec) or on FP32 storage with FP32 arithmetic (the inner solver of mixed precision).
+template <typename S> struct OpT;
+template <> struct OpT<double2> {
   const double2 *U;
   double kappa;
-  int flags;  // LQCD_APPLY_M or LQCD_APPLY_G5R
+  int flags;
   int prec;
+  lqcd_status apply(lqcd_ctx *ctx, const double2 *in, double2 *out, int nrhs) const {
+    return wilson_launch(ctx, U, kappa, in, out, nrhs, prec, flags);
+  }
 };
+template <> struct OpT<float2> {
+  const float2 *U;
+  double kappa;
+  int flags;
+  lqcd_status apply(lqcd_ctx *ctx, const float2 *in, float2 *out, int nrhs) const {
+    return wilson_launch_f32(ctx, U, kappa, in, out, nrhs, flags);
+  }
+};
+using Op = OpT<double2>;
 
 lqcd_status apply_op(lqcd_ctx *ctx, const Op &op, const double2 *in, double2 *out, int nrhs) {
-  return wilson_launch(ctx, op.U, op.kappa, in, out, nrhs, op.prec, op.flags);
+  return op.apply(ctx, in, out, nrhs);
 }
 
 lqcd_status upload(lqcd_ctx *ctx, const std::vector<cd> &h, void *dev) {
@@ -77,22 +93,24 @@ struct Rhs {
 // Enqueue Arnoldi steps j0..m-1 for every right-hand side (basis Vb with vector stride vs =
 // nrhs * N) and fill columns j0..m-1 of each Rhs::H.  Inactive right-hand sides are processed
 // too (their results are ignored).
-struct Arnoldi {
+template <typename S> struct ArnoldiT {
   lqcd_ctx *ctx;
-  Op op;
+  OpT<S> op;
   int nrhs, m;
   long long N;
-  double2 *Vb;
+  S *Vb;
   double2 *hd1, *hd2;  // [j][i][r] device, (m) x (m+1) x nrhs
   double *nrm;         // [j][r]
 };
+using Arnoldi = ArnoldiT<double2>;
 
-lqcd_status arnoldi_run(Arnoldi &a, int j0, std::vector<Rhs> &R, long long &matvecs) {
+template <typename S>
+lqcd_status arnoldi_run(ArnoldiT<S> &a, int j0, std::vector<Rhs> &R, long long &matvecs) {
   lqcd_ctx *ctx = a.ctx;
   const long long N = a.N, vs = (long long)a.nrhs * N;
   for (int j = j0; j < a.m; ++j) {
-    double2 *vj = a.Vb + j * vs, *w = a.Vb + (j + 1) * vs;
-    LQCD_TRY(apply_op(ctx, a.op, vj, w, a.nrhs));
+    S *vj = a.Vb + j * vs, *w = a.Vb + (j + 1) * vs;
+    LQCD_TRY(a.op.apply(ctx, vj, w, a.nrhs));
     double2 *h1 = a.hd1 + (long long)j * (a.m + 1) * a.nrhs;
     double2 *h2 = a.hd2 + (long long)j * (a.m + 1) * a.nrhs;
     LQCD_TRY(blas_multidot(ctx, a.Vb, vs, N, j + 1, w, N, a.nrhs, h1));
@@ -175,18 +193,21 @@ Mat restart_basis(const Mat &G, const std::vector<cd> &s) {
   return dense::orthonormalize(A);
 }
 
-struct Workspace {
-  double2 *Vb = nullptr, *Vt = nullptr, *hd1 = nullptr, *hd2 = nullptr, *coef = nullptr, *tmp = nullptr;
+template <typename S> struct WorkspaceT {
+  S *Vb = nullptr, *Vt = nullptr, *tmp = nullptr;
+  double2 *hd1 = nullptr, *hd2 = nullptr, *coef = nullptr;
   double *nrm = nullptr;
 };
+using Workspace = WorkspaceT<double2>;
 
-lqcd_status get_workspace(lqcd_ctx *ctx, int m, int k, int nrhs, Workspace &w) {
+template <typename S>
+lqcd_status get_workspace(lqcd_ctx *ctx, int m, int k, int nrhs, WorkspaceT<S> &w) {
   const long long vs = (long long)nrhs * ctx->N;
   void *p;
-  LQCD_TRY(ws_get(ctx, WS_BASIS, sizeof(double2) * (size_t)(m + 1) * vs, &p));
-  w.Vb = (double2 *)p;
-  LQCD_TRY(ws_get(ctx, WS_BASIS2, sizeof(double2) * (size_t)(std::max(k, 1) + 1) * vs, &p));
-  w.Vt = (double2 *)p;
+  LQCD_TRY(ws_get(ctx, WS_BASIS, sizeof(S) * (size_t)(m + 1) * vs, &p));
+  w.Vb = (S *)p;
+  LQCD_TRY(ws_get(ctx, WS_BASIS2, sizeof(S) * (size_t)(std::max(k, 1) + 1) * vs, &p));
+  w.Vt = (S *)p;
   const size_t hc = (size_t)std::max(m, 1) * (m + 1) * nrhs;
   LQCD_TRY(ws_get(ctx, WS_HESS, sizeof(double2) * 2 * hc + sizeof(double) * (size_t)std::max(m, 1) * nrhs + 64, &p));
   w.hd1 = (double2 *)p;
@@ -194,8 +215,8 @@ lqcd_status get_workspace(lqcd_ctx *ctx, int m, int k, int nrhs, Workspace &w) {
   w.nrm = (double *)(w.hd2 + hc);
   LQCD_TRY(ws_get(ctx, WS_COEF, sizeof(double2) * (size_t)(m + 2) * (m + 2) * nrhs, &p));
   w.coef = (double2 *)p;
-  LQCD_TRY(ws_get(ctx, WS_TMP0, sizeof(double2) * (size_t)vs, &p));
-  w.tmp = (double2 *)p;
+  LQCD_TRY(ws_get(ctx, WS_TMP0, sizeof(S) * (size_t)vs, &p));
+  w.tmp = (S *)p;
   return LQCD_OK;
 }
 
@@ -438,24 +459,27 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
 }  // namespace
 
 // ---- GMRES-Proj ----------------------------------------------------------------------------
-lqcd_status proj_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const double2 *b, double2 *x, int nrhs,
-                      const lqcd_krylov_opts *o, lqcd_solve_info *info) {
-  const double t0 = now_s();
-  LQCD_TRY(check_opts(ctx, o, nrhs));
-  if (!defl || !defl->V || !defl->Hbar_dev) return set_err(ctx, LQCD_ERR_INVALID_ARG, "GMRES-Proj needs a solver-made deflation space");
-  const int m = o->m, k = defl->k;
+// One GMRES-Proj run on storage S: cycles of (i) minimum-residual projection over the deflation
+// space (V_{k+1} = Vd on the device, Hbar_k = Hk on the host), (ii) one GMRES(m) cycle, until the
+// recursive residual of every right-hand side is below tol; with check_true (FP64 only) the
+// result is then confirmed with the true residual, continuing from it where the recursion drifted.
+struct ProjResult {
+  int cycles = 0;
+  long long matvecs = 0;
+  double worst = 0.0;     // largest relative residual (true if checked, else recursive)
+  bool converged = false;
+};
+
+template <typename S>
+lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const S *Vd, const Mat &Hk, const S *b, S *x, int nrhs, int m,
+                     double tol, int max_cycles, bool check_true, ProjResult &res) {
+  const int k = Hk.c;
   const long long N = ctx->N, vs = (long long)nrhs * N;
-  Workspace W;
+  WorkspaceT<S> W;
   LQCD_TRY(get_workspace(ctx, std::max(m, k + 1), 0, nrhs, W));
-  double2 *r_dev;
-  LQCD_TRY(ws_get(ctx, WS_TMP1, sizeof(double2) * (size_t)vs, (void **)&r_dev));
+  S *r_dev;
+  LQCD_TRY(ws_get(ctx, WS_TMP1, sizeof(S) * (size_t)vs, (void **)&r_dev));
   std::vector<Rhs> R(nrhs);
-  Mat Hk(k + 1, k);
-  for (int i = 0; i <= k; ++i)
-    for (int j = 0; j < k; ++j) {
-      const double2 v = defl->Hbar[(size_t)i * k + j];
-      Hk(i, j) = cd(v.x, v.y);
-    }
   LQCD_TRY(blas_zero(ctx, x, vs));
   LQCD_TRY(blas_copy(ctx, b, r_dev, vs));
   LQCD_TRY(blas_norms(ctx, b, N, nrhs, W.nrm));
@@ -466,15 +490,15 @@ lqcd_status proj_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const 
     R[r].H = Mat(m + 1, m);
     if (!(bn[r] > 0.0)) R[r].active = false;
   }
-  Arnoldi A{ctx, op, nrhs, m, N, W.Vb, W.hd1, W.hd2, W.nrm};
+  ArnoldiT<S> A{ctx, op, nrhs, m, N, W.Vb, W.hd1, W.hd2, W.nrm};
   long long matvecs = 0;
   int cycles = 0;
   bool all_conv = false;
   double worst = 0.0;
-  for (int cyc = 0; cyc < o->max_cycles; ++cyc) {
+  for (int cyc = 0; cyc < max_cycles; ++cyc) {
     cycles = cyc + 1;
     // (i) projection over the deflation space: d = argmin ||V_{k+1}^H r - Hbar_k d||
-    LQCD_TRY(blas_multidot(ctx, defl->V, N, 0, k + 1, r_dev, N, nrhs, W.coef));
+    LQCD_TRY(blas_multidot(ctx, Vd, N, 0, k + 1, r_dev, N, nrhs, W.coef));
     std::vector<double2> cp;
     LQCD_TRY(download(ctx, W.coef, cp, (size_t)(k + 1) * nrhs));
     std::vector<cd> dk((size_t)k * nrhs, cd(0.0, 0.0)), zk((size_t)(k + 1) * nrhs, cd(0.0, 0.0));
@@ -491,9 +515,9 @@ lqcd_status proj_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const 
       }
     }
     LQCD_TRY(upload(ctx, dk, W.coef));
-    LQCD_TRY(blas_multiaxpy(ctx, defl->V, N, 0, k, W.coef, 1.0, x, N, nrhs));
+    LQCD_TRY(blas_multiaxpy(ctx, Vd, N, 0, k, W.coef, 1.0, x, N, nrhs));
     LQCD_TRY(upload(ctx, zk, W.coef));
-    LQCD_TRY(blas_multiaxpy(ctx, defl->V, N, 0, k + 1, W.coef, -1.0, r_dev, N, nrhs));
+    LQCD_TRY(blas_multiaxpy(ctx, Vd, N, 0, k + 1, W.coef, -1.0, r_dev, N, nrhs));
     // (ii) one GMRES(m) cycle from r
     LQCD_TRY(blas_norms(ctx, r_dev, N, nrhs, W.nrm));
     std::vector<double> beta;
@@ -508,67 +532,185 @@ lqcd_status proj_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const 
     LQCD_TRY(arnoldi_run(A, 0, R, matvecs));
     std::vector<cd> dcoef((size_t)m * nrhs, cd(0.0, 0.0)), scoef((size_t)(m + 1) * nrhs, cd(0.0, 0.0));
     all_conv = true;
+    worst = 0.0;
     for (int r = 0; r < nrhs; ++r) {
       if (!R[r].active) {
         scoef[r] = beta[r];  // keep r unchanged: r = V_0 * beta
         continue;
       }
       std::vector<cd> d = dense::lstsq(R[r].H, R[r].c);
-      std::vector<cd> s = R[r].c;
+      std::vector<cd> sv = R[r].c;
       for (int i = 0; i <= m; ++i)
-        for (int j = 0; j < m; ++j) s[i] -= R[r].H(i, j) * d[j];
+        for (int j = 0; j < m; ++j) sv[i] -= R[r].H(i, j) * d[j];
       double sn = 0.0;
-      for (const cd &v : s) sn += std::norm(v);
+      for (const cd &v : sv) sn += std::norm(v);
       R[r].rel = std::sqrt(sn) / R[r].bnorm;
+      worst = std::max(worst, R[r].rel);
       for (int j = 0; j < m; ++j) dcoef[(size_t)j * nrhs + r] = d[j];
-      for (int i = 0; i <= m; ++i) scoef[(size_t)i * nrhs + r] = s[i];
-      if (R[r].rel > o->tol) all_conv = false;
+      for (int i = 0; i <= m; ++i) scoef[(size_t)i * nrhs + r] = sv[i];
+      if (R[r].rel > tol) all_conv = false;
     }
     LQCD_TRY(upload(ctx, dcoef, W.coef));
     LQCD_TRY(blas_multiaxpy(ctx, W.Vb, vs, N, m, W.coef, 1.0, x, N, nrhs));
     LQCD_TRY(upload(ctx, scoef, W.coef));
     LQCD_TRY(blas_combine(ctx, W.Vb, vs, N, m + 1, W.coef, 1, r_dev, vs, N, nrhs));
     if (all_conv) {
+      if (!check_true) break;
       // confirm with the true residual; continue from it where the recursion drifted
       std::vector<double> rel;
-      LQCD_TRY(true_residuals(ctx, op, b, x, W.tmp, nrhs, R, rel));
+      if constexpr (std::is_same<S, double2>::value) {
+        LQCD_TRY(true_residuals(ctx, op, b, x, W.tmp, nrhs, R, rel));
+      } else {
+        break;
+      }
       matvecs += nrhs;
       worst = 0.0;
       bool ok = true;
       for (int r = 0; r < nrhs; ++r) {
         worst = std::max(worst, rel[r]);
-        if (rel[r] > o->tol) ok = false;
+        if (rel[r] > tol) ok = false;
       }
       if (ok) break;
       all_conv = false;
       LQCD_TRY(blas_copy(ctx, W.tmp, r_dev, vs));
-      for (int r = 0; r < nrhs; ++r) R[r].active = rel[r] > o->tol;
+      for (int r = 0; r < nrhs; ++r) R[r].active = rel[r] > tol;
     }
     for (int r = 0; r < nrhs; ++r)
-      if (R[r].active && R[r].rel <= o->tol) R[r].active = false;
+      if (R[r].active && R[r].rel <= tol) R[r].active = false;
   }
-  if (!all_conv) {
-    std::vector<double> rel;
-    LQCD_TRY(true_residuals(ctx, op, b, x, W.tmp, nrhs, R, rel));
-    matvecs += nrhs;
+  if constexpr (std::is_same<S, double2>::value) {
+    if (!all_conv && check_true) {
+      std::vector<double> rel;
+      LQCD_TRY(true_residuals(ctx, op, b, x, W.tmp, nrhs, R, rel));
+      matvecs += nrhs;
+      worst = 0.0;
+      for (int r = 0; r < nrhs; ++r) worst = std::max(worst, rel[r]);
+    }
+  }
+  res.cycles = cycles;
+  res.matvecs = matvecs;
+  res.worst = worst;
+  res.converged = worst <= tol;
+  return LQCD_OK;
+}
+
+Mat defl_hbar(const lqcd_defl *defl) {
+  const int k = defl->k;
+  Mat Hk(k + 1, k);
+  for (int i = 0; i <= k; ++i)
+    for (int j = 0; j < k; ++j) {
+      const double2 v = defl->Hbar[(size_t)i * k + j];
+      Hk(i, j) = cd(v.x, v.y);
+    }
+  return Hk;
+}
+
+// Plain FP64 GMRES-Proj
+lqcd_status proj_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const double2 *b, double2 *x, int nrhs,
+                      const lqcd_krylov_opts *o, lqcd_solve_info *info) {
+  const double t0 = now_s();
+  LQCD_TRY(check_opts(ctx, o, nrhs));
+  if (!defl || !defl->V || !defl->Hbar_dev) return set_err(ctx, LQCD_ERR_INVALID_ARG, "GMRES-Proj needs a solver-made deflation space");
+  ProjResult res;
+  LQCD_TRY(proj_run<double2>(ctx, op, defl->V, defl_hbar(defl), b, x, nrhs, o->m, o->tol, o->max_cycles, true, res));
+  if (info) {
+    info->cycles = res.cycles;
+    info->matvecs = (long)res.matvecs;
+    info->converged = res.converged ? 1 : 0;
+    info->true_resid = res.worst;
+    info->seconds = now_s() - t0;
+  }
+  return res.converged ? LQCD_OK
+                       : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "GMRES-Proj: no convergence in %d cycles (rel %.3e)", res.cycles, res.worst);
+}
+
+// Mixed precision: FP64 defect correction around FP32 GMRES-Proj.  Each outer step solves
+// M e = r / ||r|| approximately with FP32 storage and arithmetic (inner relative residual
+// INNER_TOL), adds ||r|| e to the FP64 solution, and recomputes the true residual r = b - M x with
+// the FP64 operator; it stops when every right-hand side has ||r|| <= tol ||b|| in FP64.
+constexpr double INNER_TOL = 5e-6;
+constexpr int MAX_OUTER = 40;
+
+lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const double2 *b, double2 *x, int nrhs,
+                       const lqcd_krylov_opts *o, lqcd_solve_info *info) {
+  const double t0 = now_s();
+  LQCD_TRY(check_opts(ctx, o, nrhs));
+  if (!defl || !defl->V || !defl->Hbar_dev) return set_err(ctx, LQCD_ERR_INVALID_ARG, "GMRES-Proj needs a solver-made deflation space");
+  const long long N = ctx->N, vs = (long long)nrhs * N;
+  const int k = defl->k;
+  float2 *U32, *V32, *r32, *e32;
+  double2 *r;
+  double *sc;
+  LQCD_TRY(ws_get(ctx, WS_MIX_U, sizeof(float2) * (size_t)ctx->V * 36, (void **)&U32));
+  LQCD_TRY(ws_get(ctx, WS_MIX_V, sizeof(float2) * (size_t)(k + 1) * N, (void **)&V32));
+  LQCD_TRY(ws_get(ctx, WS_MIX_R32, sizeof(float2) * (size_t)vs, (void **)&r32));
+  LQCD_TRY(ws_get(ctx, WS_MIX_E32, sizeof(float2) * (size_t)vs, (void **)&e32));
+  LQCD_TRY(ws_get(ctx, WS_MIX_R, sizeof(double2) * (size_t)vs, (void **)&r));
+  LQCD_TRY(ws_get(ctx, WS_MIX_S, sizeof(double) * (size_t)nrhs, (void **)&sc));
+  LQCD_TRY(blas_to_f32(ctx, op.U, U32, (long long)ctx->V * 36));
+  LQCD_TRY(blas_to_f32(ctx, defl->V, V32, (long long)(k + 1) * N));
+  const OpT<float2> op32{U32, op.kappa, op.flags};
+  const Mat Hk = defl_hbar(defl);
+  LQCD_TRY(blas_zero(ctx, x, vs));
+  LQCD_TRY(blas_copy(ctx, b, r, vs));
+  LQCD_TRY(blas_norms(ctx, b, N, nrhs, sc));
+  std::vector<double> bn, rn;
+  LQCD_TRY(download(ctx, sc, bn, nrhs));
+  long long matvecs = 0;
+  int outer = 0, inner_cycles = 0;
+  double worst = 0.0;
+  bool conv = false;
+  for (outer = 0; outer <= MAX_OUTER; ++outer) {
+    LQCD_TRY(blas_norms(ctx, r, N, nrhs, sc));
+    LQCD_TRY(download(ctx, sc, rn, nrhs));
     worst = 0.0;
-    for (int r = 0; r < nrhs; ++r) worst = std::max(worst, rel[r]);
+    std::vector<double> scale(nrhs);
+    for (int i = 0; i < nrhs; ++i) {
+      const double rel = bn[i] > 0.0 ? rn[i] / bn[i] : 0.0;
+      if (!std::isfinite(rel)) return set_err(ctx, LQCD_ERR_NONFINITE, "mixed solve: non-finite residual (rhs %d)", i);
+      worst = std::max(worst, rel);
+      scale[i] = rel > o->tol ? rn[i] : 0.0;  // converged right-hand sides get a zero inner problem
+    }
+    if (worst <= o->tol) {
+      conv = true;
+      break;
+    }
+    if (outer == MAX_OUTER || inner_cycles >= o->max_cycles) break;
+    {
+      double *st;
+      LQCD_TRY(host_stage(ctx, sizeof(double) * nrhs, &st));
+      LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      memcpy(st, scale.data(), sizeof(double) * nrhs);
+      LQCD_CUDA(ctx, cudaMemcpyAsync(sc, st, sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    LQCD_TRY(blas_demote(ctx, r, sc, r32, N, nrhs));
+    ProjResult pr;
+    LQCD_TRY(proj_run<float2>(ctx, op32, V32, Hk, r32, e32, nrhs, o->m, INNER_TOL,
+                              std::max(1, o->max_cycles - inner_cycles), false, pr));
+    inner_cycles += pr.cycles;
+    matvecs += pr.matvecs;
+    LQCD_TRY(blas_promote_acc(ctx, e32, sc, x, N, nrhs));
+    // FP64 true residual r = b - M x
+    LQCD_TRY(op.apply(ctx, x, r, nrhs));
+    LQCD_TRY(blas_bminus(ctx, r, b, vs));
+    matvecs += nrhs;
   }
   if (info) {
-    info->cycles = cycles;
+    info->cycles = inner_cycles;
     info->matvecs = (long)matvecs;
-    info->converged = (worst <= o->tol) ? 1 : 0;
+    info->converged = conv ? 1 : 0;
     info->true_resid = worst;
     info->seconds = now_s() - t0;
   }
-  return (worst <= o->tol) ? LQCD_OK
-                           : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "GMRES-Proj: no convergence in %d cycles (rel %.3e)", cycles, worst);
+  return conv ? LQCD_OK
+              : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "mixed GMRES-Proj: no convergence after %d outer steps (rel %.3e)", outer, worst);
 }
 
 lqcd_status proj_core_entry(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, const double2 *b,
                             double2 *x, int nrhs, const lqcd_krylov_opts *o, lqcd_solve_info *info) {
   const int sys = defl->hermitian ? LQCD_SYS_MG5 : o->system;
-  Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, o->prec};
+  Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, LQCD_PREC_F64};
+  if (o->prec == LQCD_PREC_F32) return mixed_core(ctx, op, defl, b, x, nrhs, o, info);
   return proj_core(ctx, op, defl, b, x, nrhs, o, info);
 }
 
@@ -599,9 +741,7 @@ lqcd_status lqcd_proj_solve(lqcd_ctx *ctx, const double *links, double kappa, co
                             double *x, int nrhs, const lqcd_krylov_opts *opts, lqcd_solve_info *info) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
   if (!links || !b || !x || !opts || !defl) return set_err(ctx, LQCD_ERR_INVALID_ARG, "NULL argument");
-  const int sys = defl->hermitian ? LQCD_SYS_MG5 : opts->system;
-  Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, opts->prec};
-  return proj_core(ctx, op, defl, (const double2 *)b, (double2 *)x, nrhs, opts, info);
+  return proj_core_entry(ctx, links, kappa, defl, (const double2 *)b, (double2 *)x, nrhs, opts, info);
 }
 
 lqcd_status lqcd_defl_destroy(lqcd_defl *d) {

@@ -163,21 +163,160 @@ __global__ void scaled_acc_kernel(const double2 *__restrict__ x, double2 *__rest
   }
 }
 
-// Probe vectors: probe p of the batch = sum over the sites of colour class cls(p) of unit vectors
-// at spin-colour component comp(p); classes by (x mod px, y mod py, z mod pz, t mod pt).
-__global__ void probe_kernel(int first, int nprobe, int Lx, int Ly, int Lz, int Lt, int px, int py, int pz, int pt,
+// Probing colourings for the hopping traces.  Two sites of one colour class must be more than K
+// hops apart on the torus (K - 1 hops of P^k plus the one hop of a point-split operator), so that
+// every off-diagonal term of z_c^dag Theta P^k z_c vanishes.
+//   * scaled D4: with s = ceil((K + 1) / 2), classes are the cosets of s D4 = {v in s Z^4 :
+//     sum(v) / s even}, whose shortest non-zero vector has 2 s >= K + 1 hops; class =
+//     (x mod s per direction, parity of sum_mu floor(x_mu / s)); 2 s^4 classes.  Needs every
+//     extent divisible by 2 s (the torus periods then lie in s D4).
+//   * Cartesian fallback: class = (x mod p_mu) with p_mu the smallest divisor of L_mu that is
+//     >= K + 1, else L_mu.
+struct Colouring {
+  int s[4];
+  int parity;
+  int ncls;
+};
+
+__host__ __device__ __forceinline__ int class_of(const Colouring &c, int x, int y, int z, int t) {
+  const int base = (x % c.s[0]) + c.s[0] * ((y % c.s[1]) + c.s[1] * ((z % c.s[2]) + c.s[2] * (t % c.s[3])));
+  if (!c.parity) return base;
+  const int par = (x / c.s[0] + y / c.s[1] + z / c.s[2] + t / c.s[3]) & 1;
+  return 2 * base + par;
+}
+
+// Probe vectors: probe p of the batch (global probe first + p) has colour class g / 12 and
+// spin-colour component g % 12: a unit entry at that component on every site of the class.
+__global__ void probe_kernel(int first, int nprobe, int Lx, int Ly, int Lz, int Lt, Colouring col,
                              double2 *__restrict__ out) {
   const long long V = (long long)Lx * Ly * Lz * Lt;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (s >= V || p >= nprobe) return;
   const int x = s % Lx, y = (s / Lx) % Ly, z = (s / (Lx * Ly)) % Lz, t = s / (Lx * Ly * Lz);
-  const int cls = (x % px) + px * ((y % py) + py * ((z % pz) + pz * (t % pt)));
+  const int cls = class_of(col, x, y, z, t);
   const int g = first + p;
   const int pc = g / 12, comp = g % 12;
   double2 *o = out + ((long long)p * V + s) * 12;
 #pragma unroll
   for (int e = 0; e < 12; ++e) o[e] = make_double2((cls == pc && e == comp) ? 1.0 : 0.0, 0.0);
+}
+
+__device__ __forceinline__ Cx<double> pick(const Cx<double> a[4][3], int comp) {
+  Cx<double> r = mk<double>(0.0, 0.0);
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (3 * sp + c == comp) r = a[sp][c];
+  return r;
+}
+
+template <int MU>
+__device__ __forceinline__ Cx<double> ps_term1(const double2 *U, const double2 *w, int b, long long V, int comp) {
+  // ((1 + g_mu) U_mu(b)^dag w(b))_comp
+  Cx<double> u[9], ws[4][3], a[4][3];
+  load_link<double>(U, (long long)MU * V + b, u);
+  load_spinor<double, false>(w + 12LL * b, ws);
+  zero_sp<MU>(a);
+  term_bwd<double, MU>(ws, u, a);
+  return pick(a, comp);
+}
+
+template <int MU>
+__device__ __forceinline__ Cx<double> ps_term2(const double2 *U, const double2 *w, int m, int mp, long long V, int comp) {
+  // ((1 - g_mu) U_mu(m) w(m + mu))_comp
+  Cx<double> u[9], ws[4][3], a[4][3];
+  load_link<double>(U, (long long)MU * V + m, u);
+  load_spinor<double, false>(w + 12LL * mp, ws);
+  zero_sp<MU>(a);
+  term_fwd<double, MU>(ws, u, a);
+  return pick(a, comp);
+}
+
+// Sparse contraction of probes with P^k probes: out[p][op][t] = sum over the base sites x in
+// timeslice t of the density of z_p^dag Theta_op w_p.  z_p is a unit entry (component comp) on
+// the members of its class, so only terms at class members (and at x = member - mu for the first
+// point-split term) survive.  One block per probe, one thread per (op, t); each thread sums its
+// few members in a fixed order.
+__global__ void probe_contract_kernel(const double2 *__restrict__ U, double kappa, const double2 *__restrict__ W,
+                                      int first, int nprobe, int Lx, int Ly, int Lz, int Lt, Colouring col,
+                                      double2 *__restrict__ out) {
+  const int p = blockIdx.x;
+  if (p >= nprobe) return;
+  const long long V = (long long)Lx * Ly * Lz * Lt;
+  const double2 *w = W + (long long)p * V * 12;
+  const int g = first + p;
+  const int cls = g / 12, comp = g % 12;
+  // decode the class into its residues (and parity for the scaled-D4 colouring)
+  const int par = col.parity ? (cls & 1) : 0;
+  int base = col.parity ? (cls >> 1) : cls;
+  const int rx = base % col.s[0];
+  base /= col.s[0];
+  const int ry = base % col.s[1];
+  base /= col.s[1];
+  const int rz = base % col.s[2];
+  const int rt = base / col.s[2];
+  for (int idx = threadIdx.x; idx < 9 * Lt; idx += blockDim.x) {
+    const int op = idx / Lt, t = idx % Lt;
+    // members m of the class whose relevant base site lies in slice t: slice t itself, except for
+    // the first point-split term in the t direction (base m - t_hat), whose members are in t + 1
+    double re = 0.0, im = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int tm = (pass == 0) ? t : (t + 1) % Lt;
+      if (pass == 1 && op != 8) break;
+      if (tm % col.s[3] != rt) continue;
+      const int nt = tm / col.s[3];
+      for (int nz = 0; nz < Lz / col.s[2]; ++nz)
+        for (int ny = 0; ny < Ly / col.s[1]; ++ny)
+          for (int nx = 0; nx < Lx / col.s[0]; ++nx) {
+            if (col.parity && ((nx + ny + nz + nt) & 1) != par) continue;
+            const int x = rx + col.s[0] * nx, y = ry + col.s[1] * ny, z = rz + col.s[2] * nz;
+            const int m = x + Lx * (y + Ly * (z + Lz * tm));
+            Cx<double> v = mk<double>(0.0, 0.0);
+            if (op == 0 && pass == 0) {
+              v = load_c<double>(w + 12LL * m + comp);
+            } else if (op <= 4 && pass == 0) {
+              Cx<double> ws[4][3], gw[4][3];
+              load_spinor<double, false>(w + 12LL * m, ws);
+              if (op == 1) gamma_apply<0>(ws, gw);
+              if (op == 2) gamma_apply<1>(ws, gw);
+              if (op == 3) gamma_apply<2>(ws, gw);
+              if (op == 4) gamma_apply<3>(ws, gw);
+              v = pick(gw, comp);
+            } else if (op >= 5) {
+              const int mu = op - 5;
+              if (pass == 0) {
+                // second term at base m: - (1 - g) U(m) w(m + mu); first term for mu != t at base m - mu
+                const int xp = (x + 1) % Lx, yp = (y + 1) % Ly, zp = (z + 1) % Lz, tp = (tm + 1) % Lt;
+                const int xm = (x + Lx - 1) % Lx, ym = (y + Ly - 1) % Ly, zm = (z + Lz - 1) % Lz;
+                Cx<double> t1 = mk<double>(0.0, 0.0), t2;
+                if (mu == 0) {
+                  t2 = ps_term2<0>(U, w, m, xp + Lx * (y + Ly * (z + Lz * tm)), V, comp);
+                  t1 = ps_term1<0>(U, w, xm + Lx * (y + Ly * (z + Lz * tm)), V, comp);
+                } else if (mu == 1) {
+                  t2 = ps_term2<1>(U, w, m, x + Lx * (yp + Ly * (z + Lz * tm)), V, comp);
+                  t1 = ps_term1<1>(U, w, x + Lx * (ym + Ly * (z + Lz * tm)), V, comp);
+                } else if (mu == 2) {
+                  t2 = ps_term2<2>(U, w, m, x + Lx * (y + Ly * (zp + Lz * tm)), V, comp);
+                  t1 = ps_term1<2>(U, w, x + Lx * (y + Ly * (zm + Lz * tm)), V, comp);
+                } else {
+                  t2 = ps_term2<3>(U, w, m, x + Lx * (y + Ly * (z + Lz * tp)), V, comp);
+                }
+                v = mk<double>(kappa * (t1.x - t2.x), kappa * (t1.y - t2.y));
+              } else {
+                // first term in the t direction: member m in slice t + 1, base m - t_hat in slice t
+                const int b = x + Lx * (y + Ly * (z + Lz * t));
+                Cx<double> t1 = ps_term1<3>(U, w, b, V, comp);
+                v = mk<double>(kappa * t1.x, kappa * t1.y);
+              }
+            }
+            re += v.x;
+            im += v.y;
+          }
+    }
+    out[((long long)p * 9 + op) * Lt + t] = make_double2(re, im);
+  }
 }
 
 template <typename T>
@@ -200,10 +339,28 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-int probe_period(int L, int K) {
-  for (int p = K + 1; p < L; ++p)
-    if (L % p == 0) return p;
-  return L;
+Colouring choose_colouring(const int *d, int K) {
+  Colouring c;
+  const int sd = (K + 2) / 2;  // ceil((K + 1) / 2)
+  bool d4 = true;
+  for (int i = 0; i < 4; ++i)
+    if (d[i] % (2 * sd) != 0) d4 = false;
+  if (d4) {
+    for (int i = 0; i < 4; ++i) c.s[i] = sd;
+    c.parity = 1;
+    c.ncls = 2 * sd * sd * sd * sd;
+    return c;
+  }
+  c.parity = 0;
+  c.ncls = 1;
+  for (int i = 0; i < 4; ++i) {
+    int p = d[i];
+    for (int q = K + 1; q < d[i]; ++q)
+      if (d[i] % q == 0) { p = q; break; }
+    c.s[i] = p;
+    c.ncls *= p;
+  }
+  return c;
 }
 
 }  // namespace
@@ -346,10 +503,10 @@ static lqcd_status hop_traces_dev(lqcd_ctx *ctx, const double2 *U, double kappa,
   const int *d = ctx->dims;
   const int Lt = d[3];
   const long long N = ctx->N;
-  const int px = probe_period(d[0], K), py = probe_period(d[1], K), pz = probe_period(d[2], K), pt = probe_period(d[3], K);
-  const long long nprobes = 12LL * px * py * pz * pt;
-  // probes per batch: bounded by memory (three probe-sized buffers) and by the launch grid
-  const int B = (int)std::min<long long>(nprobes, std::max<long long>(1, std::min<long long>(64, (1LL << 31) / (N * 16 * 3))));
+  const Colouring col = choose_colouring(d, K);
+  const long long nprobes = 12LL * col.ncls;
+  // probes per batch: bounded by memory (three probe-sized buffers of at most 2 GiB together)
+  const int B = (int)std::min<long long>(nprobes, std::max<long long>(1, std::min<long long>(192, (1LL << 31) / (N * 16 * 3))));
   double2 *Z, *W0, *W1, *cd_dev;
   LQCD_TRY(ws_get(ctx, WS_PROBE, sizeof(double2) * (size_t)B * N, (void **)&Z));
   LQCD_TRY(ws_get(ctx, WS_TMP2, sizeof(double2) * (size_t)B * N, (void **)&W0));
@@ -357,18 +514,21 @@ static lqcd_status hop_traces_dev(lqcd_ctx *ctx, const double2 *U, double kappa,
   LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)K * B * 9 * Lt, (void **)&cd_dev));
   tr.assign((size_t)K * 9 * Lt, cd(0.0, 0.0));
   std::vector<double2> h;
+  const int cthreads = std::min(1024, ((9 * Lt + 31) / 32) * 32);
   for (long long p0 = 0; p0 < nprobes; p0 += B) {
     const int nb = (int)std::min<long long>(B, nprobes - p0);
     kbegin(ctx);
-    probe_kernel<<<dim3(ceil_div(ctx->V, 128), nb), 128, 0, ctx->stream>>>((int)p0, nb, d[0], d[1], d[2], d[3], px, py,
-                                                                           pz, pt, Z);
+    probe_kernel<<<dim3(ceil_div(ctx->V, 128), nb), 128, 0, ctx->stream>>>((int)p0, nb, d[0], d[1], d[2], d[3], col, Z);
     LQCD_TRY(launch_check(ctx, "probe_kernel", K_PROBE, (double)ctx->V * nb));
-    LQCD_TRY(contract_launch(ctx, U, kappa, Z, Z, nb, cd_dev));
     const double2 *cur = Z;
-    for (int k = 1; k < K; ++k) {
+    for (int k = 0; k < K; ++k) {
       double2 *nxt = (k & 1) ? W0 : W1;
-      LQCD_TRY(wilson_launch(ctx, U, kappa, cur, nxt, nb, LQCD_PREC_F64, LQCD_APPLY_HOP));
-      LQCD_TRY(contract_launch(ctx, U, kappa, Z, nxt, nb, cd_dev + (size_t)k * nb * 9 * Lt));
+      if (k > 0) LQCD_TRY(wilson_launch(ctx, U, kappa, cur, nxt, nb, LQCD_PREC_F64, LQCD_APPLY_HOP));
+      else nxt = Z;
+      kbegin(ctx);
+      probe_contract_kernel<<<nb, cthreads, 0, ctx->stream>>>(U, kappa, nxt, (int)p0, nb, d[0], d[1], d[2], d[3], col,
+                                                               cd_dev + (size_t)k * nb * 9 * Lt);
+      LQCD_TRY(launch_check(ctx, "probe_contract_kernel", K_PROBE, (double)nb * ctx->V / col.ncls));
       cur = nxt;
     }
     LQCD_TRY(download_v(ctx, cd_dev, h, (size_t)K * nb * 9 * Lt));
@@ -496,7 +656,8 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
   if (o->nnoise < 1 || o->block < 1 || o->m < 2 || o->k < 1 || o->k >= o->m || o->K < 1 || o->npoly < 0 ||
       o->npoly > 63 || o->K > 64 || !(o->tol > 0) || !(o->tol_special > 0) || o->max_cycles < 1)
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: bad options");
-  if (o->prec != LQCD_PREC_F64) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: only LQCD_PREC_F64");
+  if (o->prec != LQCD_PREC_F64 && o->prec != LQCD_PREC_F32)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: prec must be LQCD_PREC_F64 or LQCD_PREC_F32");
   const double2 *U = (const double2 *)links;
   const int Lt = ctx->dims[3];
   const long long N = ctx->N;
@@ -606,7 +767,7 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
   LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)bw * 9 * Lt, (void **)&cdv));
   const int nn = o->nnoise;
   std::vector<cd> per_noise_t((size_t)LQCD_NMODES * nn * 9 * Lt, cd(0.0, 0.0));
-  lqcd_krylov_opts po{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, LQCD_PREC_F64};
+  lqcd_krylov_opts po{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec};
   long matvecs_noise = 0;
   double worst = 0.0;
   int conv = 1;

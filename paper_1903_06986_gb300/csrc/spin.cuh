@@ -28,6 +28,13 @@ template <typename R> __device__ __forceinline__ Cx<R> load_c(const double2 *p) 
   double2 v = __ldg(p);
   return mk<R>((R)v.x, (R)v.y);
 }
+template <typename R> __device__ __forceinline__ Cx<R> load_c(const float2 *p) {
+  float2 v = __ldg(p);
+  return mk<R>((R)v.x, (R)v.y);
+}
+__device__ __forceinline__ void store_c(double2 *p, Cx<double> v) { *p = make_double2(v.x, v.y); }
+__device__ __forceinline__ void store_c(double2 *p, Cx<float> v) { *p = make_double2((double)v.x, (double)v.y); }
+__device__ __forceinline__ void store_c(float2 *p, Cx<float> v) { *p = make_float2(v.x, v.y); }
 
 // u * h for a 3x3 colour matrix u (row-major) and colour vector h
 template <typename R> __device__ __forceinline__ void mul_u(const Cx<R> u[9], const Cx<R> h[3], Cx<R> o[3]) {
@@ -63,8 +70,8 @@ template <typename R> __device__ __forceinline__ void mul_udag(const Cx<R> u[9],
   }
 }
 
-template <typename R, bool G5IN>
-__device__ __forceinline__ void load_spinor(const double2 *p, Cx<R> s[4][3]) {
+template <typename R, bool G5IN, typename S>
+__device__ __forceinline__ void load_spinor(const S *p, Cx<R> s[4][3]) {
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
@@ -132,8 +139,8 @@ __device__ __forceinline__ void term_bwd(const Cx<R> p[4][3], const Cx<R> u[9], 
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void load_link(const double2 *U, long long idx, Cx<R> u[9]) {
+template <typename R, typename S>
+__device__ __forceinline__ void load_link(const S *U, long long idx, Cx<R> u[9]) {
 #pragma unroll
   for (int i = 0; i < 9; ++i) u[i] = load_c<R>(U + idx * 9 + i);
 }

@@ -24,16 +24,17 @@ namespace {
 
 using namespace spin;
 
-// MODE: 0 = M, 1 = M g5, 2 = M^dag = g5 M g5, 3 = P
-template <typename R, int MODE>
-__global__ void __launch_bounds__(128) wilson_kernel(const double2 *__restrict__ U, const double2 *__restrict__ in,
-                                                     double2 *__restrict__ out, double kappa, int Lx, int Ly,
+// MODE: 0 = M, 1 = M g5, 2 = M^dag = g5 M g5, 3 = P.  R: arithmetic; S: storage of spinors and
+// links (double2 with R = double or float; float2 with R = float).
+template <typename R, int MODE, typename S>
+__global__ void __launch_bounds__(128) wilson_kernel(const S *__restrict__ U, const S *__restrict__ in,
+                                                     S *__restrict__ out, double kappa, int Lx, int Ly,
                                                      int Lz, int Lt, int V) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
   constexpr bool G5IN = (MODE == 1 || MODE == 2);
   const long long base = (long long)blockIdx.y * V * 12;
-  const double2 *src = in + base;
+  const S *src = in + base;
   int x = s % Lx;
   int r = s / Lx;
   int y = r % Ly;
@@ -66,12 +67,12 @@ __global__ void __launch_bounds__(128) wilson_kernel(const double2 *__restrict__
   load_spinor<R, G5IN>(src + 12LL * tp, p); load_link<R>(U, 3 * V4 + s, u);  term_fwd<R, 3>(p, u, acc);
   load_spinor<R, G5IN>(src + 12LL * tm, p); load_link<R>(U, 3 * V4 + tm, u); term_bwd<R, 3>(p, u, acc);
 
-  double2 *dst = out + base + 12LL * s;
+  S *dst = out + base + 12LL * s;
   if (MODE == 3) {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) dst[3 * a + c] = make_double2((double)acc[a][c].x, (double)acc[a][c].y);
+      for (int c = 0; c < 3; ++c) store_c(dst + 3 * a + c, acc[a][c]);
     return;
   }
   load_spinor<R, G5IN>(src + 12LL * s, p);
@@ -94,21 +95,20 @@ __global__ void __launch_bounds__(128) wilson_kernel(const double2 *__restrict__
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dst[3 * a + c] = make_double2((double)o[a][c].x, (double)o[a][c].y);
+    for (int c = 0; c < 3; ++c) store_c(dst + 3 * a + c, o[a][c]);
 }
 
-template <typename R>
-lqcd_status launch_mode(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in, double2 *out, int nrhs,
-                        int flags) {
+template <typename R, typename S>
+lqcd_status launch_mode(lqcd_ctx *ctx, const S *U, double kappa, const S *in, S *out, int nrhs, int flags) {
   dim3 block(128);
   dim3 grid(ceil_div(ctx->V, 128), nrhs);
   const int *d = ctx->dims;
   kbegin(ctx);
   switch (flags) {
-    case LQCD_APPLY_M: wilson_kernel<R, 0><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
-    case LQCD_APPLY_G5R: wilson_kernel<R, 1><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
-    case LQCD_APPLY_DAG: wilson_kernel<R, 2><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
-    case LQCD_APPLY_HOP: wilson_kernel<R, 3><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
+    case LQCD_APPLY_M: wilson_kernel<R, 0, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
+    case LQCD_APPLY_G5R: wilson_kernel<R, 1, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
+    case LQCD_APPLY_DAG: wilson_kernel<R, 2, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
+    case LQCD_APPLY_HOP: wilson_kernel<R, 3, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
     default: return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply: unknown flags %d", flags);
   }
   return launch_check(ctx, "wilson_kernel", K_WILSON, (double)ctx->V * nrhs);
@@ -119,9 +119,15 @@ lqcd_status launch_mode(lqcd_ctx *ctx, const double2 *U, double kappa, const dou
 lqcd_status wilson_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in, double2 *out, int nrhs,
                           int prec, int flags) {
   if (nrhs <= 0 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply: nrhs %d out of range", nrhs);
-  if (prec == LQCD_PREC_F64) return launch_mode<double>(ctx, U, kappa, in, out, nrhs, flags);
-  if (prec == LQCD_PREC_F32) return launch_mode<float>(ctx, U, kappa, in, out, nrhs, flags);
+  if (prec == LQCD_PREC_F64) return launch_mode<double, double2>(ctx, U, kappa, in, out, nrhs, flags);
+  if (prec == LQCD_PREC_F32) return launch_mode<float, double2>(ctx, U, kappa, in, out, nrhs, flags);
   return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply: unknown precision %d", prec);
+}
+
+lqcd_status wilson_launch_f32(lqcd_ctx *ctx, const float2 *U, double kappa, const float2 *in, float2 *out, int nrhs,
+                              int flags) {
+  if (nrhs <= 0 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson (f32): nrhs %d out of range", nrhs);
+  return launch_mode<float, float2>(ctx, U, kappa, in, out, nrhs, flags);
 }
 
 extern "C" lqcd_status lqcd_wilson_apply(lqcd_ctx *ctx, const double *links, double kappa, const double *in,

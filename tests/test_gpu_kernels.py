@@ -124,8 +124,11 @@ def test_poly_coeffs_minimiser():
     assert rel_err(got, ref) < 1e-7
 
 
-@pytest.mark.parametrize("dims,K", [((4, 4, 4, 4), 5), ((2, 2, 2, 8), 3), ((3, 2, 2, 6), 4)])
+@pytest.mark.parametrize("dims,K", [((4, 4, 4, 4), 5), ((2, 2, 2, 8), 3), ((3, 2, 2, 6), 4), ((4, 4, 4, 8), 3),
+                                    ((8, 4, 4, 8), 3)])
 def test_hop_traces_small(dims, K):
+    """The GPU probes with a scaled-D4 colouring where the extents allow it ((4,4,4,8) and (8,4,4,8)
+    with K = 3) and a Cartesian one otherwise; the oracle always uses its own Cartesian classes."""
     ctx = context(dims)
     U = synth.su3_links(dims, 0.5, 11)
     kappa = 0.13
