@@ -230,6 +230,24 @@ lqcd_status lqcd_xi_inverse(lqcd_ctx *ctx, const double *links, double kappa, co
 lqcd_status lqcd_contract(lqcd_ctx *ctx, const double *links, double kappa, const double *eta,
                           const double *w, int nrhs, double *out);
 
+/* Allocation-free variant of lqcd_contract (the paper has no counterpart; it exists for callers).
+ * Some callers cannot allocate device memory: plug-ins whose host application owns every device
+ * byte through its own allocator, code running under a hard memory budget, and latency-critical
+ * paths where a cudaMalloc (which may synchronise the device) is not acceptable.  This entry point
+ * allocates nothing and needs no context:
+ * the caller passes the lattice dims (Lx, Ly, Lz, Lt), the device links, eta, w (nrhs fields) and
+ * a device output buffer out (nrhs x 9 x Lt complex128, same layout as lqcd_contract), and a
+ * cudaStream_t (NULL = legacy default stream).  Partial sums go to a fixed 1 MiB scratch array
+ * compiled into the library, which every GPU that loads the library holds until the process exits;
+ * it requires nrhs * Lt * 9 <= 65536 and returns LQCD_ERR_INVALID_ARG otherwise (or for bad
+ * dims / NULL pointers; there is no context, hence no error string).  The first call on each device
+ * looks up the scratch array's device address, so make it before any stream capture.  All calls
+ * share the one array, which keeps the last call's contents (every entry read is written first by
+ * the same call): calls that overlap on the GPU, from any stream or thread, race and must be
+ * serialised by the caller.  Asynchronous on the stream; no other call of this library is made. */
+lqcd_status lqcd_contract_noalloc(const int dims[4], const double *links, double kappa, const double *eta,
+                                  const double *w, int nrhs, double *out, void *stream);
+
 /* ---- whole path: loop estimate on one gauge configuration ----------------------------- */
 
 typedef struct {

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "dense.h"
@@ -860,4 +861,82 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
   out->max_true_resid = worst;
   out->converged = conv;
   return conv ? LQCD_OK : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop_estimate: a noise solve did not converge (rel %.3e)", worst);
+}
+
+// ---- allocation-free contraction -------------------------------------------------------------
+// Some callers cannot allocate device memory at all: plug-ins whose host application owns every
+// device byte through its own allocator, code under a strict memory budget, or latency-critical
+// paths where a cudaMalloc (which may synchronise the device) is not acceptable.
+// lqcd_contract_noalloc serves them: the same
+// contraction as lqcd_contract, but its per-chunk partial sums live in a fixed device array that
+// is part of the library image (loaded with the module, held by every device that loads the
+// library until the process exits), the output goes to a caller-provided device buffer, and no
+// context, workspace or staging buffer is involved.
+namespace {
+
+constexpr int NOALLOC_SCRATCH_ENTRIES = 1 << 16;  // double2 entries: 1 MiB
+static __device__ __align__(256) double2 g_noalloc_scratch[NOALLOC_SCRATCH_ENTRIES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double2 *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
+std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array for the current device, looked up once per device.  A host
+// reference to g_noalloc_scratch names a host-side stand-in, not device memory, so the address
+// must come from cudaGetSymbolAddress with the device current.
+lqcd_status noalloc_setup(int dev, double2 **ptr, int *sms) {
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return LQCD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return LQCD_ERR_CUDA;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return LQCD_ERR_CUDA;
+    }
+    g_noalloc_sms[dev] = n;
+    g_noalloc_ptr[dev] = (double2 *)p;
+  }
+  *ptr = g_noalloc_ptr[dev];
+  *sms = g_noalloc_sms[dev];
+  return LQCD_OK;
+}
+
+}  // namespace
+
+extern "C" lqcd_status lqcd_contract_noalloc(const int dims[4], const double *links, double kappa, const double *eta,
+                                             const double *w, int nrhs, double *out, void *stream) {
+  if (!dims || !links || !eta || !w || !out || nrhs < 1 || nrhs > 65535) return LQCD_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2 || dims[i] > 1024) return LQCD_ERR_INVALID_ARG;
+  const int Lt = dims[3], Vs = dims[0] * dims[1] * dims[2];
+  // every (rhs, timeslice, chunk) writes its nine partial sums: at least one chunk must fit
+  const long long per_chunk = (long long)nrhs * Lt * 9;
+  if (per_chunk > NOALLOC_SCRATCH_ENTRIES) return LQCD_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return LQCD_ERR_CUDA;
+  }
+  double2 *scratch = nullptr;
+  int sms = 0;
+  LQCD_TRY(noalloc_setup(dev, &scratch, &sms));
+  const long long fit = NOALLOC_SCRATCH_ENTRIES / per_chunk;
+  const int want = std::max(1, std::min((Vs + CBT - 1) / CBT, std::max(1, (4 * sms) / std::max(1, nrhs * Lt))));
+  const int nchunk = (int)std::max<long long>(1, std::min<long long>(want, fit));
+  cudaStream_t st = (cudaStream_t)stream;
+  // the kernel writes every partial entry it later reads, so the array needs no clearing
+  contract_kernel<<<dim3(nchunk * Lt, nrhs), CBT, 0, st>>>((const double2 *)links, kappa, (const double2 *)eta,
+                                                           (const double2 *)w, dims[0], dims[1], dims[2], dims[3],
+                                                           nchunk, scratch);
+  if (cudaGetLastError() != cudaSuccess) return LQCD_ERR_CUDA;
+  const int tot = nrhs * 9 * Lt;
+  contract_final<<<ceil_div(tot, 128), 128, 0, st>>>(scratch, nchunk, Lt, nrhs, (double2 *)out);
+  if (cudaGetLastError() != cudaSuccess) return LQCD_ERR_CUDA;
+  return LQCD_OK;
 }
