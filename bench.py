@@ -299,6 +299,8 @@ def main():
             step(i, Ud, prec=1)
         stats.clear()
         barrier()
+        ctx.timing(True)
+        ctx.timing_reset()
         m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         m0.record()
         for i in range(args.steps):
@@ -307,6 +309,8 @@ def main():
         m1.record()
         barrier()
         tm_mixed = m0.elapsed_time(m1) / 1000.0
+        tmm = ctx.timing_read()
+        ctx.timing(False)
         ms_ = stats[:args.steps]
         mixed = {"value": NNOISE * args.steps * world / tm_mixed, "unit": "estimates/s",
                  "speedup_vs_fp64": t_max / tm_mixed,
@@ -314,6 +318,9 @@ def main():
                  "noise_phase_speedup_vs_fp64": (sum(x["noise_s"] for x in ms_) and
                                                  sum(x["noise_s"] for x in stats_fp64) / sum(x["noise_s"] for x in ms_)),
                  "max_true_resid": max(x["resid"] for x in ms_),
+                 "matvecs_per_noise": float(np.mean([x["mv_noise"] / NNOISE for x in ms_])),
+                 "breakdown_ms": {k: round(v[0], 1) for k, v in tmm.items()},
+                 "launches": int(sum(v[1] for v in tmm.values())),
                  "precision": "FP32 storage and arithmetic inside FP64 defect correction (true residual FP64)"}
 
     # ---- roofline of the dominant kernel class (device time over the timed region)

@@ -46,60 +46,78 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
   return v;
 }
 
-// partial[(i * nrhs + r) * nb + blockIdx.x] = sum over this block's chunk of conj(V_i^r) w^r
+// Single-launch batched inner products.  The grid is (nchunk * ngroup, nrhs): block (c, g, r) sums
+// conj(V_i^r) w^r over element chunk c for the GROUP basis vectors of group g and writes
+// partial[(i * nrhs + r) * nchunk + c]; the last block to finish for right-hand side r (a counter
+// per r, reset by that block) adds the nchunk partials of every i in chunk order and writes
+// h[i * nrhs + r].  The result does not depend on block scheduling.
 template <typename S>
-__global__ void __launch_bounds__(BT) multidot_partial(const S *__restrict__ V, long long vstride,
-                                                       long long vrs, int nvec, const S *__restrict__ w,
-                                                       long long n, int nrhs, double2 *__restrict__ partial) {
+__global__ void __launch_bounds__(BT) multidot_kernel(const S *__restrict__ V, long long vstride, long long vrs,
+                                                      int nvec, const S *__restrict__ w, long long n, int nrhs,
+                                                      int nchunk, double2 *__restrict__ partial,
+                                                      unsigned *__restrict__ counters, double2 *__restrict__ h) {
   const int r = blockIdx.y;
-  const int nb = gridDim.x;
-  const long long chunk = (n + nb - 1) / nb;
-  const long long e0 = blockIdx.x * chunk;
+  const int c = blockIdx.x % nchunk;
+  const int i0 = (blockIdx.x / nchunk) * GROUP;
+  const long long chunk = (n + nchunk - 1) / nchunk;
+  const long long e0 = c * chunk;
   const long long e1 = min(n, e0 + chunk);
   const S *wr = w + r * n;
+  const S *vr = V + r * vrs;
   __shared__ double2 red[BT / 32][GROUP];
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i0 = 0; i0 < nvec; i0 += GROUP) {
-    const int g = min(GROUP, nvec - i0);
-    S acc[GROUP];
+  const int g = min(GROUP, nvec - i0);
+  const S *vp[GROUP];
 #pragma unroll
-    for (int j = 0; j < GROUP; ++j) acc[j] = cz<S>();
+  for (int j = 0; j < GROUP; ++j) vp[j] = vr + (long long)(i0 + min(j, g - 1)) * vstride;
+  S acc[GROUP];
+#pragma unroll
+  for (int j = 0; j < GROUP; ++j) acc[j] = cz<S>();
+  if (g == GROUP) {
+    for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
+      const S wv = wr[e];
+#pragma unroll
+      for (int j = 0; j < GROUP; ++j) gfma_conj(acc[j], vp[j][e], wv);
+    }
+  } else {
     for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
       const S wv = wr[e];
 #pragma unroll
       for (int j = 0; j < GROUP; ++j)
-        if (j < g) gfma_conj(acc[j], V[(long long)(i0 + j) * vstride + r * vrs + e], wv);
+        if (j < g) gfma_conj(acc[j], vp[j][e], wv);
     }
-#pragma unroll
-    for (int j = 0; j < GROUP; ++j) {
-      double2 v = warp_sum2(to_d2(acc[j]));
-      if (lane == 0) red[warp][j] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < g) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int q = 0; q < BT / 32; ++q) s = cadd(s, red[q][threadIdx.x]);
-      partial[((long long)(i0 + threadIdx.x) * nrhs + r) * nb + blockIdx.x] = s;
-    }
-    __syncthreads();
   }
-}
-
-// out[idx] = sum_b partial[idx * nb + b]   (one block per idx, fixed order)
-__global__ void __launch_bounds__(128) reduce_partials(const double2 *__restrict__ partial, int nb,
-                                                       double2 *__restrict__ out) {
-  const int idx = blockIdx.x;
-  double2 s = make_double2(0.0, 0.0);
-  for (int b = threadIdx.x; b < nb; b += 128) s = cadd(s, partial[(long long)idx * nb + b]);
-  s = warp_sum2(s);
-  __shared__ double2 red[4];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+#pragma unroll
+  for (int j = 0; j < GROUP; ++j) {
+    double2 v = warp_sum2(to_d2(acc[j]));
+    if (lane == 0) red[warp][j] = v;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) out[idx] = cadd(cadd(red[0], red[1]), cadd(red[2], red[3]));
+  if (threadIdx.x < g) {
+    double2 sum = make_double2(0.0, 0.0);
+    for (int q = 0; q < BT / 32; ++q) sum = cadd(sum, red[q][threadIdx.x]);
+    partial[((long long)(i0 + threadIdx.x) * nrhs + r) * nchunk + c] = sum;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&counters[r], 1u) == (unsigned)(gridDim.x - 1));
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < nvec; i += BT) {
+    const double2 *pp = partial + ((long long)i * nrhs + r) * nchunk;
+    double2 sum = make_double2(0.0, 0.0);
+    for (int q = 0; q < nchunk; ++q) sum = cadd(sum, __ldcg(pp + q));
+    h[(long long)i * nrhs + r] = sum;
+  }
+  if (threadIdx.x == 0) counters[r] = 0u;
 }
 
+// Single-launch batched norms ||x^r||, same last-block scheme as multidot_kernel.
 template <typename S>
-__global__ void __launch_bounds__(BT) norm2_partial(const S *__restrict__ x, long long n, double *__restrict__ partial) {
+__global__ void __launch_bounds__(BT) norm_kernel(const S *__restrict__ x, long long n, double *__restrict__ partial,
+                                                  unsigned *__restrict__ counters, double *__restrict__ out) {
   const int r = blockIdx.y;
   const int nb = gridDim.x;
   const long long chunk = (n + nb - 1) / nb;
@@ -116,63 +134,73 @@ __global__ void __launch_bounds__(BT) norm2_partial(const S *__restrict__ x, lon
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   __shared__ double red[BT / 32];
+  __shared__ bool last;
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int q = 0; q < BT / 32; ++q) s += red[q];
-    partial[(long long)r * nb + blockIdx.x] = s;
+    double sum = 0.0;
+    for (int q = 0; q < BT / 32; ++q) sum += red[q];
+    partial[(long long)r * nb + blockIdx.x] = sum;
+    __threadfence();
+    last = (atomicAdd(&counters[r], 1u) == (unsigned)(nb - 1));
   }
-}
-
-__global__ void __launch_bounds__(128) norm2_final(const double *__restrict__ partial, int nb, double *__restrict__ out) {
-  const int r = blockIdx.x;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += 128) s += partial[(long long)r * nb + b];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __shared__ double red[4];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  if (threadIdx.x == 0) out[r] = sqrt((red[0] + red[1]) + (red[2] + red[3]));
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double sum = 0.0;
+  for (int q = 0; q < nb; ++q) sum += __ldcg(partial + (long long)r * nb + q);
+  out[r] = sqrt(sum);
+  counters[r] = 0u;
 }
 
-// w^r += sign * sum_i V_i^r h[i * nrhs + r]
+// w^r += sign * sum_i V_i^r h[i * nrhs + r]; the coefficients of this right-hand side are staged in
+// shared memory (already scaled by sign and converted to the storage precision).
+constexpr int AXPY_MAXV = 512;
 template <typename S>
 __global__ void __launch_bounds__(BT) multiaxpy_kernel(const S *__restrict__ V, long long vstride,
                                                        long long vrs, int nvec, const double2 *__restrict__ h,
                                                        double sign, S *__restrict__ w, long long n, int nrhs) {
-  const long long e = (long long)blockIdx.x * BT + threadIdx.x;
+  __shared__ S coef[AXPY_MAXV];
   const int r = blockIdx.y;
+  for (int i = threadIdx.x; i < nvec; i += BT) coef[i] = from_d2<S>(cscale(h[(long long)i * nrhs + r], sign));
+  __syncthreads();
+  const long long e = (long long)blockIdx.x * BT + threadIdx.x;
   if (e >= n) return;
+  const S *vp = V + r * vrs + e;
   S acc = w[r * n + e];
-  for (int i = 0; i < nvec; ++i) {
-    const S c = from_d2<S>(cscale(h[(long long)i * nrhs + r], sign));
-    gfma(acc, V[(long long)i * vstride + r * vrs + e], c);
-  }
+  for (int i = 0; i < nvec; ++i, vp += vstride) gfma(acc, *vp, coef[i]);
   w[r * n + e] = acc;
 }
 
-constexpr int CT = 8;  // output columns per pass in combine
-// out_c^r = sum_i V_i^r C[(i * ncol + c) * nrhs + r]
+constexpr int CT = 8;           // output columns per pass in combine
+constexpr int COMB_MAXV = 256;  // basis vectors of one combine (coefficient tile in shared memory)
+// out_c^r = sum_i V_i^r C[(i * ncol + c) * nrhs + r]; a tile of CT columns of coefficients for this
+// right-hand side is staged in shared memory per pass.
 template <typename S>
 __global__ void __launch_bounds__(BT) combine_kernel(const S *__restrict__ V, long long vstride,
                                                      long long vrs, int nvec, const double2 *__restrict__ C,
                                                      int ncol, S *__restrict__ out, long long ostride,
                                                      long long n, int nrhs) {
+  __shared__ S coef[COMB_MAXV * CT];
   const long long e = (long long)blockIdx.x * BT + threadIdx.x;
   const int r = blockIdx.y;
-  if (e >= n) return;
   for (int c0 = 0; c0 < ncol; c0 += CT) {
     const int g = min(CT, ncol - c0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < nvec * CT; q += BT) {
+      const int i = q / CT, j = q % CT;
+      coef[q] = (j < g) ? from_d2<S>(C[((long long)i * ncol + c0 + j) * nrhs + r]) : cz<S>();
+    }
+    __syncthreads();
+    if (e >= n) continue;
     S acc[CT];
 #pragma unroll
     for (int j = 0; j < CT; ++j) acc[j] = cz<S>();
-    for (int i = 0; i < nvec; ++i) {
-      const S v = V[(long long)i * vstride + r * vrs + e];
+    const S *vp = V + r * vrs + e;
+    for (int i = 0; i < nvec; ++i, vp += vstride) {
+      const S v = *vp;
 #pragma unroll
-      for (int j = 0; j < CT; ++j)
-        if (j < g) gfma(acc[j], v, from_d2<S>(C[((long long)i * ncol + c0 + j) * nrhs + r]));
+      for (int j = 0; j < CT; ++j) gfma(acc[j], v, coef[i * CT + j]);
     }
 #pragma unroll
     for (int j = 0; j < CT; ++j)
@@ -351,38 +379,53 @@ lqcd_status blas_g5(lqcd_ctx *ctx, const double2 *x, double2 *y, int nrhs) {
   return launch_check(ctx, "g5_kernel", K_BLAS1, (double)sites * 12);
 }
 
+// per-right-hand-side arrival counters of the single-launch reductions (zeroed once, left at zero)
+static lqcd_status reduction_counters(lqcd_ctx *ctx, int nrhs, unsigned **c) {
+  const size_t need = sizeof(unsigned) * (size_t)std::max(nrhs, 1);
+  const bool fresh = ctx->ws_size[WS_COUNT] < need;
+  LQCD_TRY(ws_get(ctx, WS_COUNT, need, (void **)c));
+  if (fresh) LQCD_CUDA(ctx, cudaMemsetAsync(*c, 0, ctx->ws_size[WS_COUNT], ctx->stream));
+  return LQCD_OK;
+}
+
 template <typename S>
 lqcd_status blas_norms(lqcd_ctx *ctx, const S *x, long long n, int nrhs, double *norms) {
   const int nb = partial_blocks(ctx, n, nrhs);
   void *p = nullptr;
+  unsigned *cnt = nullptr;
   LQCD_TRY(ws_get(ctx, WS_SCAL, sizeof(double) * (size_t)nb * nrhs, &p));
+  LQCD_TRY(reduction_counters(ctx, nrhs, &cnt));
   kbegin(ctx);
-  norm2_partial<S><<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(x, n, (double *)p);
-  LQCD_TRY(launch_check(ctx, "norm2_partial", K_NORM, (double)n * nrhs));
-  kbegin(ctx);
-  norm2_final<<<nrhs, 128, 0, ctx->stream>>>((const double *)p, nb, norms);
-  return launch_check(ctx, "norm2_final", K_NORM, 0.0);
+  norm_kernel<S><<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(x, n, (double *)p, cnt, norms);
+  return launch_check(ctx, "norm_kernel", K_NORM, (double)n * nrhs);
 }
 
 template <typename S>
 lqcd_status blas_multidot(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const S *w,
                           long long n, int nrhs, double2 *h) {
   if (nvec <= 0) return LQCD_OK;
-  const int nb = partial_blocks(ctx, n, nrhs);
+  // element chunks of at least 8 elements per thread; enough blocks (chunks x vector groups x
+  // right-hand sides) to cover the SMs a few times
+  const int ngroup = (nvec + GROUP - 1) / GROUP;
+  const long long max_chunks = std::max<long long>(1, n / (8LL * BT));
+  const long long want = std::max<long long>(1, (4LL * ctx->sms) / std::max<long long>(1, (long long)nrhs * ngroup));
+  const int nchunk = (int)std::min<long long>(std::min(max_chunks, want), 4096);
+  if ((long long)nchunk * ngroup > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "multidot: too many vectors");
   void *p = nullptr;
-  LQCD_TRY(ws_get(ctx, WS_PARTIAL, sizeof(double2) * (size_t)nb * nrhs * nvec, &p));
+  unsigned *cnt = nullptr;
+  LQCD_TRY(ws_get(ctx, WS_PARTIAL, sizeof(double2) * (size_t)nchunk * nrhs * nvec, &p));
+  LQCD_TRY(reduction_counters(ctx, nrhs, &cnt));
   kbegin(ctx);
-  multidot_partial<S><<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, (double2 *)p);
-  LQCD_TRY(launch_check(ctx, "multidot_partial", K_DOT, (double)n * nrhs * nvec));
-  kbegin(ctx);
-  reduce_partials<<<nvec * nrhs, 128, 0, ctx->stream>>>((const double2 *)p, nb, h);
-  return launch_check(ctx, "reduce_partials", K_DOT, 0.0);
+  multidot_kernel<S><<<dim3(nchunk * ngroup, nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, nchunk,
+                                                                         (double2 *)p, cnt, h);
+  return launch_check(ctx, "multidot_kernel", K_DOT, (double)n * nrhs * nvec);
 }
 
 template <typename S>
 lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const double2 *h,
                            double sign, S *w, long long n, int nrhs) {
   if (nvec <= 0) return LQCD_OK;
+  if (nvec > AXPY_MAXV) return set_err(ctx, LQCD_ERR_INVALID_ARG, "multiaxpy: at most %d vectors", AXPY_MAXV);
   kbegin(ctx);
   multiaxpy_kernel<S><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, h, sign, w, n, nrhs);
   return launch_check(ctx, "multiaxpy_kernel", K_AXPY, (double)n * nrhs * nvec);
@@ -392,6 +435,7 @@ template <typename S>
 lqcd_status blas_combine(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const double2 *C,
                          int ncol, S *out, long long ostride, long long n, int nrhs) {
   if (ncol <= 0) return LQCD_OK;
+  if (nvec > COMB_MAXV) return set_err(ctx, LQCD_ERR_INVALID_ARG, "combine: at most %d vectors", COMB_MAXV);
   kbegin(ctx);
   combine_kernel<S><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, C, ncol, out, ostride, n, nrhs);
   return launch_check(ctx, "combine_kernel", K_COMBINE, (double)n * nrhs * nvec * ncol);

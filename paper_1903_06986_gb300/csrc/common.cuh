@@ -82,7 +82,7 @@ lqcd_status launch_check(lqcd_ctx *ctx, const char *what, int cls, double units)
 enum WsSlot {
   WS_PARTIAL = 0, WS_SCAL, WS_TMP0, WS_TMP1, WS_TMP2, WS_TMP3, WS_BASIS, WS_HESS, WS_COEF,
   WS_BASIS2, WS_TMP4, WS_TMP5, WS_EST0, WS_EST1, WS_EST2, WS_PROBE,
-  WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_NSLOTS
+  WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_COUNT, WS_NSLOTS
 };
 lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr);
 lqcd_status host_stage(lqcd_ctx *ctx, size_t bytes, double **ptr);
@@ -140,6 +140,9 @@ static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) 
 // Wilson operator on nrhs fields (see lqcd_wilson_apply); in and out must not overlap.
 lqcd_status wilson_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in,
                           double2 *out, int nrhs, int prec, int flags);
+// FP64, right-hand side r gets M gamma_5 when bit r of g5mask is set and M otherwise (nrhs <= 64)
+lqcd_status wilson_launch_masked(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in, double2 *out,
+                                 int nrhs, unsigned long long g5mask);
 // FP32 storage and arithmetic (links converted to FP32 by the caller)
 lqcd_status wilson_launch_f32(lqcd_ctx *ctx, const float2 *U, double kappa, const float2 *in, float2 *out,
                               int nrhs, int flags);

@@ -29,15 +29,19 @@ using dense::Mat;
 
 namespace {
 
+constexpr int OP_MASKED = 4;
+
 // The operator of a solve: M or M gamma_5 (flags LQCD_APPLY_M / LQCD_APPLY_G5R) on FP64 storage
 // (arithmetic prec) or on FP32 storage with FP32 arithmetic (the inner solver of mixed precision).
 template <typename S> struct OpT;
 template <> struct OpT<double2> {
   const double2 *U;
   double kappa;
-  int flags;
+  int flags;                    // LQCD_APPLY_M, LQCD_APPLY_G5R, or OP_MASKED
   int prec;
+  unsigned long long g5mask;    // OP_MASKED: right-hand side r uses M gamma_5 when bit r is set
   lqcd_status apply(lqcd_ctx *ctx, const double2 *in, double2 *out, int nrhs) const {
+    if (flags == OP_MASKED) return wilson_launch_masked(ctx, U, kappa, in, out, nrhs, g5mask);
     return wilson_launch(ctx, U, kappa, in, out, nrhs, prec, flags);
   }
 };
@@ -55,24 +59,22 @@ lqcd_status apply_op(lqcd_ctx *ctx, const Op &op, const double2 *in, double2 *ou
   return op.apply(ctx, in, out, nrhs);
 }
 
+// Host -> device copy of small coefficient arrays.  From pageable memory cudaMemcpyAsync stages the
+// source before it returns and does not wait for earlier work in the stream, so the host vector
+// may be released immediately and the GPU keeps running.
 lqcd_status upload(lqcd_ctx *ctx, const std::vector<cd> &h, void *dev) {
   if (h.empty()) return LQCD_OK;
-  double *st = nullptr;
-  LQCD_TRY(host_stage(ctx, sizeof(cd) * h.size(), &st));
-  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // staging buffer may be in use
-  memcpy(st, h.data(), sizeof(cd) * h.size());
-  LQCD_CUDA(ctx, cudaMemcpyAsync(dev, st, sizeof(cd) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
-  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  LQCD_CUDA(ctx, cudaMemcpyAsync(dev, h.data(), sizeof(cd) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
   return LQCD_OK;
 }
 
+// Device -> host copy through the pinned staging buffer; waits for the stream.
 template <typename T>
 lqcd_status download(lqcd_ctx *ctx, const void *dev, std::vector<T> &h, size_t count) {
   h.resize(count);
   if (count == 0) return LQCD_OK;
   double *st = nullptr;
   LQCD_TRY(host_stage(ctx, sizeof(T) * count, &st));
-  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   LQCD_CUDA(ctx, cudaMemcpyAsync(st, dev, sizeof(T) * count, cudaMemcpyDeviceToHost, ctx->stream));
   LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   memcpy(h.data(), st, sizeof(T) * count);
@@ -298,8 +300,11 @@ lqcd_status ritz_pairs(lqcd_ctx *ctx, lqcd_defl *d) {
   return blas_combine(ctx, d->V, d->N, 0, k, (const double2 *)p, k, d->E, d->N, d->N, 1);
 }
 
+// hermitian[r]: right-hand side r uses the Hermitian (MINRES-DR) form of the harmonic Ritz problem.
+// defl_out (may be NULL): receives one deflation space per right-hand side.
 lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 *x, int nrhs,
-                         const lqcd_krylov_opts *o, bool hermitian, lqcd_solve_info *info, lqcd_defl **defl_out) {
+                         const lqcd_krylov_opts *o, const std::vector<char> &hermitian, lqcd_solve_info *info,
+                         std::vector<lqcd_defl *> *defl_out) {
   const double t0 = now_s();
   LQCD_TRY(check_opts(ctx, o, nrhs));
   const int m = o->m, k = o->k;
@@ -329,6 +334,7 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
   bool all_conv = false;
   std::vector<std::vector<cd>> theta_keep(nrhs);
   std::vector<Mat> P_keep(nrhs);
+  std::vector<char> rotated(nrhs, 0);
   for (int cyc = 0; cyc < o->max_cycles; ++cyc) {
     cycles = cyc + 1;
     LQCD_TRY(arnoldi_run(A, j0, R, matvecs));
@@ -359,7 +365,7 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
       std::vector<cd> th;
       Mat G;
       if (k > 0) {
-        if (!harmonic_ritz(R[r].H, k, hermitian, th, G))
+        if (!harmonic_ritz(R[r].H, k, hermitian[r] != 0, th, G))
           return set_err(ctx, LQCD_ERR_NOT_CONVERGED, "harmonic Ritz eigenproblem failed (rhs %d, cycle %d)", r, cyc);
       } else {
         G = Mat(m, 0);
@@ -395,7 +401,10 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
         cn[i] = v;
       }
       R[r].c = cn;
-      if (R[r].rel <= o->tol) R[r].active = false;
+      if (R[r].rel <= o->tol) {
+        R[r].active = false;
+        rotated[r] = 1;  // V[0..k] and H already hold this right-hand side's deflation space
+      }
     }
     j0 = k;
   }
@@ -404,46 +413,55 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
   double worst = 0.0;
   for (int r = 0; r < nrhs; ++r) worst = std::max(worst, rel[r]);
   matvecs += nrhs;
-  if (defl_out && nrhs == 1 && k > 0) {
-    lqcd_defl *d = new lqcd_defl();
-    d->ctx = ctx;
-    d->k = k;
-    d->hermitian = hermitian ? 1 : 0;
-    d->N = N;
-    d->V = d->E = nullptr;
-    d->Hbar_dev = nullptr;
-    cudaError_t e1 = cudaMalloc(&d->V, sizeof(double2) * (size_t)(k + 1) * N);
-    cudaError_t e2 = cudaMalloc(&d->E, sizeof(double2) * (size_t)k * N);
-    cudaError_t e3 = cudaMalloc(&d->Hbar_dev, sizeof(double2) * (size_t)(k + 1) * k);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
-      cudaGetLastError();
-      if (d->V) cudaFree(d->V);
-      if (d->E) cudaFree(d->E);
-      if (d->Hbar_dev) cudaFree(d->Hbar_dev);
-      delete d;
-      return set_err(ctx, LQCD_ERR_OOM, "deflation space allocation failed");
-    }
-    const Mat &P = P_keep[0];
-    std::vector<cd> pc((size_t)(m + 1) * (k + 1));
-    for (int i = 0; i <= m; ++i)
-      for (int c = 0; c <= k; ++c) pc[(size_t)i * (k + 1) + c] = P(i, c);
-    LQCD_TRY(upload(ctx, pc, W.coef));
-    LQCD_TRY(blas_combine(ctx, W.Vb, vs, N, m + 1, W.coef, k + 1, d->V, N, N, 1));
-    Mat Pk(m, k);
-    for (int i = 0; i < m; ++i)
-      for (int c = 0; c < k; ++c) Pk(i, c) = P(i, c);
-    Mat Hn = dense::matmul(dense::adjoint(P), dense::matmul(R[0].H, Pk));
-    d->Hbar.resize((size_t)(k + 1) * k);
-    std::vector<cd> hrow((size_t)(k + 1) * k);
-    for (int i = 0; i <= k; ++i)
-      for (int j = 0; j < k; ++j) {
-        d->Hbar[(size_t)i * k + j] = make_double2(Hn(i, j).real(), Hn(i, j).imag());
-        hrow[(size_t)i * k + j] = Hn(i, j);
+  if (defl_out && k > 0) {
+    for (int r = 0; r < nrhs; ++r) {
+      lqcd_defl *d = new lqcd_defl();
+      d->ctx = ctx;
+      d->k = k;
+      d->hermitian = hermitian[r] ? 1 : 0;
+      d->N = N;
+      d->V = d->E = nullptr;
+      d->Hbar_dev = nullptr;
+      cudaError_t e1 = cudaMalloc(&d->V, sizeof(double2) * (size_t)(k + 1) * N);
+      cudaError_t e2 = cudaMalloc(&d->E, sizeof(double2) * (size_t)k * N);
+      cudaError_t e3 = cudaMalloc(&d->Hbar_dev, sizeof(double2) * (size_t)(k + 1) * k);
+      if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        cudaGetLastError();
+        if (d->V) cudaFree(d->V);
+        if (d->E) cudaFree(d->E);
+        if (d->Hbar_dev) cudaFree(d->Hbar_dev);
+        delete d;
+        return set_err(ctx, LQCD_ERR_OOM, "deflation space allocation failed");
       }
-    LQCD_TRY(upload(ctx, hrow, d->Hbar_dev));
-    LQCD_TRY(ritz_pairs(ctx, d));
-    LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    *defl_out = d;
+      defl_out->push_back(d);
+      // a right-hand side that converged before the last cycle was already restarted: its space is
+      // V[0..k] with Hbar = H[0..k][0..k-1]; otherwise rotate by the final cycle's P
+      Mat P = P_keep[r];
+      Mat Hsrc = R[r].H;
+      if (rotated[r]) {
+        P = Mat(m + 1, k + 1);
+        for (int i = 0; i <= k; ++i) P(i, i) = 1.0;
+      }
+      std::vector<cd> pc((size_t)(m + 1) * (k + 1));
+      for (int i = 0; i <= m; ++i)
+        for (int c = 0; c <= k; ++c) pc[(size_t)i * (k + 1) + c] = P(i, c);
+      LQCD_TRY(upload(ctx, pc, W.coef));
+      LQCD_TRY(blas_combine(ctx, W.Vb + (long long)r * N, vs, 0, m + 1, W.coef, k + 1, d->V, N, N, 1));
+      Mat Pk(m, k);
+      for (int i = 0; i < m; ++i)
+        for (int c = 0; c < k; ++c) Pk(i, c) = P(i, c);
+      Mat Hn = dense::matmul(dense::adjoint(P), dense::matmul(Hsrc, Pk));
+      d->Hbar.resize((size_t)(k + 1) * k);
+      std::vector<cd> hrow((size_t)(k + 1) * k);
+      for (int i = 0; i <= k; ++i)
+        for (int j = 0; j < k; ++j) {
+          d->Hbar[(size_t)i * k + j] = make_double2(Hn(i, j).real(), Hn(i, j).imag());
+          hrow[(size_t)i * k + j] = Hn(i, j);
+        }
+      LQCD_TRY(upload(ctx, hrow, d->Hbar_dev));
+      LQCD_TRY(ritz_pairs(ctx, d));
+      LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
   }
   if (info) {
     info->cycles = cycles;
@@ -676,13 +694,7 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
       break;
     }
     if (outer == MAX_OUTER || inner_cycles >= o->max_cycles) break;
-    {
-      double *st;
-      LQCD_TRY(host_stage(ctx, sizeof(double) * nrhs, &st));
-      LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      memcpy(st, scale.data(), sizeof(double) * nrhs);
-      LQCD_CUDA(ctx, cudaMemcpyAsync(sc, st, sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
-    }
+    LQCD_CUDA(ctx, cudaMemcpyAsync(sc, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
     LQCD_TRY(blas_demote(ctx, r, sc, r32, N, nrhs));
     ProjResult pr;
     LQCD_TRY(proj_run<float2>(ctx, op32, V32, Hk, r32, e32, nrhs, o->m, INNER_TOL,
@@ -709,9 +721,22 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
 lqcd_status proj_core_entry(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, const double2 *b,
                             double2 *x, int nrhs, const lqcd_krylov_opts *o, lqcd_solve_info *info) {
   const int sys = defl->hermitian ? LQCD_SYS_MG5 : o->system;
-  Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, LQCD_PREC_F64};
+  Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, LQCD_PREC_F64, 0ull};
   if (o->prec == LQCD_PREC_F32) return mixed_core(ctx, op, defl, b, x, nrhs, o, info);
   return proj_core(ctx, op, defl, b, x, nrhs, o, info);
+}
+
+// The two special solves of the loop estimate in one batched run: right-hand side 0 is GMRES-DR
+// on M (its space serves GMRES-Proj), right-hand side 1 is the Hermitian form on M gamma_5 (its
+// Rayleigh-Ritz pairs serve deflation).  b2 holds the same source twice; x2 receives both solutions.
+lqcd_status special_solves(lqcd_ctx *ctx, const double *links, double kappa, const double2 *b2, double2 *x2,
+                           const lqcd_krylov_opts *o, lqcd_solve_info *info, lqcd_defl **defl_m, lqcd_defl **defl_h) {
+  Op op{(const double2 *)links, kappa, OP_MASKED, LQCD_PREC_F64, 2ull};
+  std::vector<lqcd_defl *> defls;
+  const lqcd_status st = gmresdr_core(ctx, op, b2, x2, 2, o, std::vector<char>{0, 1}, info, &defls);
+  *defl_m = defls.size() > 0 ? defls[0] : nullptr;
+  *defl_h = defls.size() > 1 ? defls[1] : nullptr;
+  return st;
 }
 
 lqcd_status gmresdr_entry(lqcd_ctx *ctx, const double *links, double kappa, const double *b, double *x, int nrhs,
@@ -721,8 +746,13 @@ lqcd_status gmresdr_entry(lqcd_ctx *ctx, const double *links, double kappa, cons
   if (defl_out) *defl_out = nullptr;
   const int sys = hermitian ? LQCD_SYS_MG5 : opts->system;
   if (sys != LQCD_SYS_M && sys != LQCD_SYS_MG5) return set_err(ctx, LQCD_ERR_INVALID_ARG, "bad system %d", sys);
-  Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, opts->prec};
-  return gmresdr_core(ctx, op, (const double2 *)b, (double2 *)x, nrhs, opts, hermitian, info, defl_out);
+  Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, opts->prec, 0ull};
+  std::vector<lqcd_defl *> defls;
+  const lqcd_status st = gmresdr_core(ctx, op, (const double2 *)b, (double2 *)x, nrhs, opts,
+                                      std::vector<char>(nrhs, hermitian ? 1 : 0), info,
+                                      (defl_out && nrhs == 1) ? &defls : nullptr);
+  if (defl_out && !defls.empty()) *defl_out = defls[0];
+  return st;
 }
 
 extern "C" {

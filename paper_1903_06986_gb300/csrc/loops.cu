@@ -647,6 +647,8 @@ lqcd_status lqcd_xi_inverse(lqcd_ctx *ctx, const double *links, double kappa, co
 }  // extern "C"
 
 // ---- whole loop estimate ----------------------------------------------------------------------
+lqcd_status special_solves(lqcd_ctx *ctx, const double *links, double kappa, const double2 *b2, double2 *x2,
+                           const lqcd_krylov_opts *o, lqcd_solve_info *info, lqcd_defl **defl_m, lqcd_defl **defl_h);
 lqcd_status proj_core_entry(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, const double2 *b,
                             double2 *x, int nrhs, const lqcd_krylov_opts *o, lqcd_solve_info *info);
 
@@ -667,7 +669,7 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
   const double t0 = now_s();
   // 1. special right-hand side: GMRES-DR on M (projection space), MINRES-DR on M' (eigenpairs)
   double2 *x0;
-  LQCD_CUDA(ctx, cudaMalloc(&x0, sizeof(double2) * (size_t)N));
+  LQCD_CUDA(ctx, cudaMalloc(&x0, sizeof(double2) * (size_t)N * 2));
   struct Guard {
     void *p;
     lqcd_defl *a, *b;
@@ -678,17 +680,15 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
     }
   } guard{x0, nullptr, nullptr};
   double2 *bs;
-  LQCD_CUDA(ctx, cudaMalloc(&bs, sizeof(double2) * (size_t)N));
+  LQCD_CUDA(ctx, cudaMalloc(&bs, sizeof(double2) * (size_t)N * 2));
   struct Guard2 { void *p; ~Guard2() { if (p) cudaFree(p); } } g2{bs};
   LQCD_TRY(noise_launch(ctx, o->seed, 0xFFFFFFFEu, 1, bs));
+  LQCD_TRY(noise_launch(ctx, o->seed, 0xFFFFFFFEu, 1, bs + N));
   lqcd_krylov_opts ko{o->m, o->k, o->tol_special, o->max_cycles, LQCD_SYS_M, LQCD_PREC_F64};
   lqcd_solve_info si{};
-  lqcd_status st = lqcd_gmresdr_solve(ctx, links, kappa, (const double *)bs, (double *)x0, 1, &ko, &si, &guard.a);
+  lqcd_status st = special_solves(ctx, links, kappa, bs, x0, &ko, &si, &guard.a, &guard.b);
   if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
   long matvecs_setup = si.matvecs;
-  st = lqcd_minresdr_solve(ctx, links, kappa, (const double *)bs, (double *)x0, 1, &ko, &si, &guard.b);
-  if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
-  matvecs_setup += si.matvecs;
   const lqcd_defl *dm = guard.a, *dh = guard.b;
   if (!dm || !dh) return set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop_estimate: no deflation space");
   const int Q = dh->k;

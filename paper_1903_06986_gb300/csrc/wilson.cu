@@ -24,15 +24,29 @@ namespace {
 
 using namespace spin;
 
-// MODE: 0 = M, 1 = M g5, 2 = M^dag = g5 M g5, 3 = P.  R: arithmetic; S: storage of spinors and
-// links (double2 with R = double or float; float2 with R = float).
+template <typename R>
+__device__ __forceinline__ void g5_inplace(Cx<R> p[4][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Cx<R> a0 = p[0][c], a1 = p[1][c];
+    p[0][c] = neg(p[2][c]);
+    p[1][c] = neg(p[3][c]);
+    p[2][c] = neg(a0);
+    p[3][c] = neg(a1);
+  }
+}
+
+// MODE: 0 = M, 1 = M g5, 2 = M^dag = g5 M g5, 3 = P, 4 = per right-hand side M or M g5 (bit r of
+// g5mask set: M g5).  R: arithmetic; S: storage of spinors and links (double2 with R = double or
+// float; float2 with R = float).
 template <typename R, int MODE, typename S>
 __global__ void __launch_bounds__(128) wilson_kernel(const S *__restrict__ U, const S *__restrict__ in,
                                                      S *__restrict__ out, double kappa, int Lx, int Ly,
-                                                     int Lz, int Lt, int V) {
+                                                     int Lz, int Lt, int V, unsigned long long g5mask) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
   constexpr bool G5IN = (MODE == 1 || MODE == 2);
+  const bool g5rt = (MODE == 4) && ((g5mask >> blockIdx.y) & 1ull);
   const long long base = (long long)blockIdx.y * V * 12;
   const S *src = in + base;
   int x = s % Lx;
@@ -58,14 +72,14 @@ __global__ void __launch_bounds__(128) wilson_kernel(const S *__restrict__ U, co
     for (int c = 0; c < 3; ++c) acc[a][c] = mk<R>(0, 0);
   Cx<R> p[4][3], u[9];
   const long long V4 = V;
-  load_spinor<R, G5IN>(src + 12LL * xp, p); load_link<R>(U, 0 * V4 + s, u);  term_fwd<R, 0>(p, u, acc);
-  load_spinor<R, G5IN>(src + 12LL * xm, p); load_link<R>(U, 0 * V4 + xm, u); term_bwd<R, 0>(p, u, acc);
-  load_spinor<R, G5IN>(src + 12LL * yp, p); load_link<R>(U, 1 * V4 + s, u);  term_fwd<R, 1>(p, u, acc);
-  load_spinor<R, G5IN>(src + 12LL * ym, p); load_link<R>(U, 1 * V4 + ym, u); term_bwd<R, 1>(p, u, acc);
-  load_spinor<R, G5IN>(src + 12LL * zp, p); load_link<R>(U, 2 * V4 + s, u);  term_fwd<R, 2>(p, u, acc);
-  load_spinor<R, G5IN>(src + 12LL * zm, p); load_link<R>(U, 2 * V4 + zm, u); term_bwd<R, 2>(p, u, acc);
-  load_spinor<R, G5IN>(src + 12LL * tp, p); load_link<R>(U, 3 * V4 + s, u);  term_fwd<R, 3>(p, u, acc);
-  load_spinor<R, G5IN>(src + 12LL * tm, p); load_link<R>(U, 3 * V4 + tm, u); term_bwd<R, 3>(p, u, acc);
+  load_spinor<R, G5IN>(src + 12LL * xp, p); if (g5rt) g5_inplace(p); load_link<R>(U, 0 * V4 + s, u); term_fwd<R, 0>(p, u, acc);
+  load_spinor<R, G5IN>(src + 12LL * xm, p); if (g5rt) g5_inplace(p); load_link<R>(U, 0 * V4 + xm, u); term_bwd<R, 0>(p, u, acc);
+  load_spinor<R, G5IN>(src + 12LL * yp, p); if (g5rt) g5_inplace(p); load_link<R>(U, 1 * V4 + s, u); term_fwd<R, 1>(p, u, acc);
+  load_spinor<R, G5IN>(src + 12LL * ym, p); if (g5rt) g5_inplace(p); load_link<R>(U, 1 * V4 + ym, u); term_bwd<R, 1>(p, u, acc);
+  load_spinor<R, G5IN>(src + 12LL * zp, p); if (g5rt) g5_inplace(p); load_link<R>(U, 2 * V4 + s, u); term_fwd<R, 2>(p, u, acc);
+  load_spinor<R, G5IN>(src + 12LL * zm, p); if (g5rt) g5_inplace(p); load_link<R>(U, 2 * V4 + zm, u); term_bwd<R, 2>(p, u, acc);
+  load_spinor<R, G5IN>(src + 12LL * tp, p); if (g5rt) g5_inplace(p); load_link<R>(U, 3 * V4 + s, u); term_fwd<R, 3>(p, u, acc);
+  load_spinor<R, G5IN>(src + 12LL * tm, p); if (g5rt) g5_inplace(p); load_link<R>(U, 3 * V4 + tm, u); term_bwd<R, 3>(p, u, acc);
 
   S *dst = out + base + 12LL * s;
   if (MODE == 3) {
@@ -76,6 +90,7 @@ __global__ void __launch_bounds__(128) wilson_kernel(const S *__restrict__ U, co
     return;
   }
   load_spinor<R, G5IN>(src + 12LL * s, p);
+  if (g5rt) g5_inplace(p);
   const R k = (R)kappa;
   Cx<R> o[4][3];
 #pragma unroll
@@ -99,16 +114,22 @@ __global__ void __launch_bounds__(128) wilson_kernel(const S *__restrict__ U, co
 }
 
 template <typename R, typename S>
-lqcd_status launch_mode(lqcd_ctx *ctx, const S *U, double kappa, const S *in, S *out, int nrhs, int flags) {
-  dim3 block(128);
-  dim3 grid(ceil_div(ctx->V, 128), nrhs);
+lqcd_status launch_mode(lqcd_ctx *ctx, const S *U, double kappa, const S *in, S *out, int nrhs, int flags,
+                        unsigned long long g5mask = 0) {
+  // 128 threads per block unless that leaves fewer than two blocks per SM (few right-hand sides on
+  // a small lattice): then smaller blocks spread the sites over more SMs
+  int bs = 128;
+  while (bs > 32 && (long long)ceil_div(ctx->V, bs) * nrhs < 2LL * ctx->sms) bs /= 2;
+  dim3 block(bs);
+  dim3 grid(ceil_div(ctx->V, bs), nrhs);
   const int *d = ctx->dims;
   kbegin(ctx);
   switch (flags) {
-    case LQCD_APPLY_M: wilson_kernel<R, 0, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
-    case LQCD_APPLY_G5R: wilson_kernel<R, 1, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
-    case LQCD_APPLY_DAG: wilson_kernel<R, 2, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
-    case LQCD_APPLY_HOP: wilson_kernel<R, 3, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V); break;
+    case LQCD_APPLY_M: wilson_kernel<R, 0, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V, 0ull); break;
+    case LQCD_APPLY_G5R: wilson_kernel<R, 1, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V, 0ull); break;
+    case LQCD_APPLY_DAG: wilson_kernel<R, 2, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V, 0ull); break;
+    case LQCD_APPLY_HOP: wilson_kernel<R, 3, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V, 0ull); break;
+    case 4: wilson_kernel<R, 4, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V, g5mask); break;
     default: return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply: unknown flags %d", flags);
   }
   return launch_check(ctx, "wilson_kernel", K_WILSON, (double)ctx->V * nrhs);
@@ -122,6 +143,12 @@ lqcd_status wilson_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const d
   if (prec == LQCD_PREC_F64) return launch_mode<double, double2>(ctx, U, kappa, in, out, nrhs, flags);
   if (prec == LQCD_PREC_F32) return launch_mode<float, double2>(ctx, U, kappa, in, out, nrhs, flags);
   return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply: unknown precision %d", prec);
+}
+
+lqcd_status wilson_launch_masked(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in, double2 *out,
+                                 int nrhs, unsigned long long g5mask) {
+  if (nrhs <= 0 || nrhs > 64) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson (masked): nrhs %d out of range", nrhs);
+  return launch_mode<double, double2>(ctx, U, kappa, in, out, nrhs, 4, g5mask);
 }
 
 lqcd_status wilson_launch_f32(lqcd_ctx *ctx, const float2 *U, double kappa, const float2 *in, float2 *out, int nrhs,
