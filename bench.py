@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--case", default=None, choices=["gmres-cycle", "gmres-cycle-f32"],
+                    help="run one small kernel case for profiling instead of the benchmark: one GMRES(30) "
+                         "cycle on 50 noises of the 8^3x16 workload (FP64, or FP32 storage)")
     return ap.parse_args()
 
 
@@ -204,10 +207,30 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def run_case(args):
+    """Small fixed workload for ncu captures of the solver kernels (no timing output)."""
+    import torch
+    from paper_1903_06986_gb300 import build, lqcd, synth
+    build.build()
+    U = torch.from_numpy(synth.su3_links(DIMS, 0.4323, LINK_SEED)).cuda()
+    ctx = lqcd.Context(DIMS)
+    etas = ctx.noise_z4(NOISE_SEED, 0, NNOISE)
+    if args.case == "gmres-cycle":
+        x, info, _ = ctx.gmresdr_solve(U, KAPPAS[-1], etas, M_DR - K_DR, 0, 1e-30, 1)
+    else:
+        _, _, defl = ctx.gmresdr_solve(U, KAPPAS[-1], etas[:1].contiguous(), M_DR - K_DR, 4, 1e-3, 5,
+                                       want_defl=True)
+        x, info = ctx.proj_solve(U, KAPPAS[-1], defl, etas, M_DR - K_DR, 1e-6, 1, prec=1)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "matvecs": info["matvecs"], "launches": ctx.launches}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
