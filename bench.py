@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--case", default=None, choices=["gmres-cycle", "gmres-cycle-f32"],
                     help="run one small kernel case for profiling instead of the benchmark: one GMRES(30) "
                          "cycle on 50 noises of the 8^3x16 workload (FP64, or FP32 storage)")
@@ -207,6 +208,52 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+DSLASH_DIMS = (24, 24, 24, 32)   # the paper's large lattice (Sec. 7); fields exceed L2 at nrhs >= 2
+HBM_PEAK_GBS = 6793.4            # measured copy bandwidth of this GB300 pool
+
+
+def dslash_rates(torch):
+    """Wilson operator throughput on the 24^3x32 lattice: FP64 (the plain path) and FP32 storage (the
+    inner operator of mixed precision).  Algorithmic bytes per launch: nrhs x V x 24 complex (one
+    spinor read, one written) plus the links once (4 x 9 complex per site); flops 1368 per site and
+    right-hand side.  CUDA events on the library stream, 2 warm-up and 5 timed launches."""
+    from paper_1903_06986_gb300 import lqcd, synth
+    ctx = lqcd.Context(DSLASH_DIMS)
+    V = int(np.prod(DSLASH_DIMS))
+    U = torch.from_numpy(synth.su3_links(DSLASH_DIMS, 0.4323, 7)).cuda()
+    U32 = ctx.to_f32(U)
+    out = {}
+    for prec, nrhs in (("f64", 1), ("f64", 8), ("f32", 1), ("f32", 8), ("f32", 16)):
+        x = ctx.noise_z4(3, 0, nrhs)
+        if prec == "f32":
+            x = ctx.to_f32(x)
+            fn = lambda: ctx.wilson_apply_f32(U32, 0.157, x, y)
+            w = 8
+        else:
+            fn = lambda: ctx.wilson_apply(U, 0.157, x, y)
+            w = 16
+        y = torch.empty_like(x)
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 5 / 1000.0
+        nbytes = nrhs * V * 24 * w + V * 36 * w
+        gbs = nbytes / t / 1e9
+        tf = 1368.0 * V * nrhs / t / 1e12
+        out["%s_rhs%d" % (prec, nrhs)] = {"ms": round(t * 1e3, 4), "GB/s": round(gbs, 1), "TFLOP/s": round(tf, 4),
+                                          "frac_hbm": round(gbs / HBM_PEAK_GBS, 4),
+                                          "frac_fp64": round(tf / FP64_PEAK_TFLOPS, 4) if prec == "f64" else None}
+        del x, y
+    ctx.close()
+    return {"lattice": "24x24x24x32", "bytes": "nrhs*V*24 complex + links once", "results": out}
+
+
 def run_case(args):
     """Small fixed workload for ncu captures of the solver kernels (no timing output)."""
     import torch
@@ -363,6 +410,8 @@ def main():
     if w[0] > 0:
         roofline["wilson_fp64_tflops"] = w[2] * WILSON_FLOPS / (w[0] / 1000.0) / 1e12
 
+    dslash = None if args.no_dslash else dslash_rates(torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, sample, _ = oracle_sample(U)
@@ -385,7 +434,7 @@ def main():
                 "roofline": roofline,
                 "e2e": {"value": e2e_value, "unit": "estimates/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
-                "clocks": clk, "cpu_baseline": cpu, "mixed_precision": mixed}
+                "clocks": clk, "cpu_baseline": cpu, "mixed_precision": mixed, "dslash": dslash}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

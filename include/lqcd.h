@@ -138,6 +138,14 @@ lqcd_status lqcd_noise_z4(lqcd_ctx *ctx, uint64_t seed, uint32_t first_noise, in
 lqcd_status lqcd_wilson_apply(lqcd_ctx *ctx, const double *links, double kappa, const double *in,
                               double *out, int nrhs, int prec, int flags);
 
+/* The inner operator of the mixed-precision solver: the same operator on FP32 storage with FP32
+ * arithmetic.  links32: device gauge field as interleaved float pairs, same layout as the FP64
+ * links; in/out: device, nrhs * 12 V float pairs, must not overlap.  flags as above. */
+lqcd_status lqcd_wilson_apply_f32(lqcd_ctx *ctx, const float *links32, double kappa, const float *in, float *out,
+                                  int nrhs, int flags);
+/* Convert n complex numbers from FP64 to FP32 storage on the device (e.g. links for the call above). */
+lqcd_status lqcd_to_f32(lqcd_ctx *ctx, const double *in, float *out, long long n);
+
 /* ---- a3 / a4: GMRES-DR and MINRES-DR (Sec. 5.3, 7, 8) --------------------------------- */
 
 /* GMRES-DR(m, k) for nrhs independent right-hand sides (each with its own Krylov basis).

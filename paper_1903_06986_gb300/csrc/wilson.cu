@@ -164,3 +164,18 @@ extern "C" lqcd_status lqcd_wilson_apply(lqcd_ctx *ctx, const double *links, dou
   if (in == out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply: in and out must not overlap");
   return wilson_launch(ctx, (const double2 *)links, kappa, (const double2 *)in, (double2 *)out, nrhs, prec, flags);
 }
+
+extern "C" lqcd_status lqcd_wilson_apply_f32(lqcd_ctx *ctx, const float *links32, double kappa, const float *in,
+                                             float *out, int nrhs, int flags) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links32 || !in || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_f32: NULL pointer");
+  if (in == out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_f32: in and out must not overlap");
+  if (flags < 0 || flags > 3) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_f32: unknown flags %d", flags);
+  return wilson_launch_f32(ctx, (const float2 *)links32, kappa, (const float2 *)in, (float2 *)out, nrhs, flags);
+}
+
+extern "C" lqcd_status lqcd_to_f32(lqcd_ctx *ctx, const double *in, float *out, long long n) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!in || !out || n < 0) return set_err(ctx, LQCD_ERR_INVALID_ARG, "to_f32: bad arguments");
+  return blas_to_f32(ctx, (const double2 *)in, (float2 *)out, n);
+}

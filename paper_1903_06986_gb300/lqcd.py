@@ -83,6 +83,8 @@ def load(path=None):
         "lqcd_set_stream": [vp, vp],
         "lqcd_noise_z4": [vp, u64, u32, i, vp],
         "lqcd_wilson_apply": [vp, vp, d, vp, vp, i, i, i],
+        "lqcd_wilson_apply_f32": [vp, vp, d, vp, vp, i, i],
+        "lqcd_to_f32": [vp, vp, vp, C.c_longlong],
         "lqcd_gmresdr_solve": [vp, vp, d, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo), C.POINTER(vp)],
         "lqcd_minresdr_solve": [vp, vp, d, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo), C.POINTER(vp)],
         "lqcd_proj_solve": [vp, vp, d, vp, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo)],
@@ -124,14 +126,15 @@ def _torch():
     return torch
 
 
-def _ptr(t):
+def _ptr(t, dtype=None):
     if t is None:
         return None
     torch = _torch()
     if not isinstance(t, torch.Tensor):
         raise TypeError("expected a torch tensor")
-    if not t.is_cuda or t.dtype != torch.complex128 or not t.is_contiguous():
-        raise ValueError("tensors must be contiguous complex128 CUDA tensors")
+    want = torch.complex128 if dtype is None else dtype
+    if not t.is_cuda or t.dtype != want or not t.is_contiguous():
+        raise ValueError("tensors must be contiguous %s CUDA tensors" % want)
     return C.c_void_p(t.data_ptr())
 
 
@@ -259,6 +262,19 @@ class Context:
         out = _torch().empty_like(inp) if out is None else out
         self._check(self.lib.lqcd_wilson_apply(self.h, _ptr(links), kappa, _ptr(inp), _ptr(out),
                                                self._nrhs(inp), prec, flags))
+        return out
+
+    def to_f32(self, t):
+        """complex128 device tensor -> complex64 copy (FP32 storage), converted on the device."""
+        out = _torch().empty(t.shape, dtype=_torch().complex64, device=self.device)
+        self._check(self.lib.lqcd_to_f32(self.h, _ptr(t), _ptr(out, _torch().complex64), t.numel()))
+        return out
+
+    def wilson_apply_f32(self, links32, kappa, inp, out=None, flags=APPLY_M):
+        c64 = _torch().complex64
+        out = _torch().empty_like(inp) if out is None else out
+        self._check(self.lib.lqcd_wilson_apply_f32(self.h, _ptr(links32, c64), kappa, _ptr(inp, c64),
+                                                   _ptr(out, c64), inp.numel() // self.N, flags))
         return out
 
     # a3 / a4

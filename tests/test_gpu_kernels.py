@@ -43,9 +43,13 @@ def test_wilson_all_forms(dims):
     for flag, ref in forms.items():
         got = host(ctx.wilson_apply(Ud, kappa, pd, flags=flag))
         assert rel_err(got, ref(psi)) < FP64_TOL, flag
-    # FP32 arithmetic on the same data (the inner operator of mixed precision)
+    # FP32 arithmetic on the same data, and FP32 storage (the inner operator of mixed precision)
     got = host(ctx.wilson_apply(Ud, kappa, pd, flags=0, prec=1))
     assert rel_err(got, forms[0](psi)) < 2e-6
+    U32, p32 = ctx.to_f32(Ud), ctx.to_f32(pd)
+    for flag, ref in forms.items():
+        got = host(ctx.wilson_apply_f32(U32, kappa, p32, flags=flag))
+        assert rel_err(got, ref(psi)) < 2e-6, flag
 
 
 @pytest.mark.parametrize("dims", DIMS[:3])
