@@ -213,26 +213,31 @@ HBM_PEAK_GBS = 6793.4            # measured copy bandwidth of this GB300 pool
 
 
 def dslash_rates(torch):
-    """Wilson operator throughput on the 24^3x32 lattice: FP64 (the plain path) and FP32 storage (the
-    inner operator of mixed precision).  Algorithmic bytes per launch: nrhs x V x 24 complex (one
-    spinor read, one written) plus the links once (4 x 9 complex per site); flops 1368 per site and
-    right-hand side.  CUDA events on the library stream, 2 warm-up and 5 timed launches."""
+    """Wilson operator throughput on the 24^3x32 lattice: the FP64 operator of the plain path
+    (canonical layout) and the packed FP32 operator of the mixed-precision inner solver (recon 12 and
+    18 links).  Algorithmic bytes per launch: each spinor read once and written once (nrhs x V x 24
+    reals) plus the links once (4 x V x 18 or 12 reals); flops 1368 per site and right-hand side.
+    CUDA events on the library stream, 2 warm-up and 5 timed launches; fields exceed L2 for nrhs > 1."""
     from paper_1903_06986_gb300 import lqcd, synth
-    ctx = lqcd.Context(DSLASH_DIMS)
+    ctx = lqcd.Context(DSLASH_DIMS, recon=12)
     V = int(np.prod(DSLASH_DIMS))
     U = torch.from_numpy(synth.su3_links(DSLASH_DIMS, 0.4323, 7)).cuda()
-    U32 = ctx.to_f32(U)
+    packed_links = {12: ctx.pack_links_f32(U, 12), 18: ctx.pack_links_f32(U, 18)}
     out = {}
-    for prec, nrhs in (("f64", 1), ("f64", 8), ("f32", 1), ("f32", 8), ("f32", 16)):
+    cases = [("f64", 18, 1), ("f64", 18, 8), ("f32packed", 12, 1), ("f32packed", 12, 8), ("f32packed", 12, 16),
+             ("f32packed", 18, 8)]
+    for prec, recon, nrhs in cases:
         x = ctx.noise_z4(3, 0, nrhs)
-        if prec == "f32":
-            x = ctx.to_f32(x)
-            fn = lambda: ctx.wilson_apply_f32(U32, 0.157, x, y)
-            w = 8
-        else:
+        if prec == "f64":
+            y = torch.empty_like(x)
             fn = lambda: ctx.wilson_apply(U, 0.157, x, y)
-            w = 16
-        y = torch.empty_like(x)
+            w, lreals = 8, 18
+        else:
+            x = ctx.pack_f32(x)
+            y = torch.empty_like(x)
+            Up = packed_links[recon]
+            fn = lambda: ctx.wilson_apply_packed(Up, recon, 0.157, x, y)
+            w, lreals = 4, recon
         for _ in range(2):
             fn()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -243,15 +248,17 @@ def dslash_rates(torch):
         e1.record()
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 5 / 1000.0
-        nbytes = nrhs * V * 24 * w + V * 36 * w
+        nbytes = nrhs * V * 48 * w + V * 4 * lreals * w
         gbs = nbytes / t / 1e9
         tf = 1368.0 * V * nrhs / t / 1e12
-        out["%s_rhs%d" % (prec, nrhs)] = {"ms": round(t * 1e3, 4), "GB/s": round(gbs, 1), "TFLOP/s": round(tf, 4),
-                                          "frac_hbm": round(gbs / HBM_PEAK_GBS, 4),
-                                          "frac_fp64": round(tf / FP64_PEAK_TFLOPS, 4) if prec == "f64" else None}
+        out["%s_recon%d_rhs%d" % (prec, recon, nrhs)] = {
+            "ms": round(t * 1e3, 4), "GB/s": round(gbs, 1), "TFLOP/s": round(tf, 4),
+            "frac_hbm": round(gbs / HBM_PEAK_GBS, 4),
+            "frac_fp64": round(tf / FP64_PEAK_TFLOPS, 4) if prec == "f64" else None}
         del x, y
     ctx.close()
-    return {"lattice": "24x24x24x32", "bytes": "nrhs*V*24 complex + links once", "results": out}
+    return {"lattice": "24x24x24x32", "bytes": "nrhs*V*24 reals read+written + links once",
+            "hbm_peak_gbs": HBM_PEAK_GBS, "results": out}
 
 
 def run_case(args):
@@ -290,7 +297,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     U, eps = make_links(rank)
-    ctx = lqcd.Context(DIMS)
+    ctx = lqcd.Context(DIMS, recon=12)     # the synthetic links are SU(3)
     Ud = torch.from_numpy(U).cuda()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stats = []

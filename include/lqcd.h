@@ -89,9 +89,11 @@ typedef struct {
 /* ---- context --------------------------------------------------------------------------- */
 
 /* Create a context for an Lx x Ly x Lz x Lt lattice (dims[0..3] = Lx, Ly, Lz, Lt, each >= 2) on
- * the current CUDA device.  link_recon must be 18 (full links).  stream is a cudaStream_t (NULL
- * = legacy default stream).  Returns LQCD_ERR_INVALID_ARG for bad dims, LQCD_ERR_CUDA if no
- * device is usable. */
+ * the current CUDA device.  link_recon is 18 (general links) or 12 (the caller declares the links
+ * special unitary: the FP32 inner operator of the mixed-precision solver then stores two rows per
+ * link and rebuilds the third; FP64 operators always read all nine entries).  stream is a
+ * cudaStream_t (NULL = legacy default stream).  Returns LQCD_ERR_INVALID_ARG for bad dims or
+ * link_recon, LQCD_ERR_CUDA if no device is usable. */
 lqcd_status lqcd_ctx_create(lqcd_ctx **ctx, const int dims[4], int link_recon, void *stream);
 lqcd_status lqcd_ctx_destroy(lqcd_ctx *ctx);
 lqcd_status lqcd_set_stream(lqcd_ctx *ctx, void *stream);
@@ -145,6 +147,21 @@ lqcd_status lqcd_wilson_apply_f32(lqcd_ctx *ctx, const float *links32, double ka
                                   int nrhs, int flags);
 /* Convert n complex numbers from FP64 to FP32 storage on the device (e.g. links for the call above). */
 lqcd_status lqcd_to_f32(lqcd_ctx *ctx, const double *in, float *out, long long n);
+
+/* Packed FP32 layout of the mixed-precision inner solver: per right-hand side, the 24 reals of a
+ * site form six float4 chunks (chunk q = complex components 2q, 2q+1 of the canonical spin-colour
+ * order), stored chunk-major: float4 (r, q, s) at index (r * 6 + q) * V + s.  Packed links: per
+ * direction, recon 12 stores rows 0 and 1 as three float4 chunks ((u00,u01), (u02,u10), (u11,u12))
+ * and rebuilds row 2 = conj(row0 x row1) (exact for SU(3) links); recon 18 stores all nine entries
+ * in five float4 chunks (last half zero).  Buffers: packed fields nrhs * 24 V floats, packed links
+ * 4 * 12 V (recon 12) or 4 * 20 V (recon 18) floats, device. */
+lqcd_status lqcd_pack_f32(lqcd_ctx *ctx, const double *in, float *out, int nrhs);
+lqcd_status lqcd_unpack_f32(lqcd_ctx *ctx, const float *in, double *out, int nrhs);
+lqcd_status lqcd_pack_links_f32(lqcd_ctx *ctx, const double *links, float *out, int recon);
+/* Packed FP32 operator (flags as lqcd_wilson_apply): one thread per site and rhs_per_thread
+ * right-hand sides (1, 2 or 4; 0 = automatic), so a link is read once per rhs_per_thread fields. */
+lqcd_status lqcd_wilson_apply_packed(lqcd_ctx *ctx, const float *links_packed, int recon, double kappa,
+                                     const float *in, float *out, int nrhs, int flags, int rhs_per_thread);
 
 /* ---- a3 / a4: GMRES-DR and MINRES-DR (Sec. 5.3, 7, 8) --------------------------------- */
 

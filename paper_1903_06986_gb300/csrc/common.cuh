@@ -23,6 +23,7 @@ struct lqcd_ctx {
   int V;                // sites
   long long N;          // complex unknowns per field, 12 V
   int device;
+  int recon;            // 12 or 18: link storage of the packed FP32 inner operator
   int sms;
   cudaStream_t stream;
   std::string err;
@@ -143,6 +144,13 @@ lqcd_status wilson_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const d
 // FP64, right-hand side r gets M gamma_5 when bit r of g5mask is set and M otherwise (nrhs <= 64)
 lqcd_status wilson_launch_masked(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in, double2 *out,
                                  int nrhs, unsigned long long g5mask);
+// Packed FP32 operator (layout in wilson.cu): links packed by pack_links_f32 (recon 12 or 18),
+// nr right-hand sides per thread (0 = automatic)
+lqcd_status wilson_launch_packed(lqcd_ctx *ctx, const float4 *U, int recon, double kappa, const float4 *in, float4 *out,
+                                 int nrhs, int flags, int nr);
+lqcd_status pack_f32(lqcd_ctx *ctx, const double2 *x, const double *scale, float4 *y, int nrhs);
+lqcd_status unpack_f32(lqcd_ctx *ctx, const float4 *c, const double *scale, double2 *x, int nrhs);
+lqcd_status pack_links_f32(lqcd_ctx *ctx, const double2 *U, float4 *P, int recon);
 // FP32 storage and arithmetic (links converted to FP32 by the caller)
 lqcd_status wilson_launch_f32(lqcd_ctx *ctx, const float2 *U, double kappa, const float2 *in, float2 *out,
                               int nrhs, int flags);

@@ -126,7 +126,7 @@ lqcd_status lqcd_ctx_create(lqcd_ctx **out, const int dims[4], int link_recon, v
   *out = nullptr;
   for (int i = 0; i < 4; ++i)
     if (dims[i] < 2 || dims[i] > 1024) return LQCD_ERR_INVALID_ARG;
-  if (link_recon != 18) return LQCD_ERR_INVALID_ARG;
+  if (link_recon != 18 && link_recon != 12) return LQCD_ERR_INVALID_ARG;
   long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
   if (V > (1LL << 28)) return LQCD_ERR_INVALID_ARG;
   int dev = 0;
@@ -138,6 +138,7 @@ lqcd_status lqcd_ctx_create(lqcd_ctx **out, const int dims[4], int link_recon, v
   c->V = (int)V;
   c->N = 12 * V;
   c->device = dev;
+  c->recon = link_recon;
   c->sms = prop.multiProcessorCount;
   c->stream = (cudaStream_t)stream;
   c->launches = 0;

@@ -45,12 +45,15 @@ template <> struct OpT<double2> {
     return wilson_launch(ctx, U, kappa, in, out, nrhs, prec, flags);
   }
 };
+// FP32 fields of the inner solver are in the packed layout (see wilson.cu); the level-1/2 kernels
+// treat them as plain float2 arrays of the same length, which is all they need.
 template <> struct OpT<float2> {
-  const float2 *U;
+  const float4 *U;  // packed links
+  int recon;
   double kappa;
   int flags;
   lqcd_status apply(lqcd_ctx *ctx, const float2 *in, float2 *out, int nrhs) const {
-    return wilson_launch_f32(ctx, U, kappa, in, out, nrhs, flags);
+    return wilson_launch_packed(ctx, U, recon, kappa, (const float4 *)in, (float4 *)out, nrhs, flags, 0);
   }
 };
 using Op = OpT<double2>;
@@ -656,18 +659,20 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
   if (!defl || !defl->V || !defl->Hbar_dev) return set_err(ctx, LQCD_ERR_INVALID_ARG, "GMRES-Proj needs a solver-made deflation space");
   const long long N = ctx->N, vs = (long long)nrhs * N;
   const int k = defl->k;
-  float2 *U32, *V32, *r32, *e32;
+  float2 *V32, *r32, *e32;
+  float4 *U32;
   double2 *r;
   double *sc;
-  LQCD_TRY(ws_get(ctx, WS_MIX_U, sizeof(float2) * (size_t)ctx->V * 36, (void **)&U32));
+  const int recon = ctx->recon;
+  LQCD_TRY(ws_get(ctx, WS_MIX_U, sizeof(float) * (size_t)ctx->V * 4 * (recon == 12 ? 12 : 20), (void **)&U32));
   LQCD_TRY(ws_get(ctx, WS_MIX_V, sizeof(float2) * (size_t)(k + 1) * N, (void **)&V32));
   LQCD_TRY(ws_get(ctx, WS_MIX_R32, sizeof(float2) * (size_t)vs, (void **)&r32));
   LQCD_TRY(ws_get(ctx, WS_MIX_E32, sizeof(float2) * (size_t)vs, (void **)&e32));
   LQCD_TRY(ws_get(ctx, WS_MIX_R, sizeof(double2) * (size_t)vs, (void **)&r));
   LQCD_TRY(ws_get(ctx, WS_MIX_S, sizeof(double) * (size_t)nrhs, (void **)&sc));
-  LQCD_TRY(blas_to_f32(ctx, op.U, U32, (long long)ctx->V * 36));
-  LQCD_TRY(blas_to_f32(ctx, defl->V, V32, (long long)(k + 1) * N));
-  const OpT<float2> op32{U32, op.kappa, op.flags};
+  LQCD_TRY(pack_links_f32(ctx, op.U, U32, recon));
+  LQCD_TRY(pack_f32(ctx, defl->V, nullptr, (float4 *)V32, k + 1));
+  const OpT<float2> op32{U32, recon, op.kappa, op.flags};
   const Mat Hk = defl_hbar(defl);
   LQCD_TRY(blas_zero(ctx, x, vs));
   LQCD_TRY(blas_copy(ctx, b, r, vs));
@@ -695,13 +700,13 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
     }
     if (outer == MAX_OUTER || inner_cycles >= o->max_cycles) break;
     LQCD_CUDA(ctx, cudaMemcpyAsync(sc, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
-    LQCD_TRY(blas_demote(ctx, r, sc, r32, N, nrhs));
+    LQCD_TRY(pack_f32(ctx, r, sc, (float4 *)r32, nrhs));
     ProjResult pr;
     LQCD_TRY(proj_run<float2>(ctx, op32, V32, Hk, r32, e32, nrhs, o->m, INNER_TOL,
                               std::max(1, o->max_cycles - inner_cycles), false, pr));
     inner_cycles += pr.cycles;
     matvecs += pr.matvecs;
-    LQCD_TRY(blas_promote_acc(ctx, e32, sc, x, N, nrhs));
+    LQCD_TRY(unpack_f32(ctx, (const float4 *)e32, sc, x, nrhs));
     // FP64 true residual r = b - M x
     LQCD_TRY(op.apply(ctx, x, r, nrhs));
     LQCD_TRY(blas_bminus(ctx, r, b, vs));

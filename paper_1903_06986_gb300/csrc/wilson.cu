@@ -179,3 +179,297 @@ extern "C" lqcd_status lqcd_to_f32(lqcd_ctx *ctx, const double *in, float *out, 
   if (!in || !out || n < 0) return set_err(ctx, LQCD_ERR_INVALID_ARG, "to_f32: bad arguments");
   return blas_to_f32(ctx, (const double2 *)in, (float2 *)out, n);
 }
+
+// ---- packed FP32 operator (the inner operator of mixed precision) ---------------------------------
+// Packed layout of FP32 fields: the 24 reals of a site (canonical order spin, colour, re/im) are six
+// float4 chunks, chunk q holding complex components 2q and 2q+1, stored chunk-major per right-hand
+// side: element (r, q, s) at [(r * 6 + q) * V + s].  A warp of consecutive sites then reads 512
+// contiguous bytes per chunk.  Links are packed per direction the same way: with RECON = 12 only
+// rows 0 and 1 are stored (three float4: (u00,u01), (u02,u10), (u11,u12)) and row 2 is rebuilt as
+// conj(row0 x row1), exact for SU(3); with RECON = 18 all nine entries are stored in five float4
+// (the last half padded).  One thread owns one site for NR right-hand sides, so every link is
+// loaded once per NR right-hand sides.
+namespace {
+
+using namespace spin;
+
+template <int RECON>
+__device__ __forceinline__ void load_link_packed(const float4 *__restrict__ U, int mu, int V, int s, Cx<float> u[9]) {
+  constexpr int NC = RECON == 12 ? 3 : 5;
+  const float4 *p = U + (long long)mu * NC * V + s;
+  const float4 a = __ldg(p), b = __ldg(p + V), c = __ldg(p + 2LL * V);
+  u[0] = mk<float>(a.x, a.y); u[1] = mk<float>(a.z, a.w);
+  u[2] = mk<float>(b.x, b.y); u[3] = mk<float>(b.z, b.w);
+  u[4] = mk<float>(c.x, c.y); u[5] = mk<float>(c.z, c.w);
+  if (RECON == 12) {
+    // row 2 = conj(row0 x row1)
+    auto cm = [](Cx<float> x, Cx<float> y) { return mk<float>(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); };
+    Cx<float> t;
+    t = cm(u[1], u[5]) - cm(u[2], u[4]); u[6] = mk<float>(t.x, -t.y);
+    t = cm(u[2], u[3]) - cm(u[0], u[5]); u[7] = mk<float>(t.x, -t.y);
+    t = cm(u[0], u[4]) - cm(u[1], u[3]); u[8] = mk<float>(t.x, -t.y);
+  } else {
+    const float4 d = __ldg(p + 3LL * V), e = __ldg(p + 4LL * V);
+    u[6] = mk<float>(d.x, d.y); u[7] = mk<float>(d.z, d.w);
+    u[8] = mk<float>(e.x, e.y);
+  }
+}
+
+__device__ __forceinline__ void load_spinor_packed(const float4 *__restrict__ p, int V, Cx<float> s[4][3]) {
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float4 v = __ldg(p + (long long)q * V);
+    const int c0 = 2 * q, c1 = 2 * q + 1;
+    s[c0 / 3][c0 % 3] = mk<float>(v.x, v.y);
+    s[c1 / 3][c1 % 3] = mk<float>(v.z, v.w);
+  }
+}
+
+__device__ __forceinline__ void store_spinor_packed(float4 *__restrict__ p, int V, const Cx<float> s[4][3]) {
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const int c0 = 2 * q, c1 = 2 * q + 1;
+    p[(long long)q * V] = make_float4(s[c0 / 3][c0 % 3].x, s[c0 / 3][c0 % 3].y, s[c1 / 3][c1 % 3].x, s[c1 / 3][c1 % 3].y);
+  }
+}
+
+template <int NR, int RECON, int MODE>
+__global__ void __launch_bounds__(128) wilson_packed_kernel(const float4 *__restrict__ U, const float4 *__restrict__ in,
+                                                            float4 *__restrict__ out, float kappa, int Lx, int Ly,
+                                                            int Lz, int Lt, int V, int nrhs) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const int r0 = blockIdx.y * NR;
+  const int nr = min(NR, nrhs - r0);
+  constexpr bool G5IN = (MODE == 1 || MODE == 2);
+  int x = s % Lx, rr = s / Lx;
+  int y = rr % Ly;
+  rr /= Ly;
+  int z = rr % Lz;
+  int t = rr / Lz;
+  const int sy = Lx, sz = Lx * Ly, st = Lx * Ly * Lz;
+  int nb[8];
+  nb[0] = (x + 1 == Lx) ? s - (Lx - 1) : s + 1;
+  nb[1] = (x == 0) ? s + (Lx - 1) : s - 1;
+  nb[2] = (y + 1 == Ly) ? s - (Ly - 1) * sy : s + sy;
+  nb[3] = (y == 0) ? s + (Ly - 1) * sy : s - sy;
+  nb[4] = (z + 1 == Lz) ? s - (Lz - 1) * sz : s + sz;
+  nb[5] = (z == 0) ? s + (Lz - 1) * sz : s - sz;
+  nb[6] = (t + 1 == Lt) ? s - (Lt - 1) * st : s + st;
+  nb[7] = (t == 0) ? s + (Lt - 1) * st : s - st;
+  Cx<float> acc[NR][4][3];
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[r][a][c] = mk<float>(0.f, 0.f);
+  Cx<float> u[9], p[4][3];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const int mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    load_link_packed<RECON>(U, mu, V, fwd ? s : nb[d], u);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r < nr) {
+        load_spinor_packed(in + (long long)(r0 + r) * 6 * V + nb[d], V, p);
+        if (G5IN) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            Cx<float> a0 = p[0][c], a1 = p[1][c];
+            p[0][c] = neg(p[2][c]); p[1][c] = neg(p[3][c]); p[2][c] = neg(a0); p[3][c] = neg(a1);
+          }
+        }
+        if (fwd) {
+          if (mu == 0) term_fwd<float, 0>(p, u, acc[r]);
+          if (mu == 1) term_fwd<float, 1>(p, u, acc[r]);
+          if (mu == 2) term_fwd<float, 2>(p, u, acc[r]);
+          if (mu == 3) term_fwd<float, 3>(p, u, acc[r]);
+        } else {
+          if (mu == 0) term_bwd<float, 0>(p, u, acc[r]);
+          if (mu == 1) term_bwd<float, 1>(p, u, acc[r]);
+          if (mu == 2) term_bwd<float, 2>(p, u, acc[r]);
+          if (mu == 3) term_bwd<float, 3>(p, u, acc[r]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (r >= nr) break;
+    float4 *dst = out + (long long)(r0 + r) * 6 * V + s;
+    if (MODE == 3) {
+      store_spinor_packed(dst, V, acc[r]);
+      continue;
+    }
+    load_spinor_packed(in + (long long)(r0 + r) * 6 * V + s, V, p);
+    if (G5IN) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Cx<float> a0 = p[0][c], a1 = p[1][c];
+        p[0][c] = neg(p[2][c]); p[1][c] = neg(p[3][c]); p[2][c] = neg(a0); p[3][c] = neg(a1);
+      }
+    }
+    Cx<float> o[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        o[a][c] = mk<float>(fmaf(-kappa, acc[r][a][c].x, p[a][c].x), fmaf(-kappa, acc[r][a][c].y, p[a][c].y));
+    if (MODE == 2) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Cx<float> a0 = o[0][c], a1 = o[1][c];
+        o[0][c] = neg(o[2][c]); o[1][c] = neg(o[3][c]); o[2][c] = neg(a0); o[3][c] = neg(a1);
+      }
+    }
+    store_spinor_packed(dst, V, o);
+  }
+}
+
+// canonical complex128 fields -> packed FP32 (optionally scaled per right-hand side by 1/s[r])
+__global__ void pack_f32_kernel(const double2 *__restrict__ x, const double *__restrict__ s, float4 *__restrict__ y,
+                                int V) {
+  const int site = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (site >= V) return;
+  double f = 1.0;
+  if (s) {
+    const double d = s[r];
+    f = d > 0.0 ? 1.0 / d : 0.0;
+  }
+  const double2 *src = x + ((long long)r * V + site) * 12;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const double2 a = src[2 * q], b = src[2 * q + 1];
+    y[((long long)r * 6 + q) * V + site] = make_float4((float)(a.x * f), (float)(a.y * f), (float)(b.x * f), (float)(b.y * f));
+  }
+}
+
+// x^r (canonical FP64) += s[r] * unpack(c^r); s == NULL: x = unpack(c)
+__global__ void unpack_f32_kernel(const float4 *__restrict__ c, const double *__restrict__ s, double2 *__restrict__ x,
+                                  int V) {
+  const int site = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (site >= V) return;
+  double2 *dst = x + ((long long)r * V + site) * 12;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float4 v = c[((long long)r * 6 + q) * V + site];
+    if (s) {
+      const double d = s[r];
+      double2 a = dst[2 * q], b = dst[2 * q + 1];
+      a.x = fma(d, (double)v.x, a.x); a.y = fma(d, (double)v.y, a.y);
+      b.x = fma(d, (double)v.z, b.x); b.y = fma(d, (double)v.w, b.y);
+      dst[2 * q] = a;
+      dst[2 * q + 1] = b;
+    } else {
+      dst[2 * q] = make_double2(v.x, v.y);
+      dst[2 * q + 1] = make_double2(v.z, v.w);
+    }
+  }
+}
+
+// FP64 links [mu][site][3][3] -> packed FP32 links (RECON 12 or 18)
+__global__ void pack_links_kernel(const double2 *__restrict__ U, float4 *__restrict__ P, int V, int recon) {
+  const int site = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mu = blockIdx.y;
+  if (site >= V) return;
+  const double2 *u = U + ((long long)mu * V + site) * 9;
+  const int nc = recon == 12 ? 3 : 5;
+  float4 *dst = P + (long long)mu * nc * V + site;
+  const int ne = recon == 12 ? 6 : 9;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    if (q >= nc) break;
+    const int e0 = 2 * q, e1 = 2 * q + 1;
+    const double2 a = u[e0];
+    const double2 b = e1 < ne ? u[e1] : make_double2(0.0, 0.0);
+    dst[(long long)q * V] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+  }
+}
+
+template <int NR, int RECON>
+lqcd_status packed_launch_nr(lqcd_ctx *ctx, const float4 *U, double kappa, const float4 *in, float4 *out, int nrhs,
+                             int flags) {
+  int bs = 128;
+  const int groups = (nrhs + NR - 1) / NR;
+  while (bs > 32 && (long long)ceil_div(ctx->V, bs) * groups < 2LL * ctx->sms) bs /= 2;
+  dim3 grid(ceil_div(ctx->V, bs), groups);
+  const int *d = ctx->dims;
+  const float k = (float)kappa;
+  kbegin(ctx);
+  switch (flags) {
+    case LQCD_APPLY_M: wilson_packed_kernel<NR, RECON, 0><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs); break;
+    case LQCD_APPLY_G5R: wilson_packed_kernel<NR, RECON, 1><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs); break;
+    case LQCD_APPLY_DAG: wilson_packed_kernel<NR, RECON, 2><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs); break;
+    case LQCD_APPLY_HOP: wilson_packed_kernel<NR, RECON, 3><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs); break;
+    default: return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: unknown flags %d", flags);
+  }
+  return launch_check(ctx, "wilson_packed_kernel", K_WILSON, (double)ctx->V * nrhs);
+}
+
+}  // namespace
+
+lqcd_status wilson_launch_packed(lqcd_ctx *ctx, const float4 *U, int recon, double kappa, const float4 *in, float4 *out,
+                                 int nrhs, int flags, int nr) {
+  if (nrhs <= 0 || nrhs > 65535 * 4) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: nrhs %d out of range", nrhs);
+  if (recon != 12 && recon != 18) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: recon must be 12 or 18");
+  if (nr <= 0) nr = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
+  if (recon == 12) {
+    if (nr == 1) return packed_launch_nr<1, 12>(ctx, U, kappa, in, out, nrhs, flags);
+    if (nr == 2) return packed_launch_nr<2, 12>(ctx, U, kappa, in, out, nrhs, flags);
+    return packed_launch_nr<4, 12>(ctx, U, kappa, in, out, nrhs, flags);
+  }
+  if (nr == 1) return packed_launch_nr<1, 18>(ctx, U, kappa, in, out, nrhs, flags);
+  if (nr == 2) return packed_launch_nr<2, 18>(ctx, U, kappa, in, out, nrhs, flags);
+  return packed_launch_nr<4, 18>(ctx, U, kappa, in, out, nrhs, flags);
+}
+
+lqcd_status pack_f32(lqcd_ctx *ctx, const double2 *x, const double *scale, float4 *y, int nrhs) {
+  kbegin(ctx);
+  pack_f32_kernel<<<dim3(ceil_div(ctx->V, 128), nrhs), 128, 0, ctx->stream>>>(x, scale, y, ctx->V);
+  return launch_check(ctx, "pack_f32_kernel", K_BLAS1, (double)ctx->N * nrhs);
+}
+
+lqcd_status unpack_f32(lqcd_ctx *ctx, const float4 *c, const double *scale, double2 *x, int nrhs) {
+  kbegin(ctx);
+  unpack_f32_kernel<<<dim3(ceil_div(ctx->V, 128), nrhs), 128, 0, ctx->stream>>>(c, scale, x, ctx->V);
+  return launch_check(ctx, "unpack_f32_kernel", K_BLAS1, (double)ctx->N * nrhs);
+}
+
+lqcd_status pack_links_f32(lqcd_ctx *ctx, const double2 *U, float4 *P, int recon) {
+  if (recon != 12 && recon != 18) return set_err(ctx, LQCD_ERR_INVALID_ARG, "pack_links: recon must be 12 or 18");
+  kbegin(ctx);
+  pack_links_kernel<<<dim3(ceil_div(ctx->V, 128), 4), 128, 0, ctx->stream>>>(U, P, ctx->V, recon);
+  return launch_check(ctx, "pack_links_kernel", K_BLAS1, (double)ctx->V * 36);
+}
+
+extern "C" lqcd_status lqcd_pack_f32(lqcd_ctx *ctx, const double *in, float *out, int nrhs) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!in || !out || nrhs < 1 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "pack_f32: bad arguments");
+  return pack_f32(ctx, (const double2 *)in, nullptr, (float4 *)out, nrhs);
+}
+
+extern "C" lqcd_status lqcd_unpack_f32(lqcd_ctx *ctx, const float *in, double *out, int nrhs) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!in || !out || nrhs < 1 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "unpack_f32: bad arguments");
+  return unpack_f32(ctx, (const float4 *)in, nullptr, (double2 *)out, nrhs);
+}
+
+extern "C" lqcd_status lqcd_pack_links_f32(lqcd_ctx *ctx, const double *links, float *out, int recon) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "pack_links_f32: NULL pointer");
+  return pack_links_f32(ctx, (const double2 *)links, (float4 *)out, recon);
+}
+
+extern "C" lqcd_status lqcd_wilson_apply_packed(lqcd_ctx *ctx, const float *links_packed, int recon, double kappa,
+                                                const float *in, float *out, int nrhs, int flags, int rhs_per_thread) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links_packed || !in || !out || in == out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_packed: bad pointers");
+  if (rhs_per_thread != 0 && rhs_per_thread != 1 && rhs_per_thread != 2 && rhs_per_thread != 4)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_packed: rhs_per_thread must be 0, 1, 2 or 4");
+  return wilson_launch_packed(ctx, (const float4 *)links_packed, recon, kappa, (const float4 *)in, (float4 *)out, nrhs,
+                              flags, rhs_per_thread);
+}

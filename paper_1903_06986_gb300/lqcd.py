@@ -85,6 +85,10 @@ def load(path=None):
         "lqcd_wilson_apply": [vp, vp, d, vp, vp, i, i, i],
         "lqcd_wilson_apply_f32": [vp, vp, d, vp, vp, i, i],
         "lqcd_to_f32": [vp, vp, vp, C.c_longlong],
+        "lqcd_pack_f32": [vp, vp, vp, i],
+        "lqcd_unpack_f32": [vp, vp, vp, i],
+        "lqcd_pack_links_f32": [vp, vp, vp, i],
+        "lqcd_wilson_apply_packed": [vp, vp, i, d, vp, vp, i, i, i],
         "lqcd_gmresdr_solve": [vp, vp, d, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo), C.POINTER(vp)],
         "lqcd_minresdr_solve": [vp, vp, d, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo), C.POINTER(vp)],
         "lqcd_proj_solve": [vp, vp, d, vp, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo)],
@@ -185,7 +189,7 @@ class Defl:
 class Context:
     """An lqcd_ctx bound to the current CUDA device and torch's current stream."""
 
-    def __init__(self, dims, stream=None):
+    def __init__(self, dims, stream=None, recon=18):
         torch = _torch()
         self.lib = load()
         self.dims = tuple(int(d) for d in dims)
@@ -195,7 +199,7 @@ class Context:
         s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         h = C.c_void_p()
         dd = (C.c_int * 4)(*self.dims)
-        st = self.lib.lqcd_ctx_create(C.byref(h), dd, 18, C.c_void_p(s))
+        st = self.lib.lqcd_ctx_create(C.byref(h), dd, recon, C.c_void_p(s))
         if st != OK:
             raise LqcdError(st, "lqcd_ctx_create failed")
         self.h = h
@@ -268,6 +272,33 @@ class Context:
         """complex128 device tensor -> complex64 copy (FP32 storage), converted on the device."""
         out = _torch().empty(t.shape, dtype=_torch().complex64, device=self.device)
         self._check(self.lib.lqcd_to_f32(self.h, _ptr(t), _ptr(out, _torch().complex64), t.numel()))
+        return out
+
+    def pack_f32(self, x):
+        """canonical complex128 block (nrhs fields) -> packed FP32 (float32 tensor, nrhs x 24 V)."""
+        n = self._nrhs(x)
+        out = _torch().empty((n, 24 * self.V), dtype=_torch().float32, device=self.device)
+        self._check(self.lib.lqcd_pack_f32(self.h, _ptr(x), _ptr(out, _torch().float32), n))
+        return out
+
+    def unpack_f32(self, p):
+        n = p.numel() // (24 * self.V)
+        out = self.field(n)
+        self._check(self.lib.lqcd_unpack_f32(self.h, _ptr(p, _torch().float32), _ptr(out), n))
+        return out
+
+    def pack_links_f32(self, links, recon=12):
+        nc = 12 if recon == 12 else 20
+        out = _torch().empty((4, nc * self.V), dtype=_torch().float32, device=self.device)
+        self._check(self.lib.lqcd_pack_links_f32(self.h, _ptr(links), _ptr(out, _torch().float32), recon))
+        return out
+
+    def wilson_apply_packed(self, links_p, recon, kappa, inp, out=None, flags=APPLY_M, rhs_per_thread=0):
+        f32 = _torch().float32
+        out = _torch().empty_like(inp) if out is None else out
+        self._check(self.lib.lqcd_wilson_apply_packed(self.h, _ptr(links_p, f32), recon, kappa, _ptr(inp, f32),
+                                                      _ptr(out, f32), inp.numel() // (24 * self.V), flags,
+                                                      rhs_per_thread))
         return out
 
     def wilson_apply_f32(self, links32, kappa, inp, out=None, flags=APPLY_M):

@@ -38,5 +38,5 @@ def test_version_and_argument_checks(lib):
     bad = (ctypes.c_int * 4)(4, 4, 1, 4)
     assert lib.lqcd_ctx_create(ctypes.byref(h), bad, 18, None) == lqcd.ERR_INVALID_ARG
     good = (ctypes.c_int * 4)(4, 4, 4, 4)
-    assert lib.lqcd_ctx_create(ctypes.byref(h), good, 12, None) == lqcd.ERR_INVALID_ARG
+    assert lib.lqcd_ctx_create(ctypes.byref(h), good, 16, None) == lqcd.ERR_INVALID_ARG
     assert lib.lqcd_wilson_apply(None, None, 0.1, None, None, 1, 0, 0) == lqcd.ERR_INVALID_ARG

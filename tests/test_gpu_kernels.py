@@ -50,6 +50,16 @@ def test_wilson_all_forms(dims):
     for flag, ref in forms.items():
         got = host(ctx.wilson_apply_f32(U32, kappa, p32, flags=flag))
         assert rel_err(got, ref(psi)) < 2e-6, flag
+    # packed FP32 operator, recon 18 and 12, 1, 2 and 4 right-hand sides per thread
+    packed = ctx.pack_f32(pd)
+    assert np.array_equal(host(ctx.unpack_f32(packed)), psi.astype(np.complex64).astype(np.complex128))
+    for recon in (18, 12):
+        Up = ctx.pack_links_f32(Ud, recon)
+        for nr in (1, 2, 4):
+            for flag, ref in forms.items():
+                got = host(ctx.unpack_f32(ctx.wilson_apply_packed(Up, recon, kappa, packed, flags=flag,
+                                                                  rhs_per_thread=nr)))
+                assert rel_err(got, ref(psi)) < 2e-6, (recon, nr, flag)
 
 
 @pytest.mark.parametrize("dims", DIMS[:3])
