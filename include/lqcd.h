@@ -311,6 +311,42 @@ typedef struct {
 lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, double kappa,
                                const lqcd_est_opts *opts, lqcd_estimate *out);
 
+/* ---- a13: derivatives (a spec addition; the paper has no derivatives) ------------ */
+
+/* Link gradient of scalar noise estimates T_n = eta_n^dag M^{-1} eta_n from x_n = M^{-1} eta_n and
+ * z_n = M^{-dag} eta_n (device, nrhs fields each).  Accumulates (+=) scale * sum_n into
+ *   grad[mu][s][a]  (device, 4 x V x 8 complex): dT/dw_a under U_mu(s) -> exp(i w lambda_a/2) U_mu(s),
+ *                   lambda_a the Gell-Mann matrices: (i kappa / 2) tr(lambda_a B) with
+ *                   B = sum_spin [(1-g_mu) U x(s+mu)] z(s)^dag - [(1+g_mu) x(s)] (U z(s+mu))^dag;
+ *   grad_links (device, 4 x V x 3 x 3 complex, may be NULL): dT/dU* + conj(dT/dU), the gradient of
+ *                   Re T with respect to the complex link entries in torch's convention. */
+lqcd_status lqcd_link_grad(lqcd_ctx *ctx, const double *links, double kappa, const double *z, const double *x,
+                           int nrhs, double scale, double *grad, double *grad_links);
+
+typedef struct {
+  double grad_scale;  /* in: factor applied to link_grad / grad_links (e.g. an upstream gradient)   */
+  double *dkappa;     /* host [2 modes: NS, PS][9 ops] complex: mean d Tr(Theta M^{-1}) / dkappa   */
+  double *dkappa_err; /* host [2][9]: error bar of the signal part (Re scalar, Im vectors)          */
+  double *per_noise;  /* host [2][nnoise][9] complex                                                 */
+  double *link_grad;  /* device [4][V][8] complex, or NULL: mean over noises of the NS scalar dT/dw  */
+  double *grad_links; /* device [4][V][3][3] complex, or NULL (needs link_grad): torch-convention   */
+  long matvecs;
+  double seconds;
+  double max_true_resid;
+  int converged;
+} lqcd_derivs;
+
+/* d Tr(Theta M^{-1}) / dkappa for the nine operators with no subtraction (NS) and with
+ * perturbative subtraction (PS, opts->K terms, differentiated term by term), and the gradient of
+ * the NS scalar estimate with respect to every link.  Per noise three solves run (x = M^{-1} eta,
+ * y = M^{-1} P x, and the adjoint w = M^{-1} g5 eta, z = g5 w) with GMRES-Proj over a GMRES-DR
+ * space of the special right-hand side, to opts->tol (opts->prec selects plain FP64 or mixed
+ * precision); nothing is kept from a previous call.  Uses opts seed, nnoise, block, m, k, m_inner,
+ * K, tol, tol_special, max_cycles, prec. */
+lqcd_status lqcd_loop_derivs(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *opts,
+                             lqcd_derivs *out);
+
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,3 +94,33 @@ def loop_estimate(U, kappa, dims, seed, nnoise, m, k, K, npoly, tol, tol_special
         out[mode]["addback_t"] = O.per_t(add[mode])
     t2 = time.perf_counter()
     return out, st, dict(setup_s=t1 - t0, noise_s=t2 - t1, solve_infos=infos)
+
+
+def loop_derivs(U, kappa, dims, seed, nnoise, m, k, K, tol, tol_special, max_cycles=2000):
+    """Derivatives of the loop estimates (see oracle/derivs.py), step by step: GMRES-DR on M for the
+    special right-hand side; per noise x = M^{-1} eta, y = M^{-1} P x and z = M^{-dag} eta by
+    GMRES-Proj; per-noise d/dkappa of the NS and PS estimates of the nine operators (PS add-back
+    derivative included) and the mean link gradient of the NS scalar estimate.
+    Returns dict(per_noise=[2, n, op], link_grad=(4, T, Z, Y, X, 8))."""
+    from . import derivs as Dv
+    A = lambda v: L.flat(L.wilson(U, kappa, L.unflat(v, dims)))
+    b0 = L.flat(rng.z4_noise(seed, rng.NOISE_SPECIAL, dims))
+    _, _, defl = Kr.gmres_dr(A, b0, m, k, tol_special, max_cycles)
+    solve = lambda f: L.unflat(Kr.gmres_proj(A, L.flat(f), defl, m - k, tol, max_cycles)[0], dims)
+    t = S.hop_traces(U, kappa, K, dims)
+    dadd = O.per_t(Dv.dpert_addback(t, kappa, K)).sum(axis=-1)
+    per = np.zeros((2, nnoise, O.NOPS), dtype=np.complex128)
+    grad = np.zeros(U.shape[:-2] + (8,), dtype=np.complex128)
+    for n in range(nnoise):
+        eta = rng.z4_noise(seed, n, dims)
+        x = solve(eta)
+        y = solve(L.hop(U, x))
+        z = L.g5(solve(L.g5(eta)))
+        d_none = Dv.dkappa_densities(U, kappa, eta, x, y).sum(axis=(-1, -2, -3, -4))
+        xt = S.hop_series(U, kappa, eta, K)
+        dxt = Dv.dpert_vector(U, kappa, eta, K)
+        d_pert = Dv.dkappa_densities(U, kappa, eta, x - xt, y - dxt).sum(axis=(-1, -2, -3, -4))
+        per[0, n] = d_none
+        per[1, n] = d_pert + dadd
+        grad += Dv.link_gradient(U, kappa, x, z) / nnoise
+    return dict(per_noise=per, link_grad=grad)

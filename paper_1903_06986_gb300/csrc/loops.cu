@@ -569,6 +569,15 @@ static lqcd_status xi_dev(lqcd_ctx *ctx, const double2 *U, double kappa, const l
   return LQCD_OK;
 }
 
+lqcd_status hop_series_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *eta, double2 *out, int nrhs,
+                              int K, const cd *c) {
+  return hop_series_dev(ctx, U, kappa, eta, out, nrhs, K, c);
+}
+
+lqcd_status hop_traces_launch(lqcd_ctx *ctx, const double2 *U, double kappa, int K, std::vector<cd> &tr) {
+  return hop_traces_dev(ctx, U, kappa, K, tr);
+}
+
 // ---- C ABI -----------------------------------------------------------------------------------
 extern "C" {
 

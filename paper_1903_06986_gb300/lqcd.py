@@ -60,6 +60,12 @@ class Estimate(C.Structure):
                 ("converged", C.c_int)]
 
 
+class Derivs(C.Structure):
+    _fields_ = [("grad_scale", C.c_double), ("dkappa", _dp), ("dkappa_err", _dp), ("per_noise", _dp),
+                ("link_grad", C.c_void_p), ("grad_links", C.c_void_p), ("matvecs", C.c_long), ("seconds", C.c_double),
+                ("max_true_resid", C.c_double), ("converged", C.c_int)]
+
+
 _LIB = None
 
 
@@ -104,6 +110,8 @@ def load(path=None):
         "lqcd_xi_inverse": [vp, vp, d, vp, i, i, vp, vp],
         "lqcd_contract": [vp, vp, d, vp, vp, i, vp],
         "lqcd_loop_estimate": [vp, vp, d, C.POINTER(EstOpts), C.POINTER(Estimate)],
+        "lqcd_link_grad": [vp, vp, d, vp, vp, i, d, vp, vp],
+        "lqcd_loop_derivs": [vp, vp, d, C.POINTER(EstOpts), C.POINTER(Derivs)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -424,6 +432,42 @@ class Context:
                     poly_a=pa, matvecs_setup=est.matvecs_setup, matvecs_noise=est.matvecs_noise,
                     seconds_setup=est.seconds_setup, seconds_noise=est.seconds_noise,
                     max_true_resid=est.max_true_resid, converged=bool(est.converged), status=st)
+
+
+def _link_grad_buffers(ctx, want_links):
+    torch = _torch()
+    lx, ly, lz, lt = ctx.dims
+    g = torch.zeros((4, lt, lz, ly, lx, 8), dtype=torch.complex128, device=ctx.device)
+    gl = torch.zeros((4, lt, lz, ly, lx, 3, 3), dtype=torch.complex128, device=ctx.device) if want_links else None
+    return g, gl
+
+
+def link_grad(ctx, links, kappa, z, x, scale=1.0, want_links=True):
+    """dT/dw (4, T, Z, Y, X, 8) and the torch-convention gradient of Re T (4, T, Z, Y, X, 3, 3), summed
+    over the right-hand sides of z and x and multiplied by scale (lqcd_link_grad)."""
+    g, gl = _link_grad_buffers(ctx, want_links)
+    ctx._check(ctx.lib.lqcd_link_grad(ctx.h, _ptr(links), kappa, _ptr(z), _ptr(x), ctx._nrhs(x), scale, _ptr(g),
+                                      _ptr(gl)))
+    return g, gl
+
+
+def loop_derivs(ctx, links, kappa, seed, nnoise, block, m, k, K, tol, tol_special, m_inner=0, max_cycles=2000,
+                prec=PREC_F64, want_grad=True, grad_scale=1.0):
+    """lqcd_loop_derivs: d/dkappa of the NS and PS estimates of the nine operators, and the link
+    gradient of the NS scalar estimate."""
+    o = EstOpts(seed, nnoise, block, m, k, m_inner, K, 0, tol, tol_special, max_cycles, SUB_NONE | SUB_PERT, prec)
+    dk = np.zeros((2, NOPS), dtype=np.complex128)
+    err = np.zeros((2, NOPS), dtype=np.float64)
+    per = np.zeros((2, nnoise, NOPS), dtype=np.complex128)
+    g, gl = _link_grad_buffers(ctx, want_grad) if want_grad else (None, None)
+    as_dp = lambda a: a.ctypes.data_as(_dp)
+    out = Derivs(grad_scale, as_dp(dk), as_dp(err), as_dp(per), C.c_void_p(g.data_ptr()) if g is not None else None,
+                 C.c_void_p(gl.data_ptr()) if gl is not None else None, 0, 0.0, 0.0, 0)
+    st = ctx.lib.lqcd_loop_derivs(ctx.h, _ptr(links), kappa, C.byref(o), C.byref(out))
+    if st not in (OK, ERR_NOT_CONVERGED):
+        ctx._check(st)
+    return dict(dkappa=dk, dkappa_err=err, per_noise=per, link_grad=g, grad_links=gl, matvecs=out.matvecs,
+                seconds=out.seconds, max_true_resid=out.max_true_resid, converged=bool(out.converged))
 
 
 def header_functions(header=None):

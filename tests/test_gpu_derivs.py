@@ -1,0 +1,92 @@
+"""GPU parity of the derivative stage (kappa and gauge links) with the oracle, and consistency of
+the derivatives with central finite differences of the GPU estimates themselves."""
+import numpy as np
+import pytest
+
+from oracle import derivs as Dv, lattice as L, pipeline as PL, rng
+from paper_1903_06986_gb300 import lqcd, synth
+from tests.gpu_util import context, dev, host, rel_err, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def rand_fields(dims, n, seed):
+    r = np.random.default_rng(seed)
+    shp = L.field_shape(dims, (n,))
+    return r.standard_normal(shp) + 1j * r.standard_normal(shp)
+
+
+def test_link_grad_kernel_matches_oracle():
+    dims = (3, 2, 4, 4)
+    ctx = context(dims)
+    U = synth.su3_links(dims, 0.5, 51)
+    kappa = 0.137
+    x, z = rand_fields(dims, 2, 1), rand_fields(dims, 2, 2)
+    g, gl = lqcd.link_grad(ctx, dev(U), kappa, dev(z), dev(x), scale=0.5)
+    ref = 0.5 * (Dv.link_gradient(U, kappa, x[0], z[0]) + Dv.link_gradient(U, kappa, x[1], z[1]))
+    assert rel_err(host(g), ref) < 1e-12
+    dU = dUc = 0
+    for r in range(2):
+        a, b = Dv.link_matrix_derivatives(U, kappa, x[r], z[r])
+        dU, dUc = dU + a, dUc + b
+    assert rel_err(host(gl), 0.5 * (dUc + dU.conj())) < 1e-12
+
+
+def test_loop_derivs_match_oracle():
+    dims, kappa = (2, 2, 2, 4), 0.14
+    ctx = context(dims)
+    U = synth.su3_links(dims, 0.45, 2)
+    N = 6
+    g = lqcd.loop_derivs(ctx, dev(U), kappa, 5, N, 3, 40, 8, 7, 1e-12, 1e-13)
+    assert g["converged"] and g["max_true_resid"] <= 1e-12
+    ref = PL.loop_derivs(U, kappa, dims, 5, N, 40, 8, 7, 1e-12, 1e-13)
+    for mode in range(2):
+        want = ref["per_noise"][mode]
+        scale = np.abs(want).max(axis=0)
+        assert np.all(np.abs(g["per_noise"][mode] - want) <= 1e-8 * scale + 1e-10), mode
+    assert rel_err(host(g["link_grad"]), ref["link_grad"]) < 1e-8
+
+
+def test_dkappa_matches_finite_difference_of_estimates():
+    """The GPU d/dkappa of the NS and PS estimates equals a fourth-order central difference of the GPU
+    loop estimate itself (same noises), for all nine operators."""
+    dims = (4, 4, 4, 4)
+    ctx = context(dims)
+    U = dev(synth.su3_links(dims, 0.3, 1))
+    kappa, h = 0.12, 1e-4
+    kw = dict(m=20, k=5, K=4, npoly=3, tol=1e-13, tol_special=1e-13)
+    d = lqcd.loop_derivs(ctx, U, kappa, 1, 4, 4, 20, 5, 4, 1e-13, 1e-13, want_grad=False)
+    est = lambda k: ctx.loop_estimate(U, k, 1, 4, 4, modes=lqcd.SUB_NONE | lqcd.SUB_PERT, **kw)["mean"]
+    f = {s: est(kappa + s * h) for s in (-2, -1, 1, 2)}
+    fd = (-f[2] + 8 * f[1] - 8 * f[-1] + f[-2]) / (12 * h)
+    for mode in range(2):
+        assert np.allclose(d["dkappa"][mode], fd[[0, 1][mode]], rtol=2e-7, atol=1e-6), mode
+
+
+def test_autograd_scalar_loop():
+    torch = torch_cuda()
+    from paper_1903_06986_gb300.autograd import scalar_loop
+    dims = (2, 2, 2, 4)
+    ctx = context(dims)
+    U0 = synth.su3_links(dims, 0.45, 3)
+    opts = dict(seed=9, nnoise=4, block=4, m=40, k=8, K=4, npoly=3, tol=1e-13, tol_special=1e-13)
+    kappa = torch.tensor(0.13, dtype=torch.float64, requires_grad=True)
+    links = dev(U0).requires_grad_(True)
+    out = scalar_loop(kappa, links, ctx, **opts)
+    out.backward()
+    f = lambda k, UU: float(scalar_loop(torch.tensor(k, dtype=torch.float64), dev(UU), ctx, **opts))
+    h = 1e-5
+    fdk = (f(0.13 + h, U0) - f(0.13 - h, U0)) / (2 * h)
+    assert abs(kappa.grad.item() - fdk) < 1e-6 * max(1.0, abs(fdk))
+    # directional derivative along Lie-algebra perturbations of a few links: dL = Re <grad, dU>
+    G = host(links.grad)
+    r = np.random.default_rng(4)
+    for _ in range(4):
+        mu = int(r.integers(4))
+        site = tuple(int(r.integers(n)) for n in L.site_shape(dims))
+        a = int(r.integers(8))
+        Up, Um = Dv.perturb_link(U0, mu, site, a, h), Dv.perturb_link(U0, mu, site, a, -h)
+        fd = (f(0.13, Up) - f(0.13, Um)) / (2 * h)
+        dU = (Up - Um) / (2 * h)
+        pred = np.real(np.vdot(G, dU))
+        assert abs(pred - fd) < 1e-6 * max(1.0, abs(fd)), (mu, site, a)
