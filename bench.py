@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
-    ap.add_argument("--case", default=None, choices=["gmres-cycle", "gmres-cycle-f32"],
+    ap.add_argument("--case", default=None, choices=["gmres-cycle", "gmres-cycle-f32", "dslash-packed"],
                     help="run one small kernel case for profiling instead of the benchmark: one GMRES(30) "
                          "cycle on 50 noises of the 8^3x16 workload (FP64, or FP32 storage)")
     return ap.parse_args()
@@ -262,10 +262,23 @@ def dslash_rates(torch):
 
 
 def run_case(args):
-    """Small fixed workload for ncu captures of the solver kernels (no timing output)."""
+    """Small fixed workloads for ncu captures (no timing output): one GMRES(30) cycle on the 50 noises
+    of the 8^3x16 workload (FP64, or the mixed solver's FP32 cycle), or four applications of the
+    packed FP32 operator (recon 12, 8 right-hand sides) on the 24^3x32 lattice."""
     import torch
     from paper_1903_06986_gb300 import build, lqcd, synth
     build.build()
+    if args.case == "dslash-packed":
+        ctx = lqcd.Context(DSLASH_DIMS, recon=12)
+        U = torch.from_numpy(synth.su3_links(DSLASH_DIMS, 0.4323, 7)).cuda()
+        Up = ctx.pack_links_f32(U, 12)
+        x = ctx.pack_f32(ctx.noise_z4(3, 0, 8))
+        y = torch.empty_like(x)
+        for _ in range(4):
+            ctx.wilson_apply_packed(Up, 12, 0.157, x, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "launches": ctx.launches}))
+        return
     U = torch.from_numpy(synth.su3_links(DIMS, 0.4323, LINK_SEED)).cuda()
     ctx = lqcd.Context(DIMS)
     etas = ctx.noise_z4(NOISE_SEED, 0, NNOISE)

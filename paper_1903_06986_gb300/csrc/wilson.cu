@@ -236,10 +236,12 @@ __device__ __forceinline__ void store_spinor_packed(float4 *__restrict__ p, int 
 template <int NR, int RECON, int MODE>
 __global__ void __launch_bounds__(128) wilson_packed_kernel(const float4 *__restrict__ U, const float4 *__restrict__ in,
                                                             float4 *__restrict__ out, float kappa, int Lx, int Ly,
-                                                            int Lz, int Lt, int V, int nrhs) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+                                                            int Lz, int Lt, int V, int nrhs, int groups) {
+  // the right-hand-side group varies fastest along the grid, so the blocks of all groups of one
+  // site block run together and read its links (and neighbour spinor lines) from L2, not DRAM
+  const int s = (blockIdx.x / groups) * blockDim.x + threadIdx.x;
   if (s >= V) return;
-  const int r0 = blockIdx.y * NR;
+  const int r0 = (blockIdx.x % groups) * NR;
   const int nr = min(NR, nrhs - r0);
   constexpr bool G5IN = (MODE == 1 || MODE == 2);
   int x = s % Lx, rr = s / Lx;
@@ -396,15 +398,17 @@ lqcd_status packed_launch_nr(lqcd_ctx *ctx, const float4 *U, double kappa, const
   int bs = 128;
   const int groups = (nrhs + NR - 1) / NR;
   while (bs > 32 && (long long)ceil_div(ctx->V, bs) * groups < 2LL * ctx->sms) bs /= 2;
-  dim3 grid(ceil_div(ctx->V, bs), groups);
+  const long long nblk = (long long)ceil_div(ctx->V, bs) * groups;
+  if (nblk > 0x7fffffffLL) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: grid too large");
+  dim3 grid((unsigned)nblk);
   const int *d = ctx->dims;
   const float k = (float)kappa;
   kbegin(ctx);
   switch (flags) {
-    case LQCD_APPLY_M: wilson_packed_kernel<NR, RECON, 0><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs); break;
-    case LQCD_APPLY_G5R: wilson_packed_kernel<NR, RECON, 1><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs); break;
-    case LQCD_APPLY_DAG: wilson_packed_kernel<NR, RECON, 2><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs); break;
-    case LQCD_APPLY_HOP: wilson_packed_kernel<NR, RECON, 3><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs); break;
+    case LQCD_APPLY_M: wilson_packed_kernel<NR, RECON, 0><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
+    case LQCD_APPLY_G5R: wilson_packed_kernel<NR, RECON, 1><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
+    case LQCD_APPLY_DAG: wilson_packed_kernel<NR, RECON, 2><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
+    case LQCD_APPLY_HOP: wilson_packed_kernel<NR, RECON, 3><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
     default: return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: unknown flags %d", flags);
   }
   return launch_check(ctx, "wilson_packed_kernel", K_WILSON, (double)ctx->V * nrhs);
@@ -414,9 +418,11 @@ lqcd_status packed_launch_nr(lqcd_ctx *ctx, const float4 *U, double kappa, const
 
 lqcd_status wilson_launch_packed(lqcd_ctx *ctx, const float4 *U, int recon, double kappa, const float4 *in, float4 *out,
                                  int nrhs, int flags, int nr) {
-  if (nrhs <= 0 || nrhs > 65535 * 4) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: nrhs %d out of range", nrhs);
+  if (nrhs <= 0) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: nrhs %d out of range", nrhs);
   if (recon != 12 && recon != 18) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: recon must be 12 or 18");
-  if (nr <= 0) nr = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
+  // measured on 24^3 x 32: with reconstructed links one right-hand side per thread is fastest (the
+  // link reconstruction is cheap, the registers saved keep occupancy up); with 18-real links two
+  if (nr <= 0) nr = (recon == 12 || nrhs < 2) ? 1 : 2;
   if (recon == 12) {
     if (nr == 1) return packed_launch_nr<1, 12>(ctx, U, kappa, in, out, nrhs, flags);
     if (nr == 2) return packed_launch_nr<2, 12>(ctx, U, kappa, in, out, nrhs, flags);
