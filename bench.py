@@ -38,6 +38,7 @@ WORKLOAD = "8^3x16 plain FP64, kappa {0.150,0.155,0.157}, 50 Z4 noises, GMRES-DR
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 DFMA / clock / SM at the 2070 MHz maximum clock
 WILSON_FLOPS = 1368        # per site per right-hand side (1320 for P, 48 for 1 - kappa P)
 L2_FLUSH_BYTES = 512 << 20
+M_INNER_MIXED = 40         # GMRES cycle length of the reduced-precision inner solves
 
 
 def parse():
@@ -50,7 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
-    ap.add_argument("--case", default=None, choices=["gmres-cycle", "gmres-cycle-f32", "dslash-packed"],
+    ap.add_argument("--case", default=None, choices=["gmres-cycle", "gmres-cycle-f32", "dslash-packed", "dslash-half"],
                     help="run one small kernel case for profiling instead of the benchmark: one GMRES(30) "
                          "cycle on 50 noises of the 8^3x16 workload (FP64, or FP32 storage)")
     return ap.parse_args()
@@ -214,9 +215,10 @@ HBM_PEAK_GBS = 6793.4            # measured copy bandwidth of this GB300 pool
 
 def dslash_rates(torch):
     """Wilson operator throughput on the 24^3x32 lattice: the FP64 operator of the plain path
-    (canonical layout) and the packed FP32 operator of the mixed-precision inner solver (recon 12 and
-    18 links).  Algorithmic bytes per launch: each spinor read once and written once (nrhs x V x 24
-    reals) plus the links once (4 x V x 18 or 12 reals); flops 1368 per site and right-hand side.
+    (canonical layout) and the packed operators of the mixed-precision inner solver (FP32, FP16 and
+    BF16 fields; FP32 links, recon 12 and 18).  Algorithmic bytes per launch: each spinor read once
+    and written once (nrhs x V x 24 reals each way) plus the links once (4 x V x 18 or 12 reals);
+    flops 1368 per site and right-hand side.
     CUDA events on the library stream, 2 warm-up and 5 timed launches; fields exceed L2 for nrhs > 1."""
     from paper_1903_06986_gb300 import lqcd, synth
     ctx = lqcd.Context(DSLASH_DIMS, recon=12)
@@ -225,13 +227,22 @@ def dslash_rates(torch):
     packed_links = {12: ctx.pack_links_f32(U, 12), 18: ctx.pack_links_f32(U, 18)}
     out = {}
     cases = [("f64", 18, 1), ("f64", 18, 8), ("f32packed", 12, 1), ("f32packed", 12, 8), ("f32packed", 12, 16),
-             ("f32packed", 18, 8)]
+             ("f32packed", 18, 8), ("f16packed", 12, 1), ("f16packed", 12, 8), ("f16packed", 12, 16),
+             ("bf16packed", 12, 8)]
     for prec, recon, nrhs in cases:
         x = ctx.noise_z4(3, 0, nrhs)
+        lw = 4
         if prec == "f64":
             y = torch.empty_like(x)
             fn = lambda: ctx.wilson_apply(U, 0.157, x, y)
-            w, lreals = 8, 18
+            w, lreals, lw = 8, 18, 8
+        elif prec in ("f16packed", "bf16packed"):
+            hp = lqcd.PREC_F16 if prec == "f16packed" else lqcd.PREC_BF16
+            x = ctx.pack_half(x, hp)
+            y = torch.empty_like(x)
+            Up = packed_links[recon]
+            fn = lambda: ctx.wilson_apply_half(Up, recon, 0.157, x, y, prec=hp)
+            w, lreals = 2, recon
         else:
             x = ctx.pack_f32(x)
             y = torch.empty_like(x)
@@ -248,7 +259,7 @@ def dslash_rates(torch):
         e1.record()
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 5 / 1000.0
-        nbytes = nrhs * V * 48 * w + V * 4 * lreals * w
+        nbytes = nrhs * V * 48 * w + V * 4 * lreals * lw
         gbs = nbytes / t / 1e9
         tf = 1368.0 * V * nrhs / t / 1e12
         out["%s_recon%d_rhs%d" % (prec, recon, nrhs)] = {
@@ -264,18 +275,22 @@ def dslash_rates(torch):
 def run_case(args):
     """Small fixed workloads for ncu captures (no timing output): one GMRES(30) cycle on the 50 noises
     of the 8^3x16 workload (FP64, or the mixed solver's FP32 cycle), or four applications of the
-    packed FP32 operator (recon 12, 8 right-hand sides) on the 24^3x32 lattice."""
+    packed FP32 or FP16 operator (recon 12, 8 right-hand sides) on the 24^3x32 lattice."""
     import torch
     from paper_1903_06986_gb300 import build, lqcd, synth
     build.build()
-    if args.case == "dslash-packed":
+    if args.case in ("dslash-packed", "dslash-half"):
         ctx = lqcd.Context(DSLASH_DIMS, recon=12)
         U = torch.from_numpy(synth.su3_links(DSLASH_DIMS, 0.4323, 7)).cuda()
         Up = ctx.pack_links_f32(U, 12)
-        x = ctx.pack_f32(ctx.noise_z4(3, 0, 8))
+        half = args.case == "dslash-half"
+        x = ctx.pack_half(ctx.noise_z4(3, 0, 8)) if half else ctx.pack_f32(ctx.noise_z4(3, 0, 8))
         y = torch.empty_like(x)
         for _ in range(4):
-            ctx.wilson_apply_packed(Up, 12, 0.157, x, y)
+            if half:
+                ctx.wilson_apply_half(Up, 12, 0.157, x, y)
+            else:
+                ctx.wilson_apply_packed(Up, 12, 0.157, x, y)
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "launches": ctx.launches}))
         return
@@ -318,11 +333,12 @@ def main():
     def step(i, links, prec=0):
         kappa = KAPPAS[i % len(KAPPAS)]
         r = ctx.loop_estimate(links, kappa, NOISE_SEED, NNOISE, BLOCK, M_DR, K_DR, K_PS, NPOLY, TOL, TOL_SPECIAL,
-                              max_cycles=1000, prec=prec)
+                              max_cycles=1000, prec=prec, m_inner=M_INNER_MIXED if prec else 0)
         if not r["converged"] or r["max_true_resid"] > TOL:
             raise RuntimeError("loop estimate did not reach the tolerance: %g" % r["max_true_resid"])
         stats.append(dict(kappa=kappa, setup_s=r["seconds_setup"], noise_s=r["seconds_noise"],
-                          mv_setup=r["matvecs_setup"], mv_noise=r["matvecs_noise"], resid=r["max_true_resid"]))
+                          mv_setup=r["matvecs_setup"], mv_noise=r["matvecs_noise"], resid=r["max_true_resid"],
+                          mean=r["mean"], stderr=r["stderr"]))
         return r
 
     for i in range(args.warmup):
@@ -381,37 +397,49 @@ def main():
         t_e2e = float(t.item())
     e2e_value = NNOISE * e2e_steps * world / t_e2e
 
-    # ---- the same steps with mixed-precision noise solves (FP32 inner GMRES-Proj inside FP64 defect
-    # correction, stopped on the FP64 true residual); setup, series, projections, contractions FP64
+    # ---- the same steps with mixed-precision noise solves (GMRES-Proj with FP32 arithmetic and FP32,
+    # FP16 or BF16 storage inside FP64 defect correction, stopped on the FP64 true residual); setup,
+    # series, projections and contractions FP64.  Every estimate is compared with the FP64 run's.
     mixed = None
     if not args.no_mixed:
-        for i in range(1):
-            step(i, Ud, prec=1)
+        mixed = {}
+        for name, prec in (("fp32", 1), ("fp16", 2), ("bf16", 3)):
+            step(0, Ud, prec=prec)
+            stats.clear()
+            barrier()
+            ctx.timing(True)
+            ctx.timing_reset()
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            m0.record()
+            for i in range(args.steps):
+                flush.zero_()
+                step(args.warmup + i, Ud, prec=prec)
+            m1.record()
+            barrier()
+            tm_mixed = m0.elapsed_time(m1) / 1000.0
+            tmm = ctx.timing_read()
+            ctx.timing(False)
+            ms_ = stats[:args.steps]
+            diff = [np.abs(a["mean"] - b["mean"]) for a, b in zip(ms_, stats_fp64)]
+            mixed[name] = {
+                "value": NNOISE * args.steps * world / tm_mixed, "unit": "estimates/s",
+                "speedup_vs_fp64": t_max / tm_mixed,
+                "noise_phase_estimates_per_s": NNOISE * len(ms_) / sum(x["noise_s"] for x in ms_),
+                "noise_phase_speedup_vs_fp64": (sum(x["noise_s"] for x in stats_fp64) /
+                                                sum(x["noise_s"] for x in ms_)),
+                "max_true_resid": max(x["resid"] for x in ms_),
+                "estimate_vs_fp64": {
+                    "max_abs_diff": float(max(d.max() for d in diff)),
+                    "max_rel_diff": float(max((d / np.maximum(np.abs(b["mean"]), 1e-300)).max()
+                                              for d, b in zip(diff, stats_fp64))),
+                    "max_diff_over_stderr": float(max((d / np.maximum(b["stderr"], 1e-300)).max()
+                                                      for d, b in zip(diff, stats_fp64)))},
+                "matvecs_per_noise": float(np.mean([x["mv_noise"] / NNOISE for x in ms_])),
+                "breakdown_ms": {k: round(v[0], 1) for k, v in tmm.items()},
+                "launches": int(sum(v[1] for v in tmm.values())),
+                "precision": "%s storage of the inner Krylov basis and deflation space, FP32 arithmetic, inside "
+                             "FP64 defect correction (true residual FP64), GMRES-Proj(%d)" % (name.upper(), M_INNER_MIXED)}
         stats.clear()
-        barrier()
-        ctx.timing(True)
-        ctx.timing_reset()
-        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        m0.record()
-        for i in range(args.steps):
-            flush.zero_()
-            step(args.warmup + i, Ud, prec=1)
-        m1.record()
-        barrier()
-        tm_mixed = m0.elapsed_time(m1) / 1000.0
-        tmm = ctx.timing_read()
-        ctx.timing(False)
-        ms_ = stats[:args.steps]
-        mixed = {"value": NNOISE * args.steps * world / tm_mixed, "unit": "estimates/s",
-                 "speedup_vs_fp64": t_max / tm_mixed,
-                 "noise_phase_estimates_per_s": NNOISE * len(ms_) / sum(x["noise_s"] for x in ms_),
-                 "noise_phase_speedup_vs_fp64": (sum(x["noise_s"] for x in ms_) and
-                                                 sum(x["noise_s"] for x in stats_fp64) / sum(x["noise_s"] for x in ms_)),
-                 "max_true_resid": max(x["resid"] for x in ms_),
-                 "matvecs_per_noise": float(np.mean([x["mv_noise"] / NNOISE for x in ms_])),
-                 "breakdown_ms": {k: round(v[0], 1) for k, v in tmm.items()},
-                 "launches": int(sum(v[1] for v in tmm.values())),
-                 "precision": "FP32 storage and arithmetic inside FP64 defect correction (true residual FP64)"}
 
     # ---- roofline of the dominant kernel class (device time over the timed region)
     dom = max(tm, key=lambda k: tm[k][0])

@@ -42,8 +42,10 @@ typedef enum {
   LQCD_ERR_OOM = 6            /* workspace allocation failed                           */
 } lqcd_status;
 
-/* Arithmetic of an operator application.  F64 is the plain FP64 path. */
-typedef enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1 } lqcd_prec;
+/* Precision of an operator application or of the inner solver of a mixed-precision solve.  F64 is
+ * the plain FP64 path; F32 is FP32 storage and arithmetic; F16 and BF16 are FP16 / BF16 storage of
+ * the fields and Krylov vectors with FP32 arithmetic. */
+typedef enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1, LQCD_PREC_F16 = 2, LQCD_PREC_BF16 = 3 } lqcd_prec;
 
 /* lqcd_wilson_apply flags (may be OR-ed only where stated) */
 #define LQCD_APPLY_M 0     /* out = M in,  M = 1 - kappa P                      (Eq. xyz556) */
@@ -76,6 +78,8 @@ typedef struct {
   int max_cycles;    /* restart cycles before LQCD_ERR_NOT_CONVERGED                         */
   int system;        /* LQCD_SYS_M or LQCD_SYS_MG5                                           */
   int prec;          /* lqcd_prec of the inner operator; LQCD_PREC_F64 for the plain path    */
+  double inner_tol;  /* mixed precision: relative residual of each inner solve (0 = default:
+                        5e-6 F32, 2e-2 F16, 1e-1 BF16)                                        */
 } lqcd_krylov_opts;
 
 typedef struct {
@@ -163,6 +167,18 @@ lqcd_status lqcd_pack_links_f32(lqcd_ctx *ctx, const double *links, float *out, 
 lqcd_status lqcd_wilson_apply_packed(lqcd_ctx *ctx, const float *links_packed, int recon, double kappa,
                                      const float *in, float *out, int nrhs, int flags, int rhs_per_thread);
 
+/* FP16 / BF16 fields (prec LQCD_PREC_F16 or LQCD_PREC_BF16) of the mixed-precision inner solver:
+ * the packed FP32 layout above with each float4 chunk stored as two FP16 or BF16 complex numbers
+ * (8 bytes), holding sigma * value with sigma = 2^floor(log2(sqrt(12 V))) so that the entries of a
+ * unit-norm field are of order one.  Buffers: nrhs * 24 V halves (2 bytes each), device.
+ * lqcd_pack_half / lqcd_unpack_half convert from / to canonical complex128 (sigma applied and
+ * removed); lqcd_wilson_apply_half applies the operator (flags as lqcd_wilson_apply) with packed
+ * FP32 links (lqcd_pack_links_f32) and FP32 arithmetic, in and out must not overlap. */
+lqcd_status lqcd_pack_half(lqcd_ctx *ctx, int prec, const double *in, void *out, int nrhs);
+lqcd_status lqcd_unpack_half(lqcd_ctx *ctx, int prec, const void *in, double *out, int nrhs);
+lqcd_status lqcd_wilson_apply_half(lqcd_ctx *ctx, int prec, const float *links_packed, int recon, double kappa,
+                                   const void *in, void *out, int nrhs, int flags);
+
 /* ---- a3 / a4: GMRES-DR and MINRES-DR (Sec. 5.3, 7, 8) --------------------------------- */
 
 /* GMRES-DR(m, k) for nrhs independent right-hand sides (each with its own Krylov basis).
@@ -187,9 +203,11 @@ lqcd_status lqcd_minresdr_solve(lqcd_ctx *ctx, const double *links, double kappa
 /* Solve A x = b for nrhs right-hand sides with GMRES-Proj over defl (made by one of the two
  * solvers above on the same A): each cycle is a minimum-residual projection over V_{k+1} and
  * Hbar_k followed by GMRES(opts->m).  opts->k is ignored.  b, x: device (nrhs * 12 V).
- * opts->prec = LQCD_PREC_F32 selects mixed precision: an FP64 defect-correction loop around the
- * same GMRES-Proj run with FP32 storage and arithmetic (inner relative residual 5e-6), stopping
- * on the FP64 true residual ||b - A x|| <= tol ||b||; opts->max_cycles bounds the inner cycles. */
+ * opts->prec = LQCD_PREC_F32, LQCD_PREC_F16 or LQCD_PREC_BF16 selects mixed precision: an FP64
+ * defect-correction loop around the same GMRES-Proj run in that storage precision with FP32
+ * arithmetic (Krylov basis and deflation space in that precision, the inner solution and residual
+ * in FP32; inner relative residual opts->inner_tol), stopping on the FP64 true residual
+ * ||b - A x|| <= tol ||b||; opts->max_cycles bounds the inner cycles. */
 lqcd_status lqcd_proj_solve(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl,
                             const double *b, double *x, int nrhs, const lqcd_krylov_opts *opts,
                             lqcd_solve_info *info);
@@ -287,8 +305,10 @@ typedef struct {
   double tol_special; /* super-convergence tolerance of the special right-hand side         */
   int max_cycles;
   int modes;          /* LQCD_SUB_* bit mask                                                 */
-  int prec;           /* LQCD_PREC_F64 (plain) or LQCD_PREC_F32 (mixed-precision noise solves;
-                         special solves, series, projections and contractions stay FP64)   */
+  int prec;           /* LQCD_PREC_F64 (plain) or LQCD_PREC_F32 / F16 / BF16 (mixed-precision
+                         noise solves; special solves, series, projections and contractions
+                         stay FP64)                                                         */
+  double inner_tol;   /* mixed precision: inner relative residual (0 = default, see above)   */
 } lqcd_est_opts;
 
 typedef struct {

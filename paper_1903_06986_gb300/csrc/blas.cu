@@ -2,11 +2,14 @@
 //
 // A "block" of nrhs vectors of length n is stored vector after vector; a multi-vector (a Krylov
 // basis) stores basis vector i of right-hand side r at V + i * vstride + r * vrs.  The kernels are
-// templates on the storage type: double2 (the FP64 path) or float2 (the FP32 inner solver of the
-// mixed-precision path, which accumulates each thread's terms in FP32 and reduces across threads
-// in FP64).  Every reduction is two-stage with a fixed order (per-block partial sums, then one
-// block per result), so results are reproducible run to run.
+// templates on the storage type: double2 (the FP64 path) or float2 / __half2 / __nv_bfloat162 (the
+// inner solver of the mixed-precision path, FP32 arithmetic; two-type forms combine a reduced-
+// precision basis with FP32 vectors).  Each thread accumulates its terms in the arithmetic type and
+// the cross-thread reduction is FP64.  Every reduction is two-stage with a fixed order (per-block
+// partial sums, then one block per result), so results are reproducible run to run.  FP16 / BF16
+// vectors hold store_sigma * value; the host passes the factors that undo it.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -15,22 +18,37 @@ namespace {
 constexpr int BT = 256;      // threads per block
 constexpr int GROUP = 8;     // basis vectors reduced together in multidot
 
-template <typename S> __device__ __forceinline__ S cz();
+// arithmetic type of a storage type
+template <typename S> struct ArithT { using T = float2; };
+template <> struct ArithT<double2> { using T = double2; };
+template <typename S> using Ar = typename ArithT<S>::T;
+
+__device__ __forceinline__ double2 ldc(double2 v) { return v; }
+__device__ __forceinline__ float2 ldc(float2 v) { return v; }
+__device__ __forceinline__ float2 ldc(__half2 v) { return __half22float2(v); }
+__device__ __forceinline__ float2 ldc(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+template <typename S> __device__ __forceinline__ S stc(Ar<S> v);
+template <> __device__ __forceinline__ double2 stc<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 stc<float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ __half2 stc<__half2>(float2 v) { return __float22half2_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat162 stc<__nv_bfloat162>(float2 v) { return __float22bfloat162_rn(v); }
+
+template <typename C> __device__ __forceinline__ C cz();
 template <> __device__ __forceinline__ double2 cz<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 cz<float2>() { return make_float2(0.f, 0.f); }
-template <typename S> __device__ __forceinline__ S from_d2(double2 v);
+template <typename C> __device__ __forceinline__ C from_d2(double2 v);
 template <> __device__ __forceinline__ double2 from_d2<double2>(double2 v) { return v; }
 template <> __device__ __forceinline__ float2 from_d2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
 __device__ __forceinline__ double2 to_d2(double2 v) { return v; }
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
 // acc += a * b and acc += conj(a) * b for double2 / float2
-template <typename S> __device__ __forceinline__ void gfma(S &acc, S a, S b) {
+template <typename C> __device__ __forceinline__ void gfma(C &acc, C a, C b) {
   acc.x = fma(a.x, b.x, acc.x);
   acc.x = fma(-a.y, b.y, acc.x);
   acc.y = fma(a.x, b.y, acc.y);
   acc.y = fma(a.y, b.x, acc.y);
 }
-template <typename S> __device__ __forceinline__ void gfma_conj(S &acc, S a, S b) {
+template <typename C> __device__ __forceinline__ void gfma_conj(C &acc, C a, C b) {
   acc.x = fma(a.x, b.x, acc.x);
   acc.x = fma(a.y, b.y, acc.x);
   acc.y = fma(a.x, b.y, acc.y);
@@ -51,41 +69,43 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
 // partial[(i * nrhs + r) * nchunk + c]; the last block to finish for right-hand side r (a counter
 // per r, reset by that block) adds the nchunk partials of every i in chunk order and writes
 // h[i * nrhs + r].  The result does not depend on block scheduling.
-template <typename S>
-__global__ void __launch_bounds__(BT) multidot_kernel(const S *__restrict__ V, long long vstride, long long vrs,
-                                                      int nvec, const S *__restrict__ w, long long n, int nrhs,
-                                                      int nchunk, double2 *__restrict__ partial,
+template <typename SV, typename SW>
+__global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, long long vstride, long long vrs,
+                                                      int nvec, const SW *__restrict__ w, long long n, int nrhs,
+                                                      int nchunk, double fac, double2 *__restrict__ partial,
                                                       unsigned *__restrict__ counters, double2 *__restrict__ h) {
+  using C = Ar<SW>;
+  static_assert(std::is_same<C, Ar<SV>>::value, "multidot: storage types of different arithmetic");
   const int r = blockIdx.y;
   const int c = blockIdx.x % nchunk;
   const int i0 = (blockIdx.x / nchunk) * GROUP;
   const long long chunk = (n + nchunk - 1) / nchunk;
   const long long e0 = c * chunk;
   const long long e1 = min(n, e0 + chunk);
-  const S *wr = w + r * n;
-  const S *vr = V + r * vrs;
+  const SW *wr = w + r * n;
+  const SV *vr = V + r * vrs;
   __shared__ double2 red[BT / 32][GROUP];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = min(GROUP, nvec - i0);
-  const S *vp[GROUP];
+  const SV *vp[GROUP];
 #pragma unroll
   for (int j = 0; j < GROUP; ++j) vp[j] = vr + (long long)(i0 + min(j, g - 1)) * vstride;
-  S acc[GROUP];
+  C acc[GROUP];
 #pragma unroll
-  for (int j = 0; j < GROUP; ++j) acc[j] = cz<S>();
+  for (int j = 0; j < GROUP; ++j) acc[j] = cz<C>();
   if (g == GROUP) {
     for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
-      const S wv = wr[e];
+      const C wv = ldc(wr[e]);
 #pragma unroll
-      for (int j = 0; j < GROUP; ++j) gfma_conj(acc[j], vp[j][e], wv);
+      for (int j = 0; j < GROUP; ++j) gfma_conj(acc[j], ldc(vp[j][e]), wv);
     }
   } else {
     for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
-      const S wv = wr[e];
+      const C wv = ldc(wr[e]);
 #pragma unroll
       for (int j = 0; j < GROUP; ++j)
-        if (j < g) gfma_conj(acc[j], vp[j][e], wv);
+        if (j < g) gfma_conj(acc[j], ldc(vp[j][e]), wv);
     }
   }
 #pragma unroll
@@ -109,24 +129,25 @@ __global__ void __launch_bounds__(BT) multidot_kernel(const S *__restrict__ V, l
     const double2 *pp = partial + ((long long)i * nrhs + r) * nchunk;
     double2 sum = make_double2(0.0, 0.0);
     for (int q = 0; q < nchunk; ++q) sum = cadd(sum, __ldcg(pp + q));
-    h[(long long)i * nrhs + r] = sum;
+    h[(long long)i * nrhs + r] = cscale(sum, fac);
   }
   if (threadIdx.x == 0) counters[r] = 0u;
 }
 
 // Single-launch batched norms ||x^r||, same last-block scheme as multidot_kernel.
 template <typename S>
-__global__ void __launch_bounds__(BT) norm_kernel(const S *__restrict__ x, long long n, double *__restrict__ partial,
-                                                  unsigned *__restrict__ counters, double *__restrict__ out) {
+__global__ void __launch_bounds__(BT) norm_kernel(const S *__restrict__ x, long long n, double fac,
+                                                  double *__restrict__ partial, unsigned *__restrict__ counters,
+                                                  double *__restrict__ out) {
   const int r = blockIdx.y;
   const int nb = gridDim.x;
   const long long chunk = (n + nb - 1) / nb;
   const long long e0 = blockIdx.x * chunk;
   const long long e1 = min(n, e0 + chunk);
   const S *xr = x + r * n;
-  decltype(S().x) a = 0;
+  decltype(Ar<S>().x) a = 0;
   for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
-    const S v = xr[e];
+    const Ar<S> v = ldc(xr[e]);
     a = fma(v.x, v.x, a);
     a = fma(v.y, v.y, a);
   }
@@ -149,39 +170,41 @@ __global__ void __launch_bounds__(BT) norm_kernel(const S *__restrict__ x, long 
   __threadfence();
   double sum = 0.0;
   for (int q = 0; q < nb; ++q) sum += __ldcg(partial + (long long)r * nb + q);
-  out[r] = sqrt(sum);
+  out[r] = sqrt(sum) * fac;
   counters[r] = 0u;
 }
 
-// w^r += sign * sum_i V_i^r h[i * nrhs + r]; the coefficients of this right-hand side are staged in
-// shared memory (already scaled by sign and converted to the storage precision).
+// w^r += sign * fac * sum_i V_i^r h[i * nrhs + r]; the coefficients of this right-hand side are
+// staged in shared memory (scaled and converted to the arithmetic type).
 constexpr int AXPY_MAXV = 512;
-template <typename S>
-__global__ void __launch_bounds__(BT) multiaxpy_kernel(const S *__restrict__ V, long long vstride,
+template <typename SV, typename SW>
+__global__ void __launch_bounds__(BT) multiaxpy_kernel(const SV *__restrict__ V, long long vstride,
                                                        long long vrs, int nvec, const double2 *__restrict__ h,
-                                                       double sign, S *__restrict__ w, long long n, int nrhs) {
-  __shared__ S coef[AXPY_MAXV];
+                                                       double sign, SW *__restrict__ w, long long n, int nrhs) {
+  using C = Ar<SW>;
+  __shared__ C coef[AXPY_MAXV];
   const int r = blockIdx.y;
-  for (int i = threadIdx.x; i < nvec; i += BT) coef[i] = from_d2<S>(cscale(h[(long long)i * nrhs + r], sign));
+  for (int i = threadIdx.x; i < nvec; i += BT) coef[i] = from_d2<C>(cscale(h[(long long)i * nrhs + r], sign));
   __syncthreads();
   const long long e = (long long)blockIdx.x * BT + threadIdx.x;
   if (e >= n) return;
-  const S *vp = V + r * vrs + e;
-  S acc = w[r * n + e];
-  for (int i = 0; i < nvec; ++i, vp += vstride) gfma(acc, *vp, coef[i]);
-  w[r * n + e] = acc;
+  const SV *vp = V + r * vrs + e;
+  C acc = ldc(w[r * n + e]);
+  for (int i = 0; i < nvec; ++i, vp += vstride) gfma(acc, ldc(*vp), coef[i]);
+  w[r * n + e] = stc<SW>(acc);
 }
 
 constexpr int CT = 8;           // output columns per pass in combine
 constexpr int COMB_MAXV = 256;  // basis vectors of one combine (coefficient tile in shared memory)
-// out_c^r = sum_i V_i^r C[(i * ncol + c) * nrhs + r]; a tile of CT columns of coefficients for this
-// right-hand side is staged in shared memory per pass.
-template <typename S>
-__global__ void __launch_bounds__(BT) combine_kernel(const S *__restrict__ V, long long vstride,
-                                                     long long vrs, int nvec, const double2 *__restrict__ C,
-                                                     int ncol, S *__restrict__ out, long long ostride,
+// out_c^r = fac * sum_i V_i^r C[(i * ncol + c) * nrhs + r]; a tile of CT columns of coefficients for
+// this right-hand side is staged in shared memory per pass.
+template <typename SV, typename SO>
+__global__ void __launch_bounds__(BT) combine_kernel(const SV *__restrict__ V, long long vstride,
+                                                     long long vrs, int nvec, const double2 *__restrict__ Cf,
+                                                     int ncol, double fac, SO *__restrict__ out, long long ostride,
                                                      long long n, int nrhs) {
-  __shared__ S coef[COMB_MAXV * CT];
+  using C = Ar<SO>;
+  __shared__ C coef[COMB_MAXV * CT];
   const long long e = (long long)blockIdx.x * BT + threadIdx.x;
   const int r = blockIdx.y;
   for (int c0 = 0; c0 < ncol; c0 += CT) {
@@ -189,22 +212,22 @@ __global__ void __launch_bounds__(BT) combine_kernel(const S *__restrict__ V, lo
     __syncthreads();
     for (int q = threadIdx.x; q < nvec * CT; q += BT) {
       const int i = q / CT, j = q % CT;
-      coef[q] = (j < g) ? from_d2<S>(C[((long long)i * ncol + c0 + j) * nrhs + r]) : cz<S>();
+      coef[q] = (j < g) ? from_d2<C>(cscale(Cf[((long long)i * ncol + c0 + j) * nrhs + r], fac)) : cz<C>();
     }
     __syncthreads();
     if (e >= n) continue;
-    S acc[CT];
+    C acc[CT];
 #pragma unroll
-    for (int j = 0; j < CT; ++j) acc[j] = cz<S>();
-    const S *vp = V + r * vrs + e;
+    for (int j = 0; j < CT; ++j) acc[j] = cz<C>();
+    const SV *vp = V + r * vrs + e;
     for (int i = 0; i < nvec; ++i, vp += vstride) {
-      const S v = *vp;
+      const C v = ldc(*vp);
 #pragma unroll
       for (int j = 0; j < CT; ++j) gfma(acc[j], v, coef[i * CT + j]);
     }
 #pragma unroll
     for (int j = 0; j < CT; ++j)
-      if (j < g) out[(long long)(c0 + j) * ostride + r * n + e] = acc[j];
+      if (j < g) out[(long long)(c0 + j) * ostride + r * n + e] = stc<SO>(acc[j]);
   }
 }
 
@@ -215,20 +238,31 @@ __global__ void invscale_kernel(S *__restrict__ x, const double *__restrict__ s,
   if (e >= n) return;
   const double d = s[r];
   const double f = d > 0.0 ? 1.0 / d : 0.0;
-  S v = x[r * n + e];
+  Ar<S> v = ldc(x[r * n + e]);
   v.x *= f;
   v.y *= f;
-  x[r * n + e] = v;
+  x[r * n + e] = stc<S>(v);
 }
 
-template <typename S>
-__global__ void copy_kernel(const S *__restrict__ x, S *__restrict__ y, long long n) {
-  for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT) y[e] = x[e];
+// y = fac * x with conversion between storage types (fac = 1 for a plain copy)
+template <typename SX, typename SY>
+__global__ void copy_kernel(const SX *__restrict__ x, SY *__restrict__ y, long long n, double fac) {
+  for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT) {
+    if constexpr (std::is_same<SX, SY>::value) {
+      y[e] = x[e];
+    } else {
+      Ar<SY> v = ldc(x[e]);
+      v.x *= fac;
+      v.y *= fac;
+      y[e] = stc<SY>(v);
+    }
+  }
 }
 
 template <typename S>
 __global__ void zero_kernel(S *__restrict__ y, long long n) {
-  for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT) y[e] = cz<S>();
+  for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT)
+    y[e] = stc<S>(cz<Ar<S>>());
 }
 
 // y^r = float(x^r / s[r]): FP64 residual block -> normalised FP32 right-hand side
@@ -346,10 +380,12 @@ int partial_blocks(lqcd_ctx *ctx, long long n, int nrhs) {
 
 }  // namespace
 
-template <typename S>
-lqcd_status blas_copy(lqcd_ctx *ctx, const S *x, S *y, long long n) {
+template <typename SX, typename SY>
+lqcd_status blas_copy(lqcd_ctx *ctx, const SX *x, SY *y, long long n) {
+  static_assert(std::is_same<SX, SY>::value || std::is_same<Ar<SX>, Ar<SY>>::value, "copy: incompatible types");
+  const double fac = store_sigma<SY>(ctx->N) / store_sigma<SX>(ctx->N);
   kbegin(ctx);
-  copy_kernel<S><<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(x, y, n);
+  copy_kernel<SX, SY><<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(x, y, n, fac);
   return launch_check(ctx, "copy_kernel", K_BLAS1, (double)n);
 }
 
@@ -396,12 +432,12 @@ lqcd_status blas_norms(lqcd_ctx *ctx, const S *x, long long n, int nrhs, double 
   LQCD_TRY(ws_get(ctx, WS_SCAL, sizeof(double) * (size_t)nb * nrhs, &p));
   LQCD_TRY(reduction_counters(ctx, nrhs, &cnt));
   kbegin(ctx);
-  norm_kernel<S><<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(x, n, (double *)p, cnt, norms);
+  norm_kernel<S><<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(x, n, 1.0 / store_sigma<S>(ctx->N), (double *)p, cnt, norms);
   return launch_check(ctx, "norm_kernel", K_NORM, (double)n * nrhs);
 }
 
-template <typename S>
-lqcd_status blas_multidot(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const S *w,
+template <typename SV, typename SW>
+lqcd_status blas_multidot(lqcd_ctx *ctx, const SV *V, long long vstride, long long vrs, int nvec, const SW *w,
                           long long n, int nrhs, double2 *h) {
   if (nvec <= 0) return LQCD_OK;
   // element chunks of at least 8 elements per thread; enough blocks (chunks x vector groups x
@@ -415,29 +451,34 @@ lqcd_status blas_multidot(lqcd_ctx *ctx, const S *V, long long vstride, long lon
   unsigned *cnt = nullptr;
   LQCD_TRY(ws_get(ctx, WS_PARTIAL, sizeof(double2) * (size_t)nchunk * nrhs * nvec, &p));
   LQCD_TRY(reduction_counters(ctx, nrhs, &cnt));
+  const double fac = 1.0 / (store_sigma<SV>(ctx->N) * store_sigma<SW>(ctx->N));
   kbegin(ctx);
-  multidot_kernel<S><<<dim3(nchunk * ngroup, nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, nchunk,
-                                                                         (double2 *)p, cnt, h);
+  multidot_kernel<SV, SW><<<dim3(nchunk * ngroup, nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs,
+                                                                                nchunk, fac, (double2 *)p, cnt, h);
   return launch_check(ctx, "multidot_kernel", K_DOT, (double)n * nrhs * nvec);
 }
 
-template <typename S>
-lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const double2 *h,
-                           double sign, S *w, long long n, int nrhs) {
+template <typename SV, typename SW>
+lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const SV *V, long long vstride, long long vrs, int nvec, const double2 *h,
+                           double sign, SW *w, long long n, int nrhs) {
   if (nvec <= 0) return LQCD_OK;
   if (nvec > AXPY_MAXV) return set_err(ctx, LQCD_ERR_INVALID_ARG, "multiaxpy: at most %d vectors", AXPY_MAXV);
+  const double fac = sign * store_sigma<SW>(ctx->N) / store_sigma<SV>(ctx->N);
   kbegin(ctx);
-  multiaxpy_kernel<S><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, h, sign, w, n, nrhs);
+  multiaxpy_kernel<SV, SW><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, h, fac, w, n,
+                                                                                nrhs);
   return launch_check(ctx, "multiaxpy_kernel", K_AXPY, (double)n * nrhs * nvec);
 }
 
-template <typename S>
-lqcd_status blas_combine(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const double2 *C,
-                         int ncol, S *out, long long ostride, long long n, int nrhs) {
+template <typename SV, typename SO>
+lqcd_status blas_combine(lqcd_ctx *ctx, const SV *V, long long vstride, long long vrs, int nvec, const double2 *C,
+                         int ncol, SO *out, long long ostride, long long n, int nrhs) {
   if (ncol <= 0) return LQCD_OK;
   if (nvec > COMB_MAXV) return set_err(ctx, LQCD_ERR_INVALID_ARG, "combine: at most %d vectors", COMB_MAXV);
+  const double fac = store_sigma<SO>(ctx->N) / store_sigma<SV>(ctx->N);
   kbegin(ctx);
-  combine_kernel<S><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, C, ncol, out, ostride, n, nrhs);
+  combine_kernel<SV, SO><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, C, ncol, fac, out,
+                                                                              ostride, n, nrhs);
   return launch_check(ctx, "combine_kernel", K_COMBINE, (double)n * nrhs * nvec * ncol);
 }
 
@@ -467,18 +508,29 @@ lqcd_status blas_to_f32(lqcd_ctx *ctx, const double2 *x, float2 *y, long long n)
 }
 
 #define LQCD_BLAS_INSTANTIATE(S)                                                                               \
-  template lqcd_status blas_copy<S>(lqcd_ctx *, const S *, S *, long long);                                     \
+  template lqcd_status blas_copy<S, S>(lqcd_ctx *, const S *, S *, long long);                                  \
   template lqcd_status blas_zero<S>(lqcd_ctx *, S *, long long);                                                \
   template lqcd_status blas_norms<S>(lqcd_ctx *, const S *, long long, int, double *);                          \
-  template lqcd_status blas_multidot<S>(lqcd_ctx *, const S *, long long, long long, int, const S *, long long,  \
-                                        int, double2 *);                                                        \
-  template lqcd_status blas_multiaxpy<S>(lqcd_ctx *, const S *, long long, long long, int, const double2 *,     \
-                                         double, S *, long long, int);                                          \
-  template lqcd_status blas_combine<S>(lqcd_ctx *, const S *, long long, long long, int, const double2 *, int,  \
-                                       S *, long long, long long, int);                                         \
   template lqcd_status blas_invscale<S>(lqcd_ctx *, S *, const double *, long long, int);
+#define LQCD_BLAS_INSTANTIATE2(SV, SW)                                                                         \
+  template lqcd_status blas_multidot<SV, SW>(lqcd_ctx *, const SV *, long long, long long, int, const SW *,     \
+                                             long long, int, double2 *);                                       \
+  template lqcd_status blas_multiaxpy<SV, SW>(lqcd_ctx *, const SV *, long long, long long, int, const double2 *, \
+                                              double, SW *, long long, int);                                   \
+  template lqcd_status blas_combine<SV, SW>(lqcd_ctx *, const SV *, long long, long long, int, const double2 *,  \
+                                            int, SW *, long long, long long, int);
 LQCD_BLAS_INSTANTIATE(double2)
 LQCD_BLAS_INSTANTIATE(float2)
+LQCD_BLAS_INSTANTIATE(__half2)
+LQCD_BLAS_INSTANTIATE(__nv_bfloat162)
+LQCD_BLAS_INSTANTIATE2(double2, double2)
+LQCD_BLAS_INSTANTIATE2(float2, float2)
+LQCD_BLAS_INSTANTIATE2(__half2, __half2)
+LQCD_BLAS_INSTANTIATE2(__half2, float2)
+LQCD_BLAS_INSTANTIATE2(__nv_bfloat162, __nv_bfloat162)
+LQCD_BLAS_INSTANTIATE2(__nv_bfloat162, float2)
+template lqcd_status blas_copy<float2, __half2>(lqcd_ctx *, const float2 *, __half2 *, long long);
+template lqcd_status blas_copy<float2, __nv_bfloat162>(lqcd_ctx *, const float2 *, __nv_bfloat162 *, long long);
 
 lqcd_status noise_launch(lqcd_ctx *ctx, uint64_t seed, uint32_t first, int nrhs, double2 *out) {
   kbegin(ctx);

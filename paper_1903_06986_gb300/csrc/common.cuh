@@ -1,8 +1,11 @@
 // Shared definitions of the liblqcd CUDA sources: context, status plumbing, complex helpers.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -151,12 +154,34 @@ lqcd_status wilson_launch_packed(lqcd_ctx *ctx, const float4 *U, int recon, doub
 lqcd_status pack_f32(lqcd_ctx *ctx, const double2 *x, const double *scale, float4 *y, int nrhs);
 lqcd_status unpack_f32(lqcd_ctx *ctx, const float4 *c, const double *scale, double2 *x, int nrhs);
 lqcd_status pack_links_f32(lqcd_ctx *ctx, const double2 *U, float4 *P, int recon);
+// The same operator and packing with FP16 / BF16 fields (S = __half2 or __nv_bfloat162; FP32 links
+// and arithmetic): the packed layout keeps the FP32 element order, each float4 chunk becoming an
+// 8-byte pair of S, so FP32 and reduced-precision vectors of one solve index alike.
+template <typename S>
+lqcd_status wilson_launch_packed_lp(lqcd_ctx *ctx, const float4 *U, int recon, double kappa, const S *in, S *out,
+                                   int nrhs, int flags);
+template <typename S> lqcd_status pack_lp(lqcd_ctx *ctx, const double2 *x, const double *scale, S *y, int nrhs);
+template <typename S> lqcd_status unpack_lp(lqcd_ctx *ctx, const S *c, const double *scale, double2 *x, int nrhs);
 // FP32 storage and arithmetic (links converted to FP32 by the caller)
 lqcd_status wilson_launch_f32(lqcd_ctx *ctx, const float2 *U, double kappa, const float2 *in, float2 *out,
                               int nrhs, int flags);
-// Batched level-1/level-2 kernels (blas.cu).  Templates are instantiated for S = double2 (FP64
-// path) and S = float2 (FP32 inner solver); coefficients and reductions are always FP64.
-template <typename S> lqcd_status blas_copy(lqcd_ctx *ctx, const S *x, S *y, long long n);
+// ----- reduced-precision storage -----------------------------------------------------------
+// Complex storage types of the inner solver: float2 (FP32), __half2 (FP16) and __nv_bfloat162
+// (BF16); arithmetic on all three is FP32.  A field stored in FP16 or BF16 holds sigma * value with
+// sigma = 2^floor(log2(sqrt(N))) for fields of N = 12 V components, so the entries of a unit
+// vector are of order one: far from the FP16 overflow (65504) and subnormal (6e-5) ranges.  Every
+// level-1/2 kernel and the packing kernels account for sigma; the operator, being linear, ignores it.
+template <typename S> struct StoreScaled { static constexpr bool value = false; };
+template <> struct StoreScaled<__half2> { static constexpr bool value = true; };
+template <> struct StoreScaled<__nv_bfloat162> { static constexpr bool value = true; };
+static inline double half_sigma(long long N) { return std::ldexp(1.0, (int)std::floor(0.5 * std::log2((double)N))); }
+template <typename S> inline double store_sigma(long long N) { return StoreScaled<S>::value ? half_sigma(N) : 1.0; }
+
+// Batched level-1/level-2 kernels (blas.cu).  Templates are instantiated for double2 (FP64 path)
+// and for the inner-solver storage types float2, __half2, __nv_bfloat162 (two-type forms mix a
+// reduced-precision basis with FP32 vectors); coefficients and cross-thread reductions are FP64.
+// Vectors of __half2 / __nv_bfloat162 are fields of ctx->N components scaled by store_sigma.
+template <typename SX, typename SY> lqcd_status blas_copy(lqcd_ctx *ctx, const SX *x, SY *y, long long n);
 template <typename S> lqcd_status blas_zero(lqcd_ctx *ctx, S *y, long long n);
 lqcd_status blas_g5(lqcd_ctx *ctx, const double2 *x, double2 *y, int nrhs);
 // t = b - t
@@ -166,17 +191,17 @@ template <typename S> lqcd_status blas_norms(lqcd_ctx *ctx, const S *x, long lon
 // Basis vector i of right-hand side r is V_i^r = V + i*vstride + r*vrs (vrs = 0: one basis shared
 // by every right-hand side); w^r = w + r*n.
 // h[i*nrhs + r] = <V_i^r, w^r> for i < nvec
-template <typename S>
-lqcd_status blas_multidot(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const S *w,
+template <typename SV, typename SW>
+lqcd_status blas_multidot(lqcd_ctx *ctx, const SV *V, long long vstride, long long vrs, int nvec, const SW *w,
                           long long n, int nrhs, double2 *h);
 // w^r += sign * sum_i V_i^r h[i*nrhs + r]
-template <typename S>
-lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const double2 *h,
-                           double sign, S *w, long long n, int nrhs);
+template <typename SV, typename SW>
+lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const SV *V, long long vstride, long long vrs, int nvec, const double2 *h,
+                           double sign, SW *w, long long n, int nrhs);
 // out_c^r = out + c*ostride + r*n = sum_i V_i^r C[(i*ncol + c)*nrhs + r] for c < ncol (no aliasing)
-template <typename S>
-lqcd_status blas_combine(lqcd_ctx *ctx, const S *V, long long vstride, long long vrs, int nvec, const double2 *C,
-                         int ncol, S *out, long long ostride, long long n, int nrhs);
+template <typename SV, typename SO>
+lqcd_status blas_combine(lqcd_ctx *ctx, const SV *V, long long vstride, long long vrs, int nvec, const double2 *C,
+                         int ncol, SO *out, long long ostride, long long n, int nrhs);
 // x^r *= 1 / s[r] (s device); zero vector if s[r] == 0
 template <typename S> lqcd_status blas_invscale(lqcd_ctx *ctx, S *x, const double *s, long long n, int nrhs);
 // y += a x with a host scalar a

@@ -215,8 +215,8 @@ extern "C" lqcd_status lqcd_loop_derivs(lqcd_ctx *ctx, const double *links, doub
   if (o->nnoise < 1 || o->block < 1 || o->m < 2 || o->k < 1 || o->k >= o->m || o->K < 1 || o->K > 64 ||
       !(o->tol > 0) || !(o->tol_special > 0) || o->max_cycles < 1 || !(kappa != 0.0))
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_derivs: bad options");
-  if (o->prec != LQCD_PREC_F64 && o->prec != LQCD_PREC_F32)
-    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_derivs: prec must be LQCD_PREC_F64 or LQCD_PREC_F32");
+  if (o->prec < LQCD_PREC_F64 || o->prec > LQCD_PREC_BF16)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_derivs: prec must be one of LQCD_PREC_*");
   const double t0 = now_s();
   const double2 *U = (const double2 *)links;
   const int Lt = ctx->dims[3];
@@ -268,7 +268,7 @@ extern "C" lqcd_status lqcd_loop_derivs(lqcd_ctx *ctx, const double *links, doub
   LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)bw * 9 * Lt * 4, (void **)&cdv));
   if (out->link_grad) LQCD_CUDA(ctx, cudaMemsetAsync(out->link_grad, 0, sizeof(double2) * (size_t)ctx->V * 32, ctx->stream));
   if (out->grad_links) LQCD_CUDA(ctx, cudaMemsetAsync(out->grad_links, 0, sizeof(double2) * (size_t)ctx->V * 36, ctx->stream));
-  lqcd_krylov_opts po{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec};
+  lqcd_krylov_opts po{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec, o->inner_tol};
   std::vector<cd> per((size_t)2 * nn * 9, cd(0.0, 0.0));
   std::vector<cd> ck(o->K);
   for (int k = 0; k < o->K; ++k) ck[k] = cd((double)k / kappa, 0.0);  // sum (k/kappa)(kappa P)^k = d/dkappa sum (kappa P)^k

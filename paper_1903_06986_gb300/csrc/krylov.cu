@@ -56,6 +56,18 @@ template <> struct OpT<float2> {
     return wilson_launch_packed(ctx, U, recon, kappa, (const float4 *)in, (float4 *)out, nrhs, flags, 0);
   }
 };
+// FP16 / BF16 fields of the inner solver: the same packed operator on reduced-precision storage
+template <typename S> struct OpLP {
+  const float4 *U;
+  int recon;
+  double kappa;
+  int flags;
+  lqcd_status apply(lqcd_ctx *ctx, const S *in, S *out, int nrhs) const {
+    return wilson_launch_packed_lp<S>(ctx, U, recon, kappa, in, out, nrhs, flags);
+  }
+};
+template <> struct OpT<__half2> : OpLP<__half2> {};
+template <> struct OpT<__nv_bfloat162> : OpLP<__nv_bfloat162> {};
 using Op = OpT<double2>;
 
 lqcd_status apply_op(lqcd_ctx *ctx, const Op &op, const double2 *in, double2 *out, int nrhs) {
@@ -252,7 +264,7 @@ lqcd_status check_opts(lqcd_ctx *ctx, const lqcd_krylov_opts *o, int nrhs) {
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "need 0 <= k < m <= 1000 (m=%d k=%d)", o->m, o->k);
   if (!(o->tol > 0.0) || o->max_cycles < 1) return set_err(ctx, LQCD_ERR_INVALID_ARG, "need tol > 0 and max_cycles >= 1");
   if (nrhs < 1 || nrhs > 4096) return set_err(ctx, LQCD_ERR_INVALID_ARG, "nrhs %d out of range", nrhs);
-  if (o->prec != LQCD_PREC_F64 && o->prec != LQCD_PREC_F32) return set_err(ctx, LQCD_ERR_INVALID_ARG, "bad precision");
+  if (o->prec < LQCD_PREC_F64 || o->prec > LQCD_PREC_BF16) return set_err(ctx, LQCD_ERR_INVALID_ARG, "bad precision");
   return LQCD_OK;
 }
 
@@ -491,15 +503,17 @@ struct ProjResult {
   bool converged = false;
 };
 
-template <typename S>
-lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const S *Vd, const Mat &Hk, const S *b, S *x, int nrhs, int m,
+// S: storage of the Krylov basis and of the deflation space Vd; SX: storage of b, x and the
+// residual (S itself, or FP32 under an FP16 / BF16 basis).
+template <typename S, typename SX = S>
+lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const S *Vd, const Mat &Hk, const SX *b, SX *x, int nrhs, int m,
                      double tol, int max_cycles, bool check_true, ProjResult &res) {
   const int k = Hk.c;
   const long long N = ctx->N, vs = (long long)nrhs * N;
   WorkspaceT<S> W;
   LQCD_TRY(get_workspace(ctx, std::max(m, k + 1), 0, nrhs, W));
-  S *r_dev;
-  LQCD_TRY(ws_get(ctx, WS_TMP1, sizeof(S) * (size_t)vs, (void **)&r_dev));
+  SX *r_dev;
+  LQCD_TRY(ws_get(ctx, WS_TMP1, sizeof(SX) * (size_t)vs, (void **)&r_dev));
   std::vector<Rhs> R(nrhs);
   LQCD_TRY(blas_zero(ctx, x, vs));
   LQCD_TRY(blas_copy(ctx, b, r_dev, vs));
@@ -579,7 +593,7 @@ lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const S *Vd, const Mat &Hk
       if (!check_true) break;
       // confirm with the true residual; continue from it where the recursion drifted
       std::vector<double> rel;
-      if constexpr (std::is_same<S, double2>::value) {
+      if constexpr (std::is_same<S, double2>::value && std::is_same<SX, double2>::value) {
         LQCD_TRY(true_residuals(ctx, op, b, x, W.tmp, nrhs, R, rel));
       } else {
         break;
@@ -599,7 +613,7 @@ lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const S *Vd, const Mat &Hk
     for (int r = 0; r < nrhs; ++r)
       if (R[r].active && R[r].rel <= tol) R[r].active = false;
   }
-  if constexpr (std::is_same<S, double2>::value) {
+  if constexpr (std::is_same<S, double2>::value && std::is_same<SX, double2>::value) {
     if (!all_conv && check_true) {
       std::vector<double> rel;
       LQCD_TRY(true_residuals(ctx, op, b, x, W.tmp, nrhs, R, rel));
@@ -645,34 +659,54 @@ lqcd_status proj_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const 
                        : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "GMRES-Proj: no convergence in %d cycles (rel %.3e)", res.cycles, res.worst);
 }
 
-// Mixed precision: FP64 defect correction around FP32 GMRES-Proj.  Each outer step solves
-// M e = r / ||r|| approximately with FP32 storage and arithmetic (inner relative residual
-// INNER_TOL), adds ||r|| e to the FP64 solution, and recomputes the true residual r = b - M x with
-// the FP64 operator; it stops when every right-hand side has ||r|| <= tol ||b|| in FP64.
-constexpr double INNER_TOL = 5e-6;
+// Mixed precision: FP64 defect correction around a reduced-precision GMRES-Proj.  Each outer step
+// solves M e = r / ||r|| approximately (inner relative residual inner_tol) with FP32 arithmetic, the
+// Krylov basis and the deflation space stored as S (FP32, FP16 or BF16) and e, r in FP32; it adds
+// ||r|| e to the FP64 solution and recomputes the true residual r = b - M x with the FP64
+// operator, and stops when every right-hand side has ||r|| <= tol ||b|| in FP64.
 constexpr int MAX_OUTER = 40;
 
+double default_inner_tol(int prec) {
+  // a few tens of the storage unit roundoff for FP16 (2^-11) and BF16 (2^-8): the Arnoldi relation
+  // of a basis stored in them holds only to about that level, so tighter inner solves mostly
+  // spend cycles the outer correction discards (measured on 8^3 x 16 at kappa 0.157); FP32 inner
+  // solves pay off down to 5e-6
+  return prec == LQCD_PREC_F16 ? 2e-2 : prec == LQCD_PREC_BF16 ? 1e-1 : 5e-6;
+}
+
+template <typename S>
 lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const double2 *b, double2 *x, int nrhs,
                        const lqcd_krylov_opts *o, lqcd_solve_info *info) {
   const double t0 = now_s();
   LQCD_TRY(check_opts(ctx, o, nrhs));
   if (!defl || !defl->V || !defl->Hbar_dev) return set_err(ctx, LQCD_ERR_INVALID_ARG, "GMRES-Proj needs a solver-made deflation space");
+  if (!(o->inner_tol >= 0.0 && o->inner_tol < 1.0)) return set_err(ctx, LQCD_ERR_INVALID_ARG, "inner_tol must be in [0, 1)");
+  const double inner_tol = o->inner_tol > 0.0 ? o->inner_tol : default_inner_tol(o->prec);
   const long long N = ctx->N, vs = (long long)nrhs * N;
   const int k = defl->k;
-  float2 *V32, *r32, *e32;
+  S *Vlp;
+  float2 *r32, *e32;
   float4 *U32;
   double2 *r;
   double *sc;
   const int recon = ctx->recon;
   LQCD_TRY(ws_get(ctx, WS_MIX_U, sizeof(float) * (size_t)ctx->V * 4 * (recon == 12 ? 12 : 20), (void **)&U32));
-  LQCD_TRY(ws_get(ctx, WS_MIX_V, sizeof(float2) * (size_t)(k + 1) * N, (void **)&V32));
+  LQCD_TRY(ws_get(ctx, WS_MIX_V, sizeof(S) * (size_t)(k + 1) * N, (void **)&Vlp));
   LQCD_TRY(ws_get(ctx, WS_MIX_R32, sizeof(float2) * (size_t)vs, (void **)&r32));
   LQCD_TRY(ws_get(ctx, WS_MIX_E32, sizeof(float2) * (size_t)vs, (void **)&e32));
   LQCD_TRY(ws_get(ctx, WS_MIX_R, sizeof(double2) * (size_t)vs, (void **)&r));
   LQCD_TRY(ws_get(ctx, WS_MIX_S, sizeof(double) * (size_t)nrhs, (void **)&sc));
   LQCD_TRY(pack_links_f32(ctx, op.U, U32, recon));
-  LQCD_TRY(pack_f32(ctx, defl->V, nullptr, (float4 *)V32, k + 1));
-  const OpT<float2> op32{U32, recon, op.kappa, op.flags};
+  if constexpr (std::is_same<S, float2>::value) {
+    LQCD_TRY(pack_f32(ctx, defl->V, nullptr, (float4 *)Vlp, k + 1));
+  } else {
+    LQCD_TRY(pack_lp<S>(ctx, defl->V, nullptr, Vlp, k + 1));
+  }
+  OpT<S> opl;
+  opl.U = U32;
+  opl.recon = recon;
+  opl.kappa = op.kappa;
+  opl.flags = op.flags;
   const Mat Hk = defl_hbar(defl);
   LQCD_TRY(blas_zero(ctx, x, vs));
   LQCD_TRY(blas_copy(ctx, b, r, vs));
@@ -702,8 +736,8 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
     LQCD_CUDA(ctx, cudaMemcpyAsync(sc, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
     LQCD_TRY(pack_f32(ctx, r, sc, (float4 *)r32, nrhs));
     ProjResult pr;
-    LQCD_TRY(proj_run<float2>(ctx, op32, V32, Hk, r32, e32, nrhs, o->m, INNER_TOL,
-                              std::max(1, o->max_cycles - inner_cycles), false, pr));
+    LQCD_TRY((proj_run<S, float2>(ctx, opl, Vlp, Hk, r32, e32, nrhs, o->m, inner_tol,
+                                  std::max(1, o->max_cycles - inner_cycles), false, pr)));
     inner_cycles += pr.cycles;
     matvecs += pr.matvecs;
     LQCD_TRY(unpack_f32(ctx, (const float4 *)e32, sc, x, nrhs));
@@ -723,11 +757,18 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
               : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "mixed GMRES-Proj: no convergence after %d outer steps (rel %.3e)", outer, worst);
 }
 
+lqcd_status mixed_dispatch(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const double2 *b, double2 *x, int nrhs,
+                           const lqcd_krylov_opts *o, lqcd_solve_info *info) {
+  if (o->prec == LQCD_PREC_F16) return mixed_core<__half2>(ctx, op, defl, b, x, nrhs, o, info);
+  if (o->prec == LQCD_PREC_BF16) return mixed_core<__nv_bfloat162>(ctx, op, defl, b, x, nrhs, o, info);
+  return mixed_core<float2>(ctx, op, defl, b, x, nrhs, o, info);
+}
+
 lqcd_status proj_core_entry(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, const double2 *b,
                             double2 *x, int nrhs, const lqcd_krylov_opts *o, lqcd_solve_info *info) {
   const int sys = defl->hermitian ? LQCD_SYS_MG5 : o->system;
   Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, LQCD_PREC_F64, 0ull};
-  if (o->prec == LQCD_PREC_F32) return mixed_core(ctx, op, defl, b, x, nrhs, o, info);
+  if (o->prec != LQCD_PREC_F64) return mixed_dispatch(ctx, op, defl, b, x, nrhs, o, info);
   return proj_core(ctx, op, defl, b, x, nrhs, o, info);
 }
 
@@ -751,6 +792,8 @@ lqcd_status gmresdr_entry(lqcd_ctx *ctx, const double *links, double kappa, cons
   if (defl_out) *defl_out = nullptr;
   const int sys = hermitian ? LQCD_SYS_MG5 : opts->system;
   if (sys != LQCD_SYS_M && sys != LQCD_SYS_MG5) return set_err(ctx, LQCD_ERR_INVALID_ARG, "bad system %d", sys);
+  if (opts->prec != LQCD_PREC_F64 && opts->prec != LQCD_PREC_F32)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "GMRES-DR / MINRES-DR: prec must be LQCD_PREC_F64 or LQCD_PREC_F32");
   Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, opts->prec, 0ull};
   std::vector<lqcd_defl *> defls;
   const lqcd_status st = gmresdr_core(ctx, op, (const double2 *)b, (double2 *)x, nrhs, opts,

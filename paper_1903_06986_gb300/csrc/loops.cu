@@ -668,8 +668,8 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
   if (o->nnoise < 1 || o->block < 1 || o->m < 2 || o->k < 1 || o->k >= o->m || o->K < 1 || o->npoly < 0 ||
       o->npoly > 63 || o->K > 64 || !(o->tol > 0) || !(o->tol_special > 0) || o->max_cycles < 1)
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: bad options");
-  if (o->prec != LQCD_PREC_F64 && o->prec != LQCD_PREC_F32)
-    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: prec must be LQCD_PREC_F64 or LQCD_PREC_F32");
+  if (o->prec < LQCD_PREC_F64 || o->prec > LQCD_PREC_BF16)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: prec must be one of LQCD_PREC_*");
   const double2 *U = (const double2 *)links;
   const int Lt = ctx->dims[3];
   const long long N = ctx->N;
@@ -777,7 +777,7 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
   LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)bw * 9 * Lt, (void **)&cdv));
   const int nn = o->nnoise;
   std::vector<cd> per_noise_t((size_t)LQCD_NMODES * nn * 9 * Lt, cd(0.0, 0.0));
-  lqcd_krylov_opts po{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec};
+  lqcd_krylov_opts po{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec, o->inner_tol};
   long matvecs_noise = 0;
   double worst = 0.0;
   int conv = 1;

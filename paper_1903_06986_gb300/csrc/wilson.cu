@@ -215,28 +215,75 @@ __device__ __forceinline__ void load_link_packed(const float4 *__restrict__ U, i
   }
 }
 
-__device__ __forceinline__ void load_spinor_packed(const float4 *__restrict__ p, int V, Cx<float> s[4][3]) {
+// A chunk of the packed layout: two complex components of one site, as one float4 (FP32) or as an
+// 8-byte pair of FP16 / BF16 complex numbers; Chunk<S>::get / put convert to and from FP32.
+struct alignas(8) h2x2 { __half2 a, b; };
+struct alignas(8) b2x2 { __nv_bfloat162 a, b; };
+template <typename S> struct Chunk;
+template <> struct Chunk<float2> {
+  using T = float4;
+  static __device__ __forceinline__ void get(const T *p, Cx<float> &a, Cx<float> &b) {
+    const float4 v = __ldg(p);
+    a = mk<float>(v.x, v.y);
+    b = mk<float>(v.z, v.w);
+  }
+  static __device__ __forceinline__ void put(T *p, Cx<float> a, Cx<float> b) { *p = make_float4(a.x, a.y, b.x, b.y); }
+};
+template <> struct Chunk<__half2> {
+  using T = h2x2;
+  static __device__ __forceinline__ void get(const T *__restrict__ p, Cx<float> &a, Cx<float> &b) {
+    const T v = *p;
+    const float2 fa = __half22float2(v.a), fb = __half22float2(v.b);
+    a = mk<float>(fa.x, fa.y);
+    b = mk<float>(fb.x, fb.y);
+  }
+  static __device__ __forceinline__ void put(T *p, Cx<float> a, Cx<float> b) {
+    T v;
+    v.a = __floats2half2_rn(a.x, a.y);
+    v.b = __floats2half2_rn(b.x, b.y);
+    *p = v;
+  }
+};
+template <> struct Chunk<__nv_bfloat162> {
+  using T = b2x2;
+  static __device__ __forceinline__ void get(const T *__restrict__ p, Cx<float> &a, Cx<float> &b) {
+    const T v = *p;
+    const float2 fa = __bfloat1622float2(v.a), fb = __bfloat1622float2(v.b);
+    a = mk<float>(fa.x, fa.y);
+    b = mk<float>(fb.x, fb.y);
+  }
+  static __device__ __forceinline__ void put(T *p, Cx<float> a, Cx<float> b) {
+    T v;
+    v.a = __floats2bfloat162_rn(a.x, a.y);
+    v.b = __floats2bfloat162_rn(b.x, b.y);
+    *p = v;
+  }
+};
+
+template <typename S>
+__device__ __forceinline__ void load_spinor_packed(const typename Chunk<S>::T *__restrict__ p, int V, Cx<float> s[4][3]) {
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
-    const float4 v = __ldg(p + (long long)q * V);
     const int c0 = 2 * q, c1 = 2 * q + 1;
-    s[c0 / 3][c0 % 3] = mk<float>(v.x, v.y);
-    s[c1 / 3][c1 % 3] = mk<float>(v.z, v.w);
+    Chunk<S>::get(p + (long long)q * V, s[c0 / 3][c0 % 3], s[c1 / 3][c1 % 3]);
   }
 }
 
-__device__ __forceinline__ void store_spinor_packed(float4 *__restrict__ p, int V, const Cx<float> s[4][3]) {
+template <typename S>
+__device__ __forceinline__ void store_spinor_packed(typename Chunk<S>::T *__restrict__ p, int V, const Cx<float> s[4][3]) {
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     const int c0 = 2 * q, c1 = 2 * q + 1;
-    p[(long long)q * V] = make_float4(s[c0 / 3][c0 % 3].x, s[c0 / 3][c0 % 3].y, s[c1 / 3][c1 % 3].x, s[c1 / 3][c1 % 3].y);
+    Chunk<S>::put(p + (long long)q * V, s[c0 / 3][c0 % 3], s[c1 / 3][c1 % 3]);
   }
 }
 
-template <int NR, int RECON, int MODE>
-__global__ void __launch_bounds__(128) wilson_packed_kernel(const float4 *__restrict__ U, const float4 *__restrict__ in,
-                                                            float4 *__restrict__ out, float kappa, int Lx, int Ly,
-                                                            int Lz, int Lt, int V, int nrhs, int groups) {
+template <typename S, int NR, int RECON, int MODE>
+__global__ void __launch_bounds__(128) wilson_packed_kernel(const float4 *__restrict__ U,
+                                                            const typename Chunk<S>::T *__restrict__ in,
+                                                            typename Chunk<S>::T *__restrict__ out, float kappa,
+                                                            int Lx, int Ly, int Lz, int Lt, int V, int nrhs,
+                                                            int groups) {
   // the right-hand-side group varies fastest along the grid, so the blocks of all groups of one
   // site block run together and read its links (and neighbour spinor lines) from L2, not DRAM
   const int s = (blockIdx.x / groups) * blockDim.x + threadIdx.x;
@@ -275,7 +322,7 @@ __global__ void __launch_bounds__(128) wilson_packed_kernel(const float4 *__rest
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       if (r < nr) {
-        load_spinor_packed(in + (long long)(r0 + r) * 6 * V + nb[d], V, p);
+        load_spinor_packed<S>(in + (long long)(r0 + r) * 6 * V + nb[d], V, p);
         if (G5IN) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
@@ -300,12 +347,12 @@ __global__ void __launch_bounds__(128) wilson_packed_kernel(const float4 *__rest
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     if (r >= nr) break;
-    float4 *dst = out + (long long)(r0 + r) * 6 * V + s;
+    typename Chunk<S>::T *dst = out + (long long)(r0 + r) * 6 * V + s;
     if (MODE == 3) {
-      store_spinor_packed(dst, V, acc[r]);
+      store_spinor_packed<S>(dst, V, acc[r]);
       continue;
     }
-    load_spinor_packed(in + (long long)(r0 + r) * 6 * V + s, V, p);
+    load_spinor_packed<S>(in + (long long)(r0 + r) * 6 * V + s, V, p);
     if (G5IN) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -326,49 +373,54 @@ __global__ void __launch_bounds__(128) wilson_packed_kernel(const float4 *__rest
         o[0][c] = neg(o[2][c]); o[1][c] = neg(o[3][c]); o[2][c] = neg(a0); o[3][c] = neg(a1);
       }
     }
-    store_spinor_packed(dst, V, o);
+    store_spinor_packed<S>(dst, V, o);
   }
 }
 
-// canonical complex128 fields -> packed FP32 (optionally scaled per right-hand side by 1/s[r])
-__global__ void pack_f32_kernel(const double2 *__restrict__ x, const double *__restrict__ s, float4 *__restrict__ y,
-                                int V) {
+// canonical complex128 fields -> packed storage S, y = sigma * x / s[r] (s == NULL: s[r] = 1)
+template <typename S>
+__global__ void pack_kernel(const double2 *__restrict__ x, const double *__restrict__ s,
+                            typename Chunk<S>::T *__restrict__ y, int V, double sigma) {
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (site >= V) return;
-  double f = 1.0;
+  double f = sigma;
   if (s) {
     const double d = s[r];
-    f = d > 0.0 ? 1.0 / d : 0.0;
+    f = d > 0.0 ? sigma / d : 0.0;
   }
   const double2 *src = x + ((long long)r * V + site) * 12;
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     const double2 a = src[2 * q], b = src[2 * q + 1];
-    y[((long long)r * 6 + q) * V + site] = make_float4((float)(a.x * f), (float)(a.y * f), (float)(b.x * f), (float)(b.y * f));
+    Chunk<S>::put(y + ((long long)r * 6 + q) * V + site, mk<float>((float)(a.x * f), (float)(a.y * f)),
+                  mk<float>((float)(b.x * f), (float)(b.y * f)));
   }
 }
 
-// x^r (canonical FP64) += s[r] * unpack(c^r); s == NULL: x = unpack(c)
-__global__ void unpack_f32_kernel(const float4 *__restrict__ c, const double *__restrict__ s, double2 *__restrict__ x,
-                                  int V) {
+// x^r (canonical FP64) += (s[r] / sigma) * unpack(c^r); s == NULL: x = unpack(c) / sigma
+template <typename S>
+__global__ void unpack_kernel(const typename Chunk<S>::T *__restrict__ c, const double *__restrict__ s,
+                              double2 *__restrict__ x, int V, double sigma) {
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (site >= V) return;
   double2 *dst = x + ((long long)r * V + site) * 12;
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
-    const float4 v = c[((long long)r * 6 + q) * V + site];
+    Cx<float> u, v;
+    Chunk<S>::get(c + ((long long)r * 6 + q) * V + site, u, v);
     if (s) {
-      const double d = s[r];
+      const double d = s[r] / sigma;
       double2 a = dst[2 * q], b = dst[2 * q + 1];
-      a.x = fma(d, (double)v.x, a.x); a.y = fma(d, (double)v.y, a.y);
-      b.x = fma(d, (double)v.z, b.x); b.y = fma(d, (double)v.w, b.y);
+      a.x = fma(d, (double)u.x, a.x); a.y = fma(d, (double)u.y, a.y);
+      b.x = fma(d, (double)v.x, b.x); b.y = fma(d, (double)v.y, b.y);
       dst[2 * q] = a;
       dst[2 * q + 1] = b;
     } else {
-      dst[2 * q] = make_double2(v.x, v.y);
-      dst[2 * q + 1] = make_double2(v.z, v.w);
+      const double d = 1.0 / sigma;
+      dst[2 * q] = make_double2(d * u.x, d * u.y);
+      dst[2 * q + 1] = make_double2(d * v.x, d * v.y);
     }
   }
 }
@@ -392,9 +444,12 @@ __global__ void pack_links_kernel(const double2 *__restrict__ U, float4 *__restr
   }
 }
 
-template <int NR, int RECON>
-lqcd_status packed_launch_nr(lqcd_ctx *ctx, const float4 *U, double kappa, const float4 *in, float4 *out, int nrhs,
+template <typename S, int NR, int RECON>
+lqcd_status packed_launch_nr(lqcd_ctx *ctx, const float4 *U, double kappa, const void *in_, void *out_, int nrhs,
                              int flags) {
+  using T = typename Chunk<S>::T;
+  const T *in = (const T *)in_;
+  T *out = (T *)out_;
   int bs = 128;
   const int groups = (nrhs + NR - 1) / NR;
   while (bs > 32 && (long long)ceil_div(ctx->V, bs) * groups < 2LL * ctx->sms) bs /= 2;
@@ -405,10 +460,10 @@ lqcd_status packed_launch_nr(lqcd_ctx *ctx, const float4 *U, double kappa, const
   const float k = (float)kappa;
   kbegin(ctx);
   switch (flags) {
-    case LQCD_APPLY_M: wilson_packed_kernel<NR, RECON, 0><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
-    case LQCD_APPLY_G5R: wilson_packed_kernel<NR, RECON, 1><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
-    case LQCD_APPLY_DAG: wilson_packed_kernel<NR, RECON, 2><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
-    case LQCD_APPLY_HOP: wilson_packed_kernel<NR, RECON, 3><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
+    case LQCD_APPLY_M: wilson_packed_kernel<S, NR, RECON, 0><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
+    case LQCD_APPLY_G5R: wilson_packed_kernel<S, NR, RECON, 1><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
+    case LQCD_APPLY_DAG: wilson_packed_kernel<S, NR, RECON, 2><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
+    case LQCD_APPLY_HOP: wilson_packed_kernel<S, NR, RECON, 3><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
     default: return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: unknown flags %d", flags);
   }
   return launch_check(ctx, "wilson_packed_kernel", K_WILSON, (double)ctx->V * nrhs);
@@ -424,26 +479,59 @@ lqcd_status wilson_launch_packed(lqcd_ctx *ctx, const float4 *U, int recon, doub
   // link reconstruction is cheap, the registers saved keep occupancy up); with 18-real links two
   if (nr <= 0) nr = (recon == 12 || nrhs < 2) ? 1 : 2;
   if (recon == 12) {
-    if (nr == 1) return packed_launch_nr<1, 12>(ctx, U, kappa, in, out, nrhs, flags);
-    if (nr == 2) return packed_launch_nr<2, 12>(ctx, U, kappa, in, out, nrhs, flags);
-    return packed_launch_nr<4, 12>(ctx, U, kappa, in, out, nrhs, flags);
+    if (nr == 1) return packed_launch_nr<float2, 1, 12>(ctx, U, kappa, in, out, nrhs, flags);
+    if (nr == 2) return packed_launch_nr<float2, 2, 12>(ctx, U, kappa, in, out, nrhs, flags);
+    return packed_launch_nr<float2, 4, 12>(ctx, U, kappa, in, out, nrhs, flags);
   }
-  if (nr == 1) return packed_launch_nr<1, 18>(ctx, U, kappa, in, out, nrhs, flags);
-  if (nr == 2) return packed_launch_nr<2, 18>(ctx, U, kappa, in, out, nrhs, flags);
-  return packed_launch_nr<4, 18>(ctx, U, kappa, in, out, nrhs, flags);
+  if (nr == 1) return packed_launch_nr<float2, 1, 18>(ctx, U, kappa, in, out, nrhs, flags);
+  if (nr == 2) return packed_launch_nr<float2, 2, 18>(ctx, U, kappa, in, out, nrhs, flags);
+  return packed_launch_nr<float2, 4, 18>(ctx, U, kappa, in, out, nrhs, flags);
 }
+
+// FP16 / BF16 fields: one right-hand side per thread (the FP32 sweep's best with recon 12; with half
+// the bytes per field the link share of the traffic only grows, which L2 absorbs across the groups)
+template <typename S>
+lqcd_status wilson_launch_packed_lp(lqcd_ctx *ctx, const float4 *U, int recon, double kappa, const S *in, S *out,
+                                   int nrhs, int flags) {
+  if (nrhs <= 0) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: nrhs %d out of range", nrhs);
+  if (recon == 12) return packed_launch_nr<S, 1, 12>(ctx, U, kappa, in, out, nrhs, flags);
+  if (recon == 18) return packed_launch_nr<S, 1, 18>(ctx, U, kappa, in, out, nrhs, flags);
+  return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: recon must be 12 or 18");
+}
+template lqcd_status wilson_launch_packed_lp<__half2>(lqcd_ctx *, const float4 *, int, double, const __half2 *,
+                                                      __half2 *, int, int);
+template lqcd_status wilson_launch_packed_lp<__nv_bfloat162>(lqcd_ctx *, const float4 *, int, double,
+                                                             const __nv_bfloat162 *, __nv_bfloat162 *, int, int);
 
 lqcd_status pack_f32(lqcd_ctx *ctx, const double2 *x, const double *scale, float4 *y, int nrhs) {
   kbegin(ctx);
-  pack_f32_kernel<<<dim3(ceil_div(ctx->V, 128), nrhs), 128, 0, ctx->stream>>>(x, scale, y, ctx->V);
-  return launch_check(ctx, "pack_f32_kernel", K_BLAS1, (double)ctx->N * nrhs);
+  pack_kernel<float2><<<dim3(ceil_div(ctx->V, 128), nrhs), 128, 0, ctx->stream>>>(x, scale, y, ctx->V, 1.0);
+  return launch_check(ctx, "pack_kernel", K_BLAS1, (double)ctx->N * nrhs);
 }
 
 lqcd_status unpack_f32(lqcd_ctx *ctx, const float4 *c, const double *scale, double2 *x, int nrhs) {
   kbegin(ctx);
-  unpack_f32_kernel<<<dim3(ceil_div(ctx->V, 128), nrhs), 128, 0, ctx->stream>>>(c, scale, x, ctx->V);
-  return launch_check(ctx, "unpack_f32_kernel", K_BLAS1, (double)ctx->N * nrhs);
+  unpack_kernel<float2><<<dim3(ceil_div(ctx->V, 128), nrhs), 128, 0, ctx->stream>>>(c, scale, x, ctx->V, 1.0);
+  return launch_check(ctx, "unpack_kernel", K_BLAS1, (double)ctx->N * nrhs);
 }
+
+template <typename S> lqcd_status pack_lp(lqcd_ctx *ctx, const double2 *x, const double *scale, S *y, int nrhs) {
+  kbegin(ctx);
+  pack_kernel<S><<<dim3(ceil_div(ctx->V, 128), nrhs), 128, 0, ctx->stream>>>(
+      x, scale, (typename Chunk<S>::T *)y, ctx->V, store_sigma<S>(ctx->N));
+  return launch_check(ctx, "pack_kernel", K_BLAS1, (double)ctx->N * nrhs);
+}
+
+template <typename S> lqcd_status unpack_lp(lqcd_ctx *ctx, const S *c, const double *scale, double2 *x, int nrhs) {
+  kbegin(ctx);
+  unpack_kernel<S><<<dim3(ceil_div(ctx->V, 128), nrhs), 128, 0, ctx->stream>>>(
+      (const typename Chunk<S>::T *)c, scale, x, ctx->V, store_sigma<S>(ctx->N));
+  return launch_check(ctx, "unpack_kernel", K_BLAS1, (double)ctx->N * nrhs);
+}
+template lqcd_status pack_lp<__half2>(lqcd_ctx *, const double2 *, const double *, __half2 *, int);
+template lqcd_status pack_lp<__nv_bfloat162>(lqcd_ctx *, const double2 *, const double *, __nv_bfloat162 *, int);
+template lqcd_status unpack_lp<__half2>(lqcd_ctx *, const __half2 *, const double *, double2 *, int);
+template lqcd_status unpack_lp<__nv_bfloat162>(lqcd_ctx *, const __nv_bfloat162 *, const double *, double2 *, int);
 
 lqcd_status pack_links_f32(lqcd_ctx *ctx, const double2 *U, float4 *P, int recon) {
   if (recon != 12 && recon != 18) return set_err(ctx, LQCD_ERR_INVALID_ARG, "pack_links: recon must be 12 or 18");
@@ -478,4 +566,34 @@ extern "C" lqcd_status lqcd_wilson_apply_packed(lqcd_ctx *ctx, const float *link
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_packed: rhs_per_thread must be 0, 1, 2 or 4");
   return wilson_launch_packed(ctx, (const float4 *)links_packed, recon, kappa, (const float4 *)in, (float4 *)out, nrhs,
                               flags, rhs_per_thread);
+}
+
+// ---- FP16 / BF16 fields ------------------------------------------------------------------------
+extern "C" lqcd_status lqcd_pack_half(lqcd_ctx *ctx, int prec, const double *in, void *out, int nrhs) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!in || !out || nrhs < 1 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "pack_half: bad arguments");
+  if (prec == LQCD_PREC_F16) return pack_lp(ctx, (const double2 *)in, nullptr, (__half2 *)out, nrhs);
+  if (prec == LQCD_PREC_BF16) return pack_lp(ctx, (const double2 *)in, nullptr, (__nv_bfloat162 *)out, nrhs);
+  return set_err(ctx, LQCD_ERR_INVALID_ARG, "pack_half: prec must be LQCD_PREC_F16 or LQCD_PREC_BF16");
+}
+
+extern "C" lqcd_status lqcd_unpack_half(lqcd_ctx *ctx, int prec, const void *in, double *out, int nrhs) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!in || !out || nrhs < 1 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "unpack_half: bad arguments");
+  if (prec == LQCD_PREC_F16) return unpack_lp(ctx, (const __half2 *)in, nullptr, (double2 *)out, nrhs);
+  if (prec == LQCD_PREC_BF16) return unpack_lp(ctx, (const __nv_bfloat162 *)in, nullptr, (double2 *)out, nrhs);
+  return set_err(ctx, LQCD_ERR_INVALID_ARG, "unpack_half: prec must be LQCD_PREC_F16 or LQCD_PREC_BF16");
+}
+
+extern "C" lqcd_status lqcd_wilson_apply_half(lqcd_ctx *ctx, int prec, const float *links_packed, int recon,
+                                              double kappa, const void *in, void *out, int nrhs, int flags) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links_packed || !in || !out || in == out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_half: bad pointers");
+  if (prec == LQCD_PREC_F16)
+    return wilson_launch_packed_lp(ctx, (const float4 *)links_packed, recon, kappa, (const __half2 *)in, (__half2 *)out,
+                                   nrhs, flags);
+  if (prec == LQCD_PREC_BF16)
+    return wilson_launch_packed_lp(ctx, (const float4 *)links_packed, recon, kappa, (const __nv_bfloat162 *)in,
+                                   (__nv_bfloat162 *)out, nrhs, flags);
+  return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_half: prec must be LQCD_PREC_F16 or LQCD_PREC_BF16");
 }

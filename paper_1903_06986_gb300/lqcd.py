@@ -15,7 +15,7 @@ import numpy as np
 from . import build as _build
 
 OK, ERR_INVALID_ARG, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_OOM = range(7)
-PREC_F64, PREC_F32 = 0, 1
+PREC_F64, PREC_F32, PREC_F16, PREC_BF16 = 0, 1, 2, 3
 APPLY_M, APPLY_G5R, APPLY_DAG, APPLY_HOP = 0, 1, 2, 3
 SYS_M, SYS_MG5 = 0, 1
 SUB_NONE, SUB_PERT, SUB_POLY, SUB_DEFL, SUB_DEFL_PERT, SUB_DEFL_POLY = (1 << i for i in range(6))
@@ -33,7 +33,7 @@ class LqcdError(RuntimeError):
 
 class KrylovOpts(C.Structure):
     _fields_ = [("m", C.c_int), ("k", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int),
-                ("system", C.c_int), ("prec", C.c_int)]
+                ("system", C.c_int), ("prec", C.c_int), ("inner_tol", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -47,7 +47,8 @@ class SolveInfo(C.Structure):
 class EstOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("nnoise", C.c_int), ("block", C.c_int), ("m", C.c_int), ("k", C.c_int),
                 ("m_inner", C.c_int), ("K", C.c_int), ("npoly", C.c_int), ("tol", C.c_double),
-                ("tol_special", C.c_double), ("max_cycles", C.c_int), ("modes", C.c_int), ("prec", C.c_int)]
+                ("tol_special", C.c_double), ("max_cycles", C.c_int), ("modes", C.c_int), ("prec", C.c_int),
+                ("inner_tol", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -95,6 +96,9 @@ def load(path=None):
         "lqcd_unpack_f32": [vp, vp, vp, i],
         "lqcd_pack_links_f32": [vp, vp, vp, i],
         "lqcd_wilson_apply_packed": [vp, vp, i, d, vp, vp, i, i, i],
+        "lqcd_pack_half": [vp, i, vp, vp, i],
+        "lqcd_unpack_half": [vp, i, vp, vp, i],
+        "lqcd_wilson_apply_half": [vp, i, vp, i, d, vp, vp, i, i],
         "lqcd_gmresdr_solve": [vp, vp, d, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo), C.POINTER(vp)],
         "lqcd_minresdr_solve": [vp, vp, d, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo), C.POINTER(vp)],
         "lqcd_proj_solve": [vp, vp, d, vp, vp, vp, i, C.POINTER(KrylovOpts), C.POINTER(SolveInfo)],
@@ -309,6 +313,28 @@ class Context:
                                                       rhs_per_thread))
         return out
 
+    def pack_half(self, x, prec=PREC_F16):
+        """canonical complex128 block -> packed FP16 / BF16 (int16 tensor of raw halves, nrhs x 24 V),
+        stored scaled by 2^floor(log2(sqrt(12 V)))."""
+        n = self._nrhs(x)
+        out = _torch().empty((n, 24 * self.V), dtype=_torch().int16, device=self.device)
+        self._check(self.lib.lqcd_pack_half(self.h, prec, _ptr(x), _ptr(out, _torch().int16), n))
+        return out
+
+    def unpack_half(self, p, prec=PREC_F16):
+        n = p.numel() // (24 * self.V)
+        out = self.field(n)
+        self._check(self.lib.lqcd_unpack_half(self.h, prec, _ptr(p, _torch().int16), _ptr(out), n))
+        return out
+
+    def wilson_apply_half(self, links_p, recon, kappa, inp, out=None, flags=APPLY_M, prec=PREC_F16):
+        i16 = _torch().int16
+        out = _torch().empty_like(inp) if out is None else out
+        self._check(self.lib.lqcd_wilson_apply_half(self.h, prec, _ptr(links_p, _torch().float32), recon, kappa,
+                                                    _ptr(inp, i16), _ptr(out, i16), inp.numel() // (24 * self.V),
+                                                    flags))
+        return out
+
     def wilson_apply_f32(self, links32, kappa, inp, out=None, flags=APPLY_M):
         c64 = _torch().complex64
         out = _torch().empty_like(inp) if out is None else out
@@ -339,9 +365,10 @@ class Context:
                             want_defl, prec)
 
     # a5
-    def proj_solve(self, links, kappa, defl, b, m, tol, max_cycles=1000, system=SYS_M, prec=PREC_F64):
+    def proj_solve(self, links, kappa, defl, b, m, tol, max_cycles=1000, system=SYS_M, prec=PREC_F64,
+                   inner_tol=0.0):
         x = _torch().empty_like(b)
-        o = KrylovOpts(m, 0, tol, max_cycles, system, prec)
+        o = KrylovOpts(m, 0, tol, max_cycles, system, prec, inner_tol)
         info = SolveInfo()
         st = self.lib.lqcd_proj_solve(self.h, _ptr(links), kappa, defl.h, _ptr(b), _ptr(x), self._nrhs(b),
                                       C.byref(o), C.byref(info))
@@ -412,9 +439,10 @@ class Context:
 
     # whole path
     def loop_estimate(self, links, kappa, seed, nnoise, block, m, k, K, npoly, tol, tol_special,
-                      m_inner=0, max_cycles=2000, modes=SUB_ALL, prec=PREC_F64):
+                      m_inner=0, max_cycles=2000, modes=SUB_ALL, prec=PREC_F64, inner_tol=0.0):
         lt = self.dims[3]
-        o = EstOpts(seed, nnoise, block, m, k, m_inner, K, npoly, tol, tol_special, max_cycles, modes, prec)
+        o = EstOpts(seed, nnoise, block, m, k, m_inner, K, npoly, tol, tol_special, max_cycles, modes, prec,
+                    inner_tol)
         per_noise = np.zeros((6, nnoise, NOPS), dtype=np.complex128)
         per_t = np.zeros((6, NOPS, lt), dtype=np.complex128)
         addback = np.zeros((6, NOPS, lt), dtype=np.complex128)
@@ -452,10 +480,11 @@ def link_grad(ctx, links, kappa, z, x, scale=1.0, want_links=True):
 
 
 def loop_derivs(ctx, links, kappa, seed, nnoise, block, m, k, K, tol, tol_special, m_inner=0, max_cycles=2000,
-                prec=PREC_F64, want_grad=True, grad_scale=1.0):
+                prec=PREC_F64, want_grad=True, grad_scale=1.0, inner_tol=0.0):
     """lqcd_loop_derivs: d/dkappa of the NS and PS estimates of the nine operators, and the link
     gradient of the NS scalar estimate."""
-    o = EstOpts(seed, nnoise, block, m, k, m_inner, K, 0, tol, tol_special, max_cycles, SUB_NONE | SUB_PERT, prec)
+    o = EstOpts(seed, nnoise, block, m, k, m_inner, K, 0, tol, tol_special, max_cycles, SUB_NONE | SUB_PERT, prec,
+                inner_tol)
     dk = np.zeros((2, NOPS), dtype=np.complex128)
     err = np.zeros((2, NOPS), dtype=np.float64)
     per = np.zeros((2, nnoise, NOPS), dtype=np.complex128)

@@ -62,6 +62,42 @@ def test_wilson_all_forms(dims):
                 assert rel_err(got, ref(psi)) < 2e-6, (recon, nr, flag)
 
 
+# unit roundoff of the storage formats: 10 and 7 stored mantissa bits, round to nearest
+HALF_U = {2: 2.0 ** -11, 3: 2.0 ** -8}
+
+
+@pytest.mark.parametrize("prec", [2, 3], ids=["fp16", "bf16"])
+@pytest.mark.parametrize("dims", DIMS[1:3])
+def test_wilson_half_storage(dims, prec):
+    """FP16 / BF16 packed fields with FP32 arithmetic.  Packing scales by a power of two (exact) and
+    rounds each component once, so the round trip is within u |x| per component (u the format's
+    unit roundoff; the FP64 -> FP32 -> half double rounding adds at most 2^-24 relative).  The
+    operator's error is the input and output rounding: ||out - ref|| <= u (||M|| ||in|| + ||ref||)
+    with ||M|| <= 1 + 16 kappa (eight hopping terms of norm 2), FP32 arithmetic far below that."""
+    ctx = context(dims)
+    U = synth.su3_links(dims, 0.45, 3)
+    kappa = 0.1537
+    psi = rand_fields(dims, 3, 4)
+    Ud, pd = dev(U), dev(psi)
+    u = HALF_U[prec]
+    packed = ctx.pack_half(pd, prec)
+    back = host(ctx.unpack_half(packed, prec))
+    for part in (np.real, np.imag):
+        assert np.all(np.abs(part(back) - part(psi)) <= (u + 2.0 ** -24) * np.abs(part(psi)) + 1e-12)
+    forms = {0: lambda f: L.wilson(U, kappa, f), 1: lambda f: L.wilson_g5(U, kappa, f),
+             2: lambda f: L.wilson_dag(U, kappa, f), 3: lambda f: L.hop(U, f)}
+    for recon in (18, 12):
+        Up = ctx.pack_links_f32(Ud, recon)
+        for flag, ref in forms.items():
+            want = ref(psi)
+            got = host(ctx.unpack_half(ctx.wilson_apply_half(Up, recon, kappa, packed, flags=flag, prec=prec), prec))
+            for r in range(3):
+                bound = u * ((1 + 16 * kappa) * np.linalg.norm(psi[r]) + np.linalg.norm(want[r]))
+                assert np.linalg.norm(got[r] - want[r]) <= bound, (recon, flag, r)
+            # and it is not merely within the bound by luck of a loose bound: error of order u
+            assert rel_err(got, want) > 1e-3 * u
+
+
 @pytest.mark.parametrize("dims", DIMS[:3])
 def test_contract_all_operators(dims):
     ctx = context(dims)

@@ -100,15 +100,17 @@ def test_gmres_proj_multi_rhs(setup):
     assert rel_err(host(xa)[0], host(x)[1]) < 10 * s["cond"] * tol
 
 
-def test_mixed_precision_proj_reaches_fp64_tolerance(setup):
-    """FP64 defect correction around the FP32 GMRES-Proj: the FP64 true residual meets 1e-10 and
-    the solution agrees with the dense FP64 solve within cond * tol, like the plain FP64 path."""
+@pytest.mark.parametrize("prec", [1, 2, 3], ids=["fp32", "fp16", "bf16"])
+def test_mixed_precision_proj_reaches_fp64_tolerance(setup, prec):
+    """FP64 defect correction around the FP32 / FP16 / BF16 GMRES-Proj: the FP64 true residual
+    (recomputed here with the dense oracle matrix) meets 1e-10 and the solution agrees with the
+    dense FP64 solve within cond * tol, like the plain FP64 path."""
     s = setup
     ctx = s["ctx"]
     _, _, defl = ctx.gmresdr_solve(s["Ud"], KAPPA, dev(L.unflat(s["b"], DIMS)), 20, 5, 1e-12, 500, want_defl=True)
     etas = rng.z4_block(2, 0, 4, DIMS)
     tol = 1e-10
-    x, info = ctx.proj_solve(s["Ud"], KAPPA, defl, dev(etas), 15, tol, 500, prec=1)
+    x, info = ctx.proj_solve(s["Ud"], KAPPA, defl, dev(etas), 15, tol, 500, prec=prec)
     assert info["converged"] and info["true_resid"] <= tol
     x64, _ = ctx.proj_solve(s["Ud"], KAPPA, defl, dev(etas), 15, tol, 500)
     for r in range(4):
