@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
+    ap.add_argument("--batch", action="store_true", help="also measure the uneven multi-lattice batch")
     ap.add_argument("--case", default=None, choices=["gmres-cycle", "gmres-cycle-f32", "dslash-packed", "dslash-half"],
                     help="run one small kernel case for profiling instead of the benchmark: one GMRES(30) "
                          "cycle on 50 noises of the 8^3x16 workload (FP64, or FP32 storage)")
@@ -272,6 +273,67 @@ def dslash_rates(torch):
             "hbm_peak_gbs": HBM_PEAK_GBS, "results": out}
 
 
+BATCH_SHAPES = ((8, 8, 8, 8), (12, 12, 12, 12), (12, 12, 12, 24), (16, 16, 16, 16))
+BATCH_NOISE = 40
+BATCH_KAPPA = 0.150
+
+
+def batching_rates(torch):
+    """Uneven multi-lattice batch: loop estimates of 40 noises each (kappa 0.150, the method
+    parameters of the main workload, 1e-10 true residual, block width picked by the autotuner) on
+    8^4, 12^4, 12^3x24 and 16^4 lattices (links of the same generator and plaquette): first one
+    after another with direct launches (this pass also makes each context's workspace), then all
+    four concurrently (lqcd_batch_loop_estimate, Krylov cycles replayed from CUDA graphs, captured
+    during the pass).  Wall time per variant; estimates/s = 160 / time.  About two minutes, so it
+    runs only with --batch."""
+    from paper_1903_06986_gb300 import lqcd, synth
+    probs = []
+    for i, dims in enumerate(BATCH_SHAPES):
+        eps = synth.eps_for_plaquette(dims, PLAQ, LINK_SEED + 10 + i)
+        U = torch.from_numpy(synth.su3_links(dims, eps, LINK_SEED + 10 + i)).cuda()
+        probs.append(dict(ctx=lqcd.Context(dims, recon=12), links=U, kappa=BATCH_KAPPA, seed=NOISE_SEED,
+                          nnoise=BATCH_NOISE, block=0, m=M_DR, k=K_DR, K=K_PS, npoly=NPOLY, tol=TOL,
+                          tol_special=TOL_SPECIAL, max_cycles=400))
+    keys = ("seed", "nnoise", "block", "m", "k", "K", "npoly", "tol", "tol_special", "max_cycles")
+
+    def sequential(graphs):
+        for p in probs:
+            p["ctx"].set_graphs(graphs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = [p["ctx"].loop_estimate(p["links"], p["kappa"], **{k: p[k] for k in keys}) for p in probs]
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, res
+
+    def concurrent():
+        for p in probs:
+            p["ctx"].set_graphs(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = lqcd.batch_loop_estimate(probs)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, res
+
+    t_dir, r_dir = sequential(False)
+    t_cc, r_cc = concurrent()
+    for a, b in zip(r_dir, r_cc):
+        if not (a["converged"] and b["converged"]) or max(a["max_true_resid"], b["max_true_resid"]) > TOL:
+            raise RuntimeError("batched loop estimate did not reach the tolerance")
+    n = BATCH_NOISE * len(probs)
+    out = {"lattices": ["x".join(map(str, d)) for d in BATCH_SHAPES], "noises_each": BATCH_NOISE,
+           "kappa": BATCH_KAPPA, "method": "as the main workload, FP64",
+           "autotuned_block": [r["block"] for r in r_cc],
+           "per_lattice_s_direct": [round(r["seconds_setup"] + r["seconds_noise"], 3) for r in r_dir],
+           "sequential_direct": {"s": round(t_dir, 3), "estimates_per_s": n / t_dir},
+           "concurrent_graphs": {"s": round(t_cc, 3), "estimates_per_s": n / t_cc},
+           "speedup_concurrent_vs_direct": t_dir / t_cc,
+           "max_abs_diff_concurrent_vs_direct": float(max(np.abs(a["mean"] - b["mean"]).max()
+                                                          for a, b in zip(r_dir, r_cc)))}
+    for p in probs:
+        p["ctx"].close()
+    return out
+
+
 def run_case(args):
     """Small fixed workloads for ncu captures (no timing output): one GMRES(30) cycle on the 50 noises
     of the 8^3x16 workload (FP64, or the mixed solver's FP32 cycle), or four applications of the
@@ -459,6 +521,12 @@ def main():
         roofline["wilson_fp64_tflops"] = w[2] * WILSON_FLOPS / (w[0] / 1000.0) / 1e12
 
     dslash = None if args.no_dslash else dslash_rates(torch)
+    batching = None
+    if args.batch:
+        try:
+            batching = batching_rates(torch)
+        except Exception as e:  # reported, not fatal: the headline numbers above stand on their own
+            batching = {"error": str(e)[:300]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -482,7 +550,8 @@ def main():
                 "roofline": roofline,
                 "e2e": {"value": e2e_value, "unit": "estimates/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
-                "clocks": clk, "cpu_baseline": cpu, "mixed_precision": mixed, "dslash": dslash}
+                "clocks": clk, "cpu_baseline": cpu, "mixed_precision": mixed, "dslash": dslash,
+                "batching": batching}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

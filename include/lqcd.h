@@ -79,7 +79,7 @@ typedef struct {
   int system;        /* LQCD_SYS_M or LQCD_SYS_MG5                                           */
   int prec;          /* lqcd_prec of the inner operator; LQCD_PREC_F64 for the plain path    */
   double inner_tol;  /* mixed precision: relative residual of each inner solve (0 = default:
-                        5e-6 F32, 2e-2 F16, 1e-1 BF16)                                        */
+                        5e-6 F32, 2e-2 F16, 5e-2 BF16)                                        */
 } lqcd_krylov_opts;
 
 typedef struct {
@@ -128,7 +128,7 @@ lqcd_status lqcd_timing_enable(lqcd_ctx *ctx, int enable);
 lqcd_status lqcd_timing_reset(lqcd_ctx *ctx);
 lqcd_status lqcd_timing_read(lqcd_ctx *ctx, int cls, double *total_ms, long *launches, double *units);
 
-/* ---- a1: Z(4) noise (Sec. 2, 3) ------------------------------------------------------- */
+/* ---- Z(4) noise (Sec. 2, 3) ------------------------------------------------------- */
 
 /* out[n] = Z(4) noise number first_noise + n, n < nrhs: entry (s, spin, colour) is
  * {1, i, -1, -i}[(w >> 2c) & 3] with c = 3 spin + colour and w word 0 of Philox-4x32-10
@@ -136,7 +136,7 @@ lqcd_status lqcd_timing_read(lqcd_ctx *ctx, int cls, double *total_ms, long *lau
  * out: device, nrhs * 12 V complex128.  Bit-exact. */
 lqcd_status lqcd_noise_z4(lqcd_ctx *ctx, uint64_t seed, uint32_t first_noise, int nrhs, double *out);
 
-/* ---- a2: Wilson operator (Eq. xyz556; Sec. 5.4) --------------------------------------- */
+/* ---- Wilson operator (Eq. xyz556; Sec. 5.4) --------------------------------------- */
 
 /* out = A in for nrhs fields, A selected by flags (LQCD_APPLY_*).  links: device gauge field;
  * in/out: device, nrhs * 12 V complex128, must not overlap.  prec must be LQCD_PREC_F64 or
@@ -179,7 +179,7 @@ lqcd_status lqcd_unpack_half(lqcd_ctx *ctx, int prec, const void *in, double *ou
 lqcd_status lqcd_wilson_apply_half(lqcd_ctx *ctx, int prec, const float *links_packed, int recon, double kappa,
                                    const void *in, void *out, int nrhs, int flags);
 
-/* ---- a3 / a4: GMRES-DR and MINRES-DR (Sec. 5.3, 7, 8) --------------------------------- */
+/* ---- GMRES-DR and MINRES-DR (Sec. 5.3, 7, 8) --------------------------------- */
 
 /* GMRES-DR(m, k) for nrhs independent right-hand sides (each with its own Krylov basis).
  * b, x: device, nrhs * 12 V complex128 (x is overwritten; the initial guess is zero).
@@ -198,15 +198,15 @@ lqcd_status lqcd_minresdr_solve(lqcd_ctx *ctx, const double *links, double kappa
                                 double *x, int nrhs, const lqcd_krylov_opts *opts,
                                 lqcd_solve_info *info, lqcd_defl **defl_out);
 
-/* ---- a5: deflated multi-RHS solves (GMRES-Proj, Sec. 5.3, 7) --------------------------- */
+/* ---- deflated multi-RHS solves (GMRES-Proj, Sec. 5.3, 7) --------------------------- */
 
 /* Solve A x = b for nrhs right-hand sides with GMRES-Proj over defl (made by one of the two
  * solvers above on the same A): each cycle is a minimum-residual projection over V_{k+1} and
  * Hbar_k followed by GMRES(opts->m).  opts->k is ignored.  b, x: device (nrhs * 12 V).
  * opts->prec = LQCD_PREC_F32, LQCD_PREC_F16 or LQCD_PREC_BF16 selects mixed precision: an FP64
  * defect-correction loop around the same GMRES-Proj run in that storage precision with FP32
- * arithmetic (Krylov basis and deflation space in that precision, the inner solution and residual
- * in FP32; inner relative residual opts->inner_tol), stopping on the FP64 true residual
+ * arithmetic (Krylov basis in that precision; deflation space, inner solution and residual in
+ * FP32; inner relative residual opts->inner_tol), stopping on the FP64 true residual
  * ||b - A x|| <= tol ||b||; opts->max_cycles bounds the inner cycles. */
 lqcd_status lqcd_proj_solve(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl,
                             const double *b, double *x, int nrhs, const lqcd_krylov_opts *opts,
@@ -228,7 +228,7 @@ lqcd_status lqcd_defl_export(const lqcd_defl *defl, double *V, double *Hbar, dou
 lqcd_status lqcd_defl_import(lqcd_ctx *ctx, int k, const double *E, const double *lam,
                              lqcd_defl **defl_out);
 
-/* ---- a6: deflation projection (HFES, Sec. 5.4) ----------------------------------------- */
+/* ---- deflation projection (HFES, Sec. 5.4) ----------------------------------------- */
 
 /* out = gamma_5 V' diag(d) V'^dagger eta for nrhs fields, V' the k eigenvectors of defl and d a
  * host array of k complex weights (1/lambda' for HFES, 1/lambda' - 1/xi' for HFPS/HFPOLY).
@@ -236,7 +236,7 @@ lqcd_status lqcd_defl_import(lqcd_ctx *ctx, int k, const double *E, const double
 lqcd_status lqcd_deflate_project(lqcd_ctx *ctx, const lqcd_defl *defl, const double *eta,
                                  double *out, int nrhs, const double *d);
 
-/* ---- a7 / a8: perturbative and polynomial series (Sec. 5.1, 5.2) ---------------------- */
+/* ---- perturbative and polynomial series (Sec. 5.1, 5.2) ---------------------- */
 
 /* out = sum_{k=0}^{K-1} c_k (kappa P)^k eta; c: host K complex, or NULL for all ones (PS). */
 lqcd_status lqcd_hop_series(lqcd_ctx *ctx, const double *links, double kappa, const double *eta,
@@ -249,14 +249,14 @@ lqcd_status lqcd_poly_apply(lqcd_ctx *ctx, const double *links, double kappa, co
 lqcd_status lqcd_poly_coeffs(lqcd_ctx *ctx, const double *links, double kappa, uint64_t seed, int n,
                              double *a);
 
-/* ---- a9: hopping traces (Sec. 5.1) ------------------------------------------------------ */
+/* ---- hopping traces (Sec. 5.1) ------------------------------------------------------ */
 
 /* t[k][op][t] = sum over the timeslice t of the exact diagonal density of Tr(Theta_op P^k),
  * k < K, by probing with colour classes whose members are more than K hops apart (host out,
  * K x 9 x Lt complex).  kappa enters only the point-split operators' own prefactor. */
 lqcd_status lqcd_hop_traces(lqcd_ctx *ctx, const double *links, double kappa, int K, double *t);
 
-/* ---- a10: 1/xi' for HFPS / HFPOLY (Sec. 5.5) ------------------------------------------- */
+/* ---- 1/xi' for HFPS / HFPOLY (Sec. 5.5) ------------------------------------------- */
 
 /* xi[q] = e'_q^dagger gamma_5 tilde M^{-1} e'_q (host out, k complex) with tilde M^{-1} the PS
  * series of K terms (sub = LQCD_SUB_PERT, coeffs ignored) or the POLY polynomial with the n+1 =
@@ -264,7 +264,7 @@ lqcd_status lqcd_hop_traces(lqcd_ctx *ctx, const double *links, double kappa, in
 lqcd_status lqcd_xi_inverse(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl,
                             int sub, int K, const double *coeffs, double *xi);
 
-/* ---- a11: operator contractions (Sec. 6, Table Table903) ------------------------------ */
+/* ---- operator contractions (Sec. 6, Table Table903) ------------------------------ */
 
 /* out[n][op][t] = sum over timeslice t of the density of eta_n^dagger Theta_op w_n (host out,
  * nrhs x 9 x Lt complex), compensated FP64 sums.  Densities: scalar eta^dag w; local
@@ -296,7 +296,8 @@ lqcd_status lqcd_contract_noalloc(const int dims[4], const double *links, double
 typedef struct {
   uint64_t seed;      /* noise seed (noises 0 .. nnoise-1; specials 2^32-2 and 2^32-1)       */
   int nnoise;         /* N                                                                   */
-  int block;          /* right-hand sides solved together (multi-RHS block width b)          */
+  int block;          /* right-hand sides solved together (multi-RHS block width b); 0 = pick
+                         it with lqcd_autotune_block among 8, 16, 32, 64 (those <= nnoise)    */
   int m, k;           /* GMRES-DR(m, k) / MINRES-DR(m, k) for the special right-hand side    */
   int m_inner;        /* GMRES cycle length inside GMRES-Proj (m - k if 0)                   */
   int K;              /* PS terms: I .. (kappa P)^{K-1}  ("seventh order" = 7)               */
@@ -325,13 +326,43 @@ typedef struct {
   double seconds_setup, seconds_noise;
   double max_true_resid;
   int converged;
+  int block;          /* right-hand-side block width used (the autotuner's pick when opts->block == 0) */
 } lqcd_estimate;
 
 /* Tr(Theta M^{-1}) for the nine operators and the requested subtraction modes (Sec. 5-7). */
 lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, double kappa,
                                const lqcd_est_opts *opts, lqcd_estimate *out);
 
-/* ---- a13: derivatives (a spec addition; the paper has no derivatives) ------------ */
+/* ---- batching -------------------------------------------------------------------------- */
+
+/* Autotuner of the right-hand-side block width of the noise solves: for each candidate width b in
+ * cand[0..ncand-1] it times, on b Z(4) noises, the marginal cost of one more GMRES-Proj(opts->m)
+ * cycle over defl (a call limited to two cycles minus one limited to one, CUDA events on the
+ * context's stream, after an untimed warm-up of each width), and picks the width with the least
+ * time per right-hand side and cycle.  opts->prec selects the path (plain FP64 or mixed
+ * precision); with LQCD_PREC_F32 it then also picks the packed operator's right-hand sides per
+ * thread (1, 2 or 4) for that width and keeps it in the context.  Outputs (host): *best;
+ * seconds[i] = seconds per right-hand side and cycle of cand[i] (may be NULL).  Candidates must be
+ * in 1..4096.  Uses the context's stream and synchronises with it. */
+lqcd_status lqcd_autotune_block(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl,
+                                const lqcd_krylov_opts *opts, const int *cand, int ncand, int *best,
+                                double *seconds);
+
+/* Replay the fixed launch sequence of each Krylov cycle (its Arnoldi steps) from a CUDA graph,
+ * captured on first use and cached per context (default on).  Off, or with device timing on, the
+ * same kernels are launched one by one. */
+lqcd_status lqcd_set_graphs(lqcd_ctx *ctx, int enable);
+
+/* Loop estimates of n independent problems (lattices of any, uneven, sizes), run concurrently: each
+ * context (all distinct) works on its own private stream from its own host thread, ordered after
+ * the work already queued on its stream (links ready there) and before the work queued there
+ * later.  links[i], kappas[i], opts[i], out[i] as lqcd_loop_estimate on ctxs[i]; status[i]
+ * receives each problem's status (host array).  Returns LQCD_OK when every problem returned
+ * LQCD_OK, otherwise the first failing status. */
+lqcd_status lqcd_batch_loop_estimate(int n, lqcd_ctx *const *ctxs, const double *const *links, const double *kappas,
+                                     const lqcd_est_opts *opts, lqcd_estimate *out, int *status);
+
+/* ---- derivatives (an addition: the paper has no derivatives) ------------ */
 
 /* Link gradient of scalar noise estimates T_n = eta_n^dag M^{-1} eta_n from x_n = M^{-1} eta_n and
  * z_n = M^{-dag} eta_n (device, nrhs fields each).  Accumulates (+=) scale * sum_n into

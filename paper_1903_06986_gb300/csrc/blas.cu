@@ -436,16 +436,32 @@ lqcd_status blas_norms(lqcd_ctx *ctx, const S *x, long long n, int nrhs, double 
   return launch_check(ctx, "norm_kernel", K_NORM, (double)n * nrhs);
 }
 
-template <typename SV, typename SW>
-lqcd_status blas_multidot(lqcd_ctx *ctx, const SV *V, long long vstride, long long vrs, int nvec, const SW *w,
-                          long long n, int nrhs, double2 *h) {
-  if (nvec <= 0) return LQCD_OK;
+static int multidot_chunks(lqcd_ctx *ctx, long long n, int nrhs, int nvec) {
   // element chunks of at least 8 elements per thread; enough blocks (chunks x vector groups x
   // right-hand sides) to cover the SMs a few times
   const int ngroup = (nvec + GROUP - 1) / GROUP;
   const long long max_chunks = std::max<long long>(1, n / (8LL * BT));
   const long long want = std::max<long long>(1, (4LL * ctx->sms) / std::max<long long>(1, (long long)nrhs * ngroup));
-  const int nchunk = (int)std::min<long long>(std::min(max_chunks, want), 4096);
+  return (int)std::min<long long>(std::min(max_chunks, want), 4096);
+}
+
+lqcd_status blas_reserve(lqcd_ctx *ctx, long long n, int nrhs, int max_nvec) {
+  size_t need = 0;
+  for (int v = 1; v <= max_nvec; ++v)
+    need = std::max(need, sizeof(double2) * (size_t)multidot_chunks(ctx, n, nrhs, v) * nrhs * v);
+  void *p = nullptr;
+  unsigned *cnt = nullptr;
+  LQCD_TRY(ws_get(ctx, WS_PARTIAL, need, &p));
+  LQCD_TRY(ws_get(ctx, WS_SCAL, sizeof(double) * (size_t)partial_blocks(ctx, n, nrhs) * nrhs, &p));
+  return reduction_counters(ctx, nrhs, &cnt);
+}
+
+template <typename SV, typename SW>
+lqcd_status blas_multidot(lqcd_ctx *ctx, const SV *V, long long vstride, long long vrs, int nvec, const SW *w,
+                          long long n, int nrhs, double2 *h) {
+  if (nvec <= 0) return LQCD_OK;
+  const int ngroup = (nvec + GROUP - 1) / GROUP;
+  const int nchunk = multidot_chunks(ctx, n, nrhs, nvec);
   if ((long long)nchunk * ngroup > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "multidot: too many vectors");
   void *p = nullptr;
   unsigned *cnt = nullptr;

@@ -45,6 +45,18 @@ struct lqcd_ctx {
   double t_ms[K_NCLASS];
   long t_count[K_NCLASS];
   double t_units[K_NCLASS];
+  // CUDA graphs of fixed launch sequences (the Arnoldi steps of a Krylov cycle), keyed by every
+  // pointer and parameter they bake in; dropped whenever a workspace buffer is reallocated
+  bool graphs;
+  cudaStream_t cap_stream;   // private stream used only to capture
+  cudaStream_t run_stream;   // private stream for concurrent batched runs
+  struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec;
+    long nlaunch;            // kernels per replay
+  };
+  std::vector<GraphEntry> graph_cache;
+  int packed_nr;             // tuned right-hand sides per thread of the packed FP32 operator (0 = built in)
 };
 
 struct lqcd_defl {
@@ -86,9 +98,19 @@ lqcd_status launch_check(lqcd_ctx *ctx, const char *what, int cls, double units)
 enum WsSlot {
   WS_PARTIAL = 0, WS_SCAL, WS_TMP0, WS_TMP1, WS_TMP2, WS_TMP3, WS_BASIS, WS_HESS, WS_COEF,
   WS_BASIS2, WS_TMP4, WS_TMP5, WS_EST0, WS_EST1, WS_EST2, WS_PROBE,
-  WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_COUNT, WS_NSLOTS
+  WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_COUNT, WS_TUNE, WS_SPEC, WS_NBLK, WS_NSLOTS
 };
 lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr);
+void graph_cache_clear(lqcd_ctx *ctx);
+// Append the raw bytes of v to a graph key
+template <typename T> inline void key_add(std::string &k, const T &v) { k.append((const char *)&v, sizeof(T)); }
+// Run enqueue(arg) (a function that only enqueues work on ctx->stream: no synchronisation and no
+// workspace growth) through a cached CUDA graph under key, capturing it on first use; with graphs
+// off or device timing on, enqueue(arg) runs directly.
+lqcd_status graph_cached(lqcd_ctx *ctx, const std::string &key, lqcd_status (*enqueue)(void *), void *arg);
+// Reserve the workspace of blas_multidot / blas_norms for vectors of length n, nrhs right-hand
+// sides and up to max_nvec basis vectors (so graph capture never grows a buffer).
+lqcd_status blas_reserve(lqcd_ctx *ctx, long long n, int nrhs, int max_nvec);
 lqcd_status host_stage(lqcd_ctx *ctx, size_t bytes, double **ptr);
 
 // ----- complex helpers (device) -----------------------------------------------------------
@@ -176,6 +198,12 @@ template <> struct StoreScaled<__half2> { static constexpr bool value = true; };
 template <> struct StoreScaled<__nv_bfloat162> { static constexpr bool value = true; };
 static inline double half_sigma(long long N) { return std::ldexp(1.0, (int)std::floor(0.5 * std::log2((double)N))); }
 template <typename S> inline double store_sigma(long long N) { return StoreScaled<S>::value ? half_sigma(N) : 1.0; }
+// distinct tag per storage type (graph keys: FP16 and BF16 have the same size)
+template <typename S> struct StoreTag;
+template <> struct StoreTag<double2> { static constexpr int value = 0; };
+template <> struct StoreTag<float2> { static constexpr int value = 1; };
+template <> struct StoreTag<__half2> { static constexpr int value = 2; };
+template <> struct StoreTag<__nv_bfloat162> { static constexpr int value = 3; };
 
 // Batched level-1/level-2 kernels (blas.cu).  Templates are instantiated for double2 (FP64 path)
 // and for the inner-solver storage types float2, __half2, __nv_bfloat162 (two-type forms mix a
@@ -214,3 +242,6 @@ lqcd_status blas_to_f32(lqcd_ctx *ctx, const double2 *x, float2 *y, long long n)
 lqcd_status contract_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *eta,
                             const double2 *w, int nrhs, double2 *out_dev);
 lqcd_status noise_launch(lqcd_ctx *ctx, uint64_t seed, uint32_t first, int nrhs, double2 *out);
+// right-hand-side block width autotuner (batch.cu); see lqcd_autotune_block
+lqcd_status autotune_block(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl,
+                           const lqcd_krylov_opts *o, const int *cand, int ncand, int *best, double *seconds);

@@ -74,6 +74,7 @@ lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr) {
   if (slot < 0 || slot >= WS_NSLOTS) return set_err(ctx, LQCD_ERR_INVALID_ARG, "bad workspace slot %d", slot);
   if (bytes == 0) bytes = 16;
   if (ctx->ws_size[slot] < bytes) {
+    graph_cache_clear(ctx);  // captured graphs hold the old addresses
     if (ctx->ws_ptr[slot]) {
       // the old buffer may still be read by queued work
       cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -92,6 +93,58 @@ lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr) {
     ctx->ws_size[slot] = bytes;
   }
   *ptr = ctx->ws_ptr[slot];
+  return LQCD_OK;
+}
+
+void graph_cache_clear(lqcd_ctx *ctx) {
+  if (ctx->graph_cache.empty()) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto &g : ctx->graph_cache) cudaGraphExecDestroy(g.exec);
+  ctx->graph_cache.clear();
+}
+
+lqcd_status graph_cached(lqcd_ctx *ctx, const std::string &key, lqcd_status (*enqueue)(void *), void *arg) {
+  if (!ctx->graphs || ctx->timing) return enqueue(arg);
+  for (auto &g : ctx->graph_cache)
+    if (g.key == key) {
+      LQCD_CUDA(ctx, cudaGraphLaunch(g.exec, ctx->stream));
+      ctx->launches += g.nlaunch;
+      return LQCD_OK;
+    }
+  cudaStream_t user = ctx->stream;
+  LQCD_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+  ctx->stream = ctx->cap_stream;
+  const long l0 = ctx->launches;
+  const lqcd_status st = enqueue(arg);
+  ctx->stream = user;
+  const long nl = ctx->launches - l0;
+  ctx->launches = l0;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  if (st != LQCD_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st;
+  }
+  if (e != cudaSuccess || !g) {
+    cudaGetLastError();
+    return set_err(ctx, LQCD_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, LQCD_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+  }
+  if (ctx->graph_cache.size() >= 32) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaGraphExecDestroy(ctx->graph_cache.front().exec);
+    ctx->graph_cache.erase(ctx->graph_cache.begin());
+  }
+  ctx->graph_cache.push_back(lqcd_ctx::GraphEntry{key, ex, nl});
+  LQCD_CUDA(ctx, cudaGraphLaunch(ex, ctx->stream));
+  ctx->launches += nl;
   return LQCD_OK;
 }
 
@@ -154,6 +207,17 @@ lqcd_status lqcd_ctx_create(lqcd_ctx **out, const int dims[4], int link_recon, v
     c->t_count[k] = 0;
     c->t_units[k] = 0.0;
   }
+  c->graphs = true;
+  c->packed_nr = 0;
+  c->cap_stream = nullptr;
+  c->run_stream = nullptr;
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->run_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return LQCD_ERR_CUDA;
+  }
   *out = c;
   return LQCD_OK;
 }
@@ -161,6 +225,10 @@ lqcd_status lqcd_ctx_create(lqcd_ctx **out, const int dims[4], int link_recon, v
 lqcd_status lqcd_ctx_destroy(lqcd_ctx *ctx) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
   cudaStreamSynchronize(ctx->stream);
+  graph_cache_clear(ctx);
+  cudaStreamSynchronize(ctx->run_stream);
+  cudaStreamDestroy(ctx->cap_stream);
+  cudaStreamDestroy(ctx->run_stream);
   for (void *p : ctx->ws_ptr)
     if (p) cudaFree(p);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
@@ -176,6 +244,13 @@ lqcd_status lqcd_set_stream(lqcd_ctx *ctx, void *stream) {
 }
 
 const char *lqcd_last_error_string(const lqcd_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+lqcd_status lqcd_set_graphs(lqcd_ctx *ctx, int enable) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  ctx->graphs = enable != 0;
+  if (!ctx->graphs) graph_cache_clear(ctx);
+  return LQCD_OK;
+}
 
 long lqcd_kernel_launches(const lqcd_ctx *ctx) { return ctx ? ctx->launches : -1; }
 

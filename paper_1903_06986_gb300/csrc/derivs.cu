@@ -1,5 +1,5 @@
-// Derivatives of the loop estimates with respect to kappa and to the gauge links (north-star
-// addition; the paper has no derivatives).
+// Derivatives of the loop estimates with respect to kappa and to the gauge links (an addition:
+// the paper has no derivatives).
 //
 // With M = 1 - kappa P (Eq. xyz556): d M^{-1}/dkappa = M^{-1} P M^{-1}, so per noise, with
 // x = M^{-1} eta and y = M^{-1} P x,

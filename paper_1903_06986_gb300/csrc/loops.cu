@@ -167,23 +167,26 @@ __global__ void scaled_acc_kernel(const double2 *__restrict__ x, double2 *__rest
 // Probing colourings for the hopping traces.  Two sites of one colour class must be more than K
 // hops apart on the torus (K - 1 hops of P^k plus the one hop of a point-split operator), so that
 // every off-diagonal term of z_c^dag Theta P^k z_c vanishes.
-//   * scaled D4: with s = ceil((K + 1) / 2), classes are the cosets of s D4 = {v in s Z^4 :
-//     sum(v) / s even}, whose shortest non-zero vector has 2 s >= K + 1 hops; class =
-//     (x mod s per direction, parity of sum_mu floor(x_mu / s)); 2 s^4 classes.  Needs every
-//     extent divisible by 2 s (the torus periods then lie in s D4).
+//   * sublattice colouring: with s = ceil((K + 1) / 2) and an integer q >= 2, classes are the
+//     cosets of  {s w : w in Z^4, sum(w) = 0 mod q}, whose shortest non-zero vector has 2 s >= K + 1
+//     hops (s (e_mu - e_nu), or q s e_mu); class = (x mod s per direction, sum_mu floor(x_mu / s)
+//     mod q); q s^4 classes.  The torus periods L_mu e_mu lie in the sublattice when s divides
+//     every extent and q divides every L_mu / s; q = 2 is the scaled D4 lattice (extents divisible
+//     by 2 s, e.g. 8^3 x 16 at K = 7), q = 3 serves 12^4 and 12^3 x 24.
 //   * Cartesian fallback: class = (x mod p_mu) with p_mu the smallest divisor of L_mu that is
 //     >= K + 1, else L_mu.
+// The colouring with fewer classes is used.
 struct Colouring {
   int s[4];
-  int parity;
+  int q;     // 1: Cartesian
   int ncls;
 };
 
 __host__ __device__ __forceinline__ int class_of(const Colouring &c, int x, int y, int z, int t) {
   const int base = (x % c.s[0]) + c.s[0] * ((y % c.s[1]) + c.s[1] * ((z % c.s[2]) + c.s[2] * (t % c.s[3])));
-  if (!c.parity) return base;
-  const int par = (x / c.s[0] + y / c.s[1] + z / c.s[2] + t / c.s[3]) & 1;
-  return 2 * base + par;
+  if (c.q == 1) return base;
+  const int res = (x / c.s[0] + y / c.s[1] + z / c.s[2] + t / c.s[3]) % c.q;
+  return c.q * base + res;
 }
 
 // Probe vectors: probe p of the batch (global probe first + p) has colour class g / 12 and
@@ -249,9 +252,9 @@ __global__ void probe_contract_kernel(const double2 *__restrict__ U, double kapp
   const double2 *w = W + (long long)p * V * 12;
   const int g = first + p;
   const int cls = g / 12, comp = g % 12;
-  // decode the class into its residues (and parity for the scaled-D4 colouring)
-  const int par = col.parity ? (cls & 1) : 0;
-  int base = col.parity ? (cls >> 1) : cls;
+  // decode the class into its residues (and the sum residue mod q of the sublattice colouring)
+  const int par = cls % col.q;
+  int base = cls / col.q;
   const int rx = base % col.s[0];
   base /= col.s[0];
   const int ry = base % col.s[1];
@@ -271,7 +274,7 @@ __global__ void probe_contract_kernel(const double2 *__restrict__ U, double kapp
       for (int nz = 0; nz < Lz / col.s[2]; ++nz)
         for (int ny = 0; ny < Ly / col.s[1]; ++ny)
           for (int nx = 0; nx < Lx / col.s[0]; ++nx) {
-            if (col.parity && ((nx + ny + nz + nt) & 1) != par) continue;
+            if (col.q > 1 && (nx + ny + nz + nt) % col.q != par) continue;
             const int x = rx + col.s[0] * nx, y = ry + col.s[1] * ny, z = rz + col.s[2] * nz;
             const int m = x + Lx * (y + Ly * (z + Lz * tm));
             Cx<double> v = mk<double>(0.0, 0.0);
@@ -342,17 +345,7 @@ double now_s() {
 
 Colouring choose_colouring(const int *d, int K) {
   Colouring c;
-  const int sd = (K + 2) / 2;  // ceil((K + 1) / 2)
-  bool d4 = true;
-  for (int i = 0; i < 4; ++i)
-    if (d[i] % (2 * sd) != 0) d4 = false;
-  if (d4) {
-    for (int i = 0; i < 4; ++i) c.s[i] = sd;
-    c.parity = 1;
-    c.ncls = 2 * sd * sd * sd * sd;
-    return c;
-  }
-  c.parity = 0;
+  c.q = 1;
   c.ncls = 1;
   for (int i = 0; i < 4; ++i) {
     int p = d[i];
@@ -361,6 +354,24 @@ Colouring choose_colouring(const int *d, int K) {
     c.s[i] = p;
     c.ncls *= p;
   }
+  const int sd = (K + 2) / 2;  // ceil((K + 1) / 2)
+  int g = 0;
+  for (int i = 0; i < 4; ++i) {
+    if (d[i] % sd != 0) return c;
+    int a = d[i] / sd, b = g;
+    while (b) { const int t = a % b; a = b; b = t; }
+    g = a;  // gcd of the L_mu / s
+  }
+  for (int q = 2; q <= g; ++q)
+    if (g % q == 0) {
+      const long long n = (long long)q * sd * sd * sd * sd;
+      if (n < c.ncls) {
+        for (int i = 0; i < 4; ++i) c.s[i] = sd;
+        c.q = q;
+        c.ncls = (int)n;
+      }
+      break;
+    }
   return c;
 }
 
@@ -665,7 +676,7 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
                                           lqcd_estimate *out) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
   if (!links || !o || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: NULL argument");
-  if (o->nnoise < 1 || o->block < 1 || o->m < 2 || o->k < 1 || o->k >= o->m || o->K < 1 || o->npoly < 0 ||
+  if (o->nnoise < 1 || o->block < 0 || o->m < 2 || o->k < 1 || o->k >= o->m || o->K < 1 || o->npoly < 0 ||
       o->npoly > 63 || o->K > 64 || !(o->tol > 0) || !(o->tol_special > 0) || o->max_cycles < 1)
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: bad options");
   if (o->prec < LQCD_PREC_F64 || o->prec > LQCD_PREC_BF16)
@@ -677,20 +688,16 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
   const int modes = o->modes ? o->modes : LQCD_SUB_ALL;
   const double t0 = now_s();
   // 1. special right-hand side: GMRES-DR on M (projection space), MINRES-DR on M' (eigenpairs)
-  double2 *x0;
-  LQCD_CUDA(ctx, cudaMalloc(&x0, sizeof(double2) * (size_t)N * 2));
+  double2 *x0, *bs;
+  LQCD_TRY(ws_get(ctx, WS_SPEC, sizeof(double2) * (size_t)N * 4, (void **)&x0));
+  bs = x0 + 2 * N;
   struct Guard {
-    void *p;
     lqcd_defl *a, *b;
     ~Guard() {
-      if (p) cudaFree(p);
       if (a) lqcd_defl_destroy(a);
       if (b) lqcd_defl_destroy(b);
     }
-  } guard{x0, nullptr, nullptr};
-  double2 *bs;
-  LQCD_CUDA(ctx, cudaMalloc(&bs, sizeof(double2) * (size_t)N * 2));
-  struct Guard2 { void *p; ~Guard2() { if (p) cudaFree(p); } } g2{bs};
+  } guard{nullptr, nullptr};
   LQCD_TRY(noise_launch(ctx, o->seed, 0xFFFFFFFEu, 1, bs));
   LQCD_TRY(noise_launch(ctx, o->seed, 0xFFFFFFFEu, 1, bs + N));
   lqcd_krylov_opts ko{o->m, o->k, o->tol_special, o->max_cycles, LQCD_SYS_M, LQCD_PREC_F64};
@@ -762,13 +769,22 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
       A(4, op, t) = pert + ep;
       A(5, op, t) = poly + eq;
     }
+  lqcd_krylov_opts po{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec, o->inner_tol};
+  int block = o->block;
+  if (block == 0) {
+    // autotuned block width among 8, 16, 32, 64 (those not above the noise count)
+    std::vector<int> cand;
+    for (int c : {8, 16, 32, 64})
+      if (c <= o->nnoise) cand.push_back(c);
+    if (cand.empty()) cand.push_back(o->nnoise);
+    LQCD_TRY(autotune_block(ctx, links, kappa, dm, &po, cand.data(), (int)cand.size(), &block, nullptr));
+  }
   const double t1 = now_s();
   // 4. noise blocks
-  const int bw = std::min(o->block, o->nnoise);
+  const int bw = std::min(block, o->nnoise);
   const long long bn = (long long)bw * N;
   double2 *eta, *x, *xp, *xq, *y, *w, *cdv;
-  LQCD_CUDA(ctx, cudaMalloc(&eta, sizeof(double2) * (size_t)bn * 6));
-  struct Guard3 { void *p; ~Guard3() { if (p) cudaFree(p); } } g3{eta};
+  LQCD_TRY(ws_get(ctx, WS_NBLK, sizeof(double2) * (size_t)bn * 6, (void **)&eta));
   x = eta + bn;
   xp = x + bn;
   xq = xp + bn;
@@ -777,7 +793,6 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
   LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)bw * 9 * Lt, (void **)&cdv));
   const int nn = o->nnoise;
   std::vector<cd> per_noise_t((size_t)LQCD_NMODES * nn * 9 * Lt, cd(0.0, 0.0));
-  lqcd_krylov_opts po{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec, o->inner_tol};
   long matvecs_noise = 0;
   double worst = 0.0;
   int conv = 1;
@@ -869,6 +884,7 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
   out->seconds_noise = t2 - t1;
   out->max_true_resid = worst;
   out->converged = conv;
+  out->block = bw;
   return conv ? LQCD_OK : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop_estimate: a noise solve did not converge (rel %.3e)", worst);
 }
 

@@ -58,7 +58,7 @@ class Estimate(C.Structure):
     _fields_ = [("per_noise", _dp), ("per_t", _dp), ("addback", _dp), ("mean", _dp), ("stderr_", _dp),
                 ("lam", _dp), ("poly_a", _dp), ("matvecs_setup", C.c_long), ("matvecs_noise", C.c_long),
                 ("seconds_setup", C.c_double), ("seconds_noise", C.c_double), ("max_true_resid", C.c_double),
-                ("converged", C.c_int)]
+                ("converged", C.c_int), ("block", C.c_int)]
 
 
 class Derivs(C.Structure):
@@ -116,6 +116,11 @@ def load(path=None):
         "lqcd_loop_estimate": [vp, vp, d, C.POINTER(EstOpts), C.POINTER(Estimate)],
         "lqcd_link_grad": [vp, vp, d, vp, vp, i, d, vp, vp],
         "lqcd_loop_derivs": [vp, vp, d, C.POINTER(EstOpts), C.POINTER(Derivs)],
+        "lqcd_set_graphs": [vp, i],
+        "lqcd_autotune_block": [vp, vp, d, vp, C.POINTER(KrylovOpts), C.POINTER(C.c_int), i, C.POINTER(C.c_int),
+                                C.POINTER(C.c_double)],
+        "lqcd_batch_loop_estimate": [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(d), C.POINTER(EstOpts),
+                                     C.POINTER(Estimate), C.POINTER(C.c_int)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -267,13 +272,13 @@ class Context:
             raise ValueError("field size %d is not a multiple of 12 V = %d" % (t.numel(), self.N))
         return n
 
-    # a1
+    # Z(4) noise
     def noise_z4(self, seed, first, nrhs, out=None):
         out = self.field(nrhs) if out is None else out
         self._check(self.lib.lqcd_noise_z4(self.h, seed, first, nrhs, _ptr(out)))
         return out
 
-    # a2
+    # Wilson operator
     def wilson_apply(self, links, kappa, inp, out=None, flags=APPLY_M, prec=PREC_F64):
         out = _torch().empty_like(inp) if out is None else out
         self._check(self.lib.lqcd_wilson_apply(self.h, _ptr(links), kappa, _ptr(inp), _ptr(out),
@@ -342,7 +347,7 @@ class Context:
                                                    _ptr(out, c64), inp.numel() // self.N, flags))
         return out
 
-    # a3 / a4
+    # GMRES-DR / MINRES-DR
     def _krylov(self, fn, links, kappa, b, m, k, tol, max_cycles, system, want_defl, prec):
         x = _torch().empty_like(b)
         o = KrylovOpts(m, k, tol, max_cycles, system, prec)
@@ -364,7 +369,7 @@ class Context:
         return self._krylov(self.lib.lqcd_minresdr_solve, links, kappa, b, m, k, tol, max_cycles, SYS_MG5,
                             want_defl, prec)
 
-    # a5
+    # deflated multi-RHS solves
     def proj_solve(self, links, kappa, defl, b, m, tol, max_cycles=1000, system=SYS_M, prec=PREC_F64,
                    inner_tol=0.0):
         x = _torch().empty_like(b)
@@ -382,14 +387,14 @@ class Context:
         self._check(self.lib.lqcd_defl_import(self.h, len(lamh), _ptr(E), lp, C.byref(dh)))
         return Defl(self, dh)
 
-    # a6
+    # deflation projection
     def deflate_project(self, defl, eta, d):
         out = _torch().empty_like(eta)
         dh, dp = _host_c(d)
         self._check(self.lib.lqcd_deflate_project(self.h, defl.h, _ptr(eta), _ptr(out), self._nrhs(eta), dp))
         return out
 
-    # a7 / a8
+    # perturbative and polynomial series
     def hop_series(self, links, kappa, eta, K, c=None):
         out = _torch().empty_like(eta)
         if c is not None:
@@ -412,13 +417,13 @@ class Context:
         self._check(self.lib.lqcd_poly_coeffs(self.h, _ptr(links), kappa, seed, n, a.ctypes.data_as(C.c_void_p)))
         return a
 
-    # a9
+    # hopping traces
     def hop_traces(self, links, kappa, K):
         t = np.zeros((K, NOPS, self.dims[3]), dtype=np.complex128)
         self._check(self.lib.lqcd_hop_traces(self.h, _ptr(links), kappa, K, t.ctypes.data_as(C.c_void_p)))
         return t
 
-    # a10
+    # 1/xi'
     def xi_inverse(self, links, kappa, defl, sub, K, coeffs=None):
         xi = np.zeros(defl.k, dtype=np.complex128)
         if coeffs is not None:
@@ -429,7 +434,7 @@ class Context:
                                              xi.ctypes.data_as(C.c_void_p)))
         return xi
 
-    # a11
+    # contractions
     def contract(self, links, kappa, eta, w):
         n = self._nrhs(eta)
         out = np.zeros((n, NOPS, self.dims[3]), dtype=np.complex128)
@@ -440,26 +445,77 @@ class Context:
     # whole path
     def loop_estimate(self, links, kappa, seed, nnoise, block, m, k, K, npoly, tol, tol_special,
                       m_inner=0, max_cycles=2000, modes=SUB_ALL, prec=PREC_F64, inner_tol=0.0):
-        lt = self.dims[3]
+        """lqcd_loop_estimate; block = 0 lets the autotuner pick the block width."""
         o = EstOpts(seed, nnoise, block, m, k, m_inner, K, npoly, tol, tol_special, max_cycles, modes, prec,
                     inner_tol)
-        per_noise = np.zeros((6, nnoise, NOPS), dtype=np.complex128)
-        per_t = np.zeros((6, NOPS, lt), dtype=np.complex128)
-        addback = np.zeros((6, NOPS, lt), dtype=np.complex128)
-        mean = np.zeros((6, NOPS), dtype=np.complex128)
-        err = np.zeros((6, NOPS), dtype=np.float64)
-        lam = np.zeros(k, dtype=np.complex128)
-        pa = np.zeros(npoly + 1, dtype=np.complex128)
-        as_dp = lambda a: a.ctypes.data_as(_dp)
-        est = Estimate(as_dp(per_noise), as_dp(per_t), as_dp(addback), as_dp(mean), as_dp(err), as_dp(lam),
-                       as_dp(pa), 0, 0, 0.0, 0.0, 0.0, 0)
+        bufs, est = _estimate_buffers(self.dims[3], nnoise, k, npoly)
         st = self.lib.lqcd_loop_estimate(self.h, _ptr(links), kappa, C.byref(o), C.byref(est))
         if st not in (OK, ERR_NOT_CONVERGED):
             self._check(st)
-        return dict(per_noise=per_noise, per_t=per_t, addback=addback, mean=mean, stderr=err, lam=lam,
-                    poly_a=pa, matvecs_setup=est.matvecs_setup, matvecs_noise=est.matvecs_noise,
-                    seconds_setup=est.seconds_setup, seconds_noise=est.seconds_noise,
-                    max_true_resid=est.max_true_resid, converged=bool(est.converged), status=st)
+        return _estimate_result(bufs, est, st)
+
+    # batching
+    def set_graphs(self, enable):
+        self._check(self.lib.lqcd_set_graphs(self.h, 1 if enable else 0))
+
+    def autotune_block(self, links, kappa, defl, m, candidates=(8, 16, 32), prec=PREC_F64, inner_tol=0.0):
+        """lqcd_autotune_block: (best width, {width: seconds per right-hand side and cycle})."""
+        o = KrylovOpts(m, 0, 1e-10, 1, SYS_M, prec, inner_tol)
+        cand = (C.c_int * len(candidates))(*candidates)
+        secs = (C.c_double * len(candidates))()
+        best = C.c_int()
+        self._check(self.lib.lqcd_autotune_block(self.h, _ptr(links), kappa, defl.h, C.byref(o), cand,
+                                                 len(candidates), C.byref(best), secs))
+        return best.value, dict(zip(candidates, list(secs)))
+
+
+def _estimate_buffers(lt, nnoise, k, npoly):
+    bufs = dict(per_noise=np.zeros((6, nnoise, NOPS), dtype=np.complex128),
+                per_t=np.zeros((6, NOPS, lt), dtype=np.complex128),
+                addback=np.zeros((6, NOPS, lt), dtype=np.complex128),
+                mean=np.zeros((6, NOPS), dtype=np.complex128),
+                stderr=np.zeros((6, NOPS), dtype=np.float64),
+                lam=np.zeros(k, dtype=np.complex128),
+                poly_a=np.zeros(npoly + 1, dtype=np.complex128))
+    as_dp = lambda a: a.ctypes.data_as(_dp)
+    est = Estimate(*[as_dp(bufs[n]) for n in ("per_noise", "per_t", "addback", "mean", "stderr", "lam", "poly_a")],
+                   0, 0, 0.0, 0.0, 0.0, 0, 0)
+    return bufs, est
+
+
+def _estimate_result(bufs, est, st):
+    return dict(bufs, matvecs_setup=est.matvecs_setup, matvecs_noise=est.matvecs_noise,
+                seconds_setup=est.seconds_setup, seconds_noise=est.seconds_noise,
+                max_true_resid=est.max_true_resid, converged=bool(est.converged), block=est.block, status=st)
+
+
+def batch_loop_estimate(problems):
+    """lqcd_batch_loop_estimate: loop estimates of several problems (distinct contexts, lattices of any
+    size) run concurrently.  problems: list of dicts with ctx, links, kappa and the keyword arguments of
+    Context.loop_estimate (seed, nnoise, block, m, k, K, npoly, tol, tol_special, and optional m_inner,
+    max_cycles, modes, prec, inner_tol).  Returns the list of result dicts (each with its status)."""
+    n = len(problems)
+    opts = (EstOpts * n)()
+    ests = (Estimate * n)()
+    keep = []
+    for i, p in enumerate(problems):
+        opts[i] = EstOpts(p["seed"], p["nnoise"], p["block"], p["m"], p["k"], p.get("m_inner", 0), p["K"], p["npoly"],
+                          p["tol"], p["tol_special"], p.get("max_cycles", 2000), p.get("modes", SUB_ALL),
+                          p.get("prec", PREC_F64), p.get("inner_tol", 0.0))
+        bufs, est = _estimate_buffers(p["ctx"].dims[3], p["nnoise"], p["k"], p["npoly"])
+        ests[i] = est
+        keep.append(bufs)
+    ctxs = (C.c_void_p * n)(*[p["ctx"].h.value for p in problems])
+    links = (C.c_void_p * n)(*[_ptr(p["links"]).value for p in problems])
+    kappas = (C.c_double * n)(*[p["kappa"] for p in problems])
+    status = (C.c_int * n)()
+    problems[0]["ctx"].lib.lqcd_batch_loop_estimate(n, ctxs, links, kappas, opts, ests, status)
+    out = []
+    for i, p in enumerate(problems):
+        if status[i] not in (OK, ERR_NOT_CONVERGED):
+            p["ctx"]._check(status[i])
+        out.append(_estimate_result(keep[i], ests[i], status[i]))
+    return out
 
 
 def _link_grad_buffers(ctx, want_links):

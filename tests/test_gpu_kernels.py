@@ -175,10 +175,13 @@ def test_poly_coeffs_minimiser():
 
 
 @pytest.mark.parametrize("dims,K", [((4, 4, 4, 4), 5), ((2, 2, 2, 8), 3), ((3, 2, 2, 6), 4), ((4, 4, 4, 8), 3),
-                                    ((8, 4, 4, 8), 3)])
+                                    ((8, 4, 4, 8), 3), ((3, 3, 3, 6), 1), ((6, 6, 6, 6), 2)])
 def test_hop_traces_small(dims, K):
-    """The GPU probes with a scaled-D4 colouring where the extents allow it ((4,4,4,8) and (8,4,4,8)
-    with K = 3) and a Cartesian one otherwise; the oracle always uses its own Cartesian classes."""
+    """The GPU probes with a sublattice colouring where the extents allow it (sum residue mod 2, the
+    scaled D4 lattice, for (4,4,4,8) and (8,4,4,8) with K = 3; mod 3 for (3,3,3,6) with K = 1 and
+    (6,6,6,6) with K = 2) and a Cartesian one otherwise; the oracle always uses its own Cartesian
+    classes.  Probing is exact only if no two sites of a class are within K hops, so any colouring
+    error shows up as a difference."""
     ctx = context(dims)
     U = synth.su3_links(dims, 0.5, 11)
     kappa = 0.13
