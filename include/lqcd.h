@@ -256,6 +256,13 @@ lqcd_status lqcd_poly_coeffs(lqcd_ctx *ctx, const double *links, double kappa, u
  * K x 9 x Lt complex).  kappa enters only the point-split operators' own prefactor. */
 lqcd_status lqcd_hop_traces(lqcd_ctx *ctx, const double *links, double kappa, int K, double *t);
 
+/* The colour classes lqcd_hop_traces probes with (host only; needs no GPU and no context): for an
+ * Lx x Ly x Lz x Lt torus (dims[0..3], each >= 2) and K >= 1 terms, *nclasses receives the class
+ * count and, when classes is not NULL, classes[s] (host, V ints; s = x + Lx (y + Ly (z + Lz t)))
+ * the class of every site.  Any two sites of one class are more than K hops apart.  Returns
+ * LQCD_ERR_INVALID_ARG for bad arguments. */
+lqcd_status lqcd_probe_classes(const int dims[4], int K, int *nclasses, int *classes);
+
 /* ---- 1/xi' for HFPS / HFPOLY (Sec. 5.5) ------------------------------------------- */
 
 /* xi[q] = e'_q^dagger gamma_5 tilde M^{-1} e'_q (host out, k complex) with tilde M^{-1} the PS

@@ -642,6 +642,22 @@ lqcd_status lqcd_deflate_project(lqcd_ctx *ctx, const lqcd_defl *defl, const dou
   return deflate_dev(ctx, defl, (const double2 *)eta, (double2 *)out, nrhs, dd.data());
 }
 
+lqcd_status lqcd_probe_classes(const int dims[4], int K, int *nclasses, int *classes) {
+  if (!dims || !nclasses || K < 1 || K > 64) return LQCD_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2 || dims[i] > 1024) return LQCD_ERR_INVALID_ARG;
+  const Colouring c = choose_colouring(dims, K);
+  *nclasses = c.ncls;
+  if (classes) {
+    long long s = 0;
+    for (int t = 0; t < dims[3]; ++t)
+      for (int z = 0; z < dims[2]; ++z)
+        for (int y = 0; y < dims[1]; ++y)
+          for (int x = 0; x < dims[0]; ++x) classes[s++] = class_of(c, x, y, z, t);
+  }
+  return LQCD_OK;
+}
+
 lqcd_status lqcd_hop_traces(lqcd_ctx *ctx, const double *links, double kappa, int K, double *t) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
   if (!links || !t || K < 1 || K > 64) return set_err(ctx, LQCD_ERR_INVALID_ARG, "hop_traces: bad arguments");

@@ -117,6 +117,7 @@ def load(path=None):
         "lqcd_link_grad": [vp, vp, d, vp, vp, i, d, vp, vp],
         "lqcd_loop_derivs": [vp, vp, d, C.POINTER(EstOpts), C.POINTER(Derivs)],
         "lqcd_set_graphs": [vp, i],
+        "lqcd_probe_classes": [C.POINTER(C.c_int), i, C.POINTER(C.c_int), vp],
         "lqcd_autotune_block": [vp, vp, d, vp, C.POINTER(KrylovOpts), C.POINTER(C.c_int), i, C.POINTER(C.c_int),
                                 C.POINTER(C.c_double)],
         "lqcd_batch_loop_estimate": [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(d), C.POINTER(EstOpts),
@@ -467,6 +468,19 @@ class Context:
         self._check(self.lib.lqcd_autotune_block(self.h, _ptr(links), kappa, defl.h, C.byref(o), cand,
                                                  len(candidates), C.byref(best), secs))
         return best.value, dict(zip(candidates, list(secs)))
+
+
+def probe_classes(dims, K):
+    """lqcd_probe_classes (host only): (number of classes, class of every site as an int array of
+    shape (T, Z, Y, X))."""
+    lib = load()
+    d = (C.c_int * 4)(*dims)
+    n = C.c_int()
+    cls = np.zeros(int(np.prod(dims)), dtype=np.int32)
+    st = lib.lqcd_probe_classes(d, K, C.byref(n), cls.ctypes.data_as(C.c_void_p))
+    if st != OK:
+        raise LqcdError(st, "probe_classes: bad arguments")
+    return n.value, cls.reshape(dims[3], dims[2], dims[1], dims[0])
 
 
 def _estimate_buffers(lt, nnoise, k, npoly):

@@ -47,6 +47,23 @@ def test_loop_derivs_match_oracle():
     assert rel_err(host(g["link_grad"]), ref["link_grad"]) < 1e-8
 
 
+@pytest.mark.parametrize("prec", [1, 2], ids=["fp32", "fp16"])
+def test_loop_derivs_mixed_precision_match_fp64(prec):
+    """The derivative solves (x, y = M^{-1} P x, z = M^{-dag} eta) in mixed precision reach the same
+    FP64 true residual as the plain path, so the derivatives agree within cond * tol."""
+    dims, kappa = (2, 2, 2, 4), 0.14
+    ctx = context(dims)
+    U = dev(synth.su3_links(dims, 0.45, 2))
+    args = (5, 6, 3, 40, 8, 7, 1e-12, 1e-13)
+    ref = lqcd.loop_derivs(ctx, U, kappa, *args)
+    got = lqcd.loop_derivs(ctx, U, kappa, *args, prec=prec)
+    assert got["converged"] and got["max_true_resid"] <= 1e-12
+    for mode in range(2):
+        scale = np.abs(ref["per_noise"][mode]).max(axis=0)
+        assert np.all(np.abs(got["per_noise"][mode] - ref["per_noise"][mode]) <= 1e-8 * scale + 1e-10), mode
+    assert rel_err(host(got["link_grad"]), host(ref["link_grad"])) < 1e-8
+
+
 def test_dkappa_matches_finite_difference_of_estimates():
     """The GPU d/dkappa of the NS and PS estimates equals a fourth-order central difference of the GPU
     loop estimate itself (same noises), for all nine operators."""
