@@ -162,8 +162,10 @@ lqcd_status lqcd_to_f32(lqcd_ctx *ctx, const double *in, float *out, long long n
 lqcd_status lqcd_pack_f32(lqcd_ctx *ctx, const double *in, float *out, int nrhs);
 lqcd_status lqcd_unpack_f32(lqcd_ctx *ctx, const float *in, double *out, int nrhs);
 lqcd_status lqcd_pack_links_f32(lqcd_ctx *ctx, const double *links, float *out, int recon);
-/* Packed FP32 operator (flags as lqcd_wilson_apply): one thread per site and rhs_per_thread
- * right-hand sides (1, 2 or 4; 0 = automatic), so a link is read once per rhs_per_thread fields. */
+/* Packed FP32 operator (flags as lqcd_wilson_apply).  rhs_per_thread: 1 = one thread per site and
+ * right-hand side; 2 = two right-hand sides per thread in the two lanes of packed FP32 arithmetic
+ * (links loaded and rebuilt once for both); 4 = four per thread, scalar; 0 = the context's
+ * setting (lqcd_set_rhs_per_thread, or the autotuner's pick), else 2. */
 lqcd_status lqcd_wilson_apply_packed(lqcd_ctx *ctx, const float *links_packed, int recon, double kappa,
                                      const float *in, float *out, int nrhs, int flags, int rhs_per_thread);
 
@@ -178,6 +180,11 @@ lqcd_status lqcd_pack_half(lqcd_ctx *ctx, int prec, const double *in, void *out,
 lqcd_status lqcd_unpack_half(lqcd_ctx *ctx, int prec, const void *in, double *out, int nrhs);
 lqcd_status lqcd_wilson_apply_half(lqcd_ctx *ctx, int prec, const float *links_packed, int recon, double kappa,
                                    const void *in, void *out, int nrhs, int flags);
+/* Right-hand sides per thread of the packed operators used by this context when a call does not
+ * choose (0 = built-in choice, paired lanes; 1; 2 = paired lanes, also for FP16 / BF16 fields;
+ * 4 = FP32 only).
+ * The mixed-precision solvers use it; lqcd_autotune_block sets it. */
+lqcd_status lqcd_set_rhs_per_thread(lqcd_ctx *ctx, int nr);
 
 /* ---- GMRES-DR and MINRES-DR (Sec. 5.3, 7, 8) --------------------------------- */
 
@@ -347,8 +354,9 @@ lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, double kappa,
  * cycle over defl (a call limited to two cycles minus one limited to one, CUDA events on the
  * context's stream, after an untimed warm-up of each width), and picks the width with the least
  * time per right-hand side and cycle.  opts->prec selects the path (plain FP64 or mixed
- * precision); with LQCD_PREC_F32 it then also picks the packed operator's right-hand sides per
- * thread (1, 2 or 4) for that width and keeps it in the context.  Outputs (host): *best;
+ * precision); with a mixed precision it then also picks the packed inner operator's right-hand
+ * sides per thread (1, 2 or 4 for FP32 fields, 1 or 2 for FP16 / BF16) for that width and keeps it
+ * in the context (as lqcd_set_rhs_per_thread).  Outputs (host): *best;
  * seconds[i] = seconds per right-hand side and cycle of cand[i] (may be NULL).  Candidates must be
  * in 1..4096.  Uses the context's stream and synchronises with it. */
 lqcd_status lqcd_autotune_block(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl,

@@ -78,33 +78,55 @@ lqcd_status autotune_block(lqcd_ctx *ctx, const double *links, double kappa, con
       *best = nb;
     }
   }
-  if (o->prec == LQCD_PREC_F32) {
-    // right-hand sides per thread of the packed FP32 operator at the chosen width
+  if (o->prec != LQCD_PREC_F64) {
+    // right-hand sides per thread of the packed inner operator at the chosen width: 1, 2 (paired
+    // lanes) or 4 for FP32 fields, 1 or 2 for FP16 / BF16 fields
     float4 *Up, *in, *out;
     const int recon = ctx->recon, nb = *best;
-    const size_t fl = (size_t)ctx->V * 24 * nb;
+    const size_t fl = (size_t)ctx->V * 24 * nb;  // floats of nb packed FP32 fields
     LQCD_TRY(ws_get(ctx, WS_MIX_U, sizeof(float) * (size_t)ctx->V * 4 * (recon == 12 ? 12 : 20), (void **)&Up));
     LQCD_TRY(ws_get(ctx, WS_TMP2, sizeof(float) * fl * 2, (void **)&in));
     out = in + fl / 4;
     LQCD_TRY(pack_links_f32(ctx, (const double2 *)links, Up, recon));
-    LQCD_TRY(pack_f32(ctx, b, nullptr, in, nb));
+    if (o->prec == LQCD_PREC_F32) {
+      LQCD_TRY(pack_f32(ctx, b, nullptr, in, nb));
+    } else if (o->prec == LQCD_PREC_F16) {
+      LQCD_TRY(pack_lp(ctx, b, nullptr, (__half2 *)in, nb));
+    } else {
+      LQCD_TRY(pack_lp(ctx, b, nullptr, (__nv_bfloat162 *)in, nb));
+    }
+    const int saved = ctx->packed_nr;
     double tb = 0.0;
     int nr_best = 1;
     for (int nr : {1, 2, 4}) {
-      if (nr > nb) break;
+      if (nr > nb || (nr == 4 && o->prec != LQCD_PREC_F32)) break;
+      ctx->packed_nr = nr;
       auto f = [&] {
-        for (int rep = 0; rep < 3; ++rep)
-          LQCD_TRY(wilson_launch_packed(ctx, Up, recon, kappa, in, out, nb, LQCD_APPLY_M, nr));
+        for (int rep = 0; rep < 3; ++rep) {
+          if (o->prec == LQCD_PREC_F32) {
+            LQCD_TRY(wilson_launch_packed(ctx, Up, recon, kappa, in, out, nb, LQCD_APPLY_M, nr));
+          } else if (o->prec == LQCD_PREC_F16) {
+            LQCD_TRY(wilson_launch_packed_lp(ctx, Up, recon, kappa, (const __half2 *)in, (__half2 *)out, nb, LQCD_APPLY_M));
+          } else {
+            LQCD_TRY(wilson_launch_packed_lp(ctx, Up, recon, kappa, (const __nv_bfloat162 *)in, (__nv_bfloat162 *)out, nb,
+                                             LQCD_APPLY_M));
+          }
+        }
         return LQCD_OK;
       };
       double t = 0.0;
-      LQCD_TRY(f());
-      LQCD_TRY(timed(ctx, f, &t));
+      lqcd_status st = f();
+      if (st == LQCD_OK) st = timed(ctx, f, &t);
+      if (st != LQCD_OK) {
+        ctx->packed_nr = saved;
+        return st;
+      }
       if (nr == 1 || t < tb) {
         tb = t;
         nr_best = nr;
       }
     }
+    if (nr_best != saved) graph_cache_clear(ctx);
     ctx->packed_nr = nr_best;
   }
   return LQCD_OK;

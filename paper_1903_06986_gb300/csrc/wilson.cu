@@ -377,6 +377,180 @@ __global__ void __launch_bounds__(128) wilson_packed_kernel(const float4 *__rest
   }
 }
 
+// ---- paired-lane variant: two right-hand sides per thread in the two lanes of packed FP32
+// arithmetic (__fadd2_rn / __fmul2_rn / __ffma2_rn, one instruction for both lanes).  The stencil
+// code is the scalar one instantiated on the lane pair P2; the links are shared by both lanes
+// (loaded and rebuilt once), the spinors of the two right-hand sides are paired component by
+// component when loaded and split when stored.
+struct P2 {
+  float2 v;
+};
+__device__ __forceinline__ P2 p2(float a, float b) { return P2{make_float2(a, b)}; }
+__device__ __forceinline__ P2 operator+(P2 a, P2 b) { return P2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ P2 operator-(P2 a) { return P2{make_float2(-a.v.x, -a.v.y)}; }
+__device__ __forceinline__ P2 operator-(P2 a, P2 b) { return P2{__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y))}; }
+__device__ __forceinline__ P2 operator*(P2 a, P2 b) { return P2{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ P2 fma(P2 a, P2 b, P2 c) { return P2{__ffma2_rn(a.v, b.v, c.v)}; }
+using ::fma;  // keep the math overloads visible next to the lane-pair one
+
+// spinors of right-hand sides r and r + 1 (pointers a, b, chunk-major) -> lane pairs
+template <typename S> struct PairIO;
+template <> struct PairIO<float2> {
+  using T = float4;
+  static __device__ __forceinline__ void load(const T *__restrict__ a, const T *__restrict__ b, int V, Cx<P2> s[4][3]) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const float4 u = __ldg(a + (long long)q * V), w = __ldg(b + (long long)q * V);
+      const int c0 = 2 * q, c1 = 2 * q + 1;
+      s[c0 / 3][c0 % 3] = mk<P2>(p2(u.x, w.x), p2(u.y, w.y));
+      s[c1 / 3][c1 % 3] = mk<P2>(p2(u.z, w.z), p2(u.w, w.w));
+    }
+  }
+  static __device__ __forceinline__ void store(T *a, T *b, int V, const Cx<P2> s[4][3], bool second) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const Cx<P2> e = s[(2 * q) / 3][(2 * q) % 3], f = s[(2 * q + 1) / 3][(2 * q + 1) % 3];
+      a[(long long)q * V] = make_float4(e.x.v.x, e.y.v.x, f.x.v.x, f.y.v.x);
+      if (second) b[(long long)q * V] = make_float4(e.x.v.y, e.y.v.y, f.x.v.y, f.y.v.y);
+    }
+  }
+};
+template <typename H, typename T2, H (*LO)(H, H), H (*HI)(H, H), float2 (*TOF)(H), H (*FROMF)(float2)>
+struct PairIOHalf {
+  using T = T2;
+  static __device__ __forceinline__ void load(const T *__restrict__ a, const T *__restrict__ b, int V, Cx<P2> s[4][3]) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const T u = a[(long long)q * V], w = b[(long long)q * V];
+      const int c0 = 2 * q, c1 = 2 * q + 1;
+      // (re_r, im_r) and (re_r+1, im_r+1) -> (re_r, re_r+1) and (im_r, im_r+1), then to FP32
+      s[c0 / 3][c0 % 3] = mk<P2>(P2{TOF(LO(u.a, w.a))}, P2{TOF(HI(u.a, w.a))});
+      s[c1 / 3][c1 % 3] = mk<P2>(P2{TOF(LO(u.b, w.b))}, P2{TOF(HI(u.b, w.b))});
+    }
+  }
+  static __device__ __forceinline__ void store(T *a, T *b, int V, const Cx<P2> s[4][3], bool second) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const Cx<P2> e = s[(2 * q) / 3][(2 * q) % 3], f = s[(2 * q + 1) / 3][(2 * q + 1) % 3];
+      const H er = FROMF(e.x.v), ei = FROMF(e.y.v), fr = FROMF(f.x.v), fi = FROMF(f.y.v);
+      T o;
+      o.a = LO(er, ei);
+      o.b = LO(fr, fi);
+      a[(long long)q * V] = o;
+      if (second) {
+        o.a = HI(er, ei);
+        o.b = HI(fr, fi);
+        b[(long long)q * V] = o;
+      }
+    }
+  }
+};
+__device__ __forceinline__ __half2 h_lo(__half2 a, __half2 b) { return __lows2half2(a, b); }
+__device__ __forceinline__ __half2 h_hi(__half2 a, __half2 b) { return __highs2half2(a, b); }
+__device__ __forceinline__ float2 h_tof(__half2 a) { return __half22float2(a); }
+__device__ __forceinline__ __half2 h_fromf(float2 a) { return __float22half2_rn(a); }
+__device__ __forceinline__ __nv_bfloat162 b_lo(__nv_bfloat162 a, __nv_bfloat162 b) { return __lows2bfloat162(a, b); }
+__device__ __forceinline__ __nv_bfloat162 b_hi(__nv_bfloat162 a, __nv_bfloat162 b) { return __highs2bfloat162(a, b); }
+__device__ __forceinline__ float2 b_tof(__nv_bfloat162 a) { return __bfloat1622float2(a); }
+__device__ __forceinline__ __nv_bfloat162 b_fromf(float2 a) { return __float22bfloat162_rn(a); }
+template <> struct PairIO<__half2> : PairIOHalf<__half2, h2x2, h_lo, h_hi, h_tof, h_fromf> {};
+template <> struct PairIO<__nv_bfloat162> : PairIOHalf<__nv_bfloat162, b2x2, b_lo, b_hi, b_tof, b_fromf> {};
+
+template <typename S, int RECON, int MODE>
+__global__ void __launch_bounds__(128, 4) wilson_pair_kernel(const float4 *__restrict__ U,
+                                                          const typename Chunk<S>::T *__restrict__ in,
+                                                          typename Chunk<S>::T *__restrict__ out, float kappa,
+                                                          int Lx, int Ly, int Lz, int Lt, int V, int nrhs,
+                                                          int groups) {
+  using T = typename Chunk<S>::T;
+  const int s = (blockIdx.x / groups) * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const int r0 = (blockIdx.x % groups) * 2;
+  const bool second = r0 + 1 < nrhs;  // an odd last right-hand side runs in both lanes, stored once
+  const T *ia = in + (long long)r0 * 6 * V;
+  const T *ib = second ? ia + 6LL * V : ia;
+  constexpr bool G5IN = (MODE == 1 || MODE == 2);
+  int x = s % Lx, rr = s / Lx;
+  int y = rr % Ly;
+  rr /= Ly;
+  int z = rr % Lz;
+  int t = rr / Lz;
+  const int sy = Lx, sz = Lx * Ly, st = Lx * Ly * Lz;
+  int nb[8];
+  nb[0] = (x + 1 == Lx) ? s - (Lx - 1) : s + 1;
+  nb[1] = (x == 0) ? s + (Lx - 1) : s - 1;
+  nb[2] = (y + 1 == Ly) ? s - (Ly - 1) * sy : s + sy;
+  nb[3] = (y == 0) ? s + (Ly - 1) * sy : s - sy;
+  nb[4] = (z + 1 == Lz) ? s - (Lz - 1) * sz : s + sz;
+  nb[5] = (z == 0) ? s + (Lz - 1) * sz : s - sz;
+  nb[6] = (t + 1 == Lt) ? s - (Lt - 1) * st : s + st;
+  nb[7] = (t == 0) ? s + (Lt - 1) * st : s - st;
+  Cx<P2> acc[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[a][c] = mk<P2>(p2(0.f, 0.f), p2(0.f, 0.f));
+  Cx<P2> u[9], p[4][3];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const int mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    {
+      Cx<float> uf[9];
+      load_link_packed<RECON>(U, mu, V, fwd ? s : nb[d], uf);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) u[i] = mk<P2>(p2(uf[i].x, uf[i].x), p2(uf[i].y, uf[i].y));
+    }
+    PairIO<S>::load(ia + nb[d], ib + nb[d], V, p);
+    if (G5IN) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Cx<P2> a0 = p[0][c], a1 = p[1][c];
+        p[0][c] = neg(p[2][c]); p[1][c] = neg(p[3][c]); p[2][c] = neg(a0); p[3][c] = neg(a1);
+      }
+    }
+    if (fwd) {
+      if (mu == 0) term_fwd<P2, 0>(p, u, acc);
+      if (mu == 1) term_fwd<P2, 1>(p, u, acc);
+      if (mu == 2) term_fwd<P2, 2>(p, u, acc);
+      if (mu == 3) term_fwd<P2, 3>(p, u, acc);
+    } else {
+      if (mu == 0) term_bwd<P2, 0>(p, u, acc);
+      if (mu == 1) term_bwd<P2, 1>(p, u, acc);
+      if (mu == 2) term_bwd<P2, 2>(p, u, acc);
+      if (mu == 3) term_bwd<P2, 3>(p, u, acc);
+    }
+  }
+  T *oa = out + (long long)r0 * 6 * V + s;
+  T *ob = oa + 6LL * V;
+  if (MODE == 3) {
+    PairIO<S>::store(oa, ob, V, acc, second);
+    return;
+  }
+  PairIO<S>::load(ia + s, ib + s, V, p);
+  if (G5IN) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Cx<P2> a0 = p[0][c], a1 = p[1][c];
+      p[0][c] = neg(p[2][c]); p[1][c] = neg(p[3][c]); p[2][c] = neg(a0); p[3][c] = neg(a1);
+    }
+  }
+  const P2 mk2 = p2(-kappa, -kappa);
+  Cx<P2> o[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[a][c] = mk<P2>(fma(mk2, acc[a][c].x, p[a][c].x), fma(mk2, acc[a][c].y, p[a][c].y));
+  if (MODE == 2) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Cx<P2> a0 = o[0][c], a1 = o[1][c];
+      o[0][c] = neg(o[2][c]); o[1][c] = neg(o[3][c]); o[2][c] = neg(a0); o[3][c] = neg(a1);
+    }
+  }
+  PairIO<S>::store(oa, ob, V, o, second);
+}
+
 // canonical complex128 fields -> packed storage S, y = sigma * x / s[r] (s == NULL: s[r] = 1)
 template <typename S>
 __global__ void pack_kernel(const double2 *__restrict__ x, const double *__restrict__ s,
@@ -444,6 +618,30 @@ __global__ void pack_links_kernel(const double2 *__restrict__ U, float4 *__restr
   }
 }
 
+template <typename S, int RECON>
+lqcd_status pair_launch(lqcd_ctx *ctx, const float4 *U, double kappa, const void *in_, void *out_, int nrhs, int flags) {
+  using T = typename Chunk<S>::T;
+  const T *in = (const T *)in_;
+  T *out = (T *)out_;
+  int bs = 128;
+  const int groups = (nrhs + 1) / 2;
+  while (bs > 32 && (long long)ceil_div(ctx->V, bs) * groups < 2LL * ctx->sms) bs /= 2;
+  const long long nblk = (long long)ceil_div(ctx->V, bs) * groups;
+  if (nblk > 0x7fffffffLL) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: grid too large");
+  dim3 grid((unsigned)nblk);
+  const int *d = ctx->dims;
+  const float k = (float)kappa;
+  kbegin(ctx);
+  switch (flags) {
+    case LQCD_APPLY_M: wilson_pair_kernel<S, RECON, 0><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
+    case LQCD_APPLY_G5R: wilson_pair_kernel<S, RECON, 1><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
+    case LQCD_APPLY_DAG: wilson_pair_kernel<S, RECON, 2><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
+    case LQCD_APPLY_HOP: wilson_pair_kernel<S, RECON, 3><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
+    default: return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: unknown flags %d", flags);
+  }
+  return launch_check(ctx, "wilson_pair_kernel", K_WILSON, (double)ctx->V * nrhs);
+}
+
 template <typename S, int NR, int RECON>
 lqcd_status packed_launch_nr(lqcd_ctx *ctx, const float4 *U, double kappa, const void *in_, void *out_, int nrhs,
                              int flags) {
@@ -475,27 +673,35 @@ lqcd_status wilson_launch_packed(lqcd_ctx *ctx, const float4 *U, int recon, doub
                                  int nrhs, int flags, int nr) {
   if (nrhs <= 0) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: nrhs %d out of range", nrhs);
   if (recon != 12 && recon != 18) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: recon must be 12 or 18");
-  // measured on 24^3 x 32: with reconstructed links one right-hand side per thread is fastest (the
-  // link reconstruction is cheap, the registers saved keep occupancy up); with 18-real links two
-  if (nr <= 0) nr = (recon == 12 || nrhs < 2) ? 1 : 2;
+  // nr: 1 = one right-hand side per thread, 2 = two in the lanes of packed FP32 arithmetic, 4 = four
+  // per thread (scalar); 0 = the context's setting (lqcd_set_rhs_per_thread or the autotuner), else
+  // 2: on 24^3 x 32 with 8 and 16 right-hand sides the paired lanes take 13 % less time than one
+  // right-hand side per thread (the stencil is bound by instruction issue, not by HBM)
+  if (nr <= 0) nr = ctx->packed_nr > 0 ? ctx->packed_nr : 2;
+  if (nr == 2 && nrhs < 2) nr = 1;
   if (recon == 12) {
     if (nr == 1) return packed_launch_nr<float2, 1, 12>(ctx, U, kappa, in, out, nrhs, flags);
-    if (nr == 2) return packed_launch_nr<float2, 2, 12>(ctx, U, kappa, in, out, nrhs, flags);
+    if (nr == 2) return pair_launch<float2, 12>(ctx, U, kappa, in, out, nrhs, flags);
     return packed_launch_nr<float2, 4, 12>(ctx, U, kappa, in, out, nrhs, flags);
   }
   if (nr == 1) return packed_launch_nr<float2, 1, 18>(ctx, U, kappa, in, out, nrhs, flags);
-  if (nr == 2) return packed_launch_nr<float2, 2, 18>(ctx, U, kappa, in, out, nrhs, flags);
+  if (nr == 2) return pair_launch<float2, 18>(ctx, U, kappa, in, out, nrhs, flags);
   return packed_launch_nr<float2, 4, 18>(ctx, U, kappa, in, out, nrhs, flags);
 }
 
-// FP16 / BF16 fields: one right-hand side per thread (the FP32 sweep's best with recon 12; with half
-// the bytes per field the link share of the traffic only grows, which L2 absorbs across the groups)
+// FP16 / BF16 fields: two right-hand sides per thread in paired lanes (19 % less time than one per
+// thread on 24^3 x 32 with 8 right-hand sides), or one when the context's setting is 1
 template <typename S>
 lqcd_status wilson_launch_packed_lp(lqcd_ctx *ctx, const float4 *U, int recon, double kappa, const S *in, S *out,
                                    int nrhs, int flags) {
   if (nrhs <= 0) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: nrhs %d out of range", nrhs);
-  if (recon == 12) return packed_launch_nr<S, 1, 12>(ctx, U, kappa, in, out, nrhs, flags);
-  if (recon == 18) return packed_launch_nr<S, 1, 18>(ctx, U, kappa, in, out, nrhs, flags);
+  const bool pair = (ctx->packed_nr == 2 || ctx->packed_nr == 0) && nrhs >= 2;
+  if (recon == 12)
+    return pair ? pair_launch<S, 12>(ctx, U, kappa, in, out, nrhs, flags)
+                : packed_launch_nr<S, 1, 12>(ctx, U, kappa, in, out, nrhs, flags);
+  if (recon == 18)
+    return pair ? pair_launch<S, 18>(ctx, U, kappa, in, out, nrhs, flags)
+                : packed_launch_nr<S, 1, 18>(ctx, U, kappa, in, out, nrhs, flags);
   return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: recon must be 12 or 18");
 }
 template lqcd_status wilson_launch_packed_lp<__half2>(lqcd_ctx *, const float4 *, int, double, const __half2 *,
@@ -596,4 +802,13 @@ extern "C" lqcd_status lqcd_wilson_apply_half(lqcd_ctx *ctx, int prec, const flo
     return wilson_launch_packed_lp(ctx, (const float4 *)links_packed, recon, kappa, (const __nv_bfloat162 *)in,
                                    (__nv_bfloat162 *)out, nrhs, flags);
   return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_half: prec must be LQCD_PREC_F16 or LQCD_PREC_BF16");
+}
+
+extern "C" lqcd_status lqcd_set_rhs_per_thread(lqcd_ctx *ctx, int nr) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (nr != 0 && nr != 1 && nr != 2 && nr != 4)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "set_rhs_per_thread: nr must be 0, 1, 2 or 4");
+  graph_cache_clear(ctx);
+  ctx->packed_nr = nr;
+  return LQCD_OK;
 }

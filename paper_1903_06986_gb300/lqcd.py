@@ -117,6 +117,7 @@ def load(path=None):
         "lqcd_link_grad": [vp, vp, d, vp, vp, i, d, vp, vp],
         "lqcd_loop_derivs": [vp, vp, d, C.POINTER(EstOpts), C.POINTER(Derivs)],
         "lqcd_set_graphs": [vp, i],
+        "lqcd_set_rhs_per_thread": [vp, i],
         "lqcd_probe_classes": [C.POINTER(C.c_int), i, C.POINTER(C.c_int), vp],
         "lqcd_autotune_block": [vp, vp, d, vp, C.POINTER(KrylovOpts), C.POINTER(C.c_int), i, C.POINTER(C.c_int),
                                 C.POINTER(C.c_double)],
@@ -456,6 +457,9 @@ class Context:
         return _estimate_result(bufs, est, st)
 
     # batching
+    def set_rhs_per_thread(self, nr):
+        self._check(self.lib.lqcd_set_rhs_per_thread(self.h, nr))
+
     def set_graphs(self, enable):
         self._check(self.lib.lqcd_set_graphs(self.h, 1 if enable else 0))
 

@@ -50,7 +50,7 @@ def test_wilson_all_forms(dims):
     for flag, ref in forms.items():
         got = host(ctx.wilson_apply_f32(U32, kappa, p32, flags=flag))
         assert rel_err(got, ref(psi)) < 2e-6, flag
-    # packed FP32 operator, recon 18 and 12, 1, 2 and 4 right-hand sides per thread
+    # packed FP32 operator, recon 18 and 12, 1, 2 (paired lanes) and 4 right-hand sides per thread
     packed = ctx.pack_f32(pd)
     assert np.array_equal(host(ctx.unpack_f32(packed)), psi.astype(np.complex64).astype(np.complex128))
     for recon in (18, 12):
@@ -86,16 +86,20 @@ def test_wilson_half_storage(dims, prec):
         assert np.all(np.abs(part(back) - part(psi)) <= (u + 2.0 ** -24) * np.abs(part(psi)) + 1e-12)
     forms = {0: lambda f: L.wilson(U, kappa, f), 1: lambda f: L.wilson_g5(U, kappa, f),
              2: lambda f: L.wilson_dag(U, kappa, f), 3: lambda f: L.hop(U, f)}
-    for recon in (18, 12):
-        Up = ctx.pack_links_f32(Ud, recon)
-        for flag, ref in forms.items():
-            want = ref(psi)
-            got = host(ctx.unpack_half(ctx.wilson_apply_half(Up, recon, kappa, packed, flags=flag, prec=prec), prec))
-            for r in range(3):
-                bound = u * ((1 + 16 * kappa) * np.linalg.norm(psi[r]) + np.linalg.norm(want[r]))
-                assert np.linalg.norm(got[r] - want[r]) <= bound, (recon, flag, r)
-            # and it is not merely within the bound by luck of a loose bound: error of order u
-            assert rel_err(got, want) > 1e-3 * u
+    for nr in (1, 2):   # one right-hand side per thread, or two in paired lanes (3 fields: one pair + odd one)
+        ctx.set_rhs_per_thread(nr)
+        for recon in (18, 12):
+            Up = ctx.pack_links_f32(Ud, recon)
+            for flag, ref in forms.items():
+                want = ref(psi)
+                got = host(ctx.unpack_half(ctx.wilson_apply_half(Up, recon, kappa, packed, flags=flag, prec=prec),
+                                           prec))
+                for r in range(3):
+                    bound = u * ((1 + 16 * kappa) * np.linalg.norm(psi[r]) + np.linalg.norm(want[r]))
+                    assert np.linalg.norm(got[r] - want[r]) <= bound, (nr, recon, flag, r)
+                # and it is not merely within the bound by luck of a loose bound: error of order u
+                assert rel_err(got, want) > 1e-3 * u
+    ctx.set_rhs_per_thread(0)
 
 
 @pytest.mark.parametrize("dims", DIMS[:3])
