@@ -26,7 +26,7 @@ Mat adjoint(const Mat &A);
 // d = argmin || c - A d ||_2 (A: rows >= cols, full column rank) by Householder QR
 std::vector<cd> lstsq(const Mat &A, const std::vector<cd> &c);
 
-// x = A^{-1} b by LU with partial pivoting; returns false if A is singular to working precision
+// x = A^{-1} b by LU with partial pivoting; returns false on an exactly zero pivot
 bool solve(const Mat &A, const std::vector<cd> &b, std::vector<cd> &x);
 
 // Complex Schur decomposition A = Z T Z^H (Hessenberg reduction + shifted QR);
