@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--batch", action="store_true", help="also measure the uneven multi-lattice batch")
-    ap.add_argument("--case", default=None, choices=["gmres-cycle", "gmres-cycle-f32", "dslash-packed", "dslash-half"],
+    ap.add_argument("--no-defl", action="store_true")
+    ap.add_argument("--case", default=None,
+                    choices=["gmres-cycle", "gmres-cycle-f32", "dslash-packed", "dslash-half", "defl-tensor"],
                     help="run one small kernel case for profiling instead of the benchmark: one GMRES(30) "
                          "cycle on 50 noises of the 8^3x16 workload (FP64, or FP32 storage)")
     return ap.parse_args()
@@ -211,7 +213,17 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 DSLASH_DIMS = (24, 24, 24, 32)   # the paper's large lattice (Sec. 7); fields exceed L2 at nrhs >= 2
-HBM_PEAK_GBS = 6793.4            # measured copy bandwidth of this GB300 pool
+def _measured_hbm_gbs(default=6789.6):
+    """Copy bandwidth measured on this GPU pool (MEASURED_PEAKS.json beside this file), else the
+    last measured value."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return default
+
+
+HBM_PEAK_GBS = _measured_hbm_gbs()
 
 
 def dslash_rates(torch):
@@ -271,6 +283,80 @@ def dslash_rates(torch):
     ctx.close()
     return {"lattice": "24x24x24x32", "bytes": "nrhs*V*24 reals read+written + links once",
             "hbm_peak_gbs": HBM_PEAK_GBS, "results": out}
+
+
+DEFL_DIMS = (24, 24, 24, 32)
+DEFL_K, DEFL_NRHS = 200, 16
+
+
+def deflation_rates(torch):
+    """HFES projection gamma_5 V' diag(d) V'^dag eta (Sec. 5.4) on the 24^3x32 lattice with 200
+    deflation vectors and 16 Z(4) noises: FP64 CUDA-core kernels against the split-precision
+    tcgen05 kernels (bf16 slices, FP64 accuracy).  The vectors are seeded Gaussian (the projection's
+    cost does not depend on their values).  CUDA events on the library stream, 1 warm-up and 3 timed
+    projections per engine; the operands (17 GB of vectors, 71 GB of slices) exceed L2 by far.
+    Algorithmic bytes of the tensor-core launches per projection: the two slice copies of V' read
+    once (7 bf16 slices per real entry, in row tiles of 128 vectors for V'^dag eta and in K chunks
+    of 32 vectors for V' C), the noise slice read once, the output fields written once."""
+    from paper_1903_06986_gb300 import lqcd
+    ctx = lqcd.Context(DEFL_DIMS)
+    V = int(np.prod(DEFL_DIMS))
+    n = 12 * V
+    k, nrhs = DEFL_K, DEFL_NRHS
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    E = torch.randn((k, n), dtype=torch.complex128, device="cuda", generator=gen)
+    E /= torch.linalg.vector_norm(E, dim=1, keepdim=True)
+    lam = (0.05 + 0.01 * np.arange(k)) * np.where(np.arange(k) % 2 == 0, 1.0, -1.0)
+    defl = ctx.defl_import(E.reshape((k,) + tuple(ctx.field(1).shape[1:])), lam.astype(np.complex128))
+    del E
+    eta = ctx.noise_z4(9, 0, nrhs)
+    d = 1.0 / lam
+    out = {}
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1000.0, r
+
+    ctx.set_defl_engine(lqcd.DEFL_FP64)
+    t64, y64 = timed(lambda: ctx.deflate_project(defl, eta, d))
+    ctx.set_defl_engine(lqcd.DEFL_TENSOR)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.deflate_project(defl, eta, d)                 # makes the slices of V' (once per space)
+    torch.cuda.synchronize()
+    t_slice = time.perf_counter() - t0
+    ctx.timing(True)
+    ctx.timing_reset()
+    ttc, ytc = timed(lambda: ctx.deflate_project(defl, eta, d))
+    tm = ctx.timing_read()
+    ctx.timing(False)
+    ctx.set_defl_engine(lqcd.DEFL_FP64)
+    err = float((ytc - y64).abs().max().item() / y64.abs().max().item())
+    L_re = 2 * n
+    np16 = max(16, ((2 * nrhs + 15) // 16) * 16)
+    bytes_alg = 14.0 * k * L_re + 2.0 * np16 * L_re + 14.0 * L_re * (((k + 31) // 32) * 32) + 8.0 * nrhs * L_re
+    ms_t, nl_t, _ = tm["tensor"]
+    per_proj = ms_t / 1000.0 / 4                      # 4 projections ran with timing on (1 warm + 3 timed)
+    gbs = bytes_alg / per_proj / 1e9
+    emu_flops = 8.0 * k * nrhs * n * 2                # the FP64 complex products emulated (two contractions)
+    out = {"lattice": "24x24x24x32", "k": k, "nrhs": nrhs, "fp64_ms": round(t64 * 1e3, 3),
+           "tensor_ms": round(ttc * 1e3, 3), "speedup": round(t64 / ttc, 2), "slice_setup_s": round(t_slice, 3),
+           "max_rel_diff_vs_fp64": err,
+           "tensor_kernel": {"launches_per_projection": nl_t / 4, "ms_per_projection": round(per_proj * 1e3, 3),
+                             "algorithmic_bytes": bytes_alg, "GB/s": round(gbs, 1),
+                             "frac_hbm": round(gbs / HBM_PEAK_GBS, 4),
+                             "fp64_equivalent_tflops": round(emu_flops / per_proj / 1e12, 3)},
+           "breakdown_ms": {kk: round(v[0] / 4, 3) for kk, v in tm.items() if v[0] > 0}}
+    defl.close()
+    ctx.close()
+    return out
 
 
 BATCH_SHAPES = ((8, 8, 8, 8), (12, 12, 12, 12), (12, 12, 12, 24), (16, 16, 16, 16))
@@ -341,6 +427,22 @@ def run_case(args):
     import torch
     from paper_1903_06986_gb300 import build, lqcd, synth
     build.build()
+    if args.case == "defl-tensor":
+        # 12^3x24, 128 vectors, 16 Z(4) noises: slices of V' 3.6 GB, two projections
+        dims = (12, 12, 12, 24)
+        ctx = lqcd.Context(dims)
+        n = 12 * int(np.prod(dims))
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        E = torch.randn((128, n), dtype=torch.complex128, device="cuda", generator=gen)
+        lam = np.linspace(0.05, 0.5, 128).astype(np.complex128)
+        defl = ctx.defl_import(E.reshape((128,) + tuple(ctx.field(1).shape[1:])), lam)
+        eta = ctx.noise_z4(9, 0, 16)
+        ctx.set_defl_engine(lqcd.DEFL_TENSOR)
+        for _ in range(2):
+            ctx.deflate_project(defl, eta, 1.0 / lam)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "launches": ctx.launches}))
+        return
     if args.case in ("dslash-packed", "dslash-half"):
         ctx = lqcd.Context(DSLASH_DIMS, recon=12)
         U = torch.from_numpy(synth.su3_links(DSLASH_DIMS, 0.4323, 7)).cuda()
@@ -521,6 +623,12 @@ def main():
         roofline["wilson_fp64_tflops"] = w[2] * WILSON_FLOPS / (w[0] / 1000.0) / 1e12
 
     dslash = None if args.no_dslash else dslash_rates(torch)
+    deflation = None
+    if not args.no_defl:
+        try:
+            deflation = deflation_rates(torch)
+        except Exception as e:  # reported, not fatal
+            deflation = {"error": str(e)[:300]}
     batching = None
     if args.batch:
         try:
@@ -551,6 +659,7 @@ def main():
                 "e2e": {"value": e2e_value, "unit": "estimates/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
                 "clocks": clk, "cpu_baseline": cpu, "mixed_precision": mixed, "dslash": dslash,
+                "deflation_tensor_cores": deflation,
                 "batching": batching}
         print(json.dumps(line))
     if world > 1:

@@ -123,7 +123,9 @@ long lqcd_kernel_launches(const lqcd_ctx *ctx);
 #define LQCD_K_BLAS1 6    /* copies, scalings, gamma_5, axpy                             */
 #define LQCD_K_NOISE 7    /* Z(4) noise generation                                       */
 #define LQCD_K_PROBE 8    /* probe-vector generation for the hopping traces              */
-#define LQCD_K_NCLASS 9
+#define LQCD_K_TENSOR 9   /* tcgen05 split-precision contractions (units: complex MACs)   */
+#define LQCD_K_SLICE 10   /* operand statistics and bf16 slicing for them (units: elements) */
+#define LQCD_K_NCLASS 11
 lqcd_status lqcd_timing_enable(lqcd_ctx *ctx, int enable);
 lqcd_status lqcd_timing_reset(lqcd_ctx *ctx);
 lqcd_status lqcd_timing_read(lqcd_ctx *ctx, int cls, double *total_ms, long *launches, double *units);
@@ -242,6 +244,31 @@ lqcd_status lqcd_defl_import(lqcd_ctx *ctx, int k, const double *E, const double
  * eta, out: device, nrhs * 12 V. */
 lqcd_status lqcd_deflate_project(lqcd_ctx *ctx, const lqcd_defl *defl, const double *eta,
                                  double *out, int nrhs, const double *d);
+
+/* ---- FP64 deflation contractions on the tensor cores (Sec. 5.4) ------------------------ */
+
+/* The two dense products of the HFES projection, V'^dagger eta and V' C, can run on the tcgen05
+ * tensor cores with FP64 accuracy by split-precision emulation: each FP64 operand row / column is
+ * scaled by a power of two and cut into seven bf16 slices of 8 bits (balanced digits), the slice
+ * products are accumulated in FP32 tensor memory in groups that stay exact integers, and the groups
+ * are folded into FP64 (error below 2^-53 of sum_i |a_i||b_i| plus FP64 rounding of the folds).
+ * A right-hand side made of small integers times one power of two (Z(4) noise) is a single exact
+ * slice.  The slices of a deflation space take 28 bytes per complex entry of device memory. */
+#define LQCD_DEFL_FP64 0   /* FP64 CUDA-core kernels (default)                                */
+#define LQCD_DEFL_TENSOR 1 /* split-precision tensor-core kernels                             */
+/* Select the engine of lqcd_deflate_project and of the HFES / HFPS / HFPOLY projections inside
+ * lqcd_loop_estimate for this context.  With LQCD_DEFL_TENSOR the slices of a deflation object
+ * are made on its first projection and kept until lqcd_defl_destroy.  LQCD_ERR_INVALID_ARG for an
+ * unknown engine. */
+lqcd_status lqcd_set_defl_engine(lqcd_ctx *ctx, int engine);
+/* G[q * nrhs + r] = E_q^dagger X_r on the tensor cores (one-shot: E is sliced on every call).
+ * E: device, k x 12V complex128 vectors (vector-major); X: device, nrhs fields; G: device output,
+ * k x nrhs complex128.  1 <= k <= 4096.  Returns LQCD_ERR_NONFINITE for a NaN / Inf input,
+ * LQCD_ERR_OOM if the slices do not fit, LQCD_ERR_TIMEOUT if a pipeline wait ran out. */
+lqcd_status lqcd_tc_vdag_x(lqcd_ctx *ctx, const double *E, int k, const double *X, int nrhs, double *G);
+/* Y_r = sum_q E_q C[q * nrhs + r] on the tensor cores (one-shot).  E as above; C: device,
+ * k x nrhs complex128; Y: device output, nrhs fields (must not overlap E or C).  Errors as above. */
+lqcd_status lqcd_tc_v_c(lqcd_ctx *ctx, const double *E, int k, const double *C, int nrhs, double *Y);
 
 /* ---- perturbative and polynomial series (Sec. 5.1, 5.2) ---------------------- */
 

@@ -127,6 +127,18 @@ def poly_addback(t, kappa, b):
     return sum(b[k] * (kappa ** k) * t[k] for k in range(len(b)))
 
 
+def defl_coeffs(E, X):
+    """C = V'^dag eta (Sec. 5.4) for the Q columns of E (N_dim, Q) and the fields X (n, ...):
+    C[q, r] = sum_i conj(E[i, q]) X_r[i].  Returns (Q, n)."""
+    xf = X.reshape(X.shape[0], -1)
+    return E.conj().T @ xf.T
+
+
+def defl_expand(E, Cm):
+    """Y_r = sum_q E[:, q] C[q, r] (the V' C of Sec. 5.4) as (n, N_dim) rows."""
+    return (E @ Cm).T
+
+
 def defl_vector(E, dvals, eta):
     """gamma_5 V' diag(dvals) V'^dag eta for fields eta (..., T, Z, Y, X, 4, 3); E is (N_dim, Q)."""
     dims_shape = eta.shape[-6:]

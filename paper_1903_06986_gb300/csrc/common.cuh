@@ -14,7 +14,8 @@
 #include "lqcd.h"
 
 // kernel classes for the optional per-class device timing (values of LQCD_K_* in lqcd.h)
-enum KClass { K_WILSON = 0, K_DOT, K_AXPY, K_COMBINE, K_NORM, K_CONTRACT, K_BLAS1, K_NOISE, K_PROBE, K_NCLASS };
+enum KClass { K_WILSON = 0, K_DOT, K_AXPY, K_COMBINE, K_NORM, K_CONTRACT, K_BLAS1, K_NOISE, K_PROBE, K_TENSOR, K_SLICE,
+              K_NCLASS };
 
 struct TimedLaunch {
   int start, end, cls;  // indices into lqcd_ctx::ev_pool
@@ -57,6 +58,7 @@ struct lqcd_ctx {
   };
   std::vector<GraphEntry> graph_cache;
   int packed_nr;             // tuned right-hand sides per thread of the packed FP32 operator (0 = built in)
+  int defl_engine;           // LQCD_DEFL_FP64 or LQCD_DEFL_TENSOR (deflation projections)
 };
 
 struct lqcd_defl {
@@ -70,6 +72,7 @@ struct lqcd_defl {
   std::vector<double2> lam;   // k eigenvalues (host)
   std::vector<double> eres;   // k eigen residual norms (host)
   double2 *Hbar_dev;    // (k+1) x k row-major (device), NULL when imported
+  void *tc;             // bf16 slices of E for the tensor-core contractions (made on first use)
 };
 
 // ----- status plumbing ------------------------------------------------------------------
@@ -98,7 +101,7 @@ lqcd_status launch_check(lqcd_ctx *ctx, const char *what, int cls, double units)
 enum WsSlot {
   WS_PARTIAL = 0, WS_SCAL, WS_TMP0, WS_TMP1, WS_TMP2, WS_TMP3, WS_BASIS, WS_HESS, WS_COEF,
   WS_BASIS2, WS_TMP4, WS_TMP5, WS_EST0, WS_EST1, WS_EST2, WS_PROBE,
-  WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_COUNT, WS_TUNE, WS_SPEC, WS_NBLK, WS_NSLOTS
+  WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_COUNT, WS_TUNE, WS_SPEC, WS_NBLK, WS_TC_STAT, WS_TC_B, WS_TC_PART, WS_TC_D, WS_NSLOTS
 };
 lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr);
 void graph_cache_clear(lqcd_ctx *ctx);
@@ -242,6 +245,13 @@ lqcd_status blas_to_f32(lqcd_ctx *ctx, const double2 *x, float2 *y, long long n)
 lqcd_status contract_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *eta,
                             const double2 *w, int nrhs, double2 *out_dev);
 lqcd_status noise_launch(lqcd_ctx *ctx, uint64_t seed, uint32_t first, int nrhs, double2 *out);
+// Tensor-core split-precision contractions with k vectors E (tcdefl.cu): slices of E made once
+// (tc_slices_make, released by tc_slices_free), then G[q * nrhs + r] = <E_q, X_r> (tc_vhx) and
+// Y_r = sum_q E_q d_q C[q * nrhs + r] (tc_vc; d device k complex or NULL); all device pointers.
+lqcd_status tc_slices_make(lqcd_ctx *ctx, const double2 *E, int k, void **out);
+void tc_slices_free(void *slices);
+lqcd_status tc_vhx(lqcd_ctx *ctx, const void *slices, const double2 *X, int nrhs, double2 *G);
+lqcd_status tc_vc(lqcd_ctx *ctx, const void *slices, const double2 *C, const double2 *d, int nrhs, double2 *Y);
 // right-hand-side block width autotuner (batch.cu); see lqcd_autotune_block
 lqcd_status autotune_block(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl,
                            const lqcd_krylov_opts *o, const int *cand, int ncand, int *best, double *seconds);

@@ -881,6 +881,7 @@ lqcd_status lqcd_defl_destroy(lqcd_defl *d) {
   if (d->V) cudaFree(d->V);
   if (d->E) cudaFree(d->E);
   if (d->Hbar_dev) cudaFree(d->Hbar_dev);
+  if (d->tc) tc_slices_free(d->tc);
   delete d;
   return LQCD_OK;
 }

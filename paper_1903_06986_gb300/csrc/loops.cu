@@ -447,6 +447,19 @@ static lqcd_status deflate_dev(lqcd_ctx *ctx, const lqcd_defl *defl, const doubl
   double2 *coef, *tmp;
   LQCD_TRY(ws_get(ctx, WS_EST1, sizeof(double2) * (size_t)k * nrhs, (void **)&coef));
   LQCD_TRY(ws_get(ctx, WS_TMP4, sizeof(double2) * (size_t)nrhs * N, (void **)&tmp));
+  if (ctx->defl_engine == LQCD_DEFL_TENSOR) {
+    // split-precision tensor-core products; the slices of E are cached in the deflation object
+    lqcd_defl *dm = const_cast<lqcd_defl *>(defl);
+    if (!dm->tc) LQCD_TRY(tc_slices_make(ctx, defl->E, k, &dm->tc));
+    double2 *dd;
+    LQCD_TRY(ws_get(ctx, WS_TC_D, sizeof(double2) * (size_t)k, (void **)&dd));
+    std::vector<double2> dh(k);
+    for (int q = 0; q < k; ++q) dh[q] = make_double2(d[q].real(), d[q].imag());
+    LQCD_TRY(upload_v(ctx, dh.data(), dd, sizeof(double2) * (size_t)k));
+    LQCD_TRY(tc_vhx(ctx, dm->tc, eta, nrhs, coef));
+    LQCD_TRY(tc_vc(ctx, dm->tc, coef, dd, nrhs, tmp));
+    return blas_g5(ctx, tmp, out, nrhs);
+  }
   LQCD_TRY(blas_multidot(ctx, defl->E, N, 0, k, eta, N, nrhs, coef));
   std::vector<double2> c;
   LQCD_TRY(download_v(ctx, coef, c, (size_t)k * nrhs));

@@ -1,0 +1,929 @@
+// FP64-accurate deflation contractions on the tcgen05 tensor cores (split-precision emulation).
+//
+// The HFES projection of Sec. 5.4, x' = gamma_5 V' Lambda'^-1 V'^dag eta, is two dense products
+// with the k deflation vectors E (k x 12V complex):
+//
+//   G = E^dag X     (k x nrhs; the reduction runs over the 24 V reals of a field)
+//   Y = E C         (nrhs fields; the reduction runs over the k vectors)
+//
+// Both are computed to FP64 accuracy with bf16 tensor-core products (Ozaki's error-free splitting,
+// Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59 (2012)):
+//
+//  * every row of the left operand is scaled by a power of two 2^e so that its entries are below
+//    1/2, and written as seven balanced base-256 digits, x 2^-e = sum_s d_s 2^(-8(s+1)) with
+//    |d_s| <= 128 (truncated after 56 bits): each slice d_s 2^(-8(s+1)) is exact in bf16;
+//  * the right operand is split the same way per column (seven slices), or, when every entry of
+//    the block is a small integer times a common power of two (Z(4) noise: 0, +-1), kept as one
+//    exact slice;
+//  * slice products d_s d'_t carry the unit 2^(-8(s+t+c)); products of one "group" g = s + t
+//    share a unit, so their FP32 sums in TMEM are exact integers as long as they stay below 2^23
+//    units.  Groups 0..3 get exact accumulators, read out (and converted to an exact 64-bit
+//    integer, then FP64) often enough to stay below that bound; groups 4..6 share one FP32
+//    accumulator whose rounding lies below 2^-56 of the leading term.  Pairs with s + t > 6 are
+//    dropped (below 2^-56 as well).
+//
+// The tensor-core kernel (tc_gemm_kernel) is a persistent, warp-specialised tcgen05 GEMM:
+//   warp 4 (one lane)  moves pre-tiled slice blocks global -> shared with cp.async.bulk into a
+//                      ring of stages guarded by mbarriers (full / empty);
+//   warp 5 (one lane)  issues tcgen05.mma.cta_group::1.kind::f16 (bf16 x bf16 -> FP32, M = 128,
+//                      N = NP, K = 16) for every slice pair into TMEM, and tcgen05.commit to free
+//                      a stage / hand an accumulator set to the epilogue;
+//   warps 0-3          read the accumulators with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31,
+//                      i.e. output rows), fold the slice groups into FP64 and write the result.
+// Two accumulator sets in TMEM (when they fit in 512 columns) let the MMAs of the next group run
+// while the epilogue drains the previous one.
+//
+// Operand storage (K-major, no swizzle): a block of R rows x 32 K elements (bf16) is made of
+// 8 x 8 "core matrices" of 128 contiguous bytes (8 rows of 16 bytes), core matrix (i, j) (row
+// group i, K group j) at byte (4 i + j) * 128.  In the tcgen05 shared-memory descriptor the K
+// direction stride between core matrices (leading byte offset) is 128 and the row-group stride
+// (stride byte offset) is 512.  The slicing kernels write the slices in exactly this order, so a
+// pipeline stage is filled by plain bulk copies.
+//
+// Every mbarrier wait is bounded in time: after about two seconds the kernel records
+// LQCD_ERR_TIMEOUT in a device flag, stops issuing work, waits (again bounded) for the copies and
+// MMAs it has in flight, frees its TMEM and returns.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int TC_M = 128;                  // rows per tile = TMEM lanes
+constexpr int TC_KCH = 32;                 // K elements per pipeline chunk (64 bytes per row)
+constexpr int TC_SA = 7;                   // slices of the row-scaled operand (7 x 8 bits)
+constexpr int TC_NACC = 5;                 // accumulators: exact groups 0..3 + rounded tail
+constexpr int TC_THREADS = 192;            // warps 0-3 epilogue, 4 loader, 5 MMA issuer
+constexpr int TC_BLK = TC_M * TC_KCH * 2;  // bytes of a full 128-row slice block (8 KB)
+constexpr int TC_MAXPAIR = 28;
+constexpr int TC_SMEM_MAX = 227 * 1024;
+constexpr int TC_SMEM_MIN = 120 * 1024;    // forces one CTA per SM (TMEM is allocated per CTA)
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // bound of every mbarrier wait
+
+// byte offset of element (row, k) of an R x 32 block in the core-matrix order above
+__host__ __device__ __forceinline__ int tile_off(int row, int k) {
+  return ((((row >> 3) << 2) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
+}
+__host__ __device__ __forceinline__ int round8(int x) { return (x + 7) & ~7; }
+
+// ---------------------------------------------------------------------------------------------
+// Digits of the splitting
+// ---------------------------------------------------------------------------------------------
+
+// Scale exponent of a row / column whose largest magnitude has the bit pattern mb: e such that
+// every entry satisfies |x| < 2^(e-1) (0 for an all-zero vector).
+__host__ __device__ __forceinline__ int scale_exp(unsigned long long mb) {
+  const int be = (int)((mb >> 52) & 0x7ff);
+  return be == 0 ? 0 : be - 1021;
+}
+
+// Balanced base-256 digits of x 2^-e truncated after 56 bits: x 2^-e ~= sum_s d[s] 2^(-8(s+1)),
+// |d[s]| <= 128, error below 2^-56.  Requires |x| < 2^(e-1).  Zeros and subnormals give 0
+// digits (the scales used here are far above the subnormal range).
+__device__ __forceinline__ void split_digits(double x, int e, int d[TC_SA]) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int be = (int)((u >> 52) & 0x7ff);
+  long long F = 0;
+  if (be != 0 && be != 0x7ff) {
+    const unsigned long long mant = (u & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = be - 1075 + 8 * TC_SA - e;  // |x| < 2^(e-1) => F < 2^55
+    if (sh >= 0) F = (long long)(mant << sh);
+    else if (sh > -64) F = (long long)(mant >> (-sh));
+  }
+#pragma unroll
+  for (int s = TC_SA - 1; s >= 1; --s) {
+    int dd = (int)(F & 255);
+    if (dd >= 128) dd -= 256;
+    d[s] = dd;
+    F = (F - dd) >> 8;
+  }
+  d[0] = (int)F;
+  if (u >> 63) {
+#pragma unroll
+    for (int s = 0; s < TC_SA; ++s) d[s] = -d[s];
+  }
+}
+
+// bf16 bits of d 2^(-8(s+1)) (exact: |d| <= 256 has at most 8 significant bits)
+__device__ __forceinline__ unsigned short slice_bits(int d, int s) {
+  const float f = (float)d * __int_as_float((127 - 8 * (s + 1)) << 23);
+  return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+// bf16 bits of a small integer d (|d| < 256)
+__device__ __forceinline__ unsigned short int_bits(int d) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Statistics and slicing kernels
+// ---------------------------------------------------------------------------------------------
+
+// Per vector v (nvec vectors of len doubles, stride len): maxbits[v] = bit pattern of max |x|,
+// minlsb[v] = smallest exponent of a lowest set bit over the nonzero entries; *flag |= 1 on a
+// NaN / Inf.  maxbits / minlsb must be initialised (0 / INT_MAX).
+__global__ void vec_stats_kernel(const double *__restrict__ x, long long len, unsigned long long *maxbits,
+                                 int *minlsb, int *flag) {
+  const int v = blockIdx.y;
+  const double *xv = x + (long long)v * len;
+  unsigned long long mb = 0;
+  int lsb = 0x7fffffff, bad = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(xv[i]) & 0x7fffffffffffffffull;
+    const int be = (int)(u >> 52);
+    if (be == 0x7ff) { bad = 1; continue; }
+    if (u > mb) mb = u;
+    if (be != 0) {
+      const unsigned long long mant = (u & 0xfffffffffffffull) | (1ull << 52);
+      lsb = min(lsb, be - 1075 + __ffsll((long long)mant) - 1);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mb, o));
+    lsb = min(lsb, __shfl_xor_sync(0xffffffffu, lsb, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mb) atomicMax(&maxbits[v], mb);
+    if (lsb != 0x7fffffff) atomicMin(&minlsb[v], lsb);
+    if (bad) atomicOr(flag, 1);
+  }
+}
+
+__global__ void stats_init_kernel(unsigned long long *maxbits, int *minlsb, int n, int *flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { maxbits[i] = 0; minlsb[i] = 0x7fffffff; }
+  if (i == 0) *flag = 0;
+}
+
+// Slices of the k deflation vectors (rows q, L = 24 V reals each) into both operand layouts:
+//   Ag (rows q, K = real index m):   tile mt = q / 128, chunk c = m / 32, slice s at
+//        Ag + mt * kcg * 7 * 8192 + (c * 7 + s) * rows8g(mt) * 64 + tile_off(q % 128, m % 32)
+//   Ac (rows m, K = q):              tile mt = m / 128, chunk c = q / 32, slice s at
+//        Ac + mt * kcc * 7 * 8192 + (c * 7 + s) * rows8c(mt) * 64 + tile_off(m % 128, q % 32)
+// where rows8 is 128 except for the last tile (its valid rows rounded up to 8).  eexp[q] = the
+// row's scale exponent.  One thread per (q, 8 consecutive reals).  Padding must be zero already.
+__global__ void slice_e_kernel(const double *__restrict__ E, int k, long long L, const unsigned long long *maxbits,
+                               int kcg, int kcc, unsigned short *__restrict__ Ag, unsigned short *__restrict__ Ac,
+                               int *eexp) {
+  const int q = blockIdx.y;
+  const long long m0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 8;
+  if (m0 >= L) return;
+  const int e = scale_exp(maxbits[q]);
+  if (m0 == 0) eexp[q] = e;
+  const double *src = E + (long long)q * L + m0;
+  int dg[8][TC_SA];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) split_digits(src[j], e, dg[j]);
+  // layout Ag: the 8 values form one 16-byte row of a core matrix
+  {
+    const int mt = q / TC_M, row = q % TC_M;
+    const int r8 = min(TC_M, round8(k - mt * TC_M));
+    const long long c = m0 / TC_KCH;
+    unsigned char *base = (unsigned char *)Ag + (size_t)mt * kcg * TC_SA * TC_BLK;
+#pragma unroll
+    for (int s = 0; s < TC_SA; ++s) {
+      uint4 w;
+      w.x = slice_bits(dg[0][s], s) | ((unsigned)slice_bits(dg[1][s], s) << 16);
+      w.y = slice_bits(dg[2][s], s) | ((unsigned)slice_bits(dg[3][s], s) << 16);
+      w.z = slice_bits(dg[4][s], s) | ((unsigned)slice_bits(dg[5][s], s) << 16);
+      w.w = slice_bits(dg[6][s], s) | ((unsigned)slice_bits(dg[7][s], s) << 16);
+      *(uint4 *)(base + (size_t)(c * TC_SA + s) * r8 * (TC_KCH * 2) + tile_off(row, (int)(m0 % TC_KCH))) = w;
+    }
+  }
+  // layout Ac: 8 consecutive rows m, one K column q
+  {
+    const long long mt = m0 / TC_M;
+    const int r8 = (int)min((long long)TC_M, (long long)round8((int)min(L - mt * TC_M, (long long)TC_M)));
+    const int c = q / TC_KCH, kk = q % TC_KCH;
+    unsigned char *base = (unsigned char *)Ac + (size_t)mt * kcc * TC_SA * TC_BLK;
+#pragma unroll
+    for (int s = 0; s < TC_SA; ++s) {
+      unsigned char *blk = base + (size_t)(c * TC_SA + s) * r8 * (TC_KCH * 2);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        *(unsigned short *)(blk + tile_off((int)((m0 + j) % TC_M), kk)) = slice_bits(dg[j][s], s);
+    }
+  }
+}
+
+// Right operand of G = E^dag X: column n = 2r is field r of X read as L reals, column 2r + 1 is
+// i conj-rotated field r (entries (Im, -Re) per complex number), so that the real products give
+// Re and Im of conj(E) . X.  small != 0: one exact slice x 2^-lsb[r] (integers below 256);
+// otherwise seven slices with the column scale.  colexp[r] receives the exponent to undo.
+// Layout: B + (c * SB + t) * NP * 64 + tile_off(n, m % 32).  One thread per (n, 8 reals).
+__global__ void slice_x_kernel(const double *__restrict__ X, int nrhs, long long L, const unsigned long long *maxbits,
+                               const int *minlsb, int small, int SB, int NP, unsigned short *__restrict__ B,
+                               int *colexp) {
+  const int n = blockIdx.y, r = n >> 1;
+  const long long m0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 8;
+  if (m0 >= L || r >= nrhs) return;
+  const int e = small ? (maxbits[r] ? minlsb[r] : 0) : scale_exp(maxbits[r]);
+  if (m0 == 0 && (n & 1) == 0) colexp[r] = e;
+  const double *src = X + (long long)r * L + m0;
+  double v[8];
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    const double re = src[j], im = src[j + 1];
+    if (n & 1) { v[j] = im; v[j + 1] = -re; } else { v[j] = re; v[j + 1] = im; }
+  }
+  const long long c = m0 / TC_KCH;
+  unsigned char *base = (unsigned char *)B + (size_t)c * SB * NP * (TC_KCH * 2) + tile_off(n, (int)(m0 % TC_KCH));
+  if (small) {
+    unsigned short h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = int_bits((int)scalbn(v[j], -e));  // exact: integer below 256
+    uint4 w;
+    w.x = h[0] | ((unsigned)h[1] << 16); w.y = h[2] | ((unsigned)h[3] << 16);
+    w.z = h[4] | ((unsigned)h[5] << 16); w.w = h[6] | ((unsigned)h[7] << 16);
+    *(uint4 *)base = w;
+  } else {
+    int dg[8][TC_SA];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) split_digits(v[j], e, dg[j]);
+#pragma unroll
+    for (int s = 0; s < TC_SA; ++s) {
+      uint4 w;
+      w.x = slice_bits(dg[0][s], s) | ((unsigned)slice_bits(dg[1][s], s) << 16);
+      w.y = slice_bits(dg[2][s], s) | ((unsigned)slice_bits(dg[3][s], s) << 16);
+      w.z = slice_bits(dg[4][s], s) | ((unsigned)slice_bits(dg[5][s], s) << 16);
+      w.w = slice_bits(dg[6][s], s) | ((unsigned)slice_bits(dg[7][s], s) << 16);
+      *(uint4 *)(base + (size_t)s * NP * (TC_KCH * 2)) = w;
+    }
+  }
+}
+
+// Right operand of Y = E C: row q of the reduction carries 2^eexp[q] d_q C[q][r] (the row scale
+// of E moved here), column n = 2r its real part and 2r + 1 its imaginary part, seven slices per
+// column with the column scale colexp[n].  d may be NULL (all ones).  One block per r.
+// Layout: B + (c * 7 + t) * NP * 64 + tile_off(n, q % 32), c = q / 32.
+__global__ void slice_c_kernel(const double2 *__restrict__ Cm, const double2 *__restrict__ d, const int *eexp, int k,
+                               int ldc, int NP, unsigned short *__restrict__ B, int *colexp) {
+  const int r = blockIdx.x;
+  __shared__ unsigned long long smax[2];
+  if (threadIdx.x < 2) smax[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long m0 = 0, m1 = 0;
+  for (int q = threadIdx.x; q < k; q += blockDim.x) {
+    double2 c = Cm[(size_t)q * ldc + r];
+    if (d) c = cmul(d[q], c);
+    const double re = scalbn(c.x, eexp[q]), im = scalbn(c.y, eexp[q]);
+    m0 = max(m0, (unsigned long long)__double_as_longlong(fabs(re)));
+    m1 = max(m1, (unsigned long long)__double_as_longlong(fabs(im)));
+  }
+  atomicMax(&smax[0], m0);
+  atomicMax(&smax[1], m1);
+  __syncthreads();
+  const int e0 = scale_exp(smax[0]), e1 = scale_exp(smax[1]);
+  if (threadIdx.x == 0) { colexp[2 * r] = e0; colexp[2 * r + 1] = e1; }
+  for (int q = threadIdx.x; q < k; q += blockDim.x) {
+    double2 c = Cm[(size_t)q * ldc + r];
+    if (d) c = cmul(d[q], c);
+    const double re = scalbn(c.x, eexp[q]), im = scalbn(c.y, eexp[q]);
+    int d0[TC_SA], d1[TC_SA];
+    split_digits(re, e0, d0);
+    split_digits(im, e1, d1);
+    const int c32 = q / TC_KCH, kk = q % TC_KCH;
+#pragma unroll
+    for (int t = 0; t < TC_SA; ++t) {
+      unsigned char *blk = (unsigned char *)B + (size_t)(c32 * TC_SA + t) * NP * (TC_KCH * 2);
+      *(unsigned short *)(blk + tile_off(2 * r, kk)) = slice_bits(d0[t], t);
+      *(unsigned short *)(blk + tile_off(2 * r + 1, kk)) = slice_bits(d1[t], t);
+    }
+  }
+}
+
+// G[q * ldg + r] = 2^(eexp[q] + colexp[r]) sum over splits of the two partial columns, r < nb
+__global__ void vhx_reduce_kernel(const double *__restrict__ part, int nsplit, int NP, long long Mtot, int k, int nb,
+                                  const int *eexp, const int *colexp, double2 *G, int ldg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k * nb) return;
+  const int q = i / nb, r = i % nb;
+  double re = 0.0, im = 0.0;
+  for (int sp = 0; sp < nsplit; ++sp) {
+    re += part[((size_t)sp * NP + 2 * r) * Mtot + q];
+    im += part[((size_t)sp * NP + 2 * r + 1) * Mtot + q];
+  }
+  const int e = eexp[q] + colexp[r];
+  G[(size_t)q * ldg + r] = make_double2(scalbn(re, e), scalbn(im, e));
+}
+
+// ---------------------------------------------------------------------------------------------
+// PTX wrappers (tcgen05, TMEM, bulk copies, mbarriers)
+// ---------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase of the given parity; false if the CTA aborted or the wait ran out of time
+// (then the abort flag and the device error flag are set).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255) == 0) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > TC_WAIT_NS) {
+        *abort_flag = 1;
+        atomicExch(err, (int)LQCD_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+// bounded wait used only while draining after an abort
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity) && gtimer() - t0 < TC_WAIT_NS) {
+  }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: no swizzle, K-direction core-matrix stride 128 B (leading
+// byte offset), row-group stride 512 B (stride byte offset), descriptor version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3ffff) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B bf16 (bits 7-9,
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ __forceinline__ uint32_t mma_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------------------------
+// The tcgen05 GEMM
+// ---------------------------------------------------------------------------------------------
+
+struct TcArgs {
+  const unsigned char *A;  // row-scaled operand, pre-tiled (see slice_e_kernel)
+  const unsigned char *B;  // column operand, pre-tiled [chunk][slice][NP x 32]
+  int mt_count;            // row tiles
+  int m_valid;             // valid rows (rows >= m_valid are neither loaded from HBM nor written)
+  int kc_count;            // K chunks of 32
+  int ksplit;              // K splits per row tile (work items = mt_count * ksplit)
+  int SB;                  // slices of B (1 or 7)
+  int kcr;                 // chunks per accumulator read-out (keeps the exact groups below 2^23 units)
+  int unit_shift;          // exact group g holds integers in units of 2^-(8 g + unit_shift)
+  int npair;
+  unsigned char ps[TC_MAXPAIR], pt[TC_MAXPAIR], pa[TC_MAXPAIR];  // slice pair -> accumulator
+  int mode;                // 0: partial sums; 1: complex columns combined into fields
+  double *part;            // mode 0: part[(split * NP + n) * Mtot + m]
+  long long Mtot;
+  const int *colexp;       // mode 1: scale exponent per column
+  int nb;                  // mode 1: complex columns (column 2r real part, 2r + 1 imaginary part)
+  double *out;             // mode 1: out[r * m_valid + m]
+  int *err;
+};
+
+__host__ __device__ constexpr int tc_stage_bytes(int SB, int NP) { return TC_SA * TC_BLK + SB * NP * TC_KCH * 2; }
+__host__ __device__ constexpr int tc_nbuf(int NP) { return 2 * TC_NACC * NP <= 512 ? 2 : 1; }
+// TMEM columns to allocate: a power of two >= 32 holding every accumulator set
+__host__ __device__ constexpr uint32_t tc_tmem_cols(int NP) {
+  return tc_nbuf(NP) * TC_NACC * NP <= 32    ? 32u
+         : tc_nbuf(NP) * TC_NACC * NP <= 64  ? 64u
+         : tc_nbuf(NP) * TC_NACC * NP <= 128 ? 128u
+         : tc_nbuf(NP) * TC_NACC * NP <= 256 ? 256u
+                                             : 512u;
+}
+
+__device__ __forceinline__ void work_range(const TcArgs &p, int w, int &mt, int &sp, int &c0, int &c1) {
+  mt = w / p.ksplit;
+  sp = w % p.ksplit;
+  c0 = (int)((long long)p.kc_count * sp / p.ksplit);
+  c1 = (int)((long long)p.kc_count * (sp + 1) / p.ksplit);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcArgs p, int stages) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int sbytes = tc_stage_bytes(p.SB, NP);
+  unsigned long long *bars = (unsigned long long *)(smem + (size_t)stages * sbytes);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * stages, accf0 = full0 + 16 * stages,
+                 acce0 = accf0 + 16, drain = acce0 + 16;
+  uint32_t *tmem_slot = (uint32_t *)(bars + 2 * stages + 5);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NBUF = tc_nbuf(NP);
+  constexpr uint32_t NCOLS = tc_tmem_cols(NP);
+  const int nwork = p.mt_count * p.ksplit;
+
+  // stage buffers start as zeros: rows that a partial tile does not load then hold finite values
+  for (int i = threadIdx.x; i < stages * sbytes / 16; i += TC_THREADS) ((uint4 *)smem)[i] = make_uint4(0, 0, 0, 0);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 4 * 32);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    // ---- loader ----
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t filled = 0;  // stages armed at least once (for the drain after an abort)
+      const uint32_t bbytes = (uint32_t)(p.SB * NP * TC_KCH * 2);
+      bool ok = true;
+      for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+        int mt, sp, c0, c1;
+        work_range(p, w, mt, sp, c0, c1);
+        const int r8 = min(TC_M, round8(p.m_valid - mt * TC_M));
+        const uint32_t ablk = (uint32_t)(r8 * TC_KCH * 2);
+        const unsigned char *abase = p.A + (size_t)mt * p.kc_count * TC_SA * TC_BLK;
+        for (int c = c0; c < c1; ++c) {
+          if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.err)) { ok = false; break; }
+          const uint32_t sA = smem_u32(smem + (size_t)stage * sbytes);
+          mbar_expect_tx(full0 + 8 * stage, TC_SA * ablk + bbytes);
+          bulk_g2s(sA, abase + (size_t)c * TC_SA * ablk, TC_SA * ablk, full0 + 8 * stage);
+          bulk_g2s(sA + TC_SA * TC_BLK, p.B + (size_t)c * bbytes, bbytes, full0 + 8 * stage);
+          filled |= 1u << stage;
+          if (++stage == stages) { stage = 0; phase ^= 1; }
+        }
+      }
+      if (!ok) {
+        // let every armed copy land before the CTA exits: stage s was last armed in the lap
+        // before the current position if s >= stage, else in the current lap
+        for (int s = 0; s < stages; ++s)
+          if (filled >> s & 1) mbar_drain(full0 + 8 * s, s < stage ? phase : phase ^ 1);
+      }
+    }
+  } else if (warp == 5) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      int stage = 0, buf = 0;
+      uint32_t phase = 0, accph[2] = {0, 0};
+      const uint32_t idesc = mma_idesc(NP);
+      bool ok = true, issued = false;
+      for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+        int mt, sp, c0, c1;
+        work_range(p, w, mt, sp, c0, c1);
+        const int r8 = min(TC_M, round8(p.m_valid - mt * TC_M));
+        const uint32_t ablk = (uint32_t)(r8 * TC_KCH * 2);
+        for (int g0 = c0; g0 < c1 && ok; g0 += p.kcr) {
+          const int g1 = min(c1, g0 + p.kcr);
+          if (!mbar_wait(acce0 + 8 * buf, accph[buf] ^ 1, abort_flag, p.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t dbase = tmem + (uint32_t)(buf * TC_NACC * NP);
+          uint32_t started = 0;
+          for (int c = g0; c < g1; ++c) {
+            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sA = smem_u32(smem + (size_t)stage * sbytes), sB = sA + TC_SA * TC_BLK;
+#pragma unroll
+            for (int j = 0; j < TC_KCH / 16; ++j) {
+              for (int i = 0; i < p.npair; ++i) {
+                const int a = p.pa[i];
+                mma_bf16(dbase + (uint32_t)(a * NP), smem_desc(sA + p.ps[i] * ablk + 256 * j),
+                         smem_desc(sB + p.pt[i] * (NP * TC_KCH * 2) + 256 * j), idesc, (started >> a) & 1u);
+                started |= 1u << a;
+              }
+            }
+            issued = true;
+            mma_commit(empty0 + 8 * stage);
+            if (++stage == stages) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          mma_commit(accf0 + 8 * buf);
+          accph[buf] ^= 1;
+          buf ^= NBUF - 1;
+        }
+      }
+      if (!ok && issued) {
+        mma_commit(drain);
+        mbar_drain(drain, 0);
+      }
+    }
+  } else {
+    // ---- epilogue: warps 0-3, thread = TMEM lane = output row ----
+    const int row = warp * 32 + lane;
+    int buf = 0;
+    uint32_t accph[2] = {0, 0};
+    bool ok = true;
+    const float sc0 = __int_as_float((127 + p.unit_shift) << 23);       // 2^unit_shift
+    const double unit3 = __longlong_as_double((long long)(1023 - 24 - p.unit_shift) << 52);
+    for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+      int mt, sp, c0, c1;
+      work_range(p, w, mt, sp, c0, c1);
+      double acc[NP];
+#pragma unroll
+      for (int n = 0; n < NP; ++n) acc[n] = 0.0;
+      for (int g0 = c0; g0 < c1; g0 += p.kcr) {
+        // the whole warp leaves together (tcgen05.ld and the shuffles below are warp-collective)
+        if (!__all_sync(0xffffffffu, mbar_wait(accf0 + 8 * buf, accph[buf], abort_flag, p.err))) {
+          ok = false;
+          break;
+        }
+        accph[buf] ^= 1;
+        tc_fence_after();
+        const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * TC_NACC * NP);
+#pragma unroll
+        for (int n0 = 0; n0 < NP; n0 += 8) {
+          float v[TC_NACC][8];
+#pragma unroll
+          for (int a = 0; a < TC_NACC; ++a) tmem_ld8(tb + (uint32_t)(a * NP + n0), v[a]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            // exact groups: integers n_g = v_g 2^(8 g + unit_shift) below 2^23, combined exactly
+            long long T = 0;
+            float sc = sc0;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              T = T * 256 + (long long)__float2int_rn(v[g][i] * sc);
+              sc *= 256.0f;
+            }
+            acc[n0 + i] += (double)T * unit3 + (double)v[4][i];
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(acce0 + 8 * buf);
+        buf ^= NBUF - 1;
+      }
+      if (!ok) break;
+      const long long m = (long long)mt * TC_M + row;
+      if (p.mode == 0) {
+        if (m < p.m_valid) {
+#pragma unroll
+          for (int n = 0; n < NP; ++n) p.part[((size_t)sp * NP + n) * p.Mtot + m] = acc[n];
+        }
+      } else {
+        // rows 2i (real part) and 2i + 1 (imaginary part) of a complex entry are lanes 2i, 2i + 1
+#pragma unroll
+        for (int r = 0; r < NP / 2; ++r) {
+          const double p1 = r < p.nb ? scalbn(acc[2 * r], p.colexp[2 * r]) : 0.0;
+          const double p2 = r < p.nb ? scalbn(acc[2 * r + 1], p.colexp[2 * r + 1]) : 0.0;
+          const double p2o = __shfl_xor_sync(0xffffffffu, p2, 1);
+          if (r < p.nb && m < p.m_valid) p.out[(size_t)r * p.m_valid + m] = (row & 1) ? p2o + p1 : p1 - p2o;
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+
+struct TcSlices {
+  int k;
+  long long L;                 // reals per vector (24 V)
+  int mtg, kcg;                // G = E^dag X operand: row tiles over q, K chunks over the reals
+  int mtc, kcc;                // Y = E C operand: row tiles over the reals, K chunks over q
+  unsigned char *Ag, *Ac;      // pre-tiled slices
+  int *eexp;                   // per-vector scale exponent (device)
+  unsigned long long *maxbits; // per-vector maximum (device)
+  int *minlsb, *flag;
+};
+
+size_t tc_bytes_g(int k, long long L) {
+  const int mt = (k + TC_M - 1) / TC_M;
+  const long long kc = (L + TC_KCH - 1) / TC_KCH;
+  return (size_t)mt * kc * TC_SA * TC_BLK;
+}
+size_t tc_bytes_c(int k, long long L) {
+  const long long mt = (L + TC_M - 1) / TC_M;
+  const int kc = (k + TC_KCH - 1) / TC_KCH;
+  return (size_t)mt * kc * TC_SA * TC_BLK;
+}
+
+template <int NP> lqcd_status tc_gemm_launch(lqcd_ctx *ctx, const TcArgs &a, double units) {
+  const int sbytes = tc_stage_bytes(a.SB, NP);
+  const int bar_bytes = 8 * (2 * 4 + 8) + 64;  // room for up to 4 stages of barriers + slot + flag
+  int stages = std::min(4, (TC_SMEM_MAX - bar_bytes - 64) / sbytes);
+  if (stages < 2) return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core contraction: stage does not fit");
+  const int smem = std::max(TC_SMEM_MIN, stages * sbytes + 8 * (2 * stages + 5) + 64);
+  LQCD_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int nwork = a.mt_count * a.ksplit;
+  const int grid = std::min(nwork, ctx->sms);
+  kbegin(ctx);
+  tc_gemm_kernel<NP><<<grid, TC_THREADS, smem, ctx->stream>>>(a, stages);
+  return launch_check(ctx, "tc_gemm_kernel", K_TENSOR, units);
+}
+
+lqcd_status tc_gemm(lqcd_ctx *ctx, int NP, const TcArgs &a, double units) {
+  switch (NP) {
+    case 16: return tc_gemm_launch<16>(ctx, a, units);
+    case 32: return tc_gemm_launch<32>(ctx, a, units);
+    case 48: return tc_gemm_launch<48>(ctx, a, units);
+    case 64: return tc_gemm_launch<64>(ctx, a, units);
+  }
+  return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core contraction: bad column count %d", NP);
+}
+
+// slice pairs (s, t) with s + t <= 6 and their accumulators min(s + t, 4)
+void tc_pairs(TcArgs &a) {
+  a.npair = 0;
+  for (int s = 0; s < TC_SA; ++s)
+    for (int t = 0; t < a.SB; ++t)
+      if (s + t <= TC_SA - 1) {
+        a.ps[a.npair] = (unsigned char)s;
+        a.pt[a.npair] = (unsigned char)t;
+        a.pa[a.npair] = (unsigned char)std::min(s + t, TC_NACC - 1);
+        ++a.npair;
+      }
+}
+
+// chunks per read-out such that an exact group (at most P pairs of products below dA * dB
+// units each) stays below 2^23 units: kcr * 32 * P * dA * dB <= 2^23
+int tc_kcr(int SB, double dB) {
+  const double P = std::min(4, SB);
+  const double kc = std::floor(8388608.0 / (P * 128.0 * dB * TC_KCH));
+  return (int)std::max(1.0, std::min(kc, 1e6));
+}
+
+lqcd_status check_flag(lqcd_ctx *ctx, int *flag_dev, const char *what) {
+  int f = 0;
+  LQCD_CUDA(ctx, cudaMemcpyAsync(&f, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (f == LQCD_ERR_TIMEOUT) return set_err(ctx, LQCD_ERR_TIMEOUT, "%s: a tensor-core pipeline wait timed out", what);
+  if (f) return set_err(ctx, LQCD_ERR_NONFINITE, "%s: non-finite input", what);
+  return LQCD_OK;
+}
+
+}  // namespace
+
+// Slices of the k vectors E (device, k x N complex, vector-major) for both contractions; the
+// buffers are allocated here and released by tc_slices_free.
+lqcd_status tc_slices_make(lqcd_ctx *ctx, const double2 *E, int k, void **out) {
+  *out = nullptr;
+  if (k <= 0 || k > 4096) return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core slices: 1 <= k <= 4096");
+  TcSlices *S = new TcSlices();
+  S->k = k;
+  S->L = 2 * ctx->N;
+  S->mtg = (k + TC_M - 1) / TC_M;
+  S->kcg = (int)((S->L + TC_KCH - 1) / TC_KCH);
+  S->mtc = (int)((S->L + TC_M - 1) / TC_M);
+  S->kcc = (k + TC_KCH - 1) / TC_KCH;
+  const size_t bg = tc_bytes_g(k, S->L), bc = tc_bytes_c(k, S->L);
+  cudaError_t e1 = cudaMalloc(&S->Ag, bg), e2 = cudaMalloc(&S->Ac, bc);
+  cudaError_t e3 = cudaMalloc(&S->eexp, sizeof(int) * (k + 2) + sizeof(unsigned long long) * k + sizeof(int) * (k + 1));
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    cudaGetLastError();
+    if (e1 == cudaSuccess) cudaFree(S->Ag);
+    if (e2 == cudaSuccess) cudaFree(S->Ac);
+    if (e3 == cudaSuccess) cudaFree(S->eexp);
+    delete S;
+    return set_err(ctx, LQCD_ERR_OOM, "tensor-core slices: %.1f GB not available", (bg + bc) / 1e9);
+  }
+  S->maxbits = (unsigned long long *)(S->eexp + k + (k & 1));
+  S->minlsb = (int *)(S->maxbits + k);
+  S->flag = S->minlsb + k;
+  *out = S;
+  LQCD_CUDA(ctx, cudaMemsetAsync(S->Ag, 0, bg, ctx->stream));
+  LQCD_CUDA(ctx, cudaMemsetAsync(S->Ac, 0, bc, ctx->stream));
+  kbegin(ctx);
+  stats_init_kernel<<<ceil_div(k, 256), 256, 0, ctx->stream>>>(S->maxbits, S->minlsb, k, S->flag);
+  LQCD_TRY(launch_check(ctx, "stats_init_kernel", K_SLICE, (double)k));
+  kbegin(ctx);
+  vec_stats_kernel<<<dim3(std::min(ceil_div(S->L, 256), 64), k), 256, 0, ctx->stream>>>((const double *)E, S->L,
+                                                                                           S->maxbits, S->minlsb, S->flag);
+  LQCD_TRY(launch_check(ctx, "vec_stats_kernel", K_SLICE, (double)k * S->L));
+  LQCD_TRY(check_flag(ctx, S->flag, "tensor-core slices"));
+  kbegin(ctx);
+  slice_e_kernel<<<dim3(ceil_div(S->L / 8, 128), k), 128, 0, ctx->stream>>>(
+      (const double *)E, k, S->L, S->maxbits, S->kcg, S->kcc, (unsigned short *)S->Ag, (unsigned short *)S->Ac, S->eexp);
+  return launch_check(ctx, "slice_e_kernel", K_SLICE, (double)k * S->L);
+}
+
+void tc_slices_free(void *p) {
+  TcSlices *S = (TcSlices *)p;
+  if (!S) return;
+  cudaFree(S->Ag);
+  cudaFree(S->Ac);
+  cudaFree(S->eexp);
+  delete S;
+}
+
+// G[q * nrhs + r] = <E_q, X_r> (device output, k x nrhs complex)
+lqcd_status tc_vhx(lqcd_ctx *ctx, const void *slices, const double2 *X, int nrhs, double2 *G) {
+  const TcSlices *S = (const TcSlices *)slices;
+  const int k = S->k;
+  for (int r0 = 0; r0 < nrhs; r0 += 32) {
+    const int nb = std::min(32, nrhs - r0);
+    const int NP = std::max(16, ((2 * nb + 15) / 16) * 16);
+    const double2 *Xb = X + (size_t)r0 * ctx->N;
+    unsigned long long *mb;
+    int *lsb, *flag, *colexp;
+    unsigned char *Bsl;
+    double *part;
+    void *p;
+    LQCD_TRY(ws_get(ctx, WS_TC_STAT, 64 * (sizeof(unsigned long long) + 2 * sizeof(int)) + 64, &p));
+    mb = (unsigned long long *)p;
+    lsb = (int *)(mb + 64);
+    colexp = lsb + 64;
+    flag = colexp + 64;
+    kbegin(ctx);
+    stats_init_kernel<<<1, 64, 0, ctx->stream>>>(mb, lsb, 64, flag);
+    LQCD_TRY(launch_check(ctx, "stats_init_kernel", K_SLICE, 64.0));
+    kbegin(ctx);
+    vec_stats_kernel<<<dim3(std::min(ceil_div(S->L, 256), 64), nb), 256, 0, ctx->stream>>>((const double *)Xb, S->L,
+                                                                                              mb, lsb, flag);
+    LQCD_TRY(launch_check(ctx, "vec_stats_kernel", K_SLICE, (double)nb * S->L));
+    // the read-out schedule depends on the operand's value range: read it back
+    std::vector<unsigned long long> hmb(nb);
+    std::vector<int> hl(nb);
+    int hflag = 0;
+    LQCD_CUDA(ctx, cudaMemcpyAsync(hmb.data(), mb, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+    LQCD_CUDA(ctx, cudaMemcpyAsync(hl.data(), lsb, sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+    LQCD_CUDA(ctx, cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (hflag) return set_err(ctx, LQCD_ERR_NONFINITE, "tensor-core V^dag X: non-finite input");
+    // small-integer operand: every column is integers below 256 times one power of two
+    bool small = true;
+    int span = 0;
+    for (int r = 0; r < nb; ++r) {
+      if (!hmb[r]) continue;
+      const int mexp = (int)((hmb[r] >> 52) & 0x7ff) - 1023;
+      span = std::max(span, mexp - hl[r]);
+      if (mexp - hl[r] > 7) small = false;
+    }
+    TcArgs a{};
+    a.SB = small ? 1 : TC_SA;
+    const double dB = small ? std::ldexp(1.0, span + 1) : 128.0;
+    a.kcr = tc_kcr(a.SB, dB);
+    a.unit_shift = small ? 8 : 16;
+    tc_pairs(a);
+    const size_t bbytes = (size_t)S->kcg * a.SB * NP * TC_KCH * 2;
+    LQCD_TRY(ws_get(ctx, WS_TC_B, bbytes, &p));
+    Bsl = (unsigned char *)p;
+    LQCD_CUDA(ctx, cudaMemsetAsync(Bsl, 0, bbytes, ctx->stream));
+    kbegin(ctx);
+    slice_x_kernel<<<dim3(ceil_div(S->L / 8, 128), 2 * nb), 128, 0, ctx->stream>>>(
+        (const double *)Xb, nb, S->L, mb, lsb, small ? 1 : 0, a.SB, NP, (unsigned short *)Bsl, colexp);
+    LQCD_TRY(launch_check(ctx, "slice_x_kernel", K_SLICE, (double)nb * S->L));
+    a.A = S->Ag;
+    a.B = Bsl;
+    a.mt_count = S->mtg;
+    a.m_valid = k;
+    a.kc_count = S->kcg;
+    a.ksplit = std::max(1, std::min(S->kcg, ctx->sms / S->mtg));
+    a.mode = 0;
+    a.Mtot = (long long)S->mtg * TC_M;
+    LQCD_TRY(ws_get(ctx, WS_TC_PART, sizeof(double) * (size_t)a.ksplit * NP * a.Mtot + 64, &p));
+    part = (double *)p;
+    a.part = part;
+    a.err = flag;
+    LQCD_TRY(tc_gemm(ctx, NP, a, (double)k * nb * ctx->N));
+    kbegin(ctx);
+    vhx_reduce_kernel<<<ceil_div(k * nb, 128), 128, 0, ctx->stream>>>(part, a.ksplit, NP, a.Mtot, k, nb, S->eexp,
+                                                                       colexp, G + r0, nrhs);
+    LQCD_TRY(launch_check(ctx, "vhx_reduce_kernel", K_SLICE, (double)k * nb));
+    LQCD_TRY(check_flag(ctx, flag, "tensor-core V^dag X"));
+  }
+  return LQCD_OK;
+}
+
+// Y_r = sum_q E_q d_q C[q * nrhs + r] (device in / out; d: device k complex or NULL)
+lqcd_status tc_vc(lqcd_ctx *ctx, const void *slices, const double2 *Cm, const double2 *d, int nrhs, double2 *Y) {
+  const TcSlices *S = (const TcSlices *)slices;
+  const int k = S->k;
+  for (int r0 = 0; r0 < nrhs; r0 += 32) {
+    const int nb = std::min(32, nrhs - r0);
+    const int NP = std::max(16, ((2 * nb + 15) / 16) * 16);
+    void *p;
+    LQCD_TRY(ws_get(ctx, WS_TC_STAT, 64 * (sizeof(unsigned long long) + 2 * sizeof(int)) + 64, &p));
+    int *colexp = (int *)((unsigned long long *)p + 64) + 64;
+    int *flag = colexp + 64;
+    const size_t bbytes = (size_t)S->kcc * TC_SA * NP * TC_KCH * 2;
+    LQCD_TRY(ws_get(ctx, WS_TC_B, bbytes, &p));
+    unsigned char *Bsl = (unsigned char *)p;
+    LQCD_CUDA(ctx, cudaMemsetAsync(Bsl, 0, bbytes, ctx->stream));
+    LQCD_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+    kbegin(ctx);
+    slice_c_kernel<<<nb, 128, 0, ctx->stream>>>(Cm + r0, d, S->eexp, k, nrhs, NP, (unsigned short *)Bsl, colexp);
+    LQCD_TRY(launch_check(ctx, "slice_c_kernel", K_SLICE, (double)k * nb));
+    TcArgs a{};
+    a.SB = TC_SA;
+    a.kcr = tc_kcr(a.SB, 128.0);
+    a.unit_shift = 16;
+    tc_pairs(a);
+    a.A = S->Ac;
+    a.B = Bsl;
+    a.mt_count = S->mtc;
+    a.m_valid = (int)S->L;
+    a.kc_count = S->kcc;
+    a.ksplit = 1;
+    a.mode = 1;
+    a.colexp = colexp;
+    a.nb = nb;
+    a.out = (double *)(Y + (size_t)r0 * ctx->N);
+    a.err = flag;
+    LQCD_TRY(tc_gemm(ctx, NP, a, (double)k * nb * ctx->N));
+    LQCD_TRY(check_flag(ctx, flag, "tensor-core V C"));
+  }
+  return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_set_defl_engine(lqcd_ctx *ctx, int engine) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (engine != LQCD_DEFL_FP64 && engine != LQCD_DEFL_TENSOR)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "set_defl_engine: unknown engine %d", engine);
+  ctx->defl_engine = engine;
+  return LQCD_OK;
+}
+
+namespace {
+// slices of caller vectors for one call, released on every exit path
+struct ScopedSlices {
+  void *p = nullptr;
+  ~ScopedSlices() { tc_slices_free(p); }
+};
+}  // namespace
+
+extern "C" lqcd_status lqcd_tc_vdag_x(lqcd_ctx *ctx, const double *E, int k, const double *X, int nrhs, double *G) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!E || !X || !G || k <= 0 || nrhs <= 0 || nrhs > 65535)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "tc_vdag_x: bad arguments");
+  ScopedSlices sl;
+  LQCD_TRY(tc_slices_make(ctx, (const double2 *)E, k, &sl.p));
+  return tc_vhx(ctx, sl.p, (const double2 *)X, nrhs, (double2 *)G);
+}
+
+extern "C" lqcd_status lqcd_tc_v_c(lqcd_ctx *ctx, const double *E, int k, const double *C, int nrhs, double *Y) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!E || !C || !Y || k <= 0 || nrhs <= 0 || nrhs > 65535)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "tc_v_c: bad arguments");
+  ScopedSlices sl;
+  LQCD_TRY(tc_slices_make(ctx, (const double2 *)E, k, &sl.p));
+  return tc_vc(ctx, sl.p, (const double2 *)C, nullptr, nrhs, (double2 *)Y);
+}

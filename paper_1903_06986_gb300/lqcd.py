@@ -22,7 +22,8 @@ SUB_NONE, SUB_PERT, SUB_POLY, SUB_DEFL, SUB_DEFL_PERT, SUB_DEFL_POLY = (1 << i f
 SUB_ALL = 63
 MODES = ["none", "pert", "poly", "defl", "defl_pert", "defl_poly"]
 NOPS = 9
-KERNEL_CLASSES = ["wilson", "dot", "axpy", "combine", "norm", "contract", "blas1", "noise", "probe"]
+KERNEL_CLASSES = ["wilson", "dot", "axpy", "combine", "norm", "contract", "blas1", "noise", "probe", "tensor", "slice"]
+DEFL_FP64, DEFL_TENSOR = 0, 1
 
 
 class LqcdError(RuntimeError):
@@ -107,6 +108,9 @@ def load(path=None):
         "lqcd_defl_export": [vp, vp, vp, vp, vp, vp],
         "lqcd_defl_import": [vp, i, vp, vp, C.POINTER(vp)],
         "lqcd_deflate_project": [vp, vp, vp, vp, i, vp],
+        "lqcd_set_defl_engine": [vp, i],
+        "lqcd_tc_vdag_x": [vp, vp, i, vp, i, vp],
+        "lqcd_tc_v_c": [vp, vp, i, vp, i, vp],
         "lqcd_hop_series": [vp, vp, d, vp, vp, i, i, vp],
         "lqcd_poly_apply": [vp, vp, d, vp, vp, i, i, vp],
         "lqcd_poly_coeffs": [vp, vp, d, u64, i, vp],
@@ -395,6 +399,24 @@ class Context:
         dh, dp = _host_c(d)
         self._check(self.lib.lqcd_deflate_project(self.h, defl.h, _ptr(eta), _ptr(out), self._nrhs(eta), dp))
         return out
+
+    def set_defl_engine(self, engine):
+        """DEFL_FP64 (CUDA-core FP64) or DEFL_TENSOR (split-precision tcgen05) deflation projections."""
+        self._check(self.lib.lqcd_set_defl_engine(self.h, engine))
+
+    def tc_vdag_x(self, E, X):
+        """G[q, r] = <E_q, X_r> on the tensor cores; E (k, ...) and X (nrhs, ...) complex128 fields."""
+        k, nrhs = E.shape[0], X.shape[0]
+        G = _torch().empty((k, nrhs), dtype=_torch().complex128, device=X.device)
+        self._check(self.lib.lqcd_tc_vdag_x(self.h, _ptr(E), k, _ptr(X), nrhs, _ptr(G)))
+        return G
+
+    def tc_v_c(self, E, Cm):
+        """Y_r = sum_q E_q C[q, r] on the tensor cores; E (k, ...) fields, C (k, nrhs) complex128."""
+        k, nrhs = Cm.shape
+        Y = _torch().empty((nrhs,) + tuple(E.shape[1:]), dtype=_torch().complex128, device=E.device)
+        self._check(self.lib.lqcd_tc_v_c(self.h, _ptr(E), k, _ptr(Cm.contiguous()), nrhs, _ptr(Y)))
+        return Y
 
     # perturbative and polynomial series
     def hop_series(self, links, kappa, eta, K, c=None):

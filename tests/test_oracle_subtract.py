@@ -182,3 +182,29 @@ def test_relative_efficiency_definition():
     assert E.relative_efficiency(1.0, 1.0) == 0.0
     assert abs(E.relative_efficiency(1 / np.sqrt(2.0), 1.0) - 100.0) < 1e-12
     assert abs(E.relative_efficiency(2.0, 1.0) + 75.0) < 1e-12
+
+
+def test_defl_products_brute_force_and_orthonormality():
+    """V'^dag eta and V' C (Sec. 5.4) by explicit Python sums on a tiny case, and the identity
+    V'^dag (V' C) = C for orthonormal columns."""
+    r = np.random.default_rng(41)
+    n, Q, nrhs = 24, 3, 2
+    E = r.standard_normal((n, Q)) + 1j * r.standard_normal((n, Q))
+    X = r.standard_normal((nrhs, n)) + 1j * r.standard_normal((nrhs, n))
+    Cm = r.standard_normal((Q, nrhs)) + 1j * r.standard_normal((Q, nrhs))
+    G = S.defl_coeffs(E, X)
+    Y = S.defl_expand(E, Cm)
+    for q in range(Q):
+        for j in range(nrhs):
+            s = 0j
+            for i in range(n):
+                s += E[i, q].conjugate() * X[j, i]
+            assert abs(G[q, j] - s) < 1e-12
+    for j in range(nrhs):
+        for i in range(n):
+            s = 0j
+            for q in range(Q):
+                s += E[i, q] * Cm[q, j]
+            assert abs(Y[j, i] - s) < 1e-12
+    Qm, _ = np.linalg.qr(E)
+    assert np.allclose(S.defl_coeffs(Qm, S.defl_expand(Qm, Cm)), Cm, atol=1e-13)
