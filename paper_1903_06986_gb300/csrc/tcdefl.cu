@@ -9,18 +9,24 @@
 // Both are computed to FP64 accuracy with bf16 tensor-core products (Ozaki's error-free splitting,
 // Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59 (2012)):
 //
-//  * every row of the left operand is scaled by a power of two 2^e so that its entries are below
-//    1/2, and written as seven balanced base-256 digits, x 2^-e = sum_s d_s 2^(-8(s+1)) with
-//    |d_s| <= 128 (truncated after 56 bits): each slice d_s 2^(-8(s+1)) is exact in bf16;
+//  * every row of the left operand (over the reduction index) is scaled by a power of two 2^e so
+//    that its entries are below 1/2, and written as seven balanced base-256 digits,
+//    x 2^-e = sum_s d_s 2^(-8(s+1)) with |d_s| <= 128 (truncated after 56 bits, an error below
+//    2^-54 of the row's largest entry): each slice d_s 2^(-8(s+1)) is exact in bf16.  The rows are
+//    the vectors E_q for G and the real components m of the fields for Y, so the two products
+//    use two slice copies of E, each with its own scales;
 //  * the right operand is split the same way per column (seven slices), or, when every entry of
 //    the block is a small integer times a common power of two (Z(4) noise: 0, +-1), kept as one
 //    exact slice;
 //  * slice products d_s d'_t carry the unit 2^(-8(s+t+c)); products of one "group" g = s + t
-//    share a unit, so their FP32 sums in TMEM are exact integers as long as they stay below 2^23
-//    units.  Groups 0..3 get exact accumulators, read out (and converted to an exact 64-bit
-//    integer, then FP64) often enough to stay below that bound; groups 4..6 share one FP32
-//    accumulator whose rounding lies below 2^-56 of the leading term.  Pairs with s + t > 6 are
-//    dropped (below 2^-56 as well).
+//    share a unit, so their FP32 sums in TMEM are exact integers as long as they stay within 2^24
+//    units (every partial sum is then an integer of at most 24 bits).  Groups 0..3 get exact accumulators, read out (and converted to an exact 64-bit
+//    integer, then FP64) often enough to stay below that bound; groups 4..7 share one FP32
+//    accumulator whose rounding lies below 2^-56 of the leading term.  Pairs with s + t > 7 are
+//    dropped (below 2^-62 of the leading term).
+//  Per entry of the result the error is thus below about 2^-52 (max_i |a_i| sum_i |b_i| +
+//  sum_i |a_i| max_i |b_i|) plus the FP64 rounding of the folds, the bound of the splitting
+//  (an FP64 dot product has 2^-53 n sum_i |a_i||b_i| in the worst case).
 //
 // The tensor-core kernel (tc_gemm_kernel) is a persistent, warp-specialised tcgen05 GEMM:
 //   warp 4 (one lane)  moves pre-tiled slice blocks global -> shared with cp.async.bulk into a
@@ -55,7 +61,7 @@ constexpr int TC_SA = 7;                   // slices of the row-scaled operand (
 constexpr int TC_NACC = 5;                 // accumulators: exact groups 0..3 + rounded tail
 constexpr int TC_THREADS = 192;            // warps 0-3 epilogue, 4 loader, 5 MMA issuer
 constexpr int TC_BLK = TC_M * TC_KCH * 2;  // bytes of a full 128-row slice block (8 KB)
-constexpr int TC_MAXPAIR = 28;
+constexpr int TC_MAXPAIR = 34;
 constexpr int TC_SMEM_MAX = 227 * 1024;
 constexpr int TC_SMEM_MIN = 120 * 1024;    // forces one CTA per SM (TMEM is allocated per CTA)
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // bound of every mbarrier wait
@@ -156,16 +162,13 @@ __global__ void stats_init_kernel(unsigned long long *maxbits, int *minlsb, int 
   if (i == 0) *flag = 0;
 }
 
-// Slices of the k deflation vectors (rows q, L = 24 V reals each) into both operand layouts:
-//   Ag (rows q, K = real index m):   tile mt = q / 128, chunk c = m / 32, slice s at
-//        Ag + mt * kcg * 7 * 8192 + (c * 7 + s) * rows8g(mt) * 64 + tile_off(q % 128, m % 32)
-//   Ac (rows m, K = q):              tile mt = m / 128, chunk c = q / 32, slice s at
-//        Ac + mt * kcc * 7 * 8192 + (c * 7 + s) * rows8c(mt) * 64 + tile_off(m % 128, q % 32)
+// Slices of the k deflation vectors as the left operand of G = E^dag X (rows q, K = real index m
+// of L = 24 V reals): tile mt = q / 128, chunk c = m / 32, slice s at
+//        Ag + mt * kcg * 7 * 8192 + (c * 7 + s) * rows8(mt) * 64 + tile_off(q % 128, m % 32)
 // where rows8 is 128 except for the last tile (its valid rows rounded up to 8).  eexp[q] = the
 // row's scale exponent.  One thread per (q, 8 consecutive reals).  Padding must be zero already.
-__global__ void slice_e_kernel(const double *__restrict__ E, int k, long long L, const unsigned long long *maxbits,
-                               int kcg, int kcc, unsigned short *__restrict__ Ag, unsigned short *__restrict__ Ac,
-                               int *eexp) {
+__global__ void slice_ag_kernel(const double *__restrict__ E, int k, long long L, const unsigned long long *maxbits,
+                                int kcg, unsigned short *__restrict__ Ag, int *eexp) {
   const int q = blockIdx.y;
   const long long m0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 8;
   if (m0 >= L) return;
@@ -175,35 +178,60 @@ __global__ void slice_e_kernel(const double *__restrict__ E, int k, long long L,
   int dg[8][TC_SA];
 #pragma unroll
   for (int j = 0; j < 8; ++j) split_digits(src[j], e, dg[j]);
-  // layout Ag: the 8 values form one 16-byte row of a core matrix
-  {
-    const int mt = q / TC_M, row = q % TC_M;
-    const int r8 = min(TC_M, round8(k - mt * TC_M));
-    const long long c = m0 / TC_KCH;
-    unsigned char *base = (unsigned char *)Ag + (size_t)mt * kcg * TC_SA * TC_BLK;
+  const int mt = q / TC_M, row = q % TC_M;
+  const int r8 = min(TC_M, round8(k - mt * TC_M));
+  const long long c = m0 / TC_KCH;
+  unsigned char *base = (unsigned char *)Ag + (size_t)mt * kcg * TC_SA * TC_BLK;
 #pragma unroll
-    for (int s = 0; s < TC_SA; ++s) {
-      uint4 w;
-      w.x = slice_bits(dg[0][s], s) | ((unsigned)slice_bits(dg[1][s], s) << 16);
-      w.y = slice_bits(dg[2][s], s) | ((unsigned)slice_bits(dg[3][s], s) << 16);
-      w.z = slice_bits(dg[4][s], s) | ((unsigned)slice_bits(dg[5][s], s) << 16);
-      w.w = slice_bits(dg[6][s], s) | ((unsigned)slice_bits(dg[7][s], s) << 16);
-      *(uint4 *)(base + (size_t)(c * TC_SA + s) * r8 * (TC_KCH * 2) + tile_off(row, (int)(m0 % TC_KCH))) = w;
-    }
+  for (int s = 0; s < TC_SA; ++s) {
+    uint4 w;
+    w.x = slice_bits(dg[0][s], s) | ((unsigned)slice_bits(dg[1][s], s) << 16);
+    w.y = slice_bits(dg[2][s], s) | ((unsigned)slice_bits(dg[3][s], s) << 16);
+    w.z = slice_bits(dg[4][s], s) | ((unsigned)slice_bits(dg[5][s], s) << 16);
+    w.w = slice_bits(dg[6][s], s) | ((unsigned)slice_bits(dg[7][s], s) << 16);
+    *(uint4 *)(base + (size_t)(c * TC_SA + s) * r8 * (TC_KCH * 2) + tile_off(row, (int)(m0 % TC_KCH))) = w;
   }
-  // layout Ac: 8 consecutive rows m, one K column q
-  {
-    const long long mt = m0 / TC_M;
-    const int r8 = (int)min((long long)TC_M, (long long)round8((int)min(L - mt * TC_M, (long long)TC_M)));
-    const int c = q / TC_KCH, kk = q % TC_KCH;
-    unsigned char *base = (unsigned char *)Ac + (size_t)mt * kcc * TC_SA * TC_BLK;
+}
+
+// Row scale of the left operand of Y = E C: rowexp[m] = scale exponent of max_q |E_q[m]| for
+// every real component m (one thread each); *flag |= 1 on a NaN / Inf.
+__global__ void rowexp_kernel(const double *__restrict__ E, int k, long long L, int *rowexp, int *flag) {
+  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= L) return;
+  unsigned long long mb = 0;
+  for (int q = 0; q < k; ++q) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(E[(long long)q * L + m]) & 0x7fffffffffffffffull;
+    if ((u >> 52) == 0x7ff) atomicOr(flag, 1);
+    else if (u > mb) mb = u;
+  }
+  rowexp[m] = scale_exp(mb);
+}
+
+// Slices of E as the left operand of Y = E C (rows = real components m, K = vector index q, row
+// scale rowexp[m]): tile mt = m / 128, chunk c = q / 32, slice s at
+//        Ac + mt * kcc * 7 * 8192 + (c * 7 + s) * rows8(mt) * 64 + tile_off(m % 128, q % 32).
+// One thread per (m, 8 consecutive q: one 16-byte core-matrix row).  Padding must be zero already.
+__global__ void slice_ac_kernel(const double *__restrict__ E, int k, long long L, const int *rowexp, int kcc,
+                                unsigned short *__restrict__ Ac) {
+  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q0 = blockIdx.y * 8;
+  if (m >= L || q0 >= k) return;
+  const int e = rowexp[m];
+  int dg[8][TC_SA];
 #pragma unroll
-    for (int s = 0; s < TC_SA; ++s) {
-      unsigned char *blk = base + (size_t)(c * TC_SA + s) * r8 * (TC_KCH * 2);
+  for (int j = 0; j < 8; ++j) split_digits(q0 + j < k ? E[(long long)(q0 + j) * L + m] : 0.0, e, dg[j]);
+  const long long mt = m / TC_M;
+  const int r8 = (int)min((long long)TC_M, (long long)round8((int)min(L - mt * TC_M, (long long)TC_M)));
+  const int c = q0 / TC_KCH;
+  unsigned char *base = (unsigned char *)Ac + (size_t)mt * kcc * TC_SA * TC_BLK;
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        *(unsigned short *)(blk + tile_off((int)((m0 + j) % TC_M), kk)) = slice_bits(dg[j][s], s);
-    }
+  for (int s = 0; s < TC_SA; ++s) {
+    uint4 w;
+    w.x = slice_bits(dg[0][s], s) | ((unsigned)slice_bits(dg[1][s], s) << 16);
+    w.y = slice_bits(dg[2][s], s) | ((unsigned)slice_bits(dg[3][s], s) << 16);
+    w.z = slice_bits(dg[4][s], s) | ((unsigned)slice_bits(dg[5][s], s) << 16);
+    w.w = slice_bits(dg[6][s], s) | ((unsigned)slice_bits(dg[7][s], s) << 16);
+    *(uint4 *)(base + (size_t)(c * TC_SA + s) * r8 * (TC_KCH * 2) + tile_off((int)(m % TC_M), q0 % TC_KCH)) = w;
   }
 }
 
@@ -253,11 +281,11 @@ __global__ void slice_x_kernel(const double *__restrict__ X, int nrhs, long long
   }
 }
 
-// Right operand of Y = E C: row q of the reduction carries 2^eexp[q] d_q C[q][r] (the row scale
-// of E moved here), column n = 2r its real part and 2r + 1 its imaginary part, seven slices per
-// column with the column scale colexp[n].  d may be NULL (all ones).  One block per r.
+// Right operand of Y = E C: row q of the reduction carries d_q C[q][r], column n = 2r its real
+// part and 2r + 1 its imaginary part, seven slices per column with the column scale colexp[n].
+// d may be NULL (all ones).  One block per r.
 // Layout: B + (c * 7 + t) * NP * 64 + tile_off(n, q % 32), c = q / 32.
-__global__ void slice_c_kernel(const double2 *__restrict__ Cm, const double2 *__restrict__ d, const int *eexp, int k,
+__global__ void slice_c_kernel(const double2 *__restrict__ Cm, const double2 *__restrict__ d, int k,
                                int ldc, int NP, unsigned short *__restrict__ B, int *colexp) {
   const int r = blockIdx.x;
   __shared__ unsigned long long smax[2];
@@ -267,7 +295,7 @@ __global__ void slice_c_kernel(const double2 *__restrict__ Cm, const double2 *__
   for (int q = threadIdx.x; q < k; q += blockDim.x) {
     double2 c = Cm[(size_t)q * ldc + r];
     if (d) c = cmul(d[q], c);
-    const double re = scalbn(c.x, eexp[q]), im = scalbn(c.y, eexp[q]);
+    const double re = c.x, im = c.y;
     m0 = max(m0, (unsigned long long)__double_as_longlong(fabs(re)));
     m1 = max(m1, (unsigned long long)__double_as_longlong(fabs(im)));
   }
@@ -279,7 +307,7 @@ __global__ void slice_c_kernel(const double2 *__restrict__ Cm, const double2 *__
   for (int q = threadIdx.x; q < k; q += blockDim.x) {
     double2 c = Cm[(size_t)q * ldc + r];
     if (d) c = cmul(d[q], c);
-    const double re = scalbn(c.x, eexp[q]), im = scalbn(c.y, eexp[q]);
+    const double re = c.x, im = c.y;
     int d0[TC_SA], d1[TC_SA];
     split_digits(re, e0, d0);
     split_digits(im, e1, d1);
@@ -311,6 +339,12 @@ __global__ void vhx_reduce_kernel(const double *__restrict__ part, int nsplit, i
 // ---------------------------------------------------------------------------------------------
 // PTX wrappers (tcgen05, TMEM, bulk copies, mbarriers)
 // ---------------------------------------------------------------------------------------------
+
+// x 2^e: one multiplication by a power of two built from its bits (scalbn outside the normal range)
+__device__ __forceinline__ double mul_pow2(double x, int e) {
+  if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
+  return scalbn(x, e);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -418,7 +452,7 @@ struct TcArgs {
   int kc_count;            // K chunks of 32
   int ksplit;              // K splits per row tile (work items = mt_count * ksplit)
   int SB;                  // slices of B (1 or 7)
-  int kcr;                 // chunks per accumulator read-out (keeps the exact groups below 2^23 units)
+  int kcr;                 // chunks per accumulator read-out (keeps the exact groups within 2^24 units)
   int unit_shift;          // exact group g holds integers in units of 2^-(8 g + unit_shift)
   int npair;
   unsigned char ps[TC_MAXPAIR], pt[TC_MAXPAIR], pa[TC_MAXPAIR];  // slice pair -> accumulator
@@ -426,6 +460,7 @@ struct TcArgs {
   double *part;            // mode 0: part[(split * NP + n) * Mtot + m]
   long long Mtot;
   const int *colexp;       // mode 1: scale exponent per column
+  const int *rowexp;       // mode 1: scale exponent per row
   int nb;                  // mode 1: complex columns (column 2r real part, 2r + 1 imaginary part)
   double *out;             // mode 1: out[r * m_valid + m]
   int *err;
@@ -598,7 +633,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
           tmem_wait_ld();
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            // exact groups: integers n_g = v_g 2^(8 g + unit_shift) below 2^23, combined exactly
+            // exact groups: integers n_g = v_g 2^(8 g + unit_shift) of at most 2^24, combined exactly
             long long T = 0;
             float sc = sc0;
 #pragma unroll
@@ -622,10 +657,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         }
       } else {
         // rows 2i (real part) and 2i + 1 (imaginary part) of a complex entry are lanes 2i, 2i + 1
+        const int re = m < p.m_valid ? p.rowexp[m] : 0;
 #pragma unroll
         for (int r = 0; r < NP / 2; ++r) {
-          const double p1 = r < p.nb ? scalbn(acc[2 * r], p.colexp[2 * r]) : 0.0;
-          const double p2 = r < p.nb ? scalbn(acc[2 * r + 1], p.colexp[2 * r + 1]) : 0.0;
+          const double p1 = r < p.nb ? mul_pow2(acc[2 * r], re + p.colexp[2 * r]) : 0.0;
+          const double p2 = r < p.nb ? mul_pow2(acc[2 * r + 1], re + p.colexp[2 * r + 1]) : 0.0;
           const double p2o = __shfl_xor_sync(0xffffffffu, p2, 1);
           if (r < p.nb && m < p.m_valid) p.out[(size_t)r * p.m_valid + m] = (row & 1) ? p2o + p1 : p1 - p2o;
         }
@@ -651,6 +687,7 @@ struct TcSlices {
   int mtc, kcc;                // Y = E C operand: row tiles over the reals, K chunks over q
   unsigned char *Ag, *Ac;      // pre-tiled slices
   int *eexp;                   // per-vector scale exponent (device)
+  int *rowexp;                 // per-real-component scale exponent of the Y = E C operand (device)
   unsigned long long *maxbits; // per-vector maximum (device)
   int *minlsb, *flag;
 };
@@ -690,12 +727,12 @@ lqcd_status tc_gemm(lqcd_ctx *ctx, int NP, const TcArgs &a, double units) {
   return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core contraction: bad column count %d", NP);
 }
 
-// slice pairs (s, t) with s + t <= 6 and their accumulators min(s + t, 4)
+// slice pairs (s, t) with s + t <= 7 and their accumulators min(s + t, 4)
 void tc_pairs(TcArgs &a) {
   a.npair = 0;
   for (int s = 0; s < TC_SA; ++s)
     for (int t = 0; t < a.SB; ++t)
-      if (s + t <= TC_SA - 1) {
+      if (s + t <= TC_SA) {
         a.ps[a.npair] = (unsigned char)s;
         a.pt[a.npair] = (unsigned char)t;
         a.pa[a.npair] = (unsigned char)std::min(s + t, TC_NACC - 1);
@@ -703,11 +740,11 @@ void tc_pairs(TcArgs &a) {
       }
 }
 
-// chunks per read-out such that an exact group (at most P pairs of products below dA * dB
-// units each) stays below 2^23 units: kcr * 32 * P * dA * dB <= 2^23
+// chunks per read-out such that an exact group (at most P pairs of products of at most dA * dB
+// units each) stays within 2^24 units: kcr * 32 * P * dA * dB <= 2^24
 int tc_kcr(int SB, double dB) {
   const double P = std::min(4, SB);
-  const double kc = std::floor(8388608.0 / (P * 128.0 * dB * TC_KCH));
+  const double kc = std::floor(16777216.0 / (P * 128.0 * dB * TC_KCH));
   return (int)std::max(1.0, std::min(kc, 1e6));
 }
 
@@ -737,11 +774,13 @@ lqcd_status tc_slices_make(lqcd_ctx *ctx, const double2 *E, int k, void **out) {
   const size_t bg = tc_bytes_g(k, S->L), bc = tc_bytes_c(k, S->L);
   cudaError_t e1 = cudaMalloc(&S->Ag, bg), e2 = cudaMalloc(&S->Ac, bc);
   cudaError_t e3 = cudaMalloc(&S->eexp, sizeof(int) * (k + 2) + sizeof(unsigned long long) * k + sizeof(int) * (k + 1));
-  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+  cudaError_t e4 = cudaMalloc(&S->rowexp, sizeof(int) * S->L);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
     cudaGetLastError();
     if (e1 == cudaSuccess) cudaFree(S->Ag);
     if (e2 == cudaSuccess) cudaFree(S->Ac);
     if (e3 == cudaSuccess) cudaFree(S->eexp);
+    if (e4 == cudaSuccess) cudaFree(S->rowexp);
     delete S;
     return set_err(ctx, LQCD_ERR_OOM, "tensor-core slices: %.1f GB not available", (bg + bc) / 1e9);
   }
@@ -760,9 +799,17 @@ lqcd_status tc_slices_make(lqcd_ctx *ctx, const double2 *E, int k, void **out) {
   LQCD_TRY(launch_check(ctx, "vec_stats_kernel", K_SLICE, (double)k * S->L));
   LQCD_TRY(check_flag(ctx, S->flag, "tensor-core slices"));
   kbegin(ctx);
-  slice_e_kernel<<<dim3(ceil_div(S->L / 8, 128), k), 128, 0, ctx->stream>>>(
-      (const double *)E, k, S->L, S->maxbits, S->kcg, S->kcc, (unsigned short *)S->Ag, (unsigned short *)S->Ac, S->eexp);
-  return launch_check(ctx, "slice_e_kernel", K_SLICE, (double)k * S->L);
+  rowexp_kernel<<<ceil_div(S->L, 256), 256, 0, ctx->stream>>>((const double *)E, k, S->L, S->rowexp, S->flag);
+  LQCD_TRY(launch_check(ctx, "rowexp_kernel", K_SLICE, (double)k * S->L));
+  LQCD_TRY(check_flag(ctx, S->flag, "tensor-core slices"));
+  kbegin(ctx);
+  slice_ag_kernel<<<dim3(ceil_div(S->L / 8, 128), k), 128, 0, ctx->stream>>>(
+      (const double *)E, k, S->L, S->maxbits, S->kcg, (unsigned short *)S->Ag, S->eexp);
+  LQCD_TRY(launch_check(ctx, "slice_ag_kernel", K_SLICE, (double)k * S->L));
+  kbegin(ctx);
+  slice_ac_kernel<<<dim3(ceil_div(S->L, 128), S->kcc * (TC_KCH / 8)), 128, 0, ctx->stream>>>(
+      (const double *)E, k, S->L, S->rowexp, S->kcc, (unsigned short *)S->Ac);
+  return launch_check(ctx, "slice_ac_kernel", K_SLICE, (double)k * S->L);
 }
 
 void tc_slices_free(void *p) {
@@ -771,6 +818,7 @@ void tc_slices_free(void *p) {
   cudaFree(S->Ag);
   cudaFree(S->Ac);
   cudaFree(S->eexp);
+  cudaFree(S->rowexp);
   delete S;
 }
 
@@ -870,7 +918,7 @@ lqcd_status tc_vc(lqcd_ctx *ctx, const void *slices, const double2 *Cm, const do
     LQCD_CUDA(ctx, cudaMemsetAsync(Bsl, 0, bbytes, ctx->stream));
     LQCD_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
     kbegin(ctx);
-    slice_c_kernel<<<nb, 128, 0, ctx->stream>>>(Cm + r0, d, S->eexp, k, nrhs, NP, (unsigned short *)Bsl, colexp);
+    slice_c_kernel<<<nb, 128, 0, ctx->stream>>>(Cm + r0, d, k, nrhs, NP, (unsigned short *)Bsl, colexp);
     LQCD_TRY(launch_check(ctx, "slice_c_kernel", K_SLICE, (double)k * nb));
     TcArgs a{};
     a.SB = TC_SA;
@@ -885,6 +933,7 @@ lqcd_status tc_vc(lqcd_ctx *ctx, const void *slices, const double2 *Cm, const do
     a.ksplit = 1;
     a.mode = 1;
     a.colexp = colexp;
+    a.rowexp = S->rowexp;
     a.nb = nb;
     a.out = (double *)(Y + (size_t)r0 * ctx->N);
     a.err = flag;
