@@ -239,44 +239,63 @@ __global__ void slice_ac_kernel(const double *__restrict__ E, int k, long long L
 // i conj-rotated field r (entries (Im, -Re) per complex number), so that the real products give
 // Re and Im of conj(E) . X.  small != 0: one exact slice x 2^-lsb[r] (integers below 256);
 // otherwise seven slices with the column scale.  colexp[r] receives the exponent to undo.
-// Layout: B + (c * SB + t) * NP * 64 + tile_off(n, m % 32).  One thread per (n, 8 reals).
+// Layout: B + (c * SB + t) * NP * 64 + tile_off(n, m % 32).  One thread per (r, 8 reals), writing
+// both columns of r; integer arithmetic only.
+__device__ __forceinline__ int small_digit(double x, int e) {
+  // x = +-mant 2^(be - 1075) is an integer multiple of 2^e below 2^(e + 8): shift the significand
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int be = (int)((u >> 52) & 0x7ff);
+  if (be == 0) return 0;
+  const unsigned long long mant = (u & 0xfffffffffffffull) | (1ull << 52);
+  const int sh = be - 1075 - e;
+  const int d = sh >= 0 ? (int)(mant << sh) : (sh > -64 ? (int)(mant >> (-sh)) : 0);
+  return (u >> 63) ? -d : d;
+}
+__device__ __forceinline__ uint4 pack8(const unsigned short h[8]) {
+  uint4 w;
+  w.x = h[0] | ((unsigned)h[1] << 16);
+  w.y = h[2] | ((unsigned)h[3] << 16);
+  w.z = h[4] | ((unsigned)h[5] << 16);
+  w.w = h[6] | ((unsigned)h[7] << 16);
+  return w;
+}
 __global__ void slice_x_kernel(const double *__restrict__ X, int nrhs, long long L, const unsigned long long *maxbits,
                                const int *minlsb, int small, int SB, int NP, unsigned short *__restrict__ B,
                                int *colexp) {
-  const int n = blockIdx.y, r = n >> 1;
+  const int r = blockIdx.y;
   const long long m0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 8;
   if (m0 >= L || r >= nrhs) return;
   const int e = small ? (maxbits[r] ? minlsb[r] : 0) : scale_exp(maxbits[r]);
-  if (m0 == 0 && (n & 1) == 0) colexp[r] = e;
+  if (m0 == 0) colexp[r] = e;
   const double *src = X + (long long)r * L + m0;
-  double v[8];
+  double v[2][8];
 #pragma unroll
   for (int j = 0; j < 8; j += 2) {
     const double re = src[j], im = src[j + 1];
-    if (n & 1) { v[j] = im; v[j + 1] = -re; } else { v[j] = re; v[j + 1] = im; }
+    v[0][j] = re; v[0][j + 1] = im;     // column 2r
+    v[1][j] = im; v[1][j + 1] = -re;    // column 2r + 1
   }
   const long long c = m0 / TC_KCH;
-  unsigned char *base = (unsigned char *)B + (size_t)c * SB * NP * (TC_KCH * 2) + tile_off(n, (int)(m0 % TC_KCH));
-  if (small) {
-    unsigned short h[8];
+  unsigned char *base = (unsigned char *)B + (size_t)c * SB * NP * (TC_KCH * 2);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) h[j] = int_bits((int)scalbn(v[j], -e));  // exact: integer below 256
-    uint4 w;
-    w.x = h[0] | ((unsigned)h[1] << 16); w.y = h[2] | ((unsigned)h[3] << 16);
-    w.z = h[4] | ((unsigned)h[5] << 16); w.w = h[6] | ((unsigned)h[7] << 16);
-    *(uint4 *)base = w;
-  } else {
-    int dg[8][TC_SA];
+  for (int h = 0; h < 2; ++h) {
+    unsigned char *row = base + tile_off(2 * r + h, (int)(m0 % TC_KCH));
+    if (small) {
+      unsigned short b[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) split_digits(v[j], e, dg[j]);
+      for (int j = 0; j < 8; ++j) b[j] = int_bits(small_digit(v[h][j], e));
+      *(uint4 *)row = pack8(b);
+    } else {
+      int dg[8][TC_SA];
 #pragma unroll
-    for (int s = 0; s < TC_SA; ++s) {
-      uint4 w;
-      w.x = slice_bits(dg[0][s], s) | ((unsigned)slice_bits(dg[1][s], s) << 16);
-      w.y = slice_bits(dg[2][s], s) | ((unsigned)slice_bits(dg[3][s], s) << 16);
-      w.z = slice_bits(dg[4][s], s) | ((unsigned)slice_bits(dg[5][s], s) << 16);
-      w.w = slice_bits(dg[6][s], s) | ((unsigned)slice_bits(dg[7][s], s) << 16);
-      *(uint4 *)(base + (size_t)s * NP * (TC_KCH * 2)) = w;
+      for (int j = 0; j < 8; ++j) split_digits(v[h][j], e, dg[j]);
+#pragma unroll
+      for (int s = 0; s < TC_SA; ++s) {
+        unsigned short b[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[j] = slice_bits(dg[j][s], s);
+        *(uint4 *)(row + (size_t)s * NP * (TC_KCH * 2)) = pack8(b);
+      }
     }
   }
 }
@@ -876,7 +895,7 @@ lqcd_status tc_vhx(lqcd_ctx *ctx, const void *slices, const double2 *X, int nrhs
     Bsl = (unsigned char *)p;
     LQCD_CUDA(ctx, cudaMemsetAsync(Bsl, 0, bbytes, ctx->stream));
     kbegin(ctx);
-    slice_x_kernel<<<dim3(ceil_div(S->L / 8, 128), 2 * nb), 128, 0, ctx->stream>>>(
+    slice_x_kernel<<<dim3(ceil_div(S->L / 8, 128), nb), 128, 0, ctx->stream>>>(
         (const double *)Xb, nb, S->L, mb, lsb, small ? 1 : 0, a.SB, NP, (unsigned short *)Bsl, colexp);
     LQCD_TRY(launch_check(ctx, "slice_x_kernel", K_SLICE, (double)nb * S->L));
     a.A = S->Ag;
