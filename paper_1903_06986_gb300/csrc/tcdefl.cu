@@ -20,22 +20,25 @@
 //    exact slice;
 //  * slice products d_s d'_t carry the unit 2^(-8(s+t+c)); products of one "group" g = s + t
 //    share a unit, so their FP32 sums in TMEM are exact integers as long as they stay within 2^24
-//    units (every partial sum is then an integer of at most 24 bits).  Groups 0..3 get exact accumulators, read out (and converted to an exact 64-bit
-//    integer, then FP64) often enough to stay below that bound; groups 4..7 share one FP32
-//    accumulator whose rounding lies below 2^-56 of the leading term.  Pairs with s + t > 7 are
-//    dropped (below 2^-62 of the leading term).
+//    units (every partial sum is then an integer of at most 24 bits).  Groups 0..4 get exact
+//    accumulators, read out (and combined as an exact 64-bit integer, then FP64) often enough to
+//    stay within that bound; groups 5..7 share one FP32 accumulator, 2^-40 below the leading
+//    group, so its rounding stays below 2^-60 of the leading term even over long reductions.
+//    Pairs with s + t > 7 are dropped (below 2^-62 of the leading term).
 //  Per entry of the result the error is thus below about 2^-52 (max_i |a_i| sum_i |b_i| +
 //  sum_i |a_i| max_i |b_i|) plus the FP64 rounding of the folds, the bound of the splitting
 //  (an FP64 dot product has 2^-53 n sum_i |a_i||b_i| in the worst case).
 //
 // The tensor-core kernel (tc_gemm_kernel) is a persistent, warp-specialised tcgen05 GEMM:
-//   warp 4 (one lane)  moves pre-tiled slice blocks global -> shared with cp.async.bulk into a
+//   warp 8 (one lane)  moves pre-tiled slice blocks global -> shared with cp.async.bulk into a
 //                      ring of stages guarded by mbarriers (full / empty);
-//   warp 5 (one lane)  issues tcgen05.mma.cta_group::1.kind::f16 (bf16 x bf16 -> FP32, M = 128,
+//   warp 9 (one lane)  issues tcgen05.mma.cta_group::1.kind::f16 (bf16 x bf16 -> FP32, M = 128,
 //                      N = NP, K = 16) for every slice pair into TMEM, and tcgen05.commit to free
 //                      a stage / hand an accumulator set to the epilogue;
-//   warps 0-3          read the accumulators with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31,
-//                      i.e. output rows), fold the slice groups into FP64 and write the result.
+//   warps 0-7          read the accumulators with tcgen05.ld (warp w owns TMEM lanes 32 (w % 4) ..
+//                      32 (w % 4) + 31, i.e. output rows; warps 0-3 take the first half of the
+//                      columns, warps 4-7 the second), fold the slice groups into FP64 and write
+//                      the result.  Eight warps hide the latency of the integer / FP64 folds.
 // Two accumulator sets in TMEM (when they fit in 512 columns) let the MMAs of the next group run
 // while the epilogue drains the previous one.
 //
@@ -58,8 +61,10 @@ namespace {
 constexpr int TC_M = 128;                  // rows per tile = TMEM lanes
 constexpr int TC_KCH = 32;                 // K elements per pipeline chunk (64 bytes per row)
 constexpr int TC_SA = 7;                   // slices of the row-scaled operand (7 x 8 bits)
-constexpr int TC_NACC = 5;                 // accumulators: exact groups 0..3 + rounded tail
-constexpr int TC_THREADS = 192;            // warps 0-3 epilogue, 4 loader, 5 MMA issuer
+constexpr int TC_NACC = 6;                 // accumulators: exact groups 0..4 + rounded tail
+constexpr int TC_NEXACT = TC_NACC - 1;
+constexpr int TC_THREADS = 320;            // warps 0-7 epilogue, 8 loader, 9 MMA issuer
+constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_BLK = TC_M * TC_KCH * 2;  // bytes of a full 128-row slice block (8 KB)
 constexpr int TC_MAXPAIR = 34;
 constexpr int TC_SMEM_MAX = 227 * 1024;
@@ -527,7 +532,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, 4 * 32);
+      mbar_init(acce0 + 8 * b, TC_EPI_WARPS * 32);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -544,7 +549,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
+  if (warp == TC_EPI_WARPS) {
     // ---- loader ----
     if (lane == 0) {
       int stage = 0;
@@ -575,7 +580,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
           if (filled >> s & 1) mbar_drain(full0 + 8 * s, s < stage ? phase : phase ^ 1);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == TC_EPI_WARPS + 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
       int stage = 0, buf = 0;
@@ -622,19 +627,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       }
     }
   } else {
-    // ---- epilogue: warps 0-3, thread = TMEM lane = output row ----
-    const int row = warp * 32 + lane;
+    // ---- epilogue: warps 0-7; thread = TMEM lane = output row, half of the columns per warp ----
+    constexpr int NH = NP / 2;                   // columns of this warp
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = quad * 32 + lane;
+    const int cb = half * NH;                    // first column of this warp
     int buf = 0;
     uint32_t accph[2] = {0, 0};
     bool ok = true;
     const float sc0 = __int_as_float((127 + p.unit_shift) << 23);       // 2^unit_shift
-    const double unit3 = __longlong_as_double((long long)(1023 - 24 - p.unit_shift) << 52);
+    // unit of the last exact group: 2^-(8 (TC_NEXACT - 1) + unit_shift)
+    const double unitx = __longlong_as_double((long long)(1023 - 8 * (TC_NEXACT - 1) - p.unit_shift) << 52);
+    int ce[NH];                                  // column scale exponents (mode 1)
+#pragma unroll
+    for (int j = 0; j < NH; ++j) ce[j] = (p.mode == 1 && cb + j < 2 * p.nb) ? p.colexp[cb + j] : 0;
     for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
       int mt, sp, c0, c1;
       work_range(p, w, mt, sp, c0, c1);
-      double acc[NP];
+      const long long m = (long long)mt * TC_M + row;
+      const int rexp = (p.mode == 1 && m < p.m_valid) ? p.rowexp[m] : 0;   // issued before the waits
+      double acc[NH];
 #pragma unroll
-      for (int n = 0; n < NP; ++n) acc[n] = 0.0;
+      for (int j = 0; j < NH; ++j) acc[j] = 0.0;
       for (int g0 = c0; g0 < c1; g0 += p.kcr) {
         // the whole warp leaves together (tcgen05.ld and the shuffles below are warp-collective)
         if (!__all_sync(0xffffffffu, mbar_wait(accf0 + 8 * buf, accph[buf], abort_flag, p.err))) {
@@ -643,24 +657,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         }
         accph[buf] ^= 1;
         tc_fence_after();
-        const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * TC_NACC * NP);
+        const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * TC_NACC * NP + cb);
 #pragma unroll
-        for (int n0 = 0; n0 < NP; n0 += 8) {
+        for (int n0 = 0; n0 < NH; n0 += 8) {
           float v[TC_NACC][8];
 #pragma unroll
           for (int a = 0; a < TC_NACC; ++a) tmem_ld8(tb + (uint32_t)(a * NP + n0), v[a]);
           tmem_wait_ld();
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            // exact groups: integers n_g = v_g 2^(8 g + unit_shift) of at most 2^24, combined exactly
+            // exact groups: integers n_g = v_g 2^(8 g + unit_shift) of at most 2^24, combined
+            // exactly into T = sum_g n_g 2^(8 (4 - g)) < 2^57
             long long T = 0;
             float sc = sc0;
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
+            for (int g = 0; g < TC_NEXACT; ++g) {
               T = T * 256 + (long long)__float2int_rn(v[g][i] * sc);
               sc *= 256.0f;
             }
-            acc[n0 + i] += (double)T * unit3 + (double)v[4][i];
+            acc[n0 + i] += (double)T * unitx + (double)v[TC_NEXACT][i];
           }
         }
         tc_fence_before();
@@ -668,19 +683,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         buf ^= NBUF - 1;
       }
       if (!ok) break;
-      const long long m = (long long)mt * TC_M + row;
       if (p.mode == 0) {
         if (m < p.m_valid) {
 #pragma unroll
-          for (int n = 0; n < NP; ++n) p.part[((size_t)sp * NP + n) * p.Mtot + m] = acc[n];
+          for (int j = 0; j < NH; ++j) p.part[((size_t)sp * NP + cb + j) * p.Mtot + m] = acc[j];
         }
       } else {
-        // rows 2i (real part) and 2i + 1 (imaginary part) of a complex entry are lanes 2i, 2i + 1
-        const int re = m < p.m_valid ? p.rowexp[m] : 0;
+        // rows 2i (real part) and 2i + 1 (imaginary part) of a complex entry are lanes 2i, 2i + 1;
+        // column pair (2r, 2r + 1) holds the real and imaginary parts of coefficient column r
 #pragma unroll
-        for (int r = 0; r < NP / 2; ++r) {
-          const double p1 = r < p.nb ? mul_pow2(acc[2 * r], re + p.colexp[2 * r]) : 0.0;
-          const double p2 = r < p.nb ? mul_pow2(acc[2 * r + 1], re + p.colexp[2 * r + 1]) : 0.0;
+        for (int j = 0; j < NH; j += 2) {
+          const int r = (cb + j) >> 1;
+          const double p1 = r < p.nb ? mul_pow2(acc[j], rexp + ce[j]) : 0.0;
+          const double p2 = r < p.nb ? mul_pow2(acc[j + 1], rexp + ce[j + 1]) : 0.0;
           const double p2o = __shfl_xor_sync(0xffffffffu, p2, 1);
           if (r < p.nb && m < p.m_valid) p.out[(size_t)r * p.m_valid + m] = (row & 1) ? p2o + p1 : p1 - p2o;
         }
@@ -762,7 +777,7 @@ void tc_pairs(TcArgs &a) {
 // chunks per read-out such that an exact group (at most P pairs of products of at most dA * dB
 // units each) stays within 2^24 units: kcr * 32 * P * dA * dB <= 2^24
 int tc_kcr(int SB, double dB) {
-  const double P = std::min(4, SB);
+  const double P = std::min(TC_NEXACT, SB);
   const double kc = std::floor(16777216.0 / (P * 128.0 * dB * TC_KCH));
   return (int)std::max(1.0, std::min(kc, 1e6));
 }
