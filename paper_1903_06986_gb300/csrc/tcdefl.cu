@@ -20,11 +20,13 @@
 //    exact slice;
 //  * slice products d_s d'_t carry the unit 2^(-8(s+t+c)); products of one "group" g = s + t
 //    share a unit, so their FP32 sums in TMEM are exact integers as long as they stay within 2^24
-//    units (every partial sum is then an integer of at most 24 bits).  Groups 0..4 get exact
-//    accumulators, read out (and combined as an exact 64-bit integer, then FP64) often enough to
-//    stay within that bound; groups 5..7 share one FP32 accumulator, 2^-40 below the leading
-//    group, so its rounding stays below 2^-60 of the leading term even over long reductions.
-//    Pairs with s + t > 7 are dropped (below 2^-62 of the leading term).
+//    units (every partial sum is then an integer of at most 24 bits).  Every group g <= 7 has its
+//    own accumulator (TMEM columns g NP .. (g+1) NP - 1): stacking the slices of the right operand
+//    along N, one MMA of left slice s against right slices t0..t1 writes A_s B_t straight into the
+//    columns of group s + t, so TMEM does the grouping.  Groups 0..4 are read out (and combined as
+//    an exact 64-bit integer, then FP64) often enough to stay within the 2^24 bound; groups 5..7,
+//    at least 2^-40 below the leading group, are added in FP32 (rounding below 2^-60 of the
+//    leading term).  Pairs with s + t > 7 are not formed (below 2^-62 of the leading term).
 //  Per entry of the result the error is thus below about 2^-52 (max_i |a_i| sum_i |b_i| +
 //  sum_i |a_i| max_i |b_i|) plus the FP64 rounding of the folds, the bound of the splitting
 //  (an FP64 dot product has 2^-53 n sum_i |a_i||b_i| in the worst case).
@@ -33,12 +35,15 @@
 //   warp 8 (one lane)  moves pre-tiled slice blocks global -> shared with cp.async.bulk into a
 //                      ring of stages guarded by mbarriers (full / empty);
 //   warp 9 (one lane)  issues tcgen05.mma.cta_group::1.kind::f16 (bf16 x bf16 -> FP32, M = 128,
-//                      N = NP, K = 16) for every slice pair into TMEM, and tcgen05.commit to free
-//                      a stage / hand an accumulator set to the epilogue;
+//                      N = (slices stacked) x NP <= 256, K = 16) into TMEM: 7 (Z(4) right operand)
+//                      to 11 MMAs per 16 reduction elements, an unrolled sequence with constant
+//                      descriptor offsets; tcgen05.commit frees a stage / hands an accumulator set
+//                      to the epilogue;
 //   warps 0-7          read the accumulators with tcgen05.ld (warp w owns TMEM lanes 32 (w % 4) ..
 //                      32 (w % 4) + 31, i.e. output rows; warps 0-3 take the first half of the
 //                      columns, warps 4-7 the second), fold the slice groups into FP64 and write
-//                      the result.  Eight warps hide the latency of the integer / FP64 folds.
+//                      the result, then zero the accumulator set (tcgen05.st) for its next use.
+//                      Eight warps hide the latency of the integer / FP64 folds.
 // Two accumulator sets in TMEM (when they fit in 512 columns) let the MMAs of the next group run
 // while the epilogue drains the previous one.
 //
@@ -61,12 +66,11 @@ namespace {
 constexpr int TC_M = 128;                  // rows per tile = TMEM lanes
 constexpr int TC_KCH = 32;                 // K elements per pipeline chunk (64 bytes per row)
 constexpr int TC_SA = 7;                   // slices of the row-scaled operand (7 x 8 bits)
-constexpr int TC_NACC = 6;                 // accumulators: exact groups 0..4 + rounded tail
-constexpr int TC_NEXACT = TC_NACC - 1;
+constexpr int TC_NGRP = 8;                 // accumulated slice groups g = s + t <= 7
+constexpr int TC_NEXACT = 5;               // groups 0..4 are exact integers; 5..7 are summed in FP32
 constexpr int TC_THREADS = 320;            // warps 0-7 epilogue, 8 loader, 9 MMA issuer
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_BLK = TC_M * TC_KCH * 2;  // bytes of a full 128-row slice block (8 KB)
-constexpr int TC_MAXPAIR = 34;
 constexpr int TC_SMEM_MAX = 227 * 1024;
 constexpr int TC_SMEM_MIN = 120 * 1024;    // forces one CTA per SM (TMEM is allocated per CTA)
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // bound of every mbarrier wait
@@ -463,6 +467,13 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// zero 8 consecutive TMEM columns of the warp's 32 lanes
+__device__ __forceinline__ void tmem_zero8(uint32_t taddr) {
+  const uint32_t z = 0;
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(z)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------------------------
 // The tcgen05 GEMM
@@ -475,11 +486,8 @@ struct TcArgs {
   int m_valid;             // valid rows (rows >= m_valid are neither loaded from HBM nor written)
   int kc_count;            // K chunks of 32
   int ksplit;              // K splits per row tile (work items = mt_count * ksplit)
-  int SB;                  // slices of B (1 or 7)
   int kcr;                 // chunks per accumulator read-out (keeps the exact groups within 2^24 units)
   int unit_shift;          // exact group g holds integers in units of 2^-(8 g + unit_shift)
-  int npair;
-  unsigned char ps[TC_MAXPAIR], pt[TC_MAXPAIR], pa[TC_MAXPAIR];  // slice pair -> accumulator
   int mode;                // 0: partial sums; 1: complex columns combined into fields
   double *part;            // mode 0: part[(split * NP + n) * Mtot + m]
   long long Mtot;
@@ -491,15 +499,17 @@ struct TcArgs {
 };
 
 __host__ __device__ constexpr int tc_stage_bytes(int SB, int NP) { return TC_SA * TC_BLK + SB * NP * TC_KCH * 2; }
-__host__ __device__ constexpr int tc_nbuf(int NP) { return 2 * TC_NACC * NP <= 512 ? 2 : 1; }
+__host__ __device__ constexpr int tc_nbuf(int NP) { return 2 * TC_NGRP * NP <= 512 ? 2 : 1; }
 // TMEM columns to allocate: a power of two >= 32 holding every accumulator set
 __host__ __device__ constexpr uint32_t tc_tmem_cols(int NP) {
-  return tc_nbuf(NP) * TC_NACC * NP <= 32    ? 32u
-         : tc_nbuf(NP) * TC_NACC * NP <= 64  ? 64u
-         : tc_nbuf(NP) * TC_NACC * NP <= 128 ? 128u
-         : tc_nbuf(NP) * TC_NACC * NP <= 256 ? 256u
+  return tc_nbuf(NP) * TC_NGRP * NP <= 32    ? 32u
+         : tc_nbuf(NP) * TC_NGRP * NP <= 64  ? 64u
+         : tc_nbuf(NP) * TC_NGRP * NP <= 128 ? 128u
+         : tc_nbuf(NP) * TC_NGRP * NP <= 256 ? 256u
                                              : 512u;
 }
+// right slices per MMA: N = slices x NP <= 256
+__host__ __device__ constexpr int tc_tch(int NP) { return 256 / NP < TC_SA ? 256 / NP : TC_SA; }
 
 __device__ __forceinline__ void work_range(const TcArgs &p, int w, int &mt, int &sp, int &c0, int &c1) {
   mt = w / p.ksplit;
@@ -508,10 +518,10 @@ __device__ __forceinline__ void work_range(const TcArgs &p, int w, int &mt, int 
   c1 = (int)((long long)p.kc_count * (sp + 1) / p.ksplit);
 }
 
-template <int NP>
+template <int NP, int SB>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcArgs p, int stages) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int sbytes = tc_stage_bytes(p.SB, NP);
+  constexpr int sbytes = tc_stage_bytes(SB, NP);
   unsigned long long *bars = (unsigned long long *)(smem + (size_t)stages * sbytes);
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * stages, accf0 = full0 + 16 * stages,
                  acce0 = accf0 + 16, drain = acce0 + 16;
@@ -548,6 +558,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // every accumulator column starts at zero: the MMAs only ever accumulate
+  if (warp < TC_EPI_WARPS) {
+    const uint32_t tq = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    for (int c = (warp >> 2) * 8; c < NBUF * TC_NGRP * NP; c += 16) tmem_zero8(tq + (uint32_t)c);
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
   if (warp == TC_EPI_WARPS) {
     // ---- loader ----
@@ -555,7 +574,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       int stage = 0;
       uint32_t phase = 0;
       uint32_t filled = 0;  // stages armed at least once (for the drain after an abort)
-      const uint32_t bbytes = (uint32_t)(p.SB * NP * TC_KCH * 2);
+      constexpr uint32_t bbytes = (uint32_t)(SB * NP * TC_KCH * 2);
       bool ok = true;
       for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
         int mt, sp, c0, c1;
@@ -563,6 +582,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         const int r8 = min(TC_M, round8(p.m_valid - mt * TC_M));
         const uint32_t ablk = (uint32_t)(r8 * TC_KCH * 2);
         const unsigned char *abase = p.A + (size_t)mt * p.kc_count * TC_SA * TC_BLK;
+        (void)sp;
         for (int c = c0; c < c1; ++c) {
           if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.err)) { ok = false; break; }
           const uint32_t sA = smem_u32(smem + (size_t)stage * sbytes);
@@ -585,7 +605,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     if (lane == 0) {
       int stage = 0, buf = 0;
       uint32_t phase = 0, accph[2] = {0, 0};
-      const uint32_t idesc = mma_idesc(NP);
       bool ok = true, issued = false;
       for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
         int mt, sp, c0, c1;
@@ -596,19 +615,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
           const int g1 = min(c1, g0 + p.kcr);
           if (!mbar_wait(acce0 + 8 * buf, accph[buf] ^ 1, abort_flag, p.err)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t dbase = tmem + (uint32_t)(buf * TC_NACC * NP);
-          uint32_t started = 0;
+          const uint32_t dbase = tmem + (uint32_t)(buf * TC_NGRP * NP);
           for (int c = g0; c < g1; ++c) {
             if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) { ok = false; break; }
             tc_fence_after();
             const uint32_t sA = smem_u32(smem + (size_t)stage * sbytes), sB = sA + TC_SA * TC_BLK;
+            // descriptors of the stage's first K step; later operands differ only in the start
+            // address field (bits 0-13, units of 16 bytes)
+            const uint64_t a0 = smem_desc(sA), b0 = smem_desc(sB);
+            const uint32_t ab16 = ablk >> 4;
 #pragma unroll
             for (int j = 0; j < TC_KCH / 16; ++j) {
-              for (int i = 0; i < p.npair; ++i) {
-                const int a = p.pa[i];
-                mma_bf16(dbase + (uint32_t)(a * NP), smem_desc(sA + p.ps[i] * ablk + 256 * j),
-                         smem_desc(sB + p.pt[i] * (NP * TC_KCH * 2) + 256 * j), idesc, (started >> a) & 1u);
-                started |= 1u << a;
+#pragma unroll
+              for (int sl = 0; sl < TC_SA; ++sl) {
+                // right slices t with sl + t <= 7, in MMAs of at most tc_tch(NP) stacked slices
+                constexpr int TCH = tc_tch(NP);
+                const int tmax = (SB - 1 < TC_NGRP - 1 - sl) ? SB - 1 : TC_NGRP - 1 - sl;
+#pragma unroll
+                for (int t0 = 0; t0 <= tmax; t0 += TCH) {
+                  const int t1 = (t0 + TCH - 1 < tmax) ? t0 + TCH - 1 : tmax;
+                  mma_bf16(dbase + (uint32_t)((sl + t0) * NP),
+                           a0 + (uint64_t)(sl * ab16 + 16 * j),
+                           b0 + (uint64_t)(t0 * (NP * TC_KCH * 2 / 16) + 16 * j),
+                           mma_idesc((t1 - t0 + 1) * NP), 1u);
+                }
               }
             }
             issued = true;
@@ -657,13 +687,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         }
         accph[buf] ^= 1;
         tc_fence_after();
-        const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * TC_NACC * NP + cb);
+        const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * TC_NGRP * NP + cb);
 #pragma unroll
         for (int n0 = 0; n0 < NH; n0 += 8) {
-          float v[TC_NACC][8];
+          float v[TC_NGRP][8];
 #pragma unroll
-          for (int a = 0; a < TC_NACC; ++a) tmem_ld8(tb + (uint32_t)(a * NP + n0), v[a]);
+          for (int a = 0; a < TC_NGRP; ++a) tmem_ld8(tb + (uint32_t)(a * NP + n0), v[a]);
           tmem_wait_ld();
+#pragma unroll
+          for (int a = 0; a < TC_NGRP; ++a) tmem_zero8(tb + (uint32_t)(a * NP + n0));   // ready for reuse
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             // exact groups: integers n_g = v_g 2^(8 g + unit_shift) of at most 2^24, combined
@@ -675,9 +707,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
               T = T * 256 + (long long)__float2int_rn(v[g][i] * sc);
               sc *= 256.0f;
             }
-            acc[n0 + i] += (double)T * unitx + (double)v[TC_NEXACT][i];
+            const float tail = (v[7][i] + v[6][i]) + v[5][i];
+            acc[n0 + i] += (double)T * unitx + (double)tail;
           }
         }
+        tmem_wait_st();
         tc_fence_before();
         mbar_arrive(acce0 + 8 * buf);
         buf ^= NBUF - 1;
@@ -737,41 +771,38 @@ size_t tc_bytes_c(int k, long long L) {
   return (size_t)mt * kc * TC_SA * TC_BLK;
 }
 
-template <int NP> lqcd_status tc_gemm_launch(lqcd_ctx *ctx, const TcArgs &a, double units) {
-  const int sbytes = tc_stage_bytes(a.SB, NP);
+template <int NP, int SB> lqcd_status tc_gemm_launch(lqcd_ctx *ctx, const TcArgs &a, double units) {
+  constexpr int sbytes = tc_stage_bytes(SB, NP);
   const int bar_bytes = 8 * (2 * 4 + 8) + 64;  // room for up to 4 stages of barriers + slot + flag
   int stages = std::min(4, (TC_SMEM_MAX - bar_bytes - 64) / sbytes);
   if (stages < 2) return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core contraction: stage does not fit");
   const int smem = std::max(TC_SMEM_MIN, stages * sbytes + 8 * (2 * stages + 5) + 64);
-  LQCD_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  LQCD_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_kernel<NP, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int nwork = a.mt_count * a.ksplit;
   const int grid = std::min(nwork, ctx->sms);
   kbegin(ctx);
-  tc_gemm_kernel<NP><<<grid, TC_THREADS, smem, ctx->stream>>>(a, stages);
+  tc_gemm_kernel<NP, SB><<<grid, TC_THREADS, smem, ctx->stream>>>(a, stages);
   return launch_check(ctx, "tc_gemm_kernel", K_TENSOR, units);
 }
 
-lqcd_status tc_gemm(lqcd_ctx *ctx, int NP, const TcArgs &a, double units) {
-  switch (NP) {
-    case 16: return tc_gemm_launch<16>(ctx, a, units);
-    case 32: return tc_gemm_launch<32>(ctx, a, units);
-    case 48: return tc_gemm_launch<48>(ctx, a, units);
-    case 64: return tc_gemm_launch<64>(ctx, a, units);
+// SB: slices of the right operand (1: small integers, 7: general)
+lqcd_status tc_gemm(lqcd_ctx *ctx, int NP, int SB, const TcArgs &a, double units) {
+  if (SB == 1) {
+    switch (NP) {
+      case 16: return tc_gemm_launch<16, 1>(ctx, a, units);
+      case 32: return tc_gemm_launch<32, 1>(ctx, a, units);
+      case 48: return tc_gemm_launch<48, 1>(ctx, a, units);
+      case 64: return tc_gemm_launch<64, 1>(ctx, a, units);
+    }
+  } else if (SB == TC_SA) {
+    switch (NP) {
+      case 16: return tc_gemm_launch<16, TC_SA>(ctx, a, units);
+      case 32: return tc_gemm_launch<32, TC_SA>(ctx, a, units);
+      case 48: return tc_gemm_launch<48, TC_SA>(ctx, a, units);
+      case 64: return tc_gemm_launch<64, TC_SA>(ctx, a, units);
+    }
   }
-  return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core contraction: bad column count %d", NP);
-}
-
-// slice pairs (s, t) with s + t <= 7 and their accumulators min(s + t, 4)
-void tc_pairs(TcArgs &a) {
-  a.npair = 0;
-  for (int s = 0; s < TC_SA; ++s)
-    for (int t = 0; t < a.SB; ++t)
-      if (s + t <= TC_SA) {
-        a.ps[a.npair] = (unsigned char)s;
-        a.pt[a.npair] = (unsigned char)t;
-        a.pa[a.npair] = (unsigned char)std::min(s + t, TC_NACC - 1);
-        ++a.npair;
-      }
+  return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core contraction: bad shape NP %d SB %d", NP, SB);
 }
 
 // chunks per read-out such that an exact group (at most P pairs of products of at most dA * dB
@@ -900,18 +931,17 @@ lqcd_status tc_vhx(lqcd_ctx *ctx, const void *slices, const double2 *X, int nrhs
       if (mexp - hl[r] > 7) small = false;
     }
     TcArgs a{};
-    a.SB = small ? 1 : TC_SA;
+    const int SB = small ? 1 : TC_SA;
     const double dB = small ? std::ldexp(1.0, span + 1) : 128.0;
-    a.kcr = tc_kcr(a.SB, dB);
+    a.kcr = tc_kcr(SB, dB);
     a.unit_shift = small ? 8 : 16;
-    tc_pairs(a);
-    const size_t bbytes = (size_t)S->kcg * a.SB * NP * TC_KCH * 2;
+    const size_t bbytes = (size_t)S->kcg * SB * NP * TC_KCH * 2;
     LQCD_TRY(ws_get(ctx, WS_TC_B, bbytes, &p));
     Bsl = (unsigned char *)p;
     LQCD_CUDA(ctx, cudaMemsetAsync(Bsl, 0, bbytes, ctx->stream));
     kbegin(ctx);
     slice_x_kernel<<<dim3(ceil_div(S->L / 8, 128), nb), 128, 0, ctx->stream>>>(
-        (const double *)Xb, nb, S->L, mb, lsb, small ? 1 : 0, a.SB, NP, (unsigned short *)Bsl, colexp);
+        (const double *)Xb, nb, S->L, mb, lsb, small ? 1 : 0, SB, NP, (unsigned short *)Bsl, colexp);
     LQCD_TRY(launch_check(ctx, "slice_x_kernel", K_SLICE, (double)nb * S->L));
     a.A = S->Ag;
     a.B = Bsl;
@@ -925,7 +955,7 @@ lqcd_status tc_vhx(lqcd_ctx *ctx, const void *slices, const double2 *X, int nrhs
     part = (double *)p;
     a.part = part;
     a.err = flag;
-    LQCD_TRY(tc_gemm(ctx, NP, a, (double)k * nb * ctx->N));
+    LQCD_TRY(tc_gemm(ctx, NP, SB, a, (double)k * nb * ctx->N));
     kbegin(ctx);
     vhx_reduce_kernel<<<ceil_div(k * nb, 128), 128, 0, ctx->stream>>>(part, a.ksplit, NP, a.Mtot, k, nb, S->eexp,
                                                                        colexp, G + r0, nrhs);
@@ -955,10 +985,8 @@ lqcd_status tc_vc(lqcd_ctx *ctx, const void *slices, const double2 *Cm, const do
     slice_c_kernel<<<nb, 128, 0, ctx->stream>>>(Cm + r0, d, k, nrhs, NP, (unsigned short *)Bsl, colexp);
     LQCD_TRY(launch_check(ctx, "slice_c_kernel", K_SLICE, (double)k * nb));
     TcArgs a{};
-    a.SB = TC_SA;
-    a.kcr = tc_kcr(a.SB, 128.0);
+    a.kcr = tc_kcr(TC_SA, 128.0);
     a.unit_shift = 16;
-    tc_pairs(a);
     a.A = S->Ac;
     a.B = Bsl;
     a.mt_count = S->mtc;
@@ -971,7 +999,7 @@ lqcd_status tc_vc(lqcd_ctx *ctx, const void *slices, const double2 *Cm, const do
     a.nb = nb;
     a.out = (double *)(Y + (size_t)r0 * ctx->N);
     a.err = flag;
-    LQCD_TRY(tc_gemm(ctx, NP, a, (double)k * nb * ctx->N));
+    LQCD_TRY(tc_gemm(ctx, NP, TC_SA, a, (double)k * nb * ctx->N));
     LQCD_TRY(check_flag(ctx, flag, "tensor-core V C"));
   }
   return LQCD_OK;
