@@ -374,6 +374,20 @@ __device__ __forceinline__ double mul_pow2(double x, int e) {
   return scalbn(x, e);
 }
 
+// (T 2^-(8 (TC_NEXACT - 1) + unit_shift) + tail) 2^e for the exact integer part T and the FP32
+// tail: both power-of-two scales are applied exactly before one conversion and one FMA; outside
+// the normal ranges the slower general form is used
+__device__ __forceinline__ double fold_scaled(long long T, float tail, int e, int unit_shift) {
+  const int e1 = e - 8 * (TC_NEXACT - 1) - unit_shift;
+  if (e1 >= -1022 && e1 <= 1023 && e >= -126 && e <= 127) {
+    const double s1 = __longlong_as_double((long long)(e1 + 1023) << 52);
+    const float tf = tail * __int_as_float((e + 127) << 23);
+    return fma((double)T, s1, (double)tf);
+  }
+  const double unitx = __longlong_as_double((long long)(1023 - 8 * (TC_NEXACT - 1) - unit_shift) << 52);
+  return mul_pow2((double)T * unitx + (double)tail, e);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -488,7 +502,6 @@ struct TcArgs {
   int ksplit;              // K splits per row tile (work items = mt_count * ksplit)
   int kcr;                 // chunks per accumulator read-out (keeps the exact groups within 2^24 units)
   int unit_shift;          // exact group g holds integers in units of 2^-(8 g + unit_shift)
-  int mode;                // 0: partial sums; 1: complex columns combined into fields
   double *part;            // mode 0: part[(split * NP + n) * Mtot + m]
   long long Mtot;
   const int *colexp;       // mode 1: scale exponent per column
@@ -518,7 +531,8 @@ __device__ __forceinline__ void work_range(const TcArgs &p, int w, int &mt, int 
   c1 = (int)((long long)p.kc_count * (sp + 1) / p.ksplit);
 }
 
-template <int NP, int SB>
+// MODE 0: partial sums of G = E^dag X; MODE 1: fields of Y = E C (see TcArgs)
+template <int NP, int SB, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcArgs p, int stages) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr int sbytes = tc_stage_bytes(SB, NP);
@@ -670,15 +684,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     const double unitx = __longlong_as_double((long long)(1023 - 8 * (TC_NEXACT - 1) - p.unit_shift) << 52);
     int ce[NH];                                  // column scale exponents (mode 1)
 #pragma unroll
-    for (int j = 0; j < NH; ++j) ce[j] = (p.mode == 1 && cb + j < 2 * p.nb) ? p.colexp[cb + j] : 0;
+    for (int j = 0; j < NH; ++j) ce[j] = (MODE == 1 && cb + j < 2 * p.nb) ? p.colexp[cb + j] : 0;
     for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
       int mt, sp, c0, c1;
       work_range(p, w, mt, sp, c0, c1);
       const long long m = (long long)mt * TC_M + row;
-      const int rexp = (p.mode == 1 && m < p.m_valid) ? p.rowexp[m] : 0;   // issued before the waits
-      double acc[NH];
+      const int rexp = (MODE == 1 && m < p.m_valid) ? p.rowexp[m] : 0;   // issued before the waits
+      // MODE 0 folds every read-out into FP64; MODE 1 (a few read-outs per tile, bounded on the
+      // host) keeps the exact part as a 64-bit integer and the FP32 tail until the final write
+      double acc[MODE == 0 ? NH : 1];
+      long long Ti[MODE == 1 ? NH : 1];
+      float tl[MODE == 1 ? NH : 1];
 #pragma unroll
-      for (int j = 0; j < NH; ++j) acc[j] = 0.0;
+      for (int j = 0; j < NH; ++j) {
+        if constexpr (MODE == 0) acc[j] = 0.0;
+        else { Ti[j] = 0; tl[j] = 0.f; }
+      }
       for (int g0 = c0; g0 < c1; g0 += p.kcr) {
         // the whole warp leaves together (tcgen05.ld and the shuffles below are warp-collective)
         if (!__all_sync(0xffffffffu, mbar_wait(accf0 + 8 * buf, accph[buf], abort_flag, p.err))) {
@@ -708,7 +729,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
               sc *= 256.0f;
             }
             const float tail = (v[7][i] + v[6][i]) + v[5][i];
-            acc[n0 + i] += (double)T * unitx + (double)tail;
+            if constexpr (MODE == 0) acc[n0 + i] += (double)T * unitx + (double)tail;
+            else { Ti[n0 + i] += T; tl[n0 + i] += tail; }
           }
         }
         tmem_wait_st();
@@ -717,7 +739,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         buf ^= NBUF - 1;
       }
       if (!ok) break;
-      if (p.mode == 0) {
+      if constexpr (MODE == 0) {
         if (m < p.m_valid) {
 #pragma unroll
           for (int j = 0; j < NH; ++j) p.part[((size_t)sp * NP + cb + j) * p.Mtot + m] = acc[j];
@@ -728,8 +750,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
 #pragma unroll
         for (int j = 0; j < NH; j += 2) {
           const int r = (cb + j) >> 1;
-          const double p1 = r < p.nb ? mul_pow2(acc[j], rexp + ce[j]) : 0.0;
-          const double p2 = r < p.nb ? mul_pow2(acc[j + 1], rexp + ce[j + 1]) : 0.0;
+          const double p1 = r < p.nb ? fold_scaled(Ti[j], tl[j], rexp + ce[j], p.unit_shift) : 0.0;
+          const double p2 = r < p.nb ? fold_scaled(Ti[j + 1], tl[j + 1], rexp + ce[j + 1], p.unit_shift) : 0.0;
           const double p2o = __shfl_xor_sync(0xffffffffu, p2, 1);
           if (r < p.nb && m < p.m_valid) p.out[(size_t)r * p.m_valid + m] = (row & 1) ? p2o + p1 : p1 - p2o;
         }
@@ -771,38 +793,35 @@ size_t tc_bytes_c(int k, long long L) {
   return (size_t)mt * kc * TC_SA * TC_BLK;
 }
 
-template <int NP, int SB> lqcd_status tc_gemm_launch(lqcd_ctx *ctx, const TcArgs &a, double units) {
+template <int NP, int SB, int MODE> lqcd_status tc_gemm_launch(lqcd_ctx *ctx, const TcArgs &a, double units) {
   constexpr int sbytes = tc_stage_bytes(SB, NP);
   const int bar_bytes = 8 * (2 * 4 + 8) + 64;  // room for up to 4 stages of barriers + slot + flag
   int stages = std::min(4, (TC_SMEM_MAX - bar_bytes - 64) / sbytes);
   if (stages < 2) return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core contraction: stage does not fit");
   const int smem = std::max(TC_SMEM_MIN, stages * sbytes + 8 * (2 * stages + 5) + 64);
-  LQCD_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_kernel<NP, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  LQCD_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_kernel<NP, SB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int nwork = a.mt_count * a.ksplit;
   const int grid = std::min(nwork, ctx->sms);
   kbegin(ctx);
-  tc_gemm_kernel<NP, SB><<<grid, TC_THREADS, smem, ctx->stream>>>(a, stages);
+  tc_gemm_kernel<NP, SB, MODE><<<grid, TC_THREADS, smem, ctx->stream>>>(a, stages);
   return launch_check(ctx, "tc_gemm_kernel", K_TENSOR, units);
 }
 
-// SB: slices of the right operand (1: small integers, 7: general)
-lqcd_status tc_gemm(lqcd_ctx *ctx, int NP, int SB, const TcArgs &a, double units) {
-  if (SB == 1) {
-    switch (NP) {
-      case 16: return tc_gemm_launch<16, 1>(ctx, a, units);
-      case 32: return tc_gemm_launch<32, 1>(ctx, a, units);
-      case 48: return tc_gemm_launch<48, 1>(ctx, a, units);
-      case 64: return tc_gemm_launch<64, 1>(ctx, a, units);
-    }
-  } else if (SB == TC_SA) {
-    switch (NP) {
-      case 16: return tc_gemm_launch<16, TC_SA>(ctx, a, units);
-      case 32: return tc_gemm_launch<32, TC_SA>(ctx, a, units);
-      case 48: return tc_gemm_launch<48, TC_SA>(ctx, a, units);
-      case 64: return tc_gemm_launch<64, TC_SA>(ctx, a, units);
-    }
+// MODE 0 (G = E^dag X partial sums) with SB = 1 (small-integer right operand) or 7 slices;
+// MODE 1 (Y = E C fields) with SB = 7
+lqcd_status tc_gemm(lqcd_ctx *ctx, int NP, int SB, int mode, const TcArgs &a, double units) {
+#define TC_NP_CASES(SBV, MV)                                              \
+  switch (NP) {                                                           \
+    case 16: return tc_gemm_launch<16, SBV, MV>(ctx, a, units);          \
+    case 32: return tc_gemm_launch<32, SBV, MV>(ctx, a, units);          \
+    case 48: return tc_gemm_launch<48, SBV, MV>(ctx, a, units);          \
+    case 64: return tc_gemm_launch<64, SBV, MV>(ctx, a, units);          \
   }
-  return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core contraction: bad shape NP %d SB %d", NP, SB);
+  if (mode == 0 && SB == 1) TC_NP_CASES(1, 0)
+  if (mode == 0 && SB == TC_SA) TC_NP_CASES(TC_SA, 0)
+  if (mode == 1 && SB == TC_SA) TC_NP_CASES(TC_SA, 1)
+#undef TC_NP_CASES
+  return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core contraction: bad shape NP %d SB %d mode %d", NP, SB, mode);
 }
 
 // chunks per read-out such that an exact group (at most P pairs of products of at most dA * dB
@@ -949,13 +968,12 @@ lqcd_status tc_vhx(lqcd_ctx *ctx, const void *slices, const double2 *X, int nrhs
     a.m_valid = k;
     a.kc_count = S->kcg;
     a.ksplit = std::max(1, std::min(S->kcg, ctx->sms / S->mtg));
-    a.mode = 0;
     a.Mtot = (long long)S->mtg * TC_M;
     LQCD_TRY(ws_get(ctx, WS_TC_PART, sizeof(double) * (size_t)a.ksplit * NP * a.Mtot + 64, &p));
     part = (double *)p;
     a.part = part;
     a.err = flag;
-    LQCD_TRY(tc_gemm(ctx, NP, SB, a, (double)k * nb * ctx->N));
+    LQCD_TRY(tc_gemm(ctx, NP, SB, 0, a, (double)k * nb * ctx->N));
     kbegin(ctx);
     vhx_reduce_kernel<<<ceil_div(k * nb, 128), 128, 0, ctx->stream>>>(part, a.ksplit, NP, a.Mtot, k, nb, S->eexp,
                                                                        colexp, G + r0, nrhs);
@@ -993,13 +1011,15 @@ lqcd_status tc_vc(lqcd_ctx *ctx, const void *slices, const double2 *Cm, const do
     a.m_valid = (int)S->L;
     a.kc_count = S->kcc;
     a.ksplit = 1;
-    a.mode = 1;
     a.colexp = colexp;
     a.rowexp = S->rowexp;
     a.nb = nb;
     a.out = (double *)(Y + (size_t)r0 * ctx->N);
     a.err = flag;
-    LQCD_TRY(tc_gemm(ctx, NP, TC_SA, a, (double)k * nb * ctx->N));
+        // the exact parts of all read-outs of a tile are summed as 64-bit integers (each < 2^57)
+    if ((S->kcc + a.kcr - 1) / a.kcr > 63)
+      return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core V C: too many read-outs per tile");
+    LQCD_TRY(tc_gemm(ctx, NP, TC_SA, 1, a, (double)k * nb * ctx->N));
     LQCD_TRY(check_flag(ctx, flag, "tensor-core V C"));
   }
   return LQCD_OK;
