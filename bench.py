@@ -38,6 +38,7 @@ WORKLOAD = "8^3x16 plain FP64, kappa {0.150,0.155,0.157}, 50 Z4 noises, GMRES-DR
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 DFMA / clock / SM at the 2070 MHz maximum clock
 WILSON_FLOPS = 1368        # per site per right-hand side (1320 for P, 48 for 1 - kappa P)
 L2_FLUSH_BYTES = 512 << 20
+MULTIDOT_DRAM_RATIO = 1.011  # ncu: (318.4 + 397.0) MB DRAM over (314.6 + 393.2) MB compulsory, two launches
 M_INNER_MIXED = 40         # GMRES cycle length of the reduced-precision inner solves
 
 
@@ -530,6 +531,7 @@ def main():
     barrier()
     t_dev = ev0.elapsed_time(ev1) / 1000.0
     tm = ctx.timing_read()
+    tbytes = ctx.timing_bytes()
     ctx.timing(False)
     launches = ctx.launches - launches0
     clk = clocks.stop()
@@ -618,6 +620,14 @@ def main():
                 "breakdown_ms": {k: round(v[0], 1) for k, v in tm.items()},
                 "class_tflops": {k: round(v[2] * flops_per_unit[k] / (v[0] / 1000.0) / 1e12, 4)
                                  for k, v in tm.items() if flops_per_unit.get(k) and v[0] > 0}}
+    if dom == "dot" and tbytes.get("dot", 0) > 0:
+        # DRAM bytes per launch: the class's compulsory bytes per launch (recorded by the library
+        # for every timed launch) times the DRAM / compulsory ratio that ncu measured on launches of
+        # the same kernel (GMRES cycle of this workload, profiles/multidot_fp64_8x8x8x16_50rhs.md)
+        roofline["traffic"] = MULTIDOT_DRAM_RATIO * tbytes["dot"] / max(nl, 1)
+        roofline["traffic_source"] = ("compulsory bytes per launch x %.3f (ncu dram__bytes_read+write over "
+                                      "compulsory bytes, multidot on 8^3x16, 50 rhs)" % MULTIDOT_DRAM_RATIO)
+        roofline["compulsory_gbs"] = tbytes["dot"] / (ms / 1000.0) / 1e9
     w = tm["wilson"]
     if w[0] > 0:
         roofline["wilson_fp64_tflops"] = w[2] * WILSON_FLOPS / (w[0] / 1000.0) / 1e12

@@ -129,6 +129,10 @@ long lqcd_kernel_launches(const lqcd_ctx *ctx);
 lqcd_status lqcd_timing_enable(lqcd_ctx *ctx, int enable);
 lqcd_status lqcd_timing_reset(lqcd_ctx *ctx);
 lqcd_status lqcd_timing_read(lqcd_ctx *ctx, int cls, double *total_ms, long *launches, double *units);
+/* Compulsory device-memory bytes (every operand element read or written once) summed over the
+ * timed launches of one class since the last reset, for the classes whose launches record them
+ * (DOT; 0 for the others).  Synchronises the stream like lqcd_timing_read. */
+lqcd_status lqcd_timing_bytes(lqcd_ctx *ctx, int cls, double *bytes);
 
 /* ---- Z(4) noise (Sec. 2, 3) ------------------------------------------------------- */
 

@@ -471,7 +471,10 @@ lqcd_status blas_multidot(lqcd_ctx *ctx, const SV *V, long long vstride, long lo
   kbegin(ctx);
   multidot_kernel<SV, SW><<<dim3(nchunk * ngroup, nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs,
                                                                                 nchunk, fac, (double2 *)p, cnt, h);
-  return launch_check(ctx, "multidot_kernel", K_DOT, (double)n * nrhs * nvec);
+  // compulsory bytes: every basis vector once (once per right-hand side when the bases differ),
+  // every w once
+  const double bytes = (double)sizeof(SV) * n * nvec * (vrs != 0 ? nrhs : 1) + (double)sizeof(SW) * n * nrhs;
+  return launch_check_bytes(ctx, "multidot_kernel", K_DOT, (double)n * nrhs * nvec, bytes);
 }
 
 template <typename SV, typename SW>

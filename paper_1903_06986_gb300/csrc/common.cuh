@@ -20,6 +20,7 @@ enum KClass { K_WILSON = 0, K_DOT, K_AXPY, K_COMBINE, K_NORM, K_CONTRACT, K_BLAS
 struct TimedLaunch {
   int start, end, cls;  // indices into lqcd_ctx::ev_pool
   double units;         // work units of the launch (see lqcd_timing_read)
+  double bytes;         // compulsory device-memory bytes of the launch (0 where not tracked)
 };
 
 struct lqcd_ctx {
@@ -46,6 +47,7 @@ struct lqcd_ctx {
   double t_ms[K_NCLASS];
   long t_count[K_NCLASS];
   double t_units[K_NCLASS];
+  double t_bytes[K_NCLASS];
   // CUDA graphs of fixed launch sequences (the Arnoldi steps of a Krylov cycle), keyed by every
   // pointer and parameter they bake in; dropped whenever a workspace buffer is reallocated
   bool graphs;
@@ -96,6 +98,8 @@ lqcd_status set_err(lqcd_ctx *ctx, lqcd_status st, const char *fmt, ...);
 void kbegin(lqcd_ctx *ctx);
 // check the launch that was just enqueued, count it, and record its end event when timing
 lqcd_status launch_check(lqcd_ctx *ctx, const char *what, int cls, double units);
+// the same, also recording the launch's compulsory bytes (each operand element read or written once)
+lqcd_status launch_check_bytes(lqcd_ctx *ctx, const char *what, int cls, double units, double bytes);
 
 // growable workspace slot (device memory owned by the context)
 enum WsSlot {

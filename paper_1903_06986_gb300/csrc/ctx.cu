@@ -38,13 +38,17 @@ void kbegin(lqcd_ctx *ctx) {
 }
 
 lqcd_status launch_check(lqcd_ctx *ctx, const char *what, int cls, double units) {
+  return launch_check_bytes(ctx, what, cls, units, 0.0);
+}
+
+lqcd_status launch_check_bytes(lqcd_ctx *ctx, const char *what, int cls, double units, double bytes) {
   ctx->launches++;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_err(ctx, LQCD_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
   if (ctx->timing && ctx->pending_start >= 0) {
     const int j = next_event(ctx);
     if (j >= 0 && cudaEventRecord(ctx->ev_pool[j], ctx->stream) == cudaSuccess)
-      ctx->timed.push_back(TimedLaunch{ctx->pending_start, j, cls, units});
+      ctx->timed.push_back(TimedLaunch{ctx->pending_start, j, cls, units, bytes});
     ctx->pending_start = -1;
     if (ctx->timed.size() >= 16384) return timing_collect(ctx);  // bound the event pool
   }
@@ -64,6 +68,7 @@ static lqcd_status timing_collect(lqcd_ctx *ctx) {
     ctx->t_ms[t.cls] += ms;
     ctx->t_count[t.cls] += 1;
     ctx->t_units[t.cls] += t.units;
+    ctx->t_bytes[t.cls] += t.bytes;
   }
   ctx->timed.clear();
   ctx->ev_used = 0;
@@ -206,6 +211,7 @@ lqcd_status lqcd_ctx_create(lqcd_ctx **out, const int dims[4], int link_recon, v
     c->t_ms[k] = 0.0;
     c->t_count[k] = 0;
     c->t_units[k] = 0.0;
+    c->t_bytes[k] = 0.0;
   }
   c->graphs = true;
   c->packed_nr = 0;
@@ -268,6 +274,7 @@ lqcd_status lqcd_timing_reset(lqcd_ctx *ctx) {
     ctx->t_ms[k] = 0.0;
     ctx->t_count[k] = 0;
     ctx->t_units[k] = 0.0;
+    ctx->t_bytes[k] = 0.0;
   }
   return LQCD_OK;
 }
@@ -279,6 +286,14 @@ lqcd_status lqcd_timing_read(lqcd_ctx *ctx, int cls, double *total_ms, long *lau
   *total_ms = ctx->t_ms[cls];
   *launches = ctx->t_count[cls];
   if (units) *units = ctx->t_units[cls];
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_timing_bytes(lqcd_ctx *ctx, int cls, double *bytes) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (cls < 0 || cls >= K_NCLASS || !bytes) return set_err(ctx, LQCD_ERR_INVALID_ARG, "timing_bytes: bad class");
+  LQCD_TRY(timing_collect(ctx));
+  *bytes = ctx->t_bytes[cls];
   return LQCD_OK;
 }
 

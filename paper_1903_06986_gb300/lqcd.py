@@ -144,6 +144,8 @@ def load(path=None):
     lib.lqcd_timing_reset.restype = C.c_int
     lib.lqcd_timing_read.argtypes = [vp, i, C.POINTER(C.c_double), C.POINTER(C.c_long), C.POINTER(C.c_double)]
     lib.lqcd_timing_read.restype = C.c_int
+    lib.lqcd_timing_bytes.argtypes = [vp, i, C.POINTER(C.c_double)]
+    lib.lqcd_timing_bytes.restype = C.c_int
     _LIB = lib
     return lib
 
@@ -261,6 +263,15 @@ class Context:
             ms, n, u = C.c_double(), C.c_long(), C.c_double()
             self._check(self.lib.lqcd_timing_read(self.h, i, C.byref(ms), C.byref(n), C.byref(u)))
             out[name] = (ms.value, n.value, u.value)
+        return out
+
+    def timing_bytes(self):
+        """{class: compulsory device-memory bytes of the timed launches} since the last reset."""
+        out = {}
+        for i, name in enumerate(KERNEL_CLASSES):
+            v = C.c_double()
+            self._check(self.lib.lqcd_timing_bytes(self.h, i, C.byref(v)))
+            out[name] = v.value
         return out
 
     def set_stream(self, stream):
