@@ -832,6 +832,8 @@ int tc_kcr(int SB, double dB) {
   return (int)std::max(1.0, std::min(kc, 1e6));
 }
 
+lqcd_status tc_slices_fill(lqcd_ctx *ctx, const double2 *E, TcSlices *S, size_t bg, size_t bc);
+
 lqcd_status check_flag(lqcd_ctx *ctx, int *flag_dev, const char *what) {
   int f = 0;
   LQCD_CUDA(ctx, cudaMemcpyAsync(&f, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -871,7 +873,20 @@ lqcd_status tc_slices_make(lqcd_ctx *ctx, const double2 *E, int k, void **out) {
   S->maxbits = (unsigned long long *)(S->eexp + k + (k & 1));
   S->minlsb = (int *)(S->maxbits + k);
   S->flag = S->minlsb + k;
+  // the object is handed out only once every slice is written: a failure (non-finite input, CUDA
+  // error) releases it, so a deflation object never keeps half-built slices
+  const lqcd_status st = tc_slices_fill(ctx, E, S, bg, bc);
+  if (st != LQCD_OK) {
+    tc_slices_free(S);  // cudaFree waits for the kernels still using the buffers
+    return st;
+  }
   *out = S;
+  return LQCD_OK;
+}
+
+namespace {
+lqcd_status tc_slices_fill(lqcd_ctx *ctx, const double2 *E, TcSlices *S, size_t bg, size_t bc) {
+  const int k = S->k;
   LQCD_CUDA(ctx, cudaMemsetAsync(S->Ag, 0, bg, ctx->stream));
   LQCD_CUDA(ctx, cudaMemsetAsync(S->Ac, 0, bc, ctx->stream));
   kbegin(ctx);
@@ -895,6 +910,7 @@ lqcd_status tc_slices_make(lqcd_ctx *ctx, const double2 *E, int k, void **out) {
       (const double *)E, k, S->L, S->rowexp, S->kcc, (unsigned short *)S->Ac);
   return launch_check(ctx, "slice_ac_kernel", K_SLICE, (double)k * S->L);
 }
+}  // namespace
 
 void tc_slices_free(void *p) {
   TcSlices *S = (TcSlices *)p;
