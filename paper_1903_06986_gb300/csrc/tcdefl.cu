@@ -494,7 +494,7 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 // ---------------------------------------------------------------------------------------------
 
 struct TcArgs {
-  const unsigned char *A;  // row-scaled operand, pre-tiled (see slice_e_kernel)
+  const unsigned char *A;  // row-scaled operand, pre-tiled (see slice_ag_kernel, slice_ac_kernel)
   const unsigned char *B;  // column operand, pre-tiled [chunk][slice][NP x 32]
   int mt_count;            // row tiles
   int m_valid;             // valid rows (rows >= m_valid are neither loaded from HBM nor written)
