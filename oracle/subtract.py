@@ -4,6 +4,7 @@ Test infrastructure (see ``oracle/__init__.py``).
 
   PS      tilde x = sum_{k=0}^{K-1} (kappa P)^k eta            (Sec. 5.1; "seventh order" = K = 7 terms)
   POLY    tilde x = sum_{j=0}^{n} a_j M^j eta, a from the Min-Res projection (Sec. 5.2)
+  ES      tilde x = V_R Lambda^{-1} V_L^dag eta                  (Sec. 5.3; left vectors from gamma_5-hermiticity)
   HFES    tilde x = gamma_5 V' Lambda'^{-1} V'^dag eta          (Sec. 5.4)
   HFPS /  tilde x = tilde x_{pert|poly} + gamma_5 V' (Lambda'^{-1} - Xi^{-1}) V'^dag eta,
   HFPOLY  1/xi'_q = e'_q^dag gamma_5 tilde M^{-1}_{pert|poly} e'_q (Sec. 5.5, reading of tilde M'^{-1} = gamma_5 tilde M^{-1})
@@ -154,6 +155,48 @@ def defl_addback(U, kappa, E, dvals, dims):
     for q in range(E.shape[1]):
         e = L.unflat(E[:, q], dims)
         out += dvals[q] * O.densities(U, kappa, e, L.g5(e))
+    return out
+
+
+def es_left_vectors(ER, lam, dims, rel_tol=1e-8):
+    """Left eigenvectors for ES (Sec. 5.3) from right eigenvectors of the gamma_5-hermitian M.
+
+    M^dag = gamma_5 M gamma_5 turns a right eigenvector of lambda* into a left eigenvector of
+    lambda: e_L(lambda_q) = gamma_5 e_R(lambda_p) / conj(e_R(lambda_p)^dag gamma_5 e_R(lambda_q)) with
+    lambda_p = conj(lambda_q), normalised so that e_L^dag e_R = 1.  ER: (N_dim, Q) right
+    eigenvectors, lam: (Q,) their eigenvalues.  Returns (EL, found): found[q] is False when no
+    computed eigenvalue lies within rel_tol |lambda_q| of conj(lambda_q) (such a mode has no left
+    vector among the Q and cannot be subtracted)."""
+    Q = ER.shape[1]
+    EL = np.zeros_like(ER)
+    found = np.zeros(Q, dtype=bool)
+    g5R = L.flat(L.g5(L.unflat(ER.T, dims))).T        # gamma_5 applied to every column
+    for q in range(Q):
+        dist = np.abs(lam - np.conj(lam[q]))
+        p = int(np.argmin(dist))
+        if dist[p] > rel_tol * max(abs(lam[q]), 1e-300):
+            continue
+        norm = np.vdot(g5R[:, p], ER[:, q])               # e_R(lambda_p)^dag gamma_5 e_R(lambda_q)
+        EL[:, q] = g5R[:, p] / np.conj(norm)
+        found[q] = True
+    return EL, found
+
+
+def es_vector(ER, EL, lam, eta):
+    """ES subtraction vector tilde x_eig = sum_q e_R^(q) (1/lambda_q) (e_L^(q)dag eta) (Sec. 5.3)."""
+    dims_shape = eta.shape[-6:]
+    ef = eta.reshape(eta.shape[:-6] + (-1,))
+    c = ef @ EL.conj()                      # (..., Q) = e_L^dag eta
+    y = (c / lam) @ ER.T
+    return y.reshape(eta.shape[:-6] + dims_shape)
+
+
+def es_addback(U, kappa, ER, EL, lam, dims):
+    """Densities of Tr(Theta tilde M^{-1}_eig) = sum_q (1/lambda_q) e_L^(q)dag Theta e_R^(q) (Sec. 5.3;
+    for Theta = 1 this is sum_q 1/lambda_q)."""
+    out = np.zeros((O.NOPS,) + L.site_shape(dims), dtype=np.complex128)
+    for q in range(ER.shape[1]):
+        out += O.densities(U, kappa, L.unflat(EL[:, q], dims), L.unflat(ER[:, q], dims)) / lam[q]
     return out
 
 

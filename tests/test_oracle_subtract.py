@@ -208,3 +208,75 @@ def test_defl_products_brute_force_and_orthonormality():
             assert abs(Y[j, i] - s) < 1e-12
     Qm, _ = np.linalg.qr(E)
     assert np.allclose(S.defl_coeffs(Qm, S.defl_expand(Qm, Cm)), Cm, atol=1e-13)
+
+
+def _full_eig_M(U, kappa):
+    M = L.dense(lambda v: L.wilson(U, kappa, v), DIMS)
+    lam, ER = np.linalg.eig(M)
+    order = np.argsort(np.abs(lam))
+    return M, lam[order], ER[:, order]
+
+
+def test_es_left_vectors_definition_and_biorthonormality():
+    """ES (Sec. 5.3): the left vectors built from gamma_5-hermiticity satisfy e_L^dag M = lambda
+    e_L^dag and e_L^(q)dag e_R^(q') = delta_qq' (checked against the dense matrix)."""
+    U = synth.su3_links(DIMS, 0.45, 36)
+    M, lam, ER = _full_eig_M(U, 0.15)
+    EL, found = S.es_left_vectors(ER, lam, DIMS)
+    assert found.all()
+    res = EL.conj().T @ M - lam[:, None] * EL.conj().T
+    assert np.abs(res).max() < 1e-9 * np.abs(M).max()
+    assert np.abs(EL.conj().T @ ER - np.eye(len(lam))).max() < 1e-8
+
+
+def test_complete_es_is_exact():
+    """With every eigenpair, tilde M^{-1}_eig is M^{-1}: the ES vector is the solution and the
+    add-backs are the exact traces (Sec. 5.3)."""
+    U = synth.su3_links(DIMS, 0.45, 37)
+    kappa = 0.15
+    M, lam, ER = _full_eig_M(U, kappa)
+    EL, _ = S.es_left_vectors(ER, lam, DIMS)
+    eta = rng.z4_noise(8, 0, DIMS)
+    x = L.unflat(np.linalg.solve(M, L.flat(eta)), DIMS)
+    assert np.allclose(S.es_vector(ER, EL, lam, eta), x, atol=1e-9)
+    tr = exact.exact_traces(U, kappa, DIMS)
+    add = S.es_addback(U, kappa, ER, EL, lam, DIMS).sum(axis=(-1, -2, -3, -4))
+    assert np.allclose(add, tr, atol=1e-8)
+
+
+def test_es_estimator_unbiased_with_exact_variance():
+    """ES with the smallest eigenpairs (closed under conjugation): Tr(tilde M^{-1}_eig) =
+    sum_q 1/lambda_q, add-backs equal the dense traces, and the estimator is unbiased for the LU
+    trace with the sample variance of Eq. xyz255."""
+    U = synth.su3_links(DIMS, 0.45, 35)
+    kappa = 0.12
+    M, lam, ER = _full_eig_M(U, kappa)
+    EL, _ = S.es_left_vectors(ER, lam, DIMS)
+    sel = set(range(8))
+    for q in list(sel):                            # add the conjugate partners
+        sel.add(int(np.argmin(np.abs(lam - np.conj(lam[q])))))
+    sel = sorted(sel)
+    ERs, ELs, ls = ER[:, sel], EL[:, sel], lam[sel]
+    tilde = ERs @ np.diag(1 / ls) @ ELs.conj().T
+    add = S.es_addback(U, kappa, ERs, ELs, ls, DIMS)
+    assert abs(add[0].sum() - np.sum(1 / ls)) < 1e-10 * abs(np.sum(1 / ls))
+    for op in range(O.NOPS):
+        Th = exact.dense_theta(U, kappa, op, DIMS)
+        ref = np.trace(Th @ tilde)
+        assert abs(add[op].sum() - ref) < 1e-10 * max(1.0, abs(ref)), op
+    Minv = np.linalg.inv(M)
+    N = 300
+    etas = rng.z4_block(78, 0, N, DIMS)
+    xs = np.stack([L.unflat(Minv @ L.flat(e), DIMS) for e in etas])
+    ws = xs - np.stack([S.es_vector(ERs, ELs, ls, e) for e in etas])
+    res = E.summarize(E.noise_terms(U, kappa, etas, ws), O.per_t(add))
+    exact_tr = exact.exact_traces(U, kappa, DIMS, Minv)
+    for op in range(O.NOPS):
+        Th = exact.dense_theta(U, kappa, op, DIMS)
+        _, vre, vim = exact.z4_variance(Th @ (Minv - tilde))
+        var = vre if O.OP_PART[op] == 0 else vim
+        sig = exact_tr[op].real if O.OP_PART[op] == 0 else exact_tr[op].imag
+        assert abs(res["signal"][op] - sig) <= 5 * np.sqrt(var / N) + 1e-10, op
+        svar = (res["stderr"][op] ** 2) * N
+        if var > 1e-20:
+            assert 0.6 < svar / var < 1.6, (op, svar, var)
