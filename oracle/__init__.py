@@ -15,7 +15,8 @@ Modules
   lattice   -- site indexing, gamma matrices, the Wilson hopping matrix P and M = 1 - kappa P (Eq. xyz556)
   rng       -- Philox-4x32-10 counter generator and Z(4) noise (Sec. 2)
   krylov    -- GMRES-DR, MINRES-DR (Hermitian form), GMRES-Proj deflated solves (Sec. 5.3, 7, 8)
-  subtract  -- PS / POLY / HFES / HFPS / HFPOLY subtraction vectors and trace add-backs (Sec. 5)
+  subtract  -- PS / POLY / ES / HFES / HFPS / HFPOLY subtraction vectors and trace add-backs (Sec. 5)
+  evenodd   -- even/odd reduced Wilson system, reconstruction, full eigenpairs from reduced ones (Sec. 7)
   operators -- the nine loop operators of Table Table903 and their per-site contractions (Sec. 6)
   estimate  -- noise estimators, error bars, relative efficiency (Sec. 5, 7)
   exact     -- dense-matrix exact traces and the exact Z(4) variance of Eq. xyz255 (Sec. 3)
