@@ -40,3 +40,13 @@ def test_version_and_argument_checks(lib):
     good = (ctypes.c_int * 4)(4, 4, 4, 4)
     assert lib.lqcd_ctx_create(ctypes.byref(h), good, 16, None) == lqcd.ERR_INVALID_ARG
     assert lib.lqcd_wilson_apply(None, None, 0.1, None, None, 1, 0, 0) == lqcd.ERR_INVALID_ARG
+
+
+def test_new_entry_points_reject_bad_arguments_without_cuda(lib):
+    # a NULL context is refused before any CUDA call (no GPU here)
+    assert lib.lqcd_set_defl_engine(None, lqcd.DEFL_TENSOR) == lqcd.ERR_INVALID_ARG
+    assert lib.lqcd_tc_vdag_x(None, None, 4, None, 1, None) == lqcd.ERR_INVALID_ARG
+    assert lib.lqcd_tc_v_c(None, None, 4, None, 1, None) == lqcd.ERR_INVALID_ARG
+    v = ctypes.c_double()
+    assert lib.lqcd_timing_bytes(None, 0, ctypes.byref(v)) == lqcd.ERR_INVALID_ARG
+    assert lqcd.KERNEL_CLASSES[9:] == ["tensor", "slice"]
