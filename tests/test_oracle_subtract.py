@@ -280,3 +280,26 @@ def test_es_estimator_unbiased_with_exact_variance():
         svar = (res["stderr"][op] ** 2) * N
         if var > 1e-20:
             assert 0.6 < svar / var < 1.6, (op, svar, var)
+
+
+def test_relative_efficiency_consistent_with_printed_table():
+    """Table 1550small prints each method's RE against NS and against PS.  With the oracle's RE
+    (used as a black box and inverted numerically) every method must imply the same error-bar
+    ratio err_PS / err_NS, up to the three printed digits; an additive form such as
+    (1 - dy^2) * 100 cannot even be inverted for the printed POLY entries."""
+    from scipy.optimize import brentq
+    import os
+    rows = [ln.split() for ln in open(os.path.join(os.path.dirname(__file__), "golden", "re_table_1550small.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 4
+
+    def dy_of(re_pct):          # error-bar ratio with E.relative_efficiency(dy, 1) = re_pct
+        return brentq(lambda d: E.relative_efficiency(d, 1.0) - re_pct, 1e-3, 10.0)
+
+    for op in range(3):
+        ratios = []
+        for r in rows:
+            vs_ns, vs_ps = float(r[1 + 2 * op]), float(r[2 + 2 * op])
+            ratios.append(dy_of(vs_ns) / dy_of(vs_ps))      # = err_PS / err_NS
+        ratios = np.array(ratios)
+        assert np.ptp(ratios) / ratios.mean() < 0.01, (op, ratios)
