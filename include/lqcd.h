@@ -273,6 +273,12 @@ lqcd_status lqcd_tc_vdag_x(lqcd_ctx *ctx, const double *E, int k, const double *
 /* Y_r = sum_q E_q C[q * nrhs + r] on the tensor cores (one-shot).  E as above; C: device,
  * k x nrhs complex128; Y: device output, nrhs fields (must not overlap E or C).  Errors as above. */
 lqcd_status lqcd_tc_v_c(lqcd_ctx *ctx, const double *E, int k, const double *C, int nrhs, double *Y);
+/* Device bytes the tensor-core slices of k vectors take on an Lx x Ly x Lz x Lt lattice (dims[0..3],
+ * each >= 2): the two slice copies kept per deflation object with LQCD_DEFL_TENSOR (and made for
+ * the duration of one lqcd_tc_vdag_x / lqcd_tc_v_c call), plus their per-row exponents.  Host
+ * only: needs no GPU and no context.  LQCD_ERR_INVALID_ARG for bad dims, k outside 1..4096 or a
+ * NULL bytes. */
+lqcd_status lqcd_tc_slice_bytes(const int dims[4], int k, size_t *bytes);
 
 /* ---- perturbative and polynomial series (Sec. 5.1, 5.2) ---------------------- */
 

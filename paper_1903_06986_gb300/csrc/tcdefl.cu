@@ -1041,6 +1041,19 @@ lqcd_status tc_vc(lqcd_ctx *ctx, const void *slices, const double2 *Cm, const do
   return LQCD_OK;
 }
 
+extern "C" lqcd_status lqcd_tc_slice_bytes(const int dims[4], int k, size_t *bytes) {
+  if (!dims || !bytes || k < 1 || k > 4096) return LQCD_ERR_INVALID_ARG;
+  long long V = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (dims[i] < 2) return LQCD_ERR_INVALID_ARG;
+    V *= dims[i];
+  }
+  const long long L = 24 * V;  // reals per field
+  *bytes = tc_bytes_g(k, L) + tc_bytes_c(k, L) + sizeof(int) * (size_t)L +
+           sizeof(int) * (k + 2) + sizeof(unsigned long long) * k + sizeof(int) * (k + 1);
+  return LQCD_OK;
+}
+
 extern "C" lqcd_status lqcd_set_defl_engine(lqcd_ctx *ctx, int engine) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
   if (engine != LQCD_DEFL_FP64 && engine != LQCD_DEFL_TENSOR)

@@ -111,6 +111,7 @@ def load(path=None):
         "lqcd_set_defl_engine": [vp, i],
         "lqcd_tc_vdag_x": [vp, vp, i, vp, i, vp],
         "lqcd_tc_v_c": [vp, vp, i, vp, i, vp],
+        "lqcd_tc_slice_bytes": [C.POINTER(C.c_int), i, C.POINTER(C.c_size_t)],
         "lqcd_hop_series": [vp, vp, d, vp, vp, i, i, vp],
         "lqcd_poly_apply": [vp, vp, d, vp, vp, i, i, vp],
         "lqcd_poly_coeffs": [vp, vp, d, u64, i, vp],
@@ -604,6 +605,17 @@ def loop_derivs(ctx, links, kappa, seed, nnoise, block, m, k, K, tol, tol_specia
         ctx._check(st)
     return dict(dkappa=dk, dkappa_err=err, per_noise=per, link_grad=g, grad_links=gl, matvecs=out.matvecs,
                 seconds=out.seconds, max_true_resid=out.max_true_resid, converged=bool(out.converged))
+
+
+def tc_slice_bytes(dims, k):
+    """Device bytes of the tensor-core slices of k vectors on a lattice of dims (Lx, Ly, Lz, Lt);
+    host only (no GPU needed)."""
+    lib = load()
+    out = C.c_size_t()
+    st = lib.lqcd_tc_slice_bytes((C.c_int * 4)(*dims), k, C.byref(out))
+    if st != OK:
+        raise LqcdError(st, "tc_slice_bytes: bad arguments")
+    return out.value
 
 
 def header_functions(header=None):

@@ -50,3 +50,19 @@ def test_new_entry_points_reject_bad_arguments_without_cuda(lib):
     v = ctypes.c_double()
     assert lib.lqcd_timing_bytes(None, 0, ctypes.byref(v)) == lqcd.ERR_INVALID_ARG
     assert lqcd.KERNEL_CLASSES[9:] == ["tensor", "slice"]
+
+
+def test_tc_slice_bytes_host_query(lib):
+    """Two slice copies of 7 bf16 (2 bytes) per real entry: at least 28 k L bytes, at most that
+    with k padded to a row tile (128) for one copy and to a chunk (32) for the other, L padded to
+    128, plus the exponent arrays."""
+    for dims, k in (((24, 24, 24, 32), 200), ((4, 4, 4, 4), 5), ((3, 5, 2, 7), 130)):
+        L = 24 * dims[0] * dims[1] * dims[2] * dims[3]
+        b = lqcd.tc_slice_bytes(dims, k)
+        pad = lambda x, m: -(-x // m) * m
+        assert 28 * k * L <= b <= 14 * pad(L, 128) * (pad(k, 128) + pad(k, 32)) + 4 * L + 32 * (k + 2)
+    assert lqcd.tc_slice_bytes((24, 24, 24, 32), 200) > 60e9     # the 24^3 x 32, 200-vector space
+    out = ctypes.c_size_t()
+    assert lib.lqcd_tc_slice_bytes((ctypes.c_int * 4)(4, 4, 1, 4), 5, ctypes.byref(out)) == lqcd.ERR_INVALID_ARG
+    assert lib.lqcd_tc_slice_bytes((ctypes.c_int * 4)(4, 4, 4, 4), 0, ctypes.byref(out)) == lqcd.ERR_INVALID_ARG
+    assert lib.lqcd_tc_slice_bytes((ctypes.c_int * 4)(4, 4, 4, 4), 5, None) == lqcd.ERR_INVALID_ARG
