@@ -276,8 +276,8 @@ lqcd_status lqcd_tc_v_c(lqcd_ctx *ctx, const double *E, int k, const double *C, 
 /* Device bytes the tensor-core slices of k vectors take on an Lx x Ly x Lz x Lt lattice (dims[0..3],
  * each >= 2): the two slice copies kept per deflation object with LQCD_DEFL_TENSOR (and made for
  * the duration of one lqcd_tc_vdag_x / lqcd_tc_v_c call), plus their per-row exponents.  Host
- * only: needs no GPU and no context.  LQCD_ERR_INVALID_ARG for bad dims, k outside 1..4096 or a
- * NULL bytes. */
+ * only: needs no GPU and no context.  LQCD_ERR_INVALID_ARG for bad dims (an extent outside 2..1024,
+ * or more than 2^28 sites, the limits of lqcd_ctx_create), k outside 1..4096 or a NULL bytes. */
 lqcd_status lqcd_tc_slice_bytes(const int dims[4], int k, size_t *bytes);
 
 /* ---- perturbative and polynomial series (Sec. 5.1, 5.2) ---------------------- */
@@ -334,8 +334,11 @@ lqcd_status lqcd_contract(lqcd_ctx *ctx, const double *links, double kappa, cons
  * cudaStream_t (NULL = legacy default stream).  Partial sums go to a fixed 1 MiB scratch array
  * compiled into the library, which every GPU that loads the library holds until the process exits;
  * it requires nrhs * Lt * 9 <= 65536 and returns LQCD_ERR_INVALID_ARG otherwise (or for bad
- * dims / NULL pointers; there is no context, hence no error string).  The first call on each device
- * looks up the scratch array's device address, so make it before any stream capture.  All calls
+ * dims: an extent outside 2..1024 or more than 2^28 sites, the limits of lqcd_ctx_create; or NULL
+ * pointers; there is no context, hence no error string).  The first call on each device looks up
+ * the scratch array's device address in the current CUDA context, so make it before any stream
+ * capture; a call in a new context of that device (after cudaDeviceReset, for instance) looks it up
+ * again, so make the first call after a reset before any capture too.  All calls
  * share the one array, which keeps the last call's contents (every entry read is written first by
  * the same call): calls that overlap on the GPU, from any stream or thread, race and must be
  * serialised by the caller.  Asynchronous on the stream; no other call of this library is made. */

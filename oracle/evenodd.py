@@ -84,12 +84,17 @@ def reconstruct(U, kappa, xe, b, dims):
     return join(xe, bo + kappa * hop_oe(U, xe, dims), dims)
 
 
-def full_eigenpairs(U, kappa, mu, Ve, dims):
+def full_eigenpairs(U, kappa, mu, Ve, dims, tol=1e-8):
     """Both full eigenpairs of M from each reduced pair (mu_q, v_e^(q)) of hat M (module docstring).
-    mu: (Q,); Ve: (Q, V/2, 4, 3).  Returns lam (2Q,) and unit right eigenvectors (2Q, T, Z, Y, X, 4, 3)."""
+    mu: (Q,); Ve: (Q, V/2, 4, 3).  Returns lam (2Q,) and unit right eigenvectors (2Q, T, Z, Y, X, 4, 3).
+    Raises ValueError for a mu with |sqrt(1 - mu)| <= tol (lambda = 1, where 1 - lambda vanishes)."""
     lams, vecs = [], []
     for q in range(len(mu)):
         r = np.sqrt(complex(1.0 - mu[q]))
+        if abs(r) <= tol:
+            # 1 - lambda = 0: the odd part kappa P_oe v_e / (1 - lambda) is undefined, so the full
+            # pair cannot be rebuilt from v_e alone
+            raise ValueError("reduced eigenvalue mu = %r is 1 to within %g: no full eigenpair" % (mu[q], tol))
         po = kappa * hop_oe(U, Ve[q], dims)
         for one_minus_lam in (r, -r):
             v = join(Ve[q], po / one_minus_lam, dims)

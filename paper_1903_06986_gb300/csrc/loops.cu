@@ -14,6 +14,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>  // driver types of the context-id query (entry points come from the runtime)
+
 #include "common.cuh"
 #include "dense.h"
 #include "spin.cuh"
@@ -932,32 +934,69 @@ constexpr int NOALLOC_SCRATCH_ENTRIES = 1 << 16;  // double2 entries: 1 MiB
 static __device__ __align__(256) double2 g_noalloc_scratch[NOALLOC_SCRATCH_ENTRIES];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
-double2 *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
-int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
+struct NoallocSlot {
+  double2 *ptr;            // device address of g_noalloc_scratch in the context below
+  unsigned long long ctx;  // id of the CUDA context it was looked up in (0: none yet)
+  int sms;
+};
+NoallocSlot g_noalloc[NOALLOC_MAX_DEVICES] = {};
 std::mutex g_noalloc_mutex;
 
-// Device address of the scratch array for the current device, looked up once per device.  A host
-// reference to g_noalloc_scratch names a host-side stand-in, not device memory, so the address
-// must come from cudaGetSymbolAddress with the device current.
+// Id of the calling thread's current CUDA context (0 when none is current yet), through the driver
+// entry points the runtime hands out (no link against the driver library).  Context ids are never
+// reused within a process, so a replaced context (cudaDeviceReset, which also reloads this
+// library's device module and moves the scratch array) never matches a stale cache entry.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+lqcd_status current_ctx_id(unsigned long long *id) {
+  static PfnCtxGetCurrent get_cur = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  if (!get_cur || !get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void **)&get_cur, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", (void **)&get_id, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !get_cur || !get_id) {
+      cudaGetLastError();
+      get_cur = nullptr;
+      get_id = nullptr;
+      return LQCD_ERR_CUDA;
+    }
+  }
+  CUcontext c = nullptr;
+  if (get_cur(&c) != CUDA_SUCCESS) return LQCD_ERR_CUDA;
+  *id = 0;
+  if (c && get_id(c, id) != CUDA_SUCCESS) return LQCD_ERR_CUDA;
+  return LQCD_OK;
+}
+
+// Device address of the scratch array in the current context of device dev, looked up once per
+// device and context.  A host reference to g_noalloc_scratch names a host-side stand-in, not
+// device memory, so the address must come from cudaGetSymbolAddress with the device current.
 lqcd_status noalloc_setup(int dev, double2 **ptr, int *sms) {
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return LQCD_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void *p = nullptr;
+  unsigned long long id = 0;
+  LQCD_TRY(current_ctx_id(&id));
+  NoallocSlot &slot = g_noalloc[dev];
+  if (!slot.ptr || id == 0 || slot.ctx != id) {
+    void *p = nullptr;  // the lookup also makes the device's primary context current if none is
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return LQCD_ERR_CUDA;
     }
+    LQCD_TRY(current_ctx_id(&id));
     int n = 0;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
       cudaGetLastError();
       return LQCD_ERR_CUDA;
     }
-    g_noalloc_sms[dev] = n;
-    g_noalloc_ptr[dev] = (double2 *)p;
+    slot.ptr = (double2 *)p;
+    slot.ctx = id;
+    slot.sms = n;
   }
-  *ptr = g_noalloc_ptr[dev];
-  *sms = g_noalloc_sms[dev];
+  *ptr = slot.ptr;
+  *sms = slot.sms;
   return LQCD_OK;
 }
 
@@ -966,8 +1005,13 @@ lqcd_status noalloc_setup(int dev, double2 **ptr, int *sms) {
 extern "C" lqcd_status lqcd_contract_noalloc(const int dims[4], const double *links, double kappa, const double *eta,
                                              const double *w, int nrhs, double *out, void *stream) {
   if (!dims || !links || !eta || !w || !out || nrhs < 1 || nrhs > 65535) return LQCD_ERR_INVALID_ARG;
-  for (int i = 0; i < 4; ++i)
+  long long V = 1;
+  for (int i = 0; i < 4; ++i) {
     if (dims[i] < 2 || dims[i] > 1024) return LQCD_ERR_INVALID_ARG;
+    V *= dims[i];
+  }
+  // the context limit: site indices (and 12 V-strided offsets per right-hand side) stay in range
+  if (V > (1LL << 28)) return LQCD_ERR_INVALID_ARG;
   const int Lt = dims[3], Vs = dims[0] * dims[1] * dims[2];
   // every (rhs, timeslice, chunk) writes its nine partial sums: at least one chunk must fit
   const long long per_chunk = (long long)nrhs * Lt * 9;

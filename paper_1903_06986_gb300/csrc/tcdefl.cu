@@ -1045,8 +1045,10 @@ extern "C" lqcd_status lqcd_tc_slice_bytes(const int dims[4], int k, size_t *byt
   if (!dims || !bytes || k < 1 || k > 4096) return LQCD_ERR_INVALID_ARG;
   long long V = 1;
   for (int i = 0; i < 4; ++i) {
-    if (dims[i] < 2) return LQCD_ERR_INVALID_ARG;
+    // the same limits as a context: extents 2..1024 and at most 2^28 sites, so no product overflows
+    if (dims[i] < 2 || dims[i] > 1024) return LQCD_ERR_INVALID_ARG;
     V *= dims[i];
+    if (V > (1LL << 28)) return LQCD_ERR_INVALID_ARG;
   }
   const long long L = 24 * V;  // reals per field
   *bytes = tc_bytes_g(k, L) + tc_bytes_c(k, L) + sizeof(int) * (size_t)L +

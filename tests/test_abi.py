@@ -66,3 +66,8 @@ def test_tc_slice_bytes_host_query(lib):
     assert lib.lqcd_tc_slice_bytes((ctypes.c_int * 4)(4, 4, 1, 4), 5, ctypes.byref(out)) == lqcd.ERR_INVALID_ARG
     assert lib.lqcd_tc_slice_bytes((ctypes.c_int * 4)(4, 4, 4, 4), 0, ctypes.byref(out)) == lqcd.ERR_INVALID_ARG
     assert lib.lqcd_tc_slice_bytes((ctypes.c_int * 4)(4, 4, 4, 4), 5, None) == lqcd.ERR_INVALID_ARG
+    # beyond the context limits (extent > 1024; more than 2^28 sites): rejected, no overflowed size
+    assert lib.lqcd_tc_slice_bytes((ctypes.c_int * 4)(4, 4, 4, 2048), 5, ctypes.byref(out)) == lqcd.ERR_INVALID_ARG
+    assert lib.lqcd_tc_slice_bytes((ctypes.c_int * 4)(1024, 1024, 1024, 1024), 200,
+                                   ctypes.byref(out)) == lqcd.ERR_INVALID_ARG
+    assert lib.lqcd_tc_slice_bytes((ctypes.c_int * 4)(256, 256, 64, 128), 1, ctypes.byref(out)) == lqcd.ERR_INVALID_ARG

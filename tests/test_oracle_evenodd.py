@@ -89,3 +89,17 @@ def test_full_eigenpairs_from_reduced_ones():
     assert len(sel) == 20
     res = EL[:, sel].conj().T @ M - lam[order][sel, None] * EL[:, sel].conj().T
     assert np.abs(res).max() < 1e-9 * np.abs(M).max()
+
+
+def test_full_eigenpairs_reject_reduced_eigenvalue_one():
+    """mu = 1 means 1 - lambda = 0: the odd part kappa P_oe v_e / (1 - lambda) does not exist, so the
+    oracle refuses instead of returning non-finite vectors (and accepts mu just away from 1)."""
+    U = synth.su3_links(DIMS, 0.45, 55)
+    ve = np.zeros((1, 12 * L.volume(DIMS) // 2 // 12, 4, 3), dtype=np.complex128)
+    ve[0, 0, 0, 0] = 1.0
+    with pytest.raises(ValueError):
+        EO.full_eigenpairs(U, 0.15, np.array([1.0 + 0j]), ve, DIMS)
+    with pytest.raises(ValueError):
+        EO.full_eigenpairs(U, 0.15, np.array([1.0 + 1e-18j]), ve, DIMS)
+    lam, vecs = EO.full_eigenpairs(U, 0.15, np.array([1.0 - 1e-6 + 0j]), ve, DIMS)
+    assert np.all(np.isfinite(vecs)) and np.all(np.isfinite(lam))

@@ -68,3 +68,9 @@ def test_noalloc_rejects_oversize_without_launching():
     rc = f(dd, ctypes.c_void_p(U.data_ptr()), 0.1, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(v.data_ptr()),
            1000, ctypes.c_void_p(v.data_ptr()), None)
     assert rc == 1
+    # more sites than a context accepts (2^29 > 2^28): rejected before any launch
+    big = (ctypes.c_int * 4)(1024, 1024, 512, 2)
+    rc = f(big, ctypes.c_void_p(U.data_ptr()), 0.1, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+           1, ctypes.c_void_p(v.data_ptr()), None)
+    assert rc == 1
+    torch.cuda.synchronize()
