@@ -14,8 +14,15 @@ steps below are Morgan's published GMRES-DR cycle, in the paper's notation where
   3. d = argmin || c - Hbar_m d ||;  x += V_m d;  s = c - Hbar_m d (the residual in V_{m+1}).
   4. Harmonic Ritz pairs of H_m:  (H_m + |h_{m+1,m}|^2 H_m^{-H} e_m e_m^T) g = theta g;  keep the k
      with smallest |theta|.
-  5. P_{k+1} = orthonormal basis of [g_1 .. g_k (padded with a zero row), s].
+  5. P_{k+1} = orthonormal basis of [g_1 .. g_k (padded with a zero row), w], w spanning the
+     orthogonal complement of range(Hbar_m) (reading: s is orthogonal to range(Hbar_m), so in exact
+     arithmetic it is parallel to w = [-conj(h_{m+1,m}) H_m^{-H} e_m; 1]; every harmonic Ritz
+     residual Hbar_m g - theta [g; 0] is parallel to w too, which is what makes step 6 exact.  Once
+     the system has converged, s is rounding noise and its direction is not w's, so w is used).
   6. V_{k+1} <- V_{m+1} P_{k+1};  Hbar_k <- P_{k+1}^H Hbar_m P_k;  c <- P_{k+1}^H s;  go to 2 with j0 = k.
+  The cycles stop when the residual is below tol and, if eig_tol is given, every Rayleigh-Ritz
+  residual of the deflation space (below) is below eig_tol as well: the "super-convergence" of the
+  first right-hand side, solved far below its tolerance so that the eigenvectors converge (Sec. 5.4, 7).
 
 Hermitian form (reading; the paper cites MINRES-DR without restating it): the same cycle on a
 Hermitian A, with step 4 solved as the Hermitian-definite generalised problem
@@ -71,26 +78,38 @@ def harmonic_ritz(Hbar, k, hermitian=False):
     return theta[order], G[:, order]
 
 
-def _restart_basis(G, s):
-    """Step 5: orthonormal P_{k+1} from the k harmonic Ritz coordinate vectors and the residual s."""
-    m1 = s.shape[0]
+def lsq_complement(Hbar):
+    """Unit vector w spanning the orthogonal complement of range(Hbar) for an (m+1) x m Hbar with
+    nonsingular H_m: Hbar^H w = 0 gives w = [-conj(h_{m+1,m}) H_m^{-H} e_m; 1], normalised."""
+    m = Hbar.shape[1]
+    em = np.zeros(m, dtype=np.complex128)
+    em[-1] = 1.0
+    f = np.linalg.solve(Hbar[:m, :m].conj().T, em)
+    w = np.concatenate([-np.conj(Hbar[m, m - 1]) * f, [1.0 + 0j]])
+    return w / np.linalg.norm(w)
+
+
+def _restart_basis(G, w):
+    """Step 5: orthonormal P_{k+1} from the k harmonic Ritz coordinate vectors and the vector w."""
+    m1 = w.shape[0]
     k = G.shape[1]
     Gp = np.zeros((m1, k), dtype=np.complex128)
     Gp[:m1 - 1, :] = G
     Q, _ = np.linalg.qr(Gp)
-    t = s - Q @ (Q.conj().T @ s)
+    t = w - Q @ (Q.conj().T @ w)
     t = t - Q @ (Q.conj().T @ t)
     t = t / np.linalg.norm(t)
     return np.concatenate([Q, t[:, None]], axis=1)
 
 
-def gmres_dr(A, b, m, k, tol, max_cycles, x0=None, hermitian=False):
+def gmres_dr(A, b, m, k, tol, max_cycles, x0=None, hermitian=False, eig_tol=None):
     """GMRES-DR(m, k) (MINRES-DR form when hermitian=True) for A x = b.
 
     Returns (x, info, defl) where defl = dict(V=V_{k+1}, Hbar=Hbar_k, theta=harmonic Ritz values)
     is the deflation space of the final cycle (A V_k = V_{k+1} Hbar_k), used by GMRES-Proj and
     by `ritz_pairs`.  info: cycles, matvecs, resid (per-cycle recursive relative residual norms),
-    true_resid (relative), converged.
+    eig_resid (largest Rayleigh-Ritz residual of the final space), true_resid (relative),
+    converged (residual below tol, and the eigen residuals below eig_tol when it is given).
     """
     n = b.shape[0]
     x = np.zeros(n, dtype=np.complex128) if x0 is None else x0.astype(np.complex128).copy()
@@ -119,11 +138,12 @@ def gmres_dr(A, b, m, k, tol, max_cycles, x0=None, hermitian=False):
         rel = np.linalg.norm(s) / bnorm
         hist.append(rel)
         theta, G = harmonic_ritz(H, k, hermitian)
-        P = _restart_basis(G, s)
+        P = _restart_basis(G, lsq_complement(H))
         Vn = V @ P
         Hn = P.conj().T @ H @ P[:m, :k]
         defl = dict(V=Vn.copy(), Hbar=Hn.copy(), theta=theta.copy())
-        if rel <= tol:
+        eres = ritz_pairs(defl, hermitian)[2].max() if k > 0 else 0.0
+        if rel <= tol and (eig_tol is None or eres <= eig_tol):
             converged = True
             break
         V[:, :k + 1] = Vn
@@ -135,7 +155,8 @@ def gmres_dr(A, b, m, k, tol, max_cycles, x0=None, hermitian=False):
         j0 = k
     true = np.linalg.norm(b - A(x)) / bnorm
     counter[0] += 1
-    info = dict(cycles=cycles, matvecs=counter[0], resid=hist, true_resid=true, converged=converged)
+    info = dict(cycles=cycles, matvecs=counter[0], resid=hist, eig_resid=eres, true_resid=true,
+                converged=converged)
     return x, info, defl
 
 
