@@ -80,6 +80,10 @@ typedef struct {
   int prec;          /* lqcd_prec of the inner operator; LQCD_PREC_F64 for the plain path    */
   double inner_tol;  /* mixed precision: relative residual of each inner solve (0 = default:
                         5e-6 F32, 2e-2 F16, 5e-2 BF16)                                        */
+  double eig_tol;    /* GMRES-DR / MINRES-DR: with eig_tol > 0 the cycles also continue until
+                        every Rayleigh-Ritz residual ||A e - lambda e|| of the restart space is
+                        <= eig_tol ("super-convergence" of the first right-hand side, which
+                        converges the eigenvectors, Sec. 5.4, 7); 0 = residual criterion only */
 } lqcd_krylov_opts;
 
 typedef struct {
@@ -240,6 +244,14 @@ lqcd_status lqcd_defl_export(const lqcd_defl *defl, double *V, double *Hbar, dou
  * lqcd_deflate_project / lqcd_xi_inverse / lqcd_loop_estimate subtraction (no projection data). */
 lqcd_status lqcd_defl_import(lqcd_ctx *ctx, int k, const double *E, const double *lam,
                              lqcd_defl **defl_out);
+/* Build a full deflation space from caller data (a checkpointed solver space, or one made
+ * elsewhere): V (device, (k+1) x 12V, vector-major, orthonormal) and Hbar (host, (k+1) x k complex
+ * row-major) with A V_k = V_{k+1} Hbar_k for A = M (hermitian = 0) or M' = M gamma_5 (hermitian = 1).
+ * The Rayleigh-Ritz eigenpairs are computed as for a solver-made space, so the object serves
+ * lqcd_proj_solve, lqcd_deflate_project and lqcd_loop_setup_from alike.  The data are copied.
+ * LQCD_ERR_NONFINITE for a NaN / Inf in Hbar, LQCD_ERR_OOM if the copies do not fit. */
+lqcd_status lqcd_defl_import_space(lqcd_ctx *ctx, int k, const double *V, const double *Hbar, int hermitian,
+                                   lqcd_defl **defl_out);
 
 /* ---- deflation projection (HFES, Sec. 5.4) ----------------------------------------- */
 
@@ -364,6 +376,13 @@ typedef struct {
                          noise solves; special solves, series, projections and contractions
                          stay FP64)                                                         */
   double inner_tol;   /* mixed precision: inner relative residual (0 = default, see above)   */
+  double eig_tol;     /* special solves: also stop only when the Rayleigh-Ritz residuals of
+                         both deflation spaces are <= eig_tol (0 = off; see lqcd_krylov_opts)  */
+  int system;         /* LQCD_SYS_M (0): GMRES-DR on M for the noise solves' GMRES-Proj space
+                         and MINRES-DR on M' for the HFES eigenpairs; LQCD_SYS_MG5: the Hermitian
+                         path, one MINRES-DR on M' for both, every noise solved as
+                         M' y = eta by GMRES-Proj over that space and x = gamma_5 y (for fields
+                         whose spectrum of M surrounds the origin, where GMRES on M stagnates) */
 } lqcd_est_opts;
 
 typedef struct {
@@ -383,9 +402,61 @@ typedef struct {
   int block;          /* right-hand-side block width used (the autotuner's pick when opts->block == 0) */
 } lqcd_estimate;
 
-/* Tr(Theta M^{-1}) for the nine operators and the requested subtraction modes (Sec. 5-7). */
+/* Tr(Theta M^{-1}) for the nine operators and the requested subtraction modes (Sec. 5-7): the
+ * setup below, then the noise phase over noises 0 .. nnoise-1, then the summary (mean, error bar). */
 lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, double kappa,
                                const lqcd_est_opts *opts, lqcd_estimate *out);
+
+/* ---- the same in two phases: per-configuration setup, then batches of noises ---------------------- */
+
+/* The setup of one gauge configuration (Sec. 5-7, done once and amortised over the noises): the
+ * special right-hand side (Z(4) noise 2^32-2) solved by GMRES-DR(m, k) on M (the GMRES-Proj space of
+ * the noise solves) and MINRES-DR(m, k) on M' (the Q = k eigenpairs of HFES), the Min-Res
+ * coefficients, the hopping traces t_k, 1/xi' for HFPS and HFPOLY, and every add-back.  A setup is
+ * also the natural checkpoint: with the counter-based noise, noises can be run in any batches and
+ * in any order, on this setup or on one rebuilt with lqcd_loop_setup_from. */
+typedef struct lqcd_loop lqcd_loop;
+typedef struct {
+  /* host arrays supplied by the caller (any may be NULL):                                   */
+  double *addback;    /* [6][9][Lt] complex: Tr(Theta tilde M^{-1}) per timeslice            */
+  double *lam;        /* [Q] complex: eigenvalues lambda'_q of M' used for deflation          */
+  double *poly_a;     /* [npoly+1] complex: Min-Res coefficients                              */
+  double *xi_pert;    /* [Q] complex: 1/xi'_q = e'_q^dag gamma_5 tilde M^{-1}_pert e'_q       */
+  double *xi_poly;    /* [Q] complex: the same with the POLY polynomial                      */
+  /* filled by the library:                                                                  */
+  int Q;              /* deflation eigenpairs                                                 */
+  int block;          /* right-hand-side block width of the noise solves (autotuned if 0 was asked) */
+  long matvecs_setup;
+  double seconds_setup;
+  double eig_resid_max; /* largest ||M' e - lambda e|| of the deflation eigenpairs (0 if unknown) */
+} lqcd_loop_info;
+typedef struct {
+  long matvecs;        /* operator applications of the noise solves and series               */
+  double seconds;      /* wall time of the call                                              */
+  double max_true_resid;
+  int converged;
+  int block;
+} lqcd_noise_info;
+/* opts as lqcd_loop_estimate (nnoise only bounds the autotuner's candidates).  *out: free with
+ * lqcd_loop_destroy.  Returns LQCD_ERR_NOT_CONVERGED only when no deflation space could be made. */
+lqcd_status lqcd_loop_setup(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *opts,
+                            lqcd_loop **out);
+/* The same setup from given spaces instead of the special solves: proj, a Krylov space of M
+ * (solver-made or lqcd_defl_import_space) for GMRES-Proj; eig, eigenpairs of M' for HFES (any
+ * deflation object); a, host npoly+1 complex Min-Res coefficients, or NULL to compute them.  proj
+ * and eig are borrowed: they must outlive the setup. */
+lqcd_status lqcd_loop_setup_from(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *opts,
+                                 const lqcd_defl *proj, const lqcd_defl *eig, const double *a, lqcd_loop **out);
+/* Noise phase for Z(4) noises first .. first+count-1 of opts->seed (first + count <= 2^32-2):
+ * per_noise_t (host, [6][count][9][Lt] complex) receives eta^dag Theta (x - tilde x) summed per
+ * timeslice for the modes in opts->modes (zero for the others; add the add-back for the estimate).
+ * links: the same gauge field as the setup.  info may be NULL.  LQCD_ERR_NOT_CONVERGED (results
+ * still written) when a noise solve stopped at max_cycles above tol. */
+lqcd_status lqcd_loop_noises(lqcd_loop *loop, const double *links, uint32_t first, int count, double *per_noise_t,
+                             lqcd_noise_info *info);
+/* Outputs of a setup (host), see lqcd_loop_info. */
+lqcd_status lqcd_loop_get(const lqcd_loop *loop, lqcd_loop_info *out);
+lqcd_status lqcd_loop_destroy(lqcd_loop *loop);
 
 /* ---- batching -------------------------------------------------------------------------- */
 

@@ -5,6 +5,10 @@ Test infrastructure (see ``oracle/__init__.py``).
   1. special right-hand side b0 = Z(4) noise NOISE_SPECIAL:
        GMRES-DR(m, k) on M   -> deflation space (V_{k+1}, Hbar_k) for GMRES-Proj,
        MINRES-DR(m, k) on M' -> Q = k eigenpairs (lambda'_q, e'_q) of M' for HFES;
+     with system="MG5" (the Hermitian path) only the MINRES-DR solve runs, and its space also
+     serves the noise solves, done on M' y = eta with x = gamma_5 y (reading: the paper moves to
+     the Hermitian system and MINRES-DR at kappa_crit, Sec. 8; a field whose spectrum of M
+     surrounds the origin needs that for the noise solves too);
   2. Min-Res polynomial coefficients a from the noise NOISE_POLY (Sec. 5.2);
   3. hopping traces t_k by probing (Sec. 5.1); 1/xi'_q for HFPS and HFPOLY (Sec. 5.5);
   4. for every noise n: eta = Z(4) noise n, x = M^{-1} eta by GMRES-Proj, and for every mode the
@@ -23,12 +27,17 @@ from . import rng
 from . import subtract as S
 
 
-def setup(U, kappa, dims, seed, m, k, K, npoly, tol_special, max_cycles=2000):
+def setup(U, kappa, dims, seed, m, k, K, npoly, tol_special, max_cycles=2000, eig_tol=None, system="M"):
     A = lambda v: L.flat(L.wilson(U, kappa, L.unflat(v, dims)))
     Ap = lambda v: L.flat(L.wilson_g5(U, kappa, L.unflat(v, dims)))
     b0 = L.flat(rng.z4_noise(seed, rng.NOISE_SPECIAL, dims))
-    _, info_m, defl_m = Kr.gmres_dr(A, b0, m, k, tol_special, max_cycles)
-    _, info_h, defl_h = Kr.gmres_dr(Ap, b0, m, k, tol_special, max_cycles, hermitian=True)
+    if system == "M":
+        _, info_m, defl_m = Kr.gmres_dr(A, b0, m, k, tol_special, max_cycles, eig_tol=eig_tol)
+    elif system != "MG5":
+        raise ValueError(system)
+    _, info_h, defl_h = Kr.gmres_dr(Ap, b0, m, k, tol_special, max_cycles, hermitian=True, eig_tol=eig_tol)
+    if system == "MG5":
+        info_m, defl_m = info_h, defl_h
     lam, Ev, eres = Kr.ritz_pairs(defl_h, hermitian=True)
     Af = lambda f: L.wilson(U, kappa, f)
     a = S.poly_coeffs(Af, rng.z4_noise(seed, rng.NOISE_POLY, dims), npoly)
@@ -37,7 +46,7 @@ def setup(U, kappa, dims, seed, m, k, K, npoly, tol_special, max_cycles=2000):
     poly = lambda f: S.poly_apply(Af, a, f)
     xi_p = S.xi_inverse(Ev, pert, dims)
     xi_q = S.xi_inverse(Ev, poly, dims)
-    return dict(A=A, defl_m=defl_m, info_m=info_m, info_h=info_h, lam=lam, Ev=Ev, eig_resid=eres,
+    return dict(A=A, Ap=Ap, system=system, defl_m=defl_m, info_m=info_m, info_h=info_h, lam=lam, Ev=Ev, eig_resid=eres,
                 a=a, b=S.a_to_b(a), t=t, xi_pert=xi_p, xi_poly=xi_q, pert=pert, poly=poly)
 
 
@@ -73,16 +82,22 @@ def solve_noises(st, dims, seed, first, count, m_inner, tol, max_cycles=2000):
     xs, infos = [], []
     for n in range(first, first + count):
         eta = L.flat(rng.z4_noise(seed, n, dims))
-        x, info = Kr.gmres_proj(st["A"], eta, st["defl_m"], m_inner, tol, max_cycles)
-        xs.append(L.unflat(x, dims))
+        if st["system"] == "MG5":
+            y, info = Kr.gmres_proj(st["Ap"], eta, st["defl_m"], m_inner, tol, max_cycles)
+            xs.append(L.g5(L.unflat(y, dims)))
+        else:
+            x, info = Kr.gmres_proj(st["A"], eta, st["defl_m"], m_inner, tol, max_cycles)
+            xs.append(L.unflat(x, dims))
         infos.append(info)
     return np.stack(xs), infos
 
 
-def loop_estimate(U, kappa, dims, seed, nnoise, m, k, K, npoly, tol, tol_special, modes=E.MODES):
-    """Run steps 1-5; returns (results per mode, setup state, timing)."""
+def loop_estimate(U, kappa, dims, seed, nnoise, m, k, K, npoly, tol, tol_special, modes=E.MODES, eig_tol=None,
+                  system="M"):
+    """Run steps 1-5; returns (results per mode, setup state, timing).  eig_tol: see krylov.gmres_dr;
+    system: "M" or "MG5" (step 1)."""
     t0 = time.perf_counter()
-    st = setup(U, kappa, dims, seed, m, k, K, npoly, tol_special)
+    st = setup(U, kappa, dims, seed, m, k, K, npoly, tol_special, eig_tol=eig_tol, system=system)
     add = addbacks(U, kappa, dims, st, K)
     t1 = time.perf_counter()
     xs, infos = solve_noises(st, dims, seed, 0, nnoise, m - k, tol)
@@ -96,7 +111,7 @@ def loop_estimate(U, kappa, dims, seed, nnoise, m, k, K, npoly, tol, tol_special
     return out, st, dict(setup_s=t1 - t0, noise_s=t2 - t1, solve_infos=infos)
 
 
-def loop_derivs(U, kappa, dims, seed, nnoise, m, k, K, tol, tol_special, max_cycles=2000):
+def loop_derivs(U, kappa, dims, seed, nnoise, m, k, K, tol, tol_special, max_cycles=2000, eig_tol=None):
     """Derivatives of the loop estimates (see oracle/derivs.py), step by step: GMRES-DR on M for the
     special right-hand side; per noise x = M^{-1} eta, y = M^{-1} P x and z = M^{-dag} eta by
     GMRES-Proj; per-noise d/dkappa of the NS and PS estimates of the nine operators (PS add-back
@@ -105,7 +120,7 @@ def loop_derivs(U, kappa, dims, seed, nnoise, m, k, K, tol, tol_special, max_cyc
     from . import derivs as Dv
     A = lambda v: L.flat(L.wilson(U, kappa, L.unflat(v, dims)))
     b0 = L.flat(rng.z4_noise(seed, rng.NOISE_SPECIAL, dims))
-    _, _, defl = Kr.gmres_dr(A, b0, m, k, tol_special, max_cycles)
+    _, _, defl = Kr.gmres_dr(A, b0, m, k, tol_special, max_cycles, eig_tol=eig_tol)
     solve = lambda f: L.unflat(Kr.gmres_proj(A, L.flat(f), defl, m - k, tol, max_cycles)[0], dims)
     t = S.hop_traces(U, kappa, K, dims)
     dadd = O.per_t(Dv.dpert_addback(t, kappa, K)).sum(axis=-1)

@@ -236,7 +236,7 @@ extern "C" lqcd_status lqcd_loop_derivs(lqcd_ctx *ctx, const double *links, doub
     }
   } guard{bs, &dm};
   LQCD_TRY(noise_launch(ctx, o->seed, 0xFFFFFFFEu, 1, bs));
-  lqcd_krylov_opts ko{o->m, o->k, o->tol_special, o->max_cycles, LQCD_SYS_M, LQCD_PREC_F64};
+  lqcd_krylov_opts ko{o->m, o->k, o->tol_special, o->max_cycles, LQCD_SYS_M, LQCD_PREC_F64, 0.0, o->eig_tol};
   lqcd_solve_info si{};
   lqcd_status st = lqcd_gmresdr_solve(ctx, links, kappa, (const double *)bs, (double *)xs, 1, &ko, &si, &dm);
   if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;

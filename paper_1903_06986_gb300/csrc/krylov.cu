@@ -12,13 +12,15 @@
 //   harmonic Ritz (H_m + |h_{m+1,m}|^2 H_m^{-H} e_m e_m^T) g = theta g, k smallest |theta|;
 //   P_{k+1} = orthonormal [g_1..g_k (zero-padded), s];  V <- V P;  Hbar <- P^H Hbar P_k;
 //   c <- P^H s;  j0 = k.
-// Hermitian form (MINRES-DR, Sec. 8): the harmonic Ritz problem is solved as the Hermitian-
-// definite H_m g = (1/theta) Hbar^H Hbar g, which gives real theta.
+// Hermitian form (MINRES-DR, Sec. 8): minimum residual over the same spaces of the Hermitian
+// M' = M gamma_5; the harmonic Ritz values are real (rounding-level imaginary parts dropped) and the
+// final Rayleigh-Ritz problem is Hermitian, giving orthonormal eigenvectors and real eigenvalues.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <memory>
 #include <type_traits>
 
 #include "common.cuh"
@@ -124,6 +126,7 @@ struct Rhs {
   bool active = true;
   double bnorm = 0.0;
   double rel = 0.0;
+  double eres = 0.0;     // largest Rayleigh-Ritz residual of the restart space (when tracked)
 };
 
 // Enqueue Arnoldi steps j0..m-1 for every right-hand side (basis Vb with vector stride vs =
@@ -228,23 +231,18 @@ bool harmonic_ritz(const Mat &H, int k, bool hermitian, std::vector<cd> &theta, 
   std::vector<int> order(m);
   std::vector<cd> th(m);
   Mat X;
-  if (hermitian) {
-    Mat Hs(m, m);
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) Hs(i, j) = 0.5 * (Hm(i, j) + std::conj(Hm(j, i)));
-    Mat B = dense::matmul(dense::adjoint(H), H);
-    std::vector<double> mu;
-    if (!dense::eigh_gen(Hs, B, mu, X)) return false;
-    for (int i = 0; i < m; ++i) th[i] = cd(1.0 / mu[i], 0.0);
-  } else {
-    std::vector<cd> em(m, cd(0.0, 0.0)), f;
-    em[m - 1] = 1.0;
-    if (!dense::solve(dense::adjoint(Hm), em, f)) return false;
-    const double h2 = std::norm(H(m, m - 1));
-    Mat F = Hm;
-    for (int i = 0; i < m; ++i) F(i, m - 1) += h2 * f[i];
-    if (!dense::eig(F, th, X)) return false;
-  }
+  // the general form for both: the equivalent Hermitian-definite form with H_m symmetrised keeps the
+  // restart relation only to the rounding asymmetry of H_m, and that error grows from cycle to cycle
+  // on long runs; for Hermitian A the theta are real and their rounding-level imaginary parts dropped
+  std::vector<cd> em(m, cd(0.0, 0.0)), f;
+  em[m - 1] = 1.0;
+  if (!dense::solve(dense::adjoint(Hm), em, f)) return false;
+  const double h2 = std::norm(H(m, m - 1));
+  Mat F = Hm;
+  for (int i = 0; i < m; ++i) F(i, m - 1) += h2 * f[i];
+  if (!dense::eig(F, th, X)) return false;
+  if (hermitian)
+    for (int i = 0; i < m; ++i) th[i] = cd(th[i].real(), 0.0);
   for (int i = 0; i < m; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return std::abs(th[a]) < std::abs(th[b]); });
   theta.resize(k);
@@ -256,7 +254,64 @@ bool harmonic_ritz(const Mat &H, int k, bool hermitian, std::vector<cd> &theta, 
   return true;
 }
 
-// P_{k+1}: orthonormal [g (zero-padded to m+1 rows) | s]
+// Unit vector spanning the orthogonal complement of range(Hbar) ((m+1) x m, H_m nonsingular):
+// Hbar^H w = 0 gives w = [-conj(h_{m+1,m}) H_m^{-H} e_m; 1].  The least-squares residual s and every
+// harmonic Ritz residual Hbar g - theta [g; 0] are parallel to it in exact arithmetic; once the
+// system has converged s is rounding noise, so the restart uses w (keeping A V_k = V_{k+1} Hbar_k
+// exact to rounding).  Falls back to s when H_m is singular.
+std::vector<cd> lsq_complement(const Mat &H, const std::vector<cd> &s) {
+  const int m = H.c;
+  Mat Hm(m, m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) Hm(i, j) = H(i, j);
+  std::vector<cd> em(m, cd(0.0, 0.0)), f;
+  em[m - 1] = 1.0;
+  if (!dense::solve(dense::adjoint(Hm), em, f)) return s;
+  std::vector<cd> w(m + 1);
+  const cd h = std::conj(H(m, m - 1));
+  double nrm = 1.0;
+  for (int i = 0; i < m; ++i) {
+    w[i] = -h * f[i];
+    nrm += std::norm(w[i]);
+  }
+  w[m] = 1.0;
+  nrm = std::sqrt(nrm);
+  if (!std::isfinite(nrm)) return s;
+  for (cd &v : w) v /= nrm;
+  return w;
+}
+
+// Largest Rayleigh-Ritz residual ||Hbar_k y - lambda [y; 0]|| of a deflation space's (k+1) x k
+// Hbar_k (the eigen residual ||A e - lambda e|| of its unit Ritz vectors); infinity on failure
+double ritz_resid_max(const Mat &Hk, bool hermitian) {
+  const int k = Hk.c;
+  Mat T(k, k);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) T(i, j) = Hk(i, j);
+  std::vector<cd> lam(k);
+  Mat Y;
+  if (hermitian) {
+    std::vector<double> w;
+    if (!dense::eigh(T, w, Y)) return INFINITY;
+    for (int i = 0; i < k; ++i) lam[i] = cd(w[i], 0.0);
+  } else if (!dense::eig(T, lam, Y)) {
+    return INFINITY;
+  }
+  double worst = 0.0;
+  for (int q = 0; q < k; ++q) {
+    double r2 = 0.0;
+    for (int i = 0; i <= k; ++i) {
+      cd v = 0.0;
+      for (int j = 0; j < k; ++j) v += Hk(i, j) * Y(j, q);
+      if (i < k) v -= lam[q] * Y(i, q);
+      r2 += std::norm(v);
+    }
+    worst = std::max(worst, std::sqrt(r2));
+  }
+  return worst;
+}
+
+// P_{k+1}: orthonormal [g (zero-padded to m+1 rows) | w]
 Mat restart_basis(const Mat &G, const std::vector<cd> &s) {
   const int m1 = (int)s.size(), k = G.c;
   Mat A(m1, k + 1);
@@ -319,6 +374,7 @@ lqcd_status check_opts(lqcd_ctx *ctx, const lqcd_krylov_opts *o, int nrhs) {
   if (o->m < 1 || o->m > 1000 || o->k < 0 || o->k >= o->m)
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "need 0 <= k < m <= 1000 (m=%d k=%d)", o->m, o->k);
   if (!(o->tol > 0.0) || o->max_cycles < 1) return set_err(ctx, LQCD_ERR_INVALID_ARG, "need tol > 0 and max_cycles >= 1");
+  if (!(o->eig_tol >= 0.0)) return set_err(ctx, LQCD_ERR_INVALID_ARG, "need eig_tol >= 0");
   if (nrhs < 1 || nrhs > 4096) return set_err(ctx, LQCD_ERR_INVALID_ARG, "nrhs %d out of range", nrhs);
   if (o->prec < LQCD_PREC_F64 || o->prec > LQCD_PREC_BF16) return set_err(ctx, LQCD_ERR_INVALID_ARG, "bad precision");
   return LQCD_OK;
@@ -404,7 +460,10 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
   int j0 = 0, cycles = 0;
   bool all_conv = false;
   std::vector<std::vector<cd>> theta_keep(nrhs);
-  std::vector<Mat> P_keep(nrhs);
+  std::vector<Mat> P_keep(nrhs), Hn_keep(nrhs);
+  // a right-hand side is done when its residual is below tol and, with eig_tol > 0, the Ritz
+  // residuals of its restart space are below eig_tol (super-convergence, Sec. 5.4, 7)
+  auto rhs_done = [&](const Rhs &q) { return q.rel <= o->tol && (o->eig_tol <= 0.0 || q.eres <= o->eig_tol); };
   std::vector<char> rotated(nrhs, 0);
   for (int cyc = 0; cyc < o->max_cycles; ++cyc) {
     cycles = cyc + 1;
@@ -441,12 +500,18 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
       } else {
         G = Mat(m, 0);
       }
-      Mat P = restart_basis(G, s[r]);
+      Mat P = restart_basis(G, lsq_complement(R[r].H, s[r]));
       for (int i = 0; i <= m; ++i)
         for (int c = 0; c <= k; ++c) pcoef[((size_t)i * (k + 1) + c) * nrhs + r] = P(i, c);
       theta_keep[r] = th;
       P_keep[r] = P;
-      if (R[r].rel > o->tol) all_conv = false;
+      // Hbar_k of the restart space (the next cycle's start, and the deflation space if last)
+      Mat Pk(m, k);
+      for (int i = 0; i < m; ++i)
+        for (int c = 0; c < k; ++c) Pk(i, c) = P(i, c);
+      Hn_keep[r] = dense::matmul(dense::adjoint(P), dense::matmul(R[r].H, Pk));
+      R[r].eres = (o->eig_tol > 0.0 && k > 0) ? ritz_resid_max(Hn_keep[r], hermitian[r] != 0) : 0.0;
+      if (!rhs_done(R[r])) all_conv = false;
     }
     const bool last = all_conv || cyc + 1 == o->max_cycles;
     if (last) break;
@@ -457,10 +522,7 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
       if (!R[r].active) continue;
       const Mat &P = P_keep[r];
       // Hbar_new = P^H Hbar P_k  ((k+1) x k), c_new = P^H s
-      Mat Pk(m, k);
-      for (int i = 0; i < m; ++i)
-        for (int c = 0; c < k; ++c) Pk(i, c) = P(i, c);
-      Mat Hn = dense::matmul(dense::adjoint(P), dense::matmul(R[r].H, Pk));
+      const Mat &Hn = Hn_keep[r];
       Mat Hfull(m + 1, m);
       for (int i = 0; i <= k; ++i)
         for (int j = 0; j < k; ++j) Hfull(i, j) = Hn(i, j);
@@ -472,7 +534,7 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
         cn[i] = v;
       }
       R[r].c = cn;
-      if (R[r].rel <= o->tol) {
+      if (rhs_done(R[r])) {
         R[r].active = false;
         rotated[r] = 1;  // V[0..k] and H already hold this right-hand side's deflation space
       }
@@ -938,6 +1000,41 @@ lqcd_status lqcd_defl_import(lqcd_ctx *ctx, int k, const double *E, const double
   d->eres.assign(k, 0.0);
   cudaStreamSynchronize(ctx->stream);
   *out = d;
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_defl_import_space(lqcd_ctx *ctx, int k, const double *V, const double *Hbar, int hermitian,
+                                   lqcd_defl **out) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!V || !Hbar || !out || k < 1 || k > 4096) return set_err(ctx, LQCD_ERR_INVALID_ARG, "defl_import_space: bad arguments");
+  *out = nullptr;
+  for (size_t i = 0; i < (size_t)(k + 1) * k * 2; ++i)
+    if (!std::isfinite(Hbar[i])) return set_err(ctx, LQCD_ERR_NONFINITE, "defl_import_space: non-finite Hbar entry");
+  lqcd_defl *d = new lqcd_defl();
+  d->ctx = ctx;
+  d->k = k;
+  d->hermitian = hermitian ? 1 : 0;
+  d->N = ctx->N;
+  d->V = d->E = nullptr;
+  d->Hbar_dev = nullptr;
+  d->tc = nullptr;
+  std::unique_ptr<lqcd_defl, lqcd_status (*)(lqcd_defl *)> guard(d, lqcd_defl_destroy);
+  cudaError_t e1 = cudaMalloc(&d->V, sizeof(double2) * (size_t)(k + 1) * d->N);
+  cudaError_t e2 = cudaMalloc(&d->E, sizeof(double2) * (size_t)k * d->N);
+  cudaError_t e3 = cudaMalloc(&d->Hbar_dev, sizeof(double2) * (size_t)(k + 1) * k);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, LQCD_ERR_OOM, "defl_import_space: allocation failed");
+  }
+  LQCD_CUDA(ctx, cudaMemcpyAsync(d->V, V, sizeof(double2) * (size_t)(k + 1) * d->N, cudaMemcpyDeviceToDevice, ctx->stream));
+  d->Hbar.resize((size_t)(k + 1) * k);
+  memcpy(d->Hbar.data(), Hbar, sizeof(double2) * d->Hbar.size());
+  std::vector<cd> hrow((size_t)(k + 1) * k);
+  for (size_t i = 0; i < hrow.size(); ++i) hrow[i] = cd(d->Hbar[i].x, d->Hbar[i].y);
+  LQCD_TRY(upload(ctx, hrow, d->Hbar_dev));
+  LQCD_TRY(ritz_pairs(ctx, d));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *out = guard.release();
   return LQCD_OK;
 }
 

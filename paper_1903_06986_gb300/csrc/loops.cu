@@ -12,6 +12,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <memory>
 #include <mutex>
 
 #include <cuda.h>  // driver types of the context-id query (entry points come from the runtime)
@@ -697,65 +698,80 @@ lqcd_status lqcd_xi_inverse(lqcd_ctx *ctx, const double *links, double kappa, co
 
 }  // extern "C"
 
-// ---- whole loop estimate ----------------------------------------------------------------------
+// ---- whole loop estimate: per-configuration setup, then noise batches ------------------------------
 lqcd_status special_solves(lqcd_ctx *ctx, const double *links, double kappa, const double2 *b2, double2 *x2,
                            const lqcd_krylov_opts *o, lqcd_solve_info *info, lqcd_defl **defl_m, lqcd_defl **defl_h);
 lqcd_status proj_core_entry(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, const double2 *b,
                             double2 *x, int nrhs, const lqcd_krylov_opts *o, lqcd_solve_info *info);
 
-extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *o,
-                                          lqcd_estimate *out) {
-  if (!ctx) return LQCD_ERR_INVALID_ARG;
-  if (!links || !o || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: NULL argument");
+// Setup state of one gauge configuration (steps 1-3): the two deflation spaces, the polynomial, the
+// 1/xi' of both combined modes and every add-back; the noise phase (step 4) reads it.
+struct lqcd_loop {
+  lqcd_ctx *ctx = nullptr;
+  double kappa = 0.0;
+  lqcd_est_opts o{};
+  int modes = 0, Kt = 0, Q = 0, block = 0;
+  lqcd_defl *dm = nullptr, *dh = nullptr;  // GMRES-Proj space of M; eigenpairs of M'
+  bool own_m = false, own_h = false;
+  std::vector<cd> a, bcoef, xi_p, xi_q, lam, dl, dlp, dlq;
+  std::vector<cd> add;  // [6][9][Lt]
+  long matvecs = 0;
+  double seconds = 0.0, eres = 0.0;
+  ~lqcd_loop() {
+    if (own_m && dm) lqcd_defl_destroy(dm);
+    if (own_h && dh) lqcd_defl_destroy(dh);
+  }
+};
+
+namespace {
+
+lqcd_status check_est_opts(lqcd_ctx *ctx, const lqcd_est_opts *o) {
   if (o->nnoise < 1 || o->block < 0 || o->m < 2 || o->k < 1 || o->k >= o->m || o->K < 1 || o->npoly < 0 ||
-      o->npoly > 63 || o->K > 64 || !(o->tol > 0) || !(o->tol_special > 0) || o->max_cycles < 1)
-    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: bad options");
+      o->npoly > 63 || o->K > 64 || !(o->tol > 0) || !(o->tol_special > 0) || o->max_cycles < 1 || !(o->eig_tol >= 0))
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop estimate: bad options");
   if (o->prec < LQCD_PREC_F64 || o->prec > LQCD_PREC_BF16)
-    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: prec must be one of LQCD_PREC_*");
-  const double2 *U = (const double2 *)links;
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop estimate: prec must be one of LQCD_PREC_*");
+  if (o->system != LQCD_SYS_M && o->system != LQCD_SYS_MG5)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop estimate: system must be LQCD_SYS_M or LQCD_SYS_MG5");
+  return LQCD_OK;
+}
+
+lqcd_krylov_opts noise_solver_opts(const lqcd_est_opts *o) {
+  return lqcd_krylov_opts{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec,
+                          o->inner_tol, 0.0};
+}
+
+// Steps 2-3 given the two spaces (L->dm, L->dh set): Min-Res coefficients (unless given), b_k,
+// hopping traces, 1/xi', the eigen add-back densities and the add-backs of all six modes; then the
+// block width (autotuned when opts->block == 0).
+lqcd_status loop_finish_setup(lqcd_loop *L, const double2 *U, const double *links, const double *a_given) {
+  lqcd_ctx *ctx = L->ctx;
+  const lqcd_est_opts *o = &L->o;
+  const double kappa = L->kappa;
   const int Lt = ctx->dims[3];
   const long long N = ctx->N;
-  const int Kt = std::max(o->K, o->npoly + 1);
-  const int modes = o->modes ? o->modes : LQCD_SUB_ALL;
-  const double t0 = now_s();
-  // 1. special right-hand side: GMRES-DR on M (projection space), MINRES-DR on M' (eigenpairs)
-  double2 *x0, *bs;
-  LQCD_TRY(ws_get(ctx, WS_SPEC, sizeof(double2) * (size_t)N * 4, (void **)&x0));
-  bs = x0 + 2 * N;
-  struct Guard {
-    lqcd_defl *a, *b;
-    ~Guard() {
-      if (a) lqcd_defl_destroy(a);
-      if (b) lqcd_defl_destroy(b);
-    }
-  } guard{nullptr, nullptr};
-  LQCD_TRY(noise_launch(ctx, o->seed, 0xFFFFFFFEu, 1, bs));
-  LQCD_TRY(noise_launch(ctx, o->seed, 0xFFFFFFFEu, 1, bs + N));
-  lqcd_krylov_opts ko{o->m, o->k, o->tol_special, o->max_cycles, LQCD_SYS_M, LQCD_PREC_F64};
-  lqcd_solve_info si{};
-  lqcd_status st = special_solves(ctx, links, kappa, bs, x0, &ko, &si, &guard.a, &guard.b);
-  if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
-  long matvecs_setup = si.matvecs;
-  const lqcd_defl *dm = guard.a, *dh = guard.b;
-  if (!dm || !dh) return set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop_estimate: no deflation space");
-  const int Q = dh->k;
-  // 2. Min-Res polynomial, 3. hopping traces and 1/xi'
-  std::vector<cd> a;
-  LQCD_TRY(poly_coeffs_dev(ctx, U, kappa, o->seed, o->npoly, a));
-  matvecs_setup += o->npoly + 1;
-  std::vector<cd> bcoef(o->npoly + 1, cd(0.0, 0.0));  // b_k = (-1)^k sum_{j>=k} C(j,k) a_j
+  const lqcd_defl *dh = L->dh;
+  L->Q = dh->k;
+  const int Q = L->Q;
+  if (a_given) {
+    L->a.assign((const cd *)a_given, (const cd *)a_given + o->npoly + 1);
+  } else {
+    LQCD_TRY(poly_coeffs_dev(ctx, U, kappa, o->seed, o->npoly, L->a));
+    L->matvecs += o->npoly + 1;
+  }
+  L->bcoef.assign(o->npoly + 1, cd(0.0, 0.0));  // b_k = (-1)^k sum_{j>=k} C(j,k) a_j
   for (int k = 0; k <= o->npoly; ++k) {
     double binom = 1.0;  // C(j, k) for j = k
     for (int j = k; j <= o->npoly; ++j) {
-      bcoef[k] += ((k & 1) ? -1.0 : 1.0) * binom * a[j];
+      L->bcoef[k] += ((k & 1) ? -1.0 : 1.0) * binom * L->a[j];
       binom = binom * (j + 1) / (j + 1 - k);
     }
   }
   std::vector<cd> tr;
-  LQCD_TRY(hop_traces_dev(ctx, U, kappa, Kt, tr));
-  std::vector<cd> xi_p, xi_q;
-  LQCD_TRY(xi_dev(ctx, U, kappa, dh, LQCD_SUB_PERT, o->K, nullptr, xi_p));
-  LQCD_TRY(xi_dev(ctx, U, kappa, dh, LQCD_SUB_POLY, o->npoly + 1, a.data(), xi_q));
+  LQCD_TRY(hop_traces_dev(ctx, U, kappa, L->Kt, tr));
+  LQCD_TRY(xi_dev(ctx, U, kappa, dh, LQCD_SUB_PERT, o->K, nullptr, L->xi_p));
+  LQCD_TRY(xi_dev(ctx, U, kappa, dh, LQCD_SUB_POLY, o->npoly + 1, L->a.data(), L->xi_q));
+  L->matvecs += (long)Q * (o->K - 1 + o->npoly);
   // eigen add-back densities: contract(e_q, g5 e_q) per q
   std::vector<cd> eig_t((size_t)Q * 9 * Lt);
   {
@@ -768,31 +784,35 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
     LQCD_TRY(download_v(ctx, cdv, h, (size_t)Q * 9 * Lt));
     for (size_t i = 0; i < h.size(); ++i) eig_t[i] = cd(h[i].x, h[i].y);
   }
-  std::vector<cd> lam(Q), dl(Q), dlp(Q), dlq(Q);
+  L->lam.resize(Q);
+  L->dl.resize(Q);
+  L->dlp.resize(Q);
+  L->dlq.resize(Q);
+  L->eres = 0.0;
   for (int q = 0; q < Q; ++q) {
-    lam[q] = cd(dh->lam[q].x, dh->lam[q].y);
-    dl[q] = 1.0 / lam[q];
-    dlp[q] = 1.0 / lam[q] - xi_p[q];
-    dlq[q] = 1.0 / lam[q] - xi_q[q];
+    L->lam[q] = cd(dh->lam[q].x, dh->lam[q].y);
+    L->dl[q] = 1.0 / L->lam[q];
+    L->dlp[q] = 1.0 / L->lam[q] - L->xi_p[q];
+    L->dlq[q] = 1.0 / L->lam[q] - L->xi_q[q];
+    if (q < (int)dh->eres.size()) L->eres = std::max(L->eres, dh->eres[q]);
   }
-  // add-backs per mode [6][9][Lt]
-  std::vector<cd> add((size_t)LQCD_NMODES * 9 * Lt, cd(0.0, 0.0));
-  auto A = [&](int mode, int op, int t) -> cd & { return add[((size_t)mode * 9 + op) * Lt + t]; };
+  L->add.assign((size_t)LQCD_NMODES * 9 * Lt, cd(0.0, 0.0));
+  auto A = [&](int mode, int op, int t) -> cd & { return L->add[((size_t)mode * 9 + op) * Lt + t]; };
   for (int op = 0; op < 9; ++op)
     for (int t = 0; t < Lt; ++t) {
       cd pert = 0.0, poly = 0.0, e1 = 0.0, ep = 0.0, eq = 0.0;
       double kk = 1.0;
-      for (int k = 0; k < Kt; ++k) {
+      for (int k = 0; k < L->Kt; ++k) {
         const cd tk = tr[((size_t)k * 9 + op) * Lt + t];
         if (k < o->K) pert += kk * tk;
-        if (k <= o->npoly) poly += bcoef[k] * kk * tk;
+        if (k <= o->npoly) poly += L->bcoef[k] * kk * tk;
         kk *= kappa;
       }
       for (int q = 0; q < Q; ++q) {
         const cd et = eig_t[((size_t)q * 9 + op) * Lt + t];
-        e1 += dl[q] * et;
-        ep += dlp[q] * et;
-        eq += dlq[q] * et;
+        e1 += L->dl[q] * et;
+        ep += L->dlp[q] * et;
+        eq += L->dlq[q] * et;
       }
       A(1, op, t) = pert;
       A(2, op, t) = poly;
@@ -800,19 +820,32 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
       A(4, op, t) = pert + ep;
       A(5, op, t) = poly + eq;
     }
-  lqcd_krylov_opts po{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec, o->inner_tol};
-  int block = o->block;
-  if (block == 0) {
+  L->block = o->block;
+  if (L->block == 0) {
     // autotuned block width among 8, 16, 32, 64 (those not above the noise count)
+    const lqcd_krylov_opts po = noise_solver_opts(o);
     std::vector<int> cand;
     for (int c : {8, 16, 32, 64})
       if (c <= o->nnoise) cand.push_back(c);
     if (cand.empty()) cand.push_back(o->nnoise);
-    LQCD_TRY(autotune_block(ctx, links, kappa, dm, &po, cand.data(), (int)cand.size(), &block, nullptr));
+    LQCD_TRY(autotune_block(ctx, links, kappa, L->dm, &po, cand.data(), (int)cand.size(), &L->block, nullptr));
   }
-  const double t1 = now_s();
-  // 4. noise blocks
-  const int bw = std::min(block, o->nnoise);
+  return LQCD_OK;
+}
+
+// Step 4 for noises first .. first+count-1: per_noise_t[((mode * count + n) * 9 + op) * Lt + t]
+lqcd_status loop_noises(lqcd_loop *L, const double *links, uint32_t first0, int count, std::vector<cd> &per_noise_t,
+                        lqcd_noise_info *info) {
+  lqcd_ctx *ctx = L->ctx;
+  const lqcd_est_opts *o = &L->o;
+  const double kappa = L->kappa;
+  const double2 *U = (const double2 *)links;
+  const int Lt = ctx->dims[3];
+  const long long N = ctx->N;
+  const int modes = L->modes;
+  const double t0 = now_s();
+  const lqcd_krylov_opts po = noise_solver_opts(o);
+  const int bw = std::max(1, std::min(L->block, count));
   const long long bn = (long long)bw * N;
   double2 *eta, *x, *xp, *xq, *y, *w, *cdv;
   LQCD_TRY(ws_get(ctx, WS_NBLK, sizeof(double2) * (size_t)bn * 6, (void **)&eta));
@@ -822,26 +855,34 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
   y = xq + bn;
   w = y + bn;
   LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)bw * 9 * Lt, (void **)&cdv));
-  const int nn = o->nnoise;
-  std::vector<cd> per_noise_t((size_t)LQCD_NMODES * nn * 9 * Lt, cd(0.0, 0.0));
-  long matvecs_noise = 0;
+  per_noise_t.assign((size_t)LQCD_NMODES * count * 9 * Lt, cd(0.0, 0.0));
+  long matvecs = 0;
   double worst = 0.0;
   int conv = 1;
   std::vector<double2> h;
-  for (int first = 0; first < nn; first += bw) {
-    const int nb = std::min(bw, nn - first);
+  const bool need_p = modes & (LQCD_SUB_PERT | LQCD_SUB_DEFL_PERT);
+  const bool need_q = modes & (LQCD_SUB_POLY | LQCD_SUB_DEFL_POLY);
+  for (int off = 0; off < count; off += bw) {
+    const int nb = std::min(bw, count - off);
     const long long len = (long long)nb * N;
-    LQCD_TRY(noise_launch(ctx, o->seed, (uint32_t)first, nb, eta));
+    LQCD_TRY(noise_launch(ctx, o->seed, first0 + (uint32_t)off, nb, eta));
     lqcd_solve_info pi{};
-    st = proj_core_entry(ctx, links, kappa, dm, eta, x, nb, &po, &pi);
-    if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
+    if (L->dm->hermitian) {
+      // M' y = eta over the Hermitian space, x = gamma_5 y (y is free until the deflation vectors)
+      const lqcd_status st = proj_core_entry(ctx, links, kappa, L->dm, eta, y, nb, &po, &pi);
+      if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
+      LQCD_TRY(blas_g5(ctx, y, x, nb));
+    } else {
+      const lqcd_status st = proj_core_entry(ctx, links, kappa, L->dm, eta, x, nb, &po, &pi);
+      if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
+    }
     if (!pi.converged) conv = 0;
     worst = std::max(worst, pi.true_resid);
-    matvecs_noise += pi.matvecs;
-    const bool need_p = modes & (LQCD_SUB_PERT | LQCD_SUB_DEFL_PERT);
-    const bool need_q = modes & (LQCD_SUB_POLY | LQCD_SUB_DEFL_POLY);
+    matvecs += pi.matvecs;
     if (need_p) LQCD_TRY(hop_series_dev(ctx, U, kappa, eta, xp, nb, o->K, nullptr));
-    if (need_q) LQCD_TRY(poly_apply_dev(ctx, U, kappa, eta, xq, nb, o->npoly, a.data()));
+    if (need_q) LQCD_TRY(poly_apply_dev(ctx, U, kappa, eta, xq, nb, o->npoly, L->a.data()));
+    if (need_p) matvecs += (long)nb * (o->K - 1);
+    if (need_q) matvecs += (long)nb * o->npoly;
     for (int mode = 0; mode < LQCD_NMODES; ++mode) {
       if (!(modes & (1 << mode))) continue;
       // w = x - tilde x
@@ -849,19 +890,160 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
       if (mode == 1 || mode == 4) LQCD_TRY(scaled_acc(ctx, xp, w, cd(-1.0, 0.0), len));
       if (mode == 2 || mode == 5) LQCD_TRY(scaled_acc(ctx, xq, w, cd(-1.0, 0.0), len));
       if (mode >= 3) {
-        const cd *dv = (mode == 3) ? dl.data() : (mode == 4 ? dlp.data() : dlq.data());
-        LQCD_TRY(deflate_dev(ctx, dh, eta, y, nb, dv));
+        const cd *dv = (mode == 3) ? L->dl.data() : (mode == 4 ? L->dlp.data() : L->dlq.data());
+        LQCD_TRY(deflate_dev(ctx, L->dh, eta, y, nb, dv));
         LQCD_TRY(scaled_acc(ctx, y, w, cd(-1.0, 0.0), len));
       }
       LQCD_TRY(contract_launch(ctx, U, kappa, eta, w, nb, cdv));
       LQCD_TRY(download_v(ctx, cdv, h, (size_t)nb * 9 * Lt));
       for (int r = 0; r < nb; ++r)
         for (int q = 0; q < 9 * Lt; ++q)
-          per_noise_t[(((size_t)mode * nn + first + r) * 9 * Lt) + q] = cd(h[(size_t)r * 9 * Lt + q].x, h[(size_t)r * 9 * Lt + q].y);
+          per_noise_t[(((size_t)mode * count + off + r) * 9 * Lt) + q] =
+              cd(h[(size_t)r * 9 * Lt + q].x, h[(size_t)r * 9 * Lt + q].y);
     }
   }
-  const double t2 = now_s();
+  if (info) {
+    info->matvecs = matvecs;
+    info->seconds = now_s() - t0;
+    info->max_true_resid = worst;
+    info->converged = conv;
+    info->block = bw;
+  }
+  return LQCD_OK;
+}
+
+lqcd_status loop_new(lqcd_ctx *ctx, double kappa, const lqcd_est_opts *o, lqcd_loop **out) {
+  LQCD_TRY(check_est_opts(ctx, o));
+  lqcd_loop *L = new lqcd_loop();
+  L->ctx = ctx;
+  L->kappa = kappa;
+  L->o = *o;
+  L->modes = o->modes ? o->modes : LQCD_SUB_ALL;
+  L->Kt = std::max(o->K, o->npoly + 1);
+  *out = L;
+  return LQCD_OK;
+}
+
+// Steps 1-3 from scratch: special solves (GMRES-DR on M, MINRES-DR on M' batched), then the rest
+lqcd_status loop_setup(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *o, lqcd_loop **out) {
+  *out = nullptr;
+  const double t0 = now_s();
+  lqcd_loop *L = nullptr;
+  LQCD_TRY(loop_new(ctx, kappa, o, &L));
+  std::unique_ptr<lqcd_loop> guard(L);
+  const long long N = ctx->N;
+  double2 *x0, *bs;
+  LQCD_TRY(ws_get(ctx, WS_SPEC, sizeof(double2) * (size_t)N * 4, (void **)&x0));
+  bs = x0 + 2 * N;
+  LQCD_TRY(noise_launch(ctx, o->seed, 0xFFFFFFFEu, 1, bs));
+  LQCD_TRY(noise_launch(ctx, o->seed, 0xFFFFFFFEu, 1, bs + N));
+  lqcd_krylov_opts ko{o->m, o->k, o->tol_special, o->max_cycles, LQCD_SYS_M, LQCD_PREC_F64, 0.0, o->eig_tol};
+  lqcd_solve_info si{};
+  lqcd_status st;
+  if (o->system == LQCD_SYS_MG5) {
+    // Hermitian path: MINRES-DR on M' alone gives both the eigenpairs and the noise solves' space
+    st = lqcd_minresdr_solve(ctx, links, kappa, (const double *)bs, (double *)x0, 1, &ko, &si, &L->dh);
+    L->dm = L->dh;
+    L->own_h = true;
+  } else {
+    st = special_solves(ctx, links, kappa, bs, x0, &ko, &si, &L->dm, &L->dh);
+    L->own_m = L->own_h = true;
+  }
+  if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
+  if (!L->dm || !L->dh) return set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop setup: no deflation space");
+  L->matvecs = si.matvecs;
+  LQCD_TRY(loop_finish_setup(L, (const double2 *)links, links, nullptr));
+  L->seconds = now_s() - t0;
+  *out = guard.release();
+  return LQCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lqcd_status lqcd_loop_setup(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *opts,
+                            lqcd_loop **out) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !opts || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_setup: NULL argument");
+  return loop_setup(ctx, links, kappa, opts, out);
+}
+
+lqcd_status lqcd_loop_setup_from(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *opts,
+                                 const lqcd_defl *proj, const lqcd_defl *eig, const double *a, lqcd_loop **out) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !opts || !proj || !eig || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_setup_from: NULL argument");
+  *out = nullptr;
+  if (!proj->V || !proj->Hbar_dev || proj->N != ctx->N)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_setup_from: proj must be a Krylov space of this lattice (solver-made or lqcd_defl_import_space)");
+  if (!eig->E || eig->N != ctx->N) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_setup_from: eig has no eigenvectors of this lattice");
+  const double t0 = now_s();
+  lqcd_loop *L = nullptr;
+  LQCD_TRY(loop_new(ctx, kappa, opts, &L));
+  std::unique_ptr<lqcd_loop> guard(L);
+  L->dm = const_cast<lqcd_defl *>(proj);
+  L->dh = const_cast<lqcd_defl *>(eig);
+  LQCD_TRY(loop_finish_setup(L, (const double2 *)links, links, a));
+  L->seconds = now_s() - t0;
+  *out = guard.release();
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_loop_noises(lqcd_loop *L, const double *links, uint32_t first, int count, double *per_noise_t,
+                             lqcd_noise_info *info) {
+  if (!L || !L->ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !per_noise_t || count < 1) return set_err(L->ctx, LQCD_ERR_INVALID_ARG, "loop_noises: bad arguments");
+  if ((uint64_t)first + (uint64_t)count > 0xFFFFFFFEull)
+    return set_err(L->ctx, LQCD_ERR_INVALID_ARG, "loop_noises: noise indices reach the reserved 2^32-2 / 2^32-1");
+  std::vector<cd> pn;
+  lqcd_noise_info ni{};
+  LQCD_TRY(loop_noises(L, links, first, count, pn, &ni));
+  memcpy(per_noise_t, pn.data(), sizeof(cd) * pn.size());
+  if (info) *info = ni;
+  return ni.converged ? LQCD_OK
+                      : set_err(L->ctx, LQCD_ERR_NOT_CONVERGED, "loop_noises: a noise solve did not converge (rel %.3e)",
+                                ni.max_true_resid);
+}
+
+lqcd_status lqcd_loop_get(const lqcd_loop *L, lqcd_loop_info *out) {
+  if (!L || !out) return LQCD_ERR_INVALID_ARG;
+  const size_t Lt = L->ctx->dims[3];
+  if (out->addback) memcpy(out->addback, L->add.data(), sizeof(cd) * L->add.size());
+  if (out->lam) memcpy(out->lam, L->lam.data(), sizeof(cd) * L->lam.size());
+  if (out->poly_a) memcpy(out->poly_a, L->a.data(), sizeof(cd) * L->a.size());
+  if (out->xi_pert) memcpy(out->xi_pert, L->xi_p.data(), sizeof(cd) * L->xi_p.size());
+  if (out->xi_poly) memcpy(out->xi_poly, L->xi_q.data(), sizeof(cd) * L->xi_q.size());
+  (void)Lt;
+  out->Q = L->Q;
+  out->block = L->block;
+  out->matvecs_setup = L->matvecs;
+  out->seconds_setup = L->seconds;
+  out->eig_resid_max = L->eres;
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_loop_destroy(lqcd_loop *L) {
+  if (!L) return LQCD_ERR_INVALID_ARG;
+  if (L->ctx) cudaStreamSynchronize(L->ctx->stream);
+  delete L;
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *o,
+                               lqcd_estimate *out) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links || !o || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: NULL argument");
+  lqcd_loop *Lp = nullptr;
+  LQCD_TRY(loop_setup(ctx, links, kappa, o, &Lp));
+  std::unique_ptr<lqcd_loop> guard(Lp);
+  const int Lt = ctx->dims[3];
+  const int nn = o->nnoise;
+  std::vector<cd> per_noise_t;
+  lqcd_noise_info ni{};
+  LQCD_TRY(loop_noises(Lp, links, 0u, nn, per_noise_t, &ni));
   // 5. summary
+  const std::vector<cd> &add = Lp->add;
+  auto A = [&](int mode, int op, int t) -> const cd & { return add[((size_t)mode * 9 + op) * Lt + t]; };
   for (int mode = 0; mode < LQCD_NMODES; ++mode) {
     for (int op = 0; op < 9; ++op) {
       cd addtot = 0.0;
@@ -907,17 +1089,21 @@ extern "C" lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, do
       }
     }
   }
-  if (out->lam) memcpy(out->lam, lam.data(), sizeof(cd) * Q);
-  if (out->poly_a) memcpy(out->poly_a, a.data(), sizeof(cd) * a.size());
-  out->matvecs_setup = matvecs_setup + (long)Q * (o->K - 1 + o->npoly);
-  out->matvecs_noise = matvecs_noise;
-  out->seconds_setup = t1 - t0;
-  out->seconds_noise = t2 - t1;
-  out->max_true_resid = worst;
-  out->converged = conv;
-  out->block = bw;
-  return conv ? LQCD_OK : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop_estimate: a noise solve did not converge (rel %.3e)", worst);
+  if (out->lam) memcpy(out->lam, Lp->lam.data(), sizeof(cd) * Lp->Q);
+  if (out->poly_a) memcpy(out->poly_a, Lp->a.data(), sizeof(cd) * Lp->a.size());
+  out->matvecs_setup = Lp->matvecs;
+  out->matvecs_noise = ni.matvecs;
+  out->seconds_setup = Lp->seconds;
+  out->seconds_noise = ni.seconds;
+  out->max_true_resid = ni.max_true_resid;
+  out->converged = ni.converged;
+  out->block = ni.block;
+  return ni.converged ? LQCD_OK
+                      : set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop_estimate: a noise solve did not converge (rel %.3e)",
+                                ni.max_true_resid);
 }
+
+}  // extern "C"
 
 // ---- allocation-free contraction -------------------------------------------------------------
 // Some callers cannot allocate device memory at all: plug-ins whose host application owns every

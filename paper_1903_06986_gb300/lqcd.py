@@ -34,7 +34,7 @@ class LqcdError(RuntimeError):
 
 class KrylovOpts(C.Structure):
     _fields_ = [("m", C.c_int), ("k", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int),
-                ("system", C.c_int), ("prec", C.c_int), ("inner_tol", C.c_double)]
+                ("system", C.c_int), ("prec", C.c_int), ("inner_tol", C.c_double), ("eig_tol", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -49,7 +49,7 @@ class EstOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("nnoise", C.c_int), ("block", C.c_int), ("m", C.c_int), ("k", C.c_int),
                 ("m_inner", C.c_int), ("K", C.c_int), ("npoly", C.c_int), ("tol", C.c_double),
                 ("tol_special", C.c_double), ("max_cycles", C.c_int), ("modes", C.c_int), ("prec", C.c_int),
-                ("inner_tol", C.c_double)]
+                ("inner_tol", C.c_double), ("eig_tol", C.c_double), ("system", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -60,6 +60,20 @@ class Estimate(C.Structure):
                 ("lam", _dp), ("poly_a", _dp), ("matvecs_setup", C.c_long), ("matvecs_noise", C.c_long),
                 ("seconds_setup", C.c_double), ("seconds_noise", C.c_double), ("max_true_resid", C.c_double),
                 ("converged", C.c_int), ("block", C.c_int)]
+
+
+class LoopInfo(C.Structure):
+    _fields_ = [("addback", _dp), ("lam", _dp), ("poly_a", _dp), ("xi_pert", _dp), ("xi_poly", _dp),
+                ("Q", C.c_int), ("block", C.c_int), ("matvecs_setup", C.c_long), ("seconds_setup", C.c_double),
+                ("eig_resid_max", C.c_double)]
+
+
+class NoiseInfo(C.Structure):
+    _fields_ = [("matvecs", C.c_long), ("seconds", C.c_double), ("max_true_resid", C.c_double),
+                ("converged", C.c_int), ("block", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class Derivs(C.Structure):
@@ -107,6 +121,12 @@ def load(path=None):
         "lqcd_defl_info": [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
         "lqcd_defl_export": [vp, vp, vp, vp, vp, vp],
         "lqcd_defl_import": [vp, i, vp, vp, C.POINTER(vp)],
+        "lqcd_defl_import_space": [vp, i, vp, vp, i, C.POINTER(vp)],
+        "lqcd_loop_setup": [vp, vp, d, C.POINTER(EstOpts), C.POINTER(vp)],
+        "lqcd_loop_setup_from": [vp, vp, d, C.POINTER(EstOpts), vp, vp, vp, C.POINTER(vp)],
+        "lqcd_loop_noises": [vp, vp, u32, i, vp, C.POINTER(NoiseInfo)],
+        "lqcd_loop_get": [vp, C.POINTER(LoopInfo)],
+        "lqcd_loop_destroy": [vp],
         "lqcd_deflate_project": [vp, vp, vp, vp, i, vp],
         "lqcd_set_defl_engine": [vp, i],
         "lqcd_tc_vdag_x": [vp, vp, i, vp, i, vp],
@@ -203,6 +223,56 @@ class Defl:
     def close(self):
         if self.h:
             self.ctx.lib.lqcd_defl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Loop:
+    """The per-configuration setup of a loop estimate (lqcd_loop): noises can then be run in batches."""
+
+    def __init__(self, ctx, handle, opts, keep=()):
+        self.ctx = ctx
+        self.h = handle
+        self.opts = opts
+        self._keep = keep          # deflation objects the setup borrows
+
+    def noises(self, links, first, count):
+        """Noise terms [6 modes][count][9 ops][Lt] (complex) of noises first .. first+count-1, and the
+        lqcd_noise_info as a dict (with the call's status)."""
+        out = np.zeros((6, count, NOPS, self.ctx.dims[3]), dtype=np.complex128)
+        info = NoiseInfo()
+        st = self.ctx.lib.lqcd_loop_noises(self.h, _ptr(links), first, count, out.ctypes.data_as(C.c_void_p),
+                                           C.byref(info))
+        if st not in (OK, ERR_NOT_CONVERGED):
+            self.ctx._check(st)
+        d = info.as_dict()
+        d["status"] = st
+        return out, d
+
+    def info(self):
+        lt = self.ctx.dims[3]
+        q = self.opts.k
+        bufs = dict(addback=np.zeros((6, NOPS, lt), dtype=np.complex128), lam=np.zeros(4096, dtype=np.complex128),
+                    poly_a=np.zeros(self.opts.npoly + 1, dtype=np.complex128),
+                    xi_pert=np.zeros(4096, dtype=np.complex128), xi_poly=np.zeros(4096, dtype=np.complex128))
+        as_dp = lambda a: a.ctypes.data_as(_dp)
+        li = LoopInfo(*[as_dp(bufs[n]) for n in ("addback", "lam", "poly_a", "xi_pert", "xi_poly")], 0, 0, 0, 0.0, 0.0)
+        self.ctx._check(self.ctx.lib.lqcd_loop_get(self.h, C.byref(li)))
+        q = li.Q
+        for n in ("lam", "xi_pert", "xi_poly"):
+            bufs[n] = bufs[n][:q].copy()
+        bufs.update(Q=q, block=li.block, matvecs_setup=li.matvecs_setup, seconds_setup=li.seconds_setup,
+                    eig_resid_max=li.eig_resid_max)
+        return bufs
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.lqcd_loop_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -366,9 +436,9 @@ class Context:
         return out
 
     # GMRES-DR / MINRES-DR
-    def _krylov(self, fn, links, kappa, b, m, k, tol, max_cycles, system, want_defl, prec):
+    def _krylov(self, fn, links, kappa, b, m, k, tol, max_cycles, system, want_defl, prec, eig_tol=0.0):
         x = _torch().empty_like(b)
-        o = KrylovOpts(m, k, tol, max_cycles, system, prec)
+        o = KrylovOpts(m, k, tol, max_cycles, system, prec, 0.0, eig_tol)
         info = SolveInfo()
         dh = C.c_void_p()
         st = fn(self.h, _ptr(links), kappa, _ptr(b), _ptr(x), self._nrhs(b), C.byref(o), C.byref(info),
@@ -379,13 +449,14 @@ class Context:
         return x, info.as_dict(), defl
 
     def gmresdr_solve(self, links, kappa, b, m, k, tol, max_cycles=1000, system=SYS_M, want_defl=False,
-                      prec=PREC_F64):
+                      prec=PREC_F64, eig_tol=0.0):
         return self._krylov(self.lib.lqcd_gmresdr_solve, links, kappa, b, m, k, tol, max_cycles, system,
-                            want_defl, prec)
+                            want_defl, prec, eig_tol)
 
-    def minresdr_solve(self, links, kappa, b, m, k, tol, max_cycles=1000, want_defl=False, prec=PREC_F64):
+    def minresdr_solve(self, links, kappa, b, m, k, tol, max_cycles=1000, want_defl=False, prec=PREC_F64,
+                       eig_tol=0.0):
         return self._krylov(self.lib.lqcd_minresdr_solve, links, kappa, b, m, k, tol, max_cycles, SYS_MG5,
-                            want_defl, prec)
+                            want_defl, prec, eig_tol)
 
     # deflated multi-RHS solves
     def proj_solve(self, links, kappa, defl, b, m, tol, max_cycles=1000, system=SYS_M, prec=PREC_F64,
@@ -404,6 +475,41 @@ class Context:
         dh = C.c_void_p()
         self._check(self.lib.lqcd_defl_import(self.h, len(lamh), _ptr(E), lp, C.byref(dh)))
         return Defl(self, dh)
+
+    def defl_import_space(self, V, Hbar, hermitian=False):
+        """Deflation space from a (k+1)-vector basis V (device) and its (k+1) x k Hbar (host)."""
+        k = Hbar.shape[1]
+        H = np.ascontiguousarray(Hbar, dtype=np.complex128)
+        dh = C.c_void_p()
+        self._check(self.lib.lqcd_defl_import_space(self.h, k, _ptr(V), H.ctypes.data_as(C.c_void_p),
+                                                    1 if hermitian else 0, C.byref(dh)))
+        return Defl(self, dh)
+
+    # loop estimate in two phases
+    @staticmethod
+    def _est_opts(seed, nnoise, block, m, k, K, npoly, tol, tol_special, m_inner=0, max_cycles=2000, modes=SUB_ALL,
+                  prec=PREC_F64, inner_tol=0.0, eig_tol=0.0, system=SYS_M):
+        return EstOpts(seed, nnoise, block, m, k, m_inner, K, npoly, tol, tol_special, max_cycles, modes, prec,
+                       inner_tol, eig_tol, system)
+
+    def loop_setup(self, links, kappa, seed, nnoise, block, m, k, K, npoly, tol, tol_special, **kw):
+        """lqcd_loop_setup: special solves, polynomial, hopping traces, 1/xi', add-backs."""
+        o = self._est_opts(seed, nnoise, block, m, k, K, npoly, tol, tol_special, **kw)
+        h = C.c_void_p()
+        self._check(self.lib.lqcd_loop_setup(self.h, _ptr(links), kappa, C.byref(o), C.byref(h)))
+        return Loop(self, h, o)
+
+    def loop_setup_from(self, links, kappa, proj, eig, a, seed, nnoise, block, m, k, K, npoly, tol, tol_special, **kw):
+        """lqcd_loop_setup_from: the setup from given spaces (proj: Krylov space of M, eig: eigenpairs
+        of M') and Min-Res coefficients a (None: computed)."""
+        o = self._est_opts(seed, nnoise, block, m, k, K, npoly, tol, tol_special, **kw)
+        h = C.c_void_p()
+        ap = None
+        if a is not None:
+            ah, ap = _host_c(a)
+        self._check(self.lib.lqcd_loop_setup_from(self.h, _ptr(links), kappa, C.byref(o), proj.h, eig.h, ap,
+                                                  C.byref(h)))
+        return Loop(self, h, o, keep=(proj, eig))
 
     # deflation projection
     def deflate_project(self, defl, eta, d):
@@ -480,10 +586,11 @@ class Context:
 
     # whole path
     def loop_estimate(self, links, kappa, seed, nnoise, block, m, k, K, npoly, tol, tol_special,
-                      m_inner=0, max_cycles=2000, modes=SUB_ALL, prec=PREC_F64, inner_tol=0.0):
+                      m_inner=0, max_cycles=2000, modes=SUB_ALL, prec=PREC_F64, inner_tol=0.0, eig_tol=0.0,
+                      system=SYS_M):
         """lqcd_loop_estimate; block = 0 lets the autotuner pick the block width."""
         o = EstOpts(seed, nnoise, block, m, k, m_inner, K, npoly, tol, tol_special, max_cycles, modes, prec,
-                    inner_tol)
+                    inner_tol, eig_tol, system)
         bufs, est = _estimate_buffers(self.dims[3], nnoise, k, npoly)
         st = self.lib.lqcd_loop_estimate(self.h, _ptr(links), kappa, C.byref(o), C.byref(est))
         if st not in (OK, ERR_NOT_CONVERGED):
@@ -553,7 +660,8 @@ def batch_loop_estimate(problems):
     for i, p in enumerate(problems):
         opts[i] = EstOpts(p["seed"], p["nnoise"], p["block"], p["m"], p["k"], p.get("m_inner", 0), p["K"], p["npoly"],
                           p["tol"], p["tol_special"], p.get("max_cycles", 2000), p.get("modes", SUB_ALL),
-                          p.get("prec", PREC_F64), p.get("inner_tol", 0.0))
+                          p.get("prec", PREC_F64), p.get("inner_tol", 0.0), p.get("eig_tol", 0.0),
+                          p.get("system", SYS_M))
         bufs, est = _estimate_buffers(p["ctx"].dims[3], p["nnoise"], p["k"], p["npoly"])
         ests[i] = est
         keep.append(bufs)
@@ -588,11 +696,11 @@ def link_grad(ctx, links, kappa, z, x, scale=1.0, want_links=True):
 
 
 def loop_derivs(ctx, links, kappa, seed, nnoise, block, m, k, K, tol, tol_special, m_inner=0, max_cycles=2000,
-                prec=PREC_F64, want_grad=True, grad_scale=1.0, inner_tol=0.0):
+                prec=PREC_F64, want_grad=True, grad_scale=1.0, inner_tol=0.0, eig_tol=0.0):
     """lqcd_loop_derivs: d/dkappa of the NS and PS estimates of the nine operators, and the link
     gradient of the NS scalar estimate."""
     o = EstOpts(seed, nnoise, block, m, k, m_inner, K, 0, tol, tol_special, max_cycles, SUB_NONE | SUB_PERT, prec,
-                inner_tol)
+                inner_tol, eig_tol)
     dk = np.zeros((2, NOPS), dtype=np.complex128)
     err = np.zeros((2, NOPS), dtype=np.float64)
     per = np.zeros((2, nnoise, NOPS), dtype=np.complex128)

@@ -37,14 +37,15 @@ def test_loop_derivs_match_oracle():
     ctx = context(dims)
     U = synth.su3_links(dims, 0.45, 2)
     N = 6
-    g = lqcd.loop_derivs(ctx, dev(U), kappa, 5, N, 3, 40, 8, 7, 1e-12, 1e-13)
-    assert g["converged"] and g["max_true_resid"] <= 1e-12
-    ref = PL.loop_derivs(U, kappa, dims, 5, N, 40, 8, 7, 1e-12, 1e-13)
+    # solves to 3e-14: x, y = M^{-1} P x and z agree within a few cond(M)^2 * 3e-14 (cond ~ 13)
+    g = lqcd.loop_derivs(ctx, dev(U), kappa, 5, N, 3, 40, 8, 7, 3e-14, 1e-14)
+    assert g["converged"] and g["max_true_resid"] <= 3e-14
+    ref = PL.loop_derivs(U, kappa, dims, 5, N, 40, 8, 7, 3e-14, 1e-14)
     for mode in range(2):
         want = ref["per_noise"][mode]
         scale = np.abs(want).max(axis=0)
-        assert np.all(np.abs(g["per_noise"][mode] - want) <= 1e-8 * scale + 1e-10), mode
-    assert rel_err(host(g["link_grad"]), ref["link_grad"]) < 1e-8
+        assert np.all(np.abs(g["per_noise"][mode] - want) <= 1e-11 * scale), mode
+    assert rel_err(host(g["link_grad"]), ref["link_grad"]) < 1e-11
 
 
 @pytest.mark.parametrize("prec", [1, 2], ids=["fp32", "fp16"])

@@ -1,58 +1,163 @@
-"""GPU parity of the whole loop-estimate path (lqcd_loop_estimate) with the oracle pipeline, per
-noise, per operator and per subtraction mode (Sec. 5-7).
+"""GPU parity of the whole loop-estimate path with the oracle pipeline, per noise, per operator,
+per timeslice and per subtraction mode (Sec. 5-7), at 1e-11 relative.
 
-Deflation enters through Ritz vectors of the special solve; those are reproducible across
-rounding orders only once converged, so the all-mode parity case uses a lattice where the
-MINRES-DR eigenpairs converge (residuals <= 1e-10).  On the 4^4, kappa = 0.150 workload (GMRES-DR(20,5),
-10 noises, 4-term PS) the modes that do not depend on eigenvectors are compared to the same
-tolerance, and the deflated ones are checked for unbiasedness against the dense-LU trace."""
+Two kinds of comparison:
+  * the noise phase on the 4^4, kappa = 0.150 workload (GMRES-DR(20,5), 10 noises, 4-term PS,
+    degree-6 POLY) with the setup built from the oracle's own spaces and coefficients
+    (lqcd_defl_import_space, lqcd_defl_import, lqcd_loop_setup_from): every noise term and add-back
+    of all six modes at 1e-11.  On this workload the Ritz vectors of GMRES-DR(20,5) stay far from
+    converged (residuals ~1e-3 when the solve converges), and unconverged Ritz vectors are not
+    reproducible across rounding orders, so the special solves are compared separately (fixed
+    cycles, test_gpu_solvers.py) and here their outputs are shared;
+  * the fully independent path (lqcd_loop_estimate against oracle.pipeline.loop_estimate) on a
+    2^3 x 4 lattice where the eigenpairs super-converge (eig_tol): NS, PS, HFES and HFPS at 1e-11;
+    POLY and HFPOLY within the bound their Min-Res coefficients allow (the coefficients solve an
+    ill-conditioned least-squares problem, so two correct solvers agree on them only to
+    cond(v) * eps; both are checked to be minimisers), and on the 4^4 workload unbiasedness of
+    every mode against the dense-LU trace with NS and PS at 1e-11.
+"""
 import numpy as np
 import pytest
 
-from oracle import exact, operators as O, pipeline as PL
+from oracle import estimate as E, exact, lattice as L, operators as O, pipeline as PL, rng, subtract as S
 from paper_1903_06986_gb300 import synth
-from tests.gpu_util import context, dev
+from tests.gpu_util import context, dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["none", "pert", "poly", "defl", "defl_pert", "defl_poly"]
+MODES = E.MODES
+TOL = 1e-11     # relative parity of loop estimates (spec target for FP64)
+NTOL = 3e-14    # noise solves: two solutions within cond(M) * 2 NTOL of each other (cond <= 18 here)
 
 
-def run_both(dims, eps, lseed, kappa, seed, N, m, k, K, npoly, tol, tol_sp, block):
-    U = synth.su3_links(dims, eps, lseed)
+def oracle_noise_terms(U, kappa, dims, st, seed, first, count, m_inner, tol):
+    """[6][count][9][Lt] noise terms eta^dag Theta (x - tilde x) and [6][9][Lt] add-backs."""
+    xs, infos = PL.solve_noises(st, dims, seed, first, count, m_inner, tol)
+    assert all(i["converged"] for i in infos)
+    etas = rng.z4_block(seed, first, count, dims)
+    out = []
+    for mode in MODES:
+        ws = xs - np.stack([PL.subtraction_vector(mode, st, e) for e in etas])
+        out.append(E.noise_terms(U, kappa, etas, ws))
+    return np.stack(out)
+
+
+def assert_close_per_op(got, want, tol, what):
+    """|got - want| <= tol * (largest |want| of that operator) elementwise; arrays [..., op, t]."""
+    scale = np.abs(want).max(axis=tuple(i for i in range(want.ndim) if i != want.ndim - 2), keepdims=True)
+    scale = np.maximum(scale, 1e-300)
+    err = np.abs(got - want) / scale
+    assert err.max() <= tol, (what, float(err.max()), np.unravel_index(err.argmax(), err.shape))
+
+
+@pytest.fixture(scope="module")
+def workload_4x4():
+    dims, kappa, seed = (4, 4, 4, 4), 0.150, 1
+    U = synth.su3_links(dims, 0.3, 1)
+    st = PL.setup(U, kappa, dims, seed, 20, 5, 4, 6, 1e-14)
+    return dims, kappa, seed, U, st
+
+
+def test_noise_phase_all_modes_on_shared_setup(workload_4x4):
+    torch = torch_cuda()
+    dims, kappa, seed, U, st = workload_4x4
+    n, k, K, npoly = 10, 5, 4, 6
     ctx = context(dims)
-    g = ctx.loop_estimate(dev(U), kappa, seed, N, block, m, k, K, npoly, tol, tol_sp)
-    ref, st, _ = PL.loop_estimate(U, kappa, dims, seed, N, m, k, K, npoly, tol, tol_sp)
-    return U, g, ref, st
-
-
-def test_all_modes_converged_eigenpairs():
-    dims, kappa = (2, 2, 2, 4), 0.150
-    U, g, ref, st = run_both(dims, 0.45, 2, kappa, 5, 6, 80, 8, 7, 6, 1e-12, 1e-14, 4)
-    assert g["converged"] and g["max_true_resid"] <= 1e-12
-    assert np.max(st["eig_resid"]) < 1e-10
-    assert np.allclose(g["lam"], st["lam"], rtol=1e-10, atol=1e-13)
-    assert np.abs(g["poly_a"] - st["a"]).max() <= 1e-7 * np.abs(st["a"]).max()
+    Ud = dev(U)
+    V = dev(np.ascontiguousarray(st["defl_m"]["V"].T).reshape((k + 1,) + L.field_shape(dims)))
+    proj = ctx.defl_import_space(V, st["defl_m"]["Hbar"], hermitian=False)
+    Ev = dev(np.ascontiguousarray(st["Ev"].T).reshape((k,) + L.field_shape(dims)))
+    eig = ctx.defl_import(Ev, st["lam"])
+    loop = ctx.loop_setup_from(Ud, kappa, proj, eig, st["a"], seed, n, n, 20, k, K, npoly, NTOL, 1e-14)
+    info = loop.info()
+    # setup outputs: 1/xi' from the shared eigenvectors, add-backs of every mode
+    assert np.allclose(info["xi_pert"], st["xi_pert"], rtol=1e-12, atol=1e-14)
+    assert np.allclose(info["xi_poly"], st["xi_poly"], rtol=1e-12, atol=1e-14)
+    add = PL.addbacks(U, kappa, dims, st, K)
+    want_add = np.stack([O.per_t(add[m]) for m in MODES])
+    assert_close_per_op(info["addback"][1:], want_add[1:], TOL, "addback")
+    assert np.abs(info["addback"][0]).max() == 0.0
+    # noise phase in two batches (3 + 7), as a resumed run would do it
+    got_a, ia = loop.noises(Ud, 0, 3)
+    got_b, ib = loop.noises(Ud, 3, 7)
+    assert ia["converged"] and ib["converged"] and max(ia["max_true_resid"], ib["max_true_resid"]) <= NTOL
+    got = np.concatenate([got_a, got_b], axis=1)
+    want = oracle_noise_terms(U, kappa, dims, st, seed, 0, n, 20 - k, NTOL)
     for i, mode in enumerate(MODES):
-        got = g["per_noise"][i]                      # [n, op]
-        want = ref[mode]["per_noise"]                # [n, op]
-        scale = np.abs(want).max(axis=0)
-        assert np.all(np.abs(got - want) <= 1e-9 * scale + 1e-12), mode
-        assert np.allclose(g["addback"][i], ref[mode]["addback_t"], rtol=1e-9, atol=1e-10), mode
-        assert np.allclose(g["stderr"][i], ref[mode]["stderr"], rtol=1e-7, atol=1e-12), mode
+        assert_close_per_op(got[i], want[i], TOL, mode)
+    loop.close()
+    proj.close()
+    eig.close()
+    torch.cuda.synchronize()
 
 
-def test_4x4_workload():
-    dims, kappa = (4, 4, 4, 4), 0.150
-    U, g, ref, st = run_both(dims, 0.3, 1, kappa, 1, 10, 20, 5, 4, 6, 1e-12, 1e-14, 10)
-    assert g["converged"] and g["max_true_resid"] <= 1e-12
-    for i, mode in enumerate(MODES[:3]):
+def test_4x4_workload_independent_setup(workload_4x4):
+    """lqcd_loop_estimate end to end on the 4^4 workload: NS and PS per noise at 1e-11 (they do not
+    depend on Ritz vectors), every mode unbiased for the dense-LU trace within 5 standard errors."""
+    dims, kappa, seed, U, st = workload_4x4
+    ctx = context(dims)
+    g = ctx.loop_estimate(dev(U), kappa, seed, 10, 10, 20, 5, 4, 6, NTOL, 1e-14)
+    assert g["converged"] and g["max_true_resid"] <= NTOL
+    ref, _, _ = PL.loop_estimate(U, kappa, dims, seed, 10, 20, 5, 4, 6, NTOL, 1e-14)
+    for i, mode in enumerate(MODES[:2]):
         got, want = g["per_noise"][i], ref[mode]["per_noise"]
         scale = np.abs(want).max(axis=0)
-        assert np.all(np.abs(got - want) <= 1e-9 * scale + 1e-12), mode
+        assert np.all(np.abs(got - want) <= TOL * scale), mode
     exact_tr = exact.exact_traces(U, kappa, dims)
     for i, mode in enumerate(MODES):
         for op in range(O.NOPS):
             sig = exact_tr[op].real if O.OP_PART[op] == 0 else exact_tr[op].imag
             est = g["mean"][i, op].real if O.OP_PART[op] == 0 else g["mean"][i, op].imag
             assert abs(est - sig) <= 5 * g["stderr"][i, op] + 1e-9, (mode, op)
+
+
+def test_all_modes_independent_with_super_converged_eigenpairs():
+    dims, kappa, seed = (2, 2, 2, 4), 0.150, 5
+    N, m, k, K, npoly = 6, 80, 8, 7, 6
+    U = synth.su3_links(dims, 0.45, 2)
+    ctx = context(dims)
+    g = ctx.loop_estimate(dev(U), kappa, seed, N, 4, m, k, K, npoly, NTOL, 1e-14, eig_tol=1e-13)
+    ref, st, _ = PL.loop_estimate(U, kappa, dims, seed, N, m, k, K, npoly, NTOL, 1e-14, eig_tol=1e-13)
+    assert g["converged"] and g["max_true_resid"] <= NTOL
+    assert np.max(st["eig_resid"]) <= 1e-13
+    assert np.allclose(g["lam"], st["lam"], rtol=1e-12, atol=1e-14)
+    # the two polynomials are both minimisers of ||b - M P(M) b|| (Sec. 5.2): equal residual norms
+    A = lambda f: L.wilson(U, kappa, f)
+    b = rng.z4_noise(seed, rng.NOISE_POLY, dims)
+    res = lambda a: np.linalg.norm(b - A(S.poly_apply(A, a, b)))
+    assert abs(res(g["poly_a"]) - res(st["a"])) <= 1e-12 * res(st["a"])
+    # bound on the POLY modes from the coefficients' conditioning: cond(v) * eps, v the Krylov powers
+    cols, w = [], b
+    for _ in range(npoly + 1):
+        w = A(w)
+        cols.append(w.ravel())
+    cond_v = np.linalg.cond(np.stack(cols, axis=1))
+    poly_tol = max(TOL, 10 * cond_v * np.finfo(float).eps)
+    for i, mode in enumerate(MODES):
+        tol = poly_tol if mode in ("poly", "defl_poly") else TOL
+        got, want = g["per_noise"][i], ref[mode]["per_noise"]
+        scale = np.abs(want).max(axis=0)
+        assert np.all(np.abs(got - want) <= tol * scale), (mode, tol)
+        assert_close_per_op(g["addback"][i], ref[mode]["addback_t"], tol, mode) if i > 0 else None
+        assert np.allclose(g["stderr"][i], ref[mode]["stderr"], rtol=1e3 * tol, atol=1e-13), mode
+
+
+def test_hermitian_path_independent():
+    """LQCD_SYS_MG5: one MINRES-DR space for eigenpairs and noise solves (M' y = eta, x = gamma_5 y)
+    against the oracle's Hermitian path, all modes but the POLY ones at 1e-11 per noise."""
+    dims, kappa, seed = (2, 2, 2, 4), 0.150, 5
+    N, m, k, K, npoly = 6, 80, 8, 7, 6
+    U = synth.su3_links(dims, 0.45, 2)
+    ctx = context(dims)
+    from paper_1903_06986_gb300 import lqcd
+    g = ctx.loop_estimate(dev(U), kappa, seed, N, 3, m, k, K, npoly, NTOL, 1e-14, eig_tol=1e-13,
+                          system=lqcd.SYS_MG5)
+    ref, st, _ = PL.loop_estimate(U, kappa, dims, seed, N, m, k, K, npoly, NTOL, 1e-14, eig_tol=1e-13,
+                                  system="MG5")
+    assert g["converged"] and g["max_true_resid"] <= NTOL
+    for i, mode in enumerate(MODES):
+        if mode in ("poly", "defl_poly"):
+            continue
+        got, want = g["per_noise"][i], ref[mode]["per_noise"]
+        scale = np.abs(want).max(axis=0)
+        assert np.all(np.abs(got - want) <= TOL * scale), mode

@@ -236,3 +236,28 @@ def test_loop_derivs_unbiased_and_link_gradient(dense_ops, derivs):
         fd = (T(Dv.perturb_link(U, mu, site, a, h)) - T(Dv.perturb_link(U, mu, site, a, -h))) / (2 * h)
         got = derivs["link_grad"][(mu,) + site + (a,)]
         assert abs(got - fd) < 1e-6 * max(1.0, abs(fd)), (mu, site, a)
+
+
+def test_hermitian_path_solves_and_estimates(dense_ops):
+    """system="MG5": one MINRES-DR space serves the eigenpairs and the noise solves (M' y = eta,
+    x = gamma_5 y); the solutions are those of M x = eta and the per-noise values follow the same
+    dense formula."""
+    d = dense_ops
+    st = PL.setup(d["U"], KAPPA, DIMS, SEED, M_DR, K_DR, K_PS, NPOLY, 1e-14, system="MG5")
+    assert st["defl_m"] is not None and st["info_m"] is st["info_h"]
+    xs, infos = PL.solve_noises(st, DIMS, SEED, 2, 3, M_DR - K_DR, 1e-13)
+    cond = np.linalg.cond(d["M"])
+    for i in range(3):
+        assert infos[i]["converged"]
+        x = d["Minv"] @ L.flat(rng.z4_noise(SEED, 2 + i, DIMS))
+        assert np.linalg.norm(L.flat(xs[i]) - x) <= 10 * cond * 1e-13 * np.linalg.norm(x)
+    out, st2, _ = PL.loop_estimate(d["U"], KAPPA, DIMS, SEED, 3, M_DR, K_DR, K_PS, NPOLY, 1e-13, 1e-14,
+                                   system="MG5")
+    td = tilde_dense(d, st2)
+    for n in range(3):
+        eta = L.flat(rng.z4_noise(SEED, n, DIMS))
+        for mode in E.MODES:
+            for op in (0, 4, 8):
+                Th = d["thetas"][op]
+                ref = np.vdot(eta, Th @ (d["Minv"] - td[mode]) @ eta) + np.trace(Th @ td[mode])
+                assert abs(out[mode]["per_noise"][n, op] - ref) < 1e-9 * max(1.0, abs(ref)), (n, mode, op)
