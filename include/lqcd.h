@@ -277,6 +277,17 @@ lqcd_status lqcd_deflate_project(lqcd_ctx *ctx, const lqcd_defl *defl, const dou
  * are made on its first projection and kept until lqcd_defl_destroy.  LQCD_ERR_INVALID_ARG for an
  * unknown engine. */
 lqcd_status lqcd_set_defl_engine(lqcd_ctx *ctx, int engine);
+/* Bound, in seconds, of every device-side wait of the tensor-core kernels (their mbarrier pipeline
+ * waits): a wait that runs out makes the kernel record LQCD_ERR_TIMEOUT, stop issuing work, let the
+ * copies and MMAs it has in flight land (under a fixed 2 s bound of its own), free its tensor
+ * memory and return, so the call returns LQCD_ERR_TIMEOUT with the context still usable.  Default
+ * 2; LQCD_ERR_INVALID_ARG outside [1e-3, 60]. */
+lqcd_status lqcd_set_wait_limit(lqcd_ctx *ctx, double seconds);
+/* Failure injection for tests of that timeout path (it faults nothing): the next tensor-core
+ * contraction launched on this context has every CTA's loader stop issuing copies after `chunks`
+ * pipeline chunks, so its MMA warp waits on a stage that nothing fills until the wait limit runs
+ * out.  One-shot; chunks < 0 cancels. */
+lqcd_status lqcd_inject_tc_stall(lqcd_ctx *ctx, int chunks);
 /* G[q * nrhs + r] = E_q^dagger X_r on the tensor cores (one-shot: E is sliced on every call).
  * E: device, k x 12V complex128 vectors (vector-major); X: device, nrhs fields; G: device output,
  * k x nrhs complex128.  1 <= k <= 4096.  Returns LQCD_ERR_NONFINITE for a NaN / Inf input,

@@ -558,6 +558,31 @@ lqcd_status noise_launch(lqcd_ctx *ctx, uint64_t seed, uint32_t first, int nrhs,
   return launch_check(ctx, "noise_kernel", K_NOISE, (double)ctx->V * nrhs);
 }
 
+// ---- input check: NaN / Inf anywhere in an FP64 array ------------------------------------------
+namespace {
+__global__ void nonfinite_kernel(const double *__restrict__ x, long long n, unsigned *__restrict__ count) {
+  unsigned bad = 0;
+  for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT)
+    bad += isfinite(x[e]) ? 0u : 1u;
+  bad = __reduce_add_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(count, bad);
+}
+}  // namespace
+
+lqcd_status check_finite(lqcd_ctx *ctx, const double *x, long long n, const char *what) {
+  unsigned *cnt;
+  LQCD_TRY(ws_get(ctx, WS_SCAL, sizeof(double) * 2, (void **)&cnt));
+  LQCD_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned), ctx->stream));
+  kbegin(ctx);
+  nonfinite_kernel<<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(x, n, cnt);
+  LQCD_TRY(launch_check(ctx, "nonfinite_kernel", K_BLAS1, (double)n / 2));
+  unsigned h = 0;
+  LQCD_CUDA(ctx, cudaMemcpyAsync(&h, cnt, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+  LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h) return set_err(ctx, LQCD_ERR_NONFINITE, "%s: %u non-finite values", what, h);
+  return LQCD_OK;
+}
+
 extern "C" lqcd_status lqcd_noise_z4(lqcd_ctx *ctx, uint64_t seed, uint32_t first_noise, int nrhs, double *out) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
   if (!out || nrhs <= 0 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "noise_z4: bad arguments");

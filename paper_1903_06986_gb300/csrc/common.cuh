@@ -61,6 +61,8 @@ struct lqcd_ctx {
   std::vector<GraphEntry> graph_cache;
   int packed_nr;             // tuned right-hand sides per thread of the packed FP32 operator (0 = built in)
   int defl_engine;           // LQCD_DEFL_FP64 or LQCD_DEFL_TENSOR (deflation projections)
+  unsigned long long tc_wait_ns;  // bound of every tensor-core pipeline wait (lqcd_set_wait_limit)
+  int tc_stop_after;         // injected stall of the next tensor-core launch (-1: none)
 };
 
 struct lqcd_defl {
@@ -249,6 +251,9 @@ lqcd_status blas_to_f32(lqcd_ctx *ctx, const double2 *x, float2 *y, long long n)
 lqcd_status contract_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *eta,
                             const double2 *w, int nrhs, double2 *out_dev);
 lqcd_status noise_launch(lqcd_ctx *ctx, uint64_t seed, uint32_t first, int nrhs, double2 *out);
+// LQCD_ERR_NONFINITE (with a message naming what) when any of the n doubles at x is NaN or Inf;
+// synchronises the stream
+lqcd_status check_finite(lqcd_ctx *ctx, const double *x, long long n, const char *what);
 // Tensor-core split-precision contractions with k vectors E (tcdefl.cu): slices of E made once
 // (tc_slices_make, released by tc_slices_free), then G[q * nrhs + r] = <E_q, X_r> (tc_vhx) and
 // Y_r = sum_q E_q d_q C[q * nrhs + r] (tc_vc; d device k complex or NULL); all device pointers.

@@ -215,6 +215,9 @@ lqcd_status lqcd_ctx_create(lqcd_ctx **out, const int dims[4], int link_recon, v
   }
   c->graphs = true;
   c->packed_nr = 0;
+  c->defl_engine = LQCD_DEFL_FP64;
+  c->tc_wait_ns = 2000000000ull;
+  c->tc_stop_after = -1;
   c->cap_stream = nullptr;
   c->run_stream = nullptr;
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||

@@ -912,8 +912,10 @@ lqcd_status loop_noises(lqcd_loop *L, const double *links, uint32_t first0, int 
   return LQCD_OK;
 }
 
-lqcd_status loop_new(lqcd_ctx *ctx, double kappa, const lqcd_est_opts *o, lqcd_loop **out) {
+lqcd_status loop_new(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *o, lqcd_loop **out) {
   LQCD_TRY(check_est_opts(ctx, o));
+  if (!std::isfinite(kappa)) return set_err(ctx, LQCD_ERR_NONFINITE, "loop setup: kappa is not finite");
+  LQCD_TRY(check_finite(ctx, links, 72LL * ctx->V, "loop setup: gauge links"));
   lqcd_loop *L = new lqcd_loop();
   L->ctx = ctx;
   L->kappa = kappa;
@@ -929,7 +931,7 @@ lqcd_status loop_setup(lqcd_ctx *ctx, const double *links, double kappa, const l
   *out = nullptr;
   const double t0 = now_s();
   lqcd_loop *L = nullptr;
-  LQCD_TRY(loop_new(ctx, kappa, o, &L));
+  LQCD_TRY(loop_new(ctx, links, kappa, o, &L));
   std::unique_ptr<lqcd_loop> guard(L);
   const long long N = ctx->N;
   double2 *x0, *bs;
@@ -979,7 +981,7 @@ lqcd_status lqcd_loop_setup_from(lqcd_ctx *ctx, const double *links, double kapp
   if (!eig->E || eig->N != ctx->N) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_setup_from: eig has no eigenvectors of this lattice");
   const double t0 = now_s();
   lqcd_loop *L = nullptr;
-  LQCD_TRY(loop_new(ctx, kappa, opts, &L));
+  LQCD_TRY(loop_new(ctx, links, kappa, opts, &L));
   std::unique_ptr<lqcd_loop> guard(L);
   L->dm = const_cast<lqcd_defl *>(proj);
   L->dh = const_cast<lqcd_defl *>(eig);

@@ -73,7 +73,7 @@ constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_BLK = TC_M * TC_KCH * 2;  // bytes of a full 128-row slice block (8 KB)
 constexpr int TC_SMEM_MAX = 227 * 1024;
 constexpr int TC_SMEM_MIN = 120 * 1024;    // forces one CTA per SM (TMEM is allocated per CTA)
-constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // bound of every mbarrier wait
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // default bound of a pipeline wait; fixed bound of a drain
 
 // byte offset of element (row, k) of an R x 32 block in the core-matrix order above
 __host__ __device__ __forceinline__ int tile_off(int row, int k) {
@@ -414,15 +414,16 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 // Wait for the phase of the given parity; false if the CTA aborted or the wait ran out of time
-// (then the abort flag and the device error flag are set).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err) {
+// (after wait_ns; then the abort flag and the device error flag are set).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err,
+                                          unsigned long long wait_ns) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   for (unsigned it = 1;; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 255) == 0) {
       if (*abort_flag) return false;
-      if (gtimer() - t0 > TC_WAIT_NS) {
+      if (gtimer() - t0 > wait_ns) {
         *abort_flag = 1;
         atomicExch(err, (int)LQCD_ERR_TIMEOUT);
         return false;
@@ -430,7 +431,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
   }
 }
-// bounded wait used only while draining after an abort
+// bounded wait used only while draining after an abort (its own fixed bound, independent of the
+// configurable one, so that copies and MMAs in flight always land before the CTA exits)
 __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
   const unsigned long long t0 = gtimer();
   while (!mbar_try(bar, parity) && gtimer() - t0 < TC_WAIT_NS) {
@@ -509,6 +511,8 @@ struct TcArgs {
   int nb;                  // mode 1: complex columns (column 2r real part, 2r + 1 imaginary part)
   double *out;             // mode 1: out[r * m_valid + m]
   int *err;
+  unsigned long long wait_ns;  // bound of every pipeline wait (the context's setting)
+  int stop_after;          // failure injection: the loader stops after this many chunks (-1: never)
 };
 
 __host__ __device__ constexpr int tc_stage_bytes(int SB, int NP) { return TC_SA * TC_BLK + SB * NP * TC_KCH * 2; }
@@ -590,6 +594,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       uint32_t filled = 0;  // stages armed at least once (for the drain after an abort)
       constexpr uint32_t bbytes = (uint32_t)(SB * NP * TC_KCH * 2);
       bool ok = true;
+      int narmed = 0;
       for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
         int mt, sp, c0, c1;
         work_range(p, w, mt, sp, c0, c1);
@@ -598,12 +603,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         const unsigned char *abase = p.A + (size_t)mt * p.kc_count * TC_SA * TC_BLK;
         (void)sp;
         for (int c = c0; c < c1; ++c) {
-          if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.err)) { ok = false; break; }
+          // injected stall: stop arming stages, so the MMA warp waits on one that nothing fills
+          if (narmed == p.stop_after) { ok = false; break; }
+          if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
           const uint32_t sA = smem_u32(smem + (size_t)stage * sbytes);
           mbar_expect_tx(full0 + 8 * stage, TC_SA * ablk + bbytes);
           bulk_g2s(sA, abase + (size_t)c * TC_SA * ablk, TC_SA * ablk, full0 + 8 * stage);
           bulk_g2s(sA + TC_SA * TC_BLK, p.B + (size_t)c * bbytes, bbytes, full0 + 8 * stage);
           filled |= 1u << stage;
+          ++narmed;
           if (++stage == stages) { stage = 0; phase ^= 1; }
         }
       }
@@ -627,11 +635,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         const uint32_t ablk = (uint32_t)(r8 * TC_KCH * 2);
         for (int g0 = c0; g0 < c1 && ok; g0 += p.kcr) {
           const int g1 = min(c1, g0 + p.kcr);
-          if (!mbar_wait(acce0 + 8 * buf, accph[buf] ^ 1, abort_flag, p.err)) { ok = false; break; }
+          if (!mbar_wait(acce0 + 8 * buf, accph[buf] ^ 1, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
           tc_fence_after();
           const uint32_t dbase = tmem + (uint32_t)(buf * TC_NGRP * NP);
           for (int c = g0; c < g1; ++c) {
-            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) { ok = false; break; }
+            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
             tc_fence_after();
             const uint32_t sA = smem_u32(smem + (size_t)stage * sbytes), sB = sA + TC_SA * TC_BLK;
             // descriptors of the stage's first K step; later operands differ only in the start
@@ -702,7 +710,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       }
       for (int g0 = c0; g0 < c1; g0 += p.kcr) {
         // the whole warp leaves together (tcgen05.ld and the shuffles below are warp-collective)
-        if (!__all_sync(0xffffffffu, mbar_wait(accf0 + 8 * buf, accph[buf], abort_flag, p.err))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(accf0 + 8 * buf, accph[buf], abort_flag, p.err, p.wait_ns))) {
           ok = false;
           break;
         }
@@ -793,7 +801,11 @@ size_t tc_bytes_c(int k, long long L) {
   return (size_t)mt * kc * TC_SA * TC_BLK;
 }
 
-template <int NP, int SB, int MODE> lqcd_status tc_gemm_launch(lqcd_ctx *ctx, const TcArgs &a, double units) {
+template <int NP, int SB, int MODE> lqcd_status tc_gemm_launch(lqcd_ctx *ctx, const TcArgs &args, double units) {
+  TcArgs a = args;
+  a.wait_ns = ctx->tc_wait_ns;
+  a.stop_after = ctx->tc_stop_after;
+  ctx->tc_stop_after = -1;  // the injection is one-shot
   constexpr int sbytes = tc_stage_bytes(SB, NP);
   const int bar_bytes = 8 * (2 * 4 + 8) + 64;  // room for up to 4 stages of barriers + slot + flag
   int stages = std::min(4, (TC_SMEM_MAX - bar_bytes - 64) / sbytes);
@@ -1053,6 +1065,20 @@ extern "C" lqcd_status lqcd_tc_slice_bytes(const int dims[4], int k, size_t *byt
   const long long L = 24 * V;  // reals per field
   *bytes = tc_bytes_g(k, L) + tc_bytes_c(k, L) + sizeof(int) * (size_t)L +
            sizeof(int) * (k + 2) + sizeof(unsigned long long) * k + sizeof(int) * (k + 1);
+  return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_set_wait_limit(lqcd_ctx *ctx, double seconds) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (!(seconds >= 1e-3 && seconds <= 60.0))
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "set_wait_limit: seconds must be in [1e-3, 60]");
+  ctx->tc_wait_ns = (unsigned long long)(seconds * 1e9);
+  return LQCD_OK;
+}
+
+extern "C" lqcd_status lqcd_inject_tc_stall(lqcd_ctx *ctx, int chunks) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  ctx->tc_stop_after = chunks < 0 ? -1 : chunks;
   return LQCD_OK;
 }
 

@@ -129,6 +129,8 @@ def load(path=None):
         "lqcd_loop_destroy": [vp],
         "lqcd_deflate_project": [vp, vp, vp, vp, i, vp],
         "lqcd_set_defl_engine": [vp, i],
+        "lqcd_set_wait_limit": [vp, d],
+        "lqcd_inject_tc_stall": [vp, i],
         "lqcd_tc_vdag_x": [vp, vp, i, vp, i, vp],
         "lqcd_tc_v_c": [vp, vp, i, vp, i, vp],
         "lqcd_tc_slice_bytes": [C.POINTER(C.c_int), i, C.POINTER(C.c_size_t)],
@@ -521,6 +523,14 @@ class Context:
     def set_defl_engine(self, engine):
         """DEFL_FP64 (CUDA-core FP64) or DEFL_TENSOR (split-precision tcgen05) deflation projections."""
         self._check(self.lib.lqcd_set_defl_engine(self.h, engine))
+
+    def set_wait_limit(self, seconds):
+        """Bound of the tensor-core kernels' device-side waits (LQCD_ERR_TIMEOUT when one runs out)."""
+        self._check(self.lib.lqcd_set_wait_limit(self.h, seconds))
+
+    def inject_tc_stall(self, chunks):
+        """Failure injection (tests): the next tensor-core launch stops loading after `chunks` chunks."""
+        self._check(self.lib.lqcd_inject_tc_stall(self.h, chunks))
 
     def tc_vdag_x(self, E, X):
         """G[q, r] = <E_q, X_r> on the tensor cores; E (k, ...) and X (nrhs, ...) complex128 fields."""
