@@ -108,6 +108,28 @@ def wilson(U, kappa, psi):
     return psi - kappa * hop(U, psi)
 
 
+def wilson_at_sites(U, kappa, psi, sites):
+    """(M psi)(x) at the listed sites only, x = (t, z, y, x) tuples, from the definition of
+    Eq. xyz556 term by term (for checking operators on lattices too large for `wilson`):
+    psi(x) - kappa sum_mu [(1 - g_mu) U_mu(x) psi(x + mu) + (1 + g_mu) U_mu(x - mu)^dag psi(x - mu)].
+    psi: one field (T, Z, Y, X, 4, 3).  Returns (len(sites), 4, 3)."""
+    ext = psi.shape[:4]
+    out = []
+    for site in sites:
+        acc = np.zeros((4, 3), dtype=np.complex128)
+        for mu in range(4):
+            ax = SITE_AXIS[mu]
+            up = list(site)
+            up[ax] = (up[ax] + 1) % ext[ax]
+            dn = list(site)
+            dn[ax] = (dn[ax] - 1) % ext[ax]
+            fwd = psi[tuple(up)] @ U[(mu,) + tuple(site)].T          # U_mu(x) psi(x + mu), per spin
+            bwd = psi[tuple(dn)] @ U[(mu,) + tuple(dn)].conj()        # U_mu(x - mu)^dag psi(x - mu)
+            acc += (ONE4 - G[mu]) @ fwd + (ONE4 + G[mu]) @ bwd
+        out.append(psi[tuple(site)] - kappa * acc)
+    return np.array(out)
+
+
 def g5(psi):
     return spin_apply(G5, psi)
 

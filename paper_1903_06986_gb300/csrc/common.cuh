@@ -12,6 +12,15 @@
 #include <vector>
 
 #include "lqcd.h"
+#include <nvtx3/nvToolsExt.h>
+
+// NVTX range of one stage of the path (visible to profilers; a no-op without one attached)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // kernel classes for the optional per-class device timing (values of LQCD_K_* in lqcd.h)
 enum KClass { K_WILSON = 0, K_DOT, K_AXPY, K_COMBINE, K_NORM, K_CONTRACT, K_BLAS1, K_NOISE, K_PROBE, K_TENSOR, K_SLICE,

@@ -467,6 +467,7 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
   std::vector<char> rotated(nrhs, 0);
   for (int cyc = 0; cyc < o->max_cycles; ++cyc) {
     cycles = cyc + 1;
+    NvtxRange nv("GMRES-DR cycle");
     LQCD_TRY(arnoldi_run(A, j0, R, matvecs));
     // least squares per right-hand side, x += V_m d
     std::vector<cd> dcoef((size_t)m * nrhs, cd(0.0, 0.0));
@@ -630,7 +631,11 @@ lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const SD *Vd, const Mat &H
   const int k = Hk.c;
   const long long N = ctx->N, vs = (long long)nrhs * N;
   WorkspaceT<S> W;
-  LQCD_TRY(get_workspace(ctx, std::max(m, k + 1), 0, nrhs, W));
+  LQCD_TRY(get_workspace(ctx, m, 0, nrhs, W));
+  if ((size_t)(k + 2) * nrhs > (size_t)(m + 2) * (m + 2) * nrhs) {
+    // the projection's coefficients ((k + 1) x nrhs) need more than the cycle's; the basis does not
+    LQCD_TRY(ws_get(ctx, WS_COEF, sizeof(double2) * (size_t)(k + 2) * nrhs, (void **)&W.coef));
+  }
   SX *r_dev;
   LQCD_TRY(ws_get(ctx, WS_TMP1, sizeof(SX) * (size_t)vs, (void **)&r_dev));
   std::vector<Rhs> R(nrhs);
@@ -651,6 +656,7 @@ lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const SD *Vd, const Mat &H
   double worst = 0.0;
   for (int cyc = 0; cyc < max_cycles; ++cyc) {
     cycles = cyc + 1;
+    NvtxRange nv("GMRES-Proj cycle");
     // (i) projection over the deflation space: d = argmin ||V_{k+1}^H r - Hbar_k d||
     LQCD_TRY(blas_multidot(ctx, Vd, N, 0, k + 1, r_dev, N, nrhs, W.coef));
     std::vector<double2> cp;
@@ -832,6 +838,7 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
   int outer = 0, inner_cycles = 0;
   double worst = 0.0;
   bool conv = false;
+  NvtxRange nv("mixed-precision defect correction");
   for (outer = 0; outer <= MAX_OUTER; ++outer) {
     LQCD_TRY(blas_norms(ctx, r, N, nrhs, sc));
     LQCD_TRY(download(ctx, sc, rn, nrhs));

@@ -753,6 +753,7 @@ lqcd_status loop_finish_setup(lqcd_loop *L, const double2 *U, const double *link
   const lqcd_defl *dh = L->dh;
   L->Q = dh->k;
   const int Q = L->Q;
+  NvtxRange nv("loop setup: polynomial, traces, 1/xi', add-backs");
   if (a_given) {
     L->a.assign((const cd *)a_given, (const cd *)a_given + o->npoly + 1);
   } else {
@@ -844,6 +845,7 @@ lqcd_status loop_noises(lqcd_loop *L, const double *links, uint32_t first0, int 
   const long long N = ctx->N;
   const int modes = L->modes;
   const double t0 = now_s();
+  NvtxRange nv("noise phase");
   const lqcd_krylov_opts po = noise_solver_opts(o);
   const int bw = std::max(1, std::min(L->block, count));
   const long long bn = (long long)bw * N;
@@ -867,6 +869,7 @@ lqcd_status loop_noises(lqcd_loop *L, const double *links, uint32_t first0, int 
     const long long len = (long long)nb * N;
     LQCD_TRY(noise_launch(ctx, o->seed, first0 + (uint32_t)off, nb, eta));
     lqcd_solve_info pi{};
+    NvtxRange nvb("noise block: solve, subtractions, contractions");
     if (L->dm->hermitian) {
       // M' y = eta over the Hermitian space, x = gamma_5 y (y is free until the deflation vectors)
       const lqcd_status st = proj_core_entry(ctx, links, kappa, L->dm, eta, y, nb, &po, &pi);
@@ -942,6 +945,7 @@ lqcd_status loop_setup(lqcd_ctx *ctx, const double *links, double kappa, const l
   lqcd_krylov_opts ko{o->m, o->k, o->tol_special, o->max_cycles, LQCD_SYS_M, LQCD_PREC_F64, 0.0, o->eig_tol};
   lqcd_solve_info si{};
   lqcd_status st;
+  NvtxRange nv("loop setup: special right-hand side solves");
   if (o->system == LQCD_SYS_MG5) {
     // Hermitian path: MINRES-DR on M' alone gives both the eigenpairs and the noise solves' space
     st = lqcd_minresdr_solve(ctx, links, kappa, (const double *)bs, (double *)x0, 1, &ko, &si, &L->dh);

@@ -69,7 +69,7 @@ def test_batch_of_uneven_lattices_matches_single_runs_and_oracle():
     same problem run alone (same kernels, same data, deterministic reductions), and the smallest
     lattice matches the oracle's loop estimate."""
     shapes = [(2, 2, 2, 4), (4, 4, 2, 4), (2, 4, 4, 6)]
-    kw = dict(seed=7, nnoise=6, block=6, m=80, k=8, K=4, npoly=3, tol=3e-14, tol_special=1e-14, eig_tol=1e-13)
+    kw = dict(seed=7, nnoise=6, block=6, m=80, k=8, K=4, npoly=3, tol=1e-13, tol_special=1e-14, eig_tol=1e-13)
     probs, single = [], []
     for i, dims in enumerate(shapes):
         ctx = context(dims)
@@ -82,7 +82,7 @@ def test_batch_of_uneven_lattices_matches_single_runs_and_oracle():
         assert np.array_equal(r["per_noise"], s["per_noise"])
         assert np.array_equal(r["mean"], s["mean"])
     dims = shapes[0]
-    ref, _, _ = PL.loop_estimate(synth.su3_links(dims, 0.4, 20), KAPPA, dims, 7, 6, 80, 8, 4, 3, 3e-14, 1e-14,
+    ref, _, _ = PL.loop_estimate(synth.su3_links(dims, 0.4, 20), KAPPA, dims, 7, 6, 80, 8, 4, 3, 1e-13, 1e-14,
                                  eig_tol=1e-13)
     for mi, mode in enumerate(E.MODES):
         # the Min-Res coefficients (POLY modes) agree only to cond(v) * eps; the other modes at 1e-11
