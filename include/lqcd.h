@@ -134,8 +134,9 @@ lqcd_status lqcd_timing_enable(lqcd_ctx *ctx, int enable);
 lqcd_status lqcd_timing_reset(lqcd_ctx *ctx);
 lqcd_status lqcd_timing_read(lqcd_ctx *ctx, int cls, double *total_ms, long *launches, double *units);
 /* Compulsory device-memory bytes (every operand element read or written once) summed over the
- * timed launches of one class since the last reset, for the classes whose launches record them
- * (DOT; 0 for the others).  Synchronises the stream like lqcd_timing_read. */
+ * timed launches of one class since the last reset, for the launches that record them (Wilson
+ * operators, DOT, AXPY, COMBINE, NORM and the basis scaling of BLAS1; other launches add 0).
+ * Synchronises the stream like lqcd_timing_read. */
 lqcd_status lqcd_timing_bytes(lqcd_ctx *ctx, int cls, double *bytes);
 
 /* ---- Z(4) noise (Sec. 2, 3) ------------------------------------------------------- */
@@ -465,6 +466,9 @@ lqcd_status lqcd_loop_setup_from(lqcd_ctx *ctx, const double *links, double kapp
  * still written) when a noise solve stopped at max_cycles above tol. */
 lqcd_status lqcd_loop_noises(lqcd_loop *loop, const double *links, uint32_t first, int count, double *per_noise_t,
                              lqcd_noise_info *info);
+/* Solver precision of the noise phase from now on (prec, inner_tol as in lqcd_est_opts; the setup
+ * itself is FP64 whatever the precision), and its block width (0 keeps the current one). */
+lqcd_status lqcd_loop_set_noise_opts(lqcd_loop *loop, int prec, double inner_tol, int block);
 /* Outputs of a setup (host), see lqcd_loop_info. */
 lqcd_status lqcd_loop_get(const lqcd_loop *loop, lqcd_loop_info *out);
 lqcd_status lqcd_loop_destroy(lqcd_loop *loop);

@@ -433,7 +433,7 @@ lqcd_status blas_norms(lqcd_ctx *ctx, const S *x, long long n, int nrhs, double 
   LQCD_TRY(reduction_counters(ctx, nrhs, &cnt));
   kbegin(ctx);
   norm_kernel<S><<<dim3(nb, nrhs), BT, 0, ctx->stream>>>(x, n, 1.0 / store_sigma<S>(ctx->N), (double *)p, cnt, norms);
-  return launch_check(ctx, "norm_kernel", K_NORM, (double)n * nrhs);
+  return launch_check_bytes(ctx, "norm_kernel", K_NORM, (double)n * nrhs, (double)sizeof(S) * n * nrhs);
 }
 
 static int multidot_chunks(lqcd_ctx *ctx, long long n, int nrhs, int nvec) {
@@ -486,7 +486,10 @@ lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const SV *V, long long vstride, long l
   kbegin(ctx);
   multiaxpy_kernel<SV, SW><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, h, fac, w, n,
                                                                                 nrhs);
-  return launch_check(ctx, "multiaxpy_kernel", K_AXPY, (double)n * nrhs * nvec);
+  // compulsory bytes: every basis vector once (per right-hand side when the bases differ), w read
+  // and written once
+  const double bytes = (double)sizeof(SV) * n * nvec * (vrs != 0 ? nrhs : 1) + 2.0 * sizeof(SW) * n * nrhs;
+  return launch_check_bytes(ctx, "multiaxpy_kernel", K_AXPY, (double)n * nrhs * nvec, bytes);
 }
 
 template <typename SV, typename SO>
@@ -498,14 +501,15 @@ lqcd_status blas_combine(lqcd_ctx *ctx, const SV *V, long long vstride, long lon
   kbegin(ctx);
   combine_kernel<SV, SO><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, C, ncol, fac, out,
                                                                               ostride, n, nrhs);
-  return launch_check(ctx, "combine_kernel", K_COMBINE, (double)n * nrhs * nvec * ncol);
+  const double bytes = (double)sizeof(SV) * n * nvec * (vrs != 0 ? nrhs : 1) + (double)sizeof(SO) * n * ncol * nrhs;
+  return launch_check_bytes(ctx, "combine_kernel", K_COMBINE, (double)n * nrhs * nvec * ncol, bytes);
 }
 
 template <typename S>
 lqcd_status blas_invscale(lqcd_ctx *ctx, S *x, const double *s, long long n, int nrhs) {
   kbegin(ctx);
   invscale_kernel<S><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(x, s, n);
-  return launch_check(ctx, "invscale_kernel", K_BLAS1, (double)n * nrhs);
+  return launch_check_bytes(ctx, "invscale_kernel", K_BLAS1, (double)n * nrhs, 2.0 * sizeof(S) * n * nrhs);
 }
 
 lqcd_status blas_demote(lqcd_ctx *ctx, const double2 *x, const double *s, float2 *y, long long n, int nrhs) {

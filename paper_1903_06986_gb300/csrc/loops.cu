@@ -390,7 +390,9 @@ lqcd_status contract_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const
   kbegin(ctx);
   contract_kernel<<<dim3(nchunk * Lt, nrhs), CBT, 0, ctx->stream>>>(U, kappa, eta, w, d[0], d[1], d[2], d[3], nchunk,
                                                                    (double2 *)p);
-  LQCD_TRY(launch_check(ctx, "contract_kernel", K_CONTRACT, (double)ctx->V * nrhs));
+  // compulsory bytes: eta and w once, the links once (point-split operators)
+  LQCD_TRY(launch_check_bytes(ctx, "contract_kernel", K_CONTRACT, (double)ctx->V * nrhs,
+                              2.0 * nrhs * ctx->N * sizeof(double2) + 36.0 * ctx->V * sizeof(double2)));
   const int tot = nrhs * 9 * Lt;
   kbegin(ctx);
   contract_final<<<ceil_div(tot, 128), 128, 0, ctx->stream>>>((const double2 *)p, nchunk, Lt, nrhs, out_dev);
@@ -1009,6 +1011,16 @@ lqcd_status lqcd_loop_noises(lqcd_loop *L, const double *links, uint32_t first, 
   return ni.converged ? LQCD_OK
                       : set_err(L->ctx, LQCD_ERR_NOT_CONVERGED, "loop_noises: a noise solve did not converge (rel %.3e)",
                                 ni.max_true_resid);
+}
+
+lqcd_status lqcd_loop_set_noise_opts(lqcd_loop *L, int prec, double inner_tol, int block) {
+  if (!L || !L->ctx) return LQCD_ERR_INVALID_ARG;
+  if (prec < LQCD_PREC_F64 || prec > LQCD_PREC_BF16 || !(inner_tol >= 0.0 && inner_tol < 1.0) || block < 0)
+    return set_err(L->ctx, LQCD_ERR_INVALID_ARG, "loop_set_noise_opts: bad arguments");
+  L->o.prec = prec;
+  L->o.inner_tol = inner_tol;
+  if (block > 0) L->block = block;
+  return LQCD_OK;
 }
 
 lqcd_status lqcd_loop_get(const lqcd_loop *L, lqcd_loop_info *out) {

@@ -132,7 +132,9 @@ lqcd_status launch_mode(lqcd_ctx *ctx, const S *U, double kappa, const S *in, S 
     case 4: wilson_kernel<R, 4, S><<<grid, block, 0, ctx->stream>>>(U, in, out, kappa, d[0], d[1], d[2], d[3], ctx->V, g5mask); break;
     default: return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply: unknown flags %d", flags);
   }
-  return launch_check(ctx, "wilson_kernel", K_WILSON, (double)ctx->V * nrhs);
+  // compulsory bytes: each field read and written once, the links once
+  const double bytes = 2.0 * nrhs * ctx->V * 12 * sizeof(S) + 36.0 * ctx->V * sizeof(S);
+  return launch_check_bytes(ctx, "wilson_kernel", K_WILSON, (double)ctx->V * nrhs, bytes);
 }
 
 }  // namespace
@@ -639,7 +641,8 @@ lqcd_status pair_launch(lqcd_ctx *ctx, const float4 *U, double kappa, const void
     case LQCD_APPLY_HOP: wilson_pair_kernel<S, RECON, 3><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
     default: return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: unknown flags %d", flags);
   }
-  return launch_check(ctx, "wilson_pair_kernel", K_WILSON, (double)ctx->V * nrhs);
+  const double bytes = 2.0 * nrhs * ctx->V * 6 * sizeof(T) + 4.0 * ctx->V * (RECON == 12 ? 3 : 5) * 16;
+  return launch_check_bytes(ctx, "wilson_pair_kernel", K_WILSON, (double)ctx->V * nrhs, bytes);
 }
 
 template <typename S, int NR, int RECON>
@@ -664,7 +667,8 @@ lqcd_status packed_launch_nr(lqcd_ctx *ctx, const float4 *U, double kappa, const
     case LQCD_APPLY_HOP: wilson_packed_kernel<S, NR, RECON, 3><<<grid, bs, 0, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups); break;
     default: return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: unknown flags %d", flags);
   }
-  return launch_check(ctx, "wilson_packed_kernel", K_WILSON, (double)ctx->V * nrhs);
+  const double bytes = 2.0 * nrhs * ctx->V * 6 * sizeof(T) + 4.0 * ctx->V * (RECON == 12 ? 3 : 5) * 16;
+  return launch_check_bytes(ctx, "wilson_packed_kernel", K_WILSON, (double)ctx->V * nrhs, bytes);
 }
 
 }  // namespace

@@ -126,6 +126,7 @@ def load(path=None):
         "lqcd_loop_setup_from": [vp, vp, d, C.POINTER(EstOpts), vp, vp, vp, C.POINTER(vp)],
         "lqcd_loop_noises": [vp, vp, u32, i, vp, C.POINTER(NoiseInfo)],
         "lqcd_loop_get": [vp, C.POINTER(LoopInfo)],
+        "lqcd_loop_set_noise_opts": [vp, i, d, i],
         "lqcd_loop_destroy": [vp],
         "lqcd_deflate_project": [vp, vp, vp, vp, i, vp],
         "lqcd_set_defl_engine": [vp, i],
@@ -255,6 +256,10 @@ class Loop:
         d = info.as_dict()
         d["status"] = st
         return out, d
+
+    def set_noise_opts(self, prec, inner_tol=0.0, block=0):
+        """Precision (and block width, 0 = unchanged) of the noise solves from now on."""
+        self.ctx._check(self.ctx.lib.lqcd_loop_set_noise_opts(self.h, prec, inner_tol, block))
 
     def info(self):
         lt = self.ctx.dims[3]
