@@ -66,7 +66,7 @@ def test_tensor_core_wait_runs_out_then_recovers():
         ctx.set_wait_limit(0.0)
     assert e.value.status == lqcd.ERR_INVALID_ARG
     ctx.set_wait_limit(0.05)
-    ctx.inject_tc_stall(1)
+    ctx.inject_tc_stall(0)
     with pytest.raises(lqcd.LqcdError) as e:
         ctx.tc_vdag_x(Ed, X)
     assert e.value.status == lqcd.ERR_TIMEOUT and "timed out" in str(e.value)
@@ -78,7 +78,7 @@ def test_tensor_core_wait_runs_out_then_recovers():
     lam = np.linspace(0.1, 0.6, k).astype(np.complex128)
     defl = ctx.defl_import(Ed, lam)
     ctx.set_defl_engine(lqcd.DEFL_TENSOR)
-    ctx.inject_tc_stall(2)
+    ctx.inject_tc_stall(0)
     with pytest.raises(lqcd.LqcdError) as e:
         ctx.deflate_project(defl, X, 1.0 / lam)
     assert e.value.status == lqcd.ERR_TIMEOUT

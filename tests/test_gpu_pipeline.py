@@ -27,7 +27,8 @@ pytestmark = pytest.mark.gpu
 
 MODES = E.MODES
 TOL = 1e-11     # relative parity of loop estimates (spec target for FP64)
-NTOL = 3e-14    # noise solves: two solutions within cond(M) * 2 NTOL of each other (cond <= 18 here)
+NTOL = 3e-14    # noise solves: two solutions within cond(M) * 2 NTOL of each other (cond(M) <= 18 in these
+                # cases, which keeps 3e-14 above the rounding floor ~ eps cond(M) of a true residual)
 
 
 def oracle_noise_terms(U, kappa, dims, st, seed, first, count, m_inner, tol):
@@ -112,7 +113,8 @@ def test_4x4_workload_independent_setup(workload_4x4):
 
 
 def test_all_modes_independent_with_super_converged_eigenpairs():
-    dims, kappa, seed = (2, 2, 2, 4), 0.150, 5
+    # kappa = 0.12: cond(M) = 12.5 here, so true residuals of 3e-14 are above the rounding floor
+    dims, kappa, seed = (2, 2, 2, 4), 0.120, 5
     N, m, k, K, npoly = 6, 80, 8, 7, 6
     U = synth.su3_links(dims, 0.45, 2)
     ctx = context(dims)
@@ -145,7 +147,7 @@ def test_all_modes_independent_with_super_converged_eigenpairs():
 def test_hermitian_path_independent():
     """LQCD_SYS_MG5: one MINRES-DR space for eigenpairs and noise solves (M' y = eta, x = gamma_5 y)
     against the oracle's Hermitian path, all modes but the POLY ones at 1e-11 per noise."""
-    dims, kappa, seed = (2, 2, 2, 4), 0.150, 5
+    dims, kappa, seed = (2, 2, 2, 4), 0.120, 5
     N, m, k, K, npoly = 6, 80, 8, 7, 6
     U = synth.su3_links(dims, 0.45, 2)
     ctx = context(dims)
