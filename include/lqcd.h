@@ -64,8 +64,13 @@ typedef enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1, LQCD_PREC_F16 = 2, LQCD_PRE
 #define LQCD_SUB_DEFL (1 << 3)      /* HFES, Sec. 5.4                                       */
 #define LQCD_SUB_DEFL_PERT (1 << 4) /* HFPS, Sec. 5.5                                       */
 #define LQCD_SUB_DEFL_POLY (1 << 5) /* HFPOLY, Sec. 5.5                                     */
-#define LQCD_SUB_ALL 63
-#define LQCD_NMODES 6
+#define LQCD_SUB_ES (1 << 6)        /* ES, Sec. 5.3: Ritz pairs of M on the GMRES-DR space,
+                                       left vectors e_L(lambda) = gamma_5 e_R(lambda*) / conj(e_R(lambda*)^dag
+                                       gamma_5 e_R(lambda)); a mode whose conjugate partner is not
+                                       among the pairs is not subtracted; with LQCD_SYS_MG5 there is
+                                       no space of M and ES subtracts nothing (equals NS)        */
+#define LQCD_SUB_ALL 127
+#define LQCD_NMODES 7
 #define LQCD_NOPS 9 /* 0 scalar, 1-4 local vector mu = x,y,z,t, 5-8 point-split mu = x,y,z,t */
 
 typedef struct lqcd_ctx lqcd_ctx;
@@ -399,11 +404,11 @@ typedef struct {
 
 typedef struct {
   /* host arrays supplied by the caller (any may be NULL):                                   */
-  double *per_noise;  /* [6 modes][nnoise][9 ops] complex: eta^dag Theta (x - tilde x), summed */
-  double *per_t;      /* [6][9][Lt] complex: per-timeslice mean over noises of the noise term */
-  double *addback;    /* [6][9][Lt] complex: Tr(Theta tilde M^{-1}) per timeslice            */
-  double *mean;       /* [6][9] complex: estimate of Tr(Theta M^{-1})                         */
-  double *stderr_;    /* [6][9] double: error bar of the signal part (Re scalar, Im vectors)  */
+  double *per_noise;  /* [7 modes][nnoise][9 ops] complex: eta^dag Theta (x - tilde x), summed */
+  double *per_t;      /* [7][9][Lt] complex: per-timeslice mean over noises of the noise term */
+  double *addback;    /* [7][9][Lt] complex: Tr(Theta tilde M^{-1}) per timeslice            */
+  double *mean;       /* [7][9] complex: estimate of Tr(Theta M^{-1})                         */
+  double *stderr_;    /* [7][9] double: error bar of the signal part (Re scalar, Im vectors)  */
   double *lam;        /* [k] complex: eigenvalues lambda'_q of M' used for deflation          */
   double *poly_a;     /* [npoly+1] complex: Min-Res coefficients                              */
   /* filled by the library:                                                                  */
@@ -430,7 +435,7 @@ lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, double kappa,
 typedef struct lqcd_loop lqcd_loop;
 typedef struct {
   /* host arrays supplied by the caller (any may be NULL):                                   */
-  double *addback;    /* [6][9][Lt] complex: Tr(Theta tilde M^{-1}) per timeslice            */
+  double *addback;    /* [7][9][Lt] complex: Tr(Theta tilde M^{-1}) per timeslice            */
   double *lam;        /* [Q] complex: eigenvalues lambda'_q of M' used for deflation          */
   double *poly_a;     /* [npoly+1] complex: Min-Res coefficients                              */
   double *xi_pert;    /* [Q] complex: 1/xi'_q = e'_q^dag gamma_5 tilde M^{-1}_pert e'_q       */
@@ -460,7 +465,7 @@ lqcd_status lqcd_loop_setup(lqcd_ctx *ctx, const double *links, double kappa, co
 lqcd_status lqcd_loop_setup_from(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *opts,
                                  const lqcd_defl *proj, const lqcd_defl *eig, const double *a, lqcd_loop **out);
 /* Noise phase for Z(4) noises first .. first+count-1 of opts->seed (first + count <= 2^32-2):
- * per_noise_t (host, [6][count][9][Lt] complex) receives eta^dag Theta (x - tilde x) summed per
+ * per_noise_t (host, [7][count][9][Lt] complex) receives eta^dag Theta (x - tilde x) summed per
  * timeslice for the modes in opts->modes (zero for the others; add the add-back for the estimate).
  * links: the same gauge field as the setup.  info may be NULL.  LQCD_ERR_NOT_CONVERGED (results
  * still written) when a noise solve stopped at max_cycles above tol. */

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import operators as O
 
-MODES = ["none", "pert", "poly", "defl", "defl_pert", "defl_poly"]
+MODES = ["none", "pert", "poly", "defl", "defl_pert", "defl_poly", "es"]
 
 
 def noise_terms(U, kappa, etas, ws):

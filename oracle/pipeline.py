@@ -9,6 +9,9 @@ Test infrastructure (see ``oracle/__init__.py``).
      serves the noise solves, done on M' y = eta with x = gamma_5 y (reading: the paper moves to
      the Hermitian system and MINRES-DR at kappa_crit, Sec. 8; a field whose spectrum of M
      surrounds the origin needs that for the noise solves too);
+     ES (Sec. 5.3) uses the Rayleigh-Ritz pairs of M on the GMRES-DR space with left vectors from
+     gamma_5-hermiticity (subtract.es_left_vectors); on the Hermitian path there is no space of M
+     and ES subtracts nothing;
   2. Min-Res polynomial coefficients a from the noise NOISE_POLY (Sec. 5.2);
   3. hopping traces t_k by probing (Sec. 5.1); 1/xi'_q for HFPS and HFPOLY (Sec. 5.5);
   4. for every noise n: eta = Z(4) noise n, x = M^{-1} eta by GMRES-Proj, and for every mode the
@@ -46,7 +49,13 @@ def setup(U, kappa, dims, seed, m, k, K, npoly, tol_special, max_cycles=2000, ei
     poly = lambda f: S.poly_apply(Af, a, f)
     xi_p = S.xi_inverse(Ev, pert, dims)
     xi_q = S.xi_inverse(Ev, poly, dims)
+    es = None
+    if system == "M":
+        lam_m, Er, _ = Kr.ritz_pairs(defl_m, hermitian=False)
+        El, found = S.es_left_vectors(Er, lam_m, dims)
+        es = (Er[:, found], El[:, found], lam_m[found])
     return dict(A=A, Ap=Ap, system=system, defl_m=defl_m, info_m=info_m, info_h=info_h, lam=lam, Ev=Ev, eig_resid=eres,
+                es=es,
                 a=a, b=S.a_to_b(a), t=t, xi_pert=xi_p, xi_poly=xi_q, pert=pert, poly=poly)
 
 
@@ -58,6 +67,7 @@ def addbacks(U, kappa, dims, st, K):
                defl=S.defl_addback(U, kappa, Ev, 1 / lam, dims))
     add["defl_pert"] = add["pert"] + S.defl_addback(U, kappa, Ev, 1 / lam - st["xi_pert"], dims)
     add["defl_poly"] = add["poly"] + S.defl_addback(U, kappa, Ev, 1 / lam - st["xi_poly"], dims)
+    add["es"] = S.es_addback(U, kappa, *st["es"], dims) if st["es"] is not None else add["none"].copy()
     return add
 
 
@@ -75,6 +85,8 @@ def subtraction_vector(mode, st, eta):
         return st["pert"](eta) + S.defl_vector(Ev, 1 / lam - st["xi_pert"], eta)
     if mode == "defl_poly":
         return st["poly"](eta) + S.defl_vector(Ev, 1 / lam - st["xi_poly"], eta)
+    if mode == "es":
+        return S.es_vector(*st["es"], eta) if st["es"] is not None else np.zeros_like(eta)
     raise ValueError(mode)
 
 

@@ -544,7 +544,11 @@ static lqcd_status hop_traces_dev(lqcd_ctx *ctx, const double2 *U, double kappa,
   LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)K * B * 9 * Lt, (void **)&cd_dev));
   tr.assign((size_t)K * 9 * Lt, cd(0.0, 0.0));
   std::vector<double2> h;
-  const int cthreads = std::min(1024, ((9 * Lt + 31) / 32) * 32);
+  // one thread per (operator, timeslice), at most what the kernel's register use allows per block
+  // (the kernel strides over the rest)
+  cudaFuncAttributes fa;
+  LQCD_CUDA(ctx, cudaFuncGetAttributes(&fa, probe_contract_kernel));
+  const int cthreads = std::max(32, std::min(std::min(1024, fa.maxThreadsPerBlock) / 32 * 32, ((9 * Lt + 31) / 32) * 32));
   for (long long p0 = 0; p0 < nprobes; p0 += B) {
     const int nb = (int)std::min<long long>(B, nprobes - p0);
     kbegin(ctx);
@@ -716,10 +720,18 @@ struct lqcd_loop {
   lqcd_defl *dm = nullptr, *dh = nullptr;  // GMRES-Proj space of M; eigenpairs of M'
   bool own_m = false, own_h = false;
   std::vector<cd> a, bcoef, xi_p, xi_q, lam, dl, dlp, dlq;
-  std::vector<cd> add;  // [6][9][Lt]
+  std::vector<cd> add;  // [LQCD_NMODES][9][Lt]
+  // ES (Sec. 5.3): Ritz pairs (lambda_q, e_R^q) of M on dm; left vectors e_L^q = gamma_5 e_R^{p(q)} /
+  // conj(n_q) with lambda_p(q) = conj(lambda_q), n_q = (gamma_5 e_R^p)^dag e_R^q; es_coef[q] =
+  // 1 / (lambda_q n_q) (0 for a mode without a partner); g5E = gamma_5 e_R (k fields, device)
+  int es_k = 0, es_found = 0;
+  std::vector<int> es_perm;
+  std::vector<cd> es_coef;
+  double2 *g5E = nullptr;
   long matvecs = 0;
   double seconds = 0.0, eres = 0.0;
   ~lqcd_loop() {
+    if (g5E) cudaFree(g5E);
     if (own_m && dm) lqcd_defl_destroy(dm);
     if (own_h && dh) lqcd_defl_destroy(dh);
   }
@@ -741,6 +753,80 @@ lqcd_status check_est_opts(lqcd_ctx *ctx, const lqcd_est_opts *o) {
 lqcd_krylov_opts noise_solver_opts(const lqcd_est_opts *o) {
   return lqcd_krylov_opts{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec,
                           o->inner_tol, 0.0};
+}
+
+// ES data (Sec. 5.3, left vectors by gamma_5-hermiticity) from the Ritz pairs of M on L->dm, and the
+// ES add-back sum_q (1 / lambda_q) e_L^q^dag Theta e_R^q per timeslice into addES(op, t)
+template <typename F>
+lqcd_status es_setup(lqcd_loop *L, const double2 *U, F addES) {
+  lqcd_ctx *ctx = L->ctx;
+  const lqcd_defl *dm = L->dm;
+  const int k = dm->k, Lt = ctx->dims[3];
+  const long long N = ctx->N;
+  L->es_k = k;
+  L->es_perm.assign(k, 0);
+  L->es_coef.assign(k, cd(0.0, 0.0));
+  L->es_found = 0;
+  std::vector<char> found(k, 0);
+  for (int q = 0; q < k; ++q) {
+    const cd lq(dm->lam[q].x, dm->lam[q].y);
+    int best = 0;
+    double dist = INFINITY;
+    for (int p = 0; p < k; ++p) {
+      const double d = std::abs(cd(dm->lam[p].x, dm->lam[p].y) - std::conj(lq));
+      if (d < dist) { dist = d; best = p; }
+    }
+    L->es_perm[q] = best;
+    found[q] = dist <= 1e-8 * std::max(std::abs(lq), 1e-300);
+  }
+  if (cudaMalloc(&L->g5E, sizeof(double2) * (size_t)k * N) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, LQCD_ERR_OOM, "ES: allocation of the left-vector basis failed");
+  }
+  LQCD_TRY(blas_g5(ctx, dm->E, L->g5E, k));
+  double2 *P5, *h, *cdv;
+  LQCD_TRY(ws_get(ctx, WS_PROBE, sizeof(double2) * (size_t)k * N, (void **)&P5));
+  LQCD_TRY(ws_get(ctx, WS_EST1, sizeof(double2) * (size_t)k, (void **)&h));
+  LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)k * 9 * Lt, (void **)&cdv));
+  for (int q = 0; q < k; ++q) LQCD_TRY(blas_copy(ctx, L->g5E + (size_t)L->es_perm[q] * N, P5 + (size_t)q * N, N));
+  // n_q = <gamma_5 e_R^p(q), e_R^q>: the basis of right-hand side q is P5_q itself
+  LQCD_TRY(blas_multidot(ctx, P5, 0, N, 1, dm->E, N, k, h));
+  std::vector<double2> nh, dens;
+  LQCD_TRY(download_v(ctx, h, nh, (size_t)k));
+  LQCD_TRY(contract_launch(ctx, U, L->kappa, P5, dm->E, k, cdv));
+  LQCD_TRY(download_v(ctx, cdv, dens, (size_t)k * 9 * Lt));
+  for (int q = 0; q < k; ++q) {
+    const cd nq(nh[q].x, nh[q].y), lq(dm->lam[q].x, dm->lam[q].y);
+    if (!found[q] || std::abs(nq) == 0.0) continue;
+    L->es_coef[q] = 1.0 / (lq * nq);
+    ++L->es_found;
+    for (int op = 0; op < 9; ++op)
+      for (int t = 0; t < Lt; ++t) {
+        const double2 v = dens[((size_t)q * 9 + op) * Lt + t];
+        addES(op, t) += L->es_coef[q] * cd(v.x, v.y);
+      }
+  }
+  return LQCD_OK;
+}
+
+// y = sum_q e_R^q (1 / lambda_q) (e_L^q^dag eta) for nb fields (the ES subtraction vector)
+lqcd_status es_vector(lqcd_loop *L, const double2 *eta, double2 *y, int nb) {
+  lqcd_ctx *ctx = L->ctx;
+  const int k = L->es_k;
+  const long long N = ctx->N;
+  double2 *g;
+  LQCD_TRY(ws_get(ctx, WS_EST1, sizeof(double2) * (size_t)k * nb, (void **)&g));
+  LQCD_TRY(blas_multidot(ctx, L->g5E, N, 0, k, eta, N, nb, g));
+  std::vector<double2> gh, c((size_t)k * nb);
+  LQCD_TRY(download_v(ctx, g, gh, (size_t)k * nb));
+  for (int q = 0; q < k; ++q)
+    for (int r = 0; r < nb; ++r) {
+      const double2 v = gh[(size_t)L->es_perm[q] * nb + r];
+      const cd w = cd(v.x, v.y) * L->es_coef[q];
+      c[(size_t)q * nb + r] = make_double2(w.real(), w.imag());
+    }
+  LQCD_TRY(upload_v(ctx, c.data(), g, sizeof(double2) * c.size()));
+  return blas_combine(ctx, L->dm->E, N, 0, k, g, 1, y, N, N, nb);
 }
 
 // Steps 2-3 given the two spaces (L->dm, L->dh set): Min-Res coefficients (unless given), b_k,
@@ -801,6 +887,7 @@ lqcd_status loop_finish_setup(lqcd_loop *L, const double2 *U, const double *link
   }
   L->add.assign((size_t)LQCD_NMODES * 9 * Lt, cd(0.0, 0.0));
   auto A = [&](int mode, int op, int t) -> cd & { return L->add[((size_t)mode * 9 + op) * Lt + t]; };
+  if ((L->modes & LQCD_SUB_ES) && !L->dm->hermitian) LQCD_TRY(es_setup(L, U, [&](int op, int t) -> cd & { return A(6, op, t); }));
   for (int op = 0; op < 9; ++op)
     for (int t = 0; t < Lt; ++t) {
       cd pert = 0.0, poly = 0.0, e1 = 0.0, ep = 0.0, eq = 0.0;
@@ -894,9 +981,13 @@ lqcd_status loop_noises(lqcd_loop *L, const double *links, uint32_t first0, int 
       LQCD_TRY(blas_copy(ctx, x, w, len));
       if (mode == 1 || mode == 4) LQCD_TRY(scaled_acc(ctx, xp, w, cd(-1.0, 0.0), len));
       if (mode == 2 || mode == 5) LQCD_TRY(scaled_acc(ctx, xq, w, cd(-1.0, 0.0), len));
-      if (mode >= 3) {
+      if (mode >= 3 && mode <= 5) {
         const cd *dv = (mode == 3) ? L->dl.data() : (mode == 4 ? L->dlp.data() : L->dlq.data());
         LQCD_TRY(deflate_dev(ctx, L->dh, eta, y, nb, dv));
+        LQCD_TRY(scaled_acc(ctx, y, w, cd(-1.0, 0.0), len));
+      }
+      if (mode == 6 && L->es_found > 0) {
+        LQCD_TRY(es_vector(L, eta, y, nb));
         LQCD_TRY(scaled_acc(ctx, y, w, cd(-1.0, 0.0), len));
       }
       LQCD_TRY(contract_launch(ctx, U, kappa, eta, w, nb, cdv));

@@ -18,9 +18,10 @@ OK, ERR_INVALID_ARG, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA, ER
 PREC_F64, PREC_F32, PREC_F16, PREC_BF16 = 0, 1, 2, 3
 APPLY_M, APPLY_G5R, APPLY_DAG, APPLY_HOP = 0, 1, 2, 3
 SYS_M, SYS_MG5 = 0, 1
-SUB_NONE, SUB_PERT, SUB_POLY, SUB_DEFL, SUB_DEFL_PERT, SUB_DEFL_POLY = (1 << i for i in range(6))
-SUB_ALL = 63
-MODES = ["none", "pert", "poly", "defl", "defl_pert", "defl_poly"]
+SUB_NONE, SUB_PERT, SUB_POLY, SUB_DEFL, SUB_DEFL_PERT, SUB_DEFL_POLY, SUB_ES = (1 << i for i in range(7))
+SUB_ALL = 127
+MODES = ["none", "pert", "poly", "defl", "defl_pert", "defl_poly", "es"]
+NMODES = len(MODES)
 NOPS = 9
 KERNEL_CLASSES = ["wilson", "dot", "axpy", "combine", "norm", "contract", "blas1", "noise", "probe", "tensor", "slice"]
 DEFL_FP64, DEFL_TENSOR = 0, 1
@@ -247,7 +248,7 @@ class Loop:
     def noises(self, links, first, count):
         """Noise terms [6 modes][count][9 ops][Lt] (complex) of noises first .. first+count-1, and the
         lqcd_noise_info as a dict (with the call's status)."""
-        out = np.zeros((6, count, NOPS, self.ctx.dims[3]), dtype=np.complex128)
+        out = np.zeros((NMODES, count, NOPS, self.ctx.dims[3]), dtype=np.complex128)
         info = NoiseInfo()
         st = self.ctx.lib.lqcd_loop_noises(self.h, _ptr(links), first, count, out.ctypes.data_as(C.c_void_p),
                                            C.byref(info))
@@ -264,7 +265,7 @@ class Loop:
     def info(self):
         lt = self.ctx.dims[3]
         q = self.opts.k
-        bufs = dict(addback=np.zeros((6, NOPS, lt), dtype=np.complex128), lam=np.zeros(4096, dtype=np.complex128),
+        bufs = dict(addback=np.zeros((NMODES, NOPS, lt), dtype=np.complex128), lam=np.zeros(4096, dtype=np.complex128),
                     poly_a=np.zeros(self.opts.npoly + 1, dtype=np.complex128),
                     xi_pert=np.zeros(4096, dtype=np.complex128), xi_poly=np.zeros(4096, dtype=np.complex128))
         as_dp = lambda a: a.ctypes.data_as(_dp)
@@ -644,11 +645,11 @@ def probe_classes(dims, K):
 
 
 def _estimate_buffers(lt, nnoise, k, npoly):
-    bufs = dict(per_noise=np.zeros((6, nnoise, NOPS), dtype=np.complex128),
-                per_t=np.zeros((6, NOPS, lt), dtype=np.complex128),
-                addback=np.zeros((6, NOPS, lt), dtype=np.complex128),
-                mean=np.zeros((6, NOPS), dtype=np.complex128),
-                stderr=np.zeros((6, NOPS), dtype=np.float64),
+    bufs = dict(per_noise=np.zeros((NMODES, nnoise, NOPS), dtype=np.complex128),
+                per_t=np.zeros((NMODES, NOPS, lt), dtype=np.complex128),
+                addback=np.zeros((NMODES, NOPS, lt), dtype=np.complex128),
+                mean=np.zeros((NMODES, NOPS), dtype=np.complex128),
+                stderr=np.zeros((NMODES, NOPS), dtype=np.float64),
                 lam=np.zeros(k, dtype=np.complex128),
                 poly_a=np.zeros(npoly + 1, dtype=np.complex128))
     as_dp = lambda a: a.ctypes.data_as(_dp)

@@ -45,7 +45,9 @@ def dense_ops():
 
 @pytest.fixture(scope="module")
 def state(dense_ops):
-    return PL.setup(dense_ops["U"], KAPPA, DIMS, SEED, M_DR, K_DR, K_PS, NPOLY, 1e-14)
+    # super-converged (Ritz residuals <= 1e-12) so that the Ritz values of M come in conjugate pairs
+    # to the pairing tolerance of the ES left vectors
+    return PL.setup(dense_ops["U"], KAPPA, DIMS, SEED, M_DR, K_DR, K_PS, NPOLY, 1e-14, eig_tol=1e-12)
 
 
 def tilde_dense(d, st):
@@ -58,6 +60,11 @@ def tilde_dense(d, st):
     out = dict(none=np.zeros((n, n), dtype=np.complex128), pert=pert, poly=poly, defl=D(1 / lam))
     out["defl_pert"] = pert + D(1 / lam - st["xi_pert"])
     out["defl_poly"] = poly + D(1 / lam - st["xi_poly"])
+    if st["es"] is not None:
+        Er, El, lm = st["es"]
+        out["es"] = Er @ np.diag(1 / lm) @ El.conj().T
+    else:
+        out["es"] = np.zeros((n, n), dtype=np.complex128)
     return out
 
 
@@ -129,6 +136,21 @@ def test_subtraction_vectors_and_addbacks_are_the_dense_matrices(dense_ops, stat
         for op in range(O.NOPS):
             ref = np.trace(d["thetas"][op] @ td[mode])
             assert abs(add[mode][op].sum() - ref) < 1e-10 * max(1.0, abs(ref)), (mode, op)
+
+
+def test_es_space_gives_left_and_right_eigenvectors_of_the_dense_matrix(dense_ops, state):
+    """ES data of the setup (Sec. 5.3): Ritz pairs of M on the GMRES-DR space with left vectors from
+    gamma_5-hermiticity, every kept pair an eigen-triple of the dense M within its Ritz residual,
+    closed under conjugation, and e_L^dag e_R = 1."""
+    d, st = dense_ops, state
+    Er, El, lm = st["es"]
+    assert len(lm) >= 4
+    for q in range(len(lm)):
+        rr = np.linalg.norm(d["M"] @ Er[:, q] - lm[q] * Er[:, q])
+        rl = np.linalg.norm(El[:, q].conj() @ d["M"] - lm[q] * El[:, q].conj())
+        assert rr < 1e-10 and rl < 1e-8 * np.linalg.norm(El[:, q])
+        assert abs(np.vdot(El[:, q], Er[:, q]) - 1) < 1e-12
+        assert np.abs(lm - np.conj(lm[q])).min() <= 1e-8 * abs(lm[q])
 
 
 def test_solve_noises_solves_the_right_systems(dense_ops, state):

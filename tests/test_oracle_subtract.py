@@ -119,6 +119,19 @@ def pipeline():
     xt = dict(none=lambda f: 0 * f, pert=pert, poly=poly, defl=lambda f: S.defl_vector(Ev, 1 / lam, f))
     xt["defl_pert"] = lambda f: pert(f) + S.defl_vector(Ev, 1 / lam - xi_p, f)
     xt["defl_poly"] = lambda f: poly(f) + S.defl_vector(Ev, 1 / lam - xi_q, f)
+    # ES with the 8 smallest eigenpairs of M and their conjugate partners (Sec. 5.3)
+    lm, ER = np.linalg.eig(M)
+    order = np.argsort(np.abs(lm))
+    lm, ER = lm[order], ER[:, order]
+    EL, _ = S.es_left_vectors(ER, lm, DIMS)
+    sel = set(range(8))
+    for q in list(sel):
+        sel.add(int(np.argmin(np.abs(lm - np.conj(lm[q])))))
+    sel = sorted(sel)
+    ERs, ELs, ls = ER[:, sel], EL[:, sel], lm[sel]
+    tilde["es"] = ERs @ np.diag(1 / ls) @ ELs.conj().T
+    add["es"] = S.es_addback(U, kappa, ERs, ELs, ls, DIMS)
+    xt["es"] = lambda f: S.es_vector(ERs, ELs, ls, f)
     return dict(U=U, kappa=kappa, Minv=Minv, tilde=tilde, add=add, xt=xt)
 
 
