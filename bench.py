@@ -678,12 +678,18 @@ def main():
                 "avg_launch_ms": ms / max(nl, 1), "launches": nl,
                 "bytes_per_launch": tbytes.get(dom, 0.0) / max(nl, 1),
                 "breakdown_ms": {k: round(v[0], 2) for k, v in tm.items() if v[0] > 0},
+                "breakdown_launches": {k: v[1] for k, v in tm.items() if v[1] > 0},
                 "class_gbs": {k: round(tbytes[k] / (v[0] / 1000.0) / 1e9, 1) for k, v in tm.items()
                               if v[0] > 0 and tbytes.get(k, 0) > 0}}
     if tbytes.get(dom, 0) > 0 and ms > 0:
         roofline["achieved"] = tbytes[dom] / (ms / 1000.0) / 1e9
         roofline["frac"] = roofline["achieved"] / HBM_PEAK_GBS
 
+    info_lam_min = lam_min
+    loop.close()
+    ctx.close()
+    del Ud
+    torch.cuda.empty_cache()
     cfg2 = None if args.no_cfg2 else cfg2_fp64(torch)
     dslash = None if args.no_dslash else dslash_rates(torch)
     deflation = None
@@ -731,8 +737,6 @@ def main():
                 "estimate_vs_fp64": errors,
                 "cfg2_fp64": cfg2, "dslash": dslash, "deflation_tensor_cores": deflation, "batching": batching}
         print(json.dumps(line))
-    loop.close()
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

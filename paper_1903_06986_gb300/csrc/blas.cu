@@ -64,11 +64,13 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
   return v;
 }
 
-// Single-launch batched inner products.  The grid is (nchunk * ngroup, nrhs): block (c, g, r) sums
-// conj(V_i^r) w^r over element chunk c for the GROUP basis vectors of group g and writes
-// partial[(i * nrhs + r) * nchunk + c]; the last block to finish for right-hand side r (a counter
-// per r, reset by that block) adds the nchunk partials of every i in chunk order and writes
-// h[i * nrhs + r].  The result does not depend on block scheduling.
+// Single-launch batched inner products.  Block b = g + ngroup (r + nrhs c) (a 1-D grid: the groups
+// and right-hand sides of one element chunk are neighbours in launch order, so the chunk of w^r and,
+// with a basis shared by all right-hand sides, the chunk of every basis vector are read from DRAM
+// once and then from L2) sums conj(V_i^r) w^r over element chunk c for the GROUP basis vectors of
+// group g and writes partial[(i * nrhs + r) * nchunk + c]; the last block to finish for right-hand
+// side r (a counter per r, reset by that block) adds the nchunk partials of every i in chunk order
+// and writes h[i * nrhs + r].  The result does not depend on block scheduling.
 template <typename SV, typename SW>
 __global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, long long vstride, long long vrs,
                                                       int nvec, const SW *__restrict__ w, long long n, int nrhs,
@@ -76,9 +78,11 @@ __global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, 
                                                       unsigned *__restrict__ counters, double2 *__restrict__ h) {
   using C = Ar<SW>;
   static_assert(std::is_same<C, Ar<SV>>::value, "multidot: storage types of different arithmetic");
-  const int r = blockIdx.y;
-  const int c = blockIdx.x % nchunk;
-  const int i0 = (blockIdx.x / nchunk) * GROUP;
+  const int ngroup = (nvec + GROUP - 1) / GROUP;
+  const int g0 = blockIdx.x % ngroup;
+  const int r = (blockIdx.x / ngroup) % nrhs;
+  const int c = blockIdx.x / (ngroup * nrhs);
+  const int i0 = g0 * GROUP;
   const long long chunk = (n + nchunk - 1) / nchunk;
   const long long e0 = c * chunk;
   const long long e1 = min(n, e0 + chunk);
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, 
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(&counters[r], 1u) == (unsigned)(gridDim.x - 1));
+  if (threadIdx.x == 0) last = (atomicAdd(&counters[r], 1u) == (unsigned)(nchunk * ngroup - 1));
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -175,7 +179,9 @@ __global__ void __launch_bounds__(BT) norm_kernel(const S *__restrict__ x, long 
 }
 
 // w^r += sign * fac * sum_i V_i^r h[i * nrhs + r]; the coefficients of this right-hand side are
-// staged in shared memory (scaled and converted to the arithmetic type).
+// staged in shared memory (scaled and converted to the arithmetic type).  Block b = r + nrhs e
+// (1-D grid): the right-hand sides of one element tile are neighbours in launch order, so a basis
+// shared by all right-hand sides is read from DRAM once per tile.
 constexpr int AXPY_MAXV = 512;
 template <typename SV, typename SW>
 __global__ void __launch_bounds__(BT) multiaxpy_kernel(const SV *__restrict__ V, long long vstride,
@@ -183,10 +189,10 @@ __global__ void __launch_bounds__(BT) multiaxpy_kernel(const SV *__restrict__ V,
                                                        double sign, SW *__restrict__ w, long long n, int nrhs) {
   using C = Ar<SW>;
   __shared__ C coef[AXPY_MAXV];
-  const int r = blockIdx.y;
+  const int r = blockIdx.x % nrhs;
   for (int i = threadIdx.x; i < nvec; i += BT) coef[i] = from_d2<C>(cscale(h[(long long)i * nrhs + r], sign));
   __syncthreads();
-  const long long e = (long long)blockIdx.x * BT + threadIdx.x;
+  const long long e = (long long)(blockIdx.x / nrhs) * BT + threadIdx.x;
   if (e >= n) return;
   const SV *vp = V + r * vrs + e;
   C acc = ldc(w[r * n + e]);
@@ -205,8 +211,9 @@ __global__ void __launch_bounds__(BT) combine_kernel(const SV *__restrict__ V, l
                                                      long long n, int nrhs) {
   using C = Ar<SO>;
   __shared__ C coef[COMB_MAXV * CT];
-  const long long e = (long long)blockIdx.x * BT + threadIdx.x;
-  const int r = blockIdx.y;
+  // block b = r + nrhs e (1-D grid): a basis shared by the right-hand sides is read once per tile
+  const long long e = (long long)(blockIdx.x / nrhs) * BT + threadIdx.x;
+  const int r = blockIdx.x % nrhs;
   for (int c0 = 0; c0 < ncol; c0 += CT) {
     const int g = min(CT, ncol - c0);
     __syncthreads();
@@ -436,19 +443,29 @@ lqcd_status blas_norms(lqcd_ctx *ctx, const S *x, long long n, int nrhs, double 
   return launch_check_bytes(ctx, "norm_kernel", K_NORM, (double)n * nrhs, (double)sizeof(S) * n * nrhs);
 }
 
-static int multidot_chunks(lqcd_ctx *ctx, long long n, int nrhs, int nvec) {
+static int multidot_chunks(lqcd_ctx *ctx, long long n, int nrhs, int nvec, bool shared) {
   // element chunks of at least 8 elements per thread; enough blocks (chunks x vector groups x
-  // right-hand sides) to cover the SMs a few times
+  // right-hand sides) to cover the SMs a few times.  With a basis shared by several right-hand
+  // sides, also chunks short enough that the blocks in flight (about 8 per SM) touch at most ~32 MB
+  // of L2, so that the basis chunk is read from DRAM once for all of them.
   const int ngroup = (nvec + GROUP - 1) / GROUP;
   const long long max_chunks = std::max<long long>(1, n / (8LL * BT));
-  const long long want = std::max<long long>(1, (4LL * ctx->sms) / std::max<long long>(1, (long long)nrhs * ngroup));
+  long long want = std::max<long long>(1, (4LL * ctx->sms) / std::max<long long>(1, (long long)nrhs * ngroup));
+  if (shared && nrhs > 1) {
+    const long long per_chunk_blocks = (long long)nrhs * ngroup;
+    const long long chunks_in_flight = std::max<long long>(1, 8LL * ctx->sms / per_chunk_blocks);
+    const long long bytes_per_elem = 16LL * (nvec + nrhs);        // upper bound (FP64 storage)
+    const long long l2_chunk = std::max<long long>(8LL * BT, (32LL << 20) / (chunks_in_flight * bytes_per_elem));
+    want = std::max(want, (n + l2_chunk - 1) / l2_chunk);
+  }
   return (int)std::min<long long>(std::min(max_chunks, want), 4096);
 }
 
 lqcd_status blas_reserve(lqcd_ctx *ctx, long long n, int nrhs, int max_nvec) {
   size_t need = 0;
   for (int v = 1; v <= max_nvec; ++v)
-    need = std::max(need, sizeof(double2) * (size_t)multidot_chunks(ctx, n, nrhs, v) * nrhs * v);
+    need = std::max(need, sizeof(double2) * (size_t)std::max(multidot_chunks(ctx, n, nrhs, v, false),
+                                                             multidot_chunks(ctx, n, nrhs, v, true)) * nrhs * v);
   void *p = nullptr;
   unsigned *cnt = nullptr;
   LQCD_TRY(ws_get(ctx, WS_PARTIAL, need, &p));
@@ -461,15 +478,15 @@ lqcd_status blas_multidot(lqcd_ctx *ctx, const SV *V, long long vstride, long lo
                           long long n, int nrhs, double2 *h) {
   if (nvec <= 0) return LQCD_OK;
   const int ngroup = (nvec + GROUP - 1) / GROUP;
-  const int nchunk = multidot_chunks(ctx, n, nrhs, nvec);
-  if ((long long)nchunk * ngroup > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "multidot: too many vectors");
+  const int nchunk = multidot_chunks(ctx, n, nrhs, nvec, vrs == 0);
+  if ((long long)nchunk * ngroup * nrhs > 0x7fffffffLL) return set_err(ctx, LQCD_ERR_INVALID_ARG, "multidot: grid too large");
   void *p = nullptr;
   unsigned *cnt = nullptr;
   LQCD_TRY(ws_get(ctx, WS_PARTIAL, sizeof(double2) * (size_t)nchunk * nrhs * nvec, &p));
   LQCD_TRY(reduction_counters(ctx, nrhs, &cnt));
   const double fac = 1.0 / (store_sigma<SV>(ctx->N) * store_sigma<SW>(ctx->N));
   kbegin(ctx);
-  multidot_kernel<SV, SW><<<dim3(nchunk * ngroup, nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs,
+  multidot_kernel<SV, SW><<<(unsigned)((long long)nchunk * ngroup * nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs,
                                                                                 nchunk, fac, (double2 *)p, cnt, h);
   // compulsory bytes: every basis vector once (once per right-hand side when the bases differ),
   // every w once
@@ -484,8 +501,8 @@ lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const SV *V, long long vstride, long l
   if (nvec > AXPY_MAXV) return set_err(ctx, LQCD_ERR_INVALID_ARG, "multiaxpy: at most %d vectors", AXPY_MAXV);
   const double fac = sign * store_sigma<SW>(ctx->N) / store_sigma<SV>(ctx->N);
   kbegin(ctx);
-  multiaxpy_kernel<SV, SW><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, h, fac, w, n,
-                                                                                nrhs);
+  multiaxpy_kernel<SV, SW><<<(unsigned)((long long)ceil_div(n, BT) * nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec,
+                                                                                                h, fac, w, n, nrhs);
   // compulsory bytes: every basis vector once (per right-hand side when the bases differ), w read
   // and written once
   const double bytes = (double)sizeof(SV) * n * nvec * (vrs != 0 ? nrhs : 1) + 2.0 * sizeof(SW) * n * nrhs;
@@ -499,8 +516,9 @@ lqcd_status blas_combine(lqcd_ctx *ctx, const SV *V, long long vstride, long lon
   if (nvec > COMB_MAXV) return set_err(ctx, LQCD_ERR_INVALID_ARG, "combine: at most %d vectors", COMB_MAXV);
   const double fac = store_sigma<SO>(ctx->N) / store_sigma<SV>(ctx->N);
   kbegin(ctx);
-  combine_kernel<SV, SO><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, C, ncol, fac, out,
-                                                                              ostride, n, nrhs);
+  combine_kernel<SV, SO><<<(unsigned)((long long)ceil_div(n, BT) * nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, C,
+                                                                                              ncol, fac, out, ostride,
+                                                                                              n, nrhs);
   const double bytes = (double)sizeof(SV) * n * nvec * (vrs != 0 ? nrhs : 1) + (double)sizeof(SO) * n * ncol * nrhs;
   return launch_check_bytes(ctx, "combine_kernel", K_COMBINE, (double)n * nrhs * nvec * ncol, bytes);
 }
