@@ -42,6 +42,7 @@ M_DR, K_DR, M_INNER = 240, 200, 40
 K_PS, NPOLY = 7, 6
 TOL, TOL_SPECIAL = 1e-10, 1e-12
 MAX_CYCLES = 400
+PREC_DEGREE = 0            # polynomial preconditioning of the noise solves (Krylov on M' p(M'))
 WORKLOAD = ("24^3x32 kappa 0.157 (plaquette 0.600), 100 Z4 noises in steps of 10, MINRES-DR(240,200) on M gamma_5, "
             "Q=200, GMRES-Proj(40) noise solves in FP16 storage / FP32 arithmetic inside FP64 defect correction to "
             "1e-10, PS K=7, POLY n=6, HFES on tensor cores, 6 modes x 9 operators")
@@ -68,6 +69,8 @@ def parse():
     ap.add_argument("--no-defl", action="store_true")
     ap.add_argument("--no-cfg2", action="store_true")
     ap.add_argument("--batch", action="store_true", help="also measure the uneven multi-lattice batch")
+    ap.add_argument("--prec-degree", type=int, default=PREC_DEGREE,
+                    help="degree of the polynomial preconditioner of the noise solves (0 = none)")
     ap.add_argument("--case", default=None,
                     choices=["gmres-cycle", "gmres-cycle-f32", "dslash-packed", "dslash-half", "defl-tensor",
                              "noise-block-f16"],
@@ -241,10 +244,13 @@ def dslash_rates(torch):
     U = torch.from_numpy(synth.su3_links(DSLASH_DIMS, 0.4323, 7)).cuda()
     packed_links = {12: ctx.pack_links_f32(U, 12), 18: ctx.pack_links_f32(U, 18)}
     out = {}
-    cases = [("f64", 18, 1), ("f64", 18, 8), ("f32packed", 12, 1), ("f32packed", 12, 8), ("f32packed", 12, 16),
-             ("f32packed", 18, 8), ("f16packed", 12, 1), ("f16packed", 12, 8), ("f16packed", 12, 16),
-             ("bf16packed", 12, 8)]
-    for prec, recon, nrhs in cases:
+    cases = [("f64", 18, 1, 0), ("f64", 18, 8, 0), ("f32packed", 12, 1, 1), ("f32packed", 12, 8, 2),
+             ("f32packed", 12, 16, 2), ("f32packed", 18, 8, 2), ("f16packed", 12, 1, 1), ("f16packed", 12, 8, 2),
+             ("f16packed", 12, 16, 2), ("bf16packed", 12, 8, 2),
+             ("f32packed", 12, 8, 3), ("f32packed", 12, 16, 3), ("f16packed", 12, 8, 3), ("f16packed", 12, 16, 3),
+             ("bf16packed", 12, 8, 3), ("bf16packed", 12, 16, 3)]
+    for prec, recon, nrhs, nr in cases:
+        ctx.set_rhs_per_thread(nr)
         x = ctx.noise_z4(3, 0, nrhs)
         lw = 4
         if prec == "f64":
@@ -262,7 +268,7 @@ def dslash_rates(torch):
             x = ctx.pack_f32(x)
             y = torch.empty_like(x)
             Up = packed_links[recon]
-            fn = lambda: ctx.wilson_apply_packed(Up, recon, 0.157, x, y)
+            fn = lambda: ctx.wilson_apply_packed(Up, recon, 0.157, x, y, rhs_per_thread=nr)
             w, lreals = 4, recon
         for _ in range(2):
             fn()
@@ -277,7 +283,8 @@ def dslash_rates(torch):
         nbytes = nrhs * V * 48 * w + V * 4 * lreals * lw
         gbs = nbytes / t / 1e9
         tf = 1368.0 * V * nrhs / t / 1e12
-        out["%s_recon%d_rhs%d" % (prec, recon, nrhs)] = {
+        key = "%s_recon%d_rhs%d" % (prec, recon, nrhs) + ("_staged" if nr == 3 else "")
+        out[key] = {
             "ms": round(t * 1e3, 4), "GB/s": round(gbs, 1), "TFLOP/s": round(tf, 4),
             "frac_hbm": round(gbs / HBM_PEAK_GBS, 4),
             "frac_fp64": round(tf / FP64_PEAK_TFLOPS, 4) if prec == "f64" else None}
@@ -579,7 +586,8 @@ def main():
     barrier()
     t0 = time.perf_counter()
     loop = ctx.loop_setup(Ud, KAPPA, NOISE_SEED, NNOISE, BLOCK, M_DR, K_DR, K_PS, NPOLY, TOL, TOL_SPECIAL,
-                          m_inner=M_INNER, max_cycles=MAX_CYCLES, prec=lqcd.PREC_F16, system=lqcd.SYS_MG5)
+                          m_inner=M_INNER, max_cycles=MAX_CYCLES, prec=lqcd.PREC_F16, system=lqcd.SYS_MG5,
+                          prec_degree=args.prec_degree)
     barrier()
     setup_s = time.perf_counter() - t0
     info = loop.info()
@@ -716,6 +724,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "lattice": "24x24x24x32", "kappa": KAPPA, "noises": NNOISE,
                            "noises_per_step": BLOCK, "Q": info["Q"], "link_eps": LINK_EPS,
+                           "poly_preconditioner_degree": args.prec_degree,
                            "precision": "FP16 storage of the inner Krylov basis, FP32 arithmetic, FP64 outer "
                                         "true residual, FP64 setup; HFES projections split-precision FP64 on "
                                         "tensor cores",

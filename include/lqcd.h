@@ -89,6 +89,12 @@ typedef struct {
                         every Rayleigh-Ritz residual ||A e - lambda e|| of the restart space is
                         <= eig_tol ("super-convergence" of the first right-hand side, which
                         converges the eigenvectors, Sec. 5.4, 7); 0 = residual criterion only */
+  int poly_degree;   /* polynomial right preconditioner (the Min-Res polynomial of Sec. 5.2 used
+                        inside the solver): the Krylov method works on B = A p(A) with
+                        p(A) = sum_j a_j A^j (A = M or M gamma_5 by the system), returns
+                        x = p(A) y (the solution of A x = b, same residual); deflation spaces
+                        made or used by the call are spaces of B.  0 = none, at most 32      */
+  const double *poly_coeffs; /* host, poly_degree + 1 complex a_j (read during the call)      */
 } lqcd_krylov_opts;
 
 typedef struct {
@@ -180,8 +186,10 @@ lqcd_status lqcd_unpack_f32(lqcd_ctx *ctx, const float *in, double *out, int nrh
 lqcd_status lqcd_pack_links_f32(lqcd_ctx *ctx, const double *links, float *out, int recon);
 /* Packed FP32 operator (flags as lqcd_wilson_apply).  rhs_per_thread: 1 = one thread per site and
  * right-hand side; 2 = two right-hand sides per thread in the two lanes of packed FP32 arithmetic
- * (links loaded and rebuilt once for both); 4 = four per thread, scalar; 0 = the context's
- * setting (lqcd_set_rhs_per_thread, or the autotuner's pick), else 2. */
+ * (links loaded and rebuilt once for both); 3 = the same with the neighbour spinors and links of
+ * the next directions staged asynchronously in shared memory (cp.async) while the current one is
+ * computed; 4 = four per thread, scalar; 0 = the context's setting (lqcd_set_rhs_per_thread, or the
+ * autotuner's pick), else 2. */
 lqcd_status lqcd_wilson_apply_packed(lqcd_ctx *ctx, const float *links_packed, int recon, double kappa,
                                      const float *in, float *out, int nrhs, int flags, int rhs_per_thread);
 
@@ -198,7 +206,7 @@ lqcd_status lqcd_wilson_apply_half(lqcd_ctx *ctx, int prec, const float *links_p
                                    const void *in, void *out, int nrhs, int flags);
 /* Right-hand sides per thread of the packed operators used by this context when a call does not
  * choose (0 = built-in choice, paired lanes; 1; 2 = paired lanes, also for FP16 / BF16 fields;
- * 4 = FP32 only).
+ * 3 = paired lanes with asynchronous staging, also for FP16 / BF16; 4 = FP32 only).
  * The mixed-precision solvers use it; lqcd_autotune_block sets it. */
 lqcd_status lqcd_set_rhs_per_thread(lqcd_ctx *ctx, int nr);
 
@@ -400,6 +408,12 @@ typedef struct {
                          path, one MINRES-DR on M' for both, every noise solved as
                          M' y = eta by GMRES-Proj over that space and x = gamma_5 y (for fields
                          whose spectrum of M surrounds the origin, where GMRES on M stagnates) */
+  int prec_degree;    /* > 0: polynomial preconditioning of the noise solves (and of the special
+                         solve that makes their space): the Min-Res polynomial p of degree
+                         prec_degree of the solver's operator A (M, or M' on the Hermitian path,
+                         real coefficients there) on the polynomial noise; the Krylov methods
+                         work on A p(A) (lqcd_krylov_opts.poly_degree).  HFES eigenvalues are then
+                         Rayleigh quotients of M' on the Ritz vectors; ES is off.  0 = none     */
 } lqcd_est_opts;
 
 typedef struct {

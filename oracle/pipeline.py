@@ -30,18 +30,45 @@ from . import rng
 from . import subtract as S
 
 
-def setup(U, kappa, dims, seed, m, k, K, npoly, tol_special, max_cycles=2000, eig_tol=None, system="M"):
+def prec_coeffs(Asolve, b, degree, hermitian):
+    """Coefficients of the polynomial preconditioner p of the noise solves (Sec. 5.2's Min-Res
+    polynomial, of the solver's operator A, on the noise b): p(A) ~ A^{-1}.  For Hermitian A the
+    Min-Res coefficients are real (b^dag A^j b is real), and their real parts are taken so that
+    A p(A) is exactly Hermitian."""
+    a = S.poly_coeffs(Asolve, b, degree)
+    return a.real.astype(np.complex128) if hermitian else a
+
+
+def setup(U, kappa, dims, seed, m, k, K, npoly, tol_special, max_cycles=2000, eig_tol=None, system="M",
+          prec_degree=0):
     A = lambda v: L.flat(L.wilson(U, kappa, L.unflat(v, dims)))
     Ap = lambda v: L.flat(L.wilson_g5(U, kappa, L.unflat(v, dims)))
     b0 = L.flat(rng.z4_noise(seed, rng.NOISE_SPECIAL, dims))
-    if system == "M":
-        _, info_m, defl_m = Kr.gmres_dr(A, b0, m, k, tol_special, max_cycles, eig_tol=eig_tol)
-    elif system != "MG5":
+    if system not in ("M", "MG5"):
         raise ValueError(system)
-    _, info_h, defl_h = Kr.gmres_dr(Ap, b0, m, k, tol_special, max_cycles, hermitian=True, eig_tol=eig_tol)
-    if system == "MG5":
+    # polynomial preconditioning (reading: the outlook of Sec. 5.2 / 10, POLY combined with deflation
+    # inside the solver): the Krylov solves of the noise system work on B = A p(A), x = p(A) y
+    Asolve = Ap if system == "MG5" else A
+    ap = None
+    Bsolve = Asolve
+    if prec_degree > 0:
+        ap = prec_coeffs(Asolve, L.flat(rng.z4_noise(seed, rng.NOISE_POLY, dims)), prec_degree, system == "MG5")
+        Bsolve = lambda v: Asolve(S.poly_apply(Asolve, ap, v))
+    if system == "M":
+        _, info_m, defl_m = Kr.gmres_dr(Bsolve, b0, m, k, tol_special, max_cycles, eig_tol=eig_tol)
+        _, info_h, defl_h = Kr.gmres_dr(Ap, b0, m, k, tol_special, max_cycles, hermitian=True, eig_tol=eig_tol)
+    else:
+        _, info_h, defl_h = Kr.gmres_dr(Bsolve, b0, m, k, tol_special, max_cycles, hermitian=True, eig_tol=eig_tol)
         info_m, defl_m = info_h, defl_h
     lam, Ev, eres = Kr.ritz_pairs(defl_h, hermitian=True)
+    if system == "MG5" and ap is not None:
+        # Ritz vectors of B' = M' p(M') are those of M' (B' is a function of M'): the eigenvalues of M'
+        # are their Rayleigh quotients, ordered by |lambda'|, with residuals ||M' e - lambda' e||
+        ME = np.stack([Ap(Ev[:, q]) for q in range(Ev.shape[1])], axis=1)
+        lam = np.einsum('iq,iq->q', Ev.conj(), ME).real.astype(np.complex128)
+        order = np.argsort(np.abs(lam), kind='stable')
+        lam, Ev, ME = lam[order], Ev[:, order], ME[:, order]
+        eres = np.linalg.norm(ME - Ev * lam[None, :], axis=0)
     Af = lambda f: L.wilson(U, kappa, f)
     a = S.poly_coeffs(Af, rng.z4_noise(seed, rng.NOISE_POLY, dims), npoly)
     t = S.hop_traces(U, kappa, max(K, npoly + 1), dims)
@@ -50,12 +77,12 @@ def setup(U, kappa, dims, seed, m, k, K, npoly, tol_special, max_cycles=2000, ei
     xi_p = S.xi_inverse(Ev, pert, dims)
     xi_q = S.xi_inverse(Ev, poly, dims)
     es = None
-    if system == "M":
+    if system == "M" and ap is None:
         lam_m, Er, _ = Kr.ritz_pairs(defl_m, hermitian=False)
         El, found = S.es_left_vectors(Er, lam_m, dims)
         es = (Er[:, found], El[:, found], lam_m[found])
     return dict(A=A, Ap=Ap, system=system, defl_m=defl_m, info_m=info_m, info_h=info_h, lam=lam, Ev=Ev, eig_resid=eres,
-                es=es,
+                es=es, Asolve=Asolve, Bsolve=Bsolve, prec_a=ap,
                 a=a, b=S.a_to_b(a), t=t, xi_pert=xi_p, xi_poly=xi_q, pert=pert, poly=poly)
 
 
@@ -94,22 +121,23 @@ def solve_noises(st, dims, seed, first, count, m_inner, tol, max_cycles=2000):
     xs, infos = [], []
     for n in range(first, first + count):
         eta = L.flat(rng.z4_noise(seed, n, dims))
-        if st["system"] == "MG5":
-            y, info = Kr.gmres_proj(st["Ap"], eta, st["defl_m"], m_inner, tol, max_cycles)
-            xs.append(L.g5(L.unflat(y, dims)))
-        else:
-            x, info = Kr.gmres_proj(st["A"], eta, st["defl_m"], m_inner, tol, max_cycles)
-            xs.append(L.unflat(x, dims))
+        # solve B y = eta over the space of B (B = A, or A p(A) with polynomial preconditioning; its
+        # relative residual is that of x = p(A) y for A x = eta), then x = gamma_5 x' on the Hermitian path
+        y, info = Kr.gmres_proj(st["Bsolve"], eta, st["defl_m"], m_inner, tol, max_cycles)
+        if st["prec_a"] is not None:
+            y = S.poly_apply(st["Asolve"], st["prec_a"], y)
+        xs.append(L.g5(L.unflat(y, dims)) if st["system"] == "MG5" else L.unflat(y, dims))
         infos.append(info)
     return np.stack(xs), infos
 
 
 def loop_estimate(U, kappa, dims, seed, nnoise, m, k, K, npoly, tol, tol_special, modes=E.MODES, eig_tol=None,
-                  system="M"):
+                  system="M", prec_degree=0):
     """Run steps 1-5; returns (results per mode, setup state, timing).  eig_tol: see krylov.gmres_dr;
-    system: "M" or "MG5" (step 1)."""
+    system: "M" or "MG5" (step 1); prec_degree: polynomial preconditioning of the noise solves."""
     t0 = time.perf_counter()
-    st = setup(U, kappa, dims, seed, m, k, K, npoly, tol_special, eig_tol=eig_tol, system=system)
+    st = setup(U, kappa, dims, seed, m, k, K, npoly, tol_special, eig_tol=eig_tol, system=system,
+               prec_degree=prec_degree)
     add = addbacks(U, kappa, dims, st, K)
     t1 = time.perf_counter()
     xs, infos = solve_noises(st, dims, seed, 0, nnoise, m - k, tol)

@@ -80,7 +80,7 @@ lqcd_status autotune_block(lqcd_ctx *ctx, const double *links, double kappa, con
   }
   if (o->prec != LQCD_PREC_F64) {
     // right-hand sides per thread of the packed inner operator at the chosen width: 1, 2 (paired
-    // lanes) or 4 for FP32 fields, 1 or 2 for FP16 / BF16 fields
+    // lanes), 3 (paired lanes, asynchronously staged) or 4 for FP32 fields, 1, 2 or 3 for FP16 / BF16
     float4 *Up, *in, *out;
     const int recon = ctx->recon, nb = *best;
     const size_t fl = (size_t)ctx->V * 24 * nb;  // floats of nb packed FP32 fields
@@ -98,8 +98,8 @@ lqcd_status autotune_block(lqcd_ctx *ctx, const double *links, double kappa, con
     const int saved = ctx->packed_nr;
     double tb = 0.0;
     int nr_best = 1;
-    for (int nr : {1, 2, 4}) {
-      if (nr > nb || (nr == 4 && o->prec != LQCD_PREC_F32)) break;
+    for (int nr : {1, 2, 3, 4}) {
+      if ((nr > 1 && nb < 2) || (nr == 4 && (nb < 4 || o->prec != LQCD_PREC_F32))) continue;
       ctx->packed_nr = nr;
       auto f = [&] {
         for (int rep = 0; rep < 3; ++rep) {

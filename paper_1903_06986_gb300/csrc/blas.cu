@@ -64,11 +64,12 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
   return v;
 }
 
-// Single-launch batched inner products.  Block b = g + ngroup (r + nrhs c) (a 1-D grid: the groups
-// and right-hand sides of one element chunk are neighbours in launch order, so the chunk of w^r and,
-// with a basis shared by all right-hand sides, the chunk of every basis vector are read from DRAM
-// once and then from L2) sums conj(V_i^r) w^r over element chunk c for the GROUP basis vectors of
-// group g and writes partial[(i * nrhs + r) * nchunk + c]; the last block to finish for right-hand
+// Single-launch batched inner products.  Block b (a 1-D grid) sums conj(V_i^r) w^r over element
+// chunk c for the GROUP basis vectors of group g and writes partial[(i * nrhs + r) * nchunk + c]:
+// with a basis shared by all right-hand sides b = g + ngroup (r + nrhs c), so that the groups and
+// right-hand sides of one chunk are neighbours in launch order and the chunk of every basis vector
+// and of every w^r is read from DRAM once and then from L2; with a basis per right-hand side
+// b = c + nchunk (g + ngroup r), consecutive blocks streaming consecutive chunks; the last block to finish for right-hand
 // side r (a counter per r, reset by that block) adds the nchunk partials of every i in chunk order
 // and writes h[i * nrhs + r].  The result does not depend on block scheduling.
 template <typename SV, typename SW>
@@ -79,9 +80,18 @@ __global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, 
   using C = Ar<SW>;
   static_assert(std::is_same<C, Ar<SV>>::value, "multidot: storage types of different arithmetic");
   const int ngroup = (nvec + GROUP - 1) / GROUP;
-  const int g0 = blockIdx.x % ngroup;
-  const int r = (blockIdx.x / ngroup) % nrhs;
-  const int c = blockIdx.x / (ngroup * nrhs);
+  int g0, r, c;
+  if (vrs == 0) {
+    // shared basis: the groups and right-hand sides of one chunk are neighbours in launch order
+    g0 = blockIdx.x % ngroup;
+    r = (blockIdx.x / ngroup) % nrhs;
+    c = blockIdx.x / (ngroup * nrhs);
+  } else {
+    // a basis per right-hand side: consecutive blocks stream consecutive chunks of one vector group
+    c = blockIdx.x % nchunk;
+    g0 = (blockIdx.x / nchunk) % ngroup;
+    r = blockIdx.x / (nchunk * ngroup);
+  }
   const int i0 = g0 * GROUP;
   const long long chunk = (n + nchunk - 1) / nchunk;
   const long long e0 = c * chunk;
@@ -240,11 +250,17 @@ __global__ void __launch_bounds__(BT) combine_kernel(const SV *__restrict__ V, l
 
 template <typename S>
 __global__ void invscale_kernel(S *__restrict__ x, const double *__restrict__ s, long long n) {
-  const long long e = (long long)blockIdx.x * BT + threadIdx.x;
+  // the reciprocal once per block, then one multiply per component in the arithmetic type
+  using R = decltype(Ar<S>().x);
+  __shared__ R f;
   const int r = blockIdx.y;
+  if (threadIdx.x == 0) {
+    const double d = s[r];
+    f = (R)(d > 0.0 ? 1.0 / d : 0.0);
+  }
+  __syncthreads();
+  const long long e = (long long)blockIdx.x * BT + threadIdx.x;
   if (e >= n) return;
-  const double d = s[r];
-  const double f = d > 0.0 ? 1.0 / d : 0.0;
   Ar<S> v = ldc(x[r * n + e]);
   v.x *= f;
   v.y *= f;
@@ -258,11 +274,27 @@ __global__ void copy_kernel(const SX *__restrict__ x, SY *__restrict__ y, long l
     if constexpr (std::is_same<SX, SY>::value) {
       y[e] = x[e];
     } else {
+      using R = decltype(Ar<SY>().x);
       Ar<SY> v = ldc(x[e]);
-      v.x *= fac;
-      v.y *= fac;
+      v.x *= (R)fac;
+      v.y *= (R)fac;
       y[e] = stc<SY>(v);
     }
+  }
+}
+
+// y = a x + b y (complex scalars; storage S, arithmetic of S; FP16 / BF16 vectors carry the same
+// store_sigma factor on both sides, which the linear combination keeps)
+template <typename S>
+__global__ void axpby_kernel(double2 a, const S *__restrict__ x, double2 b, S *__restrict__ y, long long n) {
+  using C = Ar<S>;
+  const C ca = from_d2<C>(a), cb = from_d2<C>(b);
+  for (long long e = (long long)blockIdx.x * BT + threadIdx.x; e < n; e += (long long)gridDim.x * BT) {
+    const C xv = ldc(x[e]), yv = ldc(y[e]);
+    C o = cz<C>();
+    gfma(o, ca, xv);
+    gfma(o, cb, yv);
+    y[e] = stc<S>(o);
   }
 }
 
@@ -401,6 +433,13 @@ lqcd_status blas_zero(lqcd_ctx *ctx, S *y, long long n) {
   kbegin(ctx);
   zero_kernel<S><<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(y, n);
   return launch_check(ctx, "zero_kernel", K_BLAS1, (double)n);
+}
+
+template <typename S>
+lqcd_status blas_axpby(lqcd_ctx *ctx, double2 a, const S *x, double2 b, S *y, long long n) {
+  kbegin(ctx);
+  axpby_kernel<S><<<std::min(blocks_for(n), 8 * ctx->sms), BT, 0, ctx->stream>>>(a, x, b, y, n);
+  return launch_check_bytes(ctx, "axpby_kernel", K_BLAS1, (double)n, 3.0 * sizeof(S) * n);
 }
 
 lqcd_status blas_axpy(lqcd_ctx *ctx, double2 a, const double2 *x, double2 *y, long long n) {
@@ -550,6 +589,7 @@ lqcd_status blas_to_f32(lqcd_ctx *ctx, const double2 *x, float2 *y, long long n)
 
 #define LQCD_BLAS_INSTANTIATE(S)                                                                               \
   template lqcd_status blas_copy<S, S>(lqcd_ctx *, const S *, S *, long long);                                  \
+  template lqcd_status blas_axpby<S>(lqcd_ctx *, double2, const S *, double2, S *, long long);                  \
   template lqcd_status blas_zero<S>(lqcd_ctx *, S *, long long);                                                \
   template lqcd_status blas_norms<S>(lqcd_ctx *, const S *, long long, int, double *);                          \
   template lqcd_status blas_invscale<S>(lqcd_ctx *, S *, const double *, long long, int);

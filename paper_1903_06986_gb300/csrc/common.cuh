@@ -86,6 +86,7 @@ struct lqcd_defl {
   std::vector<double> eres;   // k eigen residual norms (host)
   double2 *Hbar_dev;    // (k+1) x k row-major (device), NULL when imported
   void *tc;             // bf16 slices of E for the tensor-core contractions (made on first use)
+  void *Vf32;           // packed FP32 copy of V for mixed-precision solves (made on first use)
 };
 
 // ----- status plumbing ------------------------------------------------------------------
@@ -116,7 +117,8 @@ lqcd_status launch_check_bytes(lqcd_ctx *ctx, const char *what, int cls, double 
 enum WsSlot {
   WS_PARTIAL = 0, WS_SCAL, WS_TMP0, WS_TMP1, WS_TMP2, WS_TMP3, WS_BASIS, WS_HESS, WS_COEF,
   WS_BASIS2, WS_TMP4, WS_TMP5, WS_EST0, WS_EST1, WS_EST2, WS_PROBE,
-  WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_COUNT, WS_TUNE, WS_SPEC, WS_NBLK, WS_TC_STAT, WS_TC_B, WS_TC_PART, WS_TC_D, WS_NSLOTS
+  WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_COUNT, WS_TUNE, WS_SPEC, WS_NBLK, WS_TC_STAT, WS_TC_B, WS_TC_PART, WS_TC_D,
+  WS_POLY1, WS_POLY2, WS_POLY3, WS_NSLOTS
 };
 lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr);
 void graph_cache_clear(lqcd_ctx *ctx);
@@ -252,6 +254,8 @@ lqcd_status blas_combine(lqcd_ctx *ctx, const SV *V, long long vstride, long lon
 template <typename S> lqcd_status blas_invscale(lqcd_ctx *ctx, S *x, const double *s, long long n, int nrhs);
 // y += a x with a host scalar a
 lqcd_status blas_axpy(lqcd_ctx *ctx, double2 a, const double2 *x, double2 *y, long long n);
+// y = a x + b y with host scalars (any storage type)
+template <typename S> lqcd_status blas_axpby(lqcd_ctx *ctx, double2 a, const S *x, double2 b, S *y, long long n);
 // y^r = float(x^r / s[r])  and  x^r += s[r] * double(c^r)  (mixed-precision defect correction)
 lqcd_status blas_demote(lqcd_ctx *ctx, const double2 *x, const double *s, float2 *y, long long n, int nrhs);
 lqcd_status blas_promote_acc(lqcd_ctx *ctx, const float2 *c, const double *s, double2 *x, long long n, int nrhs);

@@ -33,16 +33,78 @@ namespace {
 
 constexpr int OP_MASKED = 4;
 
+// Polynomial right preconditioner of a solve (the Min-Res polynomial of Sec. 5.2 used inside the
+// solver): the Krylov methods work on B = A p(A), p(A) = sum_j a_j A^j, and x = p(A) y.  degree 0:
+// none.  t1, t2: two scratch blocks of the solve's right-hand sides (reserved before use, so that
+// graph capture never allocates).
+constexpr int MAX_POLY = 32;
+struct Poly {
+  int degree = 0;
+  double2 a[MAX_POLY + 1] = {};
+  void *t1 = nullptr, *t2 = nullptr;
+  void append_key(std::string &k) const {
+    key_add(k, degree);
+    for (int j = 0; j <= degree && degree > 0; ++j) key_add(k, a[j]);
+    key_add(k, t1);
+    key_add(k, t2);
+  }
+};
+
+// out = [A] p(A) in by Horner's rule with the operator's plain application (times_A: B = A p(A),
+// d + 1 applications; else p(A) alone, d applications).  in and out must not overlap t1 / t2.
+template <typename S, typename OP>
+lqcd_status poly_apply_op(lqcd_ctx *ctx, const OP &op, const Poly &pp, const S *in, S *out, int nrhs, bool times_A) {
+  const long long n = (long long)nrhs * ctx->N;
+  const int d = pp.degree;
+  S *t = (S *)pp.t1, *u = (S *)pp.t2;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  LQCD_TRY(blas_zero(ctx, t, n));
+  LQCD_TRY(blas_axpby(ctx, pp.a[d], in, zero, t, n));
+  for (int j = d - 1; j >= 0; --j) {
+    LQCD_TRY(op.apply_base(ctx, t, u, nrhs));
+    LQCD_TRY(blas_axpby(ctx, pp.a[j], in, one, u, n));
+    std::swap(t, u);
+  }
+  if (times_A) return op.apply_base(ctx, t, out, nrhs);
+  return blas_copy(ctx, (const S *)t, out, n);
+}
+
 // The operator of a solve: M or M gamma_5 (flags LQCD_APPLY_M / LQCD_APPLY_G5R) on FP64 storage
-// (arithmetic prec) or on FP32 storage with FP32 arithmetic (the inner solver of mixed precision).
+// (arithmetic prec) or on FP32 storage with FP32 arithmetic (the inner solver of mixed precision),
+// times p(A) when a polynomial preconditioner is set.
+template <typename S, typename Derived> struct PolyApply {
+  lqcd_status apply(lqcd_ctx *ctx, const S *in, S *out, int nrhs) const {
+    const Derived &d = static_cast<const Derived &>(*this);
+    if (d.pp.degree == 0) return d.apply_base(ctx, in, out, nrhs);
+    return poly_apply_op<S>(ctx, d, d.pp, in, out, nrhs, true);
+  }
+  // out = p(A) in (the solution x = p(A) y of a preconditioned solve); a plain copy without p
+  lqcd_status apply_poly(lqcd_ctx *ctx, const S *in, S *out, int nrhs) const {
+    const Derived &d = static_cast<const Derived &>(*this);
+    if (d.pp.degree == 0) return blas_copy(ctx, in, out, (long long)nrhs * ctx->N);
+    return poly_apply_op<S>(ctx, d, d.pp, in, out, nrhs, false);
+  }
+  // reserve the scratch blocks of the polynomial for nrhs right-hand sides
+  lqcd_status reserve(lqcd_ctx *ctx, int nrhs) {
+    Derived &d = static_cast<Derived &>(*this);
+    if (d.pp.degree == 0) return LQCD_OK;
+    const size_t bytes = sizeof(S) * (size_t)nrhs * ctx->N;
+    LQCD_TRY(ws_get(ctx, WS_POLY1, bytes, &d.pp.t1));
+    return ws_get(ctx, WS_POLY2, bytes, &d.pp.t2);
+  }
+};
 template <typename S> struct OpT;
-template <> struct OpT<double2> {
+template <> struct OpT<double2> : PolyApply<double2, OpT<double2>> {
   const double2 *U;
   double kappa;
   int flags;                    // LQCD_APPLY_M, LQCD_APPLY_G5R, or OP_MASKED
   int prec;
   unsigned long long g5mask;    // OP_MASKED: right-hand side r uses M gamma_5 when bit r is set
-  lqcd_status apply(lqcd_ctx *ctx, const double2 *in, double2 *out, int nrhs) const {
+  Poly pp;
+  OpT() = default;
+  OpT(const double2 *U_, double kappa_, int flags_, int prec_, unsigned long long g5mask_)
+      : U(U_), kappa(kappa_), flags(flags_), prec(prec_), g5mask(g5mask_) {}
+  lqcd_status apply_base(lqcd_ctx *ctx, const double2 *in, double2 *out, int nrhs) const {
     if (flags == OP_MASKED) return wilson_launch_masked(ctx, U, kappa, in, out, nrhs, g5mask);
     return wilson_launch(ctx, U, kappa, in, out, nrhs, prec, flags);
   }
@@ -52,16 +114,18 @@ template <> struct OpT<double2> {
     key_add(k, flags);
     key_add(k, prec);
     key_add(k, g5mask);
+    pp.append_key(k);
   }
 };
 // FP32 fields of the inner solver are in the packed layout (see wilson.cu); the level-1/2 kernels
 // treat them as plain float2 arrays of the same length, which is all they need.
-template <> struct OpT<float2> {
+template <> struct OpT<float2> : PolyApply<float2, OpT<float2>> {
   const float4 *U;  // packed links
   int recon;
   double kappa;
   int flags;
-  lqcd_status apply(lqcd_ctx *ctx, const float2 *in, float2 *out, int nrhs) const {
+  Poly pp;
+  lqcd_status apply_base(lqcd_ctx *ctx, const float2 *in, float2 *out, int nrhs) const {
     return wilson_launch_packed(ctx, U, recon, kappa, (const float4 *)in, (float4 *)out, nrhs, flags, ctx->packed_nr);
   }
   void append_key(std::string &k) const {
@@ -69,15 +133,17 @@ template <> struct OpT<float2> {
     key_add(k, recon);
     key_add(k, kappa);
     key_add(k, flags);
+    pp.append_key(k);
   }
 };
 // FP16 / BF16 fields of the inner solver: the same packed operator on reduced-precision storage
-template <typename S> struct OpLP {
+template <typename S> struct OpLP : PolyApply<S, OpLP<S>> {
   const float4 *U;
   int recon;
   double kappa;
   int flags;
-  lqcd_status apply(lqcd_ctx *ctx, const S *in, S *out, int nrhs) const {
+  Poly pp;
+  lqcd_status apply_base(lqcd_ctx *ctx, const S *in, S *out, int nrhs) const {
     return wilson_launch_packed_lp<S>(ctx, U, recon, kappa, in, out, nrhs, flags);
   }
   void append_key(std::string &k) const {
@@ -85,6 +151,7 @@ template <typename S> struct OpLP {
     key_add(k, recon);
     key_add(k, kappa);
     key_add(k, flags);
+    pp.append_key(k);
   }
 };
 template <> struct OpT<__half2> : OpLP<__half2> {};
@@ -176,6 +243,7 @@ template <typename S>
 lqcd_status arnoldi_launch(ArnoldiT<S> &a, int j0) {
   if (j0 >= a.m) return LQCD_OK;
   LQCD_TRY(blas_reserve(a.ctx, a.N, a.nrhs, a.m));
+  LQCD_TRY(a.op.reserve(a.ctx, a.nrhs));
   std::string key("arnoldi");
   key_add(key, StoreTag<S>::value);
   a.op.append_key(key);
@@ -547,6 +615,11 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
   double worst = 0.0;
   for (int r = 0; r < nrhs; ++r) worst = std::max(worst, rel[r]);
   matvecs += nrhs;
+  if (op.pp.degree > 0) {
+    // solved B y = b with B = A p(A): the solution of A x = b is x = p(A) y (same residual)
+    LQCD_TRY(op.apply_poly(ctx, x, W.tmp, nrhs));
+    LQCD_TRY(blas_copy(ctx, (const double2 *)W.tmp, x, vs));
+  }
   if (defl_out && k > 0) {
     for (int r = 0; r < nrhs; ++r) {
       lqcd_defl *d = new lqcd_defl();
@@ -773,6 +846,13 @@ lqcd_status proj_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const 
   if (!defl || !defl->V || !defl->Hbar_dev) return set_err(ctx, LQCD_ERR_INVALID_ARG, "GMRES-Proj needs a solver-made deflation space");
   ProjResult res;
   LQCD_TRY(proj_run<double2>(ctx, op, defl->V, defl_hbar(defl), b, x, nrhs, o->m, o->tol, o->max_cycles, true, res));
+  if (op.pp.degree > 0) {
+    // solved B y = b: the solution of A x = b is x = p(A) y (same residual)
+    double2 *t;
+    LQCD_TRY(ws_get(ctx, WS_POLY3, sizeof(double2) * (size_t)nrhs * ctx->N, (void **)&t));
+    LQCD_TRY(op.apply_poly(ctx, x, t, nrhs));
+    LQCD_TRY(blas_copy(ctx, (const double2 *)t, x, (long long)nrhs * ctx->N));
+  }
   if (info) {
     info->cycles = res.cycles;
     info->matvecs = (long)res.matvecs;
@@ -816,18 +896,41 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
   double *sc;
   const int recon = ctx->recon;
   LQCD_TRY(ws_get(ctx, WS_MIX_U, sizeof(float) * (size_t)ctx->V * 4 * (recon == 12 ? 12 : 20), (void **)&U32));
-  LQCD_TRY(ws_get(ctx, WS_MIX_V, sizeof(float2) * (size_t)(k + 1) * N, (void **)&Vlp));
   LQCD_TRY(ws_get(ctx, WS_MIX_R32, sizeof(float2) * (size_t)vs, (void **)&r32));
   LQCD_TRY(ws_get(ctx, WS_MIX_E32, sizeof(float2) * (size_t)vs, (void **)&e32));
   LQCD_TRY(ws_get(ctx, WS_MIX_R, sizeof(double2) * (size_t)vs, (void **)&r));
   LQCD_TRY(ws_get(ctx, WS_MIX_S, sizeof(double) * (size_t)nrhs, (void **)&sc));
   LQCD_TRY(pack_links_f32(ctx, op.U, U32, recon));
-  LQCD_TRY(pack_f32(ctx, defl->V, nullptr, (float4 *)Vlp, k + 1));
+  // the FP32 copy of the deflation space is made once per space and kept with it
+  lqcd_defl *dmut = const_cast<lqcd_defl *>(defl);
+  if (!dmut->Vf32) {
+    if (cudaMalloc(&dmut->Vf32, sizeof(float2) * (size_t)(k + 1) * N) != cudaSuccess) {
+      cudaGetLastError();
+      dmut->Vf32 = nullptr;
+      return set_err(ctx, LQCD_ERR_OOM, "mixed solve: FP32 copy of the deflation space does not fit");
+    }
+    LQCD_TRY(pack_f32(ctx, defl->V, nullptr, (float4 *)dmut->Vf32, k + 1));
+  }
+  Vlp = (float2 *)dmut->Vf32;
+  // inner operator B = A p(A) in storage S; p applied to the inner solutions in FP32; the outer
+  // residual is that of A itself
+  OpT<float2> opf;
+  opf.U = U32;
+  opf.recon = recon;
+  opf.kappa = op.kappa;
+  opf.flags = op.flags;
+  opf.pp = op.pp;
+  LQCD_TRY(opf.reserve(ctx, nrhs));
   OpT<S> opl;
   opl.U = U32;
   opl.recon = recon;
   opl.kappa = op.kappa;
   opl.flags = op.flags;
+  opl.pp = opf.pp;        // the same scratch (sized for FP32 >= S), used one after the other
+  Op opA = op;
+  opA.pp.degree = 0;
+  float2 *e32p = e32;
+  if (op.pp.degree > 0) LQCD_TRY(ws_get(ctx, WS_POLY3, sizeof(float2) * (size_t)vs, (void **)&e32p));
   const Mat Hk = defl_hbar(defl);
   LQCD_TRY(blas_zero(ctx, x, vs));
   LQCD_TRY(blas_copy(ctx, b, r, vs));
@@ -862,9 +965,10 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
                                   std::max(1, o->max_cycles - inner_cycles), false, pr)));
     inner_cycles += pr.cycles;
     matvecs += pr.matvecs;
-    LQCD_TRY(unpack_f32(ctx, (const float4 *)e32, sc, x, nrhs));
-    // FP64 true residual r = b - M x
-    LQCD_TRY(op.apply(ctx, x, r, nrhs));
+    if (op.pp.degree > 0) LQCD_TRY(opf.apply_poly(ctx, e32, e32p, nrhs));   // e = p(A) e'
+    LQCD_TRY(unpack_f32(ctx, (const float4 *)e32p, sc, x, nrhs));
+    // FP64 true residual r = b - A x
+    LQCD_TRY(opA.apply(ctx, x, r, nrhs));
     LQCD_TRY(blas_bminus(ctx, r, b, vs));
     matvecs += nrhs;
   }
@@ -886,10 +990,26 @@ lqcd_status mixed_dispatch(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, c
   return mixed_core<float2>(ctx, op, defl, b, x, nrhs, o, info);
 }
 
+// the polynomial preconditioner of a solve from its options (none when poly_degree is 0)
+lqcd_status set_poly(lqcd_ctx *ctx, Op &op, const lqcd_krylov_opts *o, int nrhs) {
+  if (o->poly_degree == 0) return LQCD_OK;
+  if (o->poly_degree < 0 || o->poly_degree > MAX_POLY || !o->poly_coeffs)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "polynomial preconditioner: degree 0..%d with coefficients", MAX_POLY);
+  if (op.flags == OP_MASKED) return set_err(ctx, LQCD_ERR_INVALID_ARG, "polynomial preconditioner: not with a masked operator");
+  op.pp.degree = o->poly_degree;
+  for (int j = 0; j <= o->poly_degree; ++j) {
+    op.pp.a[j] = make_double2(o->poly_coeffs[2 * j], o->poly_coeffs[2 * j + 1]);
+    if (!std::isfinite(op.pp.a[j].x) || !std::isfinite(op.pp.a[j].y))
+      return set_err(ctx, LQCD_ERR_NONFINITE, "polynomial preconditioner: non-finite coefficient");
+  }
+  return op.reserve(ctx, nrhs);
+}
+
 lqcd_status proj_core_entry(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, const double2 *b,
                             double2 *x, int nrhs, const lqcd_krylov_opts *o, lqcd_solve_info *info) {
   const int sys = defl->hermitian ? LQCD_SYS_MG5 : o->system;
   Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, LQCD_PREC_F64, 0ull};
+  LQCD_TRY(set_poly(ctx, op, o, nrhs));
   if (o->prec != LQCD_PREC_F64) return mixed_dispatch(ctx, op, defl, b, x, nrhs, o, info);
   return proj_core(ctx, op, defl, b, x, nrhs, o, info);
 }
@@ -917,12 +1037,50 @@ lqcd_status gmresdr_entry(lqcd_ctx *ctx, const double *links, double kappa, cons
   if (opts->prec != LQCD_PREC_F64 && opts->prec != LQCD_PREC_F32)
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "GMRES-DR / MINRES-DR: prec must be LQCD_PREC_F64 or LQCD_PREC_F32");
   Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, opts->prec, 0ull};
+  LQCD_TRY(set_poly(ctx, op, opts, nrhs));
   std::vector<lqcd_defl *> defls;
   const lqcd_status st = gmresdr_core(ctx, op, (const double2 *)b, (double2 *)x, nrhs, opts,
                                       std::vector<char>(nrhs, hermitian ? 1 : 0), info,
                                       (defl_out && nrhs == 1) ? &defls : nullptr);
   if (defl_out && !defls.empty()) *defl_out = defls[0];
   return st;
+}
+
+// Eigenvalues of A on the Ritz vectors E of a deflation space made with a polynomial preconditioner
+// (a space of B = A p(A): its Ritz vectors approximate eigenvectors of A, B being a function of A):
+// lam_q = e_q^dag A e_q (real for the Hermitian A = M gamma_5), eres_q = ||A e_q - lam_q e_q||.
+lqcd_status defl_rayleigh(lqcd_ctx *ctx, lqcd_defl *d, const double *links, double kappa, int flags) {
+  const int k = d->k;
+  const long long N = ctx->N;
+  const int chunk = 16;
+  double2 *Y, *h;
+  double *nr;
+  LQCD_TRY(ws_get(ctx, WS_TMP4, sizeof(double2) * (size_t)std::min(k, chunk) * N, (void **)&Y));
+  LQCD_TRY(ws_get(ctx, WS_EST1, sizeof(double2) * (size_t)chunk * 2 + sizeof(double) * chunk, (void **)&h));
+  nr = (double *)(h + 2 * chunk);
+  Op op{(const double2 *)links, kappa, flags, LQCD_PREC_F64, 0ull};
+  for (int q0 = 0; q0 < k; q0 += chunk) {
+    const int nb = std::min(chunk, k - q0);
+    const double2 *E = d->E + (size_t)q0 * N;
+    LQCD_TRY(op.apply(ctx, E, Y, nb));
+    // <e_q, A e_q>: the basis of right-hand side q is e_q itself
+    LQCD_TRY(blas_multidot(ctx, E, 0, N, 1, Y, N, nb, h));
+    std::vector<double2> lh;
+    LQCD_TRY(download(ctx, h, lh, (size_t)nb));
+    std::vector<cd> neg(nb);
+    for (int r = 0; r < nb; ++r) {
+      const cd l = d->hermitian ? cd(lh[r].x, 0.0) : cd(lh[r].x, lh[r].y);
+      d->lam[q0 + r] = make_double2(l.real(), l.imag());
+      neg[r] = -l;
+    }
+    LQCD_TRY(upload(ctx, neg, h + chunk));
+    LQCD_TRY(blas_multiaxpy(ctx, E, 0, N, 1, h + chunk, 1.0, Y, N, nb));   // Y = A e - lam e
+    LQCD_TRY(blas_norms(ctx, Y, N, nb, nr));
+    std::vector<double> rh;
+    LQCD_TRY(download(ctx, nr, rh, (size_t)nb));
+    for (int r = 0; r < nb; ++r) d->eres[q0 + r] = rh[r];
+  }
+  return LQCD_OK;
 }
 
 extern "C" {
@@ -950,6 +1108,7 @@ lqcd_status lqcd_defl_destroy(lqcd_defl *d) {
   if (d->V) cudaFree(d->V);
   if (d->E) cudaFree(d->E);
   if (d->Hbar_dev) cudaFree(d->Hbar_dev);
+  if (d->Vf32) cudaFree(d->Vf32);
   if (d->tc) tc_slices_free(d->tc);
   delete d;
   return LQCD_OK;

@@ -481,7 +481,7 @@ static lqcd_status deflate_dev(lqcd_ctx *ctx, const lqcd_defl *defl, const doubl
 
 // Min-Res coefficients: QR (classical Gram-Schmidt twice) of v = (M b, .., M^{n+1} b)
 static lqcd_status poly_coeffs_dev(lqcd_ctx *ctx, const double2 *U, double kappa, uint64_t seed, int n,
-                                   std::vector<cd> &a) {
+                                   std::vector<cd> &a, int flags = LQCD_APPLY_M) {
   const long long N = ctx->N;
   double2 *Q, *b, *h;
   double *nrm;
@@ -493,7 +493,7 @@ static lqcd_status poly_coeffs_dev(lqcd_ctx *ctx, const double2 *U, double kappa
   // column j of v is M^{j+1} b; build the powers in place, then orthogonalise
   const double2 *prev = b;
   for (int j = 0; j <= n; ++j) {
-    LQCD_TRY(wilson_launch(ctx, U, kappa, prev, Q + (long long)j * N, 1, LQCD_PREC_F64, LQCD_APPLY_M));
+    LQCD_TRY(wilson_launch(ctx, U, kappa, prev, Q + (long long)j * N, 1, LQCD_PREC_F64, flags));
     prev = Q + (long long)j * N;
   }
   dense::Mat R(n + 1, n + 1);
@@ -707,6 +707,7 @@ lqcd_status lqcd_xi_inverse(lqcd_ctx *ctx, const double *links, double kappa, co
 // ---- whole loop estimate: per-configuration setup, then noise batches ------------------------------
 lqcd_status special_solves(lqcd_ctx *ctx, const double *links, double kappa, const double2 *b2, double2 *x2,
                            const lqcd_krylov_opts *o, lqcd_solve_info *info, lqcd_defl **defl_m, lqcd_defl **defl_h);
+lqcd_status defl_rayleigh(lqcd_ctx *ctx, lqcd_defl *d, const double *links, double kappa, int flags);
 lqcd_status proj_core_entry(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, const double2 *b,
                             double2 *x, int nrhs, const lqcd_krylov_opts *o, lqcd_solve_info *info);
 
@@ -728,6 +729,7 @@ struct lqcd_loop {
   std::vector<int> es_perm;
   std::vector<cd> es_coef;
   double2 *g5E = nullptr;
+  std::vector<double> prec_a;  // polynomial preconditioner of the noise solves (interleaved complex)
   long matvecs = 0;
   double seconds = 0.0, eres = 0.0;
   ~lqcd_loop() {
@@ -747,12 +749,20 @@ lqcd_status check_est_opts(lqcd_ctx *ctx, const lqcd_est_opts *o) {
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop estimate: prec must be one of LQCD_PREC_*");
   if (o->system != LQCD_SYS_M && o->system != LQCD_SYS_MG5)
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop estimate: system must be LQCD_SYS_M or LQCD_SYS_MG5");
+  if (o->prec_degree < 0 || o->prec_degree > 32)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop estimate: prec_degree must be in 0..32");
   return LQCD_OK;
 }
 
-lqcd_krylov_opts noise_solver_opts(const lqcd_est_opts *o) {
-  return lqcd_krylov_opts{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec,
-                          o->inner_tol, 0.0};
+lqcd_krylov_opts noise_solver_opts(const lqcd_loop *L) {
+  const lqcd_est_opts *o = &L->o;
+  lqcd_krylov_opts k{o->m_inner > 0 ? o->m_inner : o->m - o->k, 0, o->tol, o->max_cycles, LQCD_SYS_M, o->prec,
+                     o->inner_tol, 0.0};
+  if (!L->prec_a.empty()) {
+    k.poly_degree = (int)L->prec_a.size() / 2 - 1;
+    k.poly_coeffs = L->prec_a.data();
+  }
+  return k;
 }
 
 // ES data (Sec. 5.3, left vectors by gamma_5-hermiticity) from the Ritz pairs of M on L->dm, and the
@@ -887,7 +897,8 @@ lqcd_status loop_finish_setup(lqcd_loop *L, const double2 *U, const double *link
   }
   L->add.assign((size_t)LQCD_NMODES * 9 * Lt, cd(0.0, 0.0));
   auto A = [&](int mode, int op, int t) -> cd & { return L->add[((size_t)mode * 9 + op) * Lt + t]; };
-  if ((L->modes & LQCD_SUB_ES) && !L->dm->hermitian) LQCD_TRY(es_setup(L, U, [&](int op, int t) -> cd & { return A(6, op, t); }));
+  if ((L->modes & LQCD_SUB_ES) && !L->dm->hermitian && L->prec_a.empty())
+    LQCD_TRY(es_setup(L, U, [&](int op, int t) -> cd & { return A(6, op, t); }));
   for (int op = 0; op < 9; ++op)
     for (int t = 0; t < Lt; ++t) {
       cd pert = 0.0, poly = 0.0, e1 = 0.0, ep = 0.0, eq = 0.0;
@@ -913,7 +924,7 @@ lqcd_status loop_finish_setup(lqcd_loop *L, const double2 *U, const double *link
   L->block = o->block;
   if (L->block == 0) {
     // autotuned block width among 8, 16, 32, 64 (those not above the noise count)
-    const lqcd_krylov_opts po = noise_solver_opts(o);
+    const lqcd_krylov_opts po = noise_solver_opts(L);
     std::vector<int> cand;
     for (int c : {8, 16, 32, 64})
       if (c <= o->nnoise) cand.push_back(c);
@@ -935,7 +946,7 @@ lqcd_status loop_noises(lqcd_loop *L, const double *links, uint32_t first0, int 
   const int modes = L->modes;
   const double t0 = now_s();
   NvtxRange nv("noise phase");
-  const lqcd_krylov_opts po = noise_solver_opts(o);
+  const lqcd_krylov_opts po = noise_solver_opts(L);
   const int bw = std::max(1, std::min(L->block, count));
   const long long bn = (long long)bw * N;
   double2 *eta, *x, *xp, *xq, *y, *w, *cdv;
@@ -1039,18 +1050,50 @@ lqcd_status loop_setup(lqcd_ctx *ctx, const double *links, double kappa, const l
   lqcd_solve_info si{};
   lqcd_status st;
   NvtxRange nv("loop setup: special right-hand side solves");
+  const int sflags = o->system == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M;
+  if (o->prec_degree > 0) {
+    // polynomial preconditioner of the noise solves: the Min-Res polynomial of the solver's operator
+    // (M, or M' on the Hermitian path, with real coefficients there) on the polynomial noise
+    std::vector<cd> ap;
+    LQCD_TRY(poly_coeffs_dev(ctx, (const double2 *)links, kappa, o->seed, o->prec_degree, ap, sflags));
+    L->matvecs += o->prec_degree + 1;
+    L->prec_a.resize(2 * ap.size());
+    for (size_t j = 0; j < ap.size(); ++j) {
+      L->prec_a[2 * j] = ap[j].real();
+      L->prec_a[2 * j + 1] = o->system == LQCD_SYS_MG5 ? 0.0 : ap[j].imag();
+    }
+  }
+  lqcd_krylov_opts kp = ko;
+  if (!L->prec_a.empty()) {
+    kp.poly_degree = o->prec_degree;
+    kp.poly_coeffs = L->prec_a.data();
+  }
   if (o->system == LQCD_SYS_MG5) {
-    // Hermitian path: MINRES-DR on M' alone gives both the eigenpairs and the noise solves' space
-    st = lqcd_minresdr_solve(ctx, links, kappa, (const double *)bs, (double *)x0, 1, &ko, &si, &L->dh);
+    // Hermitian path: MINRES-DR on M' (or on M' p(M')) alone gives both the eigenpairs and the
+    // noise solves' space; with the preconditioner the eigenvalues of M' are the Rayleigh quotients
+    st = lqcd_minresdr_solve(ctx, links, kappa, (const double *)bs, (double *)x0, 1, &kp, &si, &L->dh);
     L->dm = L->dh;
     L->own_h = true;
+    if (L->dh && !L->prec_a.empty()) LQCD_TRY(defl_rayleigh(ctx, L->dh, links, kappa, LQCD_APPLY_G5R));
+  } else if (!L->prec_a.empty()) {
+    lqcd_solve_info s2{};
+    st = lqcd_gmresdr_solve(ctx, links, kappa, (const double *)bs, (double *)x0, 1, &kp, &si, &L->dm);
+    L->own_m = true;
+    if (st == LQCD_OK || st == LQCD_ERR_NOT_CONVERGED) {
+      const lqcd_status st2 = lqcd_minresdr_solve(ctx, links, kappa, (const double *)bs, (double *)(x0 + N), 1, &ko, &s2,
+                                                  &L->dh);
+      L->own_h = true;
+      si.matvecs += s2.matvecs;
+      if (st2 != LQCD_OK && st2 != LQCD_ERR_NOT_CONVERGED) return st2;
+    }
   } else {
     st = special_solves(ctx, links, kappa, bs, x0, &ko, &si, &L->dm, &L->dh);
     L->own_m = L->own_h = true;
   }
+  (void)sflags;
   if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
   if (!L->dm || !L->dh) return set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop setup: no deflation space");
-  L->matvecs = si.matvecs;
+  L->matvecs += si.matvecs;
   LQCD_TRY(loop_finish_setup(L, (const double2 *)links, links, nullptr));
   L->seconds = now_s() - t0;
   *out = guard.release();

@@ -553,18 +553,212 @@ __global__ void __launch_bounds__(128, 4) wilson_pair_kernel(const float4 *__res
   PairIO<S>::store(oa, ob, V, o, second);
 }
 
+// ---- paired lanes with asynchronous staging.  The neighbour spinors (both right-hand sides of the
+// pair) and the link of each of the next directions are copied global -> shared memory with
+// cp.async while the current direction is computed, so the bytes in flight do not depend on the
+// registers a thread holds.  Every thread copies and consumes only its own entries, so the
+// per-thread cp.async groups order everything and no block barrier is needed.  Shared layout
+// (conflict-free: consecutive threads read consecutive entries):
+//   spinors [stage][12 chunks: rhs a q = 0..5, rhs b q = 0..5][128 threads]   (T = chunk type)
+//   links   [stage][NC chunks][128 threads]                                   (float4)
+constexpr int ASYNC_BT = 128;
+template <typename T> __device__ __forceinline__ void cp_async_chunk(T *smem, const T *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// lane pairs from chunks in shared memory (u: right-hand side a, w: b; chunk q at [q * ASYNC_BT])
+template <typename S> struct PairSmem;
+template <> struct PairSmem<float2> {
+  static __device__ __forceinline__ void load(const float4 *a, const float4 *b, Cx<P2> s[4][3]) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const float4 u = a[q * ASYNC_BT], w = b[q * ASYNC_BT];
+      const int c0 = 2 * q, c1 = 2 * q + 1;
+      s[c0 / 3][c0 % 3] = mk<P2>(p2(u.x, w.x), p2(u.y, w.y));
+      s[c1 / 3][c1 % 3] = mk<P2>(p2(u.z, w.z), p2(u.w, w.w));
+    }
+  }
+};
+template <typename H, typename T2, H (*LO)(H, H), H (*HI)(H, H), float2 (*TOF)(H)>
+struct PairSmemHalf {
+  static __device__ __forceinline__ void load(const T2 *a, const T2 *b, Cx<P2> s[4][3]) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const T2 u = a[q * ASYNC_BT], w = b[q * ASYNC_BT];
+      const int c0 = 2 * q, c1 = 2 * q + 1;
+      s[c0 / 3][c0 % 3] = mk<P2>(P2{TOF(LO(u.a, w.a))}, P2{TOF(HI(u.a, w.a))});
+      s[c1 / 3][c1 % 3] = mk<P2>(P2{TOF(LO(u.b, w.b))}, P2{TOF(HI(u.b, w.b))});
+    }
+  }
+};
+template <> struct PairSmem<__half2> : PairSmemHalf<__half2, h2x2, h_lo, h_hi, h_tof> {};
+template <> struct PairSmem<__nv_bfloat162> : PairSmemHalf<__nv_bfloat162, b2x2, b_lo, b_hi, b_tof> {};
+
+// link of one direction from its NC float4 chunks in shared memory (row 2 rebuilt for recon 12)
+template <int RECON>
+__device__ __forceinline__ void link_from_smem(const float4 *p, Cx<float> u[9]) {
+  const float4 a = p[0], b = p[ASYNC_BT], c = p[2 * ASYNC_BT];
+  u[0] = mk<float>(a.x, a.y); u[1] = mk<float>(a.z, a.w);
+  u[2] = mk<float>(b.x, b.y); u[3] = mk<float>(b.z, b.w);
+  u[4] = mk<float>(c.x, c.y); u[5] = mk<float>(c.z, c.w);
+  if (RECON == 12) {
+    auto cm = [](Cx<float> x, Cx<float> y) { return mk<float>(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); };
+    Cx<float> t;
+    t = cm(u[1], u[5]) - cm(u[2], u[4]); u[6] = mk<float>(t.x, -t.y);
+    t = cm(u[2], u[3]) - cm(u[0], u[5]); u[7] = mk<float>(t.x, -t.y);
+    t = cm(u[0], u[4]) - cm(u[1], u[3]); u[8] = mk<float>(t.x, -t.y);
+  } else {
+    const float4 d = p[3 * ASYNC_BT], e = p[4 * ASYNC_BT];
+    u[6] = mk<float>(d.x, d.y); u[7] = mk<float>(d.z, d.w);
+    u[8] = mk<float>(e.x, e.y);
+  }
+}
+
+template <typename S, int RECON, int MODE, int STAGES>
+__global__ void __launch_bounds__(ASYNC_BT) wilson_pair_async_kernel(const float4 *__restrict__ U,
+                                                                   const typename Chunk<S>::T *__restrict__ in,
+                                                                   typename Chunk<S>::T *__restrict__ out, float kappa,
+                                                                   int Lx, int Ly, int Lz, int Lt, int V, int nrhs,
+                                                                   int groups) {
+  using T = typename Chunk<S>::T;
+  constexpr int NC = RECON == 12 ? 3 : 5;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *ssp = (T *)smem_raw;
+  float4 *slk = (float4 *)(smem_raw + (size_t)STAGES * 12 * ASYNC_BT * sizeof(T));
+  const int tid = threadIdx.x;
+  const int s = (blockIdx.x / groups) * ASYNC_BT + tid;
+  if (s >= V) return;  // no block barrier below: threads past the lattice simply leave
+  const int r0 = (blockIdx.x % groups) * 2;
+  const bool second = r0 + 1 < nrhs;
+  const T *ia = in + (long long)r0 * 6 * V;
+  const T *ib = second ? ia + 6LL * V : ia;
+  constexpr bool G5IN = (MODE == 1 || MODE == 2);
+  int x = s % Lx, rr = s / Lx;
+  int y = rr % Ly;
+  rr /= Ly;
+  int z = rr % Lz;
+  int t = rr / Lz;
+  const int sy = Lx, sz = Lx * Ly, st = Lx * Ly * Lz;
+  int nb[8];
+  nb[0] = (x + 1 == Lx) ? s - (Lx - 1) : s + 1;
+  nb[1] = (x == 0) ? s + (Lx - 1) : s - 1;
+  nb[2] = (y + 1 == Ly) ? s - (Ly - 1) * sy : s + sy;
+  nb[3] = (y == 0) ? s + (Ly - 1) * sy : s - sy;
+  nb[4] = (z + 1 == Lz) ? s - (Lz - 1) * sz : s + sz;
+  nb[5] = (z == 0) ? s + (Lz - 1) * sz : s - sz;
+  nb[6] = (t + 1 == Lt) ? s - (Lt - 1) * st : s + st;
+  nb[7] = (t == 0) ? s + (Lt - 1) * st : s - st;
+  auto issue = [&](int d, int stage) {
+    const int mu = d >> 1;
+    const float4 *lp = U + (long long)mu * NC * V + ((d & 1) ? nb[d] : s);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cp_async_chunk(&slk[(stage * NC + c) * ASYNC_BT + tid], lp + (long long)c * V);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      cp_async_chunk(&ssp[(stage * 12 + q) * ASYNC_BT + tid], ia + (long long)q * V + nb[d]);
+      cp_async_chunk(&ssp[(stage * 12 + 6 + q) * ASYNC_BT + tid], ib + (long long)q * V + nb[d]);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < STAGES; ++d) issue(d, d);
+  Cx<P2> acc[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[a][c] = mk<P2>(p2(0.f, 0.f), p2(0.f, 0.f));
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const int stage = d % STAGES;
+    // groups issued after direction d: min(STAGES - 1, 7 - d)
+    if (7 - d >= STAGES - 1) cp_async_wait<STAGES - 1>();
+    else if (7 - d == 1) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    const int mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    Cx<P2> u[9], p[4][3];
+    {
+      Cx<float> uf[9];
+      link_from_smem<RECON>(&slk[stage * NC * ASYNC_BT + tid], uf);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) u[i] = mk<P2>(p2(uf[i].x, uf[i].x), p2(uf[i].y, uf[i].y));
+    }
+    PairSmem<S>::load(&ssp[(stage * 12) * ASYNC_BT + tid], &ssp[(stage * 12 + 6) * ASYNC_BT + tid], p);
+    if (d + STAGES < 8) issue(d + STAGES, stage);  // this thread's reads of the stage are done
+    if (G5IN) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Cx<P2> a0 = p[0][c], a1 = p[1][c];
+        p[0][c] = neg(p[2][c]); p[1][c] = neg(p[3][c]); p[2][c] = neg(a0); p[3][c] = neg(a1);
+      }
+    }
+    if (fwd) {
+      if (mu == 0) term_fwd<P2, 0>(p, u, acc);
+      if (mu == 1) term_fwd<P2, 1>(p, u, acc);
+      if (mu == 2) term_fwd<P2, 2>(p, u, acc);
+      if (mu == 3) term_fwd<P2, 3>(p, u, acc);
+    } else {
+      if (mu == 0) term_bwd<P2, 0>(p, u, acc);
+      if (mu == 1) term_bwd<P2, 1>(p, u, acc);
+      if (mu == 2) term_bwd<P2, 2>(p, u, acc);
+      if (mu == 3) term_bwd<P2, 3>(p, u, acc);
+    }
+  }
+  T *oa = out + (long long)r0 * 6 * V + s;
+  T *ob = oa + 6LL * V;
+  if (MODE == 3) {
+    PairIO<S>::store(oa, ob, V, acc, second);
+    return;
+  }
+  Cx<P2> p[4][3];
+  PairIO<S>::load(ia + s, ib + s, V, p);
+  if (G5IN) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Cx<P2> a0 = p[0][c], a1 = p[1][c];
+      p[0][c] = neg(p[2][c]); p[1][c] = neg(p[3][c]); p[2][c] = neg(a0); p[3][c] = neg(a1);
+    }
+  }
+  const P2 mk2 = p2(-kappa, -kappa);
+  Cx<P2> o[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[a][c] = mk<P2>(fma(mk2, acc[a][c].x, p[a][c].x), fma(mk2, acc[a][c].y, p[a][c].y));
+  if (MODE == 2) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Cx<P2> a0 = o[0][c], a1 = o[1][c];
+      o[0][c] = neg(o[2][c]); o[1][c] = neg(o[3][c]); o[2][c] = neg(a0); o[3][c] = neg(a1);
+    }
+  }
+  PairIO<S>::store(oa, ob, V, o, second);
+}
+
 // canonical complex128 fields -> packed storage S, y = sigma * x / s[r] (s == NULL: s[r] = 1)
 template <typename S>
 __global__ void pack_kernel(const double2 *__restrict__ x, const double *__restrict__ s,
                             typename Chunk<S>::T *__restrict__ y, int V, double sigma) {
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  if (site >= V) return;
-  double f = sigma;
-  if (s) {
-    const double d = s[r];
-    f = d > 0.0 ? sigma / d : 0.0;
+  __shared__ double fs;   // the scale once per block (one right-hand side per block row)
+  if (threadIdx.x == 0) {
+    double f = sigma;
+    if (s) {
+      const double d = s[r];
+      f = d > 0.0 ? sigma / d : 0.0;
+    }
+    fs = f;
   }
+  __syncthreads();
+  if (site >= V) return;
+  const double f = fs;
   const double2 *src = x + ((long long)r * V + site) * 12;
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
@@ -580,6 +774,9 @@ __global__ void unpack_kernel(const typename Chunk<S>::T *__restrict__ c, const 
                               double2 *__restrict__ x, int V, double sigma) {
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
+  __shared__ double ds;   // the scale once per block
+  if (threadIdx.x == 0) ds = s ? s[r] / sigma : 1.0 / sigma;
+  __syncthreads();
   if (site >= V) return;
   double2 *dst = x + ((long long)r * V + site) * 12;
 #pragma unroll
@@ -587,14 +784,14 @@ __global__ void unpack_kernel(const typename Chunk<S>::T *__restrict__ c, const 
     Cx<float> u, v;
     Chunk<S>::get(c + ((long long)r * 6 + q) * V + site, u, v);
     if (s) {
-      const double d = s[r] / sigma;
+      const double d = ds;
       double2 a = dst[2 * q], b = dst[2 * q + 1];
       a.x = fma(d, (double)u.x, a.x); a.y = fma(d, (double)u.y, a.y);
       b.x = fma(d, (double)v.x, b.x); b.y = fma(d, (double)v.y, b.y);
       dst[2 * q] = a;
       dst[2 * q + 1] = b;
     } else {
-      const double d = 1.0 / sigma;
+      const double d = ds;
       dst[2 * q] = make_double2(d * u.x, d * u.y);
       dst[2 * q + 1] = make_double2(d * v.x, d * v.y);
     }
@@ -645,6 +842,38 @@ lqcd_status pair_launch(lqcd_ctx *ctx, const float4 *U, double kappa, const void
   return launch_check_bytes(ctx, "wilson_pair_kernel", K_WILSON, (double)ctx->V * nrhs, bytes);
 }
 
+// staged variant of the paired-lane operator: 3 directions in flight for FP16 / BF16 fields, 2 for
+// FP32 fields (shared memory per block: stages x (12 x 128 chunks + NC x 128 link float4))
+template <typename S, int RECON>
+lqcd_status pair_async_launch(lqcd_ctx *ctx, const float4 *U, double kappa, const void *in_, void *out_, int nrhs,
+                              int flags) {
+  using T = typename Chunk<S>::T;
+  constexpr int STAGES = sizeof(T) == 16 ? 2 : 3;
+  constexpr int NC = RECON == 12 ? 3 : 5;
+  const T *in = (const T *)in_;
+  T *out = (T *)out_;
+  const int groups = (nrhs + 1) / 2;
+  const long long nblk = (long long)ceil_div(ctx->V, ASYNC_BT) * groups;
+  if (nblk > 0x7fffffffLL) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: grid too large");
+  const size_t smem = (size_t)STAGES * (12 * ASYNC_BT * sizeof(T) + NC * ASYNC_BT * sizeof(float4));
+  const int *d = ctx->dims;
+  const float k = (float)kappa;
+  auto go = [&](auto kern) -> lqcd_status {
+    LQCD_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kbegin(ctx);
+    kern<<<(unsigned)nblk, ASYNC_BT, smem, ctx->stream>>>(U, in, out, k, d[0], d[1], d[2], d[3], ctx->V, nrhs, groups);
+    const double bytes = 2.0 * nrhs * ctx->V * 6 * sizeof(T) + 4.0 * ctx->V * NC * 16;
+    return launch_check_bytes(ctx, "wilson_pair_async_kernel", K_WILSON, (double)ctx->V * nrhs, bytes);
+  };
+  switch (flags) {
+    case LQCD_APPLY_M: return go(wilson_pair_async_kernel<S, RECON, 0, STAGES>);
+    case LQCD_APPLY_G5R: return go(wilson_pair_async_kernel<S, RECON, 1, STAGES>);
+    case LQCD_APPLY_DAG: return go(wilson_pair_async_kernel<S, RECON, 2, STAGES>);
+    case LQCD_APPLY_HOP: return go(wilson_pair_async_kernel<S, RECON, 3, STAGES>);
+    default: return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: unknown flags %d", flags);
+  }
+}
+
 template <typename S, int NR, int RECON>
 lqcd_status packed_launch_nr(lqcd_ctx *ctx, const float4 *U, double kappa, const void *in_, void *out_, int nrhs,
                              int flags) {
@@ -682,14 +911,16 @@ lqcd_status wilson_launch_packed(lqcd_ctx *ctx, const float4 *U, int recon, doub
   // 2: on 24^3 x 32 with 8 and 16 right-hand sides the paired lanes take 13 % less time than one
   // right-hand side per thread (the stencil is bound by instruction issue, not by HBM)
   if (nr <= 0) nr = ctx->packed_nr > 0 ? ctx->packed_nr : 2;
-  if (nr == 2 && nrhs < 2) nr = 1;
+  if ((nr == 2 || nr == 3) && nrhs < 2) nr = 1;
   if (recon == 12) {
     if (nr == 1) return packed_launch_nr<float2, 1, 12>(ctx, U, kappa, in, out, nrhs, flags);
     if (nr == 2) return pair_launch<float2, 12>(ctx, U, kappa, in, out, nrhs, flags);
+    if (nr == 3) return pair_async_launch<float2, 12>(ctx, U, kappa, in, out, nrhs, flags);
     return packed_launch_nr<float2, 4, 12>(ctx, U, kappa, in, out, nrhs, flags);
   }
   if (nr == 1) return packed_launch_nr<float2, 1, 18>(ctx, U, kappa, in, out, nrhs, flags);
   if (nr == 2) return pair_launch<float2, 18>(ctx, U, kappa, in, out, nrhs, flags);
+  if (nr == 3) return pair_async_launch<float2, 18>(ctx, U, kappa, in, out, nrhs, flags);
   return packed_launch_nr<float2, 4, 18>(ctx, U, kappa, in, out, nrhs, flags);
 }
 
@@ -700,12 +931,15 @@ lqcd_status wilson_launch_packed_lp(lqcd_ctx *ctx, const float4 *U, int recon, d
                                    int nrhs, int flags) {
   if (nrhs <= 0) return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: nrhs %d out of range", nrhs);
   const bool pair = (ctx->packed_nr == 2 || ctx->packed_nr == 0) && nrhs >= 2;
+  const bool staged = ctx->packed_nr == 3 && nrhs >= 2;
   if (recon == 12)
-    return pair ? pair_launch<S, 12>(ctx, U, kappa, in, out, nrhs, flags)
-                : packed_launch_nr<S, 1, 12>(ctx, U, kappa, in, out, nrhs, flags);
+    return staged ? pair_async_launch<S, 12>(ctx, U, kappa, in, out, nrhs, flags)
+           : pair ? pair_launch<S, 12>(ctx, U, kappa, in, out, nrhs, flags)
+                  : packed_launch_nr<S, 1, 12>(ctx, U, kappa, in, out, nrhs, flags);
   if (recon == 18)
-    return pair ? pair_launch<S, 18>(ctx, U, kappa, in, out, nrhs, flags)
-                : packed_launch_nr<S, 1, 18>(ctx, U, kappa, in, out, nrhs, flags);
+    return staged ? pair_async_launch<S, 18>(ctx, U, kappa, in, out, nrhs, flags)
+           : pair ? pair_launch<S, 18>(ctx, U, kappa, in, out, nrhs, flags)
+                  : packed_launch_nr<S, 1, 18>(ctx, U, kappa, in, out, nrhs, flags);
   return set_err(ctx, LQCD_ERR_INVALID_ARG, "packed wilson: recon must be 12 or 18");
 }
 template lqcd_status wilson_launch_packed_lp<__half2>(lqcd_ctx *, const float4 *, int, double, const __half2 *,
@@ -772,8 +1006,8 @@ extern "C" lqcd_status lqcd_wilson_apply_packed(lqcd_ctx *ctx, const float *link
                                                 const float *in, float *out, int nrhs, int flags, int rhs_per_thread) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
   if (!links_packed || !in || !out || in == out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_packed: bad pointers");
-  if (rhs_per_thread != 0 && rhs_per_thread != 1 && rhs_per_thread != 2 && rhs_per_thread != 4)
-    return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_packed: rhs_per_thread must be 0, 1, 2 or 4");
+  if (rhs_per_thread < 0 || rhs_per_thread > 4)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_packed: rhs_per_thread must be 0, 1, 2, 3 or 4");
   return wilson_launch_packed(ctx, (const float4 *)links_packed, recon, kappa, (const float4 *)in, (float4 *)out, nrhs,
                               flags, rhs_per_thread);
 }
@@ -810,8 +1044,8 @@ extern "C" lqcd_status lqcd_wilson_apply_half(lqcd_ctx *ctx, int prec, const flo
 
 extern "C" lqcd_status lqcd_set_rhs_per_thread(lqcd_ctx *ctx, int nr) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
-  if (nr != 0 && nr != 1 && nr != 2 && nr != 4)
-    return set_err(ctx, LQCD_ERR_INVALID_ARG, "set_rhs_per_thread: nr must be 0, 1, 2 or 4");
+  if (nr < 0 || nr > 4)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "set_rhs_per_thread: nr must be 0, 1, 2, 3 or 4");
   graph_cache_clear(ctx);
   ctx->packed_nr = nr;
   return LQCD_OK;

@@ -35,7 +35,8 @@ class LqcdError(RuntimeError):
 
 class KrylovOpts(C.Structure):
     _fields_ = [("m", C.c_int), ("k", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int),
-                ("system", C.c_int), ("prec", C.c_int), ("inner_tol", C.c_double), ("eig_tol", C.c_double)]
+                ("system", C.c_int), ("prec", C.c_int), ("inner_tol", C.c_double), ("eig_tol", C.c_double),
+                ("poly_degree", C.c_int), ("poly_coeffs", C.c_void_p)]
 
 
 class SolveInfo(C.Structure):
@@ -50,7 +51,7 @@ class EstOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("nnoise", C.c_int), ("block", C.c_int), ("m", C.c_int), ("k", C.c_int),
                 ("m_inner", C.c_int), ("K", C.c_int), ("npoly", C.c_int), ("tol", C.c_double),
                 ("tol_special", C.c_double), ("max_cycles", C.c_int), ("modes", C.c_int), ("prec", C.c_int),
-                ("inner_tol", C.c_double), ("eig_tol", C.c_double), ("system", C.c_int)]
+                ("inner_tol", C.c_double), ("eig_tol", C.c_double), ("system", C.c_int), ("prec_degree", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -195,6 +196,16 @@ def _ptr(t, dtype=None):
 def _host_c(arr):
     a = np.ascontiguousarray(np.asarray(arr, dtype=np.complex128))
     return a, a.ctypes.data_as(C.c_void_p)
+
+
+def _set_poly(o, poly):
+    """Fill the polynomial-preconditioner fields of KrylovOpts o; returns the buffer to keep alive."""
+    if poly is None:
+        return None
+    a, ap = _host_c(poly)
+    o.poly_degree = len(a) - 1
+    o.poly_coeffs = ap
+    return a
 
 
 class Defl:
@@ -444,9 +455,10 @@ class Context:
         return out
 
     # GMRES-DR / MINRES-DR
-    def _krylov(self, fn, links, kappa, b, m, k, tol, max_cycles, system, want_defl, prec, eig_tol=0.0):
+    def _krylov(self, fn, links, kappa, b, m, k, tol, max_cycles, system, want_defl, prec, eig_tol=0.0, poly=None):
         x = _torch().empty_like(b)
         o = KrylovOpts(m, k, tol, max_cycles, system, prec, 0.0, eig_tol)
+        keep = _set_poly(o, poly)
         info = SolveInfo()
         dh = C.c_void_p()
         st = fn(self.h, _ptr(links), kappa, _ptr(b), _ptr(x), self._nrhs(b), C.byref(o), C.byref(info),
@@ -457,20 +469,22 @@ class Context:
         return x, info.as_dict(), defl
 
     def gmresdr_solve(self, links, kappa, b, m, k, tol, max_cycles=1000, system=SYS_M, want_defl=False,
-                      prec=PREC_F64, eig_tol=0.0):
+                      prec=PREC_F64, eig_tol=0.0, poly=None):
+        """poly: coefficients a_0..a_d of a polynomial right preconditioner p (Krylov on A p(A))."""
         return self._krylov(self.lib.lqcd_gmresdr_solve, links, kappa, b, m, k, tol, max_cycles, system,
-                            want_defl, prec, eig_tol)
+                            want_defl, prec, eig_tol, poly)
 
     def minresdr_solve(self, links, kappa, b, m, k, tol, max_cycles=1000, want_defl=False, prec=PREC_F64,
-                       eig_tol=0.0):
+                       eig_tol=0.0, poly=None):
         return self._krylov(self.lib.lqcd_minresdr_solve, links, kappa, b, m, k, tol, max_cycles, SYS_MG5,
-                            want_defl, prec, eig_tol)
+                            want_defl, prec, eig_tol, poly)
 
     # deflated multi-RHS solves
     def proj_solve(self, links, kappa, defl, b, m, tol, max_cycles=1000, system=SYS_M, prec=PREC_F64,
-                   inner_tol=0.0):
+                   inner_tol=0.0, poly=None):
         x = _torch().empty_like(b)
         o = KrylovOpts(m, 0, tol, max_cycles, system, prec, inner_tol)
+        keep = _set_poly(o, poly)
         info = SolveInfo()
         st = self.lib.lqcd_proj_solve(self.h, _ptr(links), kappa, defl.h, _ptr(b), _ptr(x), self._nrhs(b),
                                       C.byref(o), C.byref(info))
@@ -496,9 +510,9 @@ class Context:
     # loop estimate in two phases
     @staticmethod
     def _est_opts(seed, nnoise, block, m, k, K, npoly, tol, tol_special, m_inner=0, max_cycles=2000, modes=SUB_ALL,
-                  prec=PREC_F64, inner_tol=0.0, eig_tol=0.0, system=SYS_M):
+                  prec=PREC_F64, inner_tol=0.0, eig_tol=0.0, system=SYS_M, prec_degree=0):
         return EstOpts(seed, nnoise, block, m, k, m_inner, K, npoly, tol, tol_special, max_cycles, modes, prec,
-                       inner_tol, eig_tol, system)
+                       inner_tol, eig_tol, system, prec_degree)
 
     def loop_setup(self, links, kappa, seed, nnoise, block, m, k, K, npoly, tol, tol_special, **kw):
         """lqcd_loop_setup: special solves, polynomial, hopping traces, 1/xi', add-backs."""
@@ -603,10 +617,10 @@ class Context:
     # whole path
     def loop_estimate(self, links, kappa, seed, nnoise, block, m, k, K, npoly, tol, tol_special,
                       m_inner=0, max_cycles=2000, modes=SUB_ALL, prec=PREC_F64, inner_tol=0.0, eig_tol=0.0,
-                      system=SYS_M):
+                      system=SYS_M, prec_degree=0):
         """lqcd_loop_estimate; block = 0 lets the autotuner pick the block width."""
         o = EstOpts(seed, nnoise, block, m, k, m_inner, K, npoly, tol, tol_special, max_cycles, modes, prec,
-                    inner_tol, eig_tol, system)
+                    inner_tol, eig_tol, system, prec_degree)
         bufs, est = _estimate_buffers(self.dims[3], nnoise, k, npoly)
         st = self.lib.lqcd_loop_estimate(self.h, _ptr(links), kappa, C.byref(o), C.byref(est))
         if st not in (OK, ERR_NOT_CONVERGED):
@@ -677,7 +691,7 @@ def batch_loop_estimate(problems):
         opts[i] = EstOpts(p["seed"], p["nnoise"], p["block"], p["m"], p["k"], p.get("m_inner", 0), p["K"], p["npoly"],
                           p["tol"], p["tol_special"], p.get("max_cycles", 2000), p.get("modes", SUB_ALL),
                           p.get("prec", PREC_F64), p.get("inner_tol", 0.0), p.get("eig_tol", 0.0),
-                          p.get("system", SYS_M))
+                          p.get("system", SYS_M), p.get("prec_degree", 0))
         bufs, est = _estimate_buffers(p["ctx"].dims[3], p["nnoise"], p["k"], p["npoly"])
         ests[i] = est
         keep.append(bufs)

@@ -90,7 +90,9 @@ def test_packed_operators_24x24x24x32_sampled_sites():
     # <= 1 for Z(4) input, about 30 rounded operations deep: 30 * 2^-24 * 48 * 2 kappa < 1e-5
     fp32_abs = 1e-5
     cases = [("f32", None, 2.0 ** -24), ("f16", lqcd.PREC_F16, 2.0 ** -11), ("bf16", lqcd.PREC_BF16, 2.0 ** -8)]
-    for name, prec, u in cases:
+    cases = [(name + "/nr%d" % nr, prec, u, nr) for nr in (2, 3) for name, prec, u in cases]
+    for name, prec, u, nr in cases:
+        ctx.set_rhs_per_thread(nr)      # paired lanes, or paired lanes with staged neighbours
         if prec is None:
             y = ctx.unpack_f32(ctx.wilson_apply_packed(Up, 12, KAPPA, ctx.pack_f32(x)))
         else:

@@ -55,7 +55,7 @@ def test_wilson_all_forms(dims):
     assert np.array_equal(host(ctx.unpack_f32(packed)), psi.astype(np.complex64).astype(np.complex128))
     for recon in (18, 12):
         Up = ctx.pack_links_f32(Ud, recon)
-        for nr in (1, 2, 4):
+        for nr in (1, 2, 3, 4):   # 3: paired lanes with asynchronously staged neighbours
             for flag, ref in forms.items():
                 got = host(ctx.unpack_f32(ctx.wilson_apply_packed(Up, recon, kappa, packed, flags=flag,
                                                                   rhs_per_thread=nr)))
@@ -86,7 +86,7 @@ def test_wilson_half_storage(dims, prec):
         assert np.all(np.abs(part(back) - part(psi)) <= (u + 2.0 ** -24) * np.abs(part(psi)) + 1e-12)
     forms = {0: lambda f: L.wilson(U, kappa, f), 1: lambda f: L.wilson_g5(U, kappa, f),
              2: lambda f: L.wilson_dag(U, kappa, f), 3: lambda f: L.hop(U, f)}
-    for nr in (1, 2):   # one right-hand side per thread, or two in paired lanes (3 fields: one pair + odd one)
+    for nr in (1, 2, 3):   # one right-hand side per thread, two in paired lanes, or paired and staged (3 fields: one pair + odd one)
         ctx.set_rhs_per_thread(nr)
         for recon in (18, 12):
             Up = ctx.pack_links_f32(Ud, recon)

@@ -163,3 +163,29 @@ def test_hermitian_path_independent():
         got, want = g["per_noise"][i], ref[mode]["per_noise"]
         scale = np.abs(want).max(axis=0)
         assert np.all(np.abs(got - want) <= TOL * scale), mode
+
+
+@pytest.mark.parametrize("system", ["M", "MG5"])
+def test_polynomial_preconditioned_path_independent(system):
+    """prec_degree = 4 (Krylov solves on A p(A), x = p(A) y; Sec. 5.2's polynomial inside the
+    solver): against the oracle's preconditioned path, NS, PS, HFES and HFPS per noise at 1e-11
+    (their inputs are the converged solutions and eigenpairs), POLY modes within the bound of the
+    Min-Res coefficients' conditioning; sorted HFES eigenvalues at 1e-12."""
+    from paper_1903_06986_gb300 import lqcd
+    dims, kappa, seed = (2, 2, 2, 4), 0.120, 5
+    N, m, k, K, npoly = 4, 80, 8, 7, 6
+    U = synth.su3_links(dims, 0.45, 2)
+    ctx = context(dims)
+    sysc = lqcd.SYS_MG5 if system == "MG5" else lqcd.SYS_M
+    g = ctx.loop_estimate(dev(U), kappa, seed, N, 4, m, k, K, npoly, NTOL, 1e-14, eig_tol=1e-13, system=sysc,
+                          prec_degree=4)
+    ref, st, _ = PL.loop_estimate(U, kappa, dims, seed, N, m, k, K, npoly, NTOL, 1e-14, eig_tol=1e-13,
+                                  system=system, prec_degree=4)
+    assert g["converged"] and g["max_true_resid"] <= NTOL
+    assert np.allclose(np.sort(g["lam"].real), np.sort(st["lam"].real), rtol=1e-12, atol=1e-14)
+    for i, mode in enumerate(MODES):
+        if mode in ("poly", "defl_poly", "es"):
+            continue
+        got, want = g["per_noise"][i], ref[mode]["per_noise"]
+        scale = np.abs(want).max(axis=0)
+        assert np.all(np.abs(got - want) <= TOL * scale), mode

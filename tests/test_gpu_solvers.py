@@ -120,3 +120,27 @@ def test_mixed_precision_proj_reaches_fp64_tolerance(setup, prec):
         xe = np.linalg.solve(s["M"], b)
         assert np.linalg.norm(xm - xe) <= 10 * s["cond"] * tol * np.linalg.norm(xe)
         assert np.linalg.norm(xm - L.flat(host(x64)[r])) <= 20 * s["cond"] * tol * np.linalg.norm(xe)
+
+
+@pytest.mark.parametrize("hermitian", [False, True], ids=["gmresdr", "minresdr"])
+def test_polynomial_preconditioned_solve_matches_lu(hermitian):
+    """A solve with a polynomial right preconditioner (Krylov on A p(A), x = p(A) y) returns the
+    LU solution of A x = b within cond * tol, and its deflation space satisfies the Arnoldi relation
+    of the dense A p(A)."""
+    dims, kappa = (2, 2, 2, 4), 0.12
+    U = synth.su3_links(dims, 0.45, 2)
+    ctx = context(dims)
+    b = ctx.noise_z4(9, 0, 1)
+    A = L.dense(lambda v: (L.wilson_g5 if hermitian else L.wilson)(U, kappa, v), dims)
+    a = np.array([1.9, -0.8, 0.25, -0.03], dtype=np.complex128)
+    solve = ctx.minresdr_solve if hermitian else ctx.gmresdr_solve
+    x, info, defl = solve(dev(U), kappa, b, 30, 6, 1e-13, max_cycles=300, want_defl=True, poly=a)
+    assert info["converged"] and info["true_resid"] <= 1e-13
+    bh = host(b)[0].reshape(-1)
+    xe = np.linalg.solve(A, bh)
+    assert np.linalg.norm(host(x)[0].reshape(-1) - xe) <= 10 * np.linalg.cond(A) * 1e-13 * np.linalg.norm(xe)
+    B = A @ sum(a[j] * np.linalg.matrix_power(A, j) for j in range(len(a)))
+    ex = defl.export()
+    V = host(ex["V"]).reshape(7, -1).T
+    assert np.abs(B @ V[:, :6] - V @ ex["Hbar"]).max() < 1e-12 * np.abs(B).max()
+    defl.close()

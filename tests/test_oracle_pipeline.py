@@ -283,3 +283,47 @@ def test_hermitian_path_solves_and_estimates(dense_ops):
                 Th = d["thetas"][op]
                 ref = np.vdot(eta, Th @ (d["Minv"] - td[mode]) @ eta) + np.trace(Th @ td[mode])
                 assert abs(out[mode]["per_noise"][n, op] - ref) < 1e-9 * max(1.0, abs(ref)), (n, mode, op)
+
+
+@pytest.mark.parametrize("system", ["M", "MG5"])
+def test_polynomial_preconditioned_solves(dense_ops, system):
+    """prec_degree = 4: the noise solves work on B = A p(A) (A = M, or M' on the Hermitian path) with
+    p the Min-Res polynomial of A on the polynomial noise; the GMRES-DR space is one of the dense B,
+    the HFES eigenpairs are eigenpairs of the dense M', the solutions are the LU ones, the per-noise
+    values follow the dense formula, and the preconditioned solves need fewer Krylov steps."""
+    d = dense_ops
+    A = d["M"] @ d["G5"] if system == "MG5" else d["M"]
+    st = PL.setup(d["U"], KAPPA, DIMS, SEED, M_DR, K_DR, K_PS, NPOLY, 1e-14, system=system, prec_degree=4)
+    a = st["prec_a"]
+    if system == "MG5":
+        assert np.all(a.imag == 0.0)
+    pA = sum(a[j] * np.linalg.matrix_power(A, j) for j in range(len(a)))
+    B = A @ pA
+    b = L.flat(rng.z4_noise(SEED, rng.NOISE_POLY, DIMS))
+    cols = [np.linalg.matrix_power(A, j + 1) @ b for j in range(len(a))]
+    r = b - B @ b
+    assert max(abs(np.vdot(c, r)) / (np.linalg.norm(c) * np.linalg.norm(b)) for c in cols) < 1e-6
+    V, H = st["defl_m"]["V"], st["defl_m"]["Hbar"]
+    assert np.abs(B @ V[:, :K_DR] - V @ H).max() < 1e-11
+    Mp = d["M"] @ d["G5"]
+    res = np.linalg.norm(Mp @ st["Ev"] - st["Ev"] * st["lam"][None, :], axis=0)
+    assert np.all(res <= st["eig_resid"] + 1e-12)
+    xs, infos = PL.solve_noises(st, DIMS, SEED, 0, 2, M_DR - K_DR, 1e-12)
+    cond = np.linalg.cond(d["M"])
+    for i in range(2):
+        x = d["Minv"] @ L.flat(rng.z4_noise(SEED, i, DIMS))
+        assert np.linalg.norm(L.flat(xs[i]) - x) <= 10 * cond * 1e-12 * np.linalg.norm(x)
+    st_plain = PL.setup(d["U"], KAPPA, DIMS, SEED, M_DR, K_DR, K_PS, NPOLY, 1e-14, system=system)
+    _, infos_plain = PL.solve_noises(st_plain, DIMS, SEED, 0, 2, M_DR - K_DR, 1e-12)
+    steps = lambda inf: sum(len(i["resid"]) for i in inf)
+    assert steps(infos) < steps(infos_plain)
+    out, st2, _ = PL.loop_estimate(d["U"], KAPPA, DIMS, SEED, 2, M_DR, K_DR, K_PS, NPOLY, 1e-12, 1e-14,
+                                   system=system, prec_degree=4)
+    td = tilde_dense(d, st2)
+    for n in range(2):
+        eta = L.flat(rng.z4_noise(SEED, n, DIMS))
+        for mode in E.MODES:
+            for op in (0, 4, 8):
+                Th = d["thetas"][op]
+                ref = np.vdot(eta, Th @ (d["Minv"] - td[mode]) @ eta) + np.trace(Th @ td[mode])
+                assert abs(out[mode]["per_noise"][n, op] - ref) < 1e-8 * max(1.0, abs(ref)), (n, mode, op)
