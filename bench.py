@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-defl", action="store_true")
     ap.add_argument("--no-cfg2", action="store_true")
+    ap.add_argument("--no-cfg35", action="store_true", help="skip the 16^3x32 and 12^3x24 derivative lines")
     ap.add_argument("--batch", action="store_true", help="also measure the uneven multi-lattice batch")
     ap.add_argument("--prec-degree", type=int, default=PREC_DEGREE,
                     help="degree of the polynomial preconditioner of the noise solves (0 = none)")
@@ -537,6 +538,104 @@ def cfg2_fp64(torch):
     return out
 
 
+CFG3_DIMS = (16, 16, 16, 32)
+CFG3_M, CFG3_K = 200, 160
+CFG3_NOISE, CFG3_TIMED = 200, 64
+
+
+def cfg3_batching(torch):
+    """The 16^3 x 32 multi-right-hand-side workload in plain FP64: kappa 0.157, links of the main
+    generator at plaquette 0.6, 160 eigenvectors from one MINRES-DR(200,160) run on M' = M gamma_5
+    (GMRES-DR on M stagnates beyond this field's critical kappa), the 200 noises' block width picked
+    by the autotuner among 8, 16, 32 and 64.  Timed: the first 64 noises (whole blocks of the chosen
+    width), CUDA events on the library's stream; the rate of the other 136 is the same per noise."""
+    from paper_1903_06986_gb300 import lqcd, synth
+    U = torch.from_numpy(synth.su3_links(CFG3_DIMS, LINK_EPS, LINK_SEED + 1)).cuda()
+    ctx = lqcd.Context(CFG3_DIMS, recon=12)
+    ctx.set_defl_engine(lqcd.DEFL_TENSOR)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loop = ctx.loop_setup(U, KAPPA, NOISE_SEED, CFG3_NOISE, 0, CFG3_M, CFG3_K, K_PS, NPOLY, TOL, TOL_SPECIAL,
+                          m_inner=M_INNER, max_cycles=MAX_CYCLES, prec=lqcd.PREC_F64, system=lqcd.SYS_MG5)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = loop.info()
+    bw = info["block"]
+    loop.noises(U, 0, bw)  # warm-up: workspace and graphs at the chosen width
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ntimed = max(bw, CFG3_TIMED // bw * bw)
+    e0.record()
+    stats = [loop.noises(U, first, bw)[1] for first in range(0, ntimed, bw)]
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1000.0
+    if not all(s["converged"] and s["max_true_resid"] <= TOL for s in stats):
+        raise RuntimeError("16^3x32 noise solves did not reach the tolerance")
+    out = {"workload": "16^3x32 plain FP64, kappa 0.157 (plaquette 0.600), 200 Z4 noises in autotuned blocks, "
+                       "MINRES-DR(200,160) on M gamma_5, Q=160, GMRES-Proj(40) to 1e-10, PS K=7, POLY n=6, 6 modes",
+           "value": ntimed / t, "unit": "estimates/s", "noises_timed": ntimed,
+           "autotuned_block": bw, "block_candidates": [8, 16, 32, 64], "Q": info["Q"],
+           "setup_s": setup_s, "setup_matvecs": info["matvecs_setup"], "eig_resid_max": info["eig_resid_max"],
+           "amortised_estimates_per_s": CFG3_NOISE / (setup_s + CFG3_NOISE * t / ntimed),
+           "matvecs_per_noise": sum(s["matvecs"] for s in stats) / ntimed,
+           "max_true_resid": max(s["max_true_resid"] for s in stats)}
+    loop.close()
+    ctx.close()
+    return out
+
+
+CFG5_DIMS = (12, 12, 12, 24)
+CFG5_KAPPA, CFG5_NOISE, CFG5_BLOCK = 0.155, 64, 16
+CFG5_M, CFG5_K = 80, 40
+CFG5_H = 1e-5
+
+
+def cfg5_derivs(torch):
+    """The 12^3 x 24 differentiation workload: d Tr(Theta M^{-1}) / dkappa of the nine operators (NS
+    and PS) and the link gradient of the NS scalar estimate, 64 noises, kappa 0.155, a MINRES-DR(80,40)
+    space of M' (40 vectors) for the GMRES-Proj solves, in plain FP64 and in FP16 / FP32 mixed
+    precision (3 solves per noise, 1e-10).  Check: a central difference (h = 1e-5) of the NS and PS
+    loop estimates over the same noises against the FP64 d/dkappa."""
+    from paper_1903_06986_gb300 import lqcd, synth
+    U = torch.from_numpy(synth.su3_links(CFG5_DIMS, LINK_EPS, LINK_SEED + 2)).cuda()
+    ctx = lqcd.Context(CFG5_DIMS, recon=12)
+    args = (NOISE_SEED, CFG5_NOISE, CFG5_BLOCK, CFG5_M, CFG5_K, K_PS, TOL, TOL_SPECIAL)
+    run = lambda prec: lqcd.loop_derivs(ctx, U, CFG5_KAPPA, *args, m_inner=M_INNER, max_cycles=MAX_CYCLES,
+                                        prec=prec, system=lqcd.SYS_MG5)
+    out = {"workload": "12^3x24 kappa 0.155, 64 Z4 noises in blocks of 16, MINRES-DR(80,40) on M gamma_5, "
+                       "GMRES-Proj(40) x 3 solves per noise to 1e-10; d/dkappa of 9 operators (NS, PS K=7) and "
+                       "the link gradient of the NS scalar estimate (setup included)"}
+    res = {}
+    for name, prec in (("fp64", lqcd.PREC_F64), ("fp16", lqcd.PREC_F16)):
+        run(prec)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = run(prec)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        if not r["converged"] or r["max_true_resid"] > TOL:
+            raise RuntimeError("derivative solves did not reach the tolerance")
+        res[name] = r
+        out[name] = {"value": CFG5_NOISE / t, "unit": "noise derivatives/s", "s": t, "matvecs": r["matvecs"]}
+    d64, d16 = res["fp64"], res["fp16"]
+    g64, g16 = d64["link_grad"].cpu().numpy(), d16["link_grad"].cpu().numpy()
+    out["fp16_vs_fp64"] = {
+        "dkappa_max_rel_diff": float((np.abs(d16["dkappa"] - d64["dkappa"]) /
+                                      np.maximum(np.abs(d64["dkappa"]), 1e-300)).max()),
+        "link_grad_rel_diff": float(np.linalg.norm(g16 - g64) / np.linalg.norm(g64))}
+    # central difference of the estimates themselves (same noises, solves to 1e-12)
+    kw = dict(m=CFG5_M, k=CFG5_K, K=K_PS, npoly=NPOLY, tol=1e-12, tol_special=1e-12, m_inner=M_INNER,
+              max_cycles=MAX_CYCLES, system=lqcd.SYS_MG5, modes=lqcd.SUB_NONE | lqcd.SUB_PERT)
+    f = {sg: ctx.loop_estimate(U, CFG5_KAPPA + sg * CFG5_H, NOISE_SEED, CFG5_NOISE, CFG5_BLOCK, **kw)["mean"]
+         for sg in (-1, 1)}
+    fd = (f[1] - f[-1]) / (2 * CFG5_H)
+    rel = [float(np.max(np.abs(d64["dkappa"][m] - fd[m]) / np.maximum(np.abs(fd[m]), 1e-300))) for m in range(2)]
+    out["dkappa_vs_central_difference"] = {"h": CFG5_H, "max_rel_diff_ns": rel[0], "max_rel_diff_ps": rel[1]}
+    ctx.close()
+    return out
+
+
 def _block_first(i):
     """First noise of step i: the steps run through the 100 noises in blocks of BLOCK, cyclically."""
     return (BLOCK * i) % NNOISE
@@ -699,6 +798,18 @@ def main():
     del Ud
     torch.cuda.empty_cache()
     cfg2 = None if args.no_cfg2 else cfg2_fp64(torch)
+    cfg3 = cfg5 = None
+    if not args.no_cfg35:
+        for name, fn in (("cfg3", cfg3_batching), ("cfg5", cfg5_derivs)):
+            try:
+                r = fn(torch)
+            except Exception as e:  # reported, not fatal: the headline numbers above stand on their own
+                r = {"error": str(e)[:300]}
+            torch.cuda.empty_cache()
+            if name == "cfg3":
+                cfg3 = r
+            else:
+                cfg5 = r
     dslash = None if args.no_dslash else dslash_rates(torch)
     deflation = None
     if not args.no_defl:
@@ -744,7 +855,7 @@ def main():
                                "speedup_fp16_vs_fp64": value / (BLOCK * world / t_fp64),
                                "speedup_bf16_vs_fp64": (BLOCK * nb16 / t_bf16) / (BLOCK / t_fp64)},
                 "estimate_vs_fp64": errors,
-                "cfg2_fp64": cfg2, "dslash": dslash, "deflation_tensor_cores": deflation, "batching": batching}
+                "cfg2_fp64": cfg2, "cfg3_16x32_fp64": cfg3, "cfg5_derivs": cfg5, "dslash": dslash, "deflation_tensor_cores": deflation, "batching": batching}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -414,6 +414,15 @@ typedef struct {
                          real coefficients there) on the polynomial noise; the Krylov methods
                          work on A p(A) (lqcd_krylov_opts.poly_degree).  HFES eigenvalues are then
                          Rayleigh quotients of M' on the Ritz vectors; ES is off.  0 = none     */
+  int evenodd;        /* 1: the noise solves run on the even/odd reduced system (Sec. 7; every
+                         extent even, plain FP64 only, prec_degree 0): a reduced context of the
+                         lattice, its own GMRES-DR (MINRES-DR on hat M gamma_5 on the Hermitian
+                         path) space of the special right-hand side for GMRES-Proj, per noise
+                         hat M x_e = eta_e + kappa P_eo eta_o to a tolerance that bounds the full
+                         relative residual by tol, x_o = eta_o + kappa P_oe x_e, and the full FP64
+                         true residual checked.  ES then uses the full eigenpairs of M built from
+                         the reduced ones (lqcd_eo_full_eigenpairs).  HFES keeps the MINRES-DR
+                         eigenpairs of the full M'.  lqcd_loop_derivs rejects 1.  0 = full system */
 } lqcd_est_opts;
 
 typedef struct {
@@ -513,6 +522,14 @@ lqcd_status lqcd_autotune_block(lqcd_ctx *ctx, const double *links, double kappa
  * same kernels are launched one by one. */
 lqcd_status lqcd_set_graphs(lqcd_ctx *ctx, int enable);
 
+/* Gram-Schmidt passes per Arnoldi step of the inner GMRES-Proj cycles of mixed-precision solves
+ * (FP32, FP16 or BF16 basis): 2 = classical Gram-Schmidt twice (default), 1 = once.  One pass halves
+ * the basis traffic of the inner cycles; the orthogonality it loses is bounded by the storage
+ * rounding of a half-precision basis anyway, and the outer FP64 defect correction still stops on
+ * the FP64 true residual, so only the inner convergence rate can change.  FP64 Krylov solves
+ * always use two passes.  LQCD_ERR_INVALID_ARG for other values. */
+lqcd_status lqcd_set_inner_gs_passes(lqcd_ctx *ctx, int passes);
+
 /* Loop estimates of n independent problems (lattices of any, uneven, sizes), run concurrently: each
  * context (all distinct) works on its own private stream from its own host thread, ordered after
  * the work already queued on its stream (links ready there) and before the work queued there
@@ -551,11 +568,54 @@ typedef struct {
  * perturbative subtraction (PS, opts->K terms, differentiated term by term), and the gradient of
  * the NS scalar estimate with respect to every link.  Per noise three solves run (x = M^{-1} eta,
  * y = M^{-1} P x, and the adjoint w = M^{-1} g5 eta, z = g5 w) with GMRES-Proj over a GMRES-DR
- * space of the special right-hand side, to opts->tol (opts->prec selects plain FP64 or mixed
- * precision); nothing is kept from a previous call.  Uses opts seed, nnoise, block, m, k, m_inner,
- * K, tol, tol_special, max_cycles, prec. */
+ * space of the special right-hand side (or, with opts->system = LQCD_SYS_MG5, over a MINRES-DR
+ * space of M' with every solve done as M' y = b, x = gamma_5 y), to opts->tol (opts->prec selects
+ * plain FP64 or mixed precision); nothing is kept from a previous call.  Uses opts seed, nnoise,
+ * block, m, k, m_inner, K, tol, tol_special, max_cycles, prec, eig_tol, system. */
 lqcd_status lqcd_loop_derivs(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *opts,
                              lqcd_derivs *out);
+
+/* ---- even/odd preconditioning (Sec. 7) ------------------------------------------------------
+ * With every extent even and a site's parity (x + y + z + t) mod 2, P couples only opposite
+ * parities; eliminating the odd sites leaves the reduced matrix on the even sites
+ *   hat M = 1 - kappa^2 P_eo P_oe,  hat M x_e = b_e + kappa P_eo b_o,  x_o = b_o + kappa P_oe x_e.
+ * A reduced field holds the sites of one parity in lexicographic order of the full site index
+ * (compact index s >> 1): [nrhs][V/2][spin 4][colour 3] complex128.  Links stay the full
+ * [mu][V][3][3] array. */
+
+/* Create a reduced context for the even sites of an Lx x Ly x Lz x Lt lattice (every extent even,
+ * 2..1024, at most 2^28 sites).  Its fields have 12 V/2 complex entries, and on it
+ * lqcd_wilson_apply applies hat M (LQCD_APPLY_M), hat M gamma_5 (LQCD_APPLY_G5R; Hermitian),
+ * hat M^dag = gamma_5 hat M gamma_5 (LQCD_APPLY_DAG) or P_eo P_oe (LQCD_APPLY_HOP), in FP64 or FP32
+ * arithmetic, and lqcd_gmresdr_solve / lqcd_minresdr_solve / lqcd_proj_solve (plain precision) and
+ * lqcd_deflate_project solve and deflate the reduced system.  Entry points that need the full
+ * lattice (noise, contractions, traces, loop estimates, packed and mixed-precision operators)
+ * return LQCD_ERR_INVALID_ARG on it.  Destroy with lqcd_ctx_destroy. */
+lqcd_status lqcd_ctx_create_evenodd(lqcd_ctx **ctx, const int dims[4], int link_recon, void *stream);
+
+/* Split nrhs full fields into their even and odd halves (either output may be NULL), or join them
+ * back.  Device pointers; outputs must not overlap inputs. */
+lqcd_status lqcd_eo_split(lqcd_ctx *ctx, const double *full, double *even, double *odd, int nrhs);
+lqcd_status lqcd_eo_join(lqcd_ctx *ctx, const double *even, const double *odd, double *full, int nrhs);
+
+/* out = P_eo in (parity_out = 0: in odd, out even) or P_oe in (parity_out = 1), reduced fields. */
+lqcd_status lqcd_eo_hop(lqcd_ctx *ctx, const double *links, const double *in, double *out, int nrhs, int parity_out);
+
+/* Reduced right-hand side be = b_e + kappa P_eo b_o of nrhs full fields b. */
+lqcd_status lqcd_eo_rhs(lqcd_ctx *ctx, const double *links, double kappa, const double *b, double *be, int nrhs);
+
+/* Full solution x (nrhs full fields) from the reduced one: x_e = xe, x_o = b_o + kappa P_oe x_e. */
+lqcd_status lqcd_eo_reconstruct(lqcd_ctx *ctx, const double *links, double kappa, const double *xe, const double *b,
+                                double *x, int nrhs);
+
+/* Full eigenpairs of M from Q reduced eigenpairs (mu_q, v_e^(q)) of hat M: if M v = lambda v then
+ * hat M v_e = mu v_e with mu = 1 - (1 - lambda)^2, so each reduced pair gives the two full pairs
+ * 1 - lambda = +-sqrt(1 - mu) (principal root; + first), v = (v_e, kappa P_oe v_e / (1 - lambda))
+ * normalised to unit length.  mu: host Q complex; Ve: device Q reduced fields; lam: host 2Q
+ * complex out; E: device 2Q full fields out.  LQCD_ERR_INVALID_ARG when some |sqrt(1 - mu)| <= tol
+ * (lambda = 1: the odd half is undefined).  Synchronises the context's stream. */
+lqcd_status lqcd_eo_full_eigenpairs(lqcd_ctx *ctx, const double *links, double kappa, const double *mu,
+                                    const double *Ve, int Q, double tol, double *lam, double *E);
 
 
 #ifdef __cplusplus

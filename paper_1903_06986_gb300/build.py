@@ -16,7 +16,7 @@ SRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "liblqcd.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["ctx.cu", "wilson.cu", "blas.cu", "krylov.cu", "loops.cu", "derivs.cu", "batch.cu", "tcdefl.cu", "dense.cpp"]
+SOURCES = ["ctx.cu", "wilson.cu", "blas.cu", "krylov.cu", "loops.cu", "derivs.cu", "batch.cu", "tcdefl.cu", "evenodd.cu", "dense.cpp"]
 
 
 def nvcc():

@@ -136,6 +136,7 @@ extern "C" lqcd_status lqcd_autotune_block(lqcd_ctx *ctx, const double *links, d
                                            const lqcd_krylov_opts *opts, const int *cand, int ncand, int *best,
                                            double *seconds) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "autotune_block"));
   if (!links || !defl || !opts || !cand || ncand < 1 || !best)
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "autotune_block: bad arguments");
   if (!defl->V || !defl->Hbar_dev) return set_err(ctx, LQCD_ERR_INVALID_ARG, "autotune_block: needs a solver-made deflation space");

@@ -647,6 +647,7 @@ lqcd_status check_finite(lqcd_ctx *ctx, const double *x, long long n, const char
 
 extern "C" lqcd_status lqcd_noise_z4(lqcd_ctx *ctx, uint64_t seed, uint32_t first_noise, int nrhs, double *out) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "noise_z4"));
   if (!out || nrhs <= 0 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "noise_z4: bad arguments");
   return noise_launch(ctx, seed, first_noise, nrhs, (double2 *)out);
 }

@@ -72,6 +72,11 @@ struct lqcd_ctx {
   int defl_engine;           // LQCD_DEFL_FP64 or LQCD_DEFL_TENSOR (deflation projections)
   unsigned long long tc_wait_ns;  // bound of every tensor-core pipeline wait (lqcd_set_wait_limit)
   int tc_stop_after;         // injected stall of the next tensor-core launch (-1: none)
+  int inner_gs_passes;       // Gram-Schmidt passes of the reduced-precision inner Arnoldi (1 or 2)
+  // even/odd reduced context (lqcd_ctx_create_evenodd): fields hold the even sites only (V above is
+  // half the lattice), the operator is hat M = 1 - kappa^2 P_eo P_oe, eo_dims the full extents
+  int eo;
+  int eo_dims[4];
 };
 
 struct lqcd_defl {
@@ -118,7 +123,7 @@ enum WsSlot {
   WS_PARTIAL = 0, WS_SCAL, WS_TMP0, WS_TMP1, WS_TMP2, WS_TMP3, WS_BASIS, WS_HESS, WS_COEF,
   WS_BASIS2, WS_TMP4, WS_TMP5, WS_EST0, WS_EST1, WS_EST2, WS_PROBE,
   WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_COUNT, WS_TUNE, WS_SPEC, WS_NBLK, WS_TC_STAT, WS_TC_B, WS_TC_PART, WS_TC_D,
-  WS_POLY1, WS_POLY2, WS_POLY3, WS_NSLOTS
+  WS_POLY1, WS_POLY2, WS_POLY3, WS_EO, WS_NSLOTS
 };
 lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr);
 void graph_cache_clear(lqcd_ctx *ctx);
@@ -186,6 +191,17 @@ static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) 
 // Wilson operator on nrhs fields (see lqcd_wilson_apply); in and out must not overlap.
 lqcd_status wilson_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in,
                           double2 *out, int nrhs, int prec, int flags);
+// Reduced (even/odd) operator of an eo context: hat M, hat M gamma_5, hat M^dag or P_eo P_oe
+lqcd_status eo_schur_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in, double2 *out, int nrhs,
+                            int prec, int flags);
+// reserve the odd-site scratch of eo_schur_launch for nrhs fields (no-op on a full context)
+lqcd_status eo_reserve(lqcd_ctx *ctx, int nrhs);
+// LQCD_ERR_INVALID_ARG on an even/odd reduced context (entry points that need the full lattice)
+lqcd_status require_full(lqcd_ctx *ctx, const char *what);
+// b_e + kappa P_eo b_o (b full, be reduced) and the full solution from x_e (x_o = b_o + kappa P_oe x_e)
+lqcd_status eo_rhs_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *b, double2 *be, int nrhs);
+lqcd_status eo_reconstruct_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *xe, const double2 *b,
+                                  double2 *x, int nrhs);
 // FP64, right-hand side r gets M gamma_5 when bit r of g5mask is set and M otherwise (nrhs <= 64)
 lqcd_status wilson_launch_masked(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in, double2 *out,
                                  int nrhs, unsigned long long g5mask);

@@ -196,6 +196,7 @@ lqcd_status link_grad_launch(lqcd_ctx *ctx, const double2 *U, double kappa, cons
 extern "C" lqcd_status lqcd_link_grad(lqcd_ctx *ctx, const double *links, double kappa, const double *z, const double *x,
                                       int nrhs, double scale, double *grad, double *grad_links) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "link_grad"));
   if (!links || !z || !x || !grad || nrhs < 1) return set_err(ctx, LQCD_ERR_INVALID_ARG, "link_grad: bad arguments");
   return link_grad_launch(ctx, (const double2 *)links, kappa, (const double2 *)z, (const double2 *)x, nrhs, scale,
                           (double2 *)grad, (double2 *)grad_links);
@@ -211,12 +212,16 @@ lqcd_status hop_traces_launch(lqcd_ctx *ctx, const double2 *U, double kappa, int
 extern "C" lqcd_status lqcd_loop_derivs(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *o,
                                         lqcd_derivs *out) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "loop_derivs"));
   if (!links || !o || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_derivs: NULL argument");
   if (o->nnoise < 1 || o->block < 1 || o->m < 2 || o->k < 1 || o->k >= o->m || o->K < 1 || o->K > 64 ||
       !(o->tol > 0) || !(o->tol_special > 0) || o->max_cycles < 1 || !(kappa != 0.0))
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_derivs: bad options");
   if (o->prec < LQCD_PREC_F64 || o->prec > LQCD_PREC_BF16)
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_derivs: prec must be one of LQCD_PREC_*");
+  if (o->system != LQCD_SYS_M && o->system != LQCD_SYS_MG5)
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_derivs: system must be LQCD_SYS_M or LQCD_SYS_MG5");
+  if (o->evenodd) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_derivs: even/odd solves are not available here");
   const double t0 = now_s();
   const double2 *U = (const double2 *)links;
   const int Lt = ctx->dims[3];
@@ -238,7 +243,11 @@ extern "C" lqcd_status lqcd_loop_derivs(lqcd_ctx *ctx, const double *links, doub
   LQCD_TRY(noise_launch(ctx, o->seed, 0xFFFFFFFEu, 1, bs));
   lqcd_krylov_opts ko{o->m, o->k, o->tol_special, o->max_cycles, LQCD_SYS_M, LQCD_PREC_F64, 0.0, o->eig_tol};
   lqcd_solve_info si{};
-  lqcd_status st = lqcd_gmresdr_solve(ctx, links, kappa, (const double *)bs, (double *)xs, 1, &ko, &si, &dm);
+  // system M: GMRES-DR on M; the Hermitian path: MINRES-DR on M' = M gamma_5, and every solve of
+  // M x = b below is M' y = b, x = gamma_5 y
+  const bool herm = o->system == LQCD_SYS_MG5;
+  lqcd_status st = herm ? lqcd_minresdr_solve(ctx, links, kappa, (const double *)bs, (double *)xs, 1, &ko, &si, &dm)
+                        : lqcd_gmresdr_solve(ctx, links, kappa, (const double *)bs, (double *)xs, 1, &ko, &si, &dm);
   if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
   if (!dm) return set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop_derivs: no deflation space");
   long matvecs = si.matvecs;
@@ -261,9 +270,10 @@ extern "C" lqcd_status lqcd_loop_derivs(lqcd_ctx *ctx, const double *links, doub
   const int bw = std::min(o->block, nn);
   const long long bn = (long long)bw * N;
   double2 *eta;
-  LQCD_CUDA(ctx, cudaMalloc(&eta, sizeof(double2) * (size_t)bn * 8));
+  LQCD_CUDA(ctx, cudaMalloc(&eta, sizeof(double2) * (size_t)bn * 9));
   struct Guard2 { void *p; ~Guard2() { if (p) cudaFree(p); } } g2{eta};
   double2 *x = eta + bn, *px = x + bn, *y = px + bn, *g5e = y + bn, *w = g5e + bn, *xp = w + bn, *dxp = xp + bn;
+  double2 *hy = dxp + bn;  // the Hermitian path's M' solution before gamma_5
   double2 *cdv;
   LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)bw * 9 * Lt * 4, (void **)&cdv));
   if (out->link_grad) LQCD_CUDA(ctx, cudaMemsetAsync(out->link_grad, 0, sizeof(double2) * (size_t)ctx->V * 32, ctx->stream));
@@ -280,14 +290,17 @@ extern "C" lqcd_status lqcd_loop_derivs(lqcd_ctx *ctx, const double *links, doub
     const long long len = (long long)nb * N;
     LQCD_TRY(noise_launch(ctx, o->seed, (uint32_t)first, nb, eta));
     lqcd_solve_info a{}, b{}, c{};
-    st = proj_core_entry(ctx, links, kappa, dm, eta, x, nb, &po, &a);
-    if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
+    // x = M^{-1} rhs (directly, or gamma_5 M'^{-1} rhs on the Hermitian path)
+    auto solve = [&](const double2 *rhs, double2 *xo, lqcd_solve_info *inf) -> lqcd_status {
+      const lqcd_status s2 = proj_core_entry(ctx, links, kappa, dm, rhs, herm ? hy : xo, nb, &po, inf);
+      if (s2 != LQCD_OK && s2 != LQCD_ERR_NOT_CONVERGED) return s2;
+      return herm ? blas_g5(ctx, hy, xo, nb) : LQCD_OK;
+    };
+    LQCD_TRY(solve(eta, x, &a));
     LQCD_TRY(wilson_launch(ctx, U, kappa, x, px, nb, LQCD_PREC_F64, LQCD_APPLY_HOP));
-    st = proj_core_entry(ctx, links, kappa, dm, px, y, nb, &po, &b);
-    if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
+    LQCD_TRY(solve(px, y, &b));
     LQCD_TRY(blas_g5(ctx, eta, g5e, nb));
-    st = proj_core_entry(ctx, links, kappa, dm, g5e, w, nb, &po, &c);
-    if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
+    LQCD_TRY(solve(g5e, w, &c));
     LQCD_TRY(blas_g5(ctx, w, g5e, nb));  // z = g5 M^{-1} g5 eta (reuses the g5e buffer)
     for (const lqcd_solve_info *i : {&a, &b, &c}) {
       matvecs += i->matvecs;

@@ -87,6 +87,7 @@ template <typename S, typename Derived> struct PolyApply {
   // reserve the scratch blocks of the polynomial for nrhs right-hand sides
   lqcd_status reserve(lqcd_ctx *ctx, int nrhs) {
     Derived &d = static_cast<Derived &>(*this);
+    LQCD_TRY(eo_reserve(ctx, nrhs));
     if (d.pp.degree == 0) return LQCD_OK;
     const size_t bytes = sizeof(S) * (size_t)nrhs * ctx->N;
     LQCD_TRY(ws_get(ctx, WS_POLY1, bytes, &d.pp.t1));
@@ -207,11 +208,13 @@ template <typename S> struct ArnoldiT {
   S *Vb;
   double2 *hd1, *hd2;  // [j][i][r] device, (m) x (m+1) x nrhs
   double *nrm;         // [j][r]
+  int passes = 2;      // Gram-Schmidt passes per step: 2 (CGS2), or 1 (CGS) for reduced-precision bases
 };
 using Arnoldi = ArnoldiT<double2>;
 
-// The launches of Arnoldi steps j0..m-1 (CGS2: two passes of inner products and updates, then the
-// norm and the normalisation), nothing else: no synchronisation, so the sequence can be captured.
+// The launches of Arnoldi steps j0..m-1 (CGS2: two passes of inner products and updates, or one
+// pass when a.passes == 1, then the norm and the normalisation), nothing else: no synchronisation,
+// so the sequence can be captured.
 template <typename S> struct ArnoldiLaunch {
   ArnoldiT<S> *a;
   int j0;
@@ -229,8 +232,10 @@ lqcd_status arnoldi_enqueue(void *arg) {
     double2 *h2 = a.hd2 + (long long)j * (a.m + 1) * a.nrhs;
     LQCD_TRY(blas_multidot(ctx, a.Vb, vs, N, j + 1, w, N, a.nrhs, h1));
     LQCD_TRY(blas_multiaxpy(ctx, a.Vb, vs, N, j + 1, h1, -1.0, w, N, a.nrhs));
-    LQCD_TRY(blas_multidot(ctx, a.Vb, vs, N, j + 1, w, N, a.nrhs, h2));
-    LQCD_TRY(blas_multiaxpy(ctx, a.Vb, vs, N, j + 1, h2, -1.0, w, N, a.nrhs));
+    if (a.passes > 1) {
+      LQCD_TRY(blas_multidot(ctx, a.Vb, vs, N, j + 1, w, N, a.nrhs, h2));
+      LQCD_TRY(blas_multiaxpy(ctx, a.Vb, vs, N, j + 1, h2, -1.0, w, N, a.nrhs));
+    }
     LQCD_TRY(blas_norms(ctx, w, N, a.nrhs, a.nrm + (long long)j * a.nrhs));
     LQCD_TRY(blas_invscale(ctx, w, a.nrm + (long long)j * a.nrhs, N, a.nrhs));
   }
@@ -255,6 +260,7 @@ lqcd_status arnoldi_launch(ArnoldiT<S> &a, int j0) {
   key_add(key, a.hd2);
   key_add(key, a.nrm);
   key_add(key, j0);
+  key_add(key, a.passes);
   key_add(key, a.ctx->packed_nr);
   ArnoldiLaunch<S> arg{&a, j0};
   return graph_cached(a.ctx, key, &arnoldi_enqueue<S>, &arg);
@@ -271,7 +277,11 @@ lqcd_status arnoldi_run(ArnoldiT<S> &a, int j0, std::vector<Rhs> &R, long long &
   std::vector<double2> h1, h2;
   std::vector<double> nr;
   LQCD_TRY(download(ctx, a.hd1, h1, hcount));
-  LQCD_TRY(download(ctx, a.hd2, h2, hcount));
+  if (a.passes > 1) {
+    LQCD_TRY(download(ctx, a.hd2, h2, hcount));
+  } else {
+    h2.assign(hcount, make_double2(0.0, 0.0));
+  }
   LQCD_TRY(download(ctx, a.nrm, nr, (size_t)a.m * a.nrhs));
   for (int r = 0; r < a.nrhs; ++r) {
     if (!R[r].active) continue;
@@ -723,6 +733,7 @@ lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const SD *Vd, const Mat &H
     if (!(bn[r] > 0.0)) R[r].active = false;
   }
   ArnoldiT<S> A{ctx, op, nrhs, m, N, W.Vb, W.hd1, W.hd2, W.nrm};
+  if (!std::is_same<S, double2>::value) A.passes = ctx->inner_gs_passes;
   long long matvecs = 0;
   int cycles = 0;
   bool all_conv = false;
@@ -1010,7 +1021,10 @@ lqcd_status proj_core_entry(lqcd_ctx *ctx, const double *links, double kappa, co
   const int sys = defl->hermitian ? LQCD_SYS_MG5 : o->system;
   Op op{(const double2 *)links, kappa, sys == LQCD_SYS_MG5 ? LQCD_APPLY_G5R : LQCD_APPLY_M, LQCD_PREC_F64, 0ull};
   LQCD_TRY(set_poly(ctx, op, o, nrhs));
-  if (o->prec != LQCD_PREC_F64) return mixed_dispatch(ctx, op, defl, b, x, nrhs, o, info);
+  if (o->prec != LQCD_PREC_F64) {
+    LQCD_TRY(require_full(ctx, "mixed-precision proj_solve"));
+    return mixed_dispatch(ctx, op, defl, b, x, nrhs, o, info);
+  }
   return proj_core(ctx, op, defl, b, x, nrhs, o, info);
 }
 

@@ -617,6 +617,7 @@ extern "C" {
 lqcd_status lqcd_contract(lqcd_ctx *ctx, const double *links, double kappa, const double *eta, const double *w,
                           int nrhs, double *out) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "contract"));
   if (!links || !eta || !w || !out || nrhs < 1 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "contract: bad arguments");
   double2 *dev;
   const size_t cnt = (size_t)nrhs * 9 * ctx->dims[3];
@@ -630,6 +631,7 @@ lqcd_status lqcd_contract(lqcd_ctx *ctx, const double *links, double kappa, cons
 lqcd_status lqcd_hop_series(lqcd_ctx *ctx, const double *links, double kappa, const double *eta, double *out, int nrhs,
                             int K, const double *c) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "hop_series"));
   if (!links || !eta || !out || nrhs < 1 || K < 1 || K > 64 || eta == out)
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "hop_series: bad arguments");
   std::vector<cd> cc;
@@ -649,6 +651,7 @@ lqcd_status lqcd_poly_apply(lqcd_ctx *ctx, const double *links, double kappa, co
 
 lqcd_status lqcd_poly_coeffs(lqcd_ctx *ctx, const double *links, double kappa, uint64_t seed, int n, double *a) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "poly_coeffs"));
   if (!links || !a || n < 0 || n > 64) return set_err(ctx, LQCD_ERR_INVALID_ARG, "poly_coeffs: bad arguments");
   std::vector<cd> av;
   LQCD_TRY(poly_coeffs_dev(ctx, (const double2 *)links, kappa, seed, n, av));
@@ -682,6 +685,7 @@ lqcd_status lqcd_probe_classes(const int dims[4], int K, int *nclasses, int *cla
 
 lqcd_status lqcd_hop_traces(lqcd_ctx *ctx, const double *links, double kappa, int K, double *t) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "hop_traces"));
   if (!links || !t || K < 1 || K > 64) return set_err(ctx, LQCD_ERR_INVALID_ARG, "hop_traces: bad arguments");
   std::vector<cd> tr;
   LQCD_TRY(hop_traces_dev(ctx, (const double2 *)links, kappa, K, tr));
@@ -692,6 +696,7 @@ lqcd_status lqcd_hop_traces(lqcd_ctx *ctx, const double *links, double kappa, in
 lqcd_status lqcd_xi_inverse(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl, int sub, int K,
                             const double *coeffs, double *xi) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "xi_inverse"));
   if (!links || !defl || !xi || K < 1 || K > 65 || (sub == LQCD_SUB_POLY && !coeffs))
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "xi_inverse: bad arguments");
   std::vector<cd> cc;
@@ -730,12 +735,20 @@ struct lqcd_loop {
   std::vector<cd> es_coef;
   double2 *g5E = nullptr;
   std::vector<double> prec_a;  // polynomial preconditioner of the noise solves (interleaved complex)
+  // even/odd noise solves (opts.evenodd): the reduced context, its GMRES-Proj space, and the full
+  // eigenpairs of M mapped from the reduced ones for ES; des = the ES space (dm without even/odd)
+  lqcd_ctx *ce = nullptr;
+  lqcd_defl *dme = nullptr, *des_own = nullptr;
+  const lqcd_defl *des = nullptr;
   long matvecs = 0;
   double seconds = 0.0, eres = 0.0;
   ~lqcd_loop() {
     if (g5E) cudaFree(g5E);
     if (own_m && dm) lqcd_defl_destroy(dm);
     if (own_h && dh) lqcd_defl_destroy(dh);
+    if (des_own) lqcd_defl_destroy(des_own);
+    if (dme) lqcd_defl_destroy(dme);
+    if (ce) lqcd_ctx_destroy(ce);
   }
 };
 
@@ -751,6 +764,13 @@ lqcd_status check_est_opts(lqcd_ctx *ctx, const lqcd_est_opts *o) {
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop estimate: system must be LQCD_SYS_M or LQCD_SYS_MG5");
   if (o->prec_degree < 0 || o->prec_degree > 32)
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop estimate: prec_degree must be in 0..32");
+  if (o->evenodd != 0 && o->evenodd != 1) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop estimate: evenodd must be 0 or 1");
+  if (o->evenodd) {
+    for (int i = 0; i < 4; ++i)
+      if (ctx->dims[i] & 1) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop estimate: even/odd needs even extents");
+    if (o->prec != LQCD_PREC_F64 || o->prec_degree != 0)
+      return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop estimate: even/odd solves are plain FP64 without preconditioner");
+  }
   return LQCD_OK;
 }
 
@@ -770,7 +790,7 @@ lqcd_krylov_opts noise_solver_opts(const lqcd_loop *L) {
 template <typename F>
 lqcd_status es_setup(lqcd_loop *L, const double2 *U, F addES) {
   lqcd_ctx *ctx = L->ctx;
-  const lqcd_defl *dm = L->dm;
+  const lqcd_defl *dm = L->des;
   const int k = dm->k, Lt = ctx->dims[3];
   const long long N = ctx->N;
   L->es_k = k;
@@ -836,7 +856,89 @@ lqcd_status es_vector(lqcd_loop *L, const double2 *eta, double2 *y, int nb) {
       c[(size_t)q * nb + r] = make_double2(w.real(), w.imag());
     }
   LQCD_TRY(upload_v(ctx, c.data(), g, sizeof(double2) * c.size()));
-  return blas_combine(ctx, L->dm->E, N, 0, k, g, 1, y, N, N, nb);
+  return blas_combine(ctx, L->des->E, N, 0, k, g, 1, y, N, N, nb);
+}
+
+// ES space of an even/odd loop: the full eigenpairs of M from the Ritz pairs (mu_q, v_e^q) of hat M
+// on L->dme (both full pairs of each; a pair with mu = 1 within 1e-12 is left out)
+lqcd_status eo_es_space(lqcd_loop *L, const double *links) {
+  lqcd_ctx *ctx = L->ctx, *ce = L->ce;
+  const lqcd_defl *d = L->dme;
+  std::vector<double> mu;
+  std::vector<int> keep;
+  for (int q = 0; q < d->k; ++q) {
+    const cd m(d->lam[q].x, d->lam[q].y);
+    if (std::abs(std::sqrt(cd(1.0, 0.0) - m)) > 1e-12) {
+      keep.push_back(q);
+      mu.push_back(m.real());
+      mu.push_back(m.imag());
+    }
+  }
+  const int Q = (int)keep.size();
+  if (Q == 0) return LQCD_OK;
+  double2 *Ve = nullptr, *E = nullptr;
+  if (cudaMalloc(&Ve, sizeof(double2) * (size_t)Q * ce->N) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, LQCD_ERR_OOM, "ES (even/odd): allocation failed");
+  }
+  struct G { void *p; ~G() { if (p) cudaFree(p); } } g{Ve};
+  for (int i = 0; i < Q; ++i) LQCD_TRY(blas_copy(ce, d->E + (size_t)keep[i] * ce->N, Ve + (size_t)i * ce->N, ce->N));
+  if (cudaMalloc(&E, sizeof(double2) * 2 * (size_t)Q * ctx->N) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, LQCD_ERR_OOM, "ES (even/odd): allocation failed");
+  }
+  struct G2 { void *p; ~G2() { if (p) cudaFree(p); } } g2{E};
+  std::vector<double> lam(4 * (size_t)Q);
+  const lqcd_status st = lqcd_eo_full_eigenpairs(ce, links, L->kappa, mu.data(), (const double *)Ve, Q, 1e-12,
+                                                 lam.data(), (double *)E);
+  if (st != LQCD_OK) return set_err(ctx, st, "ES (even/odd): %s", ce->err.c_str());
+  LQCD_TRY(lqcd_defl_import(ctx, 2 * Q, (const double *)E, lam.data(), &L->des_own));
+  L->des_own->hermitian = 0;
+  return LQCD_OK;
+}
+
+// x = M^{-1} eta for nb noises through the reduced system: be = eta_e + kappa P_eo eta_o, hat M x_e =
+// be (or hat M' y_e = be, x_e = gamma_5 y_e) by GMRES-Proj to tol * min(1, ||eta|| / ||be||) (so that
+// the full relative residual, equal to ||be - hat M x_e|| / ||eta||, is at most tol), then
+// x_o = eta_o + kappa P_oe x_e; info->true_resid is the full FP64 true residual of x (r in scratch)
+lqcd_status eo_noise_solve(lqcd_loop *L, const double2 *U, const double2 *eta, double2 *x, double2 *r, int nb,
+                           lqcd_solve_info *info) {
+  lqcd_ctx *ctx = L->ctx, *ce = L->ce;
+  ce->stream = ctx->stream;
+  const long long Ne = ce->N, N = ctx->N;
+  double2 *be, *xe, *ye;
+  LQCD_TRY(ws_get(ce, WS_NBLK, sizeof(double2) * (size_t)nb * Ne * 3, (void **)&be));
+  xe = be + (size_t)nb * Ne;
+  ye = xe + (size_t)nb * Ne;
+  LQCD_TRY(eo_rhs_launch(ce, U, L->kappa, eta, be, nb));
+  double *nrm;
+  LQCD_TRY(ws_get(ctx, WS_EST2, sizeof(double) * 2 * (size_t)nb, (void **)&nrm));
+  LQCD_TRY(blas_norms(ctx, eta, N, nb, nrm));
+  LQCD_TRY(blas_norms(ce, be, Ne, nb, nrm + nb));
+  std::vector<double> nh;
+  LQCD_TRY(download_v(ctx, nrm, nh, 2 * (size_t)nb));
+  lqcd_krylov_opts po = noise_solver_opts(L);
+  double ratio = 1.0;
+  for (int i = 0; i < nb; ++i)
+    if (nh[nb + i] > 0.0) ratio = std::min(ratio, nh[i] / nh[nb + i]);
+  po.tol = L->o.tol * ratio;
+  const bool herm = L->dme->hermitian;
+  lqcd_solve_info pi{};
+  const lqcd_status st = proj_core_entry(ce, (const double *)U, L->kappa, L->dme, be, herm ? ye : xe, nb, &po, &pi);
+  if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return set_err(ctx, st, "even/odd noise solve: %s", ce->err.c_str());
+  if (herm) LQCD_TRY(blas_g5(ce, ye, xe, nb));
+  LQCD_TRY(eo_reconstruct_launch(ce, U, L->kappa, xe, eta, x, nb));
+  // full true residual r = eta - M x
+  LQCD_TRY(wilson_launch(ctx, U, L->kappa, x, r, nb, LQCD_PREC_F64, LQCD_APPLY_M));
+  LQCD_TRY(scaled_acc(ctx, eta, r, cd(-1.0, 0.0), (long long)nb * N));
+  LQCD_TRY(blas_norms(ctx, r, N, nb, nrm + nb));
+  LQCD_TRY(download_v(ctx, nrm, nh, 2 * (size_t)nb));
+  double worst = 0.0;
+  for (int i = 0; i < nb; ++i) worst = std::max(worst, nh[i] > 0.0 ? nh[nb + i] / nh[i] : 0.0);
+  *info = pi;
+  info->true_resid = worst;
+  info->converged = pi.converged && worst <= L->o.tol;
+  return LQCD_OK;
 }
 
 // Steps 2-3 given the two spaces (L->dm, L->dh set): Min-Res coefficients (unless given), b_k,
@@ -897,8 +999,16 @@ lqcd_status loop_finish_setup(lqcd_loop *L, const double2 *U, const double *link
   }
   L->add.assign((size_t)LQCD_NMODES * 9 * Lt, cd(0.0, 0.0));
   auto A = [&](int mode, int op, int t) -> cd & { return L->add[((size_t)mode * 9 + op) * Lt + t]; };
-  if ((L->modes & LQCD_SUB_ES) && !L->dm->hermitian && L->prec_a.empty())
-    LQCD_TRY(es_setup(L, U, [&](int op, int t) -> cd & { return A(6, op, t); }));
+  if ((L->modes & LQCD_SUB_ES) && L->prec_a.empty()) {
+    if (L->ce && !L->dme->hermitian) {
+      // ES from the full eigenpairs of M built from the reduced pairs (mu, v_e) of hat M (Sec. 7)
+      LQCD_TRY(eo_es_space(L, links));
+      L->des = L->des_own;
+    } else if (!L->ce && !L->dm->hermitian) {
+      L->des = L->dm;
+    }
+    if (L->des) LQCD_TRY(es_setup(L, U, [&](int op, int t) -> cd & { return A(6, op, t); }));
+  }
   for (int op = 0; op < 9; ++op)
     for (int t = 0; t < Lt; ++t) {
       cd pert = 0.0, poly = 0.0, e1 = 0.0, ep = 0.0, eq = 0.0;
@@ -929,7 +1039,12 @@ lqcd_status loop_finish_setup(lqcd_loop *L, const double2 *U, const double *link
     for (int c : {8, 16, 32, 64})
       if (c <= o->nnoise) cand.push_back(c);
     if (cand.empty()) cand.push_back(o->nnoise);
-    LQCD_TRY(autotune_block(ctx, links, kappa, L->dm, &po, cand.data(), (int)cand.size(), &L->block, nullptr));
+    if (L->ce) {
+      L->ce->stream = ctx->stream;
+      LQCD_TRY(autotune_block(L->ce, links, kappa, L->dme, &po, cand.data(), (int)cand.size(), &L->block, nullptr));
+    } else {
+      LQCD_TRY(autotune_block(ctx, links, kappa, L->dm, &po, cand.data(), (int)cand.size(), &L->block, nullptr));
+    }
   }
   return LQCD_OK;
 }
@@ -970,7 +1085,9 @@ lqcd_status loop_noises(lqcd_loop *L, const double *links, uint32_t first0, int 
     LQCD_TRY(noise_launch(ctx, o->seed, first0 + (uint32_t)off, nb, eta));
     lqcd_solve_info pi{};
     NvtxRange nvb("noise block: solve, subtractions, contractions");
-    if (L->dm->hermitian) {
+    if (L->ce) {
+      LQCD_TRY(eo_noise_solve(L, U, eta, x, y, nb, &pi));
+    } else if (L->dm->hermitian) {
       // M' y = eta over the Hermitian space, x = gamma_5 y (y is free until the deflation vectors)
       const lqcd_status st = proj_core_entry(ctx, links, kappa, L->dm, eta, y, nb, &po, &pi);
       if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED) return st;
@@ -1068,7 +1185,29 @@ lqcd_status loop_setup(lqcd_ctx *ctx, const double *links, double kappa, const l
     kp.poly_degree = o->prec_degree;
     kp.poly_coeffs = L->prec_a.data();
   }
-  if (o->system == LQCD_SYS_MG5) {
+  if (o->evenodd) {
+    // even/odd: the noise solves' space from the reduced system (GMRES-DR on hat M, or MINRES-DR on
+    // hat M gamma_5 on the Hermitian path) for the reduced special right-hand side; the HFES
+    // eigenpairs from MINRES-DR on the full M'
+    if (lqcd_ctx_create_evenodd(&L->ce, ctx->dims, ctx->recon, ctx->stream) != LQCD_OK)
+      return set_err(ctx, LQCD_ERR_CUDA, "loop setup: reduced context creation failed");
+    L->ce->graphs = ctx->graphs;
+    L->ce->defl_engine = ctx->defl_engine;
+    const long long Ne = L->ce->N;
+    double2 *be;
+    LQCD_TRY(ws_get(L->ce, WS_SPEC, sizeof(double2) * (size_t)Ne * 2, (void **)&be));
+    LQCD_TRY(eo_rhs_launch(L->ce, (const double2 *)links, kappa, bs, be, 1));
+    lqcd_solve_info se{};
+    const lqcd_status ste = o->system == LQCD_SYS_MG5
+                                ? lqcd_minresdr_solve(L->ce, links, kappa, (const double *)be, (double *)(be + Ne), 1, &ko, &se, &L->dme)
+                                : lqcd_gmresdr_solve(L->ce, links, kappa, (const double *)be, (double *)(be + Ne), 1, &ko, &se, &L->dme);
+    if (ste != LQCD_OK && ste != LQCD_ERR_NOT_CONVERGED) return set_err(ctx, ste, "loop setup (even/odd): %s", L->ce->err.c_str());
+    if (!L->dme) return set_err(ctx, LQCD_ERR_NOT_CONVERGED, "loop setup: no reduced deflation space");
+    L->matvecs += se.matvecs;
+    st = lqcd_minresdr_solve(ctx, links, kappa, (const double *)bs, (double *)x0, 1, &ko, &si, &L->dh);
+    L->dm = L->dh;
+    L->own_h = true;
+  } else if (o->system == LQCD_SYS_MG5) {
     // Hermitian path: MINRES-DR on M' (or on M' p(M')) alone gives both the eigenpairs and the
     // noise solves' space; with the preconditioner the eigenvalues of M' are the Rayleigh quotients
     st = lqcd_minresdr_solve(ctx, links, kappa, (const double *)bs, (double *)x0, 1, &kp, &si, &L->dh);
@@ -1107,6 +1246,7 @@ extern "C" {
 lqcd_status lqcd_loop_setup(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *opts,
                             lqcd_loop **out) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "loop_setup"));
   if (!links || !opts || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_setup: NULL argument");
   return loop_setup(ctx, links, kappa, opts, out);
 }
@@ -1114,6 +1254,7 @@ lqcd_status lqcd_loop_setup(lqcd_ctx *ctx, const double *links, double kappa, co
 lqcd_status lqcd_loop_setup_from(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *opts,
                                  const lqcd_defl *proj, const lqcd_defl *eig, const double *a, lqcd_loop **out) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "loop_setup_from"));
   if (!links || !opts || !proj || !eig || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_setup_from: NULL argument");
   *out = nullptr;
   if (!proj->V || !proj->Hbar_dev || proj->N != ctx->N)
@@ -1151,6 +1292,8 @@ lqcd_status lqcd_loop_set_noise_opts(lqcd_loop *L, int prec, double inner_tol, i
   if (!L || !L->ctx) return LQCD_ERR_INVALID_ARG;
   if (prec < LQCD_PREC_F64 || prec > LQCD_PREC_BF16 || !(inner_tol >= 0.0 && inner_tol < 1.0) || block < 0)
     return set_err(L->ctx, LQCD_ERR_INVALID_ARG, "loop_set_noise_opts: bad arguments");
+  if (L->ce && prec != LQCD_PREC_F64)
+    return set_err(L->ctx, LQCD_ERR_INVALID_ARG, "loop_set_noise_opts: even/odd noise solves are plain FP64");
   L->o.prec = prec;
   L->o.inner_tol = inner_tol;
   if (block > 0) L->block = block;
@@ -1184,6 +1327,7 @@ lqcd_status lqcd_loop_destroy(lqcd_loop *L) {
 lqcd_status lqcd_loop_estimate(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_est_opts *o,
                                lqcd_estimate *out) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "loop_estimate"));
   if (!links || !o || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "loop_estimate: NULL argument");
   lqcd_loop *Lp = nullptr;
   LQCD_TRY(loop_setup(ctx, links, kappa, o, &Lp));

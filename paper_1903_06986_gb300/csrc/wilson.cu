@@ -142,6 +142,7 @@ lqcd_status launch_mode(lqcd_ctx *ctx, const S *U, double kappa, const S *in, S 
 lqcd_status wilson_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in, double2 *out, int nrhs,
                           int prec, int flags) {
   if (nrhs <= 0 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply: nrhs %d out of range", nrhs);
+  if (ctx->eo) return eo_schur_launch(ctx, U, kappa, in, out, nrhs, prec, flags);
   if (prec == LQCD_PREC_F64) return launch_mode<double, double2>(ctx, U, kappa, in, out, nrhs, flags);
   if (prec == LQCD_PREC_F32) return launch_mode<float, double2>(ctx, U, kappa, in, out, nrhs, flags);
   return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply: unknown precision %d", prec);
@@ -150,12 +151,14 @@ lqcd_status wilson_launch(lqcd_ctx *ctx, const double2 *U, double kappa, const d
 lqcd_status wilson_launch_masked(lqcd_ctx *ctx, const double2 *U, double kappa, const double2 *in, double2 *out,
                                  int nrhs, unsigned long long g5mask) {
   if (nrhs <= 0 || nrhs > 64) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson (masked): nrhs %d out of range", nrhs);
+  LQCD_TRY(require_full(ctx, "wilson (masked)"));
   return launch_mode<double, double2>(ctx, U, kappa, in, out, nrhs, 4, g5mask);
 }
 
 lqcd_status wilson_launch_f32(lqcd_ctx *ctx, const float2 *U, double kappa, const float2 *in, float2 *out, int nrhs,
                               int flags) {
   if (nrhs <= 0 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson (f32): nrhs %d out of range", nrhs);
+  LQCD_TRY(require_full(ctx, "wilson_apply_f32"));
   return launch_mode<float, float2>(ctx, U, kappa, in, out, nrhs, flags);
 }
 
@@ -986,18 +989,21 @@ lqcd_status pack_links_f32(lqcd_ctx *ctx, const double2 *U, float4 *P, int recon
 
 extern "C" lqcd_status lqcd_pack_f32(lqcd_ctx *ctx, const double *in, float *out, int nrhs) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "pack_f32"));
   if (!in || !out || nrhs < 1 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "pack_f32: bad arguments");
   return pack_f32(ctx, (const double2 *)in, nullptr, (float4 *)out, nrhs);
 }
 
 extern "C" lqcd_status lqcd_unpack_f32(lqcd_ctx *ctx, const float *in, double *out, int nrhs) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "unpack_f32"));
   if (!in || !out || nrhs < 1 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "unpack_f32: bad arguments");
   return unpack_f32(ctx, (const float4 *)in, nullptr, (double2 *)out, nrhs);
 }
 
 extern "C" lqcd_status lqcd_pack_links_f32(lqcd_ctx *ctx, const double *links, float *out, int recon) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "pack_links_f32"));
   if (!links || !out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "pack_links_f32: NULL pointer");
   return pack_links_f32(ctx, (const double2 *)links, (float4 *)out, recon);
 }
@@ -1005,6 +1011,7 @@ extern "C" lqcd_status lqcd_pack_links_f32(lqcd_ctx *ctx, const double *links, f
 extern "C" lqcd_status lqcd_wilson_apply_packed(lqcd_ctx *ctx, const float *links_packed, int recon, double kappa,
                                                 const float *in, float *out, int nrhs, int flags, int rhs_per_thread) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "wilson_apply_packed"));
   if (!links_packed || !in || !out || in == out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_packed: bad pointers");
   if (rhs_per_thread < 0 || rhs_per_thread > 4)
     return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_packed: rhs_per_thread must be 0, 1, 2, 3 or 4");
@@ -1015,6 +1022,7 @@ extern "C" lqcd_status lqcd_wilson_apply_packed(lqcd_ctx *ctx, const float *link
 // ---- FP16 / BF16 fields ------------------------------------------------------------------------
 extern "C" lqcd_status lqcd_pack_half(lqcd_ctx *ctx, int prec, const double *in, void *out, int nrhs) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "pack_half"));
   if (!in || !out || nrhs < 1 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "pack_half: bad arguments");
   if (prec == LQCD_PREC_F16) return pack_lp(ctx, (const double2 *)in, nullptr, (__half2 *)out, nrhs);
   if (prec == LQCD_PREC_BF16) return pack_lp(ctx, (const double2 *)in, nullptr, (__nv_bfloat162 *)out, nrhs);
@@ -1023,6 +1031,7 @@ extern "C" lqcd_status lqcd_pack_half(lqcd_ctx *ctx, int prec, const double *in,
 
 extern "C" lqcd_status lqcd_unpack_half(lqcd_ctx *ctx, int prec, const void *in, double *out, int nrhs) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "unpack_half"));
   if (!in || !out || nrhs < 1 || nrhs > 65535) return set_err(ctx, LQCD_ERR_INVALID_ARG, "unpack_half: bad arguments");
   if (prec == LQCD_PREC_F16) return unpack_lp(ctx, (const __half2 *)in, nullptr, (double2 *)out, nrhs);
   if (prec == LQCD_PREC_BF16) return unpack_lp(ctx, (const __nv_bfloat162 *)in, nullptr, (double2 *)out, nrhs);
@@ -1032,6 +1041,7 @@ extern "C" lqcd_status lqcd_unpack_half(lqcd_ctx *ctx, int prec, const void *in,
 extern "C" lqcd_status lqcd_wilson_apply_half(lqcd_ctx *ctx, int prec, const float *links_packed, int recon,
                                               double kappa, const void *in, void *out, int nrhs, int flags) {
   if (!ctx) return LQCD_ERR_INVALID_ARG;
+  LQCD_TRY(require_full(ctx, "wilson_apply_half"));
   if (!links_packed || !in || !out || in == out) return set_err(ctx, LQCD_ERR_INVALID_ARG, "wilson_apply_half: bad pointers");
   if (prec == LQCD_PREC_F16)
     return wilson_launch_packed_lp(ctx, (const float4 *)links_packed, recon, kappa, (const __half2 *)in, (__half2 *)out,

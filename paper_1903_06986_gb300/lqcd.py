@@ -51,7 +51,8 @@ class EstOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("nnoise", C.c_int), ("block", C.c_int), ("m", C.c_int), ("k", C.c_int),
                 ("m_inner", C.c_int), ("K", C.c_int), ("npoly", C.c_int), ("tol", C.c_double),
                 ("tol_special", C.c_double), ("max_cycles", C.c_int), ("modes", C.c_int), ("prec", C.c_int),
-                ("inner_tol", C.c_double), ("eig_tol", C.c_double), ("system", C.c_int), ("prec_degree", C.c_int)]
+                ("inner_tol", C.c_double), ("eig_tol", C.c_double), ("system", C.c_int), ("prec_degree", C.c_int),
+                ("evenodd", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -148,6 +149,14 @@ def load(path=None):
         "lqcd_loop_derivs": [vp, vp, d, C.POINTER(EstOpts), C.POINTER(Derivs)],
         "lqcd_set_graphs": [vp, i],
         "lqcd_set_rhs_per_thread": [vp, i],
+        "lqcd_set_inner_gs_passes": [vp, i],
+        "lqcd_ctx_create_evenodd": [C.POINTER(vp), C.POINTER(C.c_int), i, vp],
+        "lqcd_eo_split": [vp, vp, vp, vp, i],
+        "lqcd_eo_join": [vp, vp, vp, vp, i],
+        "lqcd_eo_hop": [vp, vp, vp, vp, i, i],
+        "lqcd_eo_rhs": [vp, vp, d, vp, vp, i],
+        "lqcd_eo_reconstruct": [vp, vp, d, vp, vp, vp, i],
+        "lqcd_eo_full_eigenpairs": [vp, vp, d, vp, vp, i, d, vp, vp],
         "lqcd_probe_classes": [C.POINTER(C.c_int), i, C.POINTER(C.c_int), vp],
         "lqcd_autotune_block": [vp, vp, d, vp, C.POINTER(KrylovOpts), C.POINTER(C.c_int), i, C.POINTER(C.c_int),
                                 C.POINTER(C.c_double)],
@@ -510,9 +519,9 @@ class Context:
     # loop estimate in two phases
     @staticmethod
     def _est_opts(seed, nnoise, block, m, k, K, npoly, tol, tol_special, m_inner=0, max_cycles=2000, modes=SUB_ALL,
-                  prec=PREC_F64, inner_tol=0.0, eig_tol=0.0, system=SYS_M, prec_degree=0):
+                  prec=PREC_F64, inner_tol=0.0, eig_tol=0.0, system=SYS_M, prec_degree=0, evenodd=0):
         return EstOpts(seed, nnoise, block, m, k, m_inner, K, npoly, tol, tol_special, max_cycles, modes, prec,
-                       inner_tol, eig_tol, system, prec_degree)
+                       inner_tol, eig_tol, system, prec_degree, evenodd)
 
     def loop_setup(self, links, kappa, seed, nnoise, block, m, k, K, npoly, tol, tol_special, **kw):
         """lqcd_loop_setup: special solves, polynomial, hopping traces, 1/xi', add-backs."""
@@ -617,10 +626,10 @@ class Context:
     # whole path
     def loop_estimate(self, links, kappa, seed, nnoise, block, m, k, K, npoly, tol, tol_special,
                       m_inner=0, max_cycles=2000, modes=SUB_ALL, prec=PREC_F64, inner_tol=0.0, eig_tol=0.0,
-                      system=SYS_M, prec_degree=0):
+                      system=SYS_M, prec_degree=0, evenodd=0):
         """lqcd_loop_estimate; block = 0 lets the autotuner pick the block width."""
         o = EstOpts(seed, nnoise, block, m, k, m_inner, K, npoly, tol, tol_special, max_cycles, modes, prec,
-                    inner_tol, eig_tol, system, prec_degree)
+                    inner_tol, eig_tol, system, prec_degree, evenodd)
         bufs, est = _estimate_buffers(self.dims[3], nnoise, k, npoly)
         st = self.lib.lqcd_loop_estimate(self.h, _ptr(links), kappa, C.byref(o), C.byref(est))
         if st not in (OK, ERR_NOT_CONVERGED):
@@ -634,6 +643,10 @@ class Context:
     def set_graphs(self, enable):
         self._check(self.lib.lqcd_set_graphs(self.h, 1 if enable else 0))
 
+    def set_inner_gs_passes(self, passes):
+        """lqcd_set_inner_gs_passes: Gram-Schmidt passes (1 or 2) of mixed-precision inner cycles."""
+        self._check(self.lib.lqcd_set_inner_gs_passes(self.h, passes))
+
     def autotune_block(self, links, kappa, defl, m, candidates=(8, 16, 32), prec=PREC_F64, inner_tol=0.0):
         """lqcd_autotune_block: (best width, {width: seconds per right-hand side and cycle})."""
         o = KrylovOpts(m, 0, 1e-10, 1, SYS_M, prec, inner_tol)
@@ -644,6 +657,78 @@ class Context:
                                                  len(candidates), C.byref(best), secs))
         return best.value, dict(zip(candidates, list(secs)))
 
+
+
+class EvenOddContext(Context):
+    """lqcd_ctx_create_evenodd: the reduced (even-site) system of a full lattice (Sec. 7).  Its fields
+    are (nrhs, V/2, 4, 3) complex128 (even sites in lexicographic order), wilson_apply applies
+    hat M = 1 - kappa^2 P_eo P_oe, and the Krylov solvers of Context solve the reduced system."""
+
+    def __init__(self, dims, stream=None, recon=18):
+        torch = _torch()
+        self.lib = load()
+        self.full_dims = tuple(int(d) for d in dims)
+        self.dims = (self.full_dims[0] // 2,) + self.full_dims[1:]
+        self.V = int(np.prod(self.dims))
+        self.N = 12 * self.V
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        h = C.c_void_p()
+        dd = (C.c_int * 4)(*self.full_dims)
+        st = self.lib.lqcd_ctx_create_evenodd(C.byref(h), dd, recon, C.c_void_p(s))
+        if st != OK:
+            raise LqcdError(st, "lqcd_ctx_create_evenodd failed")
+        self.h = h
+
+    def field(self, nrhs=None):
+        torch = _torch()
+        shp = (self.V, 4, 3) if nrhs is None else (nrhs, self.V, 4, 3)
+        return torch.empty(shp, dtype=torch.complex128, device=self.device)
+
+    def full_field(self, nrhs):
+        torch = _torch()
+        lx, ly, lz, lt = self.full_dims
+        return torch.empty((nrhs, lt, lz, ly, lx, 4, 3), dtype=torch.complex128, device=self.device)
+
+    def split(self, full):
+        n = full.numel() // (2 * self.N)
+        e, o = self.field(n), self.field(n)
+        self._check(self.lib.lqcd_eo_split(self.h, _ptr(full), _ptr(e), _ptr(o), n))
+        return e, o
+
+    def join(self, even, odd):
+        n = self._nrhs(even)
+        out = self.full_field(n)
+        self._check(self.lib.lqcd_eo_join(self.h, _ptr(even), _ptr(odd), _ptr(out), n))
+        return out
+
+    def hop(self, links, inp, parity_out):
+        """P_eo inp (parity_out 0) or P_oe inp (parity_out 1)."""
+        out = _torch().empty_like(inp)
+        self._check(self.lib.lqcd_eo_hop(self.h, _ptr(links), _ptr(inp), _ptr(out), self._nrhs(inp), parity_out))
+        return out
+
+    def rhs(self, links, kappa, b):
+        n = b.numel() // (2 * self.N)
+        out = self.field(n)
+        self._check(self.lib.lqcd_eo_rhs(self.h, _ptr(links), kappa, _ptr(b), _ptr(out), n))
+        return out
+
+    def reconstruct(self, links, kappa, xe, b):
+        n = self._nrhs(xe)
+        out = self.full_field(n)
+        self._check(self.lib.lqcd_eo_reconstruct(self.h, _ptr(links), kappa, _ptr(xe), _ptr(b), _ptr(out), n))
+        return out
+
+    def full_eigenpairs(self, links, kappa, mu, Ve, tol=1e-8):
+        """(lam (2Q,), E (2Q, T, Z, Y, X, 4, 3)) of M from reduced pairs (mu (Q,), Ve (Q, V/2, 4, 3))."""
+        q = len(mu)
+        m, mp = _host_c(mu)
+        lam = np.zeros(2 * q, dtype=np.complex128)
+        E = self.full_field(2 * q)
+        self._check(self.lib.lqcd_eo_full_eigenpairs(self.h, _ptr(links), kappa, mp, _ptr(Ve.contiguous()), q, tol,
+                                                     lam.ctypes.data_as(C.c_void_p), _ptr(E)))
+        return lam, E
 
 def probe_classes(dims, K):
     """lqcd_probe_classes (host only): (number of classes, class of every site as an int array of
@@ -726,11 +811,11 @@ def link_grad(ctx, links, kappa, z, x, scale=1.0, want_links=True):
 
 
 def loop_derivs(ctx, links, kappa, seed, nnoise, block, m, k, K, tol, tol_special, m_inner=0, max_cycles=2000,
-                prec=PREC_F64, want_grad=True, grad_scale=1.0, inner_tol=0.0, eig_tol=0.0):
+                prec=PREC_F64, want_grad=True, grad_scale=1.0, inner_tol=0.0, eig_tol=0.0, system=SYS_M):
     """lqcd_loop_derivs: d/dkappa of the NS and PS estimates of the nine operators, and the link
     gradient of the NS scalar estimate."""
     o = EstOpts(seed, nnoise, block, m, k, m_inner, K, 0, tol, tol_special, max_cycles, SUB_NONE | SUB_PERT, prec,
-                inner_tol, eig_tol)
+                inner_tol, eig_tol, system)
     dk = np.zeros((2, NOPS), dtype=np.complex128)
     err = np.zeros((2, NOPS), dtype=np.float64)
     per = np.zeros((2, nnoise, NOPS), dtype=np.complex128)

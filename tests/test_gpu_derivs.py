@@ -32,13 +32,16 @@ def test_link_grad_kernel_matches_oracle():
     assert rel_err(host(gl), 0.5 * (dUc + dU.conj())) < 1e-12
 
 
-def test_loop_derivs_match_oracle():
+@pytest.mark.parametrize("system", [lqcd.SYS_M, lqcd.SYS_MG5], ids=["M", "MG5"])
+def test_loop_derivs_match_oracle(system):
+    """Both solver paths (GMRES-DR/Proj on M, and MINRES-DR/Proj on M' = M gamma_5 with x = gamma_5 y)
+    against the oracle's solves on M: the derivatives depend on the solutions only."""
     dims, kappa = (2, 2, 2, 4), 0.12
     ctx = context(dims)
     U = synth.su3_links(dims, 0.45, 2)
     N = 6
     # solves to 3e-14: x, y = M^{-1} P x and z agree within a few cond(M)^2 * 3e-14 (cond(M) = 12.5)
-    g = lqcd.loop_derivs(ctx, dev(U), kappa, 5, N, 3, 40, 8, 7, 3e-14, 1e-14)
+    g = lqcd.loop_derivs(ctx, dev(U), kappa, 5, N, 3, 40, 8, 7, 3e-14, 1e-14, system=system)
     assert g["converged"] and g["max_true_resid"] <= 3e-14
     ref = PL.loop_derivs(U, kappa, dims, 5, N, 40, 8, 7, 3e-14, 1e-14)
     for mode in range(2):
