@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cstring>
+
 #include "common.cuh"
 
 namespace {
@@ -72,7 +74,44 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
 // b = c + nchunk (g + ngroup r), consecutive blocks streaming consecutive chunks; the last block to finish for right-hand
 // side r (a counter per r, reset by that block) adds the nchunk partials of every i in chunk order
 // and writes h[i * nrhs + r].  The result does not depend on block scheduling.
-template <typename SV, typename SW>
+// conj(V_j[e]) w[e] summed into acc[j] over the elements e0 + t, e0 + t + BT, ... < e1 of this thread
+// (t = threadIdx.x), for the first g of the GROUP vectors (all of them when FULL)
+template <bool FULL, typename SV, typename SW, typename C>
+__device__ __forceinline__ void dot_range(const SV *const *vp, const SW *__restrict__ wr, long long e0, long long e1,
+                                          int g, C *acc) {
+  for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
+    const C wv = ldc(wr[e]);
+#pragma unroll
+    for (int j = 0; j < GROUP; ++j)
+      if (FULL || j < g) gfma_conj(acc[j], ldc(vp[j][e]), wv);
+  }
+}
+// the same with one 16-byte load per vector and thread (KV = 16 / sizeof(SV) elements); e0 and the
+// vectors' offsets are multiples of KV elements, the remainder of the range goes element-wise
+template <bool FULL, typename SV, typename SW, typename C>
+__device__ __forceinline__ void dot_range_vec(const SV *const *vp, const SW *__restrict__ wr, long long e0,
+                                              long long e1, int g, C *acc) {
+  constexpr int KV = 16 / sizeof(SV);
+  const long long ev = e0 + (e1 - e0) / KV * KV;
+  for (long long e = e0 + (long long)threadIdx.x * KV; e < ev; e += (long long)BT * KV) {
+    SW wv[KV];
+    const uint4 wraw = __ldg(reinterpret_cast<const uint4 *>(wr + e));
+    memcpy(wv, &wraw, 16);
+#pragma unroll
+    for (int j = 0; j < GROUP; ++j) {
+      if (FULL || j < g) {
+        SV vv[KV];
+        const uint4 vraw = __ldg(reinterpret_cast<const uint4 *>(vp[j] + e));
+        memcpy(vv, &vraw, 16);
+#pragma unroll
+        for (int q = 0; q < KV; ++q) gfma_conj(acc[j], ldc(vv[q]), ldc(wv[q]));
+      }
+    }
+  }
+  dot_range<FULL>(vp, wr, ev, e1, g, acc);
+}
+
+template <typename SV, typename SW, bool VEC>
 __global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, long long vstride, long long vrs,
                                                       int nvec, const SW *__restrict__ w, long long n, int nrhs,
                                                       int nchunk, double fac, double2 *__restrict__ partial,
@@ -93,8 +132,9 @@ __global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, 
     r = blockIdx.x / (nchunk * ngroup);
   }
   const int i0 = g0 * GROUP;
-  const long long chunk = (n + nchunk - 1) / nchunk;
-  const long long e0 = c * chunk;
+  constexpr long long KV = VEC ? 16 / sizeof(SV) : 1;
+  const long long chunk = ((n + nchunk - 1) / nchunk + KV - 1) / KV * KV;
+  const long long e0 = min(n, c * chunk);
   const long long e1 = min(n, e0 + chunk);
   const SW *wr = w + r * n;
   const SV *vr = V + r * vrs;
@@ -108,19 +148,16 @@ __global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, 
   C acc[GROUP];
 #pragma unroll
   for (int j = 0; j < GROUP; ++j) acc[j] = cz<C>();
-  if (g == GROUP) {
-    for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
-      const C wv = ldc(wr[e]);
-#pragma unroll
-      for (int j = 0; j < GROUP; ++j) gfma_conj(acc[j], ldc(vp[j][e]), wv);
-    }
+  if (VEC) {
+    if (g == GROUP)
+      dot_range_vec<true>(vp, wr, e0, e1, g, acc);
+    else
+      dot_range_vec<false>(vp, wr, e0, e1, g, acc);
   } else {
-    for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
-      const C wv = ldc(wr[e]);
-#pragma unroll
-      for (int j = 0; j < GROUP; ++j)
-        if (j < g) gfma_conj(acc[j], ldc(vp[j][e]), wv);
-    }
+    if (g == GROUP)
+      dot_range<true>(vp, wr, e0, e1, g, acc);
+    else
+      dot_range<false>(vp, wr, e0, e1, g, acc);
   }
 #pragma unroll
   for (int j = 0; j < GROUP; ++j) {
@@ -208,6 +245,42 @@ __global__ void __launch_bounds__(BT) multiaxpy_kernel(const SV *__restrict__ V,
   C acc = ldc(w[r * n + e]);
   for (int i = 0; i < nvec; ++i, vp += vstride) gfma(acc, ldc(*vp), coef[i]);
   w[r * n + e] = stc<SW>(acc);
+}
+
+// The same with KV = 16 / sizeof(SV) consecutive elements per thread and one 16-byte load per vector
+// (4- and 8-byte storage; every vector starts on a 16-byte boundary, n a multiple of KV).
+template <typename SV, typename SW>
+__global__ void __launch_bounds__(BT) multiaxpy_vec_kernel(const SV *__restrict__ V, long long vstride,
+                                                           long long vrs, int nvec, const double2 *__restrict__ h,
+                                                           double sign, SW *__restrict__ w, long long n, int nrhs) {
+  using C = Ar<SW>;
+  constexpr int KV = 16 / sizeof(SV);
+  __shared__ C coef[AXPY_MAXV];
+  const int r = blockIdx.x % nrhs;
+  for (int i = threadIdx.x; i < nvec; i += BT) coef[i] = from_d2<C>(cscale(h[(long long)i * nrhs + r], sign));
+  __syncthreads();
+  const long long e = ((long long)(blockIdx.x / nrhs) * BT + threadIdx.x) * KV;
+  if (e >= n) return;
+  const SV *vp = V + r * vrs + e;
+  SW *wp = w + r * n + e;
+  SW wv[KV];
+  uint4 raw = *reinterpret_cast<const uint4 *>(wp);
+  memcpy(wv, &raw, 16);
+  C acc[KV];
+#pragma unroll
+  for (int q = 0; q < KV; ++q) acc[q] = ldc(wv[q]);
+  for (int i = 0; i < nvec; ++i, vp += vstride) {
+    SV vv[KV];
+    const uint4 vr = __ldg(reinterpret_cast<const uint4 *>(vp));
+    memcpy(vv, &vr, 16);
+    const C cf = coef[i];
+#pragma unroll
+    for (int q = 0; q < KV; ++q) gfma(acc[q], ldc(vv[q]), cf);
+  }
+#pragma unroll
+  for (int q = 0; q < KV; ++q) wv[q] = stc<SW>(acc[q]);
+  memcpy(&raw, wv, 16);
+  *reinterpret_cast<uint4 *>(wp) = raw;
 }
 
 constexpr int CT = 8;           // output columns per pass in combine
@@ -524,9 +597,18 @@ lqcd_status blas_multidot(lqcd_ctx *ctx, const SV *V, long long vstride, long lo
   LQCD_TRY(ws_get(ctx, WS_PARTIAL, sizeof(double2) * (size_t)nchunk * nrhs * nvec, &p));
   LQCD_TRY(reduction_counters(ctx, nrhs, &cnt));
   const double fac = 1.0 / (store_sigma<SV>(ctx->N) * store_sigma<SW>(ctx->N));
+  // 16-byte loads for the 4- and 8-byte storage types when every vector starts on a 16-byte boundary
+  const bool vec = sizeof(SV) < 16 && sizeof(SV) == sizeof(SW) && ((uintptr_t)V % 16 == 0) &&
+                   ((uintptr_t)w % 16 == 0) && ((vstride * (long long)sizeof(SV)) % 16 == 0) &&
+                   ((vrs * (long long)sizeof(SV)) % 16 == 0) && ((n * (long long)sizeof(SW)) % 16 == 0);
+  const unsigned grid = (unsigned)((long long)nchunk * ngroup * nrhs);
   kbegin(ctx);
-  multidot_kernel<SV, SW><<<(unsigned)((long long)nchunk * ngroup * nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs,
-                                                                                nchunk, fac, (double2 *)p, cnt, h);
+  if (vec)
+    multidot_kernel<SV, SW, true><<<grid, BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, nchunk, fac,
+                                                               (double2 *)p, cnt, h);
+  else
+    multidot_kernel<SV, SW, false><<<grid, BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, nchunk, fac,
+                                                                (double2 *)p, cnt, h);
   // compulsory bytes: every basis vector once (once per right-hand side when the bases differ),
   // every w once
   const double bytes = (double)sizeof(SV) * n * nvec * (vrs != 0 ? nrhs : 1) + (double)sizeof(SW) * n * nrhs;
@@ -539,9 +621,19 @@ lqcd_status blas_multiaxpy(lqcd_ctx *ctx, const SV *V, long long vstride, long l
   if (nvec <= 0) return LQCD_OK;
   if (nvec > AXPY_MAXV) return set_err(ctx, LQCD_ERR_INVALID_ARG, "multiaxpy: at most %d vectors", AXPY_MAXV);
   const double fac = sign * store_sigma<SW>(ctx->N) / store_sigma<SV>(ctx->N);
+  const bool vec = sizeof(SV) < 16 && sizeof(SV) == sizeof(SW) && ((uintptr_t)V % 16 == 0) &&
+                   ((uintptr_t)w % 16 == 0) && ((vstride * (long long)sizeof(SV)) % 16 == 0) &&
+                   ((vrs * (long long)sizeof(SV)) % 16 == 0) && ((n * (long long)sizeof(SW)) % 16 == 0);
   kbegin(ctx);
-  multiaxpy_kernel<SV, SW><<<(unsigned)((long long)ceil_div(n, BT) * nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec,
-                                                                                                h, fac, w, n, nrhs);
+  if (vec) {
+    const long long kv = 16 / (long long)sizeof(SV);
+    multiaxpy_vec_kernel<SV, SW><<<(unsigned)((long long)ceil_div(n / kv, BT) * nrhs), BT, 0, ctx->stream>>>(
+        V, vstride, vrs, nvec, h, fac, w, n, nrhs);
+  } else {
+    multiaxpy_kernel<SV, SW><<<(unsigned)((long long)ceil_div(n, BT) * nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs,
+                                                                                                  nvec, h, fac, w, n,
+                                                                                                  nrhs);
+  }
   // compulsory bytes: every basis vector once (per right-hand side when the bases differ), w read
   // and written once
   const double bytes = (double)sizeof(SV) * n * nvec * (vrs != 0 ? nrhs : 1) + 2.0 * sizeof(SW) * n * nrhs;

@@ -72,7 +72,7 @@ struct lqcd_ctx {
   int defl_engine;           // LQCD_DEFL_FP64 or LQCD_DEFL_TENSOR (deflation projections)
   unsigned long long tc_wait_ns;  // bound of every tensor-core pipeline wait (lqcd_set_wait_limit)
   int tc_stop_after;         // injected stall of the next tensor-core launch (-1: none)
-  int inner_gs_passes;       // Gram-Schmidt passes of the reduced-precision inner Arnoldi (1 or 2)
+  int inner_gs_passes;       // Gram-Schmidt passes of the reduced-precision inner Arnoldi (0 = by storage)
   // even/odd reduced context (lqcd_ctx_create_evenodd): fields hold the even sites only (V above is
   // half the lattice), the operator is hat M = 1 - kappa^2 P_eo P_oe, eo_dims the full extents
   int eo;

@@ -733,7 +733,9 @@ lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const SD *Vd, const Mat &H
     if (!(bn[r] > 0.0)) R[r].active = false;
   }
   ArnoldiT<S> A{ctx, op, nrhs, m, N, W.Vb, W.hd1, W.hd2, W.nrm};
-  if (!std::is_same<S, double2>::value) A.passes = ctx->inner_gs_passes;
+  // reduced-precision inner cycles: one pass for FP16 / BF16 bases (4-byte complex), two for FP32,
+  // unless the context sets it
+  if (!std::is_same<S, double2>::value) A.passes = ctx->inner_gs_passes ? ctx->inner_gs_passes : (sizeof(S) == 4 ? 1 : 2);
   long long matvecs = 0;
   int cycles = 0;
   bool all_conv = false;

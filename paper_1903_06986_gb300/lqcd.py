@@ -644,7 +644,8 @@ class Context:
         self._check(self.lib.lqcd_set_graphs(self.h, 1 if enable else 0))
 
     def set_inner_gs_passes(self, passes):
-        """lqcd_set_inner_gs_passes: Gram-Schmidt passes (1 or 2) of mixed-precision inner cycles."""
+        """lqcd_set_inner_gs_passes: Gram-Schmidt passes (0 = by storage, 1 or 2) of mixed-precision
+        inner cycles."""
         self._check(self.lib.lqcd_set_inner_gs_passes(self.h, passes))
 
     def autotune_block(self, links, kappa, defl, m, candidates=(8, 16, 32), prec=PREC_F64, inner_tol=0.0):
