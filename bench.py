@@ -478,10 +478,13 @@ def run_case(args):
         ctx = lqcd.Context(dims, recon=12)
         U = torch.from_numpy(synth.su3_links(dims, LINK_EPS, LINK_SEED)).cuda()
         loop = ctx.loop_setup(U, KAPPA, NOISE_SEED, 10, 10, 60, 30, K_PS, NPOLY, TOL, TOL_SPECIAL, m_inner=M_INNER,
-                              max_cycles=MAX_CYCLES, prec=lqcd.PREC_F16, system=lqcd.SYS_MG5)
+                              max_cycles=MAX_CYCLES, prec=lqcd.PREC_F16, system=lqcd.SYS_MG5, inner_tol=INNER_TOL)
+        torch.cuda.synchronize()
+        setup_launches = ctx.launches
         per, ni = loop.noises(U, 0, 10)
         torch.cuda.synchronize()
-        print(json.dumps({"case": args.case, "matvecs": ni["matvecs"], "launches": ctx.launches}))
+        print(json.dumps({"case": args.case, "matvecs": ni["matvecs"], "setup_launches": setup_launches,
+                          "launches": ctx.launches}))
         return
     dims2 = DIMS2
     U = torch.from_numpy(synth.su3_links(dims2, 0.4323, SEED2)).cuda()
