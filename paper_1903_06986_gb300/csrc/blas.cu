@@ -18,7 +18,8 @@
 namespace {
 
 constexpr int BT = 256;      // threads per block
-constexpr int GROUP = 8;     // basis vectors reduced together in multidot
+constexpr int GROUP = 8;     // basis vectors reduced together in multidot (at most BT / 32)
+static_assert(GROUP <= BT / 32, "multidot: one warp per vector of a group in the final sums");
 
 // arithmetic type of a storage type
 template <typename S> struct ArithT { using T = float2; };
@@ -66,14 +67,6 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
   return v;
 }
 
-// Single-launch batched inner products.  Block b (a 1-D grid) sums conj(V_i^r) w^r over element
-// chunk c for the GROUP basis vectors of group g and writes partial[(i * nrhs + r) * nchunk + c]:
-// with a basis shared by all right-hand sides b = g + ngroup (r + nrhs c), so that the groups and
-// right-hand sides of one chunk are neighbours in launch order and the chunk of every basis vector
-// and of every w^r is read from DRAM once and then from L2; with a basis per right-hand side
-// b = c + nchunk (g + ngroup r), consecutive blocks streaming consecutive chunks; the last block to finish for right-hand
-// side r (a counter per r, reset by that block) adds the nchunk partials of every i in chunk order
-// and writes h[i * nrhs + r].  The result does not depend on block scheduling.
 // conj(V_j[e]) w[e] summed into acc[j] over the elements e0 + t, e0 + t + BT, ... < e1 of this thread
 // (t = threadIdx.x), for the first g of the GROUP vectors (all of them when FULL)
 template <bool FULL, typename SV, typename SW, typename C>
@@ -94,15 +87,19 @@ __device__ __forceinline__ void dot_range_vec(const SV *const *vp, const SW *__r
   constexpr int KV = 16 / sizeof(SV);
   const long long ev = e0 + (e1 - e0) / KV * KV;
   for (long long e = e0 + (long long)threadIdx.x * KV; e < ev; e += (long long)BT * KV) {
-    SW wv[KV];
+    // all GROUP + 1 loads of this step issued before any use, so that they are in flight together
+    uint4 vraw[GROUP];
     const uint4 wraw = __ldg(reinterpret_cast<const uint4 *>(wr + e));
+#pragma unroll
+    for (int j = 0; j < GROUP; ++j)
+      if (FULL || j < g) vraw[j] = __ldg(reinterpret_cast<const uint4 *>(vp[j] + e));
+    SW wv[KV];
     memcpy(wv, &wraw, 16);
 #pragma unroll
     for (int j = 0; j < GROUP; ++j) {
       if (FULL || j < g) {
         SV vv[KV];
-        const uint4 vraw = __ldg(reinterpret_cast<const uint4 *>(vp[j] + e));
-        memcpy(vv, &vraw, 16);
+        memcpy(vv, &vraw[j], 16);
 #pragma unroll
         for (int q = 0; q < KV; ++q) gfma_conj(acc[j], ldc(vv[q]), ldc(wv[q]));
       }
@@ -111,6 +108,16 @@ __device__ __forceinline__ void dot_range_vec(const SV *const *vp, const SW *__r
   dot_range<FULL>(vp, wr, ev, e1, g, acc);
 }
 
+// Single-launch batched inner products.  Block b (a 1-D grid) sums conj(V_i^r) w^r over element
+// chunk c for the GROUP basis vectors of group g and writes partial[(i * nrhs + r) * nchunk + c]:
+// with a basis shared by all right-hand sides b = g + ngroup (r + nrhs c), so that the groups and
+// right-hand sides of one chunk are neighbours in launch order and the chunk of every basis vector
+// and of every w^r is read from DRAM once and then from L2; with a basis per right-hand side
+// b = c + nchunk (g + ngroup r), consecutive blocks streaming consecutive chunks.  The last of the
+// nchunk blocks of (r, g) to finish (a counter per (r, g), reset by that block) adds the nchunk
+// partials of every vector of the group in a fixed order (one warp per vector) and writes
+// h[i * nrhs + r]: the result does not depend on block scheduling, and the final sums of the groups
+// run in parallel.
 template <typename SV, typename SW, bool VEC>
 __global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, long long vstride, long long vrs,
                                                       int nvec, const SW *__restrict__ w, long long n, int nrhs,
@@ -172,17 +179,23 @@ __global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, 
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(&counters[r], 1u) == (unsigned)(nchunk * ngroup - 1));
+  unsigned *cnt = counters + (long long)r * ngroup + g0;
+  if (threadIdx.x == 0) last = (atomicAdd(cnt, 1u) == (unsigned)(nchunk - 1));
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int i = threadIdx.x; i < nvec; i += BT) {
+  // the last chunk block of (r, group) finishes the group's vectors, one warp per vector: lanes
+  // stride over the chunks, then a fixed shuffle tree (the order of the additions depends only on
+  // nchunk)
+  if (warp < g) {
+    const int i = i0 + warp;
     const double2 *pp = partial + ((long long)i * nrhs + r) * nchunk;
     double2 sum = make_double2(0.0, 0.0);
-    for (int q = 0; q < nchunk; ++q) sum = cadd(sum, __ldcg(pp + q));
-    h[(long long)i * nrhs + r] = cscale(sum, fac);
+    for (int q = lane; q < nchunk; q += 32) sum = cadd(sum, __ldcg(pp + q));
+    sum = warp_sum2(sum);
+    if (lane == 0) h[(long long)i * nrhs + r] = cscale(sum, fac);
   }
-  if (threadIdx.x == 0) counters[r] = 0u;
+  if (threadIdx.x == 0) *cnt = 0u;
 }
 
 // Single-launch batched norms ||x^r||, same last-block scheme as multidot_kernel.
@@ -217,12 +230,100 @@ __global__ void __launch_bounds__(BT) norm_kernel(const S *__restrict__ x, long 
     last = (atomicAdd(&counters[r], 1u) == (unsigned)(nb - 1));
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last || threadIdx.x >= 32) return;
   __threadfence();
+  // the first warp adds the nb partials: lanes stride over them, then a fixed shuffle tree
   double sum = 0.0;
-  for (int q = 0; q < nb; ++q) sum += __ldcg(partial + (long long)r * nb + q);
-  out[r] = sqrt(sum) * fac;
-  counters[r] = 0u;
+  for (int q = threadIdx.x; q < nb; q += 32) sum += __ldcg(partial + (long long)r * nb + q);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (threadIdx.x == 0) {
+    out[r] = sqrt(sum) * fac;
+    counters[r] = 0u;
+  }
+}
+
+// Inner products with a basis shared by all right-hand sides: block b = t + ntile (g + ngroup c)
+// takes element chunk c of the GROUP vectors of group g against the RT right-hand sides of tile t,
+// so every basis element a thread loads is used for RT right-hand sides (the tiles of one chunk and
+// group are neighbours in launch order and share it through L2).  Partials and the per-(tile, group)
+// last-block final sums as in multidot_kernel.
+template <typename SV, typename SW, int RT>
+__global__ void __launch_bounds__(BT) multidot_shared_kernel(const SV *__restrict__ V, long long vstride, int nvec,
+                                                             const SW *__restrict__ w, long long n, int nrhs,
+                                                             int nchunk, double fac, double2 *__restrict__ partial,
+                                                             unsigned *__restrict__ counters,
+                                                             double2 *__restrict__ h) {
+  using C = Ar<SW>;
+  const int ngroup = (nvec + GROUP - 1) / GROUP;
+  const int ntile = (nrhs + RT - 1) / RT;
+  const int t = blockIdx.x % ntile;
+  const int g0 = (blockIdx.x / ntile) % ngroup;
+  const int c = blockIdx.x / (ntile * ngroup);
+  const int i0 = g0 * GROUP, r0 = t * RT;
+  const int g = min(GROUP, nvec - i0), nr = min(RT, nrhs - r0);
+  const long long chunk = (n + nchunk - 1) / nchunk;
+  const long long e0 = min(n, c * chunk);
+  const long long e1 = min(n, e0 + chunk);
+  const SV *vp[GROUP];
+#pragma unroll
+  for (int j = 0; j < GROUP; ++j) vp[j] = V + (long long)(i0 + min(j, g - 1)) * vstride;
+  const SW *wp[RT];
+#pragma unroll
+  for (int q = 0; q < RT; ++q) wp[q] = w + (long long)(r0 + min(q, nr - 1)) * n;
+  C acc[GROUP][RT];
+#pragma unroll
+  for (int j = 0; j < GROUP; ++j)
+#pragma unroll
+    for (int q = 0; q < RT; ++q) acc[j][q] = cz<C>();
+  for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
+    C vv[GROUP], wv[RT];
+#pragma unroll
+    for (int j = 0; j < GROUP; ++j) vv[j] = ldc(vp[j][e]);
+#pragma unroll
+    for (int q = 0; q < RT; ++q) wv[q] = ldc(wp[q][e]);
+#pragma unroll
+    for (int j = 0; j < GROUP; ++j)
+#pragma unroll
+      for (int q = 0; q < RT; ++q) gfma_conj(acc[j][q], vv[j], wv[q]);
+  }
+  __shared__ double2 red[BT / 32][GROUP * RT];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < GROUP; ++j)
+#pragma unroll
+    for (int q = 0; q < RT; ++q) {
+      const double2 v = warp_sum2(to_d2(acc[j][q]));
+      if (lane == 0) red[warp][j * RT + q] = v;
+    }
+  __syncthreads();
+  for (int p = threadIdx.x; p < GROUP * RT; p += BT) {
+    const int j = p / RT, q = p % RT;
+    if (j < g && q < nr) {
+      double2 sum = make_double2(0.0, 0.0);
+      for (int k = 0; k < BT / 32; ++k) sum = cadd(sum, red[k][p]);
+      partial[((long long)(i0 + j) * nrhs + r0 + q) * nchunk + c] = sum;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  unsigned *cnt = counters + (long long)t * ngroup + g0;
+  if (threadIdx.x == 0) last = (atomicAdd(cnt, 1u) == (unsigned)(nchunk - 1));
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // final sums of the tile's (vector, right-hand side) pairs, one warp per pair, in a fixed order
+  for (int p = warp; p < GROUP * RT; p += BT / 32) {
+    const int j = p / RT, q = p % RT;
+    if (j >= g || q >= nr) continue;
+    const double2 *pp = partial + ((long long)(i0 + j) * nrhs + r0 + q) * nchunk;
+    double2 sum = make_double2(0.0, 0.0);
+    for (int k = lane; k < nchunk; k += 32) sum = cadd(sum, __ldcg(pp + k));
+    sum = warp_sum2(sum);
+    if (lane == 0) h[(long long)(i0 + j) * nrhs + r0 + q] = cscale(sum, fac);
+  }
+  if (threadIdx.x == 0) *cnt = 0u;
 }
 
 // w^r += sign * fac * sum_i V_i^r h[i * nrhs + r]; the coefficients of this right-hand side are
@@ -321,6 +422,43 @@ __global__ void __launch_bounds__(BT) combine_kernel(const SV *__restrict__ V, l
   }
 }
 
+// The same with KV = 16 / sizeof(SV) consecutive elements per thread and one 16-byte load per basis
+// vector (4- and 8-byte basis storage on 16-byte boundaries, n a multiple of KV); one output column
+// per pass keeps the KV accumulators in registers.
+template <typename SV, typename SO>
+__global__ void __launch_bounds__(BT) combine_vec_kernel(const SV *__restrict__ V, long long vstride,
+                                                         long long vrs, int nvec, const double2 *__restrict__ Cf,
+                                                         int ncol, double fac, SO *__restrict__ out,
+                                                         long long ostride, long long n, int nrhs) {
+  using C = Ar<SO>;
+  constexpr int KV = 16 / sizeof(SV);
+  __shared__ C coef[COMB_MAXV];
+  const long long e = ((long long)(blockIdx.x / nrhs) * BT + threadIdx.x) * KV;
+  const int r = blockIdx.x % nrhs;
+  for (int c = 0; c < ncol; ++c) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < nvec; i += BT)
+      coef[i] = from_d2<C>(cscale(Cf[((long long)i * ncol + c) * nrhs + r], fac));
+    __syncthreads();
+    if (e >= n) continue;
+    C acc[KV];
+#pragma unroll
+    for (int q = 0; q < KV; ++q) acc[q] = cz<C>();
+    const SV *vp = V + r * vrs + e;
+    for (int i = 0; i < nvec; ++i, vp += vstride) {
+      SV vv[KV];
+      const uint4 raw = __ldg(reinterpret_cast<const uint4 *>(vp));
+      memcpy(vv, &raw, 16);
+      const C cf = coef[i];
+#pragma unroll
+      for (int q = 0; q < KV; ++q) gfma(acc[q], ldc(vv[q]), cf);
+    }
+    SO *op = out + (long long)c * ostride + r * n + e;
+#pragma unroll
+    for (int q = 0; q < KV; ++q) op[q] = stc<SO>(acc[q]);
+  }
+}
+
 template <typename S>
 __global__ void invscale_kernel(S *__restrict__ x, const double *__restrict__ s, long long n) {
   // the reciprocal once per block, then one multiply per component in the arithmetic type
@@ -338,6 +476,36 @@ __global__ void invscale_kernel(S *__restrict__ x, const double *__restrict__ s,
   v.x *= f;
   v.y *= f;
   x[r * n + e] = stc<S>(v);
+}
+
+// The same with KV = 16 / sizeof(S) consecutive elements per thread and one 16-byte access each way
+// (4- and 8-byte storage, x on a 16-byte boundary, n a multiple of KV)
+template <typename S>
+__global__ void invscale_vec_kernel(S *__restrict__ x, const double *__restrict__ s, long long n) {
+  using R = decltype(Ar<S>().x);
+  constexpr int KV = 16 / sizeof(S);
+  __shared__ R f;
+  const int r = blockIdx.y;
+  if (threadIdx.x == 0) {
+    const double d = s[r];
+    f = (R)(d > 0.0 ? 1.0 / d : 0.0);
+  }
+  __syncthreads();
+  const long long e = ((long long)blockIdx.x * BT + threadIdx.x) * KV;
+  if (e >= n) return;
+  uint4 *p = reinterpret_cast<uint4 *>(x + r * n + e);
+  uint4 raw = *p;
+  S v[KV];
+  memcpy(v, &raw, 16);
+#pragma unroll
+  for (int q = 0; q < KV; ++q) {
+    Ar<S> a = ldc(v[q]);
+    a.x *= f;
+    a.y *= f;
+    v[q] = stc<S>(a);
+  }
+  memcpy(&raw, v, 16);
+  *p = raw;
 }
 
 // y = fac * x with conversion between storage types (fac = 1 for a plain copy)
@@ -557,12 +725,13 @@ lqcd_status blas_norms(lqcd_ctx *ctx, const S *x, long long n, int nrhs, double 
 
 static int multidot_chunks(lqcd_ctx *ctx, long long n, int nrhs, int nvec, bool shared) {
   // element chunks of at least 8 elements per thread; enough blocks (chunks x vector groups x
-  // right-hand sides) to cover the SMs a few times.  With a basis shared by several right-hand
+  // right-hand sides) for about 16 per SM, several waves of the 4-6 resident ones, so that no SM
+  // idles at the end.  With a basis shared by several right-hand
   // sides, also chunks short enough that the blocks in flight (about 8 per SM) touch at most ~32 MB
   // of L2, so that the basis chunk is read from DRAM once for all of them.
   const int ngroup = (nvec + GROUP - 1) / GROUP;
   const long long max_chunks = std::max<long long>(1, n / (8LL * BT));
-  long long want = std::max<long long>(1, (4LL * ctx->sms) / std::max<long long>(1, (long long)nrhs * ngroup));
+  long long want = std::max<long long>(1, (16LL * ctx->sms) / std::max<long long>(1, (long long)nrhs * ngroup));
   if (shared && nrhs > 1) {
     const long long per_chunk_blocks = (long long)nrhs * ngroup;
     const long long chunks_in_flight = std::max<long long>(1, 8LL * ctx->sms / per_chunk_blocks);
@@ -582,7 +751,7 @@ lqcd_status blas_reserve(lqcd_ctx *ctx, long long n, int nrhs, int max_nvec) {
   unsigned *cnt = nullptr;
   LQCD_TRY(ws_get(ctx, WS_PARTIAL, need, &p));
   LQCD_TRY(ws_get(ctx, WS_SCAL, sizeof(double) * (size_t)partial_blocks(ctx, n, nrhs) * nrhs, &p));
-  return reduction_counters(ctx, nrhs, &cnt);
+  return reduction_counters(ctx, nrhs * ((std::max(max_nvec, 1) + GROUP - 1) / GROUP), &cnt);
 }
 
 template <typename SV, typename SW>
@@ -590,12 +759,29 @@ lqcd_status blas_multidot(lqcd_ctx *ctx, const SV *V, long long vstride, long lo
                           long long n, int nrhs, double2 *h) {
   if (nvec <= 0) return LQCD_OK;
   const int ngroup = (nvec + GROUP - 1) / GROUP;
+  if (vrs == 0 && nrhs > 1) {
+    // shared basis: RT = 2 right-hand sides per block (register budget: 16 complex accumulators)
+    constexpr int RT = 2;
+    const int ntile = (nrhs + RT - 1) / RT;
+    const int nchunk = multidot_chunks(ctx, n, ntile, nvec, false);
+    if ((long long)nchunk * ngroup * ntile > 0x7fffffffLL) return set_err(ctx, LQCD_ERR_INVALID_ARG, "multidot: grid too large");
+    void *p = nullptr;
+    unsigned *cnt = nullptr;
+    LQCD_TRY(ws_get(ctx, WS_PARTIAL, sizeof(double2) * (size_t)nchunk * nrhs * nvec, &p));
+    LQCD_TRY(reduction_counters(ctx, ntile * ngroup, &cnt));
+    const double fac = 1.0 / (store_sigma<SV>(ctx->N) * store_sigma<SW>(ctx->N));
+    kbegin(ctx);
+    multidot_shared_kernel<SV, SW, RT><<<(unsigned)((long long)nchunk * ngroup * ntile), BT, 0, ctx->stream>>>(
+        V, vstride, nvec, w, n, nrhs, nchunk, fac, (double2 *)p, cnt, h);
+    const double bytes = (double)sizeof(SV) * n * nvec + (double)sizeof(SW) * n * nrhs;
+    return launch_check_bytes(ctx, "multidot_shared_kernel", K_DOT, (double)n * nrhs * nvec, bytes);
+  }
   const int nchunk = multidot_chunks(ctx, n, nrhs, nvec, vrs == 0);
   if ((long long)nchunk * ngroup * nrhs > 0x7fffffffLL) return set_err(ctx, LQCD_ERR_INVALID_ARG, "multidot: grid too large");
   void *p = nullptr;
   unsigned *cnt = nullptr;
   LQCD_TRY(ws_get(ctx, WS_PARTIAL, sizeof(double2) * (size_t)nchunk * nrhs * nvec, &p));
-  LQCD_TRY(reduction_counters(ctx, nrhs, &cnt));
+  LQCD_TRY(reduction_counters(ctx, nrhs * ngroup, &cnt));
   const double fac = 1.0 / (store_sigma<SV>(ctx->N) * store_sigma<SW>(ctx->N));
   // 16-byte loads for the 4- and 8-byte storage types when every vector starts on a 16-byte boundary
   const bool vec = sizeof(SV) < 16 && sizeof(SV) == sizeof(SW) && ((uintptr_t)V % 16 == 0) &&
@@ -646,10 +832,18 @@ lqcd_status blas_combine(lqcd_ctx *ctx, const SV *V, long long vstride, long lon
   if (ncol <= 0) return LQCD_OK;
   if (nvec > COMB_MAXV) return set_err(ctx, LQCD_ERR_INVALID_ARG, "combine: at most %d vectors", COMB_MAXV);
   const double fac = store_sigma<SO>(ctx->N) / store_sigma<SV>(ctx->N);
+  const bool vec = sizeof(SV) < 16 && ncol <= 2 && ((uintptr_t)V % 16 == 0) &&
+                   ((vstride * (long long)sizeof(SV)) % 16 == 0) && ((vrs * (long long)sizeof(SV)) % 16 == 0) &&
+                   ((n * (long long)sizeof(SV)) % 16 == 0);
   kbegin(ctx);
-  combine_kernel<SV, SO><<<(unsigned)((long long)ceil_div(n, BT) * nrhs), BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, C,
-                                                                                              ncol, fac, out, ostride,
-                                                                                              n, nrhs);
+  if (vec) {
+    const long long kv = 16 / (long long)sizeof(SV);
+    combine_vec_kernel<SV, SO><<<(unsigned)((long long)ceil_div(n / kv, BT) * nrhs), BT, 0, ctx->stream>>>(
+        V, vstride, vrs, nvec, C, ncol, fac, out, ostride, n, nrhs);
+  } else {
+    combine_kernel<SV, SO><<<(unsigned)((long long)ceil_div(n, BT) * nrhs), BT, 0, ctx->stream>>>(
+        V, vstride, vrs, nvec, C, ncol, fac, out, ostride, n, nrhs);
+  }
   const double bytes = (double)sizeof(SV) * n * nvec * (vrs != 0 ? nrhs : 1) + (double)sizeof(SO) * n * ncol * nrhs;
   return launch_check_bytes(ctx, "combine_kernel", K_COMBINE, (double)n * nrhs * nvec * ncol, bytes);
 }
@@ -657,7 +851,12 @@ lqcd_status blas_combine(lqcd_ctx *ctx, const SV *V, long long vstride, long lon
 template <typename S>
 lqcd_status blas_invscale(lqcd_ctx *ctx, S *x, const double *s, long long n, int nrhs) {
   kbegin(ctx);
-  invscale_kernel<S><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(x, s, n);
+  if (sizeof(S) < 16 && (uintptr_t)x % 16 == 0 && (n * (long long)sizeof(S)) % 16 == 0) {
+    const long long kv = 16 / (long long)sizeof(S);
+    invscale_vec_kernel<S><<<dim3(ceil_div(n / kv, BT), nrhs), BT, 0, ctx->stream>>>(x, s, n);
+  } else {
+    invscale_kernel<S><<<dim3(ceil_div(n, BT), nrhs), BT, 0, ctx->stream>>>(x, s, n);
+  }
   return launch_check_bytes(ctx, "invscale_kernel", K_BLAS1, (double)n * nrhs, 2.0 * sizeof(S) * n * nrhs);
 }
 
