@@ -54,6 +54,10 @@ KAPPA2, NNOISE2, M2, K2, PLAQ2, SEED2 = 0.157, 50, 60, 30, 0.6, 2024
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 DFMA / clock / SM at the 2070 MHz maximum clock
 WILSON_FLOPS = 1368        # per site per right-hand side (1320 for P, 48 for 1 - kappa P)
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) per algorithmic byte of a kernel class, from an ncu capture of the same
+# kernels on the 16^3 x 32 noise block (bench.py --case noise-block-f16)
+DRAM_PER_ALGORITHMIC = {"dot": (1.017, "ncu dram__bytes_read.sum + dram__bytes_write.sum over 224 launches of "
+                                       "multidot_kernel<__half2> on 16^3x32 / their algorithmic bytes")}
 # per-noise matrix-vector products of the plain FP64 noise solves on the headline workload (GPU
 # path; the oracle runs the same algorithm): used to extrapolate the oracle's bounded sample
 MATVECS_PER_NOISE_FP64 = 650
@@ -240,12 +244,15 @@ def dslash_rates(torch):
     BF16 fields; FP32 links, recon 12 and 18).  Algorithmic bytes per launch: each spinor read once
     and written once (nrhs x V x 24 reals each way) plus the links once (4 x V x 18 or 12 reals);
     flops 1368 per site and right-hand side.
-    CUDA events on the library stream, 2 warm-up and 5 timed launches; fields exceed L2 for nrhs > 1."""
+    CUDA events on the library stream around each of 5 timed launches (after 2 warm-up ones), with
+    L2 flushed before each (a 512 MB buffer written), so that links and fields come from DRAM as
+    they do inside a solver, where the Gram-Schmidt streams evict them between applications."""
     from paper_1903_06986_gb300 import lqcd, synth
     ctx = lqcd.Context(DSLASH_DIMS, recon=12)
     V = int(np.prod(DSLASH_DIMS))
     U = torch.from_numpy(synth.su3_links(DSLASH_DIMS, 0.4323, 7)).cuda()
     packed_links = {12: ctx.pack_links_f32(U, 12), 18: ctx.pack_links_f32(U, 18)}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     out = {}
     cases = [("f64", 18, 1, 0), ("f64", 18, 8, 0), ("f32packed", 12, 1, 1), ("f32packed", 12, 8, 2),
              ("f32packed", 12, 16, 2), ("f32packed", 18, 8, 2), ("f16packed", 12, 1, 1), ("f16packed", 12, 8, 2),
@@ -275,14 +282,16 @@ def dslash_rates(torch):
             w, lreals = 4, recon
         for _ in range(2):
             fn()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
+        t = 0.0
         for _ in range(5):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
             fn()
-        e1.record()
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 5 / 1000.0
+            e1.record()
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1) / 1000.0
+        t /= 5
         nbytes = nrhs * V * 48 * w + V * 4 * lreals * lw
         gbs = nbytes / t / 1e9
         tf = 1368.0 * V * nrhs / t / 1e12
@@ -294,7 +303,7 @@ def dslash_rates(torch):
         del x, y
     ctx.close()
     return {"lattice": "24x24x24x32", "bytes": "nrhs*V*24 reals read+written + links once",
-            "hbm_peak_gbs": HBM_PEAK_GBS, "results": out}
+            "l2": "flushed before every timed launch", "hbm_peak_gbs": HBM_PEAK_GBS, "results": out}
 
 
 DEFL_DIMS = (24, 24, 24, 32)
@@ -798,6 +807,12 @@ def main():
     if tbytes.get(dom, 0) > 0 and ms > 0:
         roofline["achieved"] = tbytes[dom] / (ms / 1000.0) / 1e9
         roofline["frac"] = roofline["achieved"] / HBM_PEAK_GBS
+        if dom in DRAM_PER_ALGORITHMIC:
+            # DRAM bytes per launch: the ratio ncu measured on the same kernels (smaller lattice, the
+            # bytes per launch in proportion to the vectors read) times this run's algorithmic bytes
+            ratio, src = DRAM_PER_ALGORITHMIC[dom]
+            roofline["traffic"] = ratio * roofline["bytes_per_launch"]
+            roofline["traffic_source"] = src
 
     info_lam_min = lam_min
     loop.close()

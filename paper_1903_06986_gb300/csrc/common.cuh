@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -79,6 +80,8 @@ struct lqcd_ctx {
   int eo_dims[4];
 };
 
+namespace dense { struct QRFact; }
+
 struct lqcd_defl {
   lqcd_ctx *ctx;
   int k;
@@ -92,6 +95,8 @@ struct lqcd_defl {
   double2 *Hbar_dev;    // (k+1) x k row-major (device), NULL when imported
   void *tc;             // bf16 slices of E for the tensor-core contractions (made on first use)
   void *Vf32;           // packed FP32 copy of V for mixed-precision solves (made on first use)
+  // Householder factorisation of Hbar for the GMRES-Proj projections (made on first use)
+  std::shared_ptr<dense::QRFact> hqr;
 };
 
 // ----- status plumbing ------------------------------------------------------------------
@@ -123,7 +128,7 @@ enum WsSlot {
   WS_PARTIAL = 0, WS_SCAL, WS_TMP0, WS_TMP1, WS_TMP2, WS_TMP3, WS_BASIS, WS_HESS, WS_COEF,
   WS_BASIS2, WS_TMP4, WS_TMP5, WS_EST0, WS_EST1, WS_EST2, WS_PROBE,
   WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_COUNT, WS_TUNE, WS_SPEC, WS_NBLK, WS_TC_STAT, WS_TC_B, WS_TC_PART, WS_TC_D,
-  WS_POLY1, WS_POLY2, WS_POLY3, WS_EO, WS_NSLOTS
+  WS_POLY1, WS_POLY2, WS_POLY3, WS_EO, WS_TC_AC, WS_TC_REXP, WS_NSLOTS
 };
 lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr);
 void graph_cache_clear(lqcd_ctx *ctx);
@@ -290,6 +295,9 @@ lqcd_status tc_slices_make(lqcd_ctx *ctx, const double2 *E, int k, void **out);
 void tc_slices_free(void *slices);
 lqcd_status tc_vhx(lqcd_ctx *ctx, const void *slices, const double2 *X, int nrhs, double2 *G);
 lqcd_status tc_vc(lqcd_ctx *ctx, const void *slices, const double2 *C, const double2 *d, int nrhs, double2 *Y);
+// Y = E C for a basis used once (E: k fields, C: k x ncol device): only this product's slices, in
+// context workspace
+lqcd_status tc_vc_oneshot(lqcd_ctx *ctx, const double2 *E, int k, const double2 *C, int ncol, double2 *Y);
 // right-hand-side block width autotuner (batch.cu); see lqcd_autotune_block
 lqcd_status autotune_block(lqcd_ctx *ctx, const double *links, double kappa, const lqcd_defl *defl,
                            const lqcd_krylov_opts *o, const int *cand, int ncand, int *best, double *seconds);

@@ -47,16 +47,21 @@ static void householder(std::vector<cd> &x, cd &alpha, double &beta) {
   beta = vn > 0.0 ? 2.0 / vn : 0.0;
 }
 
-std::vector<cd> lstsq(const Mat &A0, const std::vector<cd> &c0) {
-  Mat A = A0;
-  std::vector<cd> c = c0;
+QRFact qr_factor(const Mat &A0) {
+  QRFact f;
+  f.a = A0;
+  Mat &A = f.a;
   const int m = A.r, n = A.c;
+  f.v.resize(n);
+  f.beta.assign(n, 0.0);
   for (int k = 0; k < n; ++k) {
-    std::vector<cd> v(m - k);
+    std::vector<cd> &v = f.v[k];
+    v.resize(m - k);
     for (int i = k; i < m; ++i) v[i - k] = A(i, k);
     cd alpha;
     double beta;
     householder(v, alpha, beta);
+    f.beta[k] = beta;
     if (beta == 0.0) continue;
     for (int j = k; j < n; ++j) {
       cd s = 0.0;
@@ -64,6 +69,18 @@ std::vector<cd> lstsq(const Mat &A0, const std::vector<cd> &c0) {
       s *= beta;
       for (int i = k; i < m; ++i) A(i, j) -= s * v[i - k];
     }
+  }
+  return f;
+}
+
+std::vector<cd> qr_solve(const QRFact &f, const std::vector<cd> &c0) {
+  const Mat &A = f.a;
+  const int m = A.r, n = A.c;
+  std::vector<cd> c = c0;
+  for (int k = 0; k < n; ++k) {
+    const double beta = f.beta[k];
+    if (beta == 0.0) continue;
+    const std::vector<cd> &v = f.v[k];
     cd s = 0.0;
     for (int i = k; i < m; ++i) s += std::conj(v[i - k]) * c[i];
     s *= beta;
@@ -77,6 +94,8 @@ std::vector<cd> lstsq(const Mat &A0, const std::vector<cd> &c0) {
   }
   return d;
 }
+
+std::vector<cd> lstsq(const Mat &A0, const std::vector<cd> &c0) { return qr_solve(qr_factor(A0), c0); }
 
 bool solve(const Mat &A0, const std::vector<cd> &b, std::vector<cd> &x) {
   Mat A = A0;

@@ -26,6 +26,17 @@ Mat adjoint(const Mat &A);
 // d = argmin || c - A d ||_2 (A: rows >= cols, full column rank) by Householder QR
 std::vector<cd> lstsq(const Mat &A, const std::vector<cd> &c);
 
+// The same in two steps, for many right-hand sides c with one A: the Householder factorisation
+// once (R in the upper triangle of `a`, the reflections in v / beta), then per c the reflections and
+// the back substitution (bit-identical to lstsq)
+struct QRFact {
+  Mat a;
+  std::vector<std::vector<cd>> v;
+  std::vector<double> beta;
+};
+QRFact qr_factor(const Mat &A);
+std::vector<cd> qr_solve(const QRFact &f, const std::vector<cd> &c);
+
 // x = A^{-1} b by LU with partial pivoting; returns false on an exactly zero pivot
 bool solve(const Mat &A, const std::vector<cd> &b, std::vector<cd> &x);
 

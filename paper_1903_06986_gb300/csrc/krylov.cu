@@ -459,6 +459,18 @@ lqcd_status check_opts(lqcd_ctx *ctx, const lqcd_krylov_opts *o, int nrhs) {
 }
 
 // Rayleigh-Ritz eigenpairs on span(V_k): T = Hbar_k[:k,:k]
+// Y = V C for one right-hand side's basis V (nv fields of N at stride vstride; C: device nv x ncol):
+// the dense FP64 product that rotates a Krylov basis.  With the tensor-core engine selected and a
+// contiguous basis it runs as the split-precision FP64 emulation of the deflation contractions (an
+// FP64 GEMM of 8 N nv ncol flop otherwise, FP64-pipe bound: 1.7 s for the 241 x 201 restart of
+// MINRES-DR(240,200) on 24^3 x 32), else on the FP64 combine kernel.
+lqcd_status basis_combine(lqcd_ctx *ctx, const double2 *V, long long vstride, int nv, const double2 *C, int ncol,
+                          double2 *Y) {
+  const long long N = ctx->N;
+  if (ctx->defl_engine == LQCD_DEFL_TENSOR && vstride == N) return tc_vc_oneshot(ctx, V, nv, C, ncol, Y);
+  return blas_combine(ctx, V, vstride, 0, nv, C, ncol, Y, N, N, 1);
+}
+
 lqcd_status ritz_pairs(lqcd_ctx *ctx, lqcd_defl *d) {
   const int k = d->k;
   Mat T(k, k);
@@ -502,7 +514,7 @@ lqcd_status ritz_pairs(lqcd_ctx *ctx, lqcd_defl *d) {
   void *p;
   LQCD_TRY(ws_get(ctx, WS_COEF, sizeof(cd) * C.size(), &p));
   LQCD_TRY(upload(ctx, C, p));
-  return blas_combine(ctx, d->V, d->N, 0, k, (const double2 *)p, k, d->E, d->N, d->N, 1);
+  return basis_combine(ctx, d->V, d->N, k, (const double2 *)p, k, d->E);
 }
 
 // hermitian[r]: right-hand side r uses the Hermitian (MINRES-DR) form of the harmonic Ritz problem.
@@ -595,7 +607,11 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
     const bool last = all_conv || cyc + 1 == o->max_cycles;
     if (last) break;
     LQCD_TRY(upload(ctx, pcoef, W.coef));
-    LQCD_TRY(blas_combine(ctx, W.Vb, vs, N, m + 1, W.coef, k + 1, W.Vt, vs, N, nrhs));
+    if (nrhs == 1) {
+      LQCD_TRY(basis_combine(ctx, W.Vb, vs, m + 1, W.coef, k + 1, W.Vt));
+    } else {
+      LQCD_TRY(blas_combine(ctx, W.Vb, vs, N, m + 1, W.coef, k + 1, W.Vt, vs, N, nrhs));
+    }
     LQCD_TRY(blas_copy(ctx, W.Vt, W.Vb, (long long)(k + 1) * vs));
     for (int r = 0; r < nrhs; ++r) {
       if (!R[r].active) continue;
@@ -663,7 +679,7 @@ lqcd_status gmresdr_core(lqcd_ctx *ctx, const Op &op, const double2 *b, double2 
       for (int i = 0; i <= m; ++i)
         for (int c = 0; c <= k; ++c) pc[(size_t)i * (k + 1) + c] = P(i, c);
       LQCD_TRY(upload(ctx, pc, W.coef));
-      LQCD_TRY(blas_combine(ctx, W.Vb + (long long)r * N, vs, 0, m + 1, W.coef, k + 1, d->V, N, N, 1));
+      LQCD_TRY(basis_combine(ctx, W.Vb + (long long)r * N, vs, m + 1, W.coef, k + 1, d->V));
       Mat Pk(m, k);
       for (int i = 0; i < m; ++i)
         for (int c = 0; c < k; ++c) Pk(i, c) = P(i, c);
@@ -709,8 +725,8 @@ struct ProjResult {
 // FP16 / BF16 basis); SD: storage of the deflation space Vd (FP32 under an FP16 / BF16 basis: its
 // projection multiplies by 1 / lambda and would amplify a coarser rounding of it).
 template <typename S, typename SX = S, typename SD = S>
-lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const SD *Vd, const Mat &Hk, const SX *b, SX *x, int nrhs, int m,
-                     double tol, int max_cycles, bool check_true, ProjResult &res) {
+lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const SD *Vd, const Mat &Hk, const dense::QRFact &Hq, const SX *b,
+                     SX *x, int nrhs, int m, double tol, int max_cycles, bool check_true, ProjResult &res) {
   const int k = Hk.c;
   const long long N = ctx->N, vs = (long long)nrhs * N;
   WorkspaceT<S> W;
@@ -752,7 +768,7 @@ lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const SD *Vd, const Mat &H
       if (!R[r].active) continue;
       std::vector<cd> c(k + 1);
       for (int i = 0; i <= k; ++i) c[i] = cd(cp[(size_t)i * nrhs + r].x, cp[(size_t)i * nrhs + r].y);
-      std::vector<cd> d = dense::lstsq(Hk, c);
+      std::vector<cd> d = dense::qr_solve(Hq, c);
       for (int j = 0; j < k; ++j) dk[(size_t)j * nrhs + r] = d[j];
       for (int i = 0; i <= k; ++i) {
         cd v = 0.0;
@@ -851,6 +867,13 @@ Mat defl_hbar(const lqcd_defl *defl) {
   return Hk;
 }
 
+// the space's Hbar factorised once (the projection of every GMRES-Proj cycle solves with it)
+const dense::QRFact &defl_qr(const lqcd_defl *defl) {
+  lqcd_defl *d = const_cast<lqcd_defl *>(defl);
+  if (!d->hqr) d->hqr = std::make_shared<dense::QRFact>(dense::qr_factor(defl_hbar(defl)));
+  return *d->hqr;
+}
+
 // Plain FP64 GMRES-Proj
 lqcd_status proj_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const double2 *b, double2 *x, int nrhs,
                       const lqcd_krylov_opts *o, lqcd_solve_info *info) {
@@ -858,7 +881,8 @@ lqcd_status proj_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const 
   LQCD_TRY(check_opts(ctx, o, nrhs));
   if (!defl || !defl->V || !defl->Hbar_dev) return set_err(ctx, LQCD_ERR_INVALID_ARG, "GMRES-Proj needs a solver-made deflation space");
   ProjResult res;
-  LQCD_TRY(proj_run<double2>(ctx, op, defl->V, defl_hbar(defl), b, x, nrhs, o->m, o->tol, o->max_cycles, true, res));
+  LQCD_TRY(proj_run<double2>(ctx, op, defl->V, defl_hbar(defl), defl_qr(defl), b, x, nrhs, o->m, o->tol,
+                             o->max_cycles, true, res));
   if (op.pp.degree > 0) {
     // solved B y = b: the solution of A x = b is x = p(A) y (same residual)
     double2 *t;
@@ -945,6 +969,7 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
   float2 *e32p = e32;
   if (op.pp.degree > 0) LQCD_TRY(ws_get(ctx, WS_POLY3, sizeof(float2) * (size_t)vs, (void **)&e32p));
   const Mat Hk = defl_hbar(defl);
+  const dense::QRFact &Hq = defl_qr(defl);
   LQCD_TRY(blas_zero(ctx, x, vs));
   LQCD_TRY(blas_copy(ctx, b, r, vs));
   LQCD_TRY(blas_norms(ctx, b, N, nrhs, sc));
@@ -974,7 +999,7 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
     LQCD_CUDA(ctx, cudaMemcpyAsync(sc, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
     LQCD_TRY(pack_f32(ctx, r, sc, (float4 *)r32, nrhs));
     ProjResult pr;
-    LQCD_TRY((proj_run<S, float2, float2>(ctx, opl, Vlp, Hk, r32, e32, nrhs, o->m, inner_tol,
+    LQCD_TRY((proj_run<S, float2, float2>(ctx, opl, Vlp, Hk, Hq, r32, e32, nrhs, o->m, inner_tol,
                                   std::max(1, o->max_cycles - inner_cycles), false, pr)));
     inner_cycles += pr.cycles;
     matvecs += pr.matvecs;

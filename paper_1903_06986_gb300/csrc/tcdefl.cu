@@ -1053,6 +1053,37 @@ lqcd_status tc_vc(lqcd_ctx *ctx, const void *slices, const double2 *Cm, const do
   return LQCD_OK;
 }
 
+// Y = E C (ncol output fields; E: k fields of N, vector-major; C: device, k x ncol) on the tensor
+// cores with only the operand slices of this product, built in context workspace (kept for the next
+// call of the same or smaller size): the restart rotation V_{k+1} = V_{m+1} P_{k+1} of GMRES-DR /
+// MINRES-DR and its Ritz vectors, a new basis every call.
+lqcd_status tc_vc_oneshot(lqcd_ctx *ctx, const double2 *E, int k, const double2 *C, int ncol, double2 *Y) {
+  if (k <= 0 || k > 4096 || ncol <= 0) return set_err(ctx, LQCD_ERR_INVALID_ARG, "tensor-core V C: bad sizes");
+  TcSlices S{};
+  S.k = k;
+  S.L = 2 * ctx->N;
+  S.mtc = (int)((S.L + TC_M - 1) / TC_M);
+  S.kcc = (k + TC_KCH - 1) / TC_KCH;
+  const size_t bc = tc_bytes_c(k, S.L);
+  void *p;
+  LQCD_TRY(ws_get(ctx, WS_TC_AC, bc, &p));
+  S.Ac = (unsigned char *)p;
+  LQCD_TRY(ws_get(ctx, WS_TC_REXP, sizeof(int) * (size_t)S.L + 64, &p));
+  S.rowexp = (int *)p;
+  int *flag = S.rowexp + S.L;
+  LQCD_CUDA(ctx, cudaMemsetAsync(S.Ac, 0, bc, ctx->stream));
+  LQCD_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+  kbegin(ctx);
+  rowexp_kernel<<<ceil_div(S.L, 256), 256, 0, ctx->stream>>>((const double *)E, k, S.L, S.rowexp, flag);
+  LQCD_TRY(launch_check(ctx, "rowexp_kernel", K_SLICE, (double)k * S.L));
+  LQCD_TRY(check_flag(ctx, flag, "tensor-core V C"));
+  kbegin(ctx);
+  slice_ac_kernel<<<dim3(ceil_div(S.L, 128), S.kcc * (TC_KCH / 8)), 128, 0, ctx->stream>>>(
+      (const double *)E, k, S.L, S.rowexp, S.kcc, (unsigned short *)S.Ac);
+  LQCD_TRY(launch_check(ctx, "slice_ac_kernel", K_SLICE, (double)k * S.L));
+  return tc_vc(ctx, &S, C, nullptr, ncol, Y);
+}
+
 extern "C" lqcd_status lqcd_tc_slice_bytes(const int dims[4], int k, size_t *bytes) {
   if (!dims || !bytes || k < 1 || k > 4096) return LQCD_ERR_INVALID_ARG;
   long long V = 1;

@@ -22,7 +22,8 @@ def lib():
     if cxx is None:
         pytest.skip("no host C++ compiler")
     out = os.path.join(tempfile.mkdtemp(prefix="dense_shim_"), "libdense_shim.so")
-    subprocess.run([cxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC,
+    # the library's host flags (complex products without the NaN-recovery path)
+    subprocess.run([cxx, "-O2", "-std=c++17", "-fcx-fortran-rules", "-shared", "-fPIC", "-I", CSRC,
                     os.path.join(ROOT, "tests", "native", "dense_shim.cpp"), os.path.join(CSRC, "dense.cpp"),
                     "-o", out], check=True)
     return ctypes.CDLL(out)

@@ -163,3 +163,34 @@ def test_vdag_x_and_v_c_sampled_at_full_size():
         assert abs(host(Y[j, i]) - ref) <= TC_TOL * split_bound(col[None, :], Ch[:, j:j + 1])[0, 0]
     del E, X, Y
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("hermitian", [True, False], ids=["minresdr", "gmresdr"])
+def test_restart_rotation_on_tensor_engine(hermitian):
+    """GMRES-DR / MINRES-DR with one right-hand side rotate their basis at every restart,
+    V_{k+1} = V_{m+1} P_{k+1}, and form the Ritz vectors E = V_k Y: with the tensor-core engine both
+    products run as the split-precision FP64 emulation.  Against the FP64 engine: the same solution
+    within cond(M) tol, the same Ritz values, and the final space keeps the Arnoldi relation
+    A V_k = V_{k+1} Hbar_k to 1e-12 (A = M gamma_5 or M; Sec. 5.3, 5.4)."""
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = dev(synth.su3_links(dims, 0.3, 4))
+    ctx = context(dims)
+    b = ctx.noise_z4(3, 0, 1)
+    solve = ctx.minresdr_solve if hermitian else ctx.gmresdr_solve
+    runs = {}
+    for eng in (lqcd.DEFL_FP64, lqcd.DEFL_TENSOR):
+        ctx.set_defl_engine(eng)
+        x, info, defl = solve(U, kappa, b, 30, 10, 1e-13, want_defl=True, eig_tol=1e-12)
+        assert info["converged"] and info["true_resid"] <= 1e-13
+        runs[eng] = (host(x), defl.export(), info)
+    ctx.set_defl_engine(lqcd.DEFL_FP64)
+    (x64, e64, _), (xtc, etc, itc) = runs[lqcd.DEFL_FP64], runs[lqcd.DEFL_TENSOR]
+    assert rel_err(xtc, x64) < 10 * 12.5 * 1e-13
+    assert np.allclose(np.sort_complex(etc["lam"]), np.sort_complex(e64["lam"]), rtol=1e-9, atol=1e-12)
+    V, H = etc["V"], etc["Hbar"]
+    k = H.shape[1]
+    flags = lqcd.APPLY_G5R if hermitian else lqcd.APPLY_M
+    AV = host(ctx.wilson_apply(U, kappa, V[:k].reshape((k,) + tuple(ctx.field(1).shape[1:])).contiguous(),
+                               flags=flags)).reshape(k, -1)
+    VH = (host(V).reshape(k + 1, -1).T @ H).T
+    assert np.abs(AV - VH).max() <= 1e-12 * np.abs(AV).max()
