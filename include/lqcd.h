@@ -334,8 +334,18 @@ lqcd_status lqcd_poly_coeffs(lqcd_ctx *ctx, const double *links, double kappa, u
 
 /* t[k][op][t] = sum over the timeslice t of the exact diagonal density of Tr(Theta_op P^k),
  * k < K, by probing with colour classes whose members are more than K hops apart (host out,
- * K x 9 x Lt complex).  kappa enters only the point-split operators' own prefactor. */
+ * K x 9 x Lt complex).  kappa enters only the point-split operators' own prefactor.
+ * Meet in the middle (Sec. 5.1 add-back): P is applied to the whole probe field only up to a depth
+ * h (lqcd_set_probe_depth; by default the h with the fewest site updates, e.g. 2 of the 6 orders at
+ * K = 7 with 512 classes); each higher order k is evaluated only within K - k hops of the class
+ * members, where the contraction and the later orders read it.  The result is the same trace. */
 lqcd_status lqcd_hop_traces(lqcd_ctx *ctx, const double *links, double kappa, int K, double *t);
+
+/* Full-lattice applications of P per probe in lqcd_hop_traces and in the setup of loop estimates:
+ * depth in 1..64 fixes it, capped at K - 1 (every order a full application) and raised where an
+ * order would otherwise be completed more than 8 hops around the members; 0 = chosen per call to
+ * minimise the site updates (default).  LQCD_ERR_INVALID_ARG for values outside 0..64. */
+lqcd_status lqcd_set_probe_depth(lqcd_ctx *ctx, int depth);
 
 /* The colour classes lqcd_hop_traces probes with (host only; needs no GPU and no context): for an
  * Lx x Ly x Lz x Lt torus (dims[0..3], each >= 2) and K >= 1 terms, *nclasses receives the class

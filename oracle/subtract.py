@@ -118,6 +118,84 @@ def hop_traces(U, kappa, K, dims, spacing=None, batch=256):
     return out
 
 
+def _member_distance(dims, spacing, c):
+    """Torus taxicab distance of every site to the nearest member of Cartesian class c (members:
+    x_mu = c_mu mod p_mu); per axis the nearest residue, summed (the members form a product lattice)."""
+    px, py, pz, pt = spacing
+    cx, cy, cz, ct = c % px, (c // px) % py, (c // (px * py)) % pz, c // (px * py * pz)
+    t, z, y, x = np.meshgrid(*[np.arange(l) for l in reversed(dims)], indexing='ij')
+    d = 0
+    for coord, r, p in ((x, cx, px), (y, cy, py), (z, cz, pz), (t, ct, pt)):
+        a = (coord - r) % p
+        d = d + np.minimum(a, p - a)
+    return d
+
+
+def _member_owner(dims, spacing, c):
+    """Site index (T, Z, Y, X tuple of arrays) of the member of class c nearest to every site."""
+    px, py, pz, pt = spacing
+    cs = (c % px, (c // px) % py, (c // (px * py)) % pz, c // (px * py * pz))
+    t, z, y, x = np.meshgrid(*[np.arange(l) for l in reversed(dims)], indexing='ij')
+    own = []
+    for coord, r, p, l in zip((x, y, z, t), cs, (px, py, pz, pt), dims):
+        a = (coord - r) % p
+        own.append((coord - np.where(a <= p // 2, a, a - p)) % l)
+    return own[3], own[2], own[1], own[0]
+
+
+def hop_traces_meet(U, kappa, K, dims, spacing=None, completion_radius=None):
+    """Meet-in-the-middle form of ``hop_traces`` (Sec. 5.1 add-back), the same densities t[k, op, site].
+
+    With h = ceil((K - 1) / 2) and probe fields W_j = P^j z_c (j <= h) of each colour class c:
+      * local operators (scalar, gamma_mu), every order k = j1 + j2 with j2 = min(k, h):
+        by gamma_5-hermiticity of P, (P^j1)_{x,y} = g5 [(P^j1)_{y,x}]^dag g5, so
+        tr[Gamma (P^k)_{xx}] = sum_y tr[Gamma g5 B_j1(y)^dag g5 B_j2(y)], where B_j(y) is the 12 x 12
+        block (P^j)_{y,x} read off the 12 probes of the class at site y, and x is the class member
+        nearest y (members are more than 2h hops apart, so every nonzero block has one member);
+      * point-split operators, orders k > h: the contraction reads P^k z only at the members and
+        their neighbours, so P^k z is needed only within R_k = max(1, K - k) hops of a member and
+        is formed as P applied to P^(k-1) z, then cut to that neighbourhood (``completion_radius``
+        overrides R_k, to show that a smaller one changes the result).
+    The probing classes are Cartesian with the periods of ``default_spacing``."""
+    if spacing is None:
+        spacing = default_spacing(dims, K)
+    h = (K - 1 + 1) // 2
+    cls, ncls = probe_classes(dims, spacing)
+    out = np.zeros((K, O.NOPS) + L.site_shape(dims), dtype=np.complex128)
+    I3 = np.eye(3, dtype=np.complex128)
+    g5 = np.kron(L.G5, I3)
+    gam = [np.eye(12, dtype=np.complex128)] + [np.kron(L.G[mu], I3) for mu in range(4)]
+    nsite = L.volume(dims)
+    for c in range(ncls):
+        z = np.zeros(L.field_shape(dims, (12,)), dtype=np.complex128)
+        for a in range(12):
+            z[a][cls == c, a // 3, a % 3] = 1.0
+        W = [z]
+        for j in range(1, h + 1):
+            W.append(L.hop(U, W[-1]))
+        # blocks B_j[site, comp, probe]
+        B = [w.reshape(12, nsite, 12).transpose(1, 2, 0) for w in W]
+        owner = _member_owner(dims, spacing, c)
+        for k in range(K):
+            j2 = min(k, h)
+            j1 = k - j2
+            M1 = np.einsum('ab,scb,cd->sad', g5, B[j1].conj(), g5)      # (P^j1)_{x,y}: [site y, a, comp]
+            for op in range(5):
+                q = np.einsum('ba,sac,scb->s', gam[op], M1, B[j2]).reshape(L.site_shape(dims))
+                np.add.at(out[k, op], owner, q)
+        dist = _member_distance(dims, spacing, c)
+        w = z
+        for k in range(K):
+            if k > 0:
+                w = L.hop(U, w)
+                if k > h:
+                    r = max(1, K - k) if completion_radius is None else completion_radius(K, k)
+                    w = np.where((dist <= r)[None, ..., None, None], w, 0.0)
+            d = O.densities(U, kappa, z, w).sum(axis=1)
+            out[k, 5:] += d[5:]
+    return out
+
+
 def pert_addback(t, kappa, K):
     """PS add-back densities: sum_{k<K} kappa^k t_k."""
     return sum((kappa ** k) * t[k] for k in range(K))

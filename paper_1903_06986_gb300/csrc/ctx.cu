@@ -219,6 +219,7 @@ lqcd_status lqcd_ctx_create(lqcd_ctx **out, const int dims[4], int link_recon, v
   c->tc_wait_ns = 2000000000ull;
   c->tc_stop_after = -1;
   c->inner_gs_passes = 0;
+  c->probe_depth = 0;
   c->eo = 0;
   for (int i = 0; i < 4; ++i) c->eo_dims[i] = dims[i];
   c->cap_stream = nullptr;
@@ -269,6 +270,13 @@ lqcd_status lqcd_set_inner_gs_passes(lqcd_ctx *ctx, int passes) {
   if (passes < 0 || passes > 2) return set_err(ctx, LQCD_ERR_INVALID_ARG, "set_inner_gs_passes: passes must be 0, 1 or 2");
   if (passes != ctx->inner_gs_passes) graph_cache_clear(ctx);
   ctx->inner_gs_passes = passes;
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_set_probe_depth(lqcd_ctx *ctx, int depth) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (depth < 0 || depth > 64) return set_err(ctx, LQCD_ERR_INVALID_ARG, "set_probe_depth: depth must be in 0..64");
+  ctx->probe_depth = depth;
   return LQCD_OK;
 }
 

@@ -326,6 +326,116 @@ __global__ void probe_contract_kernel(const double2 *__restrict__ U, double kapp
   }
 }
 
+// Local completion of a probe field (meet-in-the-middle hopping traces).  The contraction of order
+// k reads P^k z only at the members of the probe's class and at their eight neighbours, and
+// (P^k z)(y) needs P^(k-1) z only at the neighbours of y.  So once P^h z is known everywhere, the
+// orders k > h are needed only in the taxicab balls of radius K - k around the members: this
+// kernel evaluates (P z)(y) for every y = member + offset (offsets: the ball, as char4 (dx, dy, dz,
+// dt)), reading `in` at the neighbours of y and writing `out` at y alone.  Sites outside the balls
+// keep whatever `out` held; the next order and the contraction never read them.  Two offsets of
+// one ball may name one site on a small torus: both threads then write the same value.
+// One thread per (member, offset) pair and probe (blockIdx.y).
+__global__ void __launch_bounds__(128) hop_listed_kernel(const double2 *__restrict__ U, const double2 *__restrict__ in,
+                                                         double2 *__restrict__ out, const char4 *__restrict__ offs,
+                                                         int noff, int first, int nprobe, int Lx, int Ly, int Lz,
+                                                         int Lt, Colouring col) {
+  const int p = blockIdx.y;
+  if (p >= nprobe) return;
+  const int Nx = Lx / col.s[0], Ny = Ly / col.s[1], Nz = Lz / col.s[2], Nt = Lt / col.s[3];
+  const long long nmem = (long long)Nx * Ny * Nz * (Nt / col.q);
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nmem * noff) return;
+  const int o = (int)(i % noff);
+  long long mi = i / noff;
+  const int cls = (first + p) / 12;
+  const int par = cls % col.q;
+  int b = cls / col.q;
+  const int rx = b % col.s[0];
+  b /= col.s[0];
+  const int ry = b % col.s[1];
+  b /= col.s[1];
+  const int rz = b % col.s[2];
+  const int rt = b / col.s[2];
+  const int nx = (int)(mi % Nx);
+  mi /= Nx;
+  const int ny = (int)(mi % Ny);
+  mi /= Ny;
+  const int nz = (int)(mi % Nz);
+  const int m = (int)(mi / Nz);
+  // the member's sublattice coordinates satisfy nx + ny + nz + nt = par (mod q)
+  const int nt = col.q * m + (((par - nx - ny - nz) % col.q) + col.q) % col.q;
+  const char4 d = offs[o];
+  const int x = ((rx + col.s[0] * nx + d.x) % Lx + Lx) % Lx;
+  const int y = ((ry + col.s[1] * ny + d.y) % Ly + Ly) % Ly;
+  const int z = ((rz + col.s[2] * nz + d.z) % Lz + Lz) % Lz;
+  const int t = ((rt + col.s[3] * nt + d.w) % Lt + Lt) % Lt;
+  const long long V = (long long)Lx * Ly * Lz * Lt;
+  const int s = x + Lx * (y + Ly * (z + Lz * t));
+  const int xp = (x + 1) % Lx + Lx * (y + Ly * (z + Lz * t)), xm = (x + Lx - 1) % Lx + Lx * (y + Ly * (z + Lz * t));
+  const int yp = x + Lx * ((y + 1) % Ly + Ly * (z + Lz * t)), ym = x + Lx * ((y + Ly - 1) % Ly + Ly * (z + Lz * t));
+  const int zp = x + Lx * (y + Ly * ((z + 1) % Lz + Lz * t)), zm = x + Lx * (y + Ly * ((z + Lz - 1) % Lz + Lz * t));
+  const int tp = x + Lx * (y + Ly * (z + Lz * ((t + 1) % Lt))), tm = x + Lx * (y + Ly * (z + Lz * ((t + Lt - 1) % Lt)));
+  const double2 *src = in + (long long)p * V * 12;
+  Cx<double> acc[4][3], q[4][3], u[9];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[a][c] = mk<double>(0.0, 0.0);
+  load_spinor<double, false>(src + 12LL * xp, q); load_link<double>(U, 0 * V + s, u);  term_fwd<double, 0>(q, u, acc);
+  load_spinor<double, false>(src + 12LL * xm, q); load_link<double>(U, 0 * V + xm, u); term_bwd<double, 0>(q, u, acc);
+  load_spinor<double, false>(src + 12LL * yp, q); load_link<double>(U, 1 * V + s, u);  term_fwd<double, 1>(q, u, acc);
+  load_spinor<double, false>(src + 12LL * ym, q); load_link<double>(U, 1 * V + ym, u); term_bwd<double, 1>(q, u, acc);
+  load_spinor<double, false>(src + 12LL * zp, q); load_link<double>(U, 2 * V + s, u);  term_fwd<double, 2>(q, u, acc);
+  load_spinor<double, false>(src + 12LL * zm, q); load_link<double>(U, 2 * V + zm, u); term_bwd<double, 2>(q, u, acc);
+  load_spinor<double, false>(src + 12LL * tp, q); load_link<double>(U, 3 * V + s, u);  term_fwd<double, 3>(q, u, acc);
+  load_spinor<double, false>(src + 12LL * tm, q); load_link<double>(U, 3 * V + tm, u); term_bwd<double, 3>(q, u, acc);
+  double2 *dst = out + (long long)p * V * 12 + 12LL * s;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) store_c(dst + 3 * a + c, acc[a][c]);
+}
+
+// Taxicab ball of radius r in Z^4 (all offsets with |dx| + |dy| + |dz| + |dt| <= r).
+static std::vector<char4> taxicab_ball(int r) {
+  std::vector<char4> o;
+  for (int dt = -r; dt <= r; ++dt)
+    for (int dz = -r; dz <= r; ++dz)
+      for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx)
+          if (std::abs(dx) + std::abs(dy) + std::abs(dz) + std::abs(dt) <= r)
+            o.push_back(make_char4((signed char)dx, (signed char)dy, (signed char)dz, (signed char)dt));
+  return o;
+}
+
+// Radius of the neighbourhood in which order k of a K-term trace is still read: the contraction
+// reads offsets 0 and +-mu (radius 1), and each further order widens it by one hop.
+static inline int completion_radius(int K, int k) { return std::max(1, K - k); }
+static constexpr int PROBE_MAX_RADIUS = 8;
+
+// Full-lattice applications of P per probe for the hopping traces: every order k <= depth is a
+// full application, every order above it a local completion (hop_listed_kernel).  Chosen to
+// minimise the site updates per probe, depth + sum_{k > depth} min(1, members x |ball| / V), unless
+// the context fixes it (lqcd_set_probe_depth).
+static int probe_depth(const lqcd_ctx *ctx, const Colouring &col, int K) {
+  if (K <= 2) return K - 1;
+  // a fixed depth still keeps every completion ball within PROBE_MAX_RADIUS
+  if (ctx->probe_depth > 0) return std::min(std::max(ctx->probe_depth, K - 1 - PROBE_MAX_RADIUS), K - 1);
+  const double per_member = (double)col.ncls;  // sites per class member
+  int best = K - 1;
+  double best_cost = (double)(K - 1);
+  for (int h = 1; h < K - 1; ++h) {
+    if (completion_radius(K, h + 1) > PROBE_MAX_RADIUS) continue;
+    double cost = h;
+    for (int k = h + 1; k < K; ++k) cost += std::min(1.0, (double)taxicab_ball(completion_radius(K, k)).size() / per_member);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = h;
+    }
+  }
+  return best;
+}
+
 template <typename T>
 lqcd_status download_v(lqcd_ctx *ctx, const void *dev, std::vector<T> &h, size_t count) {
   h.resize(count);
@@ -543,6 +653,25 @@ static lqcd_status hop_traces_dev(lqcd_ctx *ctx, const double2 *U, double kappa,
   LQCD_TRY(ws_get(ctx, WS_TMP3, sizeof(double2) * (size_t)B * N, (void **)&W1));
   LQCD_TRY(ws_get(ctx, WS_EST0, sizeof(double2) * (size_t)K * B * 9 * Lt, (void **)&cd_dev));
   tr.assign((size_t)K * 9 * Lt, cd(0.0, 0.0));
+  // meet in the middle: full applications up to `depth`, local completion above it; the offsets of
+  // every completion ball, concatenated (ball_at[r] = first offset of radius r)
+  const int depth = probe_depth(ctx, col, K);
+  const long long nmem = ctx->V / col.ncls;
+  std::vector<char4> all_offs;
+  std::vector<int> ball_at(PROBE_MAX_RADIUS + 1, 0), ball_n(PROBE_MAX_RADIUS + 1, 0);
+  for (int r = 1; r <= std::min(PROBE_MAX_RADIUS, K); ++r) {
+    const std::vector<char4> b = taxicab_ball(r);
+    ball_at[r] = (int)all_offs.size();
+    ball_n[r] = (int)b.size();
+    all_offs.insert(all_offs.end(), b.begin(), b.end());
+  }
+  char4 *offs = nullptr;
+  if (depth < K - 1) {
+    LQCD_TRY(ws_get(ctx, WS_PROBE_OFF, sizeof(char4) * all_offs.size(), (void **)&offs));
+    LQCD_CUDA(ctx, cudaMemcpyAsync(offs, all_offs.data(), sizeof(char4) * all_offs.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    LQCD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   std::vector<double2> h;
   // one thread per (operator, timeslice), at most what the kernel's register use allows per block
   // (the kernel strides over the rest)
@@ -557,8 +686,22 @@ static lqcd_status hop_traces_dev(lqcd_ctx *ctx, const double2 *U, double kappa,
     const double2 *cur = Z;
     for (int k = 0; k < K; ++k) {
       double2 *nxt = (k & 1) ? W0 : W1;
-      if (k > 0) LQCD_TRY(wilson_launch(ctx, U, kappa, cur, nxt, nb, LQCD_PREC_F64, LQCD_APPLY_HOP));
-      else nxt = Z;
+      if (k > 0 && k <= depth) {
+        LQCD_TRY(wilson_launch(ctx, U, kappa, cur, nxt, nb, LQCD_PREC_F64, LQCD_APPLY_HOP));
+      } else if (k > depth) {
+        const int r = completion_radius(K, k);
+        const long long work = nmem * (long long)ball_n[r];
+        if (work >= ctx->V) {
+          LQCD_TRY(wilson_launch(ctx, U, kappa, cur, nxt, nb, LQCD_PREC_F64, LQCD_APPLY_HOP));
+        } else {
+          kbegin(ctx);
+          hop_listed_kernel<<<dim3((unsigned)ceil_div(work, 128), nb), 128, 0, ctx->stream>>>(
+              U, cur, nxt, offs + ball_at[r], ball_n[r], (int)p0, nb, d[0], d[1], d[2], d[3], col);
+          LQCD_TRY(launch_check(ctx, "hop_listed_kernel", K_PROBE, (double)work * nb));
+        }
+      } else {
+        nxt = Z;
+      }
       kbegin(ctx);
       probe_contract_kernel<<<nb, cthreads, 0, ctx->stream>>>(U, kappa, nxt, (int)p0, nb, d[0], d[1], d[2], d[3], col,
                                                                cd_dev + (size_t)k * nb * 9 * Lt);

@@ -150,6 +150,7 @@ def load(path=None):
         "lqcd_set_graphs": [vp, i],
         "lqcd_set_rhs_per_thread": [vp, i],
         "lqcd_set_inner_gs_passes": [vp, i],
+        "lqcd_set_probe_depth": [vp, i],
         "lqcd_ctx_create_evenodd": [C.POINTER(vp), C.POINTER(C.c_int), i, vp],
         "lqcd_eo_split": [vp, vp, vp, vp, i],
         "lqcd_eo_join": [vp, vp, vp, vp, i],
@@ -642,6 +643,10 @@ class Context:
 
     def set_graphs(self, enable):
         self._check(self.lib.lqcd_set_graphs(self.h, 1 if enable else 0))
+
+    def set_probe_depth(self, depth):
+        """lqcd_set_probe_depth: full applications of P per probe in the hopping traces (0 = by cost)."""
+        self._check(self.lib.lqcd_set_probe_depth(self.h, depth))
 
     def set_inner_gs_passes(self, passes):
         """lqcd_set_inner_gs_passes: Gram-Schmidt passes (0 = by storage, 1 or 2) of mixed-precision

@@ -189,9 +189,13 @@ def test_hop_traces_small(dims, K):
     ctx = context(dims)
     U = synth.su3_links(dims, 0.5, 11)
     kappa = 0.13
-    got = ctx.hop_traces(dev(U), kappa, K)
     ref = O.per_t(S.hop_traces(U, kappa, K, dims))          # [k, op, t]
-    assert rel_err(got, ref) < 1e-13
+    # meet in the middle: full applications up to the depth, local completion of the orders above
+    # it (0 = depth by cost, K - 1 = every order a full application)
+    for depth in sorted({0, 1, 2, max(1, K - 1)}):
+        ctx.set_probe_depth(depth)
+        got = ctx.hop_traces(dev(U), kappa, K)
+        assert rel_err(got, ref) < 1e-13, depth
 
 
 def test_hop_traces_full_size_properties():
@@ -211,3 +215,9 @@ def test_hop_traces_full_size_properties():
     for k in (0, 2, 4, 6):
         assert np.abs(t[k, 5:9]).max() < 1e-12 * scale
     assert abs(t[4, 0]) > 1.0 and abs(t[6, 0]) > 1.0
+    # the meet-in-the-middle default (2 full applications, orders 3..6 completed within 4..1 hops
+    # of the 16 members of each of the 512 classes) against every order applied in full
+    ctx.set_probe_depth(K - 1)
+    t_full = ctx.hop_traces(dev(synth.su3_links(dims, 0.437, 2)), kappa, K).sum(axis=-1)
+    assert rel_err(t, t_full) < 1e-13
+    ctx.set_probe_depth(0)

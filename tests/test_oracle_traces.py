@@ -131,3 +131,30 @@ def test_exact_trace_symmetries():
         gfwd = np.roll(g, -1, axis=L.SITE_AXIS[mu])
         Ug[mu] = g @ U[mu] @ np.conj(np.swapaxes(gfwd, -1, -2))
     assert np.allclose(exact.exact_traces(Ug, kappa, dims), tr, atol=1e-11)
+
+
+@pytest.mark.parametrize("dims,K", [((4, 2, 2, 4), 5), ((8, 2, 2, 2), 3), ((10, 2, 3, 2), 4), ((2, 2, 2, 2), 7)])
+def test_meet_in_the_middle_traces_equal_probing(dims, K):
+    """The meet-in-the-middle form (local operators from two half-depth probe blocks joined by
+    gamma_5-hermiticity, point-split operators completed only near the class members) gives the
+    per-site densities of full-depth probing, including classes with several members ((8,2,2,2),
+    (10,2,3,2)), odd extents and windings (2^4, K = 7)."""
+    U = synth.su3_links(dims, 0.6, 21)
+    kappa = 0.14
+    ref = S.hop_traces(U, kappa, K, dims)
+    got = S.hop_traces_meet(U, kappa, K, dims)
+    assert np.abs(got - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_meet_in_the_middle_needs_its_completion_radius():
+    """Cutting the completed orders one hop closer to the members than max(1, K - k) changes the
+    point-split traces: the radius is the smallest that keeps them exact (odd extents, so that the
+    even point-split orders, which the cut reaches, do not vanish)."""
+    dims, K = (3, 2, 2, 3), 5
+    U = synth.su3_links(dims, 0.6, 22)
+    kappa = 0.14
+    ref = S.hop_traces(U, kappa, K, dims).sum(axis=(-1, -2, -3, -4))
+    cut = S.hop_traces_meet(U, kappa, K, dims, completion_radius=lambda K_, k: max(1, K_ - k) - 1)
+    cut = cut.sum(axis=(-1, -2, -3, -4))
+    assert np.abs(cut[:, 5:] - ref[:, 5:]).max() > 1e-3
+    assert np.abs(cut[:, :5] - ref[:, :5]).max() < 1e-11 * np.abs(ref).max()
