@@ -507,6 +507,9 @@ lqcd_status lqcd_loop_noises(lqcd_loop *loop, const double *links, uint32_t firs
 /* Solver precision of the noise phase from now on (prec, inner_tol as in lqcd_est_opts; the setup
  * itself is FP64 whatever the precision), and its block width (0 keeps the current one). */
 lqcd_status lqcd_loop_set_noise_opts(lqcd_loop *loop, int prec, double inner_tol, int block);
+/* Cycle length of the noise solves' GMRES-Proj from now on (as lqcd_est_opts.m_inner: 0 = m - k).
+ * LQCD_ERR_INVALID_ARG outside 0..1024. */
+lqcd_status lqcd_loop_set_inner_restart(lqcd_loop *loop, int m_inner);
 /* Outputs of a setup (host), see lqcd_loop_info. */
 lqcd_status lqcd_loop_get(const lqcd_loop *loop, lqcd_loop_info *out);
 lqcd_status lqcd_loop_destroy(lqcd_loop *loop);
@@ -541,6 +544,16 @@ lqcd_status lqcd_set_graphs(lqcd_ctx *ctx, int enable);
  * per noise, 1.4 x faster).  FP64 Krylov solves always use two passes.  LQCD_ERR_INVALID_ARG for
  * other values. */
 lqcd_status lqcd_set_inner_gs_passes(lqcd_ctx *ctx, int passes);
+
+/* Lanczos window of the inner GMRES-Proj cycles of mixed-precision solves on the Hermitian operator
+ * M' = M gamma_5 (the Hermitian path; other operators ignore it): window w >= 2 orthogonalises each
+ * new basis vector only against the last w vectors.  For a Hermitian operator the Arnoldi
+ * recurrence is the three-term Lanczos one (MINRES-DR on M', Sec. 8), so w = 2 drops only inner
+ * products that vanish in exact arithmetic; the Arnoldi relation A V_m = V_{m+1} Hbar_m still holds
+ * by construction, the cycle's least-squares step becomes quasi-minimal where the reduced-precision
+ * basis loses orthogonality, and the outer FP64 defect correction still stops on the FP64 true
+ * residual.  0 = every vector (default).  LQCD_ERR_INVALID_ARG for 1 or values above 1024. */
+lqcd_status lqcd_set_inner_window(lqcd_ctx *ctx, int window);
 
 /* Loop estimates of n independent problems (lattices of any, uneven, sizes), run concurrently: each
  * context (all distinct) works on its own private stream from its own host thread, ordered after

@@ -75,6 +75,7 @@ struct lqcd_ctx {
   int tc_stop_after;         // injected stall of the next tensor-core launch (-1: none)
   int inner_gs_passes;       // Gram-Schmidt passes of the reduced-precision inner Arnoldi (0 = by storage)
   int probe_depth;           // full applications of P per probe in the hopping traces (0 = by cost)
+  int inner_window;          // Lanczos window of Hermitian mixed-precision inner cycles (0 = full Gram-Schmidt)
   // even/odd reduced context (lqcd_ctx_create_evenodd): fields hold the even sites only (V above is
   // half the lattice), the operator is hat M = 1 - kappa^2 P_eo P_oe, eo_dims the full extents
   int eo;

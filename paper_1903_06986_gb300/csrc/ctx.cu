@@ -220,6 +220,7 @@ lqcd_status lqcd_ctx_create(lqcd_ctx **out, const int dims[4], int link_recon, v
   c->tc_stop_after = -1;
   c->inner_gs_passes = 0;
   c->probe_depth = 0;
+  c->inner_window = 0;
   c->eo = 0;
   for (int i = 0; i < 4; ++i) c->eo_dims[i] = dims[i];
   c->cap_stream = nullptr;
@@ -270,6 +271,15 @@ lqcd_status lqcd_set_inner_gs_passes(lqcd_ctx *ctx, int passes) {
   if (passes < 0 || passes > 2) return set_err(ctx, LQCD_ERR_INVALID_ARG, "set_inner_gs_passes: passes must be 0, 1 or 2");
   if (passes != ctx->inner_gs_passes) graph_cache_clear(ctx);
   ctx->inner_gs_passes = passes;
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_set_inner_window(lqcd_ctx *ctx, int window) {
+  if (!ctx) return LQCD_ERR_INVALID_ARG;
+  if (window != 0 && (window < 2 || window > 1024))
+    return set_err(ctx, LQCD_ERR_INVALID_ARG, "set_inner_window: window must be 0 or in 2..1024");
+  if (window != ctx->inner_window) graph_cache_clear(ctx);
+  ctx->inner_window = window;
   return LQCD_OK;
 }
 

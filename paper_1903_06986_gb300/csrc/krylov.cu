@@ -209,7 +209,15 @@ template <typename S> struct ArnoldiT {
   double2 *hd1, *hd2;  // [j][i][r] device, (m) x (m+1) x nrhs
   double *nrm;         // [j][r]
   int passes = 2;      // Gram-Schmidt passes per step: 2 (CGS2), or 1 (CGS) for reduced-precision bases
+  int window = 0;      // > 0 (Hermitian operators only): orthogonalise against the last `window` vectors
 };
+
+// First basis vector step j is orthogonalised against: all of them, or the last a.window (for a
+// Hermitian operator the Arnoldi recurrence is the three-term Lanczos one, h_ij = 0 for i < j - 1,
+// so a window of 2 drops only terms that vanish in exact arithmetic)
+template <typename S> inline int gs_first(const ArnoldiT<S> &a, int j) {
+  return a.window > 0 ? std::max(0, j + 1 - a.window) : 0;
+}
 using Arnoldi = ArnoldiT<double2>;
 
 // The launches of Arnoldi steps j0..m-1 (CGS2: two passes of inner products and updates, or one
@@ -230,11 +238,13 @@ lqcd_status arnoldi_enqueue(void *arg) {
     LQCD_TRY(a.op.apply(ctx, vj, w, a.nrhs));
     double2 *h1 = a.hd1 + (long long)j * (a.m + 1) * a.nrhs;
     double2 *h2 = a.hd2 + (long long)j * (a.m + 1) * a.nrhs;
-    LQCD_TRY(blas_multidot(ctx, a.Vb, vs, N, j + 1, w, N, a.nrhs, h1));
-    LQCD_TRY(blas_multiaxpy(ctx, a.Vb, vs, N, j + 1, h1, -1.0, w, N, a.nrhs));
+    const int lo = gs_first(a, j);
+    const S *vlo = a.Vb + lo * vs;
+    LQCD_TRY(blas_multidot(ctx, vlo, vs, N, j + 1 - lo, w, N, a.nrhs, h1 + (long long)lo * a.nrhs));
+    LQCD_TRY(blas_multiaxpy(ctx, vlo, vs, N, j + 1 - lo, h1 + (long long)lo * a.nrhs, -1.0, w, N, a.nrhs));
     if (a.passes > 1) {
-      LQCD_TRY(blas_multidot(ctx, a.Vb, vs, N, j + 1, w, N, a.nrhs, h2));
-      LQCD_TRY(blas_multiaxpy(ctx, a.Vb, vs, N, j + 1, h2, -1.0, w, N, a.nrhs));
+      LQCD_TRY(blas_multidot(ctx, vlo, vs, N, j + 1 - lo, w, N, a.nrhs, h2 + (long long)lo * a.nrhs));
+      LQCD_TRY(blas_multiaxpy(ctx, vlo, vs, N, j + 1 - lo, h2 + (long long)lo * a.nrhs, -1.0, w, N, a.nrhs));
     }
     LQCD_TRY(blas_norms(ctx, w, N, a.nrhs, a.nrm + (long long)j * a.nrhs));
     LQCD_TRY(blas_invscale(ctx, w, a.nrm + (long long)j * a.nrhs, N, a.nrhs));
@@ -261,6 +271,7 @@ lqcd_status arnoldi_launch(ArnoldiT<S> &a, int j0) {
   key_add(key, a.nrm);
   key_add(key, j0);
   key_add(key, a.passes);
+  key_add(key, a.window);
   key_add(key, a.ctx->packed_nr);
   ArnoldiLaunch<S> arg{&a, j0};
   return graph_cached(a.ctx, key, &arnoldi_enqueue<S>, &arg);
@@ -286,7 +297,9 @@ lqcd_status arnoldi_run(ArnoldiT<S> &a, int j0, std::vector<Rhs> &R, long long &
   for (int r = 0; r < a.nrhs; ++r) {
     if (!R[r].active) continue;
     for (int j = j0; j < a.m; ++j) {
-      for (int i = 0; i <= j; ++i) {
+      const int lo = gs_first(a, j);
+      for (int i = 0; i < lo; ++i) R[r].H(i, j) = cd(0.0, 0.0);
+      for (int i = lo; i <= j; ++i) {
         const double2 x1 = h1[((size_t)j * (a.m + 1) + i) * a.nrhs + r];
         const double2 x2 = h2[((size_t)j * (a.m + 1) + i) * a.nrhs + r];
         R[r].H(i, j) = cd(x1.x + x2.x, x1.y + x2.y);
@@ -726,7 +739,8 @@ struct ProjResult {
 // projection multiplies by 1 / lambda and would amplify a coarser rounding of it).
 template <typename S, typename SX = S, typename SD = S>
 lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const SD *Vd, const Mat &Hk, const dense::QRFact &Hq, const SX *b,
-                     SX *x, int nrhs, int m, double tol, int max_cycles, bool check_true, ProjResult &res) {
+                     SX *x, int nrhs, int m, double tol, int max_cycles, bool check_true, ProjResult &res,
+                     int window = 0) {
   const int k = Hk.c;
   const long long N = ctx->N, vs = (long long)nrhs * N;
   WorkspaceT<S> W;
@@ -752,6 +766,7 @@ lqcd_status proj_run(lqcd_ctx *ctx, const OpT<S> &op, const SD *Vd, const Mat &H
   // reduced-precision inner cycles: one pass for FP16 / BF16 bases (4-byte complex), two for FP32,
   // unless the context sets it
   if (!std::is_same<S, double2>::value) A.passes = ctx->inner_gs_passes ? ctx->inner_gs_passes : (sizeof(S) == 4 ? 1 : 2);
+  A.window = window;
   long long matvecs = 0;
   int cycles = 0;
   bool all_conv = false;
@@ -970,6 +985,9 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
   if (op.pp.degree > 0) LQCD_TRY(ws_get(ctx, WS_POLY3, sizeof(float2) * (size_t)vs, (void **)&e32p));
   const Mat Hk = defl_hbar(defl);
   const dense::QRFact &Hq = defl_qr(defl);
+  // Lanczos window of the inner cycles: only for the Hermitian operator M' = M gamma_5 (times a
+  // polynomial with real coefficients)
+  const int window = op.flags == LQCD_APPLY_G5R ? ctx->inner_window : 0;
   LQCD_TRY(blas_zero(ctx, x, vs));
   LQCD_TRY(blas_copy(ctx, b, r, vs));
   LQCD_TRY(blas_norms(ctx, b, N, nrhs, sc));
@@ -1000,7 +1018,7 @@ lqcd_status mixed_core(lqcd_ctx *ctx, const Op &op, const lqcd_defl *defl, const
     LQCD_TRY(pack_f32(ctx, r, sc, (float4 *)r32, nrhs));
     ProjResult pr;
     LQCD_TRY((proj_run<S, float2, float2>(ctx, opl, Vlp, Hk, Hq, r32, e32, nrhs, o->m, inner_tol,
-                                  std::max(1, o->max_cycles - inner_cycles), false, pr)));
+                                  std::max(1, o->max_cycles - inner_cycles), false, pr, window)));
     inner_cycles += pr.cycles;
     matvecs += pr.matvecs;
     if (op.pp.degree > 0) LQCD_TRY(opf.apply_poly(ctx, e32, e32p, nrhs));   // e = p(A) e'

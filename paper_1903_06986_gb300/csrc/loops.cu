@@ -1443,6 +1443,13 @@ lqcd_status lqcd_loop_set_noise_opts(lqcd_loop *L, int prec, double inner_tol, i
   return LQCD_OK;
 }
 
+lqcd_status lqcd_loop_set_inner_restart(lqcd_loop *L, int m_inner) {
+  if (!L || !L->ctx) return LQCD_ERR_INVALID_ARG;
+  if (m_inner < 0 || m_inner > 1024) return set_err(L->ctx, LQCD_ERR_INVALID_ARG, "loop_set_inner_restart: m_inner must be in 0..1024");
+  L->o.m_inner = m_inner;
+  return LQCD_OK;
+}
+
 lqcd_status lqcd_loop_get(const lqcd_loop *L, lqcd_loop_info *out) {
   if (!L || !out) return LQCD_ERR_INVALID_ARG;
   const size_t Lt = L->ctx->dims[3];

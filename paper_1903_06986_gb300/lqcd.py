@@ -130,6 +130,7 @@ def load(path=None):
         "lqcd_loop_noises": [vp, vp, u32, i, vp, C.POINTER(NoiseInfo)],
         "lqcd_loop_get": [vp, C.POINTER(LoopInfo)],
         "lqcd_loop_set_noise_opts": [vp, i, d, i],
+        "lqcd_loop_set_inner_restart": [vp, i],
         "lqcd_loop_destroy": [vp],
         "lqcd_deflate_project": [vp, vp, vp, vp, i, vp],
         "lqcd_set_defl_engine": [vp, i],
@@ -151,6 +152,7 @@ def load(path=None):
         "lqcd_set_rhs_per_thread": [vp, i],
         "lqcd_set_inner_gs_passes": [vp, i],
         "lqcd_set_probe_depth": [vp, i],
+        "lqcd_set_inner_window": [vp, i],
         "lqcd_ctx_create_evenodd": [C.POINTER(vp), C.POINTER(C.c_int), i, vp],
         "lqcd_eo_split": [vp, vp, vp, vp, i],
         "lqcd_eo_join": [vp, vp, vp, vp, i],
@@ -282,6 +284,10 @@ class Loop:
     def set_noise_opts(self, prec, inner_tol=0.0, block=0):
         """Precision (and block width, 0 = unchanged) of the noise solves from now on."""
         self.ctx._check(self.ctx.lib.lqcd_loop_set_noise_opts(self.h, prec, inner_tol, block))
+
+    def set_inner_restart(self, m_inner):
+        """GMRES-Proj cycle length of the noise solves from now on (0 = m - k)."""
+        self.ctx._check(self.ctx.lib.lqcd_loop_set_inner_restart(self.h, m_inner))
 
     def info(self):
         lt = self.ctx.dims[3]
@@ -643,6 +649,10 @@ class Context:
 
     def set_graphs(self, enable):
         self._check(self.lib.lqcd_set_graphs(self.h, 1 if enable else 0))
+
+    def set_inner_window(self, window):
+        """lqcd_set_inner_window: Lanczos window of Hermitian mixed-precision inner cycles (0 = full)."""
+        self._check(self.lib.lqcd_set_inner_window(self.h, window))
 
     def set_probe_depth(self, depth):
         """lqcd_set_probe_depth: full applications of P per probe in the hopping traces (0 = by cost)."""

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import krylov as Kr, lattice as L, rng
-from paper_1903_06986_gb300 import synth
+from paper_1903_06986_gb300 import lqcd, synth
 from tests.gpu_util import context, dev, host, rel_err
 
 pytestmark = pytest.mark.gpu
@@ -120,6 +120,46 @@ def test_mixed_precision_proj_reaches_fp64_tolerance(setup, prec):
         xe = np.linalg.solve(s["M"], b)
         assert np.linalg.norm(xm - xe) <= 10 * s["cond"] * tol * np.linalg.norm(xe)
         assert np.linalg.norm(xm - L.flat(host(x64)[r])) <= 20 * s["cond"] * tol * np.linalg.norm(xe)
+
+
+@pytest.mark.parametrize("prec", [lqcd.PREC_F16, lqcd.PREC_BF16, lqcd.PREC_F32], ids=["f16", "bf16", "f32"])
+def test_lanczos_window_inner_cycles_on_hermitian_operator(setup, prec):
+    """Mixed-precision GMRES-Proj on M' = M gamma_5 (the Hermitian path) with the inner cycles
+    orthogonalising each vector against the last two only (the Lanczos recurrence of MINRES-DR,
+    Sec. 8): the FP64 true residual (dense oracle matrix) meets 1e-10, and the solution agrees with
+    the dense solve and with full Gram-Schmidt within cond * tol."""
+    s = setup
+    ctx = s["ctx"]
+    _, _, defl = ctx.minresdr_solve(s["Ud"], KAPPA, dev(L.unflat(s["b"], DIMS)), 40, 12, 1e-12, 500, want_defl=True)
+    Mp = L.dense(lambda f: L.wilson_g5(s["U"], KAPPA, f), DIMS)
+    cond = np.linalg.cond(Mp)
+    etas = rng.z4_block(3, 0, 4, DIMS)
+    tol = 1e-10
+    ctx.set_inner_window(0)
+    x_full, info_full = ctx.proj_solve(s["Ud"], KAPPA, defl, dev(etas), 30, tol, 500, prec=prec)
+    ctx.set_inner_window(2)
+    try:
+        x, info = ctx.proj_solve(s["Ud"], KAPPA, defl, dev(etas), 30, tol, 500, prec=prec)
+    finally:
+        ctx.set_inner_window(0)
+    assert info["converged"] and info["true_resid"] <= tol
+    assert info_full["converged"]
+    for r in range(4):
+        b = L.flat(etas[r])
+        xm = L.flat(host(x)[r])
+        assert np.linalg.norm(Mp @ xm - b) <= tol * np.linalg.norm(b) * 1.0001
+        xe = np.linalg.solve(Mp, b)
+        assert np.linalg.norm(xm - xe) <= 10 * cond * tol * np.linalg.norm(xe)
+        assert np.linalg.norm(xm - L.flat(host(x_full)[r])) <= 20 * cond * tol * np.linalg.norm(xe)
+
+
+def test_lanczos_window_rejects_bad_values(setup):
+    ctx = setup["ctx"]
+    with pytest.raises(Exception):
+        ctx.set_inner_window(1)
+    with pytest.raises(Exception):
+        ctx.set_inner_window(-3)
+    ctx.set_inner_window(0)
 
 
 @pytest.mark.parametrize("hermitian", [False, True], ids=["gmresdr", "minresdr"])
