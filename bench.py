@@ -6,7 +6,7 @@ Headline workload (the largest single-GPU configuration of the method): 24^3 x 3
 plaquette of 0.600 (eps = 0.4323, seed 7; recon-12 link storage in the inner operator),
 kappa = 0.157, 100 Z(4) noises, Q = 200 deflation eigenvectors of M' = M gamma_5 from one
 MINRES-DR(240,200) super-convergence solve (the Hermitian path: the same space accelerates every
-noise solve, M' y = eta by GMRES-Proj(40), x = gamma_5 y), 7-term PS and degree-6 POLY, all six
+noise solve, M' y = eta by GMRES-Proj, x = gamma_5 y), 7-term PS and degree-6 POLY, all six
 subtraction modes x nine operators, HFES projections on the tcgen05 tensor cores (split-precision
 FP64).  Noise solves: FP16 storage of the inner Krylov basis with FP32 arithmetic inside an FP64
 defect-correction loop that stops on the FP64 true residual <= 1e-10 (BF16 and plain FP64 are
@@ -39,13 +39,16 @@ KAPPA = 0.157
 LINK_EPS, LINK_SEED, NOISE_SEED = 0.4323, 7, 1
 NNOISE, BLOCK = 100, 10
 M_DR, K_DR, M_INNER = 240, 200, 40
+HEAD_M_INNER = 80         # GMRES-Proj cycle length of the headline's FP16 / BF16 noise solves
+INNER_WINDOW = 2          # Lanczos window of their inner cycles (M' is Hermitian)
 INNER_TOL = 0.1            # inner (FP16 / BF16) GMRES-Proj stopping point inside the FP64 defect correction
 K_PS, NPOLY = 7, 6
 TOL, TOL_SPECIAL = 1e-10, 1e-12
 MAX_CYCLES = 400
 PREC_DEGREE = 0            # polynomial preconditioning of the noise solves (Krylov on M' p(M'))
 WORKLOAD = ("24^3x32 kappa 0.157 (plaquette 0.600), 100 Z4 noises in steps of 10, MINRES-DR(240,200) on M gamma_5, "
-            "Q=200, GMRES-Proj(40) noise solves in FP16 storage / FP32 arithmetic (one Gram-Schmidt pass, inner "
+            "Q=200, GMRES-Proj(80) noise solves in FP16 storage / FP32 arithmetic (Lanczos window 2 on the Hermitian "
+            "M', inner "
             "tol 0.1) inside FP64 defect correction to 1e-10, PS K=7, POLY n=6, HFES on tensor cores, 6 modes x 9 "
             "operators")
 # secondary: the 8^3 x 16 plain-FP64 workload (full loop estimate per step)
@@ -57,7 +60,10 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per algorithmic byte of a kernel class, from an ncu capture of the same
 # kernels on the 16^3 x 32 noise block (bench.py --case noise-block-f16)
 DRAM_PER_ALGORITHMIC = {"dot": (1.017, "ncu dram__bytes_read.sum + dram__bytes_write.sum over 224 launches of "
-                                       "multidot_kernel<__half2> on 16^3x32 / their algorithmic bytes")}
+                                       "multidot_kernel<__half2> on 16^3x32 / their algorithmic bytes"),
+                        "wilson": (0.952, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of "
+                                          "wilson_pair_kernel on FP16 fields, 24^3x32, 8 right-hand sides, recon 12 "
+                                          "(405.0 MB) / its algorithmic bytes (425 MB)")}
 # per-noise matrix-vector products of the plain FP64 noise solves on the headline workload (GPU
 # path; the oracle runs the same algorithm): used to extrapolate the oracle's bounded sample
 MATVECS_PER_NOISE_FP64 = 650
@@ -482,11 +488,13 @@ def run_case(args):
         return
     if args.case == "noise-block-f16":
         # the headline's noise phase on a smaller lattice (16^3 x 32, kappa 0.157, Hermitian path with a
-        # MINRES-DR(60,30) space): one block of 10 noises in FP16 storage; about 3 GB on the device
+        # MINRES-DR(60,30) space, GMRES-Proj(80) with the Lanczos window): one block of 10 noises in FP16
+        # storage; about 4 GB on the device
         dims = (16, 16, 16, 32)
         ctx = lqcd.Context(dims, recon=12)
+        ctx.set_inner_window(INNER_WINDOW)
         U = torch.from_numpy(synth.su3_links(dims, LINK_EPS, LINK_SEED)).cuda()
-        loop = ctx.loop_setup(U, KAPPA, NOISE_SEED, 10, 10, 60, 30, K_PS, NPOLY, TOL, TOL_SPECIAL, m_inner=M_INNER,
+        loop = ctx.loop_setup(U, KAPPA, NOISE_SEED, 10, 10, 60, 30, K_PS, NPOLY, TOL, TOL_SPECIAL, m_inner=HEAD_M_INNER,
                               max_cycles=MAX_CYCLES, prec=lqcd.PREC_F16, system=lqcd.SYS_MG5, inner_tol=INNER_TOL)
         torch.cuda.synchronize()
         setup_launches = ctx.launches
@@ -695,12 +703,13 @@ def main():
     ctx = lqcd.Context(DIMS, recon=12)        # the synthetic links are SU(3)
     Ud = torch.from_numpy(U).cuda()
     ctx.set_defl_engine(lqcd.DEFL_TENSOR)
+    ctx.set_inner_window(INNER_WINDOW)
 
     # ---- setup of the configuration, once (reported separately, amortised below)
     barrier()
     t0 = time.perf_counter()
     loop = ctx.loop_setup(Ud, KAPPA, NOISE_SEED, NNOISE, BLOCK, M_DR, K_DR, K_PS, NPOLY, TOL, TOL_SPECIAL,
-                          m_inner=M_INNER, max_cycles=MAX_CYCLES, prec=lqcd.PREC_F16, system=lqcd.SYS_MG5,
+                          m_inner=HEAD_M_INNER, max_cycles=MAX_CYCLES, prec=lqcd.PREC_F16, system=lqcd.SYS_MG5,
                           inner_tol=INNER_TOL,
                           prec_degree=args.prec_degree)
     barrier()
@@ -756,12 +765,15 @@ def main():
         step(1 + i, "bf16")
     barrier()
     t_bf16 = max_over_ranks(time.perf_counter() - b0)
+    # plain FP64 at its own measured cycle length (GMRES-Proj(40), two Gram-Schmidt passes)
     loop.set_noise_opts(lqcd.PREC_F64)
+    loop.set_inner_restart(M_INNER)
     barrier()
     f0 = time.perf_counter()
     step(0, "fp64")
     barrier()
     t_fp64 = max_over_ranks(time.perf_counter() - f0)
+    loop.set_inner_restart(HEAD_M_INNER)
     loop.set_noise_opts(lqcd.PREC_F16, INNER_TOL)
     est64 = _estimates(outputs[("fp64", 0)], add)
     lam_min = float(np.abs(info["lam"]).min())
@@ -861,7 +873,8 @@ def main():
                            "precision": "FP16 storage of the inner Krylov basis, FP32 arithmetic, FP64 outer "
                                         "true residual, FP64 setup; HFES projections split-precision FP64 on "
                                         "tensor cores",
-                           "inner_tol": INNER_TOL, "inner_gram_schmidt_passes": 1,
+                           "inner_tol": INNER_TOL, "inner_gram_schmidt_passes": 1, "inner_m": HEAD_M_INNER,
+                           "inner_lanczos_window": INNER_WINDOW,
                            "l2": "inputs larger than L2 (Krylov bases of 10 noises: GBs per step)",
                            "parallelism": "independent gauge configuration per rank" if world > 1 else "single GPU"},
                 "gpu_launches": launches,
