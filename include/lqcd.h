@@ -504,6 +504,12 @@ lqcd_status lqcd_loop_setup_from(lqcd_ctx *ctx, const double *links, double kapp
  * still written) when a noise solve stopped at max_cycles above tol. */
 lqcd_status lqcd_loop_noises(lqcd_loop *loop, const double *links, uint32_t first, int count, double *per_noise_t,
                              lqcd_noise_info *info);
+/* lqcd_loop_noises with the gauge field in host memory (links_host: 4 x V x 3 x 3 complex, the
+ * canonical layout; pinned memory makes the copy asynchronous): the call copies it to a device
+ * buffer of the context on the context's stream, then runs the noise phase on it.  The end-to-end
+ * form of a noise block for callers whose data lives on the host. */
+lqcd_status lqcd_loop_noises_host(lqcd_loop *loop, const double *links_host, uint32_t first, int count,
+                                  double *per_noise_t, lqcd_noise_info *info);
 /* Solver precision of the noise phase from now on (prec, inner_tol as in lqcd_est_opts; the setup
  * itself is FP64 whatever the precision), and its block width (0 keeps the current one). */
 lqcd_status lqcd_loop_set_noise_opts(lqcd_loop *loop, int prec, double inner_tol, int block);

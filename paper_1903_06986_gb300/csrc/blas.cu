@@ -68,35 +68,35 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
 }
 
 // conj(V_j[e]) w[e] summed into acc[j] over the elements e0 + t, e0 + t + BT, ... < e1 of this thread
-// (t = threadIdx.x), for the first g of the GROUP vectors (all of them when FULL)
-template <bool FULL, typename SV, typename SW, typename C>
+// (t = threadIdx.x), for the first g of the G vectors (all of them when FULL)
+template <bool FULL, int G, typename SV, typename SW, typename C>
 __device__ __forceinline__ void dot_range(const SV *const *vp, const SW *__restrict__ wr, long long e0, long long e1,
                                           int g, C *acc) {
   for (long long e = e0 + threadIdx.x; e < e1; e += BT) {
     const C wv = ldc(wr[e]);
 #pragma unroll
-    for (int j = 0; j < GROUP; ++j)
+    for (int j = 0; j < G; ++j)
       if (FULL || j < g) gfma_conj(acc[j], ldc(vp[j][e]), wv);
   }
 }
 // the same with one 16-byte load per vector and thread (KV = 16 / sizeof(SV) elements); e0 and the
 // vectors' offsets are multiples of KV elements, the remainder of the range goes element-wise
-template <bool FULL, typename SV, typename SW, typename C>
+template <bool FULL, int G, typename SV, typename SW, typename C>
 __device__ __forceinline__ void dot_range_vec(const SV *const *vp, const SW *__restrict__ wr, long long e0,
                                               long long e1, int g, C *acc) {
   constexpr int KV = 16 / sizeof(SV);
   const long long ev = e0 + (e1 - e0) / KV * KV;
   for (long long e = e0 + (long long)threadIdx.x * KV; e < ev; e += (long long)BT * KV) {
-    // all GROUP + 1 loads of this step issued before any use, so that they are in flight together
-    uint4 vraw[GROUP];
+    // all G + 1 loads of this step issued before any use, so that they are in flight together
+    uint4 vraw[G];
     const uint4 wraw = __ldg(reinterpret_cast<const uint4 *>(wr + e));
 #pragma unroll
-    for (int j = 0; j < GROUP; ++j)
+    for (int j = 0; j < G; ++j)
       if (FULL || j < g) vraw[j] = __ldg(reinterpret_cast<const uint4 *>(vp[j] + e));
     SW wv[KV];
     memcpy(wv, &wraw, 16);
 #pragma unroll
-    for (int j = 0; j < GROUP; ++j) {
+    for (int j = 0; j < G; ++j) {
       if (FULL || j < g) {
         SV vv[KV];
         memcpy(vv, &vraw[j], 16);
@@ -105,12 +105,12 @@ __device__ __forceinline__ void dot_range_vec(const SV *const *vp, const SW *__r
       }
     }
   }
-  dot_range<FULL>(vp, wr, ev, e1, g, acc);
+  dot_range<FULL, G>(vp, wr, ev, e1, g, acc);
 }
 
 // Single-launch batched inner products.  Block b (a 1-D grid) sums conj(V_i^r) w^r over element
-// chunk c for the GROUP basis vectors of group g and writes partial[(i * nrhs + r) * nchunk + c]:
-// with a basis shared by all right-hand sides b = g + ngroup (r + nrhs c), so that the groups and
+// chunk c for the G basis vectors of group g (G = GROUP, or 2 for the two-vector Lanczos steps) and
+// writes partial[(i * nrhs + r) * nchunk + c]: with a basis shared by all right-hand sides b = g + ngroup (r + nrhs c), so that the groups and
 // right-hand sides of one chunk are neighbours in launch order and the chunk of every basis vector
 // and of every w^r is read from DRAM once and then from L2; with a basis per right-hand side
 // b = c + nchunk (g + ngroup r), consecutive blocks streaming consecutive chunks.  The last of the
@@ -118,14 +118,14 @@ __device__ __forceinline__ void dot_range_vec(const SV *const *vp, const SW *__r
 // partials of every vector of the group in a fixed order (one warp per vector) and writes
 // h[i * nrhs + r]: the result does not depend on block scheduling, and the final sums of the groups
 // run in parallel.
-template <typename SV, typename SW, bool VEC>
+template <typename SV, typename SW, bool VEC, int G>
 __global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, long long vstride, long long vrs,
                                                       int nvec, const SW *__restrict__ w, long long n, int nrhs,
                                                       int nchunk, double fac, double2 *__restrict__ partial,
                                                       unsigned *__restrict__ counters, double2 *__restrict__ h) {
   using C = Ar<SW>;
   static_assert(std::is_same<C, Ar<SV>>::value, "multidot: storage types of different arithmetic");
-  const int ngroup = (nvec + GROUP - 1) / GROUP;
+  const int ngroup = (nvec + G - 1) / G;
   int g0, r, c;
   if (vrs == 0) {
     // shared basis: the groups and right-hand sides of one chunk are neighbours in launch order
@@ -138,36 +138,36 @@ __global__ void __launch_bounds__(BT) multidot_kernel(const SV *__restrict__ V, 
     g0 = (blockIdx.x / nchunk) % ngroup;
     r = blockIdx.x / (nchunk * ngroup);
   }
-  const int i0 = g0 * GROUP;
+  const int i0 = g0 * G;
   constexpr long long KV = VEC ? 16 / sizeof(SV) : 1;
   const long long chunk = ((n + nchunk - 1) / nchunk + KV - 1) / KV * KV;
   const long long e0 = min(n, c * chunk);
   const long long e1 = min(n, e0 + chunk);
   const SW *wr = w + r * n;
   const SV *vr = V + r * vrs;
-  __shared__ double2 red[BT / 32][GROUP];
+  __shared__ double2 red[BT / 32][G];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = min(GROUP, nvec - i0);
-  const SV *vp[GROUP];
+  const int g = min(G, nvec - i0);
+  const SV *vp[G];
 #pragma unroll
-  for (int j = 0; j < GROUP; ++j) vp[j] = vr + (long long)(i0 + min(j, g - 1)) * vstride;
-  C acc[GROUP];
+  for (int j = 0; j < G; ++j) vp[j] = vr + (long long)(i0 + min(j, g - 1)) * vstride;
+  C acc[G];
 #pragma unroll
-  for (int j = 0; j < GROUP; ++j) acc[j] = cz<C>();
+  for (int j = 0; j < G; ++j) acc[j] = cz<C>();
   if (VEC) {
-    if (g == GROUP)
-      dot_range_vec<true>(vp, wr, e0, e1, g, acc);
+    if (g == G)
+      dot_range_vec<true, G>(vp, wr, e0, e1, g, acc);
     else
-      dot_range_vec<false>(vp, wr, e0, e1, g, acc);
+      dot_range_vec<false, G>(vp, wr, e0, e1, g, acc);
   } else {
-    if (g == GROUP)
-      dot_range<true>(vp, wr, e0, e1, g, acc);
+    if (g == G)
+      dot_range<true, G>(vp, wr, e0, e1, g, acc);
     else
-      dot_range<false>(vp, wr, e0, e1, g, acc);
+      dot_range<false, G>(vp, wr, e0, e1, g, acc);
   }
 #pragma unroll
-  for (int j = 0; j < GROUP; ++j) {
+  for (int j = 0; j < G; ++j) {
     double2 v = warp_sum2(to_d2(acc[j]));
     if (lane == 0) red[warp][j] = v;
   }
@@ -789,12 +789,17 @@ lqcd_status blas_multidot(lqcd_ctx *ctx, const SV *V, long long vstride, long lo
                    ((vrs * (long long)sizeof(SV)) % 16 == 0) && ((n * (long long)sizeof(SW)) % 16 == 0);
   const unsigned grid = (unsigned)((long long)nchunk * ngroup * nrhs);
   kbegin(ctx);
-  if (vec)
-    multidot_kernel<SV, SW, true><<<grid, BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, nchunk, fac,
-                                                               (double2 *)p, cnt, h);
+  // at most two vectors (the Lanczos window): the two-vector form, with a quarter of the registers
+  // for loads and accumulators, so that more blocks are resident to hide the DRAM latency
+  if (vec && nvec <= 2)
+    multidot_kernel<SV, SW, true, 2><<<grid, BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, nchunk, fac,
+                                                                  (double2 *)p, cnt, h);
+  else if (vec)
+    multidot_kernel<SV, SW, true, GROUP><<<grid, BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, nchunk,
+                                                                      fac, (double2 *)p, cnt, h);
   else
-    multidot_kernel<SV, SW, false><<<grid, BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, nchunk, fac,
-                                                                (double2 *)p, cnt, h);
+    multidot_kernel<SV, SW, false, GROUP><<<grid, BT, 0, ctx->stream>>>(V, vstride, vrs, nvec, w, n, nrhs, nchunk,
+                                                                       fac, (double2 *)p, cnt, h);
   // compulsory bytes: every basis vector once (once per right-hand side when the bases differ),
   // every w once
   const double bytes = (double)sizeof(SV) * n * nvec * (vrs != 0 ? nrhs : 1) + (double)sizeof(SW) * n * nrhs;

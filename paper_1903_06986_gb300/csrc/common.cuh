@@ -130,7 +130,7 @@ enum WsSlot {
   WS_PARTIAL = 0, WS_SCAL, WS_TMP0, WS_TMP1, WS_TMP2, WS_TMP3, WS_BASIS, WS_HESS, WS_COEF,
   WS_BASIS2, WS_TMP4, WS_TMP5, WS_EST0, WS_EST1, WS_EST2, WS_PROBE,
   WS_MIX_U, WS_MIX_V, WS_MIX_R32, WS_MIX_E32, WS_MIX_R, WS_MIX_S, WS_COUNT, WS_TUNE, WS_SPEC, WS_NBLK, WS_TC_STAT, WS_TC_B, WS_TC_PART, WS_TC_D,
-  WS_POLY1, WS_POLY2, WS_POLY3, WS_EO, WS_TC_AC, WS_TC_REXP, WS_PROBE_OFF, WS_NSLOTS
+  WS_POLY1, WS_POLY2, WS_POLY3, WS_EO, WS_TC_AC, WS_TC_REXP, WS_PROBE_OFF, WS_HOST_LINKS, WS_NSLOTS
 };
 lqcd_status ws_get(lqcd_ctx *ctx, int slot, size_t bytes, void **ptr);
 void graph_cache_clear(lqcd_ctx *ctx);

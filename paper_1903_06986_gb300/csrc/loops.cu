@@ -1431,6 +1431,18 @@ lqcd_status lqcd_loop_noises(lqcd_loop *L, const double *links, uint32_t first, 
                                 ni.max_true_resid);
 }
 
+lqcd_status lqcd_loop_noises_host(lqcd_loop *L, const double *links_host, uint32_t first, int count,
+                                  double *per_noise_t, lqcd_noise_info *info) {
+  if (!L || !L->ctx) return LQCD_ERR_INVALID_ARG;
+  if (!links_host) return set_err(L->ctx, LQCD_ERR_INVALID_ARG, "loop_noises_host: bad arguments");
+  lqcd_ctx *ctx = L->ctx;
+  const size_t bytes = sizeof(double2) * (size_t)4 * ctx->V * 9;
+  double2 *Ud;
+  LQCD_TRY(ws_get(ctx, WS_HOST_LINKS, bytes, (void **)&Ud));
+  LQCD_CUDA(ctx, cudaMemcpyAsync(Ud, links_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  return lqcd_loop_noises(L, (const double *)Ud, first, count, per_noise_t, info);
+}
+
 lqcd_status lqcd_loop_set_noise_opts(lqcd_loop *L, int prec, double inner_tol, int block) {
   if (!L || !L->ctx) return LQCD_ERR_INVALID_ARG;
   if (prec < LQCD_PREC_F64 || prec > LQCD_PREC_BF16 || !(inner_tol >= 0.0 && inner_tol < 1.0) || block < 0)

@@ -131,6 +131,7 @@ def load(path=None):
         "lqcd_loop_get": [vp, C.POINTER(LoopInfo)],
         "lqcd_loop_set_noise_opts": [vp, i, d, i],
         "lqcd_loop_set_inner_restart": [vp, i],
+        "lqcd_loop_noises_host": [vp, vp, u32, i, vp, C.POINTER(NoiseInfo)],
         "lqcd_loop_destroy": [vp],
         "lqcd_deflate_project": [vp, vp, vp, vp, i, vp],
         "lqcd_set_defl_engine": [vp, i],
@@ -284,6 +285,30 @@ class Loop:
     def set_noise_opts(self, prec, inner_tol=0.0, block=0):
         """Precision (and block width, 0 = unchanged) of the noise solves from now on."""
         self.ctx._check(self.ctx.lib.lqcd_loop_set_noise_opts(self.h, prec, inner_tol, block))
+
+    def noises_host(self, links_host, first, count):
+        """lqcd_loop_noises_host: as noises(), with the gauge field in host memory (a CPU tensor or a
+        numpy array, copied to the device by the call)."""
+        out = np.zeros((NMODES, count, NOPS, self.ctx.dims[3]), dtype=np.complex128)
+        info = NoiseInfo()
+        nlink = 4 * int(np.prod(self.ctx.dims)) * 9
+        if isinstance(links_host, np.ndarray):
+            if links_host.dtype != np.complex128 or not links_host.flags.c_contiguous or links_host.size != nlink:
+                raise ValueError("host links: contiguous complex128, 4 x V x 3 x 3")
+            ptr = links_host.ctypes.data_as(C.c_void_p)
+        else:
+            torch = _torch()
+            if (links_host.is_cuda or links_host.dtype != torch.complex128 or not links_host.is_contiguous()
+                    or links_host.numel() != nlink):
+                raise ValueError("host links: contiguous complex128 CPU tensor, 4 x V x 3 x 3")
+            ptr = C.c_void_p(links_host.data_ptr())
+        st = self.ctx.lib.lqcd_loop_noises_host(self.h, ptr, first, count, out.ctypes.data_as(C.c_void_p),
+                                                C.byref(info))
+        if st not in (OK, ERR_NOT_CONVERGED):
+            self.ctx._check(st)
+        d = info.as_dict()
+        d["status"] = st
+        return out, d
 
     def set_inner_restart(self, m_inner):
         """GMRES-Proj cycle length of the noise solves from now on (0 = m - k)."""

@@ -189,3 +189,35 @@ def test_polynomial_preconditioned_path_independent(system):
         got, want = g["per_noise"][i], ref[mode]["per_noise"]
         scale = np.abs(want).max(axis=0)
         assert np.all(np.abs(got - want) <= TOL * scale), mode
+
+
+def test_hermitian_mixed_lanczos_window_and_host_links():
+    """The headline's noise phase in small: Hermitian path, FP16 inner basis with the Lanczos window
+    in GMRES-Proj(30) cycles inside FP64 defect correction to 1e-10.  Its estimates agree with the
+    plain FP64 noise phase on the same setup within 4 tol ||eta||^2 / sigma_min(M) (two solutions
+    with relative residuals <= tol differ by at most 2 tol ||eta|| / sigma_min, and every operator
+    has norm <= 2); lqcd_loop_noises_host (gauge field in host memory) returns the device call's
+    results bit for bit."""
+    from paper_1903_06986_gb300 import lqcd
+    dims, kappa, seed, n = (2, 2, 2, 4), 0.120, 5, 6
+    U = synth.su3_links(dims, 0.45, 2)
+    ctx = context(dims)
+    Ud = dev(U)
+    tol = 1e-10
+    loop = ctx.loop_setup(Ud, kappa, seed, n, n, 80, 8, 7, 6, tol, 1e-14, m_inner=30, eig_tol=1e-13,
+                          system=lqcd.SYS_MG5)
+    p64, i64 = loop.noises(Ud, 0, n)
+    assert i64["converged"] and i64["max_true_resid"] <= tol
+    ph, ih = loop.noises_host(np.ascontiguousarray(U), 0, n)
+    assert np.array_equal(ph, p64) and ih["matvecs"] == i64["matvecs"]
+    ctx.set_inner_window(2)
+    try:
+        loop.set_noise_opts(lqcd.PREC_F16, 0.1)
+        p16, i16 = loop.noises(Ud, 0, n)
+    finally:
+        ctx.set_inner_window(0)
+    assert i16["converged"] and i16["max_true_resid"] <= tol
+    lam_min = np.abs(loop.info()["lam"]).min()
+    bound = 4 * tol * 12 * L.volume(dims) / lam_min
+    assert np.abs(p16 - p64).max() <= bound
+    loop.close()
