@@ -51,13 +51,17 @@ def _cgs2(V, w):
     return h + h2, w
 
 
-def _arnoldi(A, V, H, j0, m, counter):
-    """Extend A V[:, :m] = V[:, :m+1] H[:m+1, :m] from column j0 (columns < j0 already valid)."""
+def _arnoldi(A, V, H, j0, m, counter, window=0):
+    """Extend A V[:, :m] = V[:, :m+1] H[:m+1, :m] from column j0 (columns < j0 already valid).
+    window > 0 (Hermitian A only): orthogonalise against the last `window` columns; with window 2 this
+    is the three-term Lanczos recurrence of MINRES (Sec. 8), whose other Hessenberg entries vanish
+    in exact arithmetic for Hermitian A, and H is tridiagonal."""
     for j in range(j0, m):
         w = A(V[:, j])
         counter[0] += 1
-        h, w = _cgs2(V[:, :j + 1], w)
-        H[:j + 1, j] = h
+        lo = max(0, j + 1 - window) if window > 0 else 0
+        h, w = _cgs2(V[:, lo:j + 1], w)
+        H[lo:j + 1, j] = h
         nrm = np.linalg.norm(w)
         H[j + 1, j] = nrm
         V[:, j + 1] = w / nrm if nrm > 0 else 0.0
@@ -180,12 +184,12 @@ def ritz_pairs(defl, hermitian=True):
     return lam, E, res
 
 
-def gmres_proj(A, b, defl, m_inner, tol, max_cycles):
+def gmres_proj(A, b, defl, m_inner, tol, max_cycles, window=0):
     """GMRES-Proj for a later right-hand side (Sec. 5.3, 7): alternately (i) minimum-residual
     projection over the deflation space, d = argmin || V_{k+1}^H r - Hbar_k d ||, x += V_k d,
-    r -= V_{k+1} Hbar_k d; and (ii) one GMRES(m_inner) cycle from r.  Stops when the recursive
-    residual is below tol * ||b||, then re-checks with the true residual (continuing from it if
-    the recursion drifted)."""
+    r -= V_{k+1} Hbar_k d; and (ii) one GMRES(m_inner) cycle from r (on the Lanczos recurrence when
+    window = 2 and A is Hermitian, see ``_arnoldi``).  Stops when the recursive residual is below
+    tol * ||b||, then re-checks with the true residual (continuing from it if the recursion drifted)."""
     n = b.shape[0]
     Vk1, Hk = defl["V"], defl["Hbar"]
     k = Hk.shape[1]
@@ -215,7 +219,7 @@ def gmres_proj(A, b, defl, m_inner, tol, max_cycles):
         V = np.zeros((n, m_inner + 1), dtype=np.complex128)
         H = np.zeros((m_inner + 1, m_inner), dtype=np.complex128)
         V[:, 0] = r / beta
-        _arnoldi(A, V, H, 0, m_inner, counter)
+        _arnoldi(A, V, H, 0, m_inner, counter, window)
         c = np.zeros(m_inner + 1, dtype=np.complex128)
         c[0] = beta
         d = np.linalg.lstsq(H, c, rcond=None)[0]

@@ -332,8 +332,9 @@ __global__ void probe_contract_kernel(const double2 *__restrict__ U, double kapp
 // orders k > h are needed only in the taxicab balls of radius K - k around the members: this
 // kernel evaluates (P z)(y) for every y = member + offset (offsets: the ball, as char4 (dx, dy, dz,
 // dt)), reading `in` at the neighbours of y and writing `out` at y alone.  Sites outside the balls
-// keep whatever `out` held; the next order and the contraction never read them.  Two offsets of
-// one ball may name one site on a small torus: both threads then write the same value.
+// keep whatever `out` held; the next order and the contraction never read them.  One site can be
+// named twice (two offsets of one ball on a small torus, or the touching balls of two members):
+// both threads then compute it from the same inputs and store the same value.
 // One thread per (member, offset) pair and probe (blockIdx.y).
 __global__ void __launch_bounds__(128) hop_listed_kernel(const double2 *__restrict__ U, const double2 *__restrict__ in,
                                                          double2 *__restrict__ out, const char4 *__restrict__ offs,

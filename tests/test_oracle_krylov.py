@@ -92,3 +92,38 @@ def test_gmres_proj_uses_deflation(system):
     # plain restarted GMRES(m - k) needs more matrix-vector products
     xr, infor, _ = K.gmres_dr(lambda v: M @ v, b2, m - k, 0, 1e-11, 400)
     assert info["matvecs"] < infor["matvecs"]
+
+
+def test_lanczos_window_on_hermitian_operator(system):
+    """GMRES-Proj on M' = M gamma_5 with the inner cycles on the three-term Lanczos recurrence
+    (window 2, Sec. 8's MINRES): the Hessenberg matrix of a cycle is tridiagonal and equals the full
+    Arnoldi one to rounding (the dropped inner products vanish for a Hermitian operator), the Arnoldi
+    relation holds, and the solve reaches the LU solution within cond * tol.  On the non-Hermitian
+    M the same window changes the cycle: the window relies on hermiticity."""
+    U, M, Mp, b = system
+    n, m = b.shape[0], 16
+    for A, herm in ((Mp, True), (M, False)):
+        Hs, Vs = [], []
+        for window in (0, 2):
+            V = np.zeros((n, m + 1), dtype=np.complex128)
+            H = np.zeros((m + 1, m), dtype=np.complex128)
+            V[:, 0] = b / np.linalg.norm(b)
+            K._arnoldi(lambda v: A @ v, V, H, 0, m, [0], window)
+            assert np.abs(A @ V[:, :m] - V @ H).max() < 1e-12 * np.abs(A).max()
+            Hs.append(H)
+            Vs.append(V)
+        assert np.abs(np.triu(Hs[1], 2)).max() == 0.0
+        diff = np.abs(Hs[1] - Hs[0]).max() / np.abs(Hs[0]).max()
+        if herm:
+            assert diff < 1e-12
+            assert np.abs(Vs[1].conj().T @ Vs[1] - np.eye(m + 1)).max() < 1e-10
+        else:
+            assert diff > 1e-3
+    m_, k = 30, 12
+    _, _, defl = K.gmres_dr(lambda v: Mp @ v, b, m_, k, 1e-13, 300, hermitian=True)
+    b2 = L.flat(rng.z4_noise(5, 3, DIMS))
+    tol = 1e-11
+    x, info = K.gmres_proj(lambda v: Mp @ v, b2, defl, m_ - k, tol, 200, window=2)
+    assert info["converged"]
+    xe = np.linalg.solve(Mp, b2)
+    assert np.linalg.norm(x - xe) <= 10 * np.linalg.cond(Mp) * tol * np.linalg.norm(xe)
