@@ -26,7 +26,7 @@ from tests.gpu_util import context, dev, torch_cuda
 pytestmark = pytest.mark.gpu
 
 MODES = E.MODES
-TOL = 1e-11     # relative parity of loop estimates (spec target for FP64)
+TOL = 1e-11     # relative parity of loop estimates (the FP64 target of the whole path)
 NTOL = 3e-14    # noise solves: two solutions within cond(M) * 2 NTOL of each other (cond(M) <= 18 in these
                 # cases, which keeps 3e-14 above the rounding floor ~ eps cond(M) of a true residual)
 
