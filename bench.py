@@ -95,9 +95,31 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def link_seed(rank):
+    """Seed of the gauge configuration of a rank: every rank works on its own configuration."""
+    return LINK_SEED + rank
+
+
 def make_links(rank):
     from paper_1903_06986_gb300 import synth
-    return synth.su3_links(DIMS, LINK_EPS, LINK_SEED + rank)
+    return synth.su3_links(DIMS, LINK_EPS, link_seed(rank))
+
+
+def reduce_max_over_ranks(t, world, device):
+    """The largest t over the ranks of the job (t itself on one rank): a timed region ends when its
+    slowest rank ends.  device: where the collective's tensor lives ("cuda" for NCCL, "cpu" for gloo)."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    v = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
+
+
+def job_rate(units_per_rank, world, t_max):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / t_max
 
 
 # ---------------------------------------------------------------- clocks during the timed region
@@ -693,11 +715,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(t):
-        if world > 1:
-            v = torch.tensor([t], device="cuda")
-            torch.distributed.all_reduce(v, op=torch.distributed.ReduceOp.MAX)
-            return float(v.item())
-        return t
+        return reduce_max_over_ranks(t, world, "cuda")
 
     U = make_links(rank)
     ctx = lqcd.Context(DIMS, recon=12)        # the synthetic links are SU(3)
@@ -747,7 +765,7 @@ def main():
     clk = clocks.stop()
     launches = ctx.launches - launches0
     t_max = max_over_ranks(t_dev)
-    value = BLOCK * args.steps * world / t_max
+    value = job_rate(BLOCK * args.steps, world, t_max)
     per_noise_s = t_max / (BLOCK * args.steps)
 
     # ---- kernel-class breakdown of one more step (per-launch events on; not part of the value)
@@ -805,7 +823,7 @@ def main():
         step(args.warmup + i, "fp16", Uh)
     barrier()
     t_e2e = max_over_ranks(time.perf_counter() - e0)
-    e2e_value = BLOCK * e2e_steps * world / t_e2e
+    e2e_value = job_rate(BLOCK * e2e_steps, world, t_e2e)
 
     # ---- roofline of the dominant kernel class of the FP16 noise phase
     dom = max(tm, key=lambda k: tm[k][0])
