@@ -219,6 +219,22 @@ def oracle_sample(U):
     return rate, sample, time.perf_counter() - t_start
 
 
+def oracle_sample_threads(threads, timeout=600):
+    """The same bounded oracle sample in a child process whose BLAS / OpenMP pools are limited to
+    `threads` (set before numpy loads): (rate, seconds), or None if the child failed."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "r, s, dt = bench.oracle_sample(bench.make_links(0)); print(json.dumps([r, dt]))" % ROOT)
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[var] = str(threads)
+    try:
+        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=timeout)
+        rate, dt = json.loads(p.stdout.strip().splitlines()[-1])
+        return float(rate), float(dt)
+    except Exception:
+        return None
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -881,6 +897,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, sample, _ = oracle_sample(U)
         cpu = {"value": rate, "unit": "estimates/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample}
+        one = oracle_sample_threads(1)
+        cpu["one_thread"] = None if one is None else {"value": one[0], "unit": "estimates/s", "cores": 1,
+                                                     "sample_s": one[1],
+                                                     "how": "the same sample in a child process with its "
+                                                            "BLAS / OpenMP thread pools set to 1"}
 
     if rank == 0:
         line = {"metric": "deflated loop estimates/s at 1e-10 true residual", "value": value, "unit": "estimates/s",
