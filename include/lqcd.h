@@ -347,6 +347,12 @@ lqcd_status lqcd_hop_traces(lqcd_ctx *ctx, const double *links, double kappa, in
  * minimise the site updates (default).  LQCD_ERR_INVALID_ARG for values outside 0..64. */
 lqcd_status lqcd_set_probe_depth(lqcd_ctx *ctx, int depth);
 
+/* The depth lqcd_hop_traces uses (host only; needs no GPU and no context): for an Lx x Ly x Lz x Lt
+ * torus (dims[0..3], each in 2..1024), K terms and a fixed depth as lqcd_set_probe_depth sets it
+ * (0 = by cost), *depth receives the number of full applications of P per probe.
+ * LQCD_ERR_INVALID_ARG for bad arguments. */
+lqcd_status lqcd_probe_depth(const int dims[4], int K, int fixed, int *depth);
+
 /* The colour classes lqcd_hop_traces probes with (host only; needs no GPU and no context): for an
  * Lx x Ly x Lz x Lt torus (dims[0..3], each >= 2) and K >= 1 terms, *nclasses receives the class
  * count and, when classes is not NULL, classes[s] (host, V ints; s = x + Lx (y + Ly (z + Lz t)))

@@ -418,10 +418,10 @@ static constexpr int PROBE_MAX_RADIUS = 8;
 // full application, every order above it a local completion (hop_listed_kernel).  Chosen to
 // minimise the site updates per probe, depth + sum_{k > depth} min(1, members x |ball| / V), unless
 // the context fixes it (lqcd_set_probe_depth).
-static int probe_depth(const lqcd_ctx *ctx, const Colouring &col, int K) {
+static int probe_depth_for(int fixed, const Colouring &col, int K) {
   if (K <= 2) return K - 1;
   // a fixed depth still keeps every completion ball within PROBE_MAX_RADIUS
-  if (ctx->probe_depth > 0) return std::min(std::max(ctx->probe_depth, K - 1 - PROBE_MAX_RADIUS), K - 1);
+  if (fixed > 0) return std::min(std::max(fixed, K - 1 - PROBE_MAX_RADIUS), K - 1);
   const double per_member = (double)col.ncls;  // sites per class member
   int best = K - 1;
   double best_cost = (double)(K - 1);
@@ -434,7 +434,14 @@ static int probe_depth(const lqcd_ctx *ctx, const Colouring &col, int K) {
       best = h;
     }
   }
+  // orders whose ball holds at least a member's share of the lattice run in full anyway: count them
+  // in the depth, so that it is the number of full applications
+  while (best < K - 1 && (double)taxicab_ball(completion_radius(K, best + 1)).size() >= per_member) ++best;
   return best;
+}
+
+static int probe_depth(const lqcd_ctx *ctx, const Colouring &col, int K) {
+  return probe_depth_for(ctx->probe_depth, col, K);
 }
 
 template <typename T>
@@ -824,6 +831,14 @@ lqcd_status lqcd_probe_classes(const int dims[4], int K, int *nclasses, int *cla
         for (int y = 0; y < dims[1]; ++y)
           for (int x = 0; x < dims[0]; ++x) classes[s++] = class_of(c, x, y, z, t);
   }
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_probe_depth(const int dims[4], int K, int fixed, int *depth) {
+  if (!dims || !depth || K < 1 || K > 64 || fixed < 0 || fixed > 64) return LQCD_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2 || dims[i] > 1024) return LQCD_ERR_INVALID_ARG;
+  *depth = probe_depth_for(fixed, choose_colouring(dims, K), K);
   return LQCD_OK;
 }
 

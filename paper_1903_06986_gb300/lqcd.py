@@ -162,6 +162,7 @@ def load(path=None):
         "lqcd_eo_reconstruct": [vp, vp, d, vp, vp, vp, i],
         "lqcd_eo_full_eigenpairs": [vp, vp, d, vp, vp, i, d, vp, vp],
         "lqcd_probe_classes": [C.POINTER(C.c_int), i, C.POINTER(C.c_int), vp],
+        "lqcd_probe_depth": [C.POINTER(C.c_int), i, i, C.POINTER(C.c_int)],
         "lqcd_autotune_block": [vp, vp, d, vp, C.POINTER(KrylovOpts), C.POINTER(C.c_int), i, C.POINTER(C.c_int),
                                 C.POINTER(C.c_double)],
         "lqcd_batch_loop_estimate": [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(d), C.POINTER(EstOpts),
@@ -782,6 +783,17 @@ def probe_classes(dims, K):
     if st != OK:
         raise LqcdError(st, "probe_classes: bad arguments")
     return n.value, cls.reshape(dims[3], dims[2], dims[1], dims[0])
+
+
+def probe_depth(dims, K, fixed=0):
+    """lqcd_probe_depth (host only): full applications of P per probe that lqcd_hop_traces uses."""
+    lib = load()
+    d = (C.c_int * 4)(*dims)
+    out = C.c_int()
+    st = lib.lqcd_probe_depth(d, K, fixed, C.byref(out))
+    if st != OK:
+        raise LqcdError(st, "probe_depth: bad arguments")
+    return out.value
 
 
 def _estimate_buffers(lt, nnoise, k, npoly):

@@ -61,3 +61,50 @@ def test_bad_arguments_are_rejected():
         lqcd.probe_classes((1, 4, 4, 4), 3)
     with pytest.raises(lqcd.LqcdError):
         lqcd.probe_classes((4, 4, 4, 4), 0)
+
+
+def ball_size(r):
+    """Number of points of Z^4 within taxicab distance r (counted directly)."""
+    rng_ = np.arange(-r, r + 1)
+    g = np.stack(np.meshgrid(rng_, rng_, rng_, rng_, indexing="ij"), axis=-1)
+    return int((np.abs(g).sum(axis=-1) <= r).sum())
+
+
+def site_updates(h, K, per_member):
+    """Site updates per probe and lattice volume of the meet-in-the-middle traces at depth h: h full
+    applications, then order k evaluated within max(1, K - k) hops of each class member (or in full
+    where that ball holds more sites than a member's share of the lattice)."""
+    return h + sum(min(1.0, ball_size(max(1, K - k)) / per_member) for k in range(h + 1, K))
+
+
+@pytest.mark.parametrize("dims,K,expect", [((24, 24, 24, 32), 7, 2), ((8, 8, 8, 16), 7, 2), ((16, 16, 16, 32), 7, 2),
+                                           ((12, 12, 12, 24), 7, None), ((2, 2, 2, 4), 7, None), ((4, 4, 4, 4), 5, None),
+                                           ((8, 4, 4, 8), 3, 1), ((6, 6, 6, 6), 2, 1), ((3, 3, 3, 6), 1, 0)])
+def test_probe_depth_minimises_site_updates(dims, K, expect):
+    """The depth of the hopping traces (meet in the middle, Sec. 5.1 add-back): a depth of least site
+    updates per probe, every completion ball within 8 hops, the first order above it a real local
+    completion (its ball smaller than a member's share of the lattice): the depth counts the full
+    applications, 2 of the 6 orders at K = 7 with 512 classes."""
+    depth = lqcd.probe_depth(dims, K)
+    if expect is not None:
+        assert depth == expect
+    if K <= 2:
+        assert depth == K - 1
+        return
+    ncls, _ = lqcd.probe_classes(dims, K)
+    costs = {h: site_updates(h, K, ncls) for h in range(1, K) if max(1, K - h - 1) <= 8}
+    best = min(costs.values())
+    assert costs[depth] <= best + 1e-9
+    if depth < K - 1:
+        assert ball_size(max(1, K - depth - 1)) < ncls
+
+
+def test_probe_depth_fixed_values():
+    """A fixed depth is capped at K - 1 and raised where a completion would reach beyond 8 hops."""
+    assert lqcd.probe_depth((8, 8, 8, 16), 7, fixed=1) == 1
+    assert lqcd.probe_depth((8, 8, 8, 16), 7, fixed=9) == 6
+    assert lqcd.probe_depth((16, 16, 16, 32), 20, fixed=1) == 11
+    with pytest.raises(lqcd.LqcdError):
+        lqcd.probe_depth((8, 8, 8, 16), 7, fixed=-1)
+    with pytest.raises(lqcd.LqcdError):
+        lqcd.probe_depth((1, 8, 8, 16), 7)
