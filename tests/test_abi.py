@@ -50,6 +50,11 @@ def test_new_entry_points_reject_bad_arguments_without_cuda(lib):
     v = ctypes.c_double()
     assert lib.lqcd_timing_bytes(None, 0, ctypes.byref(v)) == lqcd.ERR_INVALID_ARG
     assert lqcd.KERNEL_CLASSES[9:] == ["tensor", "slice"]
+    # the probe depth, the Lanczos window and the loop's inner restart and host-links entry points
+    assert lib.lqcd_set_probe_depth(None, 2) == lqcd.ERR_INVALID_ARG
+    assert lib.lqcd_set_inner_window(None, 2) == lqcd.ERR_INVALID_ARG
+    assert lib.lqcd_loop_set_inner_restart(None, 80) == lqcd.ERR_INVALID_ARG
+    assert lib.lqcd_loop_noises_host(None, None, 0, 1, None, None) == lqcd.ERR_INVALID_ARG
 
 
 def test_tc_slice_bytes_host_query(lib):
